@@ -1,0 +1,255 @@
+/*
+ * iluk.h -- C ABI of libiluk: ILU(k) preconditioning for sparse non-symmetric
+ * Ax = b on one NVIDIA GB300 (sm_103a), after Dong & Cooperman, "A
+ * Bit-Compatible Shared Memory Parallelization for ILU(k) Preconditioning and
+ * a Bit-Compatible Generalization to Distributed Memory" (arXiv 0803.0048).
+ *
+ * The calls follow the paper's statement of the problem (Sec. 2): a symbolic
+ * phase that fixes the level-k pattern, a numeric phase that fills in the
+ * values of the incomplete factors, a triangular solve L~U~y = p applied in
+ * every iteration of a Krylov solver, and the optional level-based incomplete
+ * inverse (TPIILU, Sec. 3.5) that turns that solve into two sparse mat-vecs.
+ *
+ * General conventions (all entry points):
+ *  - Matrices are CSR, 0-based: rowptr int64[n+1] (rowptr[0] = 0,
+ *    non-decreasing), colind int32[nnz] strictly ascending inside each row,
+ *    values double[nnz].  An entry stored in the CSR arrays counts as
+ *    structurally non-zero whatever its value.
+ *  - Pointers named in these signatures are DEVICE pointers unless the
+ *    comment says "host".  They are borrowed for the duration of the call (or,
+ *    for asynchronous calls, until the stream reaches the work).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  All device work of a call is ordered on that stream.
+ *  - Handles (iluk_sym, iluk_fac, iiluk) own the device memory they allocate
+ *    (stream-ordered cudaMallocAsync on the creating call's stream) until the
+ *    matching *_destroy.  A handle must not be used concurrently from two
+ *    streams: the sweeps keep per-handle scratch (flags, an intermediate
+ *    vector) inside it.
+ *  - Return value: an iluk_status.  Calls documented as "synchronous"
+ *    synchronize `stream` before returning and also fill `info` (may be NULL).
+ *    Calls documented as "asynchronous" only enqueue work; device-side errors
+ *    they meet (a bounded wait that gave up) are recorded in the handle and
+ *    returned by the next synchronous call on it, or by iluk_fac_status().
+ *  - No call traps or aborts the GPU on bad input: every device-side check
+ *    records a status and the kernels return.  Every wait of one row on
+ *    another is bounded (iluk_set_wait_limit); running out returns
+ *    ILUK_ETIMEOUT.
+ *  - Floating point: every kernel computes in IEEE double with one rounding
+ *    per multiply and per add (no fused multiply-add) and correctly rounded
+ *    division and square root, in the sequential per-entry order of the
+ *    method, so the results are bit-identical to a sequential run.
+ */
+#ifndef ILUK_H
+#define ILUK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  ILUK_OK = 0,
+  ILUK_EINVAL = 1,      /* bad argument (n < 0, k out of range, NULL pointer, ...)      */
+  ILUK_EPATTERN = 2,    /* unsorted / duplicate / out-of-range column, bad rowptr       */
+  ILUK_ENODIAG = 3,     /* a row has no diagonal entry after the symbolic phase         */
+  ILUK_EZEROPIVOT = 4,  /* a diagonal u_ii of the factors is exactly 0.0                */
+  ILUK_ENONFINITE = 5,  /* a matrix value is NaN or infinite                            */
+  ILUK_ENOMEM = 6,      /* device allocation failed or a row exceeds the supported size */
+  ILUK_ETIMEOUT = 7,    /* a bounded wait on another row's completion gave up           */
+  ILUK_ENOCONV = 8,     /* GMRES reached maxit without meeting rtol                     */
+  ILUK_ECUDA = 9        /* a CUDA runtime call failed                                   */
+} iluk_status;
+
+/* Sparsity pattern of A (device arrays). */
+typedef struct {
+  int64_t n;
+  int64_t nnz;
+  const int64_t *rowptr;  /* int64[n+1] */
+  const int32_t *colind;  /* int32[nnz] */
+} iluk_pattern;
+
+/* Result details of a synchronous call. */
+typedef struct {
+  int32_t status;   /* same as the return value                                    */
+  int32_t iters;    /* GMRES: Arnoldi steps taken                                  */
+  int64_t row;      /* first failing row (sequential order), or -1                 */
+  double relres;    /* GMRES: true ||b - Ax|| / ||b|| at exit                      */
+  int64_t need;     /* ILUK_ENOMEM: bytes or entries that were needed (if known)   */
+  int32_t cycles;   /* GMRES: restart cycles started                               */
+  int32_t reserved;
+} iluk_info;
+
+/* Read-only view of a symbolic result (device pointers borrowed from S). */
+typedef struct {
+  int64_t n;
+  int64_t nnz;              /* entries of F = L~ + U~ (diagonal in U~)              */
+  const int64_t *rowptr;    /* int64[n+1]                                          */
+  const int32_t *colind;    /* int32[nnz], sorted within rows                       */
+  const uint8_t *level;     /* uint8[nnz], level of fill of each entry (Def. 2.3)   */
+  const int64_t *diag;      /* int64[n], position of (i,i) in colind                */
+  const int32_t *a2f;       /* int32[nnz_A], offset of A's entry inside its F row   */
+  int32_t max_row;          /* longest row of F                                    */
+  int32_t depth_lower;      /* longest dependency chain of the forward sweep       */
+  int32_t depth_upper;      /* longest dependency chain of the backward sweep      */
+  int32_t k;
+} iluk_sym_view;
+
+typedef struct iluk_sym iluk_sym;  /* symbolic result: pattern of F and levels */
+typedef struct iluk_fac iluk_fac;  /* numeric factors L~, U~ on that pattern   */
+typedef struct iiluk iiluk;        /* TPIILU incomplete inverses              */
+
+enum { ILUK_PREC_NONE = 0, ILUK_PREC_ILU = 1, ILUK_PREC_IILU = 2 };
+enum { ILUK_SCHED_AUTO = 0, ILUK_SCHED_FLAGS = 1, ILUK_SCHED_SINGLE_CTA = 2 };
+
+const char *iluk_strerror(int status);
+
+/* Upper bound, in nanoseconds, on any single wait of a row for another row's
+ * completion inside the kernels (default 20 s).  Host-side setting for the
+ * whole process; returns the previous value. */
+int64_t iluk_set_wait_limit(int64_t ns);
+
+/* Test hook for the bounded-wait path: the factorization row `row` (-1 = none)
+ * finishes its work but never publishes its completion, so every row that
+ * depends on it runs out its wait and the call returns ILUK_ETIMEOUT.  Returns
+ * the previous value.  Host-side, whole process. */
+int64_t iluk_debug_hold_row(int64_t row);
+
+/*
+ * a1. Pattern check (sparse storage, Sec. 2.1).  Synchronous.
+ * Checks rowptr[0] = 0, rowptr non-decreasing, rowptr[n] = nnz, every column in
+ * [0, n) and strictly ascending inside its row.  ILUK_EPATTERN with the
+ * smallest failing row in info->row.
+ */
+int iluk_validate(const iluk_pattern *A, iluk_info *info, void *stream);
+
+/*
+ * a2. Symbolic factorization, Phase I (Algorithm 1, Sec. 2.2) with the level
+ * of fill of Def. 2.3: level(i,j) = 0 for stored a_ij, otherwise
+ * min_{h < min(i,j)} level(i,h) + level(h,j) + 1; entries of level <= k are
+ * kept.  0 <= k <= 250.  Synchronous.  Validates A first (as iluk_validate).
+ * On success *S receives a new handle holding F's pattern, the levels, the
+ * diagonal positions and the A->F position map.  ILUK_ENODIAG (row in
+ * info->row) when some row of F lacks its diagonal.  A is only read; it may be
+ * freed after the call.
+ */
+int iluk_symbolic(const iluk_pattern *A, int k, iluk_sym **S, iluk_info *info, void *stream);
+int iluk_sym_query(const iluk_sym *S, iluk_sym_view *view);
+/* Longest dependency chains of the forward and backward sweeps over F's
+ * pattern (the number of rows on the critical path of each sweep).  Computed
+ * on first call (synchronous), cached in S afterwards. */
+int iluk_sym_depth(iluk_sym *S, int32_t *depth_lower, int32_t *depth_upper, void *stream);
+/* Copy S's arrays into caller-owned device buffers (any pointer may be NULL
+ * to skip that array).  Asynchronous. */
+int iluk_sym_export(const iluk_sym *S, int64_t *rowptr, int32_t *colind, uint8_t *level,
+                    int64_t *diag, void *stream);
+void iluk_sym_destroy(iluk_sym *S);
+
+/*
+ * a3. Numeric factorization, Phase II, row-wise IKJ elimination (Eq. 1;
+ * Eqs. lufactor2, lufactor of Sec. 3.5): F starts as A on F's pattern (fill
+ * positions +0.0); for each row i and each h in L(i) ascending,
+ * f_ih <- f_ih / f_hh, then f_ij <- f_ij - f_ih * f_hj for every j > h stored
+ * in both rows.  A_val: device double[nnz_A] in S's A pattern order.
+ * Synchronous.  *F receives a new handle (it refers to S, which must outlive
+ * it).  ILUK_EZEROPIVOT / ILUK_ENONFINITE with the first failing row.
+ */
+int iluk_numeric(const iluk_sym *S, const double *A_val, iluk_fac **F, iluk_info *info,
+                 void *stream);
+/* Re-run the numeric phase into an existing handle with new values. */
+int iluk_refactor(iluk_fac *F, const double *A_val, iluk_info *info, void *stream);
+/* Device pointer to the factor values (double[nnz_F], F's pattern order). */
+int iluk_fac_values(const iluk_fac *F, const double **val);
+/* Copy the factor values into a caller-owned device buffer double[nnz_F].
+ * Asynchronous. */
+int iluk_fac_export(const iluk_fac *F, double *val, void *stream);
+/* Status recorded by asynchronous calls on F since the last query; clears it. */
+int iluk_fac_status(iluk_fac *F, iluk_info *info, void *stream);
+void iluk_fac_destroy(iluk_fac *F);
+
+/*
+ * a4. Preconditioner application (Eq. triangleSolve): y = (L~U~)^-1 p by a
+ * forward sweep x_i = p_i - sum_{h<i} f_ih x_h (Eq. forwardsubA, h ascending)
+ * and a backward sweep y_i = (x_i - sum_{j>i} f_ij y_j) / f_ii (j ascending).
+ * With transpose != 0: y = (L~U~)^-T p = L~^-T U~^-T p on the explicit
+ * transpose of F (built on the first transposed call; make that first call
+ * outside any stream capture).  p, y: device double[n]; p and y may alias.
+ * Asynchronous.  `sched` picks the schedule (ILUK_SCHED_*).
+ */
+int iluk_apply(iluk_fac *F, const double *p, double *y, int transpose, void *stream);
+int iluk_apply_sched(iluk_fac *F, const double *p, double *y, int transpose, int sched,
+                     void *stream);
+/* Fix the sweep schedule of F (ILUK_SCHED_AUTO lets the first application
+ * outside a stream capture time both schedules and keep the faster one). */
+int iluk_set_schedule(iluk_fac *F, int sched);
+int iluk_get_schedule(const iluk_fac *F);
+
+/*
+ * a5. TPIILU (Sec. 3.5).  Build: beta_it = f_it - sum_{t<h<i} f_ih beta_ht on
+ * F's lower pattern (Eq. inversedefine, h ascending), and the mirror image
+ * gamma_it = u^_it - sum_{i<h<t} u^_ih gamma_ht with u^_it = u_it / u_ii on the
+ * strictly upper pattern (rows last to first, h descending).  The result g is
+ * aligned with F: -beta on lower positions, -gamma on strictly upper positions,
+ * u_ii on the diagonal.  Synchronous; *M receives a new handle that refers to
+ * F's symbolic handle.
+ * Apply: y = (I + G_U) D^-1 (I + G_L) p, each row summed left to right with the
+ * own term added last.  Asynchronous.
+ */
+int iiluk_build(const iluk_fac *F, iiluk **M, iluk_info *info, void *stream);
+int iiluk_values(const iiluk *M, const double **g);
+/* Copy g into a caller-owned device buffer double[nnz_F].  Asynchronous. */
+int iiluk_export(const iiluk *M, double *g, void *stream);
+int iiluk_apply(const iiluk *M, const double *p, double *y, void *stream);
+void iiluk_destroy(iiluk *M);
+
+/*
+ * Sparse mat-vec y = A x (transpose = 0; each row summed left to right from
+ * +0.0) on A's pattern and values.  Asynchronous.
+ */
+int iluk_spmv(const iluk_pattern *A, const double *A_val, const double *x, double *y,
+              void *stream);
+
+/*
+ * Fixed-order inner product: 4096 partial sums, partial p summing i = p,
+ * p+4096, ... left to right from +0.0, then the pairwise tree
+ * s[p] += s[p+w] for w = 2048, ..., 1.  out: device double[1].  Asynchronous.
+ */
+int iluk_dot(int64_t n, const double *x, const double *y, double *out, void *stream);
+
+/*
+ * a6. Restarted GMRES(m), right preconditioned (the solver works with
+ * A M^-1, Sec. 2), x0 = 0, modified Gram-Schmidt with the fixed-order inner
+ * product above, Givens rotations.  Stops when |g_{j+1}| / ||b|| <= rtol and
+ * the true residual ||b - Ax|| / ||b|| confirms it at the end of the cycle.
+ * prec_kind: ILUK_PREC_NONE (prec ignored), ILUK_PREC_ILU (prec = iluk_fac*),
+ * ILUK_PREC_IILU (prec = iiluk*).  transpose != 0 solves A^T x = b with
+ * M^-T (ILU only).  b, x: device double[n].  maxit bounds the total number of
+ * Arnoldi steps.  Synchronous; ILUK_ENOCONV when maxit is reached.
+ */
+int gmres_solve(const iluk_pattern *A, const double *A_val, int prec_kind, void *prec,
+                const double *b, double *x, int restart, double rtol, int maxit,
+                int transpose, iluk_info *info, void *stream);
+
+/*
+ * a8 helper. Gradient of a loss through x = A^-1 b with respect to the stored
+ * entries of A: gA[p] = -lambda_i * x_j for entry p = (i, j), where lambda
+ * solves A^T lambda = dL/dx.  Asynchronous.
+ */
+int iluk_adjoint_scatter(const iluk_pattern *A, const double *lambda, const double *x,
+                         double *gA, void *stream);
+
+/*
+ * a7. Batched numeric factorization: nbatch value sets on one pattern.
+ * A_vals: device double[nbatch * nnz_A] (set-major); F_vals: device
+ * double[nbatch * nnz_F].  One persistent launch.  Every set's factors are
+ * bit-identical to iluk_numeric on that set.  infos: host iluk_info[nbatch]
+ * (may be NULL).  Synchronous; returns the first failing set's status.
+ */
+int iluk_numeric_batched(const iluk_sym *S, int64_t nbatch, const double *A_vals,
+                         double *F_vals, iluk_info *infos, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ILUK_H */

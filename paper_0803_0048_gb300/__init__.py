@@ -1,0 +1,15 @@
+"""ILU(k) preconditioning for sparse non-symmetric Ax = b on one GB300.
+
+After Dong & Cooperman, "A Bit-Compatible Shared Memory Parallelization for
+ILU(k) Preconditioning and a Bit-Compatible Generalization to Distributed
+Memory" (arXiv 0803.0048).  The work runs in libiluk.so (CUDA, sm_103a,
+declared in include/iluk.h); this package is its thin Python binding.
+"""
+from . import _lib
+from .api import (CsrPattern, Factors, IlukError, IncompleteInverse, Symbolic, adjoint_scatter,
+                  debug_hold_row, dot, gmres, iiluk_build, numeric, numeric_batched,
+                  set_wait_limit, spmv, symbolic, validate)
+
+__all__ = ["CsrPattern", "Factors", "IlukError", "IncompleteInverse", "Symbolic",
+           "adjoint_scatter", "debug_hold_row", "dot", "gmres", "iiluk_build", "numeric",
+           "numeric_batched", "set_wait_limit", "spmv", "symbolic", "validate"]

@@ -1,0 +1,276 @@
+"""Python binding of libiluk with torch tensors (same names as the C ABI).
+
+PyTorch provides device memory and the current CUDA stream; every step of
+the method runs in the library's kernels.  All tensors must live on the
+current CUDA device: CSR row pointers int64, column indices int32, values and
+vectors float64.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from typing import Optional, Tuple
+
+import torch
+
+from . import _lib as L
+
+
+class IlukError(RuntimeError):
+    def __init__(self, status: int, info: Optional[L.Info] = None, what: str = ""):
+        lib = L.load()
+        msg = lib.iluk_strerror(status).decode()
+        row = info.row if info is not None else -1
+        super().__init__(f"{what}: {msg} (status {status}, row {row})")
+        self.status = status
+        self.row = row
+        self.info = info
+
+
+def _stream() -> int:
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _check_dev(*ts):
+    for t in ts:
+        if t is not None and not t.is_cuda:
+            raise ValueError("tensors must be on a CUDA device")
+        if t is not None and not t.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+
+
+def _call(fn, *args, info=None, what=""):
+    st = fn(*args)
+    if st != L.OK:
+        raise IlukError(st, info, what or fn.__name__)
+    return st
+
+
+class CsrPattern:
+    """A CSR pattern on the device, plus the C struct that points at it."""
+
+    def __init__(self, rowptr: torch.Tensor, colind: torch.Tensor):
+        _check_dev(rowptr, colind)
+        assert rowptr.dtype == torch.int64 and colind.dtype == torch.int32
+        self.rowptr, self.colind = rowptr, colind
+        self.n = rowptr.numel() - 1
+        self.nnz = colind.numel()
+        self.c = L.Pattern(self.n, self.nnz, rowptr.data_ptr(), colind.data_ptr())
+
+    @property
+    def ref(self):
+        return C.byref(self.c)
+
+
+def validate(rowptr: torch.Tensor, colind: torch.Tensor) -> Tuple[int, int]:
+    """a1: returns (status, first bad row)."""
+    A = CsrPattern(rowptr, colind)
+    info = L.Info()
+    st = L.load().iluk_validate(A.ref, C.byref(info), C.c_void_p(_stream()))
+    return st, info.row
+
+
+class Symbolic:
+    """Result of the symbolic phase (pattern of F = L~ + U~ and levels)."""
+
+    def __init__(self, handle, A: CsrPattern, k: int):
+        self.h = handle
+        self.A = A
+        self.k = k
+        v = L.SymView()
+        L.load().iluk_sym_query(self.h, C.byref(v))
+        self.n, self.nnz, self.max_row = v.n, v.nnz, v.max_row
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            torch.cuda.synchronize()
+            L.load().iluk_sym_destroy(self.h)
+            self.h = None
+
+    def pattern(self):
+        """(rowptr int64, colind int32, level uint8, diag int64) device copies."""
+        dev = self.A.rowptr.device
+        rp = torch.empty(self.n + 1, dtype=torch.int64, device=dev)
+        ci = torch.empty(self.nnz, dtype=torch.int32, device=dev)
+        lv = torch.empty(self.nnz, dtype=torch.uint8, device=dev)
+        dg = torch.empty(self.n, dtype=torch.int64, device=dev)
+        _call(L.load().iluk_sym_export, self.h, _ptr(rp), _ptr(ci), _ptr(lv), _ptr(dg),
+              C.c_void_p(_stream()))
+        return rp, ci, lv, dg
+
+    def depth(self) -> Tuple[int, int]:
+        dl, du = C.c_int32(), C.c_int32()
+        _call(L.load().iluk_sym_depth, self.h, C.byref(dl), C.byref(du), C.c_void_p(_stream()))
+        return dl.value, du.value
+
+
+def symbolic(rowptr: torch.Tensor, colind: torch.Tensor, k: int) -> Symbolic:
+    """a2: symbolic ILU(k) (Algorithm 1 with the levels of Def. 2.3)."""
+    A = CsrPattern(rowptr, colind)
+    h = C.c_void_p()
+    info = L.Info()
+    _call(L.load().iluk_symbolic, A.ref, int(k), C.byref(h), C.byref(info),
+          C.c_void_p(_stream()), info=info, what="iluk_symbolic")
+    return Symbolic(h, A, k)
+
+
+class Factors:
+    """Numeric ILU(k) factors on a symbolic pattern."""
+
+    def __init__(self, handle, S: Symbolic):
+        self.h = handle
+        self.S = S
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            torch.cuda.synchronize()
+            L.load().iluk_fac_destroy(self.h)
+            self.h = None
+
+    def values(self) -> torch.Tensor:
+        out = torch.empty(self.S.nnz, dtype=torch.float64, device=self.S.A.rowptr.device)
+        _call(L.load().iluk_fac_export, self.h, _ptr(out), C.c_void_p(_stream()))
+        return out
+
+    def refactor(self, vals: torch.Tensor) -> None:
+        _check_dev(vals)
+        info = L.Info()
+        _call(L.load().iluk_refactor, self.h, _ptr(vals), C.byref(info), C.c_void_p(_stream()),
+              info=info, what="iluk_refactor")
+
+    def apply(self, p: torch.Tensor, out: Optional[torch.Tensor] = None, transpose: bool = False,
+              sched: int = L.SCHED_AUTO) -> torch.Tensor:
+        """a4: y = (L~U~)^-1 p (or ^-T)."""
+        _check_dev(p)
+        y = torch.empty_like(p) if out is None else out
+        _call(L.load().iluk_apply_sched, self.h, _ptr(p), _ptr(y), int(transpose), int(sched),
+              C.c_void_p(_stream()))
+        return y
+
+    def status(self) -> int:
+        info = L.Info()
+        return L.load().iluk_fac_status(self.h, C.byref(info), C.c_void_p(_stream()))
+
+    def set_schedule(self, sched: int) -> None:
+        _call(L.load().iluk_set_schedule, self.h, int(sched))
+
+    def schedule(self) -> int:
+        return L.load().iluk_get_schedule(self.h)
+
+
+def numeric(S: Symbolic, vals: torch.Tensor) -> Factors:
+    """a3: numeric IKJ factorization (Eq. 1)."""
+    _check_dev(vals)
+    assert vals.dtype == torch.float64 and vals.numel() == S.A.nnz
+    h = C.c_void_p()
+    info = L.Info()
+    _call(L.load().iluk_numeric, S.h, _ptr(vals), C.byref(h), C.byref(info),
+          C.c_void_p(_stream()), info=info, what="iluk_numeric")
+    return Factors(h, S)
+
+
+class IncompleteInverse:
+    """TPIILU level-based incomplete inverses (Sec. 3.5)."""
+
+    def __init__(self, handle, F: Factors):
+        self.h = handle
+        self.F = F
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            torch.cuda.synchronize()
+            L.load().iiluk_destroy(self.h)
+            self.h = None
+
+    def values(self) -> torch.Tensor:
+        out = torch.empty(self.F.S.nnz, dtype=torch.float64, device=self.F.S.A.rowptr.device)
+        _call(L.load().iiluk_export, self.h, _ptr(out), C.c_void_p(_stream()))
+        return out
+
+    def apply(self, p: torch.Tensor, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        _check_dev(p)
+        y = torch.empty_like(p) if out is None else out
+        _call(L.load().iiluk_apply, self.h, _ptr(p), _ptr(y), C.c_void_p(_stream()))
+        return y
+
+
+def iiluk_build(F: Factors) -> IncompleteInverse:
+    """a5: build the TPIILU incomplete inverses from the factors."""
+    h = C.c_void_p()
+    info = L.Info()
+    _call(L.load().iiluk_build, F.h, C.byref(h), C.byref(info), C.c_void_p(_stream()),
+          info=info, what="iiluk_build")
+    return IncompleteInverse(h, F)
+
+
+def spmv(rowptr, colind, vals, x, out=None):
+    A = CsrPattern(rowptr, colind)
+    _check_dev(vals, x)
+    y = torch.empty_like(x) if out is None else out
+    _call(L.load().iluk_spmv, A.ref, _ptr(vals), _ptr(x), _ptr(y), C.c_void_p(_stream()))
+    return y
+
+
+def dot(x: torch.Tensor, y: torch.Tensor) -> torch.Tensor:
+    """Fixed-shape inner product (4096 strided partials, pairwise tree)."""
+    _check_dev(x, y)
+    out = torch.empty(1, dtype=torch.float64, device=x.device)
+    _call(L.load().iluk_dot, x.numel(), _ptr(x), _ptr(y), _ptr(out), C.c_void_p(_stream()))
+    return out
+
+
+def gmres(rowptr, colind, vals, b, prec=None, restart=30, rtol=1e-8, maxit=10000,
+          transpose=False, x=None, check=True):
+    """a6: right-preconditioned GMRES(m) from x0 = 0.  ``prec`` is None, a
+    Factors (ILU(k) sweeps) or an IncompleteInverse (TPIILU).
+    Returns (x, info)."""
+    A = CsrPattern(rowptr, colind)
+    _check_dev(vals, b)
+    xo = torch.empty_like(b) if x is None else x
+    if prec is None:
+        kind, ph = L.PREC_NONE, None
+    elif isinstance(prec, Factors):
+        kind, ph = L.PREC_ILU, prec.h
+    elif isinstance(prec, IncompleteInverse):
+        kind, ph = L.PREC_IILU, prec.h
+    else:
+        raise TypeError("prec must be None, Factors or IncompleteInverse")
+    info = L.Info()
+    st = L.load().gmres_solve(A.ref, _ptr(vals), kind, ph, _ptr(b), _ptr(xo), int(restart),
+                              float(rtol), int(maxit), int(transpose), C.byref(info),
+                              C.c_void_p(_stream()))
+    if check and st != L.OK:
+        raise IlukError(st, info, "gmres_solve")
+    return xo, info
+
+
+def adjoint_scatter(rowptr, colind, lam, x, out=None):
+    """gA[p] = -lambda_i x_j on A's pattern."""
+    A = CsrPattern(rowptr, colind)
+    _check_dev(lam, x)
+    g = torch.empty(A.nnz, dtype=torch.float64, device=x.device) if out is None else out
+    _call(L.load().iluk_adjoint_scatter, A.ref, _ptr(lam), _ptr(x), _ptr(g),
+          C.c_void_p(_stream()))
+    return g
+
+
+def numeric_batched(S: Symbolic, vals: torch.Tensor, out: Optional[torch.Tensor] = None):
+    """a7: factor ``vals`` [nbatch, nnz_A] on one pattern in one launch.
+    Returns (F values [nbatch, nnz_F], per-set statuses)."""
+    _check_dev(vals)
+    nb = vals.shape[0]
+    F = torch.empty(nb, S.nnz, dtype=torch.float64, device=vals.device) if out is None else out
+    infos = (L.Info * max(nb, 1))()
+    L.load().iluk_numeric_batched(S.h, nb, _ptr(vals), _ptr(F), infos, C.c_void_p(_stream()))
+    return F, [infos[i].status for i in range(nb)]
+
+
+def set_wait_limit(ns: int) -> int:
+    return L.load().iluk_set_wait_limit(int(ns))
+
+
+def debug_hold_row(row: int) -> int:
+    return L.load().iluk_debug_hold_row(int(row))

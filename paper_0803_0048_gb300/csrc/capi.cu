@@ -1,0 +1,860 @@
+// capi.cu -- the C ABI of libiluk (declared in include/iluk.h): handles,
+// stream-ordered device memory, error reporting, the symbolic retry loop, the
+// restarted GMRES(m) driver and the sweep-schedule autotuner.
+//
+// Host arithmetic (Givens rotations, back substitution of the small
+// Hessenberg system) is compiled with FMA contraction off, one IEEE rounding
+// per operation, like the kernels.
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "internal.h"
+
+using namespace iluk;
+
+namespace {
+
+int64_t initial_wait_limit() {
+  // ILUK_WAIT_LIMIT_NS overrides the default bound on a single wait (20 s).
+  const char *e = std::getenv("ILUK_WAIT_LIMIT_NS");
+  if (e) {
+    long long v = std::atoll(e);
+    if (v > 0) return v;
+  }
+  return 20LL * 1000 * 1000 * 1000;
+}
+std::atomic<int64_t> g_wait_limit_ns{initial_wait_limit()};
+std::atomic<int64_t> g_hold_row{-1};
+
+struct DevCache {
+  int sms = 0, smem = 0;
+};
+DevCache g_dev[64];
+std::mutex g_dev_mu;
+
+const DevCache &dev() {
+  int d = 0;
+  cudaGetDevice(&d);
+  if (d < 0 || d >= 64) d = 0;
+  std::lock_guard<std::mutex> lk(g_dev_mu);
+  DevCache &c = g_dev[d];
+  if (c.sms == 0) {
+    cudaDeviceGetAttribute(&c.sms, cudaDevAttrMultiProcessorCount, d);
+    cudaDeviceGetAttribute(&c.smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, d);
+    if (c.sms <= 0) c.sms = 1;
+    if (c.smem <= 0) c.smem = 48 * 1024;
+  }
+  return c;
+}
+
+template <typename T>
+cudaError_t dalloc(T **p, size_t count, cudaStream_t s) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  return cudaMallocAsync((void **)p, count * sizeof(T), s);
+}
+
+template <typename T>
+void dfree(T *&p, cudaStream_t s) {
+  if (p) cudaFreeAsync(p, s);
+  p = nullptr;
+}
+
+int fail(iluk_info *info, int st, int64_t row = -1, int64_t need = 0) {
+  if (info) {
+    info->status = st;
+    info->row = row;
+    info->need = need;
+  }
+  return st;
+}
+
+void info_init(iluk_info *info) {
+  if (info) {
+    std::memset(info, 0, sizeof(*info));
+    info->row = -1;
+  }
+}
+
+#define CK(call)                                        \
+  do {                                                  \
+    cudaError_t _e = (call);                            \
+    if (_e != cudaSuccess) return fail(info, _e == cudaErrorMemoryAllocation ? ILUK_ENOMEM : ILUK_ECUDA); \
+  } while (0)
+
+// Read a device error word; returns status and row.
+int read_err(const DevErr *d, cudaStream_t s, int64_t *row, uint64_t *need) {
+  DevErr h;
+  cudaError_t e = cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return ILUK_ECUDA;
+  if (need) *need = h.need;
+  if (h.key == kNoErr) {
+    if (row) *row = -1;
+    return ILUK_OK;
+  }
+  if (row) *row = (int64_t)(h.key >> 8);
+  return (int)(h.key & 0xff);
+}
+
+int64_t next_pow2(int64_t v) {
+  int64_t p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
+
+}  // namespace
+
+namespace iluk {
+int64_t wait_limit() { return g_wait_limit_ns.load(); }
+int64_t hold_row() { return g_hold_row.load(); }
+int num_sms() { return dev().sms; }
+int max_smem_optin() { return dev().smem; }
+}  // namespace iluk
+
+extern "C" {
+
+const char *iluk_strerror(int st) {
+  switch (st) {
+    case ILUK_OK: return "ok";
+    case ILUK_EINVAL: return "invalid argument";
+    case ILUK_EPATTERN: return "invalid CSR pattern";
+    case ILUK_ENODIAG: return "missing diagonal entry";
+    case ILUK_EZEROPIVOT: return "zero pivot";
+    case ILUK_ENONFINITE: return "non-finite matrix value";
+    case ILUK_ENOMEM: return "out of device memory or row too long";
+    case ILUK_ETIMEOUT: return "bounded wait for another row gave up";
+    case ILUK_ENOCONV: return "GMRES did not converge within maxit";
+    case ILUK_ECUDA: return "CUDA runtime error";
+    default: return "unknown status";
+  }
+}
+
+int64_t iluk_set_wait_limit(int64_t ns) {
+  if (ns <= 0) ns = 1;
+  return g_wait_limit_ns.exchange(ns);
+}
+
+int64_t iluk_debug_hold_row(int64_t row) { return g_hold_row.exchange(row); }
+
+int iluk_validate(const iluk_pattern *A, iluk_info *info, void *stream) {
+  info_init(info);
+  if (!A || A->n < 0 || A->nnz < 0 || !A->rowptr || (A->nnz > 0 && !A->colind))
+    return fail(info, ILUK_EINVAL);
+  if (A->n > INT32_MAX) return fail(info, ILUK_EINVAL);
+  cudaStream_t s = (cudaStream_t)stream;
+  DevErr *err = nullptr;
+  CK(dalloc(&err, 1, s));
+  CK(launch_fill_err(err, s));
+  CK(launch_validate(A->n, A->nnz, A->rowptr, A->colind, err, s));
+  int64_t row;
+  int st = read_err(err, s, &row, nullptr);
+  dfree(err, s);
+  return fail(info, st, row);
+}
+
+void iluk_sym_destroy(iluk_sym *S) {
+  if (!S) return;
+  cudaStream_t s = 0;
+  dfree(S->rowptr, s);
+  dfree(S->colind, s);
+  dfree(S->level, s);
+  dfree(S->diag, s);
+  dfree(S->arowptr, s);
+  dfree(S->a2f, s);
+  delete S;
+}
+
+int iluk_symbolic(const iluk_pattern *A, int k, iluk_sym **out, iluk_info *info, void *stream) {
+  info_init(info);
+  if (!out) return fail(info, ILUK_EINVAL);
+  *out = nullptr;
+  if (k < 0 || k > 250) return fail(info, ILUK_EINVAL);
+  int st = iluk_validate(A, info, stream);
+  if (st != ILUK_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t n = A->n, nnz = A->nnz;
+
+  iluk_sym *S = new iluk_sym();
+  S->n = n;
+  S->nnzA = nnz;
+  S->k = k;
+  DevErr *err = nullptr;
+  SymArena ar{};
+  int64_t *scan_tmp = nullptr;
+  auto cleanup = [&]() {
+    dfree(err, s);
+    dfree(ar.col, s);
+    dfree(ar.lev, s);
+    dfree(ar.top, s);
+    dfree(ar.row_off, s);
+    dfree(ar.row_len, s);
+    dfree(ar.row_ust, s);
+    dfree(ar.ready, s);
+    dfree(ar.ticket, s);
+    dfree(scan_tmp, s);
+  };
+#define CKS(call)                                                   \
+  do {                                                              \
+    cudaError_t _e = (call);                                        \
+    if (_e != cudaSuccess) {                                        \
+      cleanup();                                                    \
+      iluk_sym_destroy(S);                                          \
+      return fail(info, _e == cudaErrorMemoryAllocation ? ILUK_ENOMEM : ILUK_ECUDA); \
+    }                                                               \
+  } while (0)
+
+  CKS(dalloc(&err, 1, s));
+  CKS(dalloc(&ar.row_off, n, s));
+  CKS(dalloc(&ar.row_len, n, s));
+  CKS(dalloc(&ar.row_ust, n, s));
+  CKS(dalloc(&ar.ready, n, s));
+  CKS(dalloc(&ar.ticket, 1, s));
+  CKS(dalloc(&ar.top, 1, s));
+
+  // Capacity of a row in shared memory and of the arena; grown on demand.
+  int cap = 256;
+  int64_t mult = (k == 0) ? 1 : (k == 1) ? 8 : (k == 2) ? 17 : 65;
+  int64_t arena_cap = nnz * mult + 1024;
+  const int max_cap = max_smem_optin() / 5 / 32 * 32;
+  size_t free_b = 0, total_b = 0;
+  cudaMemGetInfo(&free_b, &total_b);
+  const int64_t arena_max = (int64_t)(free_b / 2 / 5);
+  if (arena_cap > arena_max) arena_cap = arena_max;
+
+  for (int attempt = 0;; ++attempt) {
+    if (!ar.col) {
+      CKS(dalloc(&ar.col, arena_cap, s));
+      CKS(dalloc(&ar.lev, arena_cap, s));
+    }
+    ar.cap = arena_cap;
+    CKS(cudaMemsetAsync(ar.ready, 0, n * sizeof(int), s));
+    CKS(cudaMemsetAsync(ar.ticket, 0, sizeof(unsigned long long), s));
+    CKS(cudaMemsetAsync(ar.top, 0, sizeof(unsigned long long), s));
+    CKS(launch_fill_err(err, s));
+    CKS(launch_symbolic_rows(n, A->rowptr, A->colind, k, ar, err, cap, s));
+    int64_t row;
+    uint64_t need = 0;
+    st = read_err(err, s, &row, &need);
+    if (st == ILUK_ECUDA) { cleanup(); iluk_sym_destroy(S); return fail(info, st); }
+    if (st != ILUK_ENOMEM) {
+      if (st != ILUK_OK) { cleanup(); iluk_sym_destroy(S); return fail(info, st, row); }
+      break;
+    }
+    unsigned long long top = 0;
+    CKS(cudaMemcpy(&top, ar.top, sizeof(top), cudaMemcpyDeviceToHost));
+    if ((int64_t)need > cap) {
+      if ((int64_t)need > max_cap) {
+        cleanup(); iluk_sym_destroy(S);
+        return fail(info, ILUK_ENOMEM, row, (int64_t)need);
+      }
+      cap = (int)next_pow2((int64_t)need);
+      if (cap > max_cap) cap = max_cap;
+    } else {
+      int64_t want = arena_cap * 2;
+      if ((int64_t)(top + top / 4) > want) want = (int64_t)(top + top / 4);
+      if (want > arena_max) {
+        cleanup(); iluk_sym_destroy(S);
+        return fail(info, ILUK_ENOMEM, row, want * 5);
+      }
+      arena_cap = want;
+      dfree(ar.col, s);
+      dfree(ar.lev, s);
+    }
+    if (attempt > 40) { cleanup(); iluk_sym_destroy(S); return fail(info, ILUK_ENOMEM, row); }
+  }
+
+  // Compaction into CSR.
+  CKS(dalloc(&S->rowptr, n + 1, s));
+  CKS(dalloc(&scan_tmp, scan_tmp_elems(n), s));
+  CKS(launch_scan_lengths(n, ar.row_len, S->rowptr, scan_tmp, s));
+  int64_t nnzF = 0;
+  CKS(cudaMemcpyAsync(&nnzF, S->rowptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  CKS(cudaStreamSynchronize(s));
+  S->nnz = nnzF;
+  int32_t *maxrow = nullptr;
+  CKS(dalloc(&S->colind, nnzF, s));
+  CKS(dalloc(&S->level, nnzF, s));
+  CKS(dalloc(&S->diag, n, s));
+  CKS(dalloc(&S->a2f, nnz, s));
+  CKS(dalloc(&S->arowptr, n + 1, s));
+  CKS(dalloc(&maxrow, 1, s));
+  CKS(cudaMemsetAsync(maxrow, 0, sizeof(int32_t), s));
+  CKS(launch_symbolic_compact(n, ar, S->rowptr, S->colind, S->level, S->diag, maxrow, s));
+  CKS(launch_a2f(n, A->rowptr, A->colind, S->rowptr, S->colind, S->a2f, s));
+  CKS(cudaMemcpyAsync(S->arowptr, A->rowptr, (n + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+  int32_t mr = 0;
+  CKS(cudaMemcpyAsync(&mr, maxrow, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  CKS(cudaStreamSynchronize(s));
+  S->max_row = mr;
+  dfree(maxrow, s);
+  cleanup();
+#undef CKS
+  *out = S;
+  return fail(info, ILUK_OK);
+}
+
+int iluk_sym_query(const iluk_sym *S, iluk_sym_view *v) {
+  if (!S || !v) return ILUK_EINVAL;
+  v->n = S->n;
+  v->nnz = S->nnz;
+  v->rowptr = S->rowptr;
+  v->colind = S->colind;
+  v->level = S->level;
+  v->diag = S->diag;
+  v->a2f = S->a2f;
+  v->max_row = S->max_row;
+  v->depth_lower = S->depth_lower;
+  v->depth_upper = S->depth_upper;
+  v->k = S->k;
+  return ILUK_OK;
+}
+
+int iluk_sym_export(const iluk_sym *S, int64_t *rowptr, int32_t *colind, uint8_t *level,
+                    int64_t *diag, void *stream) {
+  iluk_info *info = nullptr;
+  if (!S) return ILUK_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  const cudaMemcpyKind k = cudaMemcpyDeviceToDevice;
+  if (rowptr) CK(cudaMemcpyAsync(rowptr, S->rowptr, (S->n + 1) * sizeof(int64_t), k, s));
+  if (colind && S->nnz) CK(cudaMemcpyAsync(colind, S->colind, S->nnz * sizeof(int32_t), k, s));
+  if (level && S->nnz) CK(cudaMemcpyAsync(level, S->level, S->nnz, k, s));
+  if (diag && S->n) CK(cudaMemcpyAsync(diag, S->diag, S->n * sizeof(int64_t), k, s));
+  return ILUK_OK;
+}
+
+int iluk_sym_depth(iluk_sym *S, int32_t *depth_lower, int32_t *depth_upper, void *stream) {
+  iluk_info *info = nullptr;
+  if (!S) return ILUK_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (S->depth_lower < 0) {
+    const int64_t n = S->n;
+    int32_t *depth = nullptr, *mx = nullptr;
+    int *ready = nullptr;
+    unsigned long long *ticket = nullptr;
+    DevErr *err = nullptr;
+    CK(dalloc(&depth, n, s));
+    CK(dalloc(&mx, 2, s));
+    CK(dalloc(&ready, n, s));
+    CK(dalloc(&ticket, 1, s));
+    CK(dalloc(&err, 1, s));
+    CK(cudaMemsetAsync(mx, 0, 2 * sizeof(int32_t), s));
+    CK(launch_fill_err(err, s));
+    for (int upper = 0; upper < 2; ++upper) {
+      CK(cudaMemsetAsync(ready, 0, n * sizeof(int), s));
+      CK(cudaMemsetAsync(ticket, 0, sizeof(unsigned long long), s));
+      CK(launch_depth(n, S->rowptr, S->colind, S->diag, depth, ready, ticket, upper, mx + upper,
+                      err, s));
+    }
+    int32_t h[2] = {0, 0};
+    CK(cudaMemcpyAsync(h, mx, sizeof(h), cudaMemcpyDeviceToHost, s));
+    int st = read_err(err, s, nullptr, nullptr);
+    dfree(depth, s);
+    dfree(mx, s);
+    dfree(ready, s);
+    dfree(ticket, s);
+    dfree(err, s);
+    if (st != ILUK_OK) return st;
+    S->depth_lower = h[0];
+    S->depth_upper = h[1];
+  }
+  if (depth_lower) *depth_lower = S->depth_lower;
+  if (depth_upper) *depth_upper = S->depth_upper;
+  return ILUK_OK;
+}
+
+void iluk_fac_destroy(iluk_fac *F) {
+  if (!F) return;
+  cudaStream_t s = 0;
+  dfree(F->val, s);
+  dfree(F->sync, s);
+  dfree(F->tmp, s);
+  dfree(F->err, s);
+  dfree(F->trowptr, s);
+  dfree(F->tcolind, s);
+  dfree(F->tdiag, s);
+  dfree(F->tval, s);
+  delete F;
+}
+
+static int numeric_into(iluk_fac *F, const double *A_val, iluk_info *info, cudaStream_t s) {
+  const iluk_sym *S = F->S;
+  // numeric uses the sweep scratch: [0..1] ticket, [4..4+n) ready flags
+  CK(cudaMemsetAsync(F->sync, 0, sweep_sync_ints(S->n) * sizeof(int), s));
+  CK(launch_fill_err(F->err, s));
+  CK(launch_numeric(S, A_val, F->val, F->sync + 4, reinterpret_cast<unsigned long long *>(F->sync),
+                    F->err, s));
+  int64_t row;
+  int st = read_err(F->err, s, &row, nullptr);
+  CK(launch_fill_err(F->err, s));
+  // factor values changed: drop the transpose
+  dfree(F->trowptr, s);
+  dfree(F->tcolind, s);
+  dfree(F->tdiag, s);
+  dfree(F->tval, s);
+  return fail(info, st, row);
+}
+
+int iluk_numeric(const iluk_sym *S, const double *A_val, iluk_fac **out, iluk_info *info,
+                 void *stream) {
+  info_init(info);
+  if (!S || !out || (!A_val && S->nnzA > 0)) return fail(info, ILUK_EINVAL);
+  *out = nullptr;
+  cudaStream_t s = (cudaStream_t)stream;
+  iluk_fac *F = new iluk_fac();
+  F->S = S;
+  cudaError_t e = dalloc(&F->val, S->nnz, s);
+  if (e == cudaSuccess) e = dalloc(&F->sync, sweep_sync_ints(S->n), s);
+  if (e == cudaSuccess) e = dalloc(&F->tmp, S->n, s);
+  if (e == cudaSuccess) e = dalloc(&F->err, 2, s);
+  if (e != cudaSuccess) {
+    iluk_fac_destroy(F);
+    return fail(info, e == cudaErrorMemoryAllocation ? ILUK_ENOMEM : ILUK_ECUDA);
+  }
+  int st = numeric_into(F, A_val, info, s);
+  if (st != ILUK_OK) {
+    iluk_fac_destroy(F);
+    return st;
+  }
+  *out = F;
+  return ILUK_OK;
+}
+
+int iluk_refactor(iluk_fac *F, const double *A_val, iluk_info *info, void *stream) {
+  info_init(info);
+  if (!F || (!A_val && F->S->nnzA > 0)) return fail(info, ILUK_EINVAL);
+  return numeric_into(F, A_val, info, (cudaStream_t)stream);
+}
+
+int iluk_fac_values(const iluk_fac *F, const double **val) {
+  if (!F || !val) return ILUK_EINVAL;
+  *val = F->val;
+  return ILUK_OK;
+}
+
+int iluk_fac_export(const iluk_fac *F, double *val, void *stream) {
+  iluk_info *info = nullptr;
+  if (!F || !val) return ILUK_EINVAL;
+  if (F->S->nnz)
+    CK(cudaMemcpyAsync(val, F->val, F->S->nnz * sizeof(double), cudaMemcpyDeviceToDevice,
+                       (cudaStream_t)stream));
+  return ILUK_OK;
+}
+
+int iluk_fac_status(iluk_fac *F, iluk_info *info, void *stream) {
+  info_init(info);
+  if (!F) return fail(info, ILUK_EINVAL);
+  cudaStream_t s = (cudaStream_t)stream;
+  int64_t row;
+  int st = read_err(F->err, s, &row, nullptr);
+  CK(launch_fill_err(F->err, s));
+  return fail(info, st, row);
+}
+
+static int ensure_transpose(iluk_fac *F, cudaStream_t s) {
+  iluk_info *info = nullptr;
+  if (F->trowptr) return ILUK_OK;
+  const iluk_sym *S = F->S;
+  int32_t *cursor = nullptr;
+  int64_t *scan_tmp = nullptr;
+  CK(dalloc(&F->trowptr, S->n + 1, s));
+  CK(dalloc(&F->tcolind, S->nnz, s));
+  CK(dalloc(&F->tdiag, S->n, s));
+  CK(dalloc(&F->tval, S->nnz, s));
+  CK(dalloc(&cursor, S->n, s));
+  CK(dalloc(&scan_tmp, scan_tmp_elems(S->n), s));
+  CK(launch_transpose(S->n, S->nnz, S->rowptr, S->colind, F->val, F->trowptr, F->tcolind,
+                      F->tval, F->tdiag, cursor, scan_tmp, s));
+  dfree(cursor, s);
+  dfree(scan_tmp, s);
+  return ILUK_OK;
+}
+
+// Autotuner: time both sweep schedules once on this factorization and keep
+// the faster one (skipped while the stream is being captured).
+static int pick_schedule(iluk_fac *F, cudaStream_t s) {
+  if (F->sched != ILUK_SCHED_AUTO) return F->sched;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(s, &cs);
+  if (cs != cudaStreamCaptureStatusNone) return ILUK_SCHED_FLAGS;
+  const iluk_sym *S = F->S;
+  double *p = nullptr, *y = nullptr;
+  if (dalloc(&p, S->n, s) != cudaSuccess || dalloc(&y, S->n, s) != cudaSuccess) {
+    dfree(p, s);
+    return ILUK_SCHED_FLAGS;
+  }
+  cudaMemsetAsync(p, 0, S->n * sizeof(double), s);
+  float best = 1e30f;
+  int pick = ILUK_SCHED_FLAGS;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  for (int sched : {ILUK_SCHED_FLAGS, ILUK_SCHED_SINGLE_CTA}) {
+    float ms_min = 1e30f;
+    for (int rep = 0; rep < 3; ++rep) {
+      cudaEventRecord(e0, s);
+      launch_apply(S->n, S->rowptr, S->colind, S->diag, F->val, p, F->tmp, y, F->sync, 0, sched,
+                   F->err, s);
+      cudaEventRecord(e1, s);
+      cudaEventSynchronize(e1);
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0 && ms < ms_min) ms_min = ms;
+    }
+    if (ms_min < best) {
+      best = ms_min;
+      pick = sched;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  dfree(p, s);
+  dfree(y, s);
+  F->sched = pick;
+  return pick;
+}
+
+int iluk_apply_sched(iluk_fac *F, const double *p, double *y, int transpose, int sched,
+                     void *stream) {
+  iluk_info *info = nullptr;
+  if (!F || (!p && F->S->n) || (!y && F->S->n)) return ILUK_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  const iluk_sym *S = F->S;
+  if (sched == ILUK_SCHED_AUTO) sched = pick_schedule(F, s);
+  if (transpose) {
+    int st = ensure_transpose(F, s);
+    if (st != ILUK_OK) return st;
+    CK(launch_apply(S->n, F->trowptr, F->tcolind, F->tdiag, F->tval, p, F->tmp, y, F->sync, 1,
+                    sched, F->err, s));
+  } else {
+    CK(launch_apply(S->n, S->rowptr, S->colind, S->diag, F->val, p, F->tmp, y, F->sync, 0, sched,
+                    F->err, s));
+  }
+  return ILUK_OK;
+}
+
+int iluk_apply(iluk_fac *F, const double *p, double *y, int transpose, void *stream) {
+  return iluk_apply_sched(F, p, y, transpose, ILUK_SCHED_AUTO, stream);
+}
+
+int iluk_set_schedule(iluk_fac *F, int sched) {
+  if (!F || sched < 0 || sched > 2) return ILUK_EINVAL;
+  F->sched = sched;
+  return ILUK_OK;
+}
+
+int iluk_get_schedule(const iluk_fac *F) { return F ? F->sched : -1; }
+
+void iiluk_destroy(iiluk *M) {
+  if (!M) return;
+  cudaStream_t s = 0;
+  dfree(M->g, s);
+  dfree(M->tmp, s);
+  delete M;
+}
+
+int iiluk_build(const iluk_fac *F, iiluk **out, iluk_info *info, void *stream) {
+  info_init(info);
+  if (!F || !out) return fail(info, ILUK_EINVAL);
+  *out = nullptr;
+  cudaStream_t s = (cudaStream_t)stream;
+  const iluk_sym *S = F->S;
+  iiluk *M = new iiluk();
+  M->S = S;
+  int *sync = nullptr;
+  DevErr *err = nullptr;
+  cudaError_t e = dalloc(&M->g, S->nnz, s);
+  if (e == cudaSuccess) e = dalloc(&M->tmp, S->n, s);
+  if (e == cudaSuccess) e = dalloc(&sync, 4 + 2 * S->n, s);
+  if (e == cudaSuccess) e = dalloc(&err, 2, s);
+  if (e == cudaSuccess) e = launch_fill_err(err, s);
+  if (e == cudaSuccess) e = launch_fill_err(err + 1, s);
+  if (e == cudaSuccess) e = launch_iiluk_build(S, F->val, M->g, sync, err, s);
+  int st = ILUK_OK;
+  int64_t row = -1;
+  if (e == cudaSuccess) {
+    int64_t r0, r1;
+    int s0 = read_err(err, s, &r0, nullptr);
+    int s1 = read_err(err + 1, s, &r1, nullptr);
+    if (s0 != ILUK_OK) { st = s0; row = r0; }
+    else if (s1 != ILUK_OK) { st = s1; row = S->n - 1 - r1; }
+  } else {
+    st = e == cudaErrorMemoryAllocation ? ILUK_ENOMEM : ILUK_ECUDA;
+  }
+  dfree(sync, s);
+  dfree(err, s);
+  if (st != ILUK_OK) {
+    iiluk_destroy(M);
+    return fail(info, st, row);
+  }
+  *out = M;
+  return fail(info, ILUK_OK);
+}
+
+int iiluk_values(const iiluk *M, const double **g) {
+  if (!M || !g) return ILUK_EINVAL;
+  *g = M->g;
+  return ILUK_OK;
+}
+
+int iiluk_export(const iiluk *M, double *g, void *stream) {
+  iluk_info *info = nullptr;
+  if (!M || !g) return ILUK_EINVAL;
+  if (M->S->nnz)
+    CK(cudaMemcpyAsync(g, M->g, M->S->nnz * sizeof(double), cudaMemcpyDeviceToDevice,
+                       (cudaStream_t)stream));
+  return ILUK_OK;
+}
+
+int iiluk_apply(const iiluk *M, const double *p, double *y, void *stream) {
+  iluk_info *info = nullptr;
+  if (!M) return ILUK_EINVAL;
+  CK(launch_iiluk_apply(M->S, M->g, p, M->tmp, y, (cudaStream_t)stream));
+  return ILUK_OK;
+}
+
+int iluk_spmv(const iluk_pattern *A, const double *A_val, const double *x, double *y,
+              void *stream) {
+  iluk_info *info = nullptr;
+  if (!A) return ILUK_EINVAL;
+  CK(launch_spmv(A->n, A->rowptr, A->colind, A_val, x, y, nullptr, (cudaStream_t)stream));
+  return ILUK_OK;
+}
+
+int iluk_dot(int64_t n, const double *x, const double *y, double *out, void *stream) {
+  iluk_info *info = nullptr;
+  cudaStream_t s = (cudaStream_t)stream;
+  DotScratch ds{};
+  CK(dalloc(&ds.partial, kDotP, s));
+  CK(dalloc(&ds.counter, 1, s));
+  CK(cudaMemsetAsync(ds.counter, 0, sizeof(unsigned), s));
+  CK(launch_dot(n, x, y, out, 0, ds, s));
+  dfree(ds.partial, s);
+  dfree(ds.counter, s);
+  return ILUK_OK;
+}
+
+int iluk_adjoint_scatter(const iluk_pattern *A, const double *lambda, const double *x, double *gA,
+                         void *stream) {
+  iluk_info *info = nullptr;
+  if (!A) return ILUK_EINVAL;
+  CK(launch_adjoint_scatter(A->n, A->rowptr, A->colind, lambda, x, gA, (cudaStream_t)stream));
+  return ILUK_OK;
+}
+
+int iluk_numeric_batched(const iluk_sym *S, int64_t nbatch, const double *A_vals, double *F_vals,
+                         iluk_info *infos, void *stream) {
+  iluk_info *info = nullptr;
+  if (!S || nbatch < 0) return ILUK_EINVAL;
+  if (nbatch == 0) return ILUK_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  int *ready = nullptr;
+  unsigned long long *ticket = nullptr;
+  DevErr *errs = nullptr;
+  CK(dalloc(&ready, S->n * nbatch, s));
+  CK(dalloc(&ticket, 1, s));
+  CK(dalloc(&errs, nbatch, s));
+  CK(cudaMemsetAsync(ready, 0, S->n * nbatch * sizeof(int), s));
+  CK(cudaMemsetAsync(ticket, 0, sizeof(unsigned long long), s));
+  CK(cudaMemsetAsync(errs, 0xff, nbatch * sizeof(DevErr), s));
+  CK(launch_numeric_batched(S, nbatch, A_vals, F_vals, ready, ticket, errs, s));
+  std::vector<DevErr> h(nbatch);
+  CK(cudaMemcpyAsync(h.data(), errs, nbatch * sizeof(DevErr), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  dfree(ready, s);
+  dfree(ticket, s);
+  dfree(errs, s);
+  int first = ILUK_OK;
+  for (int64_t b = 0; b < nbatch; ++b) {
+    int st = h[b].key == kNoErr ? ILUK_OK : (int)(h[b].key & 0xff);
+    if (infos) {
+      std::memset(&infos[b], 0, sizeof(iluk_info));
+      infos[b].status = st;
+      infos[b].row = st == ILUK_OK ? -1 : (int64_t)(h[b].key >> 8);
+    }
+    if (first == ILUK_OK && st != ILUK_OK) first = st;
+  }
+  return first;
+}
+
+// ---------------------------------------------------------------------------
+// GMRES(m)
+// ---------------------------------------------------------------------------
+int gmres_solve(const iluk_pattern *A, const double *A_val, int prec_kind, void *prec,
+                const double *b, double *x, int m, double rtol, int maxit, int transpose,
+                iluk_info *info, void *stream) {
+  info_init(info);
+  if (!A || m < 1 || maxit < 0 || A->n < 0) return fail(info, ILUK_EINVAL);
+  if (prec_kind != ILUK_PREC_NONE && !prec) return fail(info, ILUK_EINVAL);
+  if (transpose && prec_kind == ILUK_PREC_IILU) return fail(info, ILUK_EINVAL);
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t n = A->n;
+  iluk_fac *F = prec_kind == ILUK_PREC_ILU ? (iluk_fac *)prec : nullptr;
+  iiluk *M = prec_kind == ILUK_PREC_IILU ? (iiluk *)prec : nullptr;
+
+  // operator rows: A, or the explicit transpose of A
+  const int64_t *orp = A->rowptr;
+  const int32_t *oci = A->colind;
+  const double *ov = A_val;
+  int64_t *trp = nullptr;
+  int32_t *tci = nullptr;
+  double *tv = nullptr;
+  if (transpose) {
+    int32_t *cursor = nullptr;
+    int64_t *scan_tmp = nullptr;
+    CK(dalloc(&trp, n + 1, s));
+    CK(dalloc(&tci, A->nnz, s));
+    CK(dalloc(&tv, A->nnz, s));
+    CK(dalloc(&cursor, n, s));
+    CK(dalloc(&scan_tmp, scan_tmp_elems(n), s));
+    CK(launch_transpose(n, A->nnz, A->rowptr, A->colind, A_val, trp, tci, tv, nullptr, cursor,
+                        scan_tmp, s));
+    dfree(cursor, s);
+    dfree(scan_tmp, s);
+    orp = trp;
+    oci = tci;
+    ov = tv;
+  }
+  const int64_t ldv = n > 0 ? n : 1;
+  double *V = nullptr, *w = nullptr, *z = nullptr, *u = nullptr, *Hd = nullptr, *dsc = nullptr,
+         *dy = nullptr;
+  DotScratch ds{};
+  CK(dalloc(&V, (size_t)ldv * (m + 1), s));
+  CK(dalloc(&w, ldv, s));
+  CK(dalloc(&z, ldv, s));
+  CK(dalloc(&u, ldv, s));
+  CK(dalloc(&Hd, (size_t)(m + 1) * m, s));
+  CK(dalloc(&dsc, 4, s));
+  CK(dalloc(&dy, m, s));
+  CK(dalloc(&ds.partial, kDotP, s));
+  CK(dalloc(&ds.counter, 1, s));
+  CK(cudaMemsetAsync(ds.counter, 0, sizeof(unsigned), s));
+  if (F && transpose) {
+    int st = ensure_transpose(F, s);
+    if (st != ILUK_OK) return fail(info, st);
+  }
+  const int sched = F ? pick_schedule(F, s) : 0;
+
+  auto precond = [&](const double *in, double *outv) -> cudaError_t {
+    if (F) {
+      if (transpose)
+        return launch_apply(n, F->trowptr, F->tcolind, F->tdiag, F->tval, in, F->tmp, outv,
+                            F->sync, 1, sched, F->err, s);
+      return launch_apply(n, F->S->rowptr, F->S->colind, F->S->diag, F->val, in, F->tmp, outv,
+                          F->sync, 0, sched, F->err, s);
+    }
+    if (M) return launch_iiluk_apply(M->S, M->g, in, M->tmp, outv, s);
+    return cudaMemcpyAsync(outv, in, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  };
+
+  std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m), sn(m), gv(m + 1), yv(m),
+      col(m + 2);
+  int status = ILUK_ENOCONV;
+  int iters = 0, cycles = 0;
+  double relres = 0.0;
+  double bnorm = 0.0;
+  CK(launch_dot(n, b, b, dsc + 0, 1, ds, s));
+  CK(cudaMemcpyAsync(&bnorm, dsc + 0, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  CK(cudaMemsetAsync(x, 0, n * sizeof(double), s));
+  if (bnorm == 0.0) {
+    status = ILUK_OK;
+  } else {
+    for (;;) {
+      // r = b - A x  (r lives in w)
+      CK(launch_spmv(n, orp, oci, ov, x, w, b, s));
+      CK(launch_dot(n, w, w, dsc + 1, 1, ds, s));
+      double beta = 0.0;
+      CK(cudaMemcpyAsync(&beta, dsc + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      relres = beta / bnorm;
+      if (relres <= rtol) { status = ILUK_OK; break; }
+      if (iters >= maxit) { status = ILUK_ENOCONV; break; }
+      ++cycles;
+      CK(launch_scale_div(n, w, dsc + 1, V, s));
+      gv[0] = beta;
+      int jend = -1;
+      bool bad = false;
+      for (int j = 0; j < m; ++j) {
+        double *vj = V + (size_t)j * ldv;
+        double *hc = Hd + (size_t)j * (m + 1);  // column j of H
+        CK(precond(vj, z));
+        CK(launch_spmv(n, orp, oci, ov, z, w, nullptr, s));
+        CK(launch_dot(n, w, V, hc + 0, 0, ds, s));
+        for (int i = 0; i <= j; ++i) {
+          const double *vi = V + (size_t)i * ldv;
+          if (i < j)
+            CK(launch_mgs_step(n, w, vi, hc + i, V + (size_t)(i + 1) * ldv, hc + i + 1, 0, ds, s));
+          else
+            CK(launch_mgs_step(n, w, vi, hc + i, w, hc + j + 1, 1, ds, s));
+        }
+        CK(launch_scale_div(n, w, hc + j + 1, V + (size_t)(j + 1) * ldv, s));
+        CK(cudaMemcpyAsync(col.data(), hc, (j + 2) * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        for (int i = 0; i <= j + 1; ++i) H[(size_t)i * m + j] = col[i];
+        const double hn = col[j + 1];
+        for (int i = 0; i < j; ++i) {  // previous rotations
+          const double a = H[(size_t)i * m + j], c = H[(size_t)(i + 1) * m + j];
+          const double t1 = cs[i] * a, t2 = sn[i] * c;
+          const double t3 = sn[i] * a, t4 = cs[i] * c;
+          H[(size_t)i * m + j] = t1 + t2;
+          H[(size_t)(i + 1) * m + j] = t4 - t3;
+        }
+        const double a = H[(size_t)j * m + j], c = H[(size_t)(j + 1) * m + j];
+        const double aa = a * a, cc = c * c;
+        const double rr = std::sqrt(aa + cc);
+        if (rr == 0.0) { bad = true; break; }
+        cs[j] = a / rr;
+        sn[j] = c / rr;
+        H[(size_t)j * m + j] = rr;
+        H[(size_t)(j + 1) * m + j] = 0.0;
+        gv[j + 1] = -(sn[j] * gv[j]);
+        gv[j] = cs[j] * gv[j];
+        ++iters;
+        jend = j;
+        const bool breakdown = hn == 0.0;
+        if (std::fabs(gv[j + 1]) / bnorm <= rtol || iters >= maxit || breakdown) break;
+      }
+      if (bad) { status = ILUK_EINVAL; break; }
+      for (int i = jend; i >= 0; --i) {
+        double sacc = gv[i];
+        for (int l = i + 1; l <= jend; ++l) {
+          const double prod = H[(size_t)i * m + l] * yv[l];
+          sacc = sacc - prod;
+        }
+        yv[i] = sacc / H[(size_t)i * m + i];
+      }
+      CK(cudaMemcpyAsync(dy, yv.data(), (jend + 1) * sizeof(double), cudaMemcpyHostToDevice, s));
+      CK(launch_combine(n, V, ldv, dy, jend + 1, u, s));
+      CK(precond(u, z));
+      CK(launch_add(n, x, z, s));
+    }
+  }
+  CK(cudaStreamSynchronize(s));
+  int64_t prow = -1;
+  if (F) {
+    int pst = read_err(F->err, s, &prow, nullptr);
+    if (pst != ILUK_OK) {
+      launch_fill_err(F->err, s);
+      status = pst;
+    }
+  }
+  dfree(V, s); dfree(w, s); dfree(z, s); dfree(u, s); dfree(Hd, s); dfree(dsc, s); dfree(dy, s);
+  dfree(ds.partial, s); dfree(ds.counter, s);
+  dfree(trp, s); dfree(tci, s); dfree(tv, s);
+  if (info) {
+    info->status = status;
+    info->iters = iters;
+    info->relres = relres;
+    info->cycles = cycles;
+    info->row = prow;
+  }
+  return status;
+}
+
+}  // extern "C"

@@ -1,0 +1,118 @@
+// common.cuh -- device helpers shared by the libiluk kernels.
+//
+// Row-to-row synchronisation: a row publishes its result with a release store
+// to its ready flag; a dependent row spins on the flag with acquire loads.
+// Every wait is bounded by a time limit read from %globaltimer; on running
+// out, or when an earlier row has failed, the wait returns false and the
+// kernel records a status and returns (no trap, no endless loop).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/iluk.h"
+
+#define FULL_MASK 0xffffffffu
+
+namespace iluk {
+
+// Error word: (row << 8) | code, combined with atomicMin so that the smallest
+// failing row wins, whatever order the rows fail in.  ~0ull means "no error".
+struct DevErr {
+  unsigned long long key;
+  unsigned long long need;
+};
+
+static constexpr unsigned long long kNoErr = ~0ull;
+
+__device__ __forceinline__ unsigned long long err_key(int64_t row, int code) {
+  return ((unsigned long long)row << 8) | (unsigned long long)code;
+}
+
+__device__ __forceinline__ void set_err(DevErr *e, int64_t row, int code) {
+  atomicMin(&e->key, err_key(row, code));
+}
+
+__device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned long long *p) {
+  return *((volatile const unsigned long long *)p);
+}
+
+// True if a row smaller than `row` has failed (its dependants must stop).
+__device__ __forceinline__ bool earlier_failed(const DevErr *e, int64_t row) {
+  unsigned long long k = ld_volatile_u64(&e->key);
+  return k != kNoErr && (int64_t)(k >> 8) < row;
+}
+
+__device__ __forceinline__ bool any_failed(const DevErr *e) {
+  return ld_volatile_u64(&e->key) != kNoErr;
+}
+
+__device__ __forceinline__ int ld_acquire(const int *p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release(int *p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Spin until *flag != 0.  Returns false if the limit ran out or a row before
+// `row` failed.  Called by all lanes of a warp that need the flag.
+__device__ __forceinline__ bool wait_flag(const int *flag, const DevErr *err, int64_t row,
+                                          int64_t limit_ns) {
+  if (ld_acquire(flag)) return true;
+  uint64_t t0 = globaltimer_ns();
+  unsigned backoff = 32;
+  for (;;) {
+    if (ld_acquire(flag)) return true;
+    if (earlier_failed(err, row)) return false;
+    if ((int64_t)(globaltimer_ns() - t0) > limit_ns) return false;
+    __nanosleep(backoff);
+    if (backoff < 256) backoff <<= 1;
+  }
+}
+
+// Publish: every lane has finished its stores for the row; make them visible
+// at GPU scope before the flag.
+__device__ __forceinline__ void warp_publish(int *flag, int lane) {
+  __threadfence();
+  __syncwarp();
+  if (lane == 0) st_release(flag, 1);
+}
+
+// Lower bound of `key` in the sorted array a[lo, hi).
+template <typename T>
+__device__ __forceinline__ int lower_bound_i(const T *a, int lo, int hi, T key) {
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (a[mid] < key) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+template <typename T>
+__device__ __forceinline__ int64_t lower_bound_l(const T *a, int64_t lo, int64_t hi, T key) {
+  while (lo < hi) {
+    int64_t mid = (lo + hi) >> 1;
+    if (a[mid] < key) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+// One IEEE multiply then one IEEE subtract, each rounded to nearest.
+__device__ __forceinline__ double sub_prod(double acc, double a, double b) {
+  return __dsub_rn(acc, __dmul_rn(a, b));
+}
+
+__device__ __forceinline__ double add_prod(double acc, double a, double b) {
+  return __dadd_rn(acc, __dmul_rn(a, b));
+}
+
+}  // namespace iluk

@@ -1,0 +1,120 @@
+// internal.h -- host-side declarations shared by the libiluk translation units.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+// Handle layouts (opaque in the public header).
+struct iluk_sym {
+  int64_t n = 0, nnz = 0, nnzA = 0;
+  int k = 0;
+  int64_t *rowptr = nullptr;   // F pattern
+  int32_t *colind = nullptr;
+  uint8_t *level = nullptr;
+  int64_t *diag = nullptr;
+  int64_t *arowptr = nullptr;  // copy of A's row pointers
+  int32_t *a2f = nullptr;      // offset of each A entry inside its F row
+  int32_t max_row = 0;
+  int32_t depth_lower = -1, depth_upper = -1;
+};
+
+struct iluk_fac {
+  const iluk_sym *S = nullptr;
+  double *val = nullptr;          // F values
+  int *sync = nullptr;            // tickets + flags for sweeps: see sweeps.cu
+  double *tmp = nullptr;          // intermediate vector of the two sweeps
+  iluk::DevErr *err = nullptr;    // status of asynchronous calls
+  // explicit transpose of F for (L~U~)^-T, built on first use
+  int64_t *trowptr = nullptr;
+  int32_t *tcolind = nullptr;
+  int64_t *tdiag = nullptr;
+  double *tval = nullptr;
+  int sched = 0;                  // schedule picked for the sweeps (ILUK_SCHED_*)
+};
+
+struct iiluk {
+  const iluk_sym *S = nullptr;
+  double *g = nullptr;
+  double *tmp = nullptr;
+};
+
+namespace iluk {
+
+int64_t wait_limit();
+int64_t hold_row();              // test hook: a row whose flag is never published
+
+// Sizes of the persistent grids (filled on first use per device).
+int num_sms();
+int max_smem_optin();
+
+// Validation / utilities (validate.cu)
+cudaError_t launch_validate(int64_t n, int64_t nnz, const int64_t *rp, const int32_t *ci,
+                            DevErr *err, cudaStream_t s);
+// out[0] = 0, out[i+1] = sum_{r<=i} len[r]  (int32 lengths -> int64 offsets)
+cudaError_t launch_scan_lengths(int64_t n, const int32_t *len, int64_t *out, int64_t *tmp,
+                                cudaStream_t s);
+int64_t scan_tmp_elems(int64_t n);
+cudaError_t launch_fill_err(DevErr *err, cudaStream_t s);
+
+// Symbolic (symbolic.cu)
+struct SymArena {
+  int32_t *col; uint8_t *lev; int64_t cap; unsigned long long *top;
+  int64_t *row_off; int32_t *row_len; int32_t *row_ust;
+  int *ready; unsigned long long *ticket;
+};
+cudaError_t launch_symbolic_rows(int64_t n, const int64_t *arp, const int32_t *aci, int k,
+                                 const SymArena &ar, DevErr *err, int cap, cudaStream_t s);
+size_t symbolic_smem_per_warp(int cap);
+cudaError_t launch_symbolic_compact(int64_t n, const SymArena &ar, const int64_t *frp,
+                                    int32_t *fci, uint8_t *flev, int64_t *fdiag, int32_t *maxrow,
+                                    cudaStream_t s);
+cudaError_t launch_a2f(int64_t n, const int64_t *arp, const int32_t *aci, const int64_t *frp,
+                       const int32_t *fci, int32_t *a2f, cudaStream_t s);
+cudaError_t launch_depth(int64_t n, const int64_t *frp, const int32_t *fci, const int64_t *fdiag,
+                         int32_t *depth, int *ready, unsigned long long *ticket, int upper,
+                         int32_t *maxdepth, DevErr *err, cudaStream_t s);
+
+// Numeric (numeric.cu)
+cudaError_t launch_numeric(const iluk_sym *S, const double *aval, double *fval, int *ready,
+                           unsigned long long *ticket, DevErr *err, cudaStream_t s);
+cudaError_t launch_numeric_batched(const iluk_sym *S, int64_t nbatch, const double *avals,
+                                   double *fvals, int *ready, unsigned long long *ticket,
+                                   DevErr *errs, cudaStream_t s);
+
+// Sweeps (sweeps.cu)
+size_t sweep_sync_ints(int64_t n);
+cudaError_t launch_apply(int64_t n, const int64_t *rp, const int32_t *ci, const int64_t *dg,
+                         const double *v, const double *p, double *tmp, double *y, int *sync,
+                         int transpose, int sched, DevErr *err, cudaStream_t s);
+cudaError_t launch_transpose(int64_t n, int64_t nnz, const int64_t *rp, const int32_t *ci,
+                             const double *v, int64_t *trp, int32_t *tci, double *tv,
+                             int64_t *tdiag, int32_t *cursor, int64_t *scan_tmp, cudaStream_t s);
+
+// TPIILU (tpiilu.cu)
+cudaError_t launch_iiluk_build(const iluk_sym *S, const double *fval, double *g, int *sync,
+                               DevErr *err, cudaStream_t s);
+cudaError_t launch_iiluk_apply(const iluk_sym *S, const double *g, const double *p, double *tmp,
+                               double *y, cudaStream_t s);
+
+// Krylov pieces (krylov.cu)
+constexpr int kDotP = 4096;
+struct DotScratch { double *partial; unsigned int *counter; };
+cudaError_t launch_spmv(int64_t n, const int64_t *rp, const int32_t *ci, const double *v,
+                        const double *x, double *y, const double *b_minus, cudaStream_t s);
+cudaError_t launch_dot(int64_t n, const double *x, const double *y, double *out, int take_sqrt,
+                       const DotScratch &ds, cudaStream_t s);
+cudaError_t launch_mgs_step(int64_t n, double *w, const double *vi, const double *hij,
+                            const double *vnext, double *out, int take_sqrt,
+                            const DotScratch &ds, cudaStream_t s);
+cudaError_t launch_scale_div(int64_t n, const double *x, const double *den, double *y,
+                             cudaStream_t s);
+cudaError_t launch_combine(int64_t n, const double *V, int64_t ldv, const double *y, int cnt,
+                           double *u, cudaStream_t s);
+cudaError_t launch_add(int64_t n, double *x, const double *z, cudaStream_t s);
+cudaError_t launch_adjoint_scatter(int64_t n, const int64_t *rp, const int32_t *ci,
+                                   const double *lam, const double *x, double *gA,
+                                   cudaStream_t s);
+
+}  // namespace iluk

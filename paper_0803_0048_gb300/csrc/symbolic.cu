@@ -1,0 +1,338 @@
+// symbolic.cu -- a2: symbolic ILU(k) factorization (Algorithm 1, Sec. 2.2)
+// with the level of fill of Def. 2.3, one warp per row.
+//
+// Row j's permitted set is kept sorted in the warp's slice of shared memory
+// (columns int32 + levels uint8).  Its entries below the diagonal are walked
+// in ascending order, including those inserted during the walk; for each
+// such i with level(j,i) < k the warp waits for row i to be final, then
+// merges row i's entries t > i: weight = level(j,i) + level(i,t) + 1, a
+// min-update when t is present, an insertion when weight <= k.  Entries with
+// level(j,i) >= k, or with weight > k, cannot change anything and are
+// skipped.  Finished rows go to a bump arena (the device analogue of the
+// paper's thread-private allocation arenas, Sec. 3.3) and are compacted into
+// CSR afterwards (Sec. 3.4).
+//
+// With k <= 1 rows are independent (Sec. 3.3: only level-0 entries can cause
+// fill), so the warp reads the pivot rows straight from A and never waits.
+#include <climits>
+
+#include "internal.h"
+
+namespace iluk {
+
+constexpr int kSymThreads = 256;
+
+size_t symbolic_smem_per_warp(int cap) { return (size_t)cap * 5; }
+
+template <bool INDEP>
+__global__ void __launch_bounds__(kSymThreads)
+k_symbolic_rows(int64_t n, const int64_t *__restrict__ arp, const int32_t *__restrict__ aci,
+                int k, int32_t *arena_col, uint8_t *arena_lev, int64_t arena_cap,
+                unsigned long long *arena_top, int64_t *row_off, int32_t *row_len,
+                int32_t *row_ust, int *ready, unsigned long long *ticket, DevErr *err, int cap,
+                int64_t limit_ns) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  const int nwarps = blockDim.x >> 5;
+  int32_t *cols = reinterpret_cast<int32_t *>(smem) + (size_t)wib * cap;
+  uint8_t *lev = smem + (size_t)nwarps * cap * 4 + (size_t)wib * cap;
+
+  for (;;) {
+    unsigned long long tk = 0;
+    if (lane == 0) tk = atomicAdd(ticket, 1ull);
+    const int64_t row = (int64_t)__shfl_sync(FULL_MASK, tk, 0);
+    if (row >= n) return;
+    if (earlier_failed(err, row)) return;
+
+    const int64_t a0 = arp[row], a1 = arp[row + 1];
+    int m = (int)(a1 - a0);
+    if (a1 - a0 > cap) {
+      if (lane == 0) {
+        set_err(err, row, ILUK_ENOMEM);
+        atomicMax(&err->need, (unsigned long long)(a1 - a0));
+      }
+      return;
+    }
+    for (int q = lane; q < m; q += 32) {
+      cols[q] = aci[a0 + q];
+      lev[q] = 0;
+    }
+    __syncwarp();
+
+    bool ok = true;
+    for (int p = 0; p < m; ++p) {
+      const int i = cols[p];
+      if (i >= row) break;
+      const int lji = lev[p];
+      if (lji >= k) continue;  // weight would exceed k for every t
+      const int32_t *ucol;
+      const uint8_t *ulev = nullptr;
+      int ulen;
+      if (INDEP) {
+        const int64_t b0 = arp[i], b1 = arp[i + 1];
+        const int64_t s = lower_bound_l(aci, b0, b1, (int32_t)(i + 1));
+        ucol = aci + s;
+        ulen = (int)(b1 - s);
+      } else {
+        if (!wait_flag(&ready[i], err, row, limit_ns)) {
+          if (lane == 0 && !earlier_failed(err, row)) set_err(err, row, ILUK_ETIMEOUT);
+          ok = false;
+          break;
+        }
+        const int64_t off = *((volatile int64_t *)&row_off[i]);
+        const int len = *((volatile int32_t *)&row_len[i]);
+        const int ust = *((volatile int32_t *)&row_ust[i]);
+        ucol = arena_col + off + ust;
+        ulev = arena_lev + off + ust;
+        ulen = len - ust;
+      }
+      const int limit = k - 1 - lji;  // level(i,t) must not exceed this
+      for (int base = 0; base < ulen; base += 32) {
+        const int q = base + lane;
+        int t = INT_MAX, lt = 255;
+        if (q < ulen) {
+          t = ucol[q];
+          lt = INDEP ? 0 : (int)ulev[q];
+        }
+        const bool cand = (q < ulen) && lt <= limit;
+        const int w = lji + lt + 1;
+        int pos = 0;
+        bool found = false;
+        if (cand) {
+          pos = lower_bound_i(cols, p + 1, m, (int32_t)t);
+          found = pos < m && cols[pos] == t;
+          if (found && w < (int)lev[pos]) lev[pos] = (uint8_t)w;
+        }
+        const bool ins = cand && !found;
+        const unsigned insmask = __ballot_sync(FULL_MASK, ins);
+        __syncwarp();
+        if (insmask) {
+          const int c = __popc(insmask);
+          if (m + c > cap) {
+            if (lane == 0) {
+              set_err(err, row, ILUK_ENOMEM);
+              atomicMax(&err->need, (unsigned long long)(m + c));
+            }
+            ok = false;
+            break;
+          }
+          const int lb = ins ? pos : INT_MAX;
+          const int lbmin = __reduce_min_sync(FULL_MASK, lb);
+          // Shift the tail [lbmin, m) up, top chunk first, so that every
+          // element moves past the insertions that precede it.
+          for (int top = m - 1; top >= lbmin; top -= 32) {
+            const int q2 = top - lane;
+            const bool act = q2 >= lbmin;
+            int32_t cv = 0;
+            uint8_t lv = 0;
+            if (act) {
+              cv = cols[q2];
+              lv = lev[q2];
+            }
+            int sh = 0;
+#pragma unroll
+            for (int r = 0; r < 32; ++r) sh += (__shfl_sync(FULL_MASK, lb, r) <= q2) ? 1 : 0;
+            __syncwarp();
+            if (act) {
+              cols[q2 + sh] = cv;
+              lev[q2 + sh] = lv;
+            }
+            __syncwarp();
+          }
+          if (ins) {
+            const int rank = __popc(insmask & ((1u << lane) - 1u));
+            cols[pos + rank] = t;
+            lev[pos + rank] = (uint8_t)w;
+          }
+          m += c;
+          __syncwarp();
+        }
+      }
+      if (!ok) break;
+    }
+    if (!ok) return;
+
+    // Row final.  Upper part starts at the first column > row.
+    const int dpos = lower_bound_i(cols, 0, m, (int32_t)row);
+    const bool has_diag = dpos < m && cols[dpos] == row;
+    const int ust = has_diag ? dpos + 1 : dpos;
+    if (!has_diag && lane == 0) set_err(err, row, ILUK_ENODIAG);
+
+    unsigned long long off = 0;
+    if (lane == 0) off = atomicAdd(arena_top, (unsigned long long)m);
+    off = __shfl_sync(FULL_MASK, off, 0);
+    if ((int64_t)(off + m) > arena_cap) {
+      if (lane == 0) set_err(err, row, ILUK_ENOMEM);
+      return;
+    }
+    for (int q = lane; q < m; q += 32) {
+      arena_col[off + q] = cols[q];
+      arena_lev[off + q] = lev[q];
+    }
+    if (lane == 0) {
+      row_off[row] = (int64_t)off;
+      row_len[row] = m;
+      row_ust[row] = ust;
+    }
+    if (!INDEP) warp_publish(&ready[row], lane);
+    __syncwarp();
+  }
+}
+
+cudaError_t launch_symbolic_rows(int64_t n, const int64_t *arp, const int32_t *aci, int k,
+                                 const SymArena &ar, DevErr *err, int cap, cudaStream_t s) {
+  const size_t per_warp = symbolic_smem_per_warp(cap);
+  int warps = kSymThreads / 32;
+  while (warps > 1 && per_warp * warps > (size_t)max_smem_optin()) warps >>= 1;
+  const size_t smem = per_warp * warps;
+  const int threads = warps * 32;
+  const bool indep = k <= 1;
+  cudaError_t e;
+  int blocks_per_sm = 0;
+  if (indep) {
+    e = cudaFuncSetAttribute(k_symbolic_rows<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    if (e != cudaSuccess) return e;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_symbolic_rows<true>, threads,
+                                                  smem);
+  } else {
+    e = cudaFuncSetAttribute(k_symbolic_rows<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    if (e != cudaSuccess) return e;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_symbolic_rows<false>,
+                                                  threads, smem);
+  }
+  if (blocks_per_sm < 1) blocks_per_sm = 1;
+  int64_t want = (n + warps - 1) / warps;
+  int64_t grid = (int64_t)blocks_per_sm * num_sms();
+  if (grid > want) grid = want;
+  if (grid < 1) grid = 1;
+  if (indep)
+    k_symbolic_rows<true><<<(unsigned)grid, threads, smem, s>>>(
+        n, arp, aci, k, ar.col, ar.lev, ar.cap, ar.top, ar.row_off, ar.row_len, ar.row_ust,
+        ar.ready, ar.ticket, err, cap, wait_limit());
+  else
+    k_symbolic_rows<false><<<(unsigned)grid, threads, smem, s>>>(
+        n, arp, aci, k, ar.col, ar.lev, ar.cap, ar.top, ar.row_off, ar.row_len, ar.row_ust,
+        ar.ready, ar.ticket, err, cap, wait_limit());
+  return cudaGetLastError();
+}
+
+// Copy every row from the arena into CSR order; record the diagonal position
+// and the longest row.
+__global__ void k_symbolic_compact(int64_t n, const int32_t *__restrict__ acol,
+                                   const uint8_t *__restrict__ alev,
+                                   const int64_t *__restrict__ row_off,
+                                   const int32_t *__restrict__ row_len,
+                                   const int32_t *__restrict__ row_ust,
+                                   const int64_t *__restrict__ frp, int32_t *fci, uint8_t *flev,
+                                   int64_t *fdiag, int32_t *maxrow) {
+  const int lane = threadIdx.x & 31;
+  int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t row = w; row < n; row += nw) {
+    const int64_t off = row_off[row], dst = frp[row];
+    const int len = row_len[row];
+    for (int q = lane; q < len; q += 32) {
+      fci[dst + q] = acol[off + q];
+      flev[dst + q] = alev[off + q];
+    }
+    if (lane == 0) {
+      fdiag[row] = dst + row_ust[row] - 1;
+      atomicMax(maxrow, len);
+    }
+  }
+}
+
+cudaError_t launch_symbolic_compact(int64_t n, const SymArena &ar, const int64_t *frp,
+                                    int32_t *fci, uint8_t *flev, int64_t *fdiag, int32_t *maxrow,
+                                    cudaStream_t s) {
+  int64_t blocks = (n * 32 + 255) / 256;
+  int64_t cap = (int64_t)num_sms() * 16;
+  if (blocks > cap) blocks = cap;
+  if (blocks < 1) blocks = 1;
+  k_symbolic_compact<<<(unsigned)blocks, 256, 0, s>>>(n, ar.col, ar.lev, ar.row_off, ar.row_len,
+                                                       ar.row_ust, frp, fci, flev, fdiag, maxrow);
+  return cudaGetLastError();
+}
+
+// a2f[p] = offset of A's entry p inside its F row (A's pattern is a subset).
+__global__ void k_a2f(int64_t n, const int64_t *__restrict__ arp, const int32_t *__restrict__ aci,
+                      const int64_t *__restrict__ frp, const int32_t *__restrict__ fci,
+                      int32_t *a2f) {
+  const int lane = threadIdx.x & 31;
+  int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t row = w; row < n; row += nw) {
+    const int64_t f0 = frp[row], f1 = frp[row + 1];
+    for (int64_t p = arp[row] + lane; p < arp[row + 1]; p += 32) {
+      const int64_t pos = lower_bound_l(fci, f0, f1, aci[p]);
+      a2f[p] = (int32_t)(pos - f0);
+    }
+  }
+}
+
+cudaError_t launch_a2f(int64_t n, const int64_t *arp, const int32_t *aci, const int64_t *frp,
+                       const int32_t *fci, int32_t *a2f, cudaStream_t s) {
+  int64_t blocks = (n * 32 + 255) / 256;
+  int64_t cap = (int64_t)num_sms() * 16;
+  if (blocks > cap) blocks = cap;
+  if (blocks < 1) blocks = 1;
+  k_a2f<<<(unsigned)blocks, 256, 0, s>>>(n, arp, aci, frp, fci, a2f);
+  return cudaGetLastError();
+}
+
+// Depth of each row in the dependency DAG of a sweep: 1 + max depth of the
+// rows it reads (lower part ascending, or upper part descending).  Warp per
+// row with ready flags, like the factorization itself.
+__global__ void k_depth(int64_t n, const int64_t *__restrict__ frp, const int32_t *__restrict__ fci,
+                        const int64_t *__restrict__ fdiag, int32_t *depth, int *ready,
+                        unsigned long long *ticket, int upper, int32_t *maxdepth, DevErr *err,
+                        int64_t limit_ns) {
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    unsigned long long tk = 0;
+    if (lane == 0) tk = atomicAdd(ticket, 1ull);
+    const int64_t t = (int64_t)__shfl_sync(FULL_MASK, tk, 0);
+    if (t >= n) return;
+    const int64_t row = upper ? n - 1 - t : t;
+    const int64_t b0 = upper ? fdiag[row] + 1 : frp[row];
+    const int64_t b1 = upper ? frp[row + 1] : fdiag[row];
+    int d = 0;
+    bool ok = true;
+    for (int64_t q = b0 + lane; q < b1; q += 32) {
+      const int h = fci[q];
+      if (!wait_flag(&ready[h], err, upper ? (n - 1 - row) : row, limit_ns)) {
+        ok = false;
+        break;
+      }
+      const int dh = *((volatile int32_t *)&depth[h]);
+      d = dh > d ? dh : d;
+    }
+    if (__any_sync(FULL_MASK, !ok)) {
+      if (lane == 0) set_err(err, upper ? (n - 1 - row) : row, ILUK_ETIMEOUT);
+      return;
+    }
+    d = __reduce_max_sync(FULL_MASK, d) + 1;
+    if (lane == 0) {
+      depth[row] = d;
+      atomicMax(maxdepth, d);
+    }
+    warp_publish(&ready[row], lane);
+  }
+}
+
+cudaError_t launch_depth(int64_t n, const int64_t *frp, const int32_t *fci, const int64_t *fdiag,
+                         int32_t *depth, int *ready, unsigned long long *ticket, int upper,
+                         int32_t *maxdepth, DevErr *err, cudaStream_t s) {
+  int64_t blocks = (n * 32 + 255) / 256;
+  int64_t cap = (int64_t)num_sms() * 8;
+  if (blocks > cap) blocks = cap;
+  if (blocks < 1) blocks = 1;
+  k_depth<<<(unsigned)blocks, 256, 0, s>>>(n, frp, fci, fdiag, depth, ready, ticket, upper,
+                                            maxdepth, err, wait_limit());
+  return cudaGetLastError();
+}
+
+}  // namespace iluk

@@ -1,0 +1,166 @@
+// tpiilu.cu -- a5: the level-based incomplete inverse (TPIILU, Sec. 3.5).
+//
+// Lower part (Eq. inversedefine restricted to F's lower pattern):
+//   beta_it = f_it - sum_{t<h<i} f_ih beta_ht,
+// one warp per row, rows ascending with ready flags: b_i. starts as the
+// final multipliers of row i; for each h in L(i) ascending, after row h is
+// final, b_it <- b_it - f_ih * beta_ht for every t < h stored in both rows.
+// The stored value is -beta (Eq. flipfactor), so a dependant reads
+// beta_ht = -g_ht, an exact negation.
+//
+// Upper part, the mirror image (rows last to first, pivots right to left):
+//   gamma_it = u^_it - sum_{i<h<t} u^_ih gamma_ht,  u^_it = u_it / u_ii,
+// stored as -gamma; the diagonal position keeps u_ii.
+//
+// Apply: z_i = (sum_{t<i} g_it p_t + p_i) / u_ii, then
+// y_i = sum_{t>i} g_it z_t + z_i; each sum runs left to right starting from
+// its first product, the own term added last (Eq. forwardsubB).
+#include "internal.h"
+
+namespace iluk {
+
+constexpr int kIiThreads = 256;
+
+template <bool LOWER>
+__global__ void __launch_bounds__(kIiThreads)
+k_iiluk_build(int64_t n, const int64_t *__restrict__ frp, const int32_t *__restrict__ fci,
+              const int64_t *__restrict__ fdiag, const double *__restrict__ fval, double *g,
+              int *ready, unsigned long long *ticket, DevErr *err, int cap, int64_t limit_ns) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  const int nwarps = blockDim.x >> 5;
+  double *sval = reinterpret_cast<double *>(smem) + (size_t)wib * cap;
+  int32_t *scol = reinterpret_cast<int32_t *>(smem + (size_t)nwarps * cap * 8) + (size_t)wib * cap;
+
+  for (;;) {
+    unsigned long long tk = 0;
+    if (lane == 0) tk = atomicAdd(ticket, 1ull);
+    const int64_t t = (int64_t)__shfl_sync(FULL_MASK, tk, 0);
+    if (t >= n) return;
+    if (earlier_failed(err, t)) continue;
+    const int64_t row = LOWER ? t : n - 1 - t;
+    const int64_t d = fdiag[row];
+    const int64_t s0 = LOWER ? frp[row] : d + 1;      // segment of the row handled here
+    const int m = (int)((LOWER ? d : frp[row + 1]) - s0);
+    const double uii = fval[d];
+    const bool in_smem = m <= cap;
+    const int32_t *rc = in_smem ? scol : fci + s0;
+    double *rv = in_smem ? sval : g + s0;  // long rows work in the output in place
+    for (int q = lane; q < m; q += 32) {
+      const double init = LOWER ? fval[s0 + q] : __ddiv_rn(fval[s0 + q], uii);
+      if (in_smem) scol[q] = fci[s0 + q];
+      rv[q] = init;
+    }
+    __syncwarp();
+    bool ok = true;
+    for (int qq = 0; qq < m; ++qq) {
+      const int q = LOWER ? qq : m - 1 - qq;  // pivots ascending / descending
+      const int h = rc[q];
+      if (!wait_flag(&ready[h], err, t, limit_ns)) {
+        ok = false;
+        break;
+      }
+      const double coef = LOWER ? fval[s0 + q] : __ddiv_rn(fval[s0 + q], uii);
+      const int64_t hd = fdiag[h];
+      const int64_t r0 = LOWER ? frp[h] : hd + 1;
+      const int64_t r1 = LOWER ? hd : frp[h + 1];
+      for (int64_t r = r0 + lane; r < r1; r += 32) {
+        const int32_t col = fci[r];
+        const double prev = -*((volatile double *)&g[r]);  // beta_ht or gamma_ht
+        const int pos = LOWER ? lower_bound_i(rc, 0, q, col) : lower_bound_i(rc, q + 1, m, col);
+        const int hi = LOWER ? q : m;
+        if (pos < hi && rc[pos] == col) rv[pos] = sub_prod(rv[pos], coef, prev);
+      }
+      __syncwarp();
+    }
+    if (!__all_sync(FULL_MASK, ok)) {
+      if (lane == 0 && !earlier_failed(err, t)) set_err(err, t, ILUK_ETIMEOUT);
+      continue;
+    }
+    for (int q = lane; q < m; q += 32) g[s0 + q] = -rv[q];
+    if (!LOWER && lane == 0) g[d] = uii;
+    warp_publish(&ready[row], lane);
+  }
+}
+
+cudaError_t launch_iiluk_build(const iluk_sym *S, const double *fval, double *g, int *sync,
+                               DevErr *err, cudaStream_t s) {
+  const int64_t n = S->n;
+  if (n == 0) return cudaSuccess;
+  int cap = S->max_row < 32 ? 32 : ((S->max_row + 31) & ~31);
+  int warps = kIiThreads / 32;
+  const size_t budget = (size_t)max_smem_optin();
+  while (warps > 1 && (size_t)cap * 12 * warps > budget) warps >>= 1;
+  if ((size_t)cap * 12 * warps > budget) cap = (int)(budget / 12 / warps) & ~31;
+  const size_t smem = (size_t)cap * 12 * warps;
+  unsigned long long *tick = reinterpret_cast<unsigned long long *>(sync);
+  int *fl_l = sync + 4, *fl_u = sync + 4 + n;
+  cudaError_t e = cudaMemsetAsync(sync, 0, (4 + 2 * (size_t)n) * sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  int bps = 0;
+  e = cudaFuncSetAttribute(k_iiluk_build<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_iiluk_build<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem);
+  if (e != cudaSuccess) return e;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_iiluk_build<true>, warps * 32, smem);
+  if (bps < 1) bps = 1;
+  int64_t grid = (int64_t)bps * num_sms();
+  const int64_t want = (n + warps - 1) / warps;
+  if (grid > want) grid = want;
+  k_iiluk_build<true><<<(unsigned)grid, warps * 32, smem, s>>>(
+      n, S->rowptr, S->colind, S->diag, fval, g, fl_l, tick, err, cap, wait_limit());
+  k_iiluk_build<false><<<(unsigned)grid, warps * 32, smem, s>>>(
+      n, S->rowptr, S->colind, S->diag, fval, g, fl_u, tick + 1, err + 1, cap, wait_limit());
+  return cudaGetLastError();
+}
+
+// Apply: warp per row, products in parallel, ordered left-to-right sum.
+template <bool LOWER>
+__global__ void __launch_bounds__(256)
+k_iiluk_apply(int64_t n, const int64_t *__restrict__ frp, const int32_t *__restrict__ fci,
+              const int64_t *__restrict__ fdiag, const double *__restrict__ g,
+              const double *__restrict__ in, double *__restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < n; row += nw) {
+    const int64_t d = fdiag[row];
+    const int64_t b0 = LOWER ? frp[row] : d + 1;
+    const int64_t b1 = LOWER ? d : frp[row + 1];
+    double s = 0.0;
+    bool first = true;
+    for (int64_t base = b0; base < b1; base += 32) {
+      const int64_t q = base + lane;
+      double prod = 0.0;
+      if (q < b1) prod = __dmul_rn(g[q], in[fci[q]]);
+      const int cnt = (b1 - base) < 32 ? (int)(b1 - base) : 32;
+      for (int l = 0; l < cnt; ++l) {
+        const double pr = __shfl_sync(FULL_MASK, prod, l);
+        s = first ? pr : __dadd_rn(s, pr);
+        first = false;
+      }
+    }
+    const double own = in[row];
+    double x = (b1 > b0) ? __dadd_rn(s, own) : own;
+    if (LOWER) x = __ddiv_rn(x, g[d]);
+    if (lane == 0) out[row] = x;
+  }
+}
+
+cudaError_t launch_iiluk_apply(const iluk_sym *S, const double *g, const double *p, double *tmp,
+                               double *y, cudaStream_t s) {
+  const int64_t n = S->n;
+  if (n == 0) return cudaSuccess;
+  int64_t blocks = (n * 32 + 255) / 256;
+  const int64_t cap = (int64_t)num_sms() * 8;
+  if (blocks > cap) blocks = cap;
+  k_iiluk_apply<true><<<(unsigned)blocks, 256, 0, s>>>(n, S->rowptr, S->colind, S->diag, g, p,
+                                                       tmp);
+  k_iiluk_apply<false><<<(unsigned)blocks, 256, 0, s>>>(n, S->rowptr, S->colind, S->diag, g, tmp,
+                                                        y);
+  return cudaGetLastError();
+}
+
+}  // namespace iluk

@@ -1,0 +1,123 @@
+"""Device-side error reporting: bad inputs are turned into statuses, never into
+GPU faults, and every row-to-row wait is bounded.
+
+All failures are made on the host (bad CSR arrays, a zero pivot, a NaN, a row
+whose completion is withheld by the test hook); none of them faults or hangs
+the GPU.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_0803_0048_gb300 as P
+from paper_0803_0048_gb300 import _lib as L
+from paper_0803_0048_gb300 import workloads as W
+
+from gpu_helpers import to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def dev_pattern(rp, ci):
+    return (torch.tensor(rp, dtype=torch.int64, device="cuda"),
+            torch.tensor(ci, dtype=torch.int32, device="cuda"))
+
+
+@pytest.mark.parametrize("rp,ci,row", [
+    ([0, 2, 3], [1, 0, 1], 0),        # unsorted
+    ([0, 2, 3], [0, 0, 1], 0),        # duplicate
+    ([0, 1, 3], [0, 0, 2], 1),        # out of range
+    ([0, 2, 1, 3], [0, 1, 1], 1),     # decreasing rowptr
+    ([0, 2, 3], [0, 1], 0),           # rowptr[n] != nnz
+])
+def test_bad_patterns_rejected(rp, ci, row):
+    r, c = dev_pattern(rp, ci)
+    st, bad = P.validate(r, c)
+    assert st == L.EPATTERN and bad == row
+    with pytest.raises(P.IlukError) as e:
+        P.symbolic(r, c, 1)
+    assert e.value.status == L.EPATTERN
+
+
+def test_missing_diagonal_and_fill_diagonal():
+    A = W.dense_to_csr(np.array([[1.0, 1.0, 0.0], [1.0, 0.0, 1.0], [0.0, 1.0, 1.0]]))
+    rp, ci, av = to_dev(A)
+    with pytest.raises(P.IlukError) as e:
+        P.symbolic(rp, ci, 0)
+    assert e.value.status == L.ENODIAG and e.value.row == 1
+    S = P.symbolic(rp, ci, 1)  # (1,1) enters as a level-1 fill through h = 0
+    _, _, lev, dg = S.pattern()
+    assert lev[dg[1]].item() == 1
+
+
+def test_zero_pivot_reports_first_row():
+    n = 300
+    A = W.random_sparse(n, 0.02, 3)
+    D = W.csr_to_dense(A)
+    D[40, 40] = 0.0
+    D[200, 200] = 0.0
+    mask = W.csr_to_dense(A) != 0
+    A2 = W.dense_to_csr(D, mask)
+    st, bad, frp, fci, _ = oracle.symbolic(n, A2.rowptr, A2.colind, 1)
+    st, bad, _ = oracle.numeric(n, A2.rowptr, A2.colind, A2.val, frp, fci)
+    rp, ci, av = to_dev(A2)
+    S = P.symbolic(rp, ci, 1)
+    with pytest.raises(P.IlukError) as e:
+        P.numeric(S, av)
+    assert e.value.status == L.EZEROPIVOT == st
+    assert e.value.row == bad
+
+
+def test_nonfinite_value():
+    A = W.random_sparse(100, 0.05, 4)
+    A.val[A.rowptr[30]] = np.nan
+    rp, ci, av = to_dev(A)
+    S = P.symbolic(rp, ci, 2)
+    with pytest.raises(P.IlukError) as e:
+        P.numeric(S, av)
+    assert e.value.status == L.ENONFINITE and e.value.row == 30
+
+
+def test_bounded_wait_times_out_and_gpu_stays_usable():
+    A = W.conv_diff(16, 2, (1.0, 1.0))
+    rp, ci, av = to_dev(A)
+    S = P.symbolic(rp, ci, 1)
+    old = P.set_wait_limit(50_000_000)  # 50 ms
+    P.debug_hold_row(100)
+    try:
+        with pytest.raises(P.IlukError) as e:
+            P.numeric(S, av)
+        assert e.value.status == L.ETIMEOUT
+        assert e.value.row > 100
+    finally:
+        P.debug_hold_row(-1)
+        P.set_wait_limit(old)
+    F = P.numeric(S, av)  # the context is still healthy
+    ref = oracle.factor(A, 1)
+    assert np.array_equal(F.values().cpu().numpy(), ref["val"])
+
+
+def test_empty_and_single_row():
+    rp, ci = dev_pattern([0], [])
+    S = P.symbolic(rp, ci, 2)
+    assert S.n == 0 and S.nnz == 0
+    rp, ci = dev_pattern([0, 1], [0])
+    S = P.symbolic(rp, ci, 2)
+    F = P.numeric(S, torch.tensor([4.0], dtype=torch.float64, device="cuda"))
+    y = F.apply(torch.tensor([2.0], dtype=torch.float64, device="cuda"))
+    assert y.item() == 0.5
+
+
+def test_gmres_reports_nonconvergence():
+    A = W.conv_diff(20, 2, (20.0, 20.0))
+    rp, ci, av = to_dev(A)
+    b = torch.ones(A.n, dtype=torch.float64, device="cuda")
+    x, info = P.gmres(rp, ci, av, b, None, restart=5, rtol=1e-12, maxit=12, check=False)
+    assert info.status == L.ENOCONV and info.iters == 12
