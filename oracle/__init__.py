@@ -151,7 +151,7 @@ def lsolve(n, frp, fci, fv, p):
 
 
 def usolve(n, frp, fci, fv, x):
-    """Backward sweep with U~ (divide by u_ii last)."""
+    """Backward sweep with U~, each row right to left, divide by u_ii last."""
     return _vec_call("orc_usolve", n, frp, fci, fv, x)
 
 

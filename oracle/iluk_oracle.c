@@ -225,8 +225,12 @@ int orc_numeric(int64_t n, const int64_t *arp, const int32_t *aci, const double 
 
 /* ------------------------------------------------------------------------ */
 /* Triangular sweeps, Eq. triangleSolve: L~ U~ y = p.                        */
-/* Forward (Eq. forwardsubA): x_i = p_i - sum_{h<i} f_ih x_h, h ascending.   */
-/* Backward: y_i = (x_i - sum_{j>i} f_ij y_j) / f_ii, j ascending.           */
+/* Forward (Eq. forwardsubA): x_i = p_i - sum_{h<i} f_ih x_h, h ascending    */
+/* (left to right, farthest column first).                                   */
+/* Backward: y_i = (x_i - sum_{j>i} f_ij y_j) / f_ii, j descending: the      */
+/* mirror image of the forward sweep, rows last to first and each row right  */
+/* to left (the order Sec. 3.5 gives for the upper factor), so again the     */
+/* farthest column is subtracted first and the nearest last.                 */
 /* ------------------------------------------------------------------------ */
 static int64_t diag_pos(const int64_t *frp, const int32_t *fci, int64_t i)
 {
@@ -252,7 +256,7 @@ void orc_usolve(int64_t n, const int64_t *frp, const int32_t *fci, const double 
   for (int64_t i = n - 1; i >= 0; --i) {
     int64_t d = diag_pos(frp, fci, i);
     double s = x[i];
-    for (int64_t q = d + 1; q < frp[i + 1]; ++q) {
+    for (int64_t q = frp[i + 1] - 1; q > d; --q) {
       double prod = fv[q] * y[fci[q]];
       s = s - prod;
     }
@@ -295,7 +299,7 @@ void orc_transpose(int64_t n, const int64_t *rp, const int32_t *ci, const double
 /* column <= i (diagonal u_ii at column i), L~^T the part with column > i    */
 /* (unit diagonal).                                                          */
 /* Forward:  z_i = (p_i - sum_{c<i} t_ic z_c) / t_ii, c ascending.           */
-/* Backward: y_i = z_i - sum_{c>i} t_ic y_c, c ascending, i = n-1..0.         */
+/* Backward: y_i = z_i - sum_{c>i} t_ic y_c, c descending, i = n-1..0.        */
 void orc_apply_t(int64_t n, const int64_t *trp, const int32_t *tci, const double *tv,
                  const double *p, double *y)
 {
@@ -312,7 +316,7 @@ void orc_apply_t(int64_t n, const int64_t *trp, const int32_t *tci, const double
   for (int64_t i = n - 1; i >= 0; --i) {
     int64_t d = diag_pos(trp, tci, i);
     double s = z[i];
-    for (int64_t q = d + 1; q < trp[i + 1]; ++q) {
+    for (int64_t q = trp[i + 1] - 1; q > d; --q) {
       double prod = tv[q] * y[tci[q]];
       s = s - prod;
     }
