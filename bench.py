@@ -1,0 +1,349 @@
+#!/usr/bin/env python
+"""Benchmark of the ILU(k)-preconditioned solve on one GB300.
+
+Workload (default): the random banded non-symmetric system with n = 160,000
+rows, 9 off-diagonals per row inside |j - i| <= 2000, values uniform in
+[-1, 1] and diagonal 1.2 * sum |a_ij|, b = A x* for a uniform x*.  One step is
+one pass of the whole hot path on it: pattern check + symbolic ILU(2) +
+numeric ILU(2) + right-preconditioned GMRES(50) with the ILU(2) sweeps to a
+1e-8 relative residual, all in libiluk's kernels.
+
+Printed: one JSON line with ms per step (device-timed, inputs resident in
+HBM), the same measured end to end from pinned host buffers, the roofline of
+the dominant kernel, the sequential CPU oracle as a baseline, clocks sampled
+during the timed region, and per-phase times.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--k 2] [--impl reference]
+
+With --impl reference the arm timed is the sequential oracle (C, one host
+core) on the same workload and metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ILU(k) factor+apply ms & HBM GB/s (% peak); batched/adjoint vs plain, 1e-8 res"
+L2_BYTES = 129 * 1024 * 1024
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--k", type=int, default=2)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-steps", type=int, default=2, help="oracle steps for cpu_baseline")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def workload(k):
+    from paper_0803_0048_gb300 import workloads as W
+    return W.random_band_160k(k=k)
+
+
+def alg_bytes(n, nnzA, nnzF, nnzL):
+    """Compulsory bytes per launch of each kernel kind (each array touched once)."""
+    nnzU = nnzF - nnzL
+    return {
+        # A values + A->F map + both row-pointer arrays + F columns + diagonal + F values out
+        "numeric": 12 * nnzA + 16 * (n + 1) + 4 * nnzF + 8 * n + 8 * nnzF,
+        # read A pattern, write F pattern + levels via the arena, diagonal
+        "symbolic": 8 * (n + 1) + 4 * nnzA + 5 * nnzF,
+        # one sweep: its half of F (cols + vals), row pointers, diagonal, in/out vectors
+        "sweep": (12 * nnzL + 8 * (n + 1) + 8 * n + 24 * n + 12 * nnzU + 8 * (n + 1) + 8 * n
+                  + 24 * n) / 2.0,
+        "spmv": 12 * nnzA + 8 * (n + 1) + 16 * n,
+    }
+
+
+def ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_0803_0048_gb300 as P
+    from paper_0803_0048_gb300 import _lib as L
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+
+    Pb = workload(args.k)
+    A = Pb.A
+    n, nnzA = A.n, A.nnz
+    rp = torch.from_numpy(A.rowptr).to(dev)
+    ci = torch.from_numpy(A.colind).to(dev)
+    av = torch.from_numpy(A.val).to(dev)
+    b = torch.from_numpy(Pb.b).to(dev)
+    stream = torch.cuda.current_stream()
+
+    sched = [L.SCHED_AUTO]
+
+    def step(rp_, ci_, av_, b_):
+        st, row = P.validate(rp_, ci_)
+        assert st == 0
+        S = P.symbolic(rp_, ci_, Pb.k)
+        F = P.numeric(S, av_)
+        F.set_schedule(sched[0])
+        x, info = P.gmres(rp_, ci_, av_, b_, F, restart=Pb.restart, rtol=Pb.rtol)
+        return S, F, x, info
+
+    # warm-up (the first apply times both sweep schedules; keep its choice)
+    for _ in range(max(args.warmup, 1)):
+        S, F, x, info = step(rp, ci, av, b)
+        sched[0] = F.schedule()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # device-timed region: inputs resident in HBM (F alone is larger than L2)
+    launches0 = P.launch_count()
+    P.prof_enable(True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            S, F, x, info = step(rp, ci, av, b)
+        ev1.record(stream)
+        barrier()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    prof = P.prof_read()
+    P.prof_enable(False)
+    launches = (P.launch_count() - launches0) // args.steps
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # end to end through the public API from pinned host buffers
+    h_rp = torch.from_numpy(A.rowptr).pin_memory()
+    h_ci = torch.from_numpy(A.colind).pin_memory()
+    h_av = torch.from_numpy(A.val).pin_memory()
+    h_b = torch.from_numpy(Pb.b).pin_memory()
+    h_x = torch.empty(n, dtype=torch.float64).pin_memory()
+    d_rp, d_ci, d_av, d_b = (torch.empty_like(t, device=dev) for t in (h_rp, h_ci, h_av, h_b))
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        for d, h in ((d_rp, h_rp), (d_ci, h_ci), (d_av, h_av), (d_b, h_b)):
+            d.copy_(h, non_blocking=True)
+        S2, F2, x2, info2 = step(d_rp, d_ci, d_av, d_b)
+        h_x.copy_(x2, non_blocking=True)
+    e1.record(stream)
+    barrier()
+    ms_e2e = e0.elapsed_time(e1) / args.steps
+    h2d = h_rp.numel() * 8 + h_ci.numel() * 4 + h_av.numel() * 8 + h_b.numel() * 8
+    d2h = n * 8
+
+    # structure of the factors (for the roofline numerators)
+    frp, fci, flev, fdg = [t.cpu().numpy() for t in S.pattern()]
+    nnzF = int(frp[-1])
+    nnzL = int(np.sum(fdg - frp[:-1]))
+    depth = S.depth()
+    ab = alg_bytes(n, nnzA, nnzF, nnzL)
+    hbm, peak_src = measured_peaks()
+    kinds = {"numeric": "numeric", "symbolic": "symbolic", "sweep": "sweep", "spmv": "spmv"}
+    per_kind = {}
+    for kname, (tot_ms, cnt) in prof.items():
+        if cnt:
+            per_kind[kname] = {"ms_total_per_step": tot_ms / args.steps,
+                               "launches_per_step": cnt / args.steps,
+                               "ms_per_launch": tot_ms / cnt}
+    dom = max((k for k in per_kind if k in kinds), key=lambda k: per_kind[k]["ms_total_per_step"])
+    dur_s = per_kind[dom]["ms_per_launch"] / 1e3
+    achieved = ab[dom] / dur_s / 1e9
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tpath):
+        with open(tpath) as f:
+            traffic = json.load(f).get(f"{dom}_k{Pb.k}")
+
+    out = {
+        "metric": METRIC, "value": round(ms, 4), "unit": "ms", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"random_band_n{n}_hw2000_k{Pb.k}_gmres{Pb.restart}_rtol1e-8",
+                   "n": n, "nnz_A": nnzA, "nnz_F": nnzF, "k": Pb.k, "restart": Pb.restart,
+                   "rtol": Pb.rtol, "depth_lower": depth[0], "depth_upper": depth[1],
+                   "l2": f"inputs larger than L2: F is {(12 * nnzF) / 2**20:.0f} MiB > 129 MiB",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "roofline": {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 3), "peak": hbm,
+                     "unit": "GB/s", "frac": round(achieved / hbm, 6), "traffic": traffic,
+                     "alg_bytes_per_launch": ab[dom], "peak_source": peak_src},
+        "e2e": {"value": round(ms_e2e, 4), "unit": "ms", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+        "gmres": {"iters": info.iters, "relres": info.relres, "sched": ["auto", "flags",
+                  "single_cta"][sched[0]]},
+        "kernels": per_kind,
+    }
+
+    if rank == 0 and not args.no_cpu:
+        out["cpu_baseline"], parity = cpu_baseline(Pb, args.cpu_steps, F.values().cpu().numpy(),
+                                                   x.cpu().numpy())
+        out["parity"] = parity
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def oracle_step(Pb):
+    import oracle
+    A = Pb.A
+    st, bad = oracle.check_pattern(A.n, A.rowptr, A.colind)
+    F = oracle.factor(A, Pb.k)
+    st, x, it, rel, _ = oracle.gmres(A.n, A.rowptr, A.colind, A.val, Pb.b, oracle.PREC_ILU,
+                                     (F["rowptr"], F["colind"], F["val"]), Pb.restart, Pb.rtol,
+                                     dotmode=oracle.DOT_TREE)
+    return F, x, it
+
+
+def cpu_baseline(Pb, steps, fv_gpu=None, x_gpu=None):
+    import oracle
+    oracle.build()
+    ts = []
+    for _ in range(max(steps, 1)):
+        t0 = time.perf_counter()
+        F, x, it = oracle_step(Pb)
+        ts.append(time.perf_counter() - t0)
+    ms = 1e3 * statistics.median(ts)
+    parity = None
+    if fv_gpu is not None:
+        fo = F["val"]
+        parity = {"factor_ulp_mismatches": int(np.sum(fo.view(np.int64) != fv_gpu.view(np.int64))),
+                  "x_bit_mismatches": int(np.sum(x.view(np.int64) != x_gpu.view(np.int64))),
+                  "oracle_iters": it}
+    return ({"value": round(ms, 2), "unit": "ms", "cores": 1, "kind": "oracle",
+             "sample": f"{len(ts)} full steps (pattern check + symbolic + numeric + GMRES, "
+                       f"fixed-tree dots) of the same workload, median"}, parity)
+
+
+def reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    Pb = workload(args.k)
+    for _ in range(args.warmup):
+        oracle_step(Pb)
+    ts = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle_step(Pb)
+        ts.append(time.perf_counter() - t0)
+    ms = 1e3 * sum(ts) / len(ts)
+    out = {"impl": "reference", "metric": METRIC, "value": round(ms, 3), "unit": "ms",
+           "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": round(ms, 3), "higher_is_better": False, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": f"random_band_n{Pb.A.n}_hw2000_k{Pb.k}_gmres{Pb.restart}_rtol1e-8"},
+           "cpu_baseline": {"value": round(ms, 3), "unit": "ms", "cores": 1, "kind": "oracle",
+                            "sample": "each step one full oracle pass of the workload"},
+           "e2e": {"value": round(ms, 3), "unit": "ms", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference(args)
+    else:
+        ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -116,6 +116,23 @@ int64_t iluk_set_wait_limit(int64_t ns);
  * the previous value.  Host-side, whole process. */
 int64_t iluk_debug_hold_row(int64_t row);
 
+/* Number of CUDA kernels this library has launched in the process so far
+ * (memsets and copies are not counted). */
+int64_t iluk_launch_count(void);
+
+/* Kernel timing.  While enabled, every kernel launch of the kinds below is
+ * bracketed by CUDA events on its own stream.  iluk_prof_read synchronizes
+ * those events and fills ms[kind] (total milliseconds) and count[kind]
+ * (launches) for kind < nkinds (host arrays).  Enabling clears the records. */
+enum {
+  ILUK_PROF_VALIDATE = 0, ILUK_PROF_SYMBOLIC = 1, ILUK_PROF_COMPACT = 2, ILUK_PROF_DEPTH = 3,
+  ILUK_PROF_NUMERIC = 4, ILUK_PROF_SWEEP = 5 /* forward sweeps */, ILUK_PROF_TRANSPOSE = 6, ILUK_PROF_IILU_BUILD = 7,
+  ILUK_PROF_IILU_APPLY = 8, ILUK_PROF_SPMV = 9, ILUK_PROF_DOT = 10, ILUK_PROF_VECTOR = 11,
+  ILUK_PROF_SWEEP_BWD = 12, ILUK_PROF_KINDS = 13
+};
+int iluk_prof_enable(int on);
+int iluk_prof_read(double *ms, int64_t *count, int nkinds);
+
 /*
  * a1. Pattern check (sparse storage, Sec. 2.1).  Synchronous.
  * Checks rowptr[0] = 0, rowptr non-decreasing, rowptr[n] = nnz, every column in

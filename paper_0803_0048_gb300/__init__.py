@@ -7,9 +7,11 @@ declared in include/iluk.h); this package is its thin Python binding.
 """
 from . import _lib
 from .api import (CsrPattern, Factors, IlukError, IncompleteInverse, Symbolic, adjoint_scatter,
-                  debug_hold_row, dot, gmres, iiluk_build, numeric, numeric_batched,
-                  set_wait_limit, spmv, symbolic, validate)
+                  debug_hold_row, dot, gmres, iiluk_build, launch_count, numeric,
+                  numeric_batched, prof_enable, prof_read, set_wait_limit, spmv, symbolic,
+                  validate)
 
 __all__ = ["CsrPattern", "Factors", "IlukError", "IncompleteInverse", "Symbolic",
-           "adjoint_scatter", "debug_hold_row", "dot", "gmres", "iiluk_build", "numeric",
-           "numeric_batched", "set_wait_limit", "spmv", "symbolic", "validate"]
+           "adjoint_scatter", "debug_hold_row", "dot", "gmres", "iiluk_build", "launch_count",
+           "numeric", "numeric_batched", "prof_enable", "prof_read", "set_wait_limit", "spmv",
+           "symbolic", "validate"]

@@ -16,6 +16,8 @@ LIB_PATH = os.path.join(HERE, "_build", "libiluk.so")
 OK, EINVAL, EPATTERN, ENODIAG, EZEROPIVOT, ENONFINITE, ENOMEM, ETIMEOUT, ENOCONV, ECUDA = range(10)
 PREC_NONE, PREC_ILU, PREC_IILU = 0, 1, 2
 SCHED_AUTO, SCHED_FLAGS, SCHED_SINGLE_CTA = 0, 1, 2
+PROF_KINDS = ["validate", "symbolic", "compact", "depth", "numeric", "sweep", "transpose",
+              "iilu_build", "iilu_apply", "spmv", "dot", "vector", "sweep_bwd"]
 
 
 class Pattern(C.Structure):
@@ -43,6 +45,9 @@ SIGNATURES = [
     ("iluk_strerror", C.c_char_p, [I]),
     ("iluk_set_wait_limit", I64, [I64]),
     ("iluk_debug_hold_row", I64, [I64]),
+    ("iluk_launch_count", I64, []),
+    ("iluk_prof_enable", I, [I]),
+    ("iluk_prof_read", I, [P, P, I]),
     ("iluk_validate", I, [P, P, P]),
     ("iluk_symbolic", I, [P, I, PP, P, P]),
     ("iluk_sym_query", I, [P, P]),

@@ -274,3 +274,21 @@ def set_wait_limit(ns: int) -> int:
 
 def debug_hold_row(row: int) -> int:
     return L.load().iluk_debug_hold_row(int(row))
+
+
+def launch_count() -> int:
+    """Kernels launched by libiluk in this process so far."""
+    return int(L.load().iluk_launch_count())
+
+
+def prof_enable(on: bool = True) -> None:
+    L.load().iluk_prof_enable(int(on))
+
+
+def prof_read() -> dict:
+    """{kind: (total ms, launches)} for the kernels timed since prof_enable."""
+    nk = len(L.PROF_KINDS)
+    ms = (C.c_double * nk)()
+    cnt = (C.c_int64 * nk)()
+    _call(L.load().iluk_prof_read, ms, cnt, nk)
+    return {L.PROF_KINDS[k]: (ms[k], cnt[k]) for k in range(nk)}

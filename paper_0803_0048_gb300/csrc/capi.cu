@@ -30,6 +30,7 @@ int64_t initial_wait_limit() {
 }
 std::atomic<int64_t> g_wait_limit_ns{initial_wait_limit()};
 std::atomic<int64_t> g_hold_row{-1};
+std::atomic<int64_t> g_launches{0};
 
 struct DevCache {
   int sms = 0, smem = 0;
@@ -113,6 +114,44 @@ int64_t next_pow2(int64_t v) {
 namespace iluk {
 int64_t wait_limit() { return g_wait_limit_ns.load(); }
 int64_t hold_row() { return g_hold_row.load(); }
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+namespace {
+struct ProfRec {
+  int kind;
+  cudaEvent_t e0, e1;
+};
+std::atomic<bool> g_prof{false};
+std::mutex g_prof_mu;
+std::vector<ProfRec> g_prof_recs;
+std::vector<cudaEvent_t> g_prof_pool;
+
+cudaEvent_t prof_event() {
+  if (!g_prof_pool.empty()) {
+    cudaEvent_t e = g_prof_pool.back();
+    g_prof_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+}  // namespace
+
+bool prof_on() { return g_prof.load(std::memory_order_relaxed); }
+
+int prof_begin(int kind, cudaStream_t s) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  ProfRec r{kind, prof_event(), prof_event()};
+  cudaEventRecord(r.e0, s);
+  g_prof_recs.push_back(r);
+  return (int)g_prof_recs.size() - 1;
+}
+
+void prof_end(int slot, cudaStream_t s) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  if (slot >= 0 && slot < (int)g_prof_recs.size()) cudaEventRecord(g_prof_recs[slot].e1, s);
+}
 int num_sms() { return dev().sms; }
 int max_smem_optin() { return dev().smem; }
 }  // namespace iluk
@@ -142,6 +181,40 @@ int64_t iluk_set_wait_limit(int64_t ns) {
 
 int64_t iluk_debug_hold_row(int64_t row) { return g_hold_row.exchange(row); }
 
+int64_t iluk_launch_count(void) { return g_launches.load(); }
+
+int iluk_prof_enable(int on) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  if (on) {
+    for (auto &r : g_prof_recs) {
+      cudaEventSynchronize(r.e1);
+      g_prof_pool.push_back(r.e0);
+      g_prof_pool.push_back(r.e1);
+    }
+    g_prof_recs.clear();
+  }
+  g_prof.store(on != 0);
+  return ILUK_OK;
+}
+
+int iluk_prof_read(double *ms, int64_t *count, int nkinds) {
+  if (nkinds < 0 || (nkinds > 0 && (!ms || !count))) return ILUK_EINVAL;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  for (int k = 0; k < nkinds; ++k) {
+    ms[k] = 0.0;
+    count[k] = 0;
+  }
+  for (auto &r : g_prof_recs) {
+    if (r.kind < 0 || r.kind >= nkinds) continue;
+    if (cudaEventSynchronize(r.e1) != cudaSuccess) return ILUK_ECUDA;
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, r.e0, r.e1) != cudaSuccess) return ILUK_ECUDA;
+    ms[r.kind] += t;
+    count[r.kind] += 1;
+  }
+  return ILUK_OK;
+}
+
 int iluk_validate(const iluk_pattern *A, iluk_info *info, void *stream) {
   info_init(info);
   if (!A || A->n < 0 || A->nnz < 0 || !A->rowptr || (A->nnz > 0 && !A->colind))
@@ -167,6 +240,8 @@ void iluk_sym_destroy(iluk_sym *S) {
   dfree(S->diag, s);
   dfree(S->arowptr, s);
   dfree(S->a2f, s);
+  dfree(S->lord.order, s);
+  dfree(S->uord.order, s);
   delete S;
 }
 
@@ -218,7 +293,7 @@ int iluk_symbolic(const iluk_pattern *A, int k, iluk_sym **out, iluk_info *info,
   CKS(dalloc(&ar.top, 1, s));
 
   // Capacity of a row in shared memory and of the arena; grown on demand.
-  int cap = 256;
+  int cap = k <= 1 ? 256 : 1024;
   int64_t mult = (k == 0) ? 1 : (k == 1) ? 8 : (k == 2) ? 17 : 65;
   int64_t arena_cap = nnz * mult + 1024;
   const int max_cap = max_smem_optin() / 5 / 32 * 32;
@@ -294,6 +369,15 @@ int iluk_symbolic(const iluk_pattern *A, int k, iluk_sym **out, iluk_info *info,
   S->max_row = mr;
   dfree(maxrow, s);
   cleanup();
+  // level orders of the two sweeps
+  st = build_levels(n, S->rowptr, S->colind, S->diag, true, &S->lord, s);
+  if (st == ILUK_OK) st = build_levels(n, S->rowptr, S->colind, S->diag, false, &S->uord, s);
+  if (st != ILUK_OK) {
+    iluk_sym_destroy(S);
+    return fail(info, st);
+  }
+  S->depth_lower = S->lord.nlev;
+  S->depth_upper = S->uord.nlev;
 #undef CKS
   *out = S;
   return fail(info, ILUK_OK);
@@ -329,40 +413,8 @@ int iluk_sym_export(const iluk_sym *S, int64_t *rowptr, int32_t *colind, uint8_t
 }
 
 int iluk_sym_depth(iluk_sym *S, int32_t *depth_lower, int32_t *depth_upper, void *stream) {
-  iluk_info *info = nullptr;
+  (void)stream;
   if (!S) return ILUK_EINVAL;
-  cudaStream_t s = (cudaStream_t)stream;
-  if (S->depth_lower < 0) {
-    const int64_t n = S->n;
-    int32_t *depth = nullptr, *mx = nullptr;
-    int *ready = nullptr;
-    unsigned long long *ticket = nullptr;
-    DevErr *err = nullptr;
-    CK(dalloc(&depth, n, s));
-    CK(dalloc(&mx, 2, s));
-    CK(dalloc(&ready, n, s));
-    CK(dalloc(&ticket, 1, s));
-    CK(dalloc(&err, 1, s));
-    CK(cudaMemsetAsync(mx, 0, 2 * sizeof(int32_t), s));
-    CK(launch_fill_err(err, s));
-    for (int upper = 0; upper < 2; ++upper) {
-      CK(cudaMemsetAsync(ready, 0, n * sizeof(int), s));
-      CK(cudaMemsetAsync(ticket, 0, sizeof(unsigned long long), s));
-      CK(launch_depth(n, S->rowptr, S->colind, S->diag, depth, ready, ticket, upper, mx + upper,
-                      err, s));
-    }
-    int32_t h[2] = {0, 0};
-    CK(cudaMemcpyAsync(h, mx, sizeof(h), cudaMemcpyDeviceToHost, s));
-    int st = read_err(err, s, nullptr, nullptr);
-    dfree(depth, s);
-    dfree(mx, s);
-    dfree(ready, s);
-    dfree(ticket, s);
-    dfree(err, s);
-    if (st != ILUK_OK) return st;
-    S->depth_lower = h[0];
-    S->depth_upper = h[1];
-  }
   if (depth_lower) *depth_lower = S->depth_lower;
   if (depth_upper) *depth_upper = S->depth_upper;
   return ILUK_OK;
@@ -379,6 +431,8 @@ void iluk_fac_destroy(iluk_fac *F) {
   dfree(F->tcolind, s);
   dfree(F->tdiag, s);
   dfree(F->tval, s);
+  dfree(F->tlord.order, s);
+  dfree(F->tuord.order, s);
   delete F;
 }
 
@@ -392,7 +446,8 @@ static int numeric_into(iluk_fac *F, const double *A_val, iluk_info *info, cudaS
   int64_t row;
   int st = read_err(F->err, s, &row, nullptr);
   CK(launch_fill_err(F->err, s));
-  // factor values changed: drop the transpose
+  // factor values changed: drop the transpose (its level orders depend only
+  // on the pattern and are kept)
   dfree(F->trowptr, s);
   dfree(F->tcolind, s);
   dfree(F->tdiag, s);
@@ -412,6 +467,7 @@ int iluk_numeric(const iluk_sym *S, const double *A_val, iluk_fac **out, iluk_in
   if (e == cudaSuccess) e = dalloc(&F->sync, sweep_sync_ints(S->n), s);
   if (e == cudaSuccess) e = dalloc(&F->tmp, S->n, s);
   if (e == cudaSuccess) e = dalloc(&F->err, 2, s);
+  if (e == cudaSuccess) e = launch_fill_pending(S->n, F->tmp, s);
   if (e != cudaSuccess) {
     iluk_fac_destroy(F);
     return fail(info, e == cudaErrorMemoryAllocation ? ILUK_ENOMEM : ILUK_ECUDA);
@@ -452,6 +508,7 @@ int iluk_fac_status(iluk_fac *F, iluk_info *info, void *stream) {
   cudaStream_t s = (cudaStream_t)stream;
   int64_t row;
   int st = read_err(F->err, s, &row, nullptr);
+  if (st != ILUK_OK) CK(launch_fill_pending(F->S->n, F->tmp, s));  // an aborted sweep
   CK(launch_fill_err(F->err, s));
   return fail(info, st, row);
 }
@@ -472,6 +529,12 @@ static int ensure_transpose(iluk_fac *F, cudaStream_t s) {
                       F->tval, F->tdiag, cursor, scan_tmp, s));
   dfree(cursor, s);
   dfree(scan_tmp, s);
+  if (!F->tlord.order && S->n) {
+    int st = build_levels(S->n, F->trowptr, F->tcolind, F->tdiag, true, &F->tlord, s);
+    if (st == ILUK_OK)
+      st = build_levels(S->n, F->trowptr, F->tcolind, F->tdiag, false, &F->tuord, s);
+    if (st != ILUK_OK) return st;
+  }
   return ILUK_OK;
 }
 
@@ -498,8 +561,8 @@ static int pick_schedule(iluk_fac *F, cudaStream_t s) {
     float ms_min = 1e30f;
     for (int rep = 0; rep < 3; ++rep) {
       cudaEventRecord(e0, s);
-      launch_apply(S->n, S->rowptr, S->colind, S->diag, F->val, p, F->tmp, y, F->sync, 0, sched,
-                   F->err, s);
+      launch_apply(S->n, S->rowptr, S->colind, S->diag, F->val, S->lord, S->uord, p, F->tmp, y, 0,
+                   sched, F->err, s);
       cudaEventRecord(e1, s);
       cudaEventSynchronize(e1);
       float ms = 0;
@@ -529,11 +592,11 @@ int iluk_apply_sched(iluk_fac *F, const double *p, double *y, int transpose, int
   if (transpose) {
     int st = ensure_transpose(F, s);
     if (st != ILUK_OK) return st;
-    CK(launch_apply(S->n, F->trowptr, F->tcolind, F->tdiag, F->tval, p, F->tmp, y, F->sync, 1,
-                    sched, F->err, s));
+    CK(launch_apply(S->n, F->trowptr, F->tcolind, F->tdiag, F->tval, F->tlord, F->tuord, p,
+                    F->tmp, y, 1, sched, F->err, s));
   } else {
-    CK(launch_apply(S->n, S->rowptr, S->colind, S->diag, F->val, p, F->tmp, y, F->sync, 0, sched,
-                    F->err, s));
+    CK(launch_apply(S->n, S->rowptr, S->colind, S->diag, F->val, S->lord, S->uord, p, F->tmp, y,
+                    0, sched, F->err, s));
   }
   return ILUK_OK;
 }
@@ -743,10 +806,10 @@ int gmres_solve(const iluk_pattern *A, const double *A_val, int prec_kind, void 
   auto precond = [&](const double *in, double *outv) -> cudaError_t {
     if (F) {
       if (transpose)
-        return launch_apply(n, F->trowptr, F->tcolind, F->tdiag, F->tval, in, F->tmp, outv,
-                            F->sync, 1, sched, F->err, s);
-      return launch_apply(n, F->S->rowptr, F->S->colind, F->S->diag, F->val, in, F->tmp, outv,
-                          F->sync, 0, sched, F->err, s);
+        return launch_apply(n, F->trowptr, F->tcolind, F->tdiag, F->tval, F->tlord, F->tuord,
+                            in, F->tmp, outv, 1, sched, F->err, s);
+      return launch_apply(n, F->S->rowptr, F->S->colind, F->S->diag, F->val, F->S->lord,
+                          F->S->uord, in, F->tmp, outv, 0, sched, F->err, s);
     }
     if (M) return launch_iiluk_apply(M->S, M->g, in, M->tmp, outv, s);
     return cudaMemcpyAsync(outv, in, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
@@ -841,6 +904,7 @@ int gmres_solve(const iluk_pattern *A, const double *A_val, int prec_kind, void 
     int pst = read_err(F->err, s, &prow, nullptr);
     if (pst != ILUK_OK) {
       launch_fill_err(F->err, s);
+      launch_fill_pending(n, F->tmp, s);
       status = pst;
     }
   }

@@ -6,6 +6,14 @@
 
 #include "common.cuh"
 
+// Rows of one sweep DAG in level order, every level padded with -1 to a
+// multiple of 32 entries (see levels.cu).
+struct LevelOrder {
+  int32_t *order = nullptr;
+  int64_t len = 0;
+  int32_t nlev = 0;
+};
+
 // Handle layouts (opaque in the public header).
 struct iluk_sym {
   int64_t n = 0, nnz = 0, nnzA = 0;
@@ -18,6 +26,7 @@ struct iluk_sym {
   int32_t *a2f = nullptr;      // offset of each A entry inside its F row
   int32_t max_row = 0;
   int32_t depth_lower = -1, depth_upper = -1;
+  LevelOrder lord, uord;       // forward / backward sweep level orders
 };
 
 struct iluk_fac {
@@ -31,6 +40,7 @@ struct iluk_fac {
   int32_t *tcolind = nullptr;
   int64_t *tdiag = nullptr;
   double *tval = nullptr;
+  LevelOrder tlord, tuord;        // level orders of the transposed sweeps
   int sched = 0;                  // schedule picked for the sweeps (ILUK_SCHED_*)
 };
 
@@ -43,6 +53,21 @@ struct iiluk {
 namespace iluk {
 
 int64_t wait_limit();
+void note_launch();              // counts kernel launches (iluk_launch_count)
+
+// Optional per-kernel timing with CUDA events on the launching stream
+// (iluk_prof_enable / iluk_prof_read).  Kinds are listed in include/iluk.h.
+bool prof_on();
+int prof_begin(int kind, cudaStream_t s);
+void prof_end(int slot, cudaStream_t s);
+struct ProfScope {
+  int slot;
+  cudaStream_t s;
+  ProfScope(int kind, cudaStream_t st) : slot(prof_on() ? prof_begin(kind, st) : -1), s(st) {}
+  ~ProfScope() {
+    if (slot >= 0) prof_end(slot, s);
+  }
+};
 int64_t hold_row();              // test hook: a row whose flag is never published
 
 // Sizes of the persistent grids (filled on first use per device).
@@ -72,9 +97,10 @@ cudaError_t launch_symbolic_compact(int64_t n, const SymArena &ar, const int64_t
                                     cudaStream_t s);
 cudaError_t launch_a2f(int64_t n, const int64_t *arp, const int32_t *aci, const int64_t *frp,
                        const int32_t *fci, int32_t *a2f, cudaStream_t s);
-cudaError_t launch_depth(int64_t n, const int64_t *frp, const int32_t *fci, const int64_t *fdiag,
-                         int32_t *depth, int *ready, unsigned long long *ticket, int upper,
-                         int32_t *maxdepth, DevErr *err, cudaStream_t s);
+
+// Levels (levels.cu): synchronous; allocates lo->order on success.
+int build_levels(int64_t n, const int64_t *rp, const int32_t *ci, const int64_t *dg, bool forward,
+                 LevelOrder *lo, cudaStream_t s);
 
 // Numeric (numeric.cu)
 cudaError_t launch_numeric(const iluk_sym *S, const double *aval, double *fval, int *ready,
@@ -85,9 +111,13 @@ cudaError_t launch_numeric_batched(const iluk_sym *S, int64_t nbatch, const doub
 
 // Sweeps (sweeps.cu)
 size_t sweep_sync_ints(int64_t n);
+// y = (LU)^-1 p (or ^-T on the transposed arrays).  tmp must hold the pending
+// marker in every entry on entry, and does again on exit.
 cudaError_t launch_apply(int64_t n, const int64_t *rp, const int32_t *ci, const int64_t *dg,
-                         const double *v, const double *p, double *tmp, double *y, int *sync,
-                         int transpose, int sched, DevErr *err, cudaStream_t s);
+                         const double *v, const LevelOrder &fwd, const LevelOrder &bwd,
+                         const double *p, double *tmp, double *y, int transpose, int sched,
+                         DevErr *err, cudaStream_t s);
+cudaError_t launch_fill_pending(int64_t n, double *x, cudaStream_t s);
 cudaError_t launch_transpose(int64_t n, int64_t nnz, const int64_t *rp, const int32_t *ci,
                              const double *v, int64_t *trp, int32_t *tci, double *tv,
                              int64_t *tdiag, int32_t *cursor, int64_t *scan_tmp, cudaStream_t s);

@@ -42,11 +42,13 @@ k_spmv(int64_t n, const int64_t *__restrict__ rp, const int32_t *__restrict__ ci
 
 cudaError_t launch_spmv(int64_t n, const int64_t *rp, const int32_t *ci, const double *v,
                         const double *x, double *y, const double *b_minus, cudaStream_t s) {
+  ProfScope prof_scope(ILUK_PROF_SPMV, s);
   if (n == 0) return cudaSuccess;
   int64_t blocks = (n * 32 + 255) / 256;
   const int64_t cap = (int64_t)num_sms() * 8;
   if (blocks > cap) blocks = cap;
   k_spmv<<<(unsigned)blocks, 256, 0, s>>>(n, rp, ci, v, x, y, b_minus);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -83,7 +85,9 @@ k_dot(int64_t n, const double *__restrict__ x, const double *__restrict__ y, dou
 
 cudaError_t launch_dot(int64_t n, const double *x, const double *y, double *out, int take_sqrt,
                        const DotScratch &ds, cudaStream_t s) {
+  ProfScope prof_scope(ILUK_PROF_DOT, s);
   k_dot<<<kDotBlocks, kDotThreads, 0, s>>>(n, x, y, ds.partial, ds.counter, out, take_sqrt);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -107,8 +111,10 @@ k_mgs_step(int64_t n, double *w, const double *__restrict__ vi, const double *hi
 cudaError_t launch_mgs_step(int64_t n, double *w, const double *vi, const double *hij,
                             const double *vnext, double *out, int take_sqrt,
                             const DotScratch &ds, cudaStream_t s) {
+  ProfScope prof_scope(ILUK_PROF_DOT, s);
   k_mgs_step<<<kDotBlocks, kDotThreads, 0, s>>>(n, w, vi, hij, vnext, ds.partial, ds.counter, out,
                                                 take_sqrt);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -130,8 +136,10 @@ static unsigned vec_blocks(int64_t n) {
 
 cudaError_t launch_scale_div(int64_t n, const double *x, const double *den, double *y,
                              cudaStream_t s) {
+  ProfScope prof_scope(ILUK_PROF_VECTOR, s);
   if (n == 0) return cudaSuccess;
   k_scale_div<<<vec_blocks(n), 256, 0, s>>>(n, x, den, y);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -148,8 +156,10 @@ __global__ void k_combine(int64_t n, const double *__restrict__ V, int64_t ldv,
 
 cudaError_t launch_combine(int64_t n, const double *V, int64_t ldv, const double *y, int cnt,
                            double *u, cudaStream_t s) {
+  ProfScope prof_scope(ILUK_PROF_VECTOR, s);
   if (n == 0) return cudaSuccess;
   k_combine<<<vec_blocks(n), 256, 0, s>>>(n, V, ldv, y, cnt, u);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -160,8 +170,10 @@ __global__ void k_add(int64_t n, double *x, const double *__restrict__ z) {
 }
 
 cudaError_t launch_add(int64_t n, double *x, const double *z, cudaStream_t s) {
+  ProfScope prof_scope(ILUK_PROF_VECTOR, s);
   if (n == 0) return cudaSuccess;
   k_add<<<vec_blocks(n), 256, 0, s>>>(n, x, z);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -180,11 +192,13 @@ __global__ void k_adjoint_scatter(int64_t n, const int64_t *__restrict__ rp,
 cudaError_t launch_adjoint_scatter(int64_t n, const int64_t *rp, const int32_t *ci,
                                    const double *lam, const double *x, double *gA,
                                    cudaStream_t s) {
+  ProfScope prof_scope(ILUK_PROF_VECTOR, s);
   if (n == 0) return cudaSuccess;
   int64_t blocks = (n * 32 + 255) / 256;
   const int64_t cap = (int64_t)num_sms() * 8;
   if (blocks > cap) blocks = cap;
   k_adjoint_scatter<<<(unsigned)blocks, 256, 0, s>>>(n, rp, ci, lam, x, gA);
+  note_launch();
   return cudaGetLastError();
 }
 

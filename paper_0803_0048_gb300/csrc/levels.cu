@@ -1,0 +1,185 @@
+// levels.cu -- level sets of the two sweep DAGs (the level/backward
+// scheduling of the paper's related work: Anderson 1988, Heroux 1991).
+//
+// depth(i) = 1 + max depth(h) over the rows h that row i reads (h < i in the
+// forward sweep, h > i in the backward sweep); rows of equal depth are
+// independent.  The sweeps walk rows in level order, with every level
+// starting on a warp boundary (short levels are padded with -1), so the 32
+// rows of a warp never depend on one another: a warp's lanes only ever wait
+// for rows held by other warps.
+#include "internal.h"
+
+namespace iluk {
+
+constexpr int kDepthThreads = 1024;
+
+// One CTA, one warp per row (rows claimed in sweep order through a shared
+// ticket).  depth[] doubles as the ready flag: 0 until the row is final.
+template <bool FORWARD>
+__global__ void __launch_bounds__(kDepthThreads, 1)
+k_depth_cta(int64_t n, const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
+            const int64_t *__restrict__ dg, int32_t *depth, int32_t *maxdepth, DevErr *err,
+            int64_t limit_ns) {
+  __shared__ unsigned long long sticket;
+  __shared__ int sfail;
+  if (threadIdx.x == 0) {
+    sticket = 0;
+    sfail = 0;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  int dmax_local = 0;
+  for (;;) {
+    unsigned long long tk = 0;
+    if (lane == 0) tk = atomicAdd(&sticket, 1ull);
+    const int64_t t = (int64_t)__shfl_sync(FULL_MASK, tk, 0);
+    if (t >= n) break;
+    const int64_t row = FORWARD ? t : n - 1 - t;
+    const int64_t d = dg[row];
+    const int64_t b0 = FORWARD ? rp[row] : d + 1;
+    const int64_t b1 = FORWARD ? d : rp[row + 1];
+    int dm = 0;
+    bool ok = true;
+    for (int64_t base = b0; base < b1; base += 32) {
+      const int64_t q = base + lane;
+      int v = 1;
+      const int32_t *src = nullptr;
+      if (q < b1) {
+        src = &depth[ci[q]];
+        asm volatile("ld.relaxed.cta.global.b32 %0, [%1];" : "=r"(v) : "l"(src));
+      }
+      if (__any_sync(FULL_MASK, v == 0)) {
+        const uint64_t t0 = globaltimer_ns();
+        while (__any_sync(FULL_MASK, v == 0)) {
+          if (v == 0) asm volatile("ld.relaxed.cta.global.b32 %0, [%1];" : "=r"(v) : "l"(src));
+          if (*((volatile int *)&sfail) || (int64_t)(globaltimer_ns() - t0) > limit_ns) {
+            ok = false;
+            break;
+          }
+        }
+      }
+      if (!__all_sync(FULL_MASK, ok)) break;
+      if (q < b1 && v > dm) dm = v;
+    }
+    if (!__all_sync(FULL_MASK, ok)) {
+      if (lane == 0) {
+        atomicExch(&sfail, 1);
+        set_err(err, t, ILUK_ETIMEOUT);
+      }
+      return;
+    }
+    dm = __reduce_max_sync(FULL_MASK, dm) + 1;
+    if (lane == 0) {
+      asm volatile("st.relaxed.cta.global.b32 [%0], %1;" ::"l"(&depth[row]), "r"(dm) : "memory");
+      if (dm > dmax_local) dmax_local = dm;
+    }
+  }
+  if (lane == 0 && dmax_local) atomicMax(maxdepth, dmax_local);
+}
+
+__global__ void k_level_count(int64_t n, const int32_t *__restrict__ depth, int32_t *cnt) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(&cnt[depth[i] - 1], 1);
+}
+
+__global__ void k_level_pad(int64_t nlev, int32_t *cnt) {
+  for (int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; l < nlev;
+       l += (int64_t)gridDim.x * blockDim.x)
+    cnt[l] = (cnt[l] + 31) & ~31;
+}
+
+__global__ void k_level_scatter(int64_t n, const int32_t *__restrict__ depth,
+                                const int64_t *__restrict__ lstart, int32_t *cursor,
+                                int32_t *order) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int l = depth[i] - 1;
+    order[lstart[l] + atomicAdd(&cursor[l], 1)] = (int32_t)i;
+  }
+}
+
+static unsigned grid_for(int64_t n) {
+  int64_t b = (n + 255) / 256;
+  const int64_t cap = (int64_t)num_sms() * 8;
+  if (b > cap) b = cap;
+  return (unsigned)(b < 1 ? 1 : b);
+}
+
+// Synchronous: computes the depths, then the padded level order.  On success
+// lo->order is a new device allocation of lo->len entries.
+int build_levels(int64_t n, const int64_t *rp, const int32_t *ci, const int64_t *dg, bool forward,
+                 LevelOrder *lo, cudaStream_t s) {
+  ProfScope prof_scope(ILUK_PROF_DEPTH, s);
+  lo->order = nullptr;
+  lo->len = 0;
+  lo->nlev = 0;
+  if (n == 0) return ILUK_OK;
+  int32_t *depth = nullptr, *mx = nullptr, *cnt = nullptr, *cursor = nullptr;
+  int64_t *lstart = nullptr, *scan_tmp = nullptr;
+  DevErr *err = nullptr;
+  int st = ILUK_OK;
+  auto cleanup = [&]() {
+    if (depth) cudaFreeAsync(depth, s);
+    if (mx) cudaFreeAsync(mx, s);
+    if (cnt) cudaFreeAsync(cnt, s);
+    if (cursor) cudaFreeAsync(cursor, s);
+    if (lstart) cudaFreeAsync(lstart, s);
+    if (scan_tmp) cudaFreeAsync(scan_tmp, s);
+    if (err) cudaFreeAsync(err, s);
+  };
+#define CKL(call)                              \
+  do {                                         \
+    if ((call) != cudaSuccess) {               \
+      cleanup();                               \
+      return ILUK_ECUDA;                       \
+    }                                          \
+  } while (0)
+  CKL(cudaMallocAsync((void **)&depth, n * sizeof(int32_t), s));
+  CKL(cudaMallocAsync((void **)&mx, sizeof(int32_t), s));
+  CKL(cudaMallocAsync((void **)&err, sizeof(DevErr), s));
+  CKL(cudaMemsetAsync(depth, 0, n * sizeof(int32_t), s));
+  CKL(cudaMemsetAsync(mx, 0, sizeof(int32_t), s));
+  CKL(launch_fill_err(err, s));
+  if (forward)
+    k_depth_cta<true><<<1, kDepthThreads, 0, s>>>(n, rp, ci, dg, depth, mx, err, wait_limit());
+  else
+    k_depth_cta<false><<<1, kDepthThreads, 0, s>>>(n, rp, ci, dg, depth, mx, err, wait_limit());
+  note_launch();
+  CKL(cudaGetLastError());
+  DevErr herr;
+  int32_t nlev = 0;
+  CKL(cudaMemcpyAsync(&herr, err, sizeof(herr), cudaMemcpyDeviceToHost, s));
+  CKL(cudaMemcpyAsync(&nlev, mx, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  CKL(cudaStreamSynchronize(s));
+  if (herr.key != kNoErr) {
+    cleanup();
+    return (int)(herr.key & 0xff);
+  }
+  CKL(cudaMallocAsync((void **)&cnt, (size_t)nlev * sizeof(int32_t), s));
+  CKL(cudaMallocAsync((void **)&cursor, (size_t)nlev * sizeof(int32_t), s));
+  CKL(cudaMallocAsync((void **)&lstart, ((size_t)nlev + 1) * sizeof(int64_t), s));
+  CKL(cudaMallocAsync((void **)&scan_tmp, (size_t)scan_tmp_elems(nlev) * sizeof(int64_t), s));
+  CKL(cudaMemsetAsync(cnt, 0, (size_t)nlev * sizeof(int32_t), s));
+  CKL(cudaMemsetAsync(cursor, 0, (size_t)nlev * sizeof(int32_t), s));
+  k_level_count<<<grid_for(n), 256, 0, s>>>(n, depth, cnt);
+  note_launch();
+  k_level_pad<<<grid_for(nlev), 256, 0, s>>>(nlev, cnt);
+  note_launch();
+  CKL(launch_scan_lengths(nlev, cnt, lstart, scan_tmp, s));
+  int64_t len = 0;
+  CKL(cudaMemcpyAsync(&len, lstart + nlev, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  CKL(cudaStreamSynchronize(s));
+  CKL(cudaMallocAsync((void **)&lo->order, (size_t)len * sizeof(int32_t), s));
+  CKL(cudaMemsetAsync(lo->order, 0xff, (size_t)len * sizeof(int32_t), s));
+  k_level_scatter<<<grid_for(n), 256, 0, s>>>(n, depth, lstart, cursor, lo->order);
+  note_launch();
+  CKL(cudaGetLastError());
+#undef CKL
+  cleanup();
+  lo->len = len;
+  lo->nlev = nlev;
+  return st;
+}
+
+}  // namespace iluk

@@ -127,6 +127,7 @@ static int numeric_cap(const iluk_sym *S, int *warps_out, size_t *smem_out) {
 static cudaError_t launch_numeric_impl(const iluk_sym *S, int64_t nbatch, const double *avals,
                                        double *fvals, int *ready, unsigned long long *ticket,
                                        DevErr *errs, cudaStream_t s) {
+  ProfScope prof_scope(ILUK_PROF_NUMERIC, s);
   int warps;
   size_t smem;
   const int cap = numeric_cap(S, &warps, &smem);
@@ -143,6 +144,7 @@ static cudaError_t launch_numeric_impl(const iluk_sym *S, int64_t nbatch, const 
   k_numeric<<<(unsigned)grid, warps * 32, smem, s>>>(
       S->n, nbatch, S->arowptr, S->a2f, avals, S->nnzA, S->rowptr, S->colind, S->diag, fvals,
       S->nnz, ready, ticket, errs, cap, wait_limit(), hold_row());
+  note_launch();
   return cudaGetLastError();
 }
 

@@ -2,19 +2,19 @@
 // iteration (Eq. triangleSolve), and its transpose.
 //
 // Forward (Eq. forwardsubA): x_i = p_i - sum_{h<i} f_ih x_h, h ascending.
-// Backward: y_i = (x_i - sum_{j>i} f_ij y_j) / f_ii, j ascending.
-// Each row's subtraction chain keeps the sequential order: lanes form the
-// products in parallel once the rows they read are final, then the warp runs
-// the chain left to right (one rounding per product, one per difference).
+// Backward: y_i = (x_i - sum_{j>i} f_ij y_j) / f_ii, j descending (the mirror
+// image: rows last to first, each row right to left).
+// Each row's subtraction chain keeps the sequential order (one rounding per
+// product, one per difference) and is run by one thread.
 //
 // Two schedules of the same row task:
-//  * FLAGS: persistent grid over all SMs, one warp per row, rows claimed by
-//    an ascending ticket, per-row ready flags in global memory (release /
-//    acquire at GPU scope).  Suits wide dependency DAGs.
-//  * SINGLE_CTA: one 1024-thread block on one SM, ready bits in shared
-//    memory and CTA-scope ordering, so a dependency is seen within tens of
-//    cycles instead of an L2 round trip.  Suits deep, narrow DAGs, where the
-//    chain of row-to-row hand-offs, not bandwidth, sets the time.
+//  * FLAGS (multi-SM): a co-resident grid over all SMs, one thread per row;
+//    a dependency crosses SMs through L2 (relaxed GPU-scope loads and
+//    stores).  Suits wide dependency DAGs, which need the FP64 throughput of
+//    many SMs.
+//  * SINGLE_CTA: one 1024-thread block on one SM; a dependency is handed over
+//    through the SM's L1 within a couple of hundred cycles.  Suits deep,
+//    narrow DAGs, where the chain of row-to-row hand-offs sets the time.
 //
 // The transposed solve (L~U~)^-T p runs the same kernels on an explicit CSR
 // transpose T = F^T: forward with division by t_ii (U~^T), then backward with
@@ -23,186 +23,232 @@
 
 namespace iluk {
 
-constexpr int kSweepThreads = 256;
-constexpr int kCtaThreads = 1024;
-
-// sync layout: [0] ticket fwd (u64), [2] ticket bwd (u64), [4..4+n) flags
-// fwd, [4+n..4+2n) flags bwd.
+// Scratch ints kept per factor handle for the factorization's ready flags.
 size_t sweep_sync_ints(int64_t n) { return 4 + 2 * (size_t)n; }
 
-template <bool FORWARD, bool DIVIDE>
-__global__ void __launch_bounds__(kSweepThreads)
-k_sweep_flags(int64_t n, const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
-              const int64_t *__restrict__ dg, const double *__restrict__ v,
-              const double *in, double *out, int *flag, unsigned long long *ticket,
-              DevErr *err, int64_t limit_ns) {
-  const int lane = threadIdx.x & 31;
-  for (;;) {
-    unsigned long long tk = 0;
-    if (lane == 0) tk = atomicAdd(ticket, 1ull);
-    const int64_t t = (int64_t)__shfl_sync(FULL_MASK, tk, 0);
-    if (t >= n) return;
-    const int64_t row = FORWARD ? t : n - 1 - t;
-    const int64_t d = dg[row];
-    const int64_t b0 = FORWARD ? rp[row] : d + 1;
-    const int64_t b1 = FORWARD ? d : rp[row + 1];
-    double s = in[row];
-    bool ok = true;
-    for (int64_t base = b0; base < b1; base += 32) {
-      const int64_t q = base + lane;
-      double prod = 0.0;
-      if (q < b1) {
-        const int32_t c = ci[q];
-        const double f = v[q];
-        if (wait_flag(&flag[c], err, t, limit_ns))
-          prod = __dmul_rn(f, *((volatile double *)&out[c]));
-        else
-          ok = false;
-      }
-      if (!__all_sync(FULL_MASK, ok)) break;
-      const int cnt = (b1 - base) < 32 ? (int)(b1 - base) : 32;
-      for (int l = 0; l < cnt; ++l) s = __dsub_rn(s, __shfl_sync(FULL_MASK, prod, l));
-    }
-    if (!__all_sync(FULL_MASK, ok)) {
-      if (lane == 0 && !earlier_failed(err, t)) set_err(err, t, ILUK_ETIMEOUT);
-      return;
-    }
-    if (DIVIDE) s = __ddiv_rn(s, v[d]);
-    if (lane == 0) out[row] = s;
-    warp_publish(&flag[row], lane);
-  }
-}
+constexpr int kCtaThreads = 1024;
+constexpr int kGridThreads = 256;
 
-// Shared-memory ready bits, CTA scope.
-__device__ __forceinline__ bool cta_bit(const unsigned *bits, int64_t r) {
-  return (((volatile const unsigned *)bits)[r >> 5] >> (r & 31)) & 1u;
-}
+// Sweep outputs double as their own ready flags: an entry holds kPending (a
+// signalling NaN, which no arithmetic produces) until its row is final, so a
+// row that reads x_c simply polls x_c.  No flag array, no fence, no memset.
+constexpr unsigned long long kPending = 0x7FF0DEADBEEFCAFEull;
+constexpr unsigned long long kQuietNaN = 0x7FF8000000000000ull;
 
-__device__ __forceinline__ double ld_relaxed_cta(const double *p) {
+template <bool GPU_SCOPE>
+__device__ __forceinline__ double ld_val(const double *p) {
   double v;
-  asm volatile("ld.relaxed.cta.global.f64 %0, [%1];" : "=d"(v) : "l"(p) : "memory");
+  if (GPU_SCOPE)
+    asm volatile("ld.relaxed.gpu.global.f64 %0, [%1];" : "=d"(v) : "l"(p));
+  else
+    asm volatile("ld.relaxed.cta.global.f64 %0, [%1];" : "=d"(v) : "l"(p));
   return v;
 }
 
-__device__ __forceinline__ void st_relaxed_cta(double *p, double v) {
-  asm volatile("st.relaxed.cta.global.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
+template <bool GPU_SCOPE>
+__device__ __forceinline__ void st_val(double *p, double v) {
+  if (GPU_SCOPE)
+    asm volatile("st.relaxed.gpu.global.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
+  else
+    asm volatile("st.relaxed.cta.global.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
 }
 
-template <bool FORWARD, bool DIVIDE>
-__global__ void __launch_bounds__(kCtaThreads, 1)
-k_sweep_cta(int64_t n, const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
-            const int64_t *__restrict__ dg, const double *__restrict__ v, const double *in,
-            double *out, DevErr *err, int64_t limit_ns) {
-  extern __shared__ unsigned bits[];
-  __shared__ unsigned long long sticket;
-  __shared__ int sfail;
-  const int64_t words = (n + 31) >> 5;
-  for (int64_t w = threadIdx.x; w < words; w += blockDim.x) bits[w] = 0u;
-  if (threadIdx.x == 0) {
-    sticket = 0;
-    sfail = 0;
-  }
-  __syncthreads();
+__device__ __forceinline__ bool pending(double v) {
+  return (unsigned long long)__double_as_longlong(v) == kPending;
+}
+
+// Wait for *p to leave the pending state; false on time-out or on a failure
+// recorded by another thread.
+// Rows of a sweep are taken 32 at a time from the level order (a warp's 32
+// rows belong to one level, padding slots hold -1), and the warp walks the
+// 32 subtraction chains in lockstep, a window of W entries at a time: it
+// loads the W values each lane needs, waits (warp-uniformly) until none of
+// them is pending, then forms the products and the differences with every
+// lane active.  Keeping the FP64 instructions converged matters on GB300,
+// where an FP64 warp instruction occupies the pipe for ~20 SM cycles however
+// few lanes it serves.  Each chain still runs left to right in its own lane.
+// `clear` (may alias `in`) gets kPending at position `row` once in[row] has
+// been read, which re-arms the buffer the next sweep writes.
+template <bool FORWARD, bool DIVIDE, bool GPU_SCOPE, int W>
+__global__ void __launch_bounds__(GPU_SCOPE ? kGridThreads : kCtaThreads)
+k_sweep(const int32_t *__restrict__ order, int64_t len, const int64_t *__restrict__ rp,
+        const int32_t *__restrict__ ci, const int64_t *__restrict__ dg,
+        const double *__restrict__ v, const double *in, double *out, double *clear, DevErr *err,
+        int64_t limit_ns) {
   const int lane = threadIdx.x & 31;
-  for (;;) {
-    unsigned long long tk = 0;
-    if (lane == 0) tk = atomicAdd(&sticket, 1ull);
-    const int64_t t = (int64_t)__shfl_sync(FULL_MASK, tk, 0);
-    if (t >= n) return;
-    const int64_t row = FORWARD ? t : n - 1 - t;
-    const int64_t d = dg[row];
-    const int64_t b0 = FORWARD ? rp[row] : d + 1;
-    const int64_t b1 = FORWARD ? d : rp[row + 1];
-    double s = in[row];
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t slot0 = gw * 32; slot0 < len; slot0 += nw * 32) {
+    const int64_t row = order[slot0 + lane];
+    // Entry e (0-based, in subtraction order) of this row sits at
+    // first + step * e: left to right in the forward sweep, right to left in
+    // the backward sweep, so the nearest columns, whose rows finish last, are
+    // always subtracted last.
+    int64_t first = 0, d = 0;
+    int mylen = 0;
+    double s = 0.0;
+    if (row >= 0) {
+      d = dg[row];
+      if (FORWARD) {
+        first = rp[row];
+        mylen = (int)(d - first);
+      } else {
+        first = rp[row + 1] - 1;
+        mylen = (int)(first - d);
+      }
+      s = in[row];
+      if (clear) clear[row] = __longlong_as_double((long long)kPending);
+    }
+    constexpr int64_t step = FORWARD ? 1 : -1;
+    const int maxlen = __reduce_max_sync(FULL_MASK, mylen);
+    // Chains are right-aligned across the warp: lane entry e runs at lockstep
+    // position e + (maxlen - mylen), so every lane's newest dependencies fall
+    // in the last windows.
+    const int off = maxlen - mylen;
     bool ok = true;
-    for (int64_t base = b0; base < b1; base += 32) {
-      const int64_t q = base + lane;
-      double prod = 0.0;
-      if (q < b1) {
-        const int32_t c = ci[q];
-        const double f = v[q];
-        if (!cta_bit(bits, c)) {
-          const uint64_t t0 = globaltimer_ns();
-          while (!cta_bit(bits, c)) {
-            if (*((volatile int *)&sfail)) { ok = false; break; }
-            if ((int64_t)(globaltimer_ns() - t0) > limit_ns) { ok = false; break; }
+    for (int q0 = 0; q0 < maxlen; q0 += W) {
+      int32_t c[W];
+      double f[W], x[W];
+      bool pend = false;
+#pragma unroll
+      for (int u = 0; u < W; ++u) {
+        const int e = q0 + u - off;
+        if (e >= 0 && e < mylen) {
+          c[u] = ci[first + step * e];
+          f[u] = v[first + step * e];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < W; ++u) {
+        const int e = q0 + u - off;
+        if (e >= 0 && e < mylen) {
+          x[u] = ld_val<GPU_SCOPE>(&out[c[u]]);
+          pend |= pending(x[u]);
+        }
+      }
+      if (__any_sync(FULL_MASK, pend)) {
+        // Wait with little memory traffic: each lane re-reads only its first
+        // pending value per round, and the warp sleeps between rounds, so the
+        // warps that can make progress keep the load pipe.
+        const uint64_t t0 = globaltimer_ns();
+        unsigned backoff = 16;
+        for (unsigned it = 0; __any_sync(FULL_MASK, pend); ++it) {
+          pend = false;
+          bool polled = false;
+#pragma unroll
+          for (int u = 0; u < W; ++u) {
+            const int e = q0 + u - off;
+            if (e >= 0 && e < mylen && pending(x[u])) {
+              if (!polled) {
+                x[u] = ld_val<GPU_SCOPE>(&out[c[u]]);
+                polled = pending(x[u]);
+              }
+              pend |= pending(x[u]);
+            }
+          }
+          if ((it & 15u) == 15u &&
+              (any_failed(err) || (int64_t)(globaltimer_ns() - t0) > limit_ns)) {
+            ok = false;
+            break;
+          }
+          if (__any_sync(FULL_MASK, pend)) {
+            __nanosleep(backoff);
+            if (backoff < (GPU_SCOPE ? 256u : 128u)) backoff <<= 1;
           }
         }
-        __threadfence_block();
-        prod = __dmul_rn(f, ld_relaxed_cta(&out[c]));
+        if (!__all_sync(FULL_MASK, ok)) break;
       }
-      if (!__all_sync(FULL_MASK, ok)) break;
-      const int cnt = (b1 - base) < 32 ? (int)(b1 - base) : 32;
-      for (int l = 0; l < cnt; ++l) s = __dsub_rn(s, __shfl_sync(FULL_MASK, prod, l));
+#pragma unroll
+      for (int u = 0; u < W; ++u) {
+        const int e = q0 + u - off;
+        if (e >= 0 && e < mylen) x[u] = __dmul_rn(f[u], x[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < W; ++u) {
+        const int e = q0 + u - off;
+        if (e >= 0 && e < mylen) s = __dsub_rn(s, x[u]);
+      }
     }
     if (!__all_sync(FULL_MASK, ok)) {
-      if (lane == 0) {
-        atomicExch(&sfail, 1);
-        set_err(err, t, ILUK_ETIMEOUT);
-      }
+      if (row >= 0) set_err(err, row, ILUK_ETIMEOUT);
       return;
     }
-    if (DIVIDE) s = __ddiv_rn(s, v[d]);
-    if (lane == 0) {
-      st_relaxed_cta(&out[row], s);
-      __threadfence_block();
-      atomicOr(&bits[row >> 5], 1u << (row & 31));
+    if (DIVIDE && row >= 0) s = __ddiv_rn(s, v[d]);
+    if (row >= 0) {
+      if ((unsigned long long)__double_as_longlong(s) == kPending)
+        s = __longlong_as_double((long long)kQuietNaN);
+      st_val<GPU_SCOPE>(&out[row], s);
     }
-    __syncwarp();
   }
 }
 
-static int64_t flags_grid(int64_t n) {
-  int64_t g = (int64_t)num_sms() * (2048 / kSweepThreads);
-  int64_t want = (n + (kSweepThreads / 32) - 1) / (kSweepThreads / 32);
-  if (g > want) g = want;
-  return g < 1 ? 1 : g;
+__global__ void k_fill_pending(int64_t n, double *x) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = __longlong_as_double((long long)kPending);
 }
 
-template <bool FORWARD, bool DIVIDE>
-static cudaError_t run_sweep(int64_t n, const int64_t *rp, const int32_t *ci, const int64_t *dg,
-                             const double *v, const double *in, double *out, int *flag,
-                             unsigned long long *ticket, int sched, DevErr *err, cudaStream_t s) {
+cudaError_t launch_fill_pending(int64_t n, double *x, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
-  if (sched == ILUK_SCHED_SINGLE_CTA) {
-    const size_t smem = (size_t)((n + 31) >> 5) * 4;
-    cudaError_t e = cudaFuncSetAttribute(k_sweep_cta<FORWARD, DIVIDE>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_sweep_cta<FORWARD, DIVIDE><<<1, kCtaThreads, smem, s>>>(n, rp, ci, dg, v, in, out, err,
-                                                              wait_limit());
-  } else {
-    k_sweep_flags<FORWARD, DIVIDE><<<(unsigned)flags_grid(n), kSweepThreads, 0, s>>>(
-        n, rp, ci, dg, v, in, out, flag, ticket, err, wait_limit());
-  }
+  int64_t b = (n + 255) / 256;
+  const int64_t cap = (int64_t)num_sms() * 8;
+  if (b > cap) b = cap;
+  k_fill_pending<<<(unsigned)b, 256, 0, s>>>(n, x);
+  note_launch();
   return cudaGetLastError();
 }
 
-// Largest n whose ready bits fit one block's shared memory.
-static bool cta_fits(int64_t n) {
-  return (size_t)((n + 31) >> 5) * 4 + 64 <= (size_t)max_smem_optin();
+template <bool FORWARD, bool DIVIDE>
+static cudaError_t run_sweep(const LevelOrder &lo, const int64_t *rp, const int32_t *ci,
+                             const int64_t *dg, const double *v, const double *in, double *out,
+                             double *clear, int sched, DevErr *err, cudaStream_t s) {
+  ProfScope prof_scope(FORWARD ? ILUK_PROF_SWEEP : ILUK_PROF_SWEEP_BWD, s);
+  if (lo.len == 0) return cudaSuccess;
+  int64_t limit = wait_limit();
+  const int32_t *order = lo.order;
+  int64_t len = lo.len;
+  if (sched == ILUK_SCHED_SINGLE_CTA) {
+    k_sweep<FORWARD, DIVIDE, false, 4><<<1, kCtaThreads, 0, s>>>(order, len, rp, ci, dg, v, in,
+                                                                out, clear, err, limit);
+    note_launch();
+    return cudaGetLastError();
+  }
+  // Multi-SM: every block must be resident (rows wait on rows of other
+  // blocks), so the grid is launched cooperatively and sized by occupancy.
+  int bps = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_sweep<FORWARD, DIVIDE, true, 8>,
+                                                kGridThreads, 0);
+  if (bps > 2) bps = 2;
+  if (bps < 1) bps = 1;
+  int64_t grid = (int64_t)bps * num_sms();
+  const int64_t want = (len + kGridThreads - 1) / kGridThreads;  // one warp per 32 slots
+  if (grid > want) grid = want;
+  void *args[] = {(void *)&order, (void *)&len, (void *)&rp, (void *)&ci, (void *)&dg,
+                  (void *)&v, (void *)&in, (void *)&out, (void *)&clear, (void *)&err,
+                  (void *)&limit};
+  cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_sweep<FORWARD, DIVIDE, true, 8>,
+                                              dim3((unsigned)grid), dim3(kGridThreads), args, 0, s);
+  note_launch();
+  return e;
 }
 
 cudaError_t launch_apply(int64_t n, const int64_t *rp, const int32_t *ci, const int64_t *dg,
-                         const double *v, const double *p, double *tmp, double *y, int *sync,
-                         int transpose, int sched, DevErr *err, cudaStream_t s) {
-  if (sched == ILUK_SCHED_SINGLE_CTA && !cta_fits(n)) sched = ILUK_SCHED_FLAGS;
+                         const double *v, const LevelOrder &fwd, const LevelOrder &bwd,
+                         const double *p, double *tmp, double *y, int transpose, int sched,
+                         DevErr *err, cudaStream_t s) {
   if (sched != ILUK_SCHED_SINGLE_CTA) sched = ILUK_SCHED_FLAGS;
-  unsigned long long *tick = reinterpret_cast<unsigned long long *>(sync);
-  int *fl_f = sync + 4, *fl_b = sync + 4 + n;
+  (void)n;
   cudaError_t e;
-  if (sched == ILUK_SCHED_FLAGS) {
-    e = cudaMemsetAsync(sync, 0, sweep_sync_ints(n) * sizeof(int), s);
-    if (e != cudaSuccess) return e;
-  }
+  // tmp is pending on entry (left so by the previous backward sweep); the
+  // forward sweep re-arms y, the backward sweep re-arms tmp.
   if (!transpose) {
-    e = run_sweep<true, false>(n, rp, ci, dg, v, p, tmp, fl_f, tick, sched, err, s);
+    e = run_sweep<true, false>(fwd, rp, ci, dg, v, p, tmp, y, sched, err, s);
     if (e != cudaSuccess) return e;
-    return run_sweep<false, true>(n, rp, ci, dg, v, tmp, y, fl_b, tick + 1, sched, err, s);
+    return run_sweep<false, true>(bwd, rp, ci, dg, v, tmp, y, tmp, sched, err, s);
   }
-  e = run_sweep<true, true>(n, rp, ci, dg, v, p, tmp, fl_f, tick, sched, err, s);
+  e = run_sweep<true, true>(fwd, rp, ci, dg, v, p, tmp, y, sched, err, s);
   if (e != cudaSuccess) return e;
-  return run_sweep<false, false>(n, rp, ci, dg, v, tmp, y, fl_b, tick + 1, sched, err, s);
+  return run_sweep<false, false>(bwd, rp, ci, dg, v, tmp, y, tmp, sched, err, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -257,17 +303,21 @@ __global__ void k_sort_rows_t(int64_t n, const int64_t *__restrict__ trp, int32_
 cudaError_t launch_transpose(int64_t n, int64_t nnz, const int64_t *rp, const int32_t *ci,
                              const double *v, int64_t *trp, int32_t *tci, double *tv,
                              int64_t *tdiag, int32_t *cursor, int64_t *scan_tmp, cudaStream_t s) {
+  ProfScope prof_scope(ILUK_PROF_TRANSPOSE, s);
   if (n == 0) return cudaMemsetAsync(trp, 0, sizeof(int64_t), s);
   int64_t g = (int64_t)num_sms() * 8;
   cudaError_t e = cudaMemsetAsync(cursor, 0, (size_t)n * sizeof(int32_t), s);
   if (e != cudaSuccess) return e;
   k_count_cols<<<(unsigned)g, 256, 0, s>>>(nnz, ci, cursor);
+  note_launch();
   e = launch_scan_lengths(n, cursor, trp, scan_tmp, s);
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(cursor, 0, (size_t)n * sizeof(int32_t), s);
   if (e != cudaSuccess) return e;
   k_scatter_t<<<(unsigned)g, 256, 0, s>>>(n, rp, ci, v, trp, cursor, tci, tv);
+  note_launch();
   k_sort_rows_t<<<(unsigned)g, 256, 0, s>>>(n, trp, tci, tv, tdiag);
+  note_launch();
   return cudaGetLastError();
 }
 

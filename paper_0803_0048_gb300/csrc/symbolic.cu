@@ -182,6 +182,7 @@ k_symbolic_rows(int64_t n, const int64_t *__restrict__ arp, const int32_t *__res
 
 cudaError_t launch_symbolic_rows(int64_t n, const int64_t *arp, const int32_t *aci, int k,
                                  const SymArena &ar, DevErr *err, int cap, cudaStream_t s) {
+  ProfScope prof_scope(ILUK_PROF_SYMBOLIC, s);
   const size_t per_warp = symbolic_smem_per_warp(cap);
   int warps = kSymThreads / 32;
   while (warps > 1 && per_warp * warps > (size_t)max_smem_optin()) warps >>= 1;
@@ -216,6 +217,7 @@ cudaError_t launch_symbolic_rows(int64_t n, const int64_t *arp, const int32_t *a
     k_symbolic_rows<false><<<(unsigned)grid, threads, smem, s>>>(
         n, arp, aci, k, ar.col, ar.lev, ar.cap, ar.top, ar.row_off, ar.row_len, ar.row_ust,
         ar.ready, ar.ticket, err, cap, wait_limit());
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -248,12 +250,14 @@ __global__ void k_symbolic_compact(int64_t n, const int32_t *__restrict__ acol,
 cudaError_t launch_symbolic_compact(int64_t n, const SymArena &ar, const int64_t *frp,
                                     int32_t *fci, uint8_t *flev, int64_t *fdiag, int32_t *maxrow,
                                     cudaStream_t s) {
+  ProfScope prof_scope(ILUK_PROF_COMPACT, s);
   int64_t blocks = (n * 32 + 255) / 256;
   int64_t cap = (int64_t)num_sms() * 16;
   if (blocks > cap) blocks = cap;
   if (blocks < 1) blocks = 1;
   k_symbolic_compact<<<(unsigned)blocks, 256, 0, s>>>(n, ar.col, ar.lev, ar.row_off, ar.row_len,
                                                        ar.row_ust, frp, fci, flev, fdiag, maxrow);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -275,63 +279,13 @@ __global__ void k_a2f(int64_t n, const int64_t *__restrict__ arp, const int32_t 
 
 cudaError_t launch_a2f(int64_t n, const int64_t *arp, const int32_t *aci, const int64_t *frp,
                        const int32_t *fci, int32_t *a2f, cudaStream_t s) {
+  ProfScope prof_scope(ILUK_PROF_COMPACT, s);
   int64_t blocks = (n * 32 + 255) / 256;
   int64_t cap = (int64_t)num_sms() * 16;
   if (blocks > cap) blocks = cap;
   if (blocks < 1) blocks = 1;
   k_a2f<<<(unsigned)blocks, 256, 0, s>>>(n, arp, aci, frp, fci, a2f);
-  return cudaGetLastError();
-}
-
-// Depth of each row in the dependency DAG of a sweep: 1 + max depth of the
-// rows it reads (lower part ascending, or upper part descending).  Warp per
-// row with ready flags, like the factorization itself.
-__global__ void k_depth(int64_t n, const int64_t *__restrict__ frp, const int32_t *__restrict__ fci,
-                        const int64_t *__restrict__ fdiag, int32_t *depth, int *ready,
-                        unsigned long long *ticket, int upper, int32_t *maxdepth, DevErr *err,
-                        int64_t limit_ns) {
-  const int lane = threadIdx.x & 31;
-  for (;;) {
-    unsigned long long tk = 0;
-    if (lane == 0) tk = atomicAdd(ticket, 1ull);
-    const int64_t t = (int64_t)__shfl_sync(FULL_MASK, tk, 0);
-    if (t >= n) return;
-    const int64_t row = upper ? n - 1 - t : t;
-    const int64_t b0 = upper ? fdiag[row] + 1 : frp[row];
-    const int64_t b1 = upper ? frp[row + 1] : fdiag[row];
-    int d = 0;
-    bool ok = true;
-    for (int64_t q = b0 + lane; q < b1; q += 32) {
-      const int h = fci[q];
-      if (!wait_flag(&ready[h], err, upper ? (n - 1 - row) : row, limit_ns)) {
-        ok = false;
-        break;
-      }
-      const int dh = *((volatile int32_t *)&depth[h]);
-      d = dh > d ? dh : d;
-    }
-    if (__any_sync(FULL_MASK, !ok)) {
-      if (lane == 0) set_err(err, upper ? (n - 1 - row) : row, ILUK_ETIMEOUT);
-      return;
-    }
-    d = __reduce_max_sync(FULL_MASK, d) + 1;
-    if (lane == 0) {
-      depth[row] = d;
-      atomicMax(maxdepth, d);
-    }
-    warp_publish(&ready[row], lane);
-  }
-}
-
-cudaError_t launch_depth(int64_t n, const int64_t *frp, const int32_t *fci, const int64_t *fdiag,
-                         int32_t *depth, int *ready, unsigned long long *ticket, int upper,
-                         int32_t *maxdepth, DevErr *err, cudaStream_t s) {
-  int64_t blocks = (n * 32 + 255) / 256;
-  int64_t cap = (int64_t)num_sms() * 8;
-  if (blocks > cap) blocks = cap;
-  if (blocks < 1) blocks = 1;
-  k_depth<<<(unsigned)blocks, 256, 0, s>>>(n, frp, fci, fdiag, depth, ready, ticket, upper,
-                                            maxdepth, err, wait_limit());
+  note_launch();
   return cudaGetLastError();
 }
 

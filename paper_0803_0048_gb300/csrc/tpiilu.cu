@@ -110,10 +110,18 @@ cudaError_t launch_iiluk_build(const iluk_sym *S, const double *fval, double *g,
   int64_t grid = (int64_t)bps * num_sms();
   const int64_t want = (n + warps - 1) / warps;
   if (grid > want) grid = want;
-  k_iiluk_build<true><<<(unsigned)grid, warps * 32, smem, s>>>(
-      n, S->rowptr, S->colind, S->diag, fval, g, fl_l, tick, err, cap, wait_limit());
-  k_iiluk_build<false><<<(unsigned)grid, warps * 32, smem, s>>>(
-      n, S->rowptr, S->colind, S->diag, fval, g, fl_u, tick + 1, err + 1, cap, wait_limit());
+  {
+    ProfScope prof_scope(ILUK_PROF_IILU_BUILD, s);
+    k_iiluk_build<true><<<(unsigned)grid, warps * 32, smem, s>>>(
+        n, S->rowptr, S->colind, S->diag, fval, g, fl_l, tick, err, cap, wait_limit());
+    note_launch();
+  }
+  {
+    ProfScope prof_scope(ILUK_PROF_IILU_BUILD, s);
+    k_iiluk_build<false><<<(unsigned)grid, warps * 32, smem, s>>>(
+        n, S->rowptr, S->colind, S->diag, fval, g, fl_u, tick + 1, err + 1, cap, wait_limit());
+    note_launch();
+  }
   return cudaGetLastError();
 }
 
@@ -156,10 +164,18 @@ cudaError_t launch_iiluk_apply(const iluk_sym *S, const double *g, const double 
   int64_t blocks = (n * 32 + 255) / 256;
   const int64_t cap = (int64_t)num_sms() * 8;
   if (blocks > cap) blocks = cap;
-  k_iiluk_apply<true><<<(unsigned)blocks, 256, 0, s>>>(n, S->rowptr, S->colind, S->diag, g, p,
+  {
+    ProfScope prof_scope(ILUK_PROF_IILU_APPLY, s);
+    k_iiluk_apply<true><<<(unsigned)blocks, 256, 0, s>>>(n, S->rowptr, S->colind, S->diag, g, p,
                                                        tmp);
-  k_iiluk_apply<false><<<(unsigned)blocks, 256, 0, s>>>(n, S->rowptr, S->colind, S->diag, g, tmp,
+    note_launch();
+  }
+  {
+    ProfScope prof_scope(ILUK_PROF_IILU_APPLY, s);
+    k_iiluk_apply<false><<<(unsigned)blocks, 256, 0, s>>>(n, S->rowptr, S->colind, S->diag, g, tmp,
                                                         y);
+    note_launch();
+  }
   return cudaGetLastError();
 }
 

@@ -23,9 +23,11 @@ __global__ void k_validate(int64_t n, int64_t nnz, const int64_t *__restrict__ r
 
 cudaError_t launch_validate(int64_t n, int64_t nnz, const int64_t *rp, const int32_t *ci,
                             DevErr *err, cudaStream_t s) {
+  ProfScope prof_scope(ILUK_PROF_VALIDATE, s);
   int64_t blocks = (n + 255) / 256;
   if (blocks == 0) blocks = 1;
   k_validate<<<(unsigned)blocks, 256, 0, s>>>(n, nnz, rp, ci, err);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -36,6 +38,7 @@ __global__ void k_fill_err(DevErr *err) {
 
 cudaError_t launch_fill_err(DevErr *err, cudaStream_t s) {
   k_fill_err<<<1, 1, 0, s>>>(err);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -109,13 +112,17 @@ int64_t scan_tmp_elems(int64_t n) { return (n + kScanTile - 1) / kScanTile + 1; 
 
 cudaError_t launch_scan_lengths(int64_t n, const int32_t *len, int64_t *out, int64_t *tmp,
                                 cudaStream_t s) {
+  ProfScope prof_scope(ILUK_PROF_COMPACT, s);
   int64_t nb = (n + kScanTile - 1) / kScanTile;
   if (nb == 0) {
     return cudaMemsetAsync(out, 0, sizeof(int64_t), s);
   }
   k_scan_block_sums<<<(unsigned)nb, kScanThreads, 0, s>>>(n, len, tmp);
+  note_launch();
   k_scan_top<<<1, kScanThreads, 0, s>>>(nb, tmp);
+  note_launch();
   k_scan_apply<<<(unsigned)nb, kScanThreads, 0, s>>>(n, len, tmp, out);
+  note_launch();
   return cudaGetLastError();
 }
 
