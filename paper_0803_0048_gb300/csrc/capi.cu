@@ -441,8 +441,8 @@ static int numeric_into(iluk_fac *F, const double *A_val, iluk_info *info, cudaS
   // numeric uses the sweep scratch: [0..1] ticket, [4..4+n) ready flags
   CK(cudaMemsetAsync(F->sync, 0, sweep_sync_ints(S->n) * sizeof(int), s));
   CK(launch_fill_err(F->err, s));
-  CK(launch_numeric(S, A_val, F->val, F->sync + 4, reinterpret_cast<unsigned long long *>(F->sync),
-                    F->err, s));
+  CK(launch_numeric(S, A_val, F->val, reinterpret_cast<unsigned long long *>(F->sync), F->err,
+                    s));
   int64_t row;
   int st = read_err(F->err, s, &row, nullptr);
   CK(launch_fill_err(F->err, s));
@@ -716,20 +716,16 @@ int iluk_numeric_batched(const iluk_sym *S, int64_t nbatch, const double *A_vals
   if (!S || nbatch < 0) return ILUK_EINVAL;
   if (nbatch == 0) return ILUK_OK;
   cudaStream_t s = (cudaStream_t)stream;
-  int *ready = nullptr;
   unsigned long long *ticket = nullptr;
   DevErr *errs = nullptr;
-  CK(dalloc(&ready, S->n * nbatch, s));
   CK(dalloc(&ticket, 1, s));
   CK(dalloc(&errs, nbatch, s));
-  CK(cudaMemsetAsync(ready, 0, S->n * nbatch * sizeof(int), s));
   CK(cudaMemsetAsync(ticket, 0, sizeof(unsigned long long), s));
   CK(cudaMemsetAsync(errs, 0xff, nbatch * sizeof(DevErr), s));
-  CK(launch_numeric_batched(S, nbatch, A_vals, F_vals, ready, ticket, errs, s));
+  CK(launch_numeric_batched(S, nbatch, A_vals, F_vals, ticket, errs, s));
   std::vector<DevErr> h(nbatch);
   CK(cudaMemcpyAsync(h.data(), errs, nbatch * sizeof(DevErr), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
-  dfree(ready, s);
   dfree(ticket, s);
   dfree(errs, s);
   int first = ILUK_OK;

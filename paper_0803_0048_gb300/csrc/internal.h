@@ -103,11 +103,12 @@ int build_levels(int64_t n, const int64_t *rp, const int32_t *ci, const int64_t 
                  LevelOrder *lo, cudaStream_t s);
 
 // Numeric (numeric.cu)
-cudaError_t launch_numeric(const iluk_sym *S, const double *aval, double *fval, int *ready,
+// The factor values double as ready flags (numeric.cu); fval is overwritten.
+cudaError_t launch_numeric(const iluk_sym *S, const double *aval, double *fval,
                            unsigned long long *ticket, DevErr *err, cudaStream_t s);
 cudaError_t launch_numeric_batched(const iluk_sym *S, int64_t nbatch, const double *avals,
-                                   double *fvals, int *ready, unsigned long long *ticket,
-                                   DevErr *errs, cudaStream_t s);
+                                   double *fvals, unsigned long long *ticket, DevErr *errs,
+                                   cudaStream_t s);
 
 // Sweeps (sweeps.cu)
 size_t sweep_sync_ints(int64_t n);

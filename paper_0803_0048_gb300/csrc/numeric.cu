@@ -2,13 +2,13 @@
 // (Eq. 1; Eqs. lufactor2 and lufactor of Sec. 3.5), one warp per row.
 //
 // Row i is scattered from A onto F's pattern in the warp's shared-memory
-// slice (fill positions +0.0).  For each h in L(i), ascending, the warp waits
-// for row h to be final, forms the multiplier f_ih <- f_ih / f_hh (IEEE
-// division) and applies f_ij <- f_ij - f_ih * f_hj (one rounding for the
-// product, one for the difference) to every j > h of row h that row i also
-// stores.  Lanes own distinct j, so each entry sees its updates in ascending
-// h, exactly as the sequential algorithm does.  The finished row is written
-// back and its ready flag released.
+// slice (fill positions +0.0).  For each h in L(i), ascending, the warp finds
+// where row h's entries j > h fall in row i (pattern only, before row h is
+// final), waits for the values of row h, forms the multiplier
+// f_ih <- f_ih / f_hh (IEEE division) and applies f_ij <- f_ij - f_ih * f_hj
+// (one rounding for the product, one for the difference).  Lanes own
+// distinct j, so each entry sees its updates in ascending h, exactly as the
+// sequential algorithm does.  The finished row is then written back.
 //
 // The batched form runs `nbatch` value sets on the same pattern in the same
 // persistent launch: tickets are handed out row-major over (row, set), so
@@ -20,13 +20,60 @@ namespace iluk {
 
 constexpr int kNumThreads = 256;
 
+// Factor values double as ready flags: the output array is filled with
+// kPendingF before the launch, and a row's entries change from kPendingF to
+// their final values when the row is written back.  A row that needs pivot
+// row h reads f_hh and the f_hj directly, retrying while they are pending; no
+// separate flag, fence or release store is needed.  The input values are
+// checked to be finite, so no computed value can equal the marker (a
+// signalling NaN).
+constexpr unsigned long long kPendingF = 0x7FF0DEADBEEFCAFEull;
+
+__device__ __forceinline__ bool pend_f(double v) {
+  return (unsigned long long)__double_as_longlong(v) == kPendingF;
+}
+
+__device__ __forceinline__ double ld_gpu(const double *p) {
+  double v;
+  asm volatile("ld.relaxed.gpu.global.f64 %0, [%1];" : "=d"(v) : "l"(p));
+  return v;
+}
+
+// Warp-uniform wait until the lane's value at p (lanes with active == false
+// pass) is no longer pending.  Returns false on time-out or when a row
+// before `row` has failed.
+__device__ __forceinline__ bool wait_vals(const double *p, bool active, double *val,
+                                          const DevErr *err, int64_t row, int64_t limit_ns) {
+  bool pend = active && pend_f(*val);
+  if (!__any_sync(FULL_MASK, pend)) return true;
+  const uint64_t t0 = globaltimer_ns();
+  unsigned backoff = 32;
+  for (unsigned it = 0;; ++it) {
+    if (pend) {
+      *val = ld_gpu(p);
+      pend = pend_f(*val);
+    }
+    if (!__any_sync(FULL_MASK, pend)) return true;
+    if ((it & 7u) == 7u &&
+        (earlier_failed(err, row) || (int64_t)(globaltimer_ns() - t0) > limit_ns))
+      return false;
+    __nanosleep(backoff);
+    if (backoff < 256u) backoff <<= 1;
+  }
+}
+
+__global__ void k_fill_pending_f(int64_t n, double *x) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = __longlong_as_double((long long)kPendingF);
+}
+
 __global__ void __launch_bounds__(kNumThreads)
 k_numeric(int64_t n, int64_t nbatch, const int64_t *__restrict__ arp,
           const int32_t *__restrict__ a2f, const double *__restrict__ aval, int64_t astride,
           const int64_t *__restrict__ frp, const int32_t *__restrict__ fci,
-          const int64_t *__restrict__ fdiag, double *fval, int64_t fstride, int *ready,
-          unsigned long long *ticket, DevErr *errs, int cap, int64_t limit_ns,
-          int64_t hold) {
+          const int64_t *__restrict__ fdiag, double *fval, int64_t fstride,
+          unsigned long long *ticket, DevErr *errs, int cap, int64_t limit_ns, int64_t hold) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
@@ -45,22 +92,19 @@ k_numeric(int64_t n, int64_t nbatch, const int64_t *__restrict__ arp,
     DevErr *err = errs + set;
     if (earlier_failed(err, row)) continue;
     double *fv = fval + set * fstride;
-    int *rdy = ready + set * n;
     const double *av = aval + set * astride;
 
     const int64_t b0 = frp[row];
     const int m = (int)(frp[row + 1] - b0);
     const int dp = (int)(fdiag[row] - b0);
-    const bool in_smem = m <= cap;
-    const int32_t *rc = in_smem ? scols : fci + b0;
-    double *rv = in_smem ? svals : fv + b0;
-    if (in_smem) {
-      for (int q = lane; q < m; q += 32) {
-        scols[q] = fci[b0 + q];
-        svals[q] = 0.0;
-      }
-    } else {
-      for (int q = lane; q < m; q += 32) fv[b0 + q] = 0.0;
+    // The slice holds the whole row (numeric_cap sizes it for the longest
+    // row of F): the output segment cannot serve as scratch, since other rows
+    // read it as soon as an entry leaves the pending state.
+    const int32_t *rc = scols;
+    double *rv = svals;
+    for (int q = lane; q < m; q += 32) {
+      scols[q] = fci[b0 + q];
+      svals[q] = 0.0;
     }
     __syncwarp();
     bool bad = false;
@@ -71,29 +115,49 @@ k_numeric(int64_t n, int64_t nbatch, const int64_t *__restrict__ arp,
     }
     if (__any_sync(FULL_MASK, bad)) {
       if (lane == 0) set_err(err, row, ILUK_ENONFINITE);
-      warp_publish(&rdy[row], lane);
       continue;
     }
     __syncwarp();
 
     bool ok = true;
-    for (int q = 0; q < dp; ++q) {
+    for (int q = 0; q < dp && ok; ++q) {
       const int h = rc[q];
-      if (!wait_flag(&rdy[h], err, row, limit_ns)) {
-        ok = false;
-        break;
-      }
       const int64_t hd = fdiag[h];
-      const double piv = *((volatile double *)&fv[hd]);
-      const double fih = __ddiv_rn(rv[q], piv);
-      __syncwarp();
-      if (lane == 0) rv[q] = fih;
       const int64_t u1 = frp[h + 1];
-      for (int64_t r = hd + 1 + lane; r < u1; r += 32) {
-        const int32_t j = fci[r];
-        const double fhj = *((volatile double *)&fv[r]);
-        const int pos = lower_bound_i(rc, q + 1, m, j);
-        if (pos < m && rc[pos] == j) rv[pos] = sub_prod(rv[pos], fih, fhj);
+      double piv = ld_gpu(&fv[hd]);
+      for (int64_t base = hd + 1; base < u1 || base == hd + 1; base += 32) {
+        // pattern work first (static), then the values of row h
+        const int64_t r = base + lane;
+        const bool inr = r < u1;
+        int pos = -1;
+        double fhj = 0.0;
+        if (inr) {
+          const int32_t j = fci[r];
+          const int ps = lower_bound_i(rc, q + 1, m, j);
+          if (ps < m && rc[ps] == j) {
+            pos = ps;
+            fhj = ld_gpu(&fv[r]);
+          }
+        }
+        if (base == hd + 1) {
+          if (!wait_vals(&fv[hd], true, &piv, err, row, limit_ns)) {
+            ok = false;
+            break;
+          }
+        }
+        if (!wait_vals(&fv[r], pos >= 0, &fhj, err, row, limit_ns)) {
+          ok = false;
+          break;
+        }
+        if (base == hd + 1) {
+          const double fih = __ddiv_rn(rv[q], piv);
+          __syncwarp();
+          if (lane == 0) rv[q] = fih;
+          __syncwarp();
+        }
+        const double fih = rv[q];
+        if (pos >= 0) rv[pos] = sub_prod(rv[pos], fih, fhj);
+        if (base + 32 >= u1) break;
       }
       __syncwarp();
     }
@@ -101,12 +165,10 @@ k_numeric(int64_t n, int64_t nbatch, const int64_t *__restrict__ arp,
       if (lane == 0 && !earlier_failed(err, row)) set_err(err, row, ILUK_ETIMEOUT);
       continue;
     }
-    if (in_smem) {
-      for (int q = lane; q < m; q += 32) fv[b0 + q] = svals[q];
-    }
-    __syncwarp();
     if (lane == 0 && rv[dp] == 0.0) set_err(err, row, ILUK_EZEROPIVOT);
-    if (row != hold) warp_publish(&rdy[row], lane);
+    if (row != hold)
+      for (int q = lane; q < m; q += 32) fv[b0 + q] = svals[q];
+    __syncwarp();
   }
 }
 
@@ -118,19 +180,28 @@ static int numeric_cap(const iluk_sym *S, int *warps_out, size_t *smem_out) {
   int warps = kNumThreads / 32;
   const size_t budget = (size_t)max_smem_optin();
   while (warps > 1 && (size_t)cap * 12 * warps > budget) warps >>= 1;
-  if ((size_t)cap * 12 * warps > budget) cap = (int)(budget / 12 / warps) & ~31;  // long rows in global
+  if ((size_t)cap * 12 * warps > budget) return -1;  // a row of F exceeds shared memory
   *warps_out = warps;
   *smem_out = (size_t)cap * 12 * warps;
   return cap;
 }
 
 static cudaError_t launch_numeric_impl(const iluk_sym *S, int64_t nbatch, const double *avals,
-                                       double *fvals, int *ready, unsigned long long *ticket,
-                                       DevErr *errs, cudaStream_t s) {
+                                       double *fvals, unsigned long long *ticket, DevErr *errs,
+                                       cudaStream_t s) {
   ProfScope prof_scope(ILUK_PROF_NUMERIC, s);
   int warps;
   size_t smem;
   const int cap = numeric_cap(S, &warps, &smem);
+  if (cap < 0) return cudaErrorMemoryAllocation;
+  {
+    const int64_t nv = S->nnz * nbatch;
+    int64_t b = (nv + 255) / 256;
+    if (b > (int64_t)num_sms() * 8) b = (int64_t)num_sms() * 8;
+    if (b < 1) b = 1;
+    k_fill_pending_f<<<(unsigned)b, 256, 0, s>>>(nv, fvals);
+    note_launch();
+  }
   cudaError_t e = cudaFuncSetAttribute(k_numeric, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
@@ -143,20 +214,20 @@ static cudaError_t launch_numeric_impl(const iluk_sym *S, int64_t nbatch, const 
   if (grid < 1) grid = 1;
   k_numeric<<<(unsigned)grid, warps * 32, smem, s>>>(
       S->n, nbatch, S->arowptr, S->a2f, avals, S->nnzA, S->rowptr, S->colind, S->diag, fvals,
-      S->nnz, ready, ticket, errs, cap, wait_limit(), hold_row());
+      S->nnz, ticket, errs, cap, wait_limit(), hold_row());
   note_launch();
   return cudaGetLastError();
 }
 
-cudaError_t launch_numeric(const iluk_sym *S, const double *aval, double *fval, int *ready,
+cudaError_t launch_numeric(const iluk_sym *S, const double *aval, double *fval,
                            unsigned long long *ticket, DevErr *err, cudaStream_t s) {
-  return launch_numeric_impl(S, 1, aval, fval, ready, ticket, err, s);
+  return launch_numeric_impl(S, 1, aval, fval, ticket, err, s);
 }
 
 cudaError_t launch_numeric_batched(const iluk_sym *S, int64_t nbatch, const double *avals,
-                                   double *fvals, int *ready, unsigned long long *ticket,
-                                   DevErr *errs, cudaStream_t s) {
-  return launch_numeric_impl(S, nbatch, avals, fvals, ready, ticket, errs, s);
+                                   double *fvals, unsigned long long *ticket, DevErr *errs,
+                                   cudaStream_t s) {
+  return launch_numeric_impl(S, nbatch, avals, fvals, ticket, errs, s);
 }
 
 }  // namespace iluk

@@ -2,9 +2,9 @@
 //
 // Lower part (Eq. inversedefine restricted to F's lower pattern):
 //   beta_it = f_it - sum_{t<h<i} f_ih beta_ht,
-// one warp per row, rows ascending with ready flags: b_i. starts as the
-// final multipliers of row i; for each h in L(i) ascending, after row h is
-// final, b_it <- b_it - f_ih * beta_ht for every t < h stored in both rows.
+// one warp per row, rows ascending: b_i. starts as the final multipliers of
+// row i; for each h in L(i) ascending, once the values of row h are final,
+// b_it <- b_it - f_ih * beta_ht for every t < h stored in both rows.
 // The stored value is -beta (Eq. flipfactor), so a dependant reads
 // beta_ht = -g_ht, an exact negation.
 //
@@ -21,17 +21,38 @@ namespace iluk {
 
 constexpr int kIiThreads = 256;
 
+// The output g doubles as the ready flag of each row, as in the numeric
+// phase: g is filled with kPendingG before the launch and a dependant reads
+// the values it needs, retrying while they are pending.
+constexpr unsigned long long kPendingG = 0x7FF0DEADBEEFCAFEull;
+
+__device__ __forceinline__ bool pend_g(double v) {
+  return (unsigned long long)__double_as_longlong(v) == kPendingG;
+}
+
+__device__ __forceinline__ double ld_gpu_g(const double *p) {
+  double v;
+  asm volatile("ld.relaxed.gpu.global.f64 %0, [%1];" : "=d"(v) : "l"(p));
+  return v;
+}
+
+__global__ void k_fill_pending_g(int64_t n, double *x) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = __longlong_as_double((long long)kPendingG);
+}
+
 template <bool LOWER>
 __global__ void __launch_bounds__(kIiThreads)
 k_iiluk_build(int64_t n, const int64_t *__restrict__ frp, const int32_t *__restrict__ fci,
               const int64_t *__restrict__ fdiag, const double *__restrict__ fval, double *g,
-              int *ready, unsigned long long *ticket, DevErr *err, int cap, int64_t limit_ns) {
+              unsigned long long *ticket, DevErr *err, int cap, int64_t limit_ns) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   const int nwarps = blockDim.x >> 5;
-  double *sval = reinterpret_cast<double *>(smem) + (size_t)wib * cap;
-  int32_t *scol = reinterpret_cast<int32_t *>(smem + (size_t)nwarps * cap * 8) + (size_t)wib * cap;
+  double *rv = reinterpret_cast<double *>(smem) + (size_t)wib * cap;
+  int32_t *rc = reinterpret_cast<int32_t *>(smem + (size_t)nwarps * cap * 8) + (size_t)wib * cap;
 
   for (;;) {
     unsigned long long tk = 0;
@@ -41,36 +62,57 @@ k_iiluk_build(int64_t n, const int64_t *__restrict__ frp, const int32_t *__restr
     if (earlier_failed(err, t)) continue;
     const int64_t row = LOWER ? t : n - 1 - t;
     const int64_t d = fdiag[row];
-    const int64_t s0 = LOWER ? frp[row] : d + 1;      // segment of the row handled here
+    const int64_t s0 = LOWER ? frp[row] : d + 1;  // segment of the row handled here
     const int m = (int)((LOWER ? d : frp[row + 1]) - s0);
     const double uii = fval[d];
-    const bool in_smem = m <= cap;
-    const int32_t *rc = in_smem ? scol : fci + s0;
-    double *rv = in_smem ? sval : g + s0;  // long rows work in the output in place
     for (int q = lane; q < m; q += 32) {
-      const double init = LOWER ? fval[s0 + q] : __ddiv_rn(fval[s0 + q], uii);
-      if (in_smem) scol[q] = fci[s0 + q];
-      rv[q] = init;
+      rc[q] = fci[s0 + q];
+      rv[q] = LOWER ? fval[s0 + q] : __ddiv_rn(fval[s0 + q], uii);
     }
     __syncwarp();
     bool ok = true;
-    for (int qq = 0; qq < m; ++qq) {
+    for (int qq = 0; qq < m && ok; ++qq) {
       const int q = LOWER ? qq : m - 1 - qq;  // pivots ascending / descending
       const int h = rc[q];
-      if (!wait_flag(&ready[h], err, t, limit_ns)) {
-        ok = false;
-        break;
-      }
       const double coef = LOWER ? fval[s0 + q] : __ddiv_rn(fval[s0 + q], uii);
       const int64_t hd = fdiag[h];
       const int64_t r0 = LOWER ? frp[h] : hd + 1;
       const int64_t r1 = LOWER ? hd : frp[h + 1];
-      for (int64_t r = r0 + lane; r < r1; r += 32) {
-        const int32_t col = fci[r];
-        const double prev = -*((volatile double *)&g[r]);  // beta_ht or gamma_ht
-        const int pos = LOWER ? lower_bound_i(rc, 0, q, col) : lower_bound_i(rc, q + 1, m, col);
-        const int hi = LOWER ? q : m;
-        if (pos < hi && rc[pos] == col) rv[pos] = sub_prod(rv[pos], coef, prev);
+      for (int64_t base = r0; base < r1; base += 32) {
+        const int64_t r = base + lane;
+        int pos = -1;
+        double gv = 0.0;
+        if (r < r1) {
+          const int32_t col = fci[r];
+          const int lo = LOWER ? 0 : q + 1, hi = LOWER ? q : m;
+          const int ps = lower_bound_i(rc, lo, hi, col);
+          if (ps < hi && rc[ps] == col) {
+            pos = ps;
+            gv = ld_gpu_g(&g[r]);
+          }
+        }
+        bool pend = pos >= 0 && pend_g(gv);
+        if (__any_sync(FULL_MASK, pend)) {
+          const uint64_t t0 = globaltimer_ns();
+          unsigned backoff = 32;
+          for (unsigned it = 0;; ++it) {
+            if (pend) {
+              gv = ld_gpu_g(&g[r]);
+              pend = pend_g(gv);
+            }
+            if (!__any_sync(FULL_MASK, pend)) break;
+            if ((it & 7u) == 7u &&
+                (earlier_failed(err, t) || (int64_t)(globaltimer_ns() - t0) > limit_ns)) {
+              ok = false;
+              break;
+            }
+            __nanosleep(backoff);
+            if (backoff < 256u) backoff <<= 1;
+          }
+          if (!__all_sync(FULL_MASK, ok)) break;
+        }
+        // beta_ht = -g_ht (or gamma_ht = -g_ht), an exact negation
+        if (pos >= 0) rv[pos] = sub_prod(rv[pos], coef, -gv);
       }
       __syncwarp();
     }
@@ -80,7 +122,7 @@ k_iiluk_build(int64_t n, const int64_t *__restrict__ frp, const int32_t *__restr
     }
     for (int q = lane; q < m; q += 32) g[s0 + q] = -rv[q];
     if (!LOWER && lane == 0) g[d] = uii;
-    warp_publish(&ready[row], lane);
+    __syncwarp();
   }
 }
 
@@ -92,12 +134,18 @@ cudaError_t launch_iiluk_build(const iluk_sym *S, const double *fval, double *g,
   int warps = kIiThreads / 32;
   const size_t budget = (size_t)max_smem_optin();
   while (warps > 1 && (size_t)cap * 12 * warps > budget) warps >>= 1;
-  if ((size_t)cap * 12 * warps > budget) cap = (int)(budget / 12 / warps) & ~31;
+  if ((size_t)cap * 12 * warps > budget) return cudaErrorMemoryAllocation;
   const size_t smem = (size_t)cap * 12 * warps;
   unsigned long long *tick = reinterpret_cast<unsigned long long *>(sync);
-  int *fl_l = sync + 4, *fl_u = sync + 4 + n;
-  cudaError_t e = cudaMemsetAsync(sync, 0, (4 + 2 * (size_t)n) * sizeof(int), s);
+  cudaError_t e = cudaMemsetAsync(sync, 0, 4 * sizeof(int), s);
   if (e != cudaSuccess) return e;
+  {
+    int64_t b = (S->nnz + 255) / 256;
+    if (b > (int64_t)num_sms() * 8) b = (int64_t)num_sms() * 8;
+    if (b < 1) b = 1;
+    k_fill_pending_g<<<(unsigned)b, 256, 0, s>>>(S->nnz, g);
+    note_launch();
+  }
   int bps = 0;
   e = cudaFuncSetAttribute(k_iiluk_build<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem);
@@ -113,13 +161,13 @@ cudaError_t launch_iiluk_build(const iluk_sym *S, const double *fval, double *g,
   {
     ProfScope prof_scope(ILUK_PROF_IILU_BUILD, s);
     k_iiluk_build<true><<<(unsigned)grid, warps * 32, smem, s>>>(
-        n, S->rowptr, S->colind, S->diag, fval, g, fl_l, tick, err, cap, wait_limit());
+        n, S->rowptr, S->colind, S->diag, fval, g, tick, err, cap, wait_limit());
     note_launch();
   }
   {
     ProfScope prof_scope(ILUK_PROF_IILU_BUILD, s);
     k_iiluk_build<false><<<(unsigned)grid, warps * 32, smem, s>>>(
-        n, S->rowptr, S->colind, S->diag, fval, g, fl_u, tick + 1, err + 1, cap, wait_limit());
+        n, S->rowptr, S->colind, S->diag, fval, g, tick + 1, err + 1, cap, wait_limit());
     note_launch();
   }
   return cudaGetLastError();
