@@ -128,7 +128,7 @@ enum {
   ILUK_PROF_VALIDATE = 0, ILUK_PROF_SYMBOLIC = 1, ILUK_PROF_COMPACT = 2, ILUK_PROF_DEPTH = 3,
   ILUK_PROF_NUMERIC = 4, ILUK_PROF_SWEEP = 5 /* forward sweeps */, ILUK_PROF_TRANSPOSE = 6, ILUK_PROF_IILU_BUILD = 7,
   ILUK_PROF_IILU_APPLY = 8, ILUK_PROF_SPMV = 9, ILUK_PROF_DOT = 10, ILUK_PROF_VECTOR = 11,
-  ILUK_PROF_SWEEP_BWD = 12, ILUK_PROF_KINDS = 13
+  ILUK_PROF_SWEEP_BWD = 12, ILUK_PROF_BATCH = 13, ILUK_PROF_KINDS = 14
 };
 int iluk_prof_enable(int on);
 int iluk_prof_read(double *ms, int64_t *count, int nkinds);
@@ -265,6 +265,44 @@ int iluk_adjoint_scatter(const iluk_pattern *A, const double *lambda, const doub
  */
 int iluk_numeric_batched(const iluk_sym *S, int64_t nbatch, const double *A_vals,
                          double *F_vals, iluk_info *infos, void *stream);
+
+/*
+ * a7. Batched solve: every item is numerically factored (ILU(k) on its
+ * symbolic handle) and solved by right-preconditioned GMRES(restart) with the
+ * ILU sweeps, all items in ONE persistent launch (each CTA takes the next item
+ * and runs its whole pipeline).  Items may have different patterns and sizes;
+ * items sharing an iluk_sym share its pattern arrays.  Every item's x (and its
+ * iteration count and residual) is bit-identical to iluk_numeric + gmres_solve
+ * on that item alone.
+ *
+ * iluk_batch_create: synchronous; copies the item descriptors (device
+ * pointers, borrowed until iluk_batch_destroy) and allocates the workspace.
+ * restart <= 64.
+ * iluk_batch_solve: asynchronous, no host round trip and no allocation, so it
+ * can be recorded in a CUDA graph by stream capture; the first call outside a
+ * capture times the two CTA widths (512 and 1024 threads per item) and keeps
+ * the faster (autotuner).  New values written into the same a_val / b buffers
+ * are picked up by the next call.
+ * iluk_batch_results: synchronous; infos (host, may be NULL) gets one entry per
+ * item; returns the first item's non-OK status, if any.
+ */
+typedef struct {
+  const iluk_sym *S;        /* symbolic handle of this item's pattern            */
+  const int64_t *a_rowptr;  /* device int64[n+1], the pattern S was built from   */
+  const int32_t *a_colind;  /* device int32[nnz_A]                               */
+  const double *a_val;      /* device double[nnz_A]                              */
+  const double *b;          /* device double[n]                                  */
+  double *x;                /* device double[n], output                          */
+} iluk_batch_item;
+typedef struct iluk_batch iluk_batch;
+
+int iluk_batch_create(const iluk_batch_item *items, int64_t nitems, int restart, double rtol,
+                      int maxit, iluk_batch **B, void *stream);
+int iluk_batch_solve(iluk_batch *B, void *stream);
+int iluk_batch_results(iluk_batch *B, iluk_info *infos, void *stream);
+/* Threads per item chosen by the autotuner (0 until the first solve). */
+int iluk_batch_width(const iluk_batch *B);
+void iluk_batch_destroy(iluk_batch *B);
 
 #ifdef __cplusplus
 }

@@ -6,12 +6,13 @@ Memory" (arXiv 0803.0048).  The work runs in libiluk.so (CUDA, sm_103a,
 declared in include/iluk.h); this package is its thin Python binding.
 """
 from . import _lib
-from .api import (CsrPattern, Factors, IlukError, IncompleteInverse, Symbolic, adjoint_scatter,
+from .autograd import IlukSolve, IlukSolver
+from .api import (BatchSolve, CsrPattern, Factors, IlukError, IncompleteInverse, Symbolic, adjoint_scatter,
                   debug_hold_row, dot, gmres, iiluk_build, launch_count, numeric,
                   numeric_batched, prof_enable, prof_read, set_wait_limit, spmv, symbolic,
                   validate)
 
-__all__ = ["CsrPattern", "Factors", "IlukError", "IncompleteInverse", "Symbolic",
+__all__ = ["IlukSolve", "IlukSolver", "BatchSolve", "CsrPattern", "Factors", "IlukError", "IncompleteInverse", "Symbolic",
            "adjoint_scatter", "debug_hold_row", "dot", "gmres", "iiluk_build", "launch_count",
            "numeric", "numeric_batched", "prof_enable", "prof_read", "set_wait_limit", "spmv",
            "symbolic", "validate"]

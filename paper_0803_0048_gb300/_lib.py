@@ -17,7 +17,7 @@ OK, EINVAL, EPATTERN, ENODIAG, EZEROPIVOT, ENONFINITE, ENOMEM, ETIMEOUT, ENOCONV
 PREC_NONE, PREC_ILU, PREC_IILU = 0, 1, 2
 SCHED_AUTO, SCHED_FLAGS, SCHED_SINGLE_CTA = 0, 1, 2
 PROF_KINDS = ["validate", "symbolic", "compact", "depth", "numeric", "sweep", "transpose",
-              "iilu_build", "iilu_apply", "spmv", "dot", "vector", "sweep_bwd"]
+              "iilu_build", "iilu_apply", "spmv", "dot", "vector", "sweep_bwd", "batch"]
 
 
 class Pattern(C.Structure):
@@ -29,6 +29,11 @@ class Info(C.Structure):
     _fields_ = [("status", C.c_int32), ("iters", C.c_int32), ("row", C.c_int64),
                 ("relres", C.c_double), ("need", C.c_int64), ("cycles", C.c_int32),
                 ("reserved", C.c_int32)]
+
+
+class BatchItem(C.Structure):
+    _fields_ = [("S", C.c_void_p), ("a_rowptr", C.c_void_p), ("a_colind", C.c_void_p),
+                ("a_val", C.c_void_p), ("b", C.c_void_p), ("x", C.c_void_p)]
 
 
 class SymView(C.Structure):
@@ -74,6 +79,11 @@ SIGNATURES = [
     ("gmres_solve", I, [P, P, I, P, P, P, I, D, I, I, P, P]),
     ("iluk_adjoint_scatter", I, [P, P, P, P, P]),
     ("iluk_numeric_batched", I, [P, I64, P, P, P, P]),
+    ("iluk_batch_create", I, [P, I64, I, D, I, PP, P]),
+    ("iluk_batch_solve", I, [P, P]),
+    ("iluk_batch_results", I, [P, P, P]),
+    ("iluk_batch_width", I, [P]),
+    ("iluk_batch_destroy", None, [P]),
 ]
 
 _lock = threading.Lock()

@@ -292,3 +292,42 @@ def prof_read() -> dict:
     cnt = (C.c_int64 * nk)()
     _call(L.load().iluk_prof_read, ms, cnt, nk)
     return {L.PROF_KINDS[k]: (ms[k], cnt[k]) for k in range(nk)}
+
+
+class BatchSolve:
+    """a7: factor + GMRES for many systems in one persistent launch.
+
+    ``items`` is a list of (Symbolic, a_vals, b, x) with device tensors; the
+    x tensors receive the solutions.  ``solve()`` only enqueues work (it can be
+    captured in a CUDA graph after a first call outside the capture);
+    ``results()`` synchronizes and returns one Info per item."""
+
+    def __init__(self, items, restart=30, rtol=1e-8, maxit=10000):
+        self.items = list(items)  # keep the tensors alive
+        arr = (L.BatchItem * max(len(self.items), 1))()
+        for i, (S, vals, b, x) in enumerate(self.items):
+            _check_dev(vals, b, x)
+            arr[i] = L.BatchItem(S.h.value if isinstance(S.h, C.c_void_p) else S.h,
+                                 S.A.rowptr.data_ptr(), S.A.colind.data_ptr(), vals.data_ptr(),
+                                 b.data_ptr(), x.data_ptr())
+        self.h = C.c_void_p()
+        _call(L.load().iluk_batch_create, arr, len(self.items), int(restart), float(rtol),
+              int(maxit), C.byref(self.h), C.c_void_p(_stream()))
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            torch.cuda.synchronize()
+            L.load().iluk_batch_destroy(self.h)
+            self.h = None
+
+    def solve(self) -> None:
+        _call(L.load().iluk_batch_solve, self.h, C.c_void_p(_stream()))
+
+    def results(self):
+        n = len(self.items)
+        infos = (L.Info * max(n, 1))()
+        L.load().iluk_batch_results(self.h, infos, C.c_void_p(_stream()))
+        return [infos[i] for i in range(n)]
+
+    def width(self) -> int:
+        return L.load().iluk_batch_width(self.h)

@@ -20,7 +20,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libiluk.so")
 SOURCES = ["capi.cu", "validate.cu", "symbolic.cu", "numeric.cu", "sweeps.cu", "tpiilu.cu",
-           "krylov.cu", "levels.cu"]
+           "krylov.cu", "levels.cu", "batched.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "--fmad=false", "-Xcompiler", "-fPIC",
          "-Xcompiler", "-ffp-contract=off", "-Xcompiler", "-fno-fast-math",

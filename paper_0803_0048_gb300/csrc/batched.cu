@@ -1,0 +1,431 @@
+// batched.cu -- a7: many systems, numerically factored and solved in one
+// persistent launch.
+//
+// Each CTA of a persistent grid takes the next instance (an atomic ticket) and
+// runs its whole pipeline alone: ILU(k) numeric factorization, then
+// right-preconditioned GMRES(m) with the ILU sweeps, exactly the algorithm of
+// the single-instance path.  Inside a CTA there is no waiting on flags: the
+// factorization and both sweeps walk the instance's level sets (built by the
+// symbolic phase) with a __syncthreads between levels, and the warps walk the
+// rows of a level with converged FP64 instructions.  Inner products follow the
+// same 4096-partial fixed tree as the single-instance path, so every instance
+// is bit-identical to solving it on its own.  Instances may have different
+// patterns and sizes (uneven grids); those sharing one symbolic handle share
+// its pattern arrays.  The work is enqueued asynchronously with no host
+// round trip, so a stream capture records it as a graph.
+#include "internal.h"
+
+namespace iluk {
+
+constexpr int kBMaxRestart = 64;
+
+struct BatchItemDev {
+  int64_t n, nnzA, nnzF;
+  const int64_t *arp;
+  const int32_t *aci;
+  const double *aval;
+  const int64_t *frp;
+  const int32_t *fci;
+  const int64_t *fdiag;
+  const int64_t *farp;  // A row pointers as stored by the symbolic phase
+  const int32_t *a2f;
+  const int32_t *lord;
+  const int64_t *lstart;
+  int32_t nlev_l;
+  const int32_t *uord;
+  const int64_t *ustart;
+  int32_t nlev_u;
+  const double *b;
+  double *x;
+};
+
+struct BatchResultDev {
+  int32_t status, iters, cycles, pad;
+  int64_t row;
+  double relres;
+};
+
+struct BatchWork {
+  double *fval, *V, *w, *z, *u, *tmp;
+  int64_t ldv;  // stride between basis vectors
+};
+
+// --- in-CTA building blocks -------------------------------------------------
+
+// Fixed-shape inner product (same shape as k_dot): partial p sums i = p,
+// p + 4096, ... from +0.0; pairwise tree.  If `upd` is set, first applies
+// w_i <- w_i - h * v_i to the indices the partial owns.  Result broadcast.
+template <int NT>
+__device__ double cta_dot(int64_t n, double *w, const double *v, double h, bool upd,
+                          const double *y, double *sh, bool take_sqrt) {
+  for (int k = 0; k < kDotP / NT; ++k) {
+    const int p = threadIdx.x + k * NT;
+    double s = 0.0;
+    for (int64_t i = p; i < n; i += kDotP) {
+      double wi = w[i];
+      if (upd) {
+        wi = __dsub_rn(wi, __dmul_rn(h, v[i]));
+        w[i] = wi;
+      }
+      s = __dadd_rn(s, __dmul_rn(wi, y == nullptr ? wi : y[i]));
+    }
+    sh[p] = s;
+  }
+  __syncthreads();
+  for (int wdt = kDotP / 2; wdt >= 1; wdt >>= 1) {
+    for (int p = threadIdx.x; p < wdt; p += NT) sh[p] = __dadd_rn(sh[p], sh[p + wdt]);
+    __syncthreads();
+  }
+  const double r = take_sqrt ? __dsqrt_rn(sh[0]) : sh[0];
+  __syncthreads();
+  return r;
+}
+
+// y = A x (bm == nullptr) or y = bm - A x; rows summed left to right from 0.
+template <int NT>
+__device__ void cta_spmv(const BatchItemDev &it, const double *x, double *y, const double *bm) {
+  for (int64_t row = threadIdx.x; row < it.n; row += NT) {
+    double s = 0.0;
+    for (int64_t p = it.arp[row]; p < it.arp[row + 1]; ++p)
+      s = __dadd_rn(s, __dmul_rn(it.aval[p], x[it.aci[p]]));
+    y[row] = bm ? __dsub_rn(bm[row], s) : s;
+  }
+  __syncthreads();
+}
+
+// One sweep, level by level; the 32 rows a warp takes from a level run their
+// chains in lockstep (right-aligned), forward left to right, backward right
+// to left, exactly the order of the single-instance kernels.
+template <int NT, bool FORWARD>
+__device__ void cta_sweep(const BatchItemDev &it, const double *fv, const double *in, double *out) {
+  const int32_t *order = FORWARD ? it.lord : it.uord;
+  const int64_t *start = FORWARD ? it.lstart : it.ustart;
+  const int nlev = FORWARD ? it.nlev_l : it.nlev_u;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int l = 0; l < nlev; ++l) {
+    for (int64_t s0 = start[l] + (int64_t)wid * 32; s0 < start[l + 1]; s0 += NT) {
+      const int64_t row = order[s0 + lane];
+      int64_t first = 0, d = 0;
+      int mylen = 0;
+      double s = 0.0;
+      if (row >= 0) {
+        d = it.fdiag[row];
+        if (FORWARD) {
+          first = it.frp[row];
+          mylen = (int)(d - first);
+        } else {
+          first = it.frp[row + 1] - 1;
+          mylen = (int)(first - d);
+        }
+        s = in[row];
+      }
+      const int maxlen = __reduce_max_sync(FULL_MASK, mylen);
+      const int off = maxlen - mylen;
+      for (int q = 0; q < maxlen; ++q) {
+        const int e = q - off;
+        if (e >= 0) {
+          const int64_t pq = FORWARD ? first + e : first - e;
+          s = __dsub_rn(s, __dmul_rn(fv[pq], out[it.fci[pq]]));
+        }
+      }
+      if (row >= 0) out[row] = FORWARD ? s : __ddiv_rn(s, fv[d]);
+    }
+    __syncthreads();
+  }
+}
+
+// Numeric factorization, level by level over the forward level sets; one
+// warp per row, the row in the warp's shared slice, pivots ascending.
+template <int NT>
+__device__ bool cta_numeric(const BatchItemDev &it, double *fv, double *svals, int32_t *scols,
+                            int cap, BatchResultDev *res) {
+  constexpr int kBWarps = NT / 32;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  double *rv = svals + (size_t)wid * cap;
+  int32_t *rc = scols + (size_t)wid * cap;
+  __shared__ int s_bad;
+  __shared__ long long s_badrow;
+  if (threadIdx.x == 0) {
+    s_bad = 0;
+    s_badrow = 0x7fffffffffffffffLL;
+  }
+  __syncthreads();
+  for (int l = 0; l < it.nlev_l; ++l) {
+    for (int64_t slot = it.lstart[l] + wid; slot < it.lstart[l + 1]; slot += kBWarps) {
+      const int64_t row = it.lord[slot];
+      if (row < 0) continue;
+      const int64_t b0 = it.frp[row];
+      const int m = (int)(it.frp[row + 1] - b0);
+      const int dp = (int)(it.fdiag[row] - b0);
+      for (int q = lane; q < m; q += 32) {
+        rc[q] = it.fci[b0 + q];
+        rv[q] = 0.0;
+      }
+      __syncwarp();
+      bool bad = false;
+      for (int64_t p = it.farp[row] + lane; p < it.farp[row + 1]; p += 32) {
+        const double a = it.aval[p];
+        if (!isfinite(a)) bad = true;
+        rv[it.a2f[p]] = a;
+      }
+      if (__any_sync(FULL_MASK, bad)) {
+        if (lane == 0) {
+          atomicCAS(&s_bad, 0, ILUK_ENONFINITE);
+          atomicMin(&s_badrow, (long long)row);
+        }
+      }
+      __syncwarp();
+      for (int q = 0; q < dp; ++q) {
+        const int h = rc[q];
+        const int64_t hd = it.fdiag[h];
+        const double fih = __ddiv_rn(rv[q], fv[hd]);
+        __syncwarp();
+        if (lane == 0) rv[q] = fih;
+        __syncwarp();
+        for (int64_t r = hd + 1 + lane; r < it.frp[h + 1]; r += 32) {
+          const int32_t j = it.fci[r];
+          const int pos = lower_bound_i(rc, q + 1, m, j);
+          if (pos < m && rc[pos] == j) rv[pos] = sub_prod(rv[pos], fih, fv[r]);
+        }
+        __syncwarp();
+      }
+      for (int q = lane; q < m; q += 32) fv[b0 + q] = rv[q];
+      if (lane == 0 && rv[dp] == 0.0) {
+        atomicCAS(&s_bad, 0, ILUK_EZEROPIVOT);
+        atomicMin(&s_badrow, (long long)row);
+      }
+      __syncwarp();
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && s_bad) {
+    res->status = s_bad;
+    res->row = s_badrow;
+  }
+  __syncthreads();
+  return s_bad == 0;
+}
+
+template <int NT>
+__device__ void cta_apply(const BatchItemDev &it, const double *fv, const double *p, double *tmp,
+                          double *y) {
+  cta_sweep<NT, true>(it, fv, p, tmp);
+  cta_sweep<NT, false>(it, fv, tmp, y);
+}
+
+template <int NT>
+__device__ void cta_vec_div(int64_t n, const double *x, double den, double *y) {
+  if (den != 0.0)
+    for (int64_t i = threadIdx.x; i < n; i += NT) y[i] = __ddiv_rn(x[i], den);
+  __syncthreads();
+}
+
+// --- the persistent kernel ---------------------------------------------------
+
+template <int NT>
+__global__ void __launch_bounds__(NT, 1024 / NT)
+k_batch_solve(const BatchItemDev *items, int64_t nitems, BatchResultDev *results,
+              BatchWork *work, unsigned long long *ticket, int m, double rtol, int maxit,
+              int cap) {
+  constexpr int kBWarps = NT / 32;
+  extern __shared__ __align__(16) unsigned char smem[];
+  double *sh = reinterpret_cast<double *>(smem);                 // kDotP doubles
+  double *svals = sh + kDotP;                                    // kBWarps * cap
+  int32_t *scols = reinterpret_cast<int32_t *>(svals + (size_t)kBWarps * cap);
+  __shared__ double H[(kBMaxRestart + 1) * kBMaxRestart];
+  __shared__ double cs[kBMaxRestart], sn[kBMaxRestart], gv[kBMaxRestart + 1], yv[kBMaxRestart];
+  __shared__ unsigned long long s_item;
+  __shared__ int s_stop;
+  const BatchWork wk = work[blockIdx.x];
+
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(ticket, 1ull);
+    __syncthreads();
+    const unsigned long long id = s_item;
+    __syncthreads();
+    if (id >= (unsigned long long)nitems) return;
+    const BatchItemDev it = items[id];
+    BatchResultDev *res = results + id;
+    const int64_t n = it.n;
+    if (threadIdx.x == 0) {
+      res->status = ILUK_OK;
+      res->row = -1;
+      res->iters = 0;
+      res->cycles = 0;
+      res->relres = 0.0;
+    }
+    if (!cta_numeric<NT>(it, wk.fval, svals, scols, cap, res)) continue;
+
+    // GMRES(m): the same steps, in the same order, as gmres_solve.
+    const double bnorm = cta_dot<NT>(n, const_cast<double *>(it.b), nullptr, 0.0, false, nullptr,
+                                     sh, true);
+    for (int64_t i = threadIdx.x; i < n; i += NT) it.x[i] = 0.0;
+    __syncthreads();
+    int iters = 0, cycles = 0;
+    double relres = 0.0;
+    int status = ILUK_ENOCONV;
+    if (bnorm == 0.0) status = ILUK_OK;
+    while (bnorm != 0.0) {
+      cta_spmv<NT>(it, it.x, wk.w, it.b);
+      const double beta = cta_dot<NT>(n, wk.w, nullptr, 0.0, false, nullptr, sh, true);
+      relres = beta / bnorm;
+      if (relres <= rtol) { status = ILUK_OK; break; }
+      if (iters >= maxit) { status = ILUK_ENOCONV; break; }
+      ++cycles;
+      cta_vec_div<NT>(n, wk.w, beta, wk.V);
+      if (threadIdx.x == 0) gv[0] = beta;
+      int jend = -1;
+      for (int j = 0; j < m; ++j) {
+        double *vj = wk.V + (size_t)j * wk.ldv;
+        cta_apply<NT>(it, wk.fval, vj, wk.tmp, wk.z);
+        cta_spmv<NT>(it, wk.z, wk.w, nullptr);
+        double hval = cta_dot<NT>(n, wk.w, nullptr, 0.0, false, wk.V, sh, false);
+        if (threadIdx.x == 0) H[0 * m + j] = hval;
+        for (int i = 0; i <= j; ++i) {
+          const double *vi = wk.V + (size_t)i * wk.ldv;
+          const double *vn = (i < j) ? wk.V + (size_t)(i + 1) * wk.ldv : nullptr;
+          hval = cta_dot<NT>(n, wk.w, vi, hval, true, vn, sh, i == j);
+          if (threadIdx.x == 0) H[(i + 1) * m + j] = hval;
+        }
+        const double hn = hval;
+        cta_vec_div<NT>(n, wk.w, hn, wk.V + (size_t)(j + 1) * wk.ldv);
+        if (threadIdx.x == 0) {
+          s_stop = 0;
+          for (int i = 0; i < j; ++i) {
+            const double a = H[i * m + j], c = H[(i + 1) * m + j];
+            const double t1 = __dmul_rn(cs[i], a), t2 = __dmul_rn(sn[i], c);
+            const double t3 = __dmul_rn(sn[i], a), t4 = __dmul_rn(cs[i], c);
+            H[i * m + j] = __dadd_rn(t1, t2);
+            H[(i + 1) * m + j] = __dsub_rn(t4, t3);
+          }
+          const double a = H[j * m + j], c = H[(j + 1) * m + j];
+          const double rr = __dsqrt_rn(__dadd_rn(__dmul_rn(a, a), __dmul_rn(c, c)));
+          if (rr == 0.0) {
+            s_stop = 2;
+          } else {
+            cs[j] = __ddiv_rn(a, rr);
+            sn[j] = __ddiv_rn(c, rr);
+            H[j * m + j] = rr;
+            H[(j + 1) * m + j] = 0.0;
+            gv[j + 1] = -__dmul_rn(sn[j], gv[j]);
+            gv[j] = __dmul_rn(cs[j], gv[j]);
+            const bool conv = __ddiv_rn(fabs(gv[j + 1]), bnorm) <= rtol;
+            if (conv || iters + 1 >= maxit || hn == 0.0) s_stop = 1;
+          }
+        }
+        __syncthreads();
+        if (s_stop == 2) break;
+        ++iters;
+        jend = j;
+        if (s_stop == 1) break;
+      }
+      if (s_stop == 2) { status = ILUK_EINVAL; break; }
+      if (threadIdx.x == 0) {
+        for (int i = jend; i >= 0; --i) {
+          double sacc = gv[i];
+          for (int l = i + 1; l <= jend; ++l) sacc = __dsub_rn(sacc, __dmul_rn(H[i * m + l], yv[l]));
+          yv[i] = __ddiv_rn(sacc, H[i * m + i]);
+        }
+      }
+      __syncthreads();
+      for (int64_t q = threadIdx.x; q < n; q += NT) {
+        double sacc = 0.0;
+        for (int jj = 0; jj <= jend; ++jj)
+          sacc = __dadd_rn(sacc, __dmul_rn(yv[jj], wk.V[(size_t)jj * wk.ldv + q]));
+        wk.u[q] = sacc;
+      }
+      __syncthreads();
+      cta_apply<NT>(it, wk.fval, wk.u, wk.tmp, wk.z);
+      for (int64_t i = threadIdx.x; i < n; i += NT) it.x[i] = __dadd_rn(it.x[i], wk.z[i]);
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      res->status = status;
+      res->iters = iters;
+      res->cycles = cycles;
+      res->relres = relres;
+    }
+    __syncthreads();
+  }
+}
+
+size_t batch_smem_bytes(int nt, int cap) {
+  return (size_t)kDotP * 8 + (size_t)(nt / 32) * cap * 12;
+}
+
+int batch_max_restart() { return kBMaxRestart; }
+
+template <int NT>
+static cudaError_t launch_bs(const void *items, int64_t nitems, void *results, void *work,
+                             int64_t nwork, unsigned long long *ticket, int m, double rtol,
+                             int maxit, int cap, cudaStream_t s) {
+  const size_t smem = batch_smem_bytes(NT, cap);
+  cudaError_t e = cudaFuncSetAttribute(k_batch_solve<NT>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_batch_solve<NT><<<(unsigned)nwork, NT, smem, s>>>(
+      (const BatchItemDev *)items, nitems, (BatchResultDev *)results, (BatchWork *)work, ticket, m,
+      rtol, maxit, cap);
+  note_launch();
+  return cudaGetLastError();
+}
+
+// nt = threads per instance (512 or 1024); nwork CTAs (<= the work slots).
+cudaError_t launch_batch_solve(int nt, const void *items, int64_t nitems, void *results,
+                               void *work, int64_t nwork, unsigned long long *ticket, int m,
+                               double rtol, int maxit, int cap, cudaStream_t s) {
+  ProfScope prof_scope(ILUK_PROF_BATCH, s);
+  cudaError_t e = cudaMemsetAsync(ticket, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  if (nt == 512)
+    return launch_bs<512>(items, nitems, results, work, nwork, ticket, m, rtol, maxit, cap, s);
+  return launch_bs<1024>(items, nitems, results, work, nwork, ticket, m, rtol, maxit, cap, s);
+}
+
+size_t batch_item_bytes() { return sizeof(BatchItemDev); }
+size_t batch_result_bytes() { return sizeof(BatchResultDev); }
+size_t batch_work_bytes() { return sizeof(BatchWork); }
+
+// Host-side packing of descriptors (layouts are private to this file).
+void batch_pack_item(void *dst, const iluk_sym *S, const int64_t *arp, const int32_t *aci,
+                     const double *aval, const double *b, double *x) {
+  BatchItemDev d;
+  d.n = S->n;
+  d.nnzA = S->nnzA;
+  d.nnzF = S->nnz;
+  d.arp = arp;
+  d.aci = aci;
+  d.aval = aval;
+  d.frp = S->rowptr;
+  d.fci = S->colind;
+  d.fdiag = S->diag;
+  d.farp = S->arowptr;
+  d.a2f = S->a2f;
+  d.lord = S->lord.order;
+  d.lstart = S->lord.lstart;
+  d.nlev_l = S->lord.nlev;
+  d.uord = S->uord.order;
+  d.ustart = S->uord.lstart;
+  d.nlev_u = S->uord.nlev;
+  d.b = b;
+  d.x = x;
+  *reinterpret_cast<BatchItemDev *>(dst) = d;
+}
+
+void batch_pack_work(void *dst, double *fval, double *V, double *w, double *z, double *u,
+                     double *tmp, int64_t ldv) {
+  BatchWork d{fval, V, w, z, u, tmp, ldv};
+  *reinterpret_cast<BatchWork *>(dst) = d;
+}
+
+void batch_unpack_result(const void *src, int32_t *status, int32_t *iters, int32_t *cycles,
+                         int64_t *row, double *relres) {
+  const BatchResultDev &r = *reinterpret_cast<const BatchResultDev *>(src);
+  *status = r.status;
+  *iters = r.iters;
+  *cycles = r.cycles;
+  *row = r.row;
+  *relres = r.relres;
+}
+
+}  // namespace iluk

@@ -242,6 +242,8 @@ void iluk_sym_destroy(iluk_sym *S) {
   dfree(S->a2f, s);
   dfree(S->lord.order, s);
   dfree(S->uord.order, s);
+  dfree(S->lord.lstart, s);
+  dfree(S->uord.lstart, s);
   delete S;
 }
 
@@ -433,6 +435,8 @@ void iluk_fac_destroy(iluk_fac *F) {
   dfree(F->tval, s);
   dfree(F->tlord.order, s);
   dfree(F->tuord.order, s);
+  dfree(F->tlord.lstart, s);
+  dfree(F->tuord.lstart, s);
   delete F;
 }
 
@@ -735,6 +739,173 @@ int iluk_numeric_batched(const iluk_sym *S, int64_t nbatch, const double *A_vals
       std::memset(&infos[b], 0, sizeof(iluk_info));
       infos[b].status = st;
       infos[b].row = st == ILUK_OK ? -1 : (int64_t)(h[b].key >> 8);
+    }
+    if (first == ILUK_OK && st != ILUK_OK) first = st;
+  }
+  return first;
+}
+
+// ---------------------------------------------------------------------------
+// Batched persistent solve
+// ---------------------------------------------------------------------------
+}  // extern "C"
+
+struct iluk_batch {
+  int64_t nitems = 0;
+  int restart = 30, maxit = 10000, cap = 32, width = 0;
+  double rtol = 1e-8;
+  int64_t nwork = 0;  // work slots (CTAs of the widest grid)
+  void *items = nullptr, *results = nullptr, *work = nullptr;
+  unsigned long long *ticket = nullptr;
+  std::vector<double *> bufs;
+};
+
+extern "C" {
+
+void iluk_batch_destroy(iluk_batch *B) {
+  if (!B) return;
+  cudaStream_t s = 0;
+  for (auto p : B->bufs) cudaFreeAsync(p, s);
+  if (B->items) cudaFreeAsync(B->items, s);
+  if (B->results) cudaFreeAsync(B->results, s);
+  if (B->work) cudaFreeAsync(B->work, s);
+  if (B->ticket) cudaFreeAsync(B->ticket, s);
+  delete B;
+}
+
+int iluk_batch_create(const iluk_batch_item *items, int64_t nitems, int restart, double rtol,
+                      int maxit, iluk_batch **out, void *stream) {
+  iluk_info *info = nullptr;
+  if (!out || nitems < 0 || (nitems > 0 && !items) || restart < 1 ||
+      restart > batch_max_restart() || maxit < 0)
+    return ILUK_EINVAL;
+  *out = nullptr;
+  cudaStream_t s = (cudaStream_t)stream;
+  iluk_batch *B = new iluk_batch();
+  B->nitems = nitems;
+  B->restart = restart;
+  B->rtol = rtol;
+  B->maxit = maxit;
+  int64_t maxn = 1, maxf = 1;
+  int maxrow = 1;
+  std::vector<unsigned char> hitems(batch_item_bytes() * (nitems ? nitems : 1));
+  for (int64_t i = 0; i < nitems; ++i) {
+    const iluk_batch_item &it = items[i];
+    if (!it.S || !it.a_rowptr || !it.b || !it.x || (it.S->nnzA && (!it.a_colind || !it.a_val))) {
+      delete B;
+      return ILUK_EINVAL;
+    }
+    batch_pack_item(hitems.data() + i * batch_item_bytes(), it.S, it.a_rowptr, it.a_colind,
+                    it.a_val, it.b, it.x);
+    if (it.S->n > maxn) maxn = it.S->n;
+    if (it.S->nnz > maxf) maxf = it.S->nnz;
+    if (it.S->max_row > maxrow) maxrow = it.S->max_row;
+  }
+  B->cap = (maxrow + 31) & ~31;
+  if (batch_smem_bytes(1024, B->cap) + 40 * 1024 > (size_t)max_smem_optin()) {
+    delete B;
+    return ILUK_ENOMEM;  // a row of F too long for the per-warp slices
+  }
+  // Work slots: enough for the widest grid (two 512-thread CTAs per SM).
+  B->nwork = 2 * (int64_t)num_sms();
+  const int64_t ldv = maxn;
+  auto cleanup = [&]() { iluk_batch_destroy(B); };
+  if (dalloc((unsigned char **)&B->items, hitems.size(), s) != cudaSuccess ||
+      dalloc((unsigned char **)&B->results, batch_result_bytes() * (nitems ? nitems : 1), s) !=
+          cudaSuccess ||
+      dalloc((unsigned char **)&B->work, batch_work_bytes() * B->nwork, s) != cudaSuccess ||
+      dalloc(&B->ticket, 1, s) != cudaSuccess) {
+    cleanup();
+    return ILUK_ENOMEM;
+  }
+  std::vector<unsigned char> hwork(batch_work_bytes() * B->nwork);
+  for (int64_t w = 0; w < B->nwork; ++w) {
+    double *fval, *V, *vw, *z, *u, *tmp;
+    if (dalloc(&fval, maxf, s) != cudaSuccess || (B->bufs.push_back(fval), false) ||
+        dalloc(&V, (size_t)ldv * (restart + 1), s) != cudaSuccess ||
+        (B->bufs.push_back(V), false) || dalloc(&vw, ldv, s) != cudaSuccess ||
+        (B->bufs.push_back(vw), false) || dalloc(&z, ldv, s) != cudaSuccess ||
+        (B->bufs.push_back(z), false) || dalloc(&u, ldv, s) != cudaSuccess ||
+        (B->bufs.push_back(u), false) || dalloc(&tmp, ldv, s) != cudaSuccess) {
+      cleanup();
+      return ILUK_ENOMEM;
+    }
+    B->bufs.push_back(tmp);
+    batch_pack_work(hwork.data() + w * batch_work_bytes(), fval, V, vw, z, u, tmp, ldv);
+  }
+  CK(cudaMemcpyAsync(B->items, hitems.data(), hitems.size(), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(B->work, hwork.data(), hwork.size(), cudaMemcpyHostToDevice, s));
+  CK(cudaStreamSynchronize(s));
+  *out = B;
+  return ILUK_OK;
+}
+
+static cudaError_t batch_launch(iluk_batch *B, int width, cudaStream_t s) {
+  const int64_t grid = (width == 512 ? 2 : 1) * (int64_t)num_sms();
+  return launch_batch_solve(width, B->items, B->nitems, B->results, B->work, grid, B->ticket,
+                            B->restart, B->rtol, B->maxit, B->cap, s);
+}
+
+int iluk_batch_solve(iluk_batch *B, void *stream) {
+  iluk_info *info = nullptr;
+  if (!B) return ILUK_EINVAL;
+  if (B->nitems == 0) return ILUK_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (B->width == 0) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(s, &cs);
+    if (cs != cudaStreamCaptureStatusNone) {
+      B->width = 1024;
+    } else {
+      // Autotuner: run the whole batch at both widths, keep the faster.
+      cudaEvent_t e0, e1;
+      cudaEventCreate(&e0);
+      cudaEventCreate(&e1);
+      float best = 1e30f;
+      for (int w : {512, 1024}) {
+        cudaEventRecord(e0, s);
+        CK(batch_launch(B, w, s));
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+          best = ms;
+          B->width = w;
+        }
+      }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return ILUK_OK;  // results do not depend on the width: the last run holds them
+    }
+  }
+  CK(batch_launch(B, B->width, s));
+  return ILUK_OK;
+}
+
+int iluk_batch_width(const iluk_batch *B) { return B ? B->width : 0; }
+
+int iluk_batch_results(iluk_batch *B, iluk_info *infos, void *stream) {
+  iluk_info *info = nullptr;
+  if (!B) return ILUK_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<unsigned char> h(batch_result_bytes() * (B->nitems ? B->nitems : 1));
+  CK(cudaMemcpyAsync(h.data(), B->results, batch_result_bytes() * B->nitems,
+                     cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  int first = ILUK_OK;
+  for (int64_t i = 0; i < B->nitems; ++i) {
+    int32_t st, it, cyc;
+    int64_t row;
+    double rel;
+    batch_unpack_result(h.data() + i * batch_result_bytes(), &st, &it, &cyc, &row, &rel);
+    if (infos) {
+      std::memset(&infos[i], 0, sizeof(iluk_info));
+      infos[i].status = st;
+      infos[i].iters = it;
+      infos[i].cycles = cyc;
+      infos[i].row = row;
+      infos[i].relres = rel;
     }
     if (first == ILUK_OK && st != ILUK_OK) first = st;
   }

@@ -10,6 +10,7 @@
 // multiple of 32 entries (see levels.cu).
 struct LevelOrder {
   int32_t *order = nullptr;
+  int64_t *lstart = nullptr;  // int64[nlev+1]: first slot of each level
   int64_t len = 0;
   int32_t nlev = 0;
 };
@@ -147,5 +148,21 @@ cudaError_t launch_add(int64_t n, double *x, const double *z, cudaStream_t s);
 cudaError_t launch_adjoint_scatter(int64_t n, const int64_t *rp, const int32_t *ci,
                                    const double *lam, const double *x, double *gA,
                                    cudaStream_t s);
+
+// Batched persistent solve (batched.cu)
+size_t batch_item_bytes();
+size_t batch_result_bytes();
+size_t batch_work_bytes();
+size_t batch_smem_bytes(int nt, int cap);
+int batch_max_restart();
+void batch_pack_item(void *dst, const iluk_sym *S, const int64_t *arp, const int32_t *aci,
+                     const double *aval, const double *b, double *x);
+void batch_pack_work(void *dst, double *fval, double *V, double *w, double *z, double *u,
+                     double *tmp, int64_t ldv);
+void batch_unpack_result(const void *src, int32_t *status, int32_t *iters, int32_t *cycles,
+                         int64_t *row, double *relres);
+cudaError_t launch_batch_solve(int nt, const void *items, int64_t nitems, void *results,
+                               void *work, int64_t nwork, unsigned long long *ticket, int m,
+                               double rtol, int maxit, int cap, cudaStream_t s);
 
 }  // namespace iluk

@@ -124,7 +124,6 @@ int build_levels(int64_t n, const int64_t *rp, const int32_t *ci, const int64_t 
     if (mx) cudaFreeAsync(mx, s);
     if (cnt) cudaFreeAsync(cnt, s);
     if (cursor) cudaFreeAsync(cursor, s);
-    if (lstart) cudaFreeAsync(lstart, s);
     if (scan_tmp) cudaFreeAsync(scan_tmp, s);
     if (err) cudaFreeAsync(err, s);
   };
@@ -132,6 +131,7 @@ int build_levels(int64_t n, const int64_t *rp, const int32_t *ci, const int64_t 
   do {                                         \
     if ((call) != cudaSuccess) {               \
       cleanup();                               \
+      if (lstart) cudaFreeAsync(lstart, s);    \
       return ILUK_ECUDA;                       \
     }                                          \
   } while (0)
@@ -177,6 +177,7 @@ int build_levels(int64_t n, const int64_t *rp, const int32_t *ci, const int64_t 
   CKL(cudaGetLastError());
 #undef CKL
   cleanup();
+  lo->lstart = lstart;
   lo->len = len;
   lo->nlev = nlev;
   return st;

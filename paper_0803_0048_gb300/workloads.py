@@ -194,11 +194,12 @@ def fd_values(P: FDPattern, theta: Optional[torch.Tensor], beta: Sequence[float]
             raise ValueError("upwind assembly here expects beta >= 0")
     if theta is None:
         theta = torch.ones(n, dtype=torch.float64)
-    idx = torch.arange(n, dtype=torch.int64)
+    dev = theta.device
+    idx = torch.arange(n, dtype=torch.int64, device=dev)
     nnz = int(P.rowptr[-1])
-    slot = torch.from_numpy(P.slot)
-    diag = torch.zeros(n, dtype=torch.float64)
-    val = torch.zeros(nnz, dtype=torch.float64)
+    slot = torch.from_numpy(P.slot).to(dev)
+    diag = torch.zeros(n, dtype=torch.float64, device=dev)
+    val = torch.zeros(nnz, dtype=torch.float64, device=dev)
     for c in range(d):
         stride = N ** c
         coord = (idx // stride) % N
