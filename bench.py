@@ -47,6 +47,11 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-steps", type=int, default=2, help="oracle steps for cpu_baseline")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--workload", default="band", choices=["band", "batched", "adjoint"],
+                    help="band: the n=160,000 headline; batched: 512 value sets on 32^3 plus "
+                         "64 uneven grids in one launch; adjoint: 256^2 differentiable solve")
+    ap.add_argument("--nsets", type=int, default=512)
+    ap.add_argument("--ngrids", type=int, default=64)
     return ap.parse_args()
 
 
@@ -337,10 +342,145 @@ def reference(args):
     print(json.dumps(out), flush=True)
 
 
+def batched(args):
+    """512 value sets on one 32^3 7-point pattern + 64 uneven grids 16^3-40^3,
+    ILU(1) factor + GMRES(30) to 1e-8, all in one persistent launch; against
+    looping the single-instance path (iluk_numeric + gmres_solve) over the same
+    items on the same GPU."""
+    import torch
+
+    import paper_0803_0048_gb300 as P
+    from paper_0803_0048_gb300 import workloads as W
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    A0, vals, bs, _ = W.batched_values(args.nsets, 32)
+    grids = W.uneven_grids(args.ngrids)
+    rp = torch.from_numpy(A0.rowptr).to(dev)
+    ci = torch.from_numpy(A0.colind).to(dev)
+    S0 = P.symbolic(rp, ci, 1)
+    items, plain = [], []
+    for sidx in range(args.nsets):
+        v = torch.from_numpy(vals[sidx]).to(dev)
+        b = torch.from_numpy(bs[sidx]).to(dev)
+        items.append((S0, v, b, torch.empty(A0.n, dtype=torch.float64, device=dev)))
+        plain.append((S0, rp, ci, v, b))
+    for g in grids:
+        r = torch.from_numpy(g.A.rowptr).to(dev)
+        c = torch.from_numpy(g.A.colind).to(dev)
+        S = P.symbolic(r, c, 1)
+        v = torch.from_numpy(g.A.val).to(dev)
+        b = torch.from_numpy(g.b).to(dev)
+        items.append((S, v, b, torch.empty(g.A.n, dtype=torch.float64, device=dev)))
+        plain.append((S, r, c, v, b))
+    B = P.BatchSolve(items, restart=30, rtol=1e-8)
+    for _ in range(max(args.warmup, 1)):
+        B.solve()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clk:
+        ev0.record()
+        for _ in range(args.steps):
+            B.solve()
+        ev1.record()
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    res = B.results()
+    # the same items, one at a time through the single-instance path
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record()
+    mism = 0
+    for (S, r, c, v, b), (_, _, _, xb), rr in zip(plain, items, res):
+        F = P.numeric(S, v)
+        x, info = P.gmres(r, c, v, b, F, restart=30, rtol=1e-8, check=False)
+        mism += int((x.view(torch.int64) != xb.view(torch.int64)).sum().item())
+        mism += int(info.iters != rr.iters)
+    t1.record()
+    torch.cuda.synchronize()
+    loop_ms = t0.elapsed_time(t1)
+    out = {"metric": METRIC, "value": round(ms, 3), "unit": "ms", "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
+           "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": f"batched_{args.nsets}x32^3_plus_{args.ngrids}_uneven_k1_gmres30",
+                      "items": len(items), "width": B.width()},
+           "loop_single_path_ms": round(loop_ms, 3),
+           "speedup_vs_loop": round(loop_ms / ms, 2),
+           "bit_mismatches_vs_single": mism,
+           "max_iters": max(r.iters for r in res),
+           "all_converged": all(r.status == 0 for r in res),
+           "clocks": clk.summary()}
+    print(json.dumps(out), flush=True)
+
+
+def adjoint(args):
+    """2D 256^2 diffusion-convection with per-cell theta: x = A(theta)^-1 b by
+    ILU(2)-GMRES(30), L = ||x - x_t||^2, dL/dtheta and dL/db by the adjoint."""
+    import torch
+
+    import paper_0803_0048_gb300 as P
+    from paper_0803_0048_gb300 import workloads as W
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    Pt, theta, beta, b, xt = W.adjoint_problem(256)
+    rp = torch.from_numpy(Pt.rowptr).to(dev)
+    ci = torch.from_numpy(Pt.colind).to(dev)
+    solver = P.IlukSolver(rp, ci, k=2, restart=30, rtol=1e-8)
+    bd = torch.from_numpy(b).to(dev)
+    xtd = torch.from_numpy(xt).to(dev)
+    th0 = torch.from_numpy(theta).to(dev)
+
+    def fwd_bwd():
+        th = th0.clone().requires_grad_(True)
+        bb = bd.clone().requires_grad_(True)
+        x = solver.solve(W.fd_values(Pt, th, beta), bb)
+        L = ((x - xtd) ** 2).sum()
+        L.backward()
+        return th.grad, bb.grad
+
+    def fwd_only():
+        with torch.no_grad():
+            return solver.solve(W.fd_values(Pt, th0, beta), bd)
+
+    for _ in range(max(args.warmup, 1)):
+        fwd_bwd()
+        fwd_only()
+    torch.cuda.synchronize()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    e[0].record()
+    for _ in range(args.steps):
+        fwd_bwd()
+    e[1].record()
+    for _ in range(args.steps):
+        fwd_only()
+    e[2].record()
+    torch.cuda.synchronize()
+    ms_fb = e[0].elapsed_time(e[1]) / args.steps
+    ms_f = e[1].elapsed_time(e[2]) / args.steps
+    n_theta = Pt.n
+    out = {"metric": METRIC, "value": round(ms_fb, 3), "unit": "ms", "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_fb, 3),
+           "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": "adjoint_2d_256^2_k2_gmres30", "n": Pt.n,
+                      "n_theta": n_theta},
+           "forward_only_ms": round(ms_f, 3),
+           "backward_over_forward": round((ms_fb - ms_f) / ms_f, 3),
+           "forward_iters": solver.last_forward.iters,
+           "adjoint_iters": solver.last_backward.iters if solver.last_backward else None,
+           "loop_plain_gradient_ms_estimate": round(2 * n_theta * ms_f, 1),
+           "speedup_vs_loop": round(2 * n_theta * ms_f / ms_fb, 1)}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         reference(args)
+    elif args.workload == "batched":
+        batched(args)
+    elif args.workload == "adjoint":
+        adjoint(args)
     else:
         ours(args)
 
