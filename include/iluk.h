@@ -218,6 +218,26 @@ int iiluk_values(const iiluk *M, const double **g);
 /* Copy g into a caller-owned device buffer double[nnz_F].  Asynchronous. */
 int iiluk_export(const iiluk *M, double *g, void *stream);
 int iiluk_apply(const iiluk *M, const double *p, double *y, void *stream);
+
+/*
+ * The same TPIILU apply for callers that cannot allocate device memory (their
+ * memory belongs to another runtime or a fixed pool, or allocation is not
+ * allowed where they run).  Not from the paper, which has no counterpart: an
+ * interface addition.  The caller passes F's pattern (rowptr int64[n+1],
+ * colind int32[nnz], diag int64[n], as exported by iluk_sym_export), the
+ * TPIILU values g (double[nnz], as exported by iiluk_export), p and y (device
+ * double[n]); the result is bit-identical to iiluk_apply.  The intermediate
+ * vector lives in a static device array of ILUK_NOALLOC_MAX_N doubles (8 MiB)
+ * that every device loading the library keeps until exit; n above that limit
+ * returns ILUK_ENOMEM.  The call allocates nothing.  The first call on a
+ * device looks up the array's device address (make it before any stream
+ * capture).  All calls share the one array: calls that overlap on the GPU
+ * (other streams, or other host threads) race on it.  Asynchronous.
+ */
+#define ILUK_NOALLOC_MAX_N (1 << 20)
+int iiluk_apply_noalloc(int64_t n, const int64_t *rowptr, const int32_t *colind,
+                        const int64_t *diag, const double *g, const double *p, double *y,
+                        void *stream);
 void iiluk_destroy(iiluk *M);
 
 /*

@@ -73,6 +73,7 @@ SIGNATURES = [
     ("iiluk_values", I, [P, PP]),
     ("iiluk_export", I, [P, P, P]),
     ("iiluk_apply", I, [P, P, P, P]),
+    ("iiluk_apply_noalloc", I, [I64, P, P, P, P, P, P, P]),
     ("iiluk_destroy", None, [P]),
     ("iluk_spmv", I, [P, P, P, P, P]),
     ("iluk_dot", I, [I64, P, P, P, P]),

@@ -15,6 +15,8 @@
 // Apply: z_i = (sum_{t<i} g_it p_t + p_i) / u_ii, then
 // y_i = sum_{t>i} g_it z_t + z_i; each sum runs left to right starting from
 // its first product, the own term added last (Eq. forwardsubB).
+#include <mutex>
+
 #include "internal.h"
 
 namespace iluk {
@@ -228,3 +230,54 @@ cudaError_t launch_iiluk_apply(const iluk_sym *S, const double *g, const double 
 }
 
 }  // namespace iluk
+
+// ---------------------------------------------------------------------------
+// iiluk_apply_noalloc: the TPIILU apply for callers that cannot allocate device
+// memory -- code whose memory belongs to another runtime or a pre-sized pool,
+// or a solve loop where allocation is not allowed.  The caller passes every
+// input and output; the intermediate vector between the two mat-vecs lives
+// in this file-scope array instead of a cudaMalloc'd buffer.  Every device
+// that loads the library holds the array (ILUK_NOALLOC_MAX_N doubles) until
+// the process exits.
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) double g_noalloc_z[ILUK_NOALLOC_MAX_N];
+
+namespace {
+std::mutex g_noalloc_mu;
+double *g_noalloc_ptr[64] = {};  // device address of g_noalloc_z, per device
+}  // namespace
+
+extern "C" int iiluk_apply_noalloc(int64_t n, const int64_t *rowptr, const int32_t *colind,
+                                   const int64_t *diag, const double *g, const double *p,
+                                   double *y, void *stream) {
+  using namespace iluk;
+  if (n < 0 || (n > 0 && (!rowptr || !colind || !diag || !g || !p || !y))) return ILUK_EINVAL;
+  if (n > ILUK_NOALLOC_MAX_N) return ILUK_ENOMEM;  // larger than the static scratch
+  if (n == 0) return ILUK_OK;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return ILUK_ECUDA;
+  double *z = nullptr;
+  {
+    // Set-up, once per device, with that device current: the host-side name
+    // of the array is only a stand-in, so ask the runtime for its address.
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+      double *ptr = nullptr;
+      if (cudaGetSymbolAddress((void **)&ptr, g_noalloc_z) != cudaSuccess || !ptr)
+        return ILUK_ECUDA;
+      g_noalloc_ptr[dev] = ptr;
+    }
+    z = g_noalloc_ptr[dev];
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  int64_t blocks = (n * 32 + 255) / 256;
+  const int64_t cap = (int64_t)num_sms() * 8;
+  if (blocks > cap) blocks = cap;
+  // The lower pass writes every z_i before the upper pass reads it, so the
+  // array needs no clearing between calls.
+  k_iiluk_apply<true><<<(unsigned)blocks, 256, 0, s>>>(n, rowptr, colind, diag, g, p, z);
+  note_launch();
+  k_iiluk_apply<false><<<(unsigned)blocks, 256, 0, s>>>(n, rowptr, colind, diag, g, z, y);
+  note_launch();
+  return cudaGetLastError() == cudaSuccess ? ILUK_OK : ILUK_ECUDA;
+}
