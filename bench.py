@@ -35,6 +35,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "ILU(k) factor+apply ms & HBM GB/s (% peak); batched/adjoint vs plain, 1e-8 res"
+SCHED_NAMES = ["auto", "lockstep_grid", "lockstep_cta", "lockstep_cluster", "warp_grid",
+               "warp_cluster"]
 L2_BYTES = 129 * 1024 * 1024
 
 
@@ -236,7 +238,8 @@ def ours(args):
     depth = S.depth()
     ab = alg_bytes(n, nnzA, nnzF, nnzL)
     hbm, peak_src = measured_peaks()
-    kinds = {"numeric": "numeric", "symbolic": "symbolic", "sweep": "sweep", "spmv": "spmv"}
+    kinds = {"numeric": "numeric", "symbolic": "symbolic", "sweep": "sweep", "sweep_bwd": "sweep",
+             "spmv": "spmv"}
     per_kind = {}
     for kname, (tot_ms, cnt) in prof.items():
         if cnt:
@@ -245,7 +248,7 @@ def ours(args):
                                "ms_per_launch": tot_ms / cnt}
     dom = max((k for k in per_kind if k in kinds), key=lambda k: per_kind[k]["ms_total_per_step"])
     dur_s = per_kind[dom]["ms_per_launch"] / 1e3
-    achieved = ab[dom] / dur_s / 1e9
+    achieved = ab[kinds[dom]] / dur_s / 1e9
     traffic = None
     tpath = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tpath):
@@ -264,13 +267,14 @@ def ours(args):
                    "parallelism": "replicas" if world > 1 else "single"},
         "roofline": {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 3), "peak": hbm,
                      "unit": "GB/s", "frac": round(achieved / hbm, 6), "traffic": traffic,
-                     "alg_bytes_per_launch": ab[dom], "peak_source": peak_src},
+                     "alg_bytes_per_launch": ab[kinds[dom]], "peak_source": peak_src},
         "e2e": {"value": round(ms_e2e, 4), "unit": "ms", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
-        "gmres": {"iters": info.iters, "relres": info.relres, "sched": ["auto", "flags",
-                  "single_cta"][sched[0]]},
+        "gmres": {"iters": info.iters, "relres": info.relres,
+                  "sweep_schedule": {"forward": SCHED_NAMES[sched[0] & 0xff],
+                                     "backward": SCHED_NAMES[(sched[0] >> 8) & 0xff]}},
         "kernels": per_kind,
     }
 

@@ -101,7 +101,14 @@ typedef struct iluk_fac iluk_fac;  /* numeric factors L~, U~ on that pattern   *
 typedef struct iiluk iiluk;        /* TPIILU incomplete inverses              */
 
 enum { ILUK_PREC_NONE = 0, ILUK_PREC_ILU = 1, ILUK_PREC_IILU = 2 };
-enum { ILUK_SCHED_AUTO = 0, ILUK_SCHED_FLAGS = 1, ILUK_SCHED_SINGLE_CTA = 2 };
+/* Sweep schedules (all give bit-identical results): rows of a level in
+ * lockstep warps over all SMs (FLAGS), on one SM (SINGLE_CTA) or on one
+ * thread-block cluster (CLUSTER); one warp per row over all SMs (WARP_GRID)
+ * or on one cluster (WARP_CLUSTER).  AUTO times them and keeps the fastest. */
+enum {
+  ILUK_SCHED_AUTO = 0, ILUK_SCHED_FLAGS = 1, ILUK_SCHED_SINGLE_CTA = 2, ILUK_SCHED_CLUSTER = 3,
+  ILUK_SCHED_WARP_GRID = 4, ILUK_SCHED_WARP_CLUSTER = 5
+};
 
 const char *iluk_strerror(int status);
 
@@ -197,8 +204,10 @@ void iluk_fac_destroy(iluk_fac *F);
 int iluk_apply(iluk_fac *F, const double *p, double *y, int transpose, void *stream);
 int iluk_apply_sched(iluk_fac *F, const double *p, double *y, int transpose, int sched,
                      void *stream);
-/* Fix the sweep schedule of F (ILUK_SCHED_AUTO lets the first application
- * outside a stream capture time both schedules and keep the faster one). */
+/* Fix the sweep schedule of F: one ILUK_SCHED_* value for both sweeps, or
+ * forward | backward << 8.  ILUK_SCHED_AUTO (the default) lets the first
+ * application outside a stream capture time every schedule on each sweep and
+ * keep the fastest (iluk_get_schedule then returns the packed pair). */
 int iluk_set_schedule(iluk_fac *F, int sched);
 int iluk_get_schedule(const iluk_fac *F);
 

@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libiluk.so")
 
 OK, EINVAL, EPATTERN, ENODIAG, EZEROPIVOT, ENONFINITE, ENOMEM, ETIMEOUT, ENOCONV, ECUDA = range(10)
 PREC_NONE, PREC_ILU, PREC_IILU = 0, 1, 2
-SCHED_AUTO, SCHED_FLAGS, SCHED_SINGLE_CTA = 0, 1, 2
+SCHED_AUTO, SCHED_FLAGS, SCHED_SINGLE_CTA, SCHED_CLUSTER, SCHED_WARP_GRID, SCHED_WARP_CLUSTER = 0, 1, 2, 3, 4, 5
 PROF_KINDS = ["validate", "symbolic", "compact", "depth", "numeric", "sweep", "transpose",
               "iilu_build", "iilu_apply", "spmv", "dot", "vector", "sweep_bwd", "batch"]
 

@@ -542,48 +542,71 @@ static int ensure_transpose(iluk_fac *F, cudaStream_t s) {
   return ILUK_OK;
 }
 
-// Autotuner: time both sweep schedules once on this factorization and keep
-// the faster one (skipped while the stream is being captured).
+// Autotuner: time every sweep schedule once on this factorization, forward
+// and backward sweeps separately, and keep the fastest of each (packed as
+// forward | backward << 8).  Skipped while the stream is being captured.
 static int pick_schedule(iluk_fac *F, cudaStream_t s) {
   if (F->sched != ILUK_SCHED_AUTO) return F->sched;
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   cudaStreamIsCapturing(s, &cs);
-  if (cs != cudaStreamCaptureStatusNone) return ILUK_SCHED_FLAGS;
+  if (cs != cudaStreamCaptureStatusNone) return ILUK_SCHED_WARP_GRID;
   const iluk_sym *S = F->S;
   double *p = nullptr, *y = nullptr;
   if (dalloc(&p, S->n, s) != cudaSuccess || dalloc(&y, S->n, s) != cudaSuccess) {
     dfree(p, s);
-    return ILUK_SCHED_FLAGS;
+    return ILUK_SCHED_WARP_GRID;
   }
   cudaMemsetAsync(p, 0, S->n * sizeof(double), s);
-  float best = 1e30f;
-  int pick = ILUK_SCHED_FLAGS;
-  cudaEvent_t e0, e1;
+  float best_f = 1e30f, best_b = 1e30f;
+  int pick_f = ILUK_SCHED_WARP_GRID, pick_b = ILUK_SCHED_WARP_GRID;
+  const bool prof = g_prof.exchange(false);  // the trial runs are not profiled
+  cudaEvent_t e0, e1, e2;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  for (int sched : {ILUK_SCHED_FLAGS, ILUK_SCHED_SINGLE_CTA}) {
-    float ms_min = 1e30f;
+  cudaEventCreate(&e2);
+  for (int sched : {ILUK_SCHED_FLAGS, ILUK_SCHED_SINGLE_CTA, ILUK_SCHED_CLUSTER,
+                    ILUK_SCHED_WARP_GRID, ILUK_SCHED_WARP_CLUSTER}) {
+    float mf = 1e30f, mb = 1e30f;
     for (int rep = 0; rep < 3; ++rep) {
+      // the forward sweep alone, then the backward sweep alone, on the same
+      // level orders the real applies use
+      LevelOrder none;
       cudaEventRecord(e0, s);
-      launch_apply(S->n, S->rowptr, S->colind, S->diag, F->val, S->lord, S->uord, p, F->tmp, y, 0,
+      launch_apply(S->n, S->rowptr, S->colind, S->diag, F->val, S->lord, none, p, F->tmp, y, 0,
                    sched, F->err, s);
       cudaEventRecord(e1, s);
-      cudaEventSynchronize(e1);
-      float ms = 0;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (rep > 0 && ms < ms_min) ms_min = ms;
+      launch_apply(S->n, S->rowptr, S->colind, S->diag, F->val, none, S->uord, p, F->tmp, y, 0,
+                   sched, F->err, s);
+      cudaEventRecord(e2, s);
+      cudaEventSynchronize(e2);
+      float a = 0, b = 0;
+      cudaEventElapsedTime(&a, e0, e1);
+      cudaEventElapsedTime(&b, e1, e2);
+      if (rep > 0) {
+        if (a < mf) mf = a;
+        if (b < mb) mb = b;
+      }
     }
-    if (ms_min < best) {
-      best = ms_min;
-      pick = sched;
+    if (mf < best_f) {
+      best_f = mf;
+      pick_f = sched;
+    }
+    if (mb < best_b) {
+      best_b = mb;
+      pick_b = sched;
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  cudaEventDestroy(e2);
+  // the timing runs may leave tmp partly armed: restore the invariant
+  launch_fill_pending(S->n, F->tmp, s);
+  launch_fill_err(F->err, s);
+  g_prof.store(prof);
   dfree(p, s);
   dfree(y, s);
-  F->sched = pick;
-  return pick;
+  F->sched = pick_f | (pick_b << 8);
+  return F->sched;
 }
 
 int iluk_apply_sched(iluk_fac *F, const double *p, double *y, int transpose, int sched,
@@ -610,7 +633,10 @@ int iluk_apply(iluk_fac *F, const double *p, double *y, int transpose, void *str
 }
 
 int iluk_set_schedule(iluk_fac *F, int sched) {
-  if (!F || sched < 0 || sched > 2) return ILUK_EINVAL;
+  const int sf = sched & 0xff, sb = (sched >> 8) & 0xff;
+  if (!F || sched < 0 || sched > 0xffff || sf > ILUK_SCHED_WARP_CLUSTER ||
+      sb > ILUK_SCHED_WARP_CLUSTER)
+    return ILUK_EINVAL;
   F->sched = sched;
   return ILUK_OK;
 }

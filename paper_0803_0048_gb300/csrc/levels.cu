@@ -52,7 +52,9 @@ k_depth_cta(int64_t n, const int64_t *__restrict__ rp, const int32_t *__restrict
         const uint64_t t0 = globaltimer_ns();
         while (__any_sync(FULL_MASK, v == 0)) {
           if (v == 0) asm volatile("ld.relaxed.cta.global.b32 %0, [%1];" : "=r"(v) : "l"(src));
-          if (*((volatile int *)&sfail) || (int64_t)(globaltimer_ns() - t0) > limit_ns) {
+          const bool stop =
+              *((volatile int *)&sfail) || (int64_t)(globaltimer_ns() - t0) > limit_ns;
+          if (__any_sync(FULL_MASK, stop)) {  // the whole warp gives up together
             ok = false;
             break;
           }

@@ -54,11 +54,50 @@ __device__ __forceinline__ bool wait_vals(const double *p, bool active, double *
       pend = pend_f(*val);
     }
     if (!__any_sync(FULL_MASK, pend)) return true;
-    if ((it & 7u) == 7u &&
-        (earlier_failed(err, row) || (int64_t)(globaltimer_ns() - t0) > limit_ns))
-      return false;
+    const bool stop = (it & 7u) == 7u &&
+                      (earlier_failed(err, row) || (int64_t)(globaltimer_ns() - t0) > limit_ns);
+    if (__any_sync(FULL_MASK, stop)) return false;  // the whole warp gives up together
     __nanosleep(backoff);
-    if (backoff < 256u) backoff <<= 1;
+    if (backoff < 128u) backoff <<= 1;
+  }
+}
+
+// What a warp needs from pivot row h before its values are final: where
+// its first 64 entries j > h fall in the current row (pos, -1 if absent),
+// and loads of those values and of f_hh already issued.
+struct PivotPre {
+  int64_t hd, u1;
+  int pos0, pos1;
+  double piv, f0, f1;
+};
+
+__device__ __forceinline__ void prefetch_pivot(PivotPre &pp, int q, const int32_t *rc, int m,
+                                               const int64_t *__restrict__ fdiag,
+                                               const int64_t *__restrict__ frp,
+                                               const int32_t *__restrict__ fci, const double *fv,
+                                               int lane) {
+  const int h = rc[q];
+  pp.hd = fdiag[h];
+  pp.u1 = frp[h + 1];
+  pp.piv = ld_gpu(&fv[pp.hd]);
+  pp.pos0 = pp.pos1 = -1;
+  pp.f0 = pp.f1 = 0.0;
+  const int64_t r0 = pp.hd + 1 + lane, r1 = r0 + 32;
+  if (r0 < pp.u1) {
+    const int32_t j = fci[r0];
+    const int ps = lower_bound_i(rc, q + 1, m, j);
+    if (ps < m && rc[ps] == j) {
+      pp.pos0 = ps;
+      pp.f0 = ld_gpu(&fv[r0]);
+    }
+  }
+  if (r1 < pp.u1) {
+    const int32_t j = fci[r1];
+    const int ps = lower_bound_i(rc, q + 1, m, j);
+    if (ps < m && rc[ps] == j) {
+      pp.pos1 = ps;
+      pp.f1 = ld_gpu(&fv[r1]);
+    }
   }
 }
 
@@ -119,19 +158,31 @@ k_numeric(int64_t n, int64_t nbatch, const int64_t *__restrict__ arp,
     }
     __syncwarp();
 
+    // Pivots are software-pipelined: while the values of pivot q are awaited,
+    // the pattern work and the value loads of pivot q+1 are already issued.
+    // A prefetch covers the first 64 entries j > h of the pivot row (two per
+    // lane); longer pivot rows finish their tail inline.
     bool ok = true;
+    PivotPre cur, nxt;
+    if (dp > 0) prefetch_pivot(cur, 0, rc, m, fdiag, frp, fci, fv, lane);
     for (int q = 0; q < dp && ok; ++q) {
-      const int h = rc[q];
-      const int64_t hd = fdiag[h];
-      const int64_t u1 = frp[h + 1];
-      double piv = ld_gpu(&fv[hd]);
-      for (int64_t base = hd + 1; base < u1 || base == hd + 1; base += 32) {
-        // pattern work first (static), then the values of row h
+      if (q + 1 < dp) prefetch_pivot(nxt, q + 1, rc, m, fdiag, frp, fci, fv, lane);
+      if (!wait_vals(&fv[cur.hd], true, &cur.piv, err, row, limit_ns) ||
+          !wait_vals(&fv[cur.hd + 1 + lane], cur.pos0 >= 0, &cur.f0, err, row, limit_ns) ||
+          !wait_vals(&fv[cur.hd + 33 + lane], cur.pos1 >= 0, &cur.f1, err, row, limit_ns)) {
+        ok = false;
+        break;
+      }
+      const double fih = __ddiv_rn(rv[q], cur.piv);
+      __syncwarp();
+      if (lane == 0) rv[q] = fih;
+      if (cur.pos0 >= 0) rv[cur.pos0] = sub_prod(rv[cur.pos0], fih, cur.f0);
+      if (cur.pos1 >= 0) rv[cur.pos1] = sub_prod(rv[cur.pos1], fih, cur.f1);
+      for (int64_t base = cur.hd + 65; base < cur.u1; base += 32) {  // long pivot rows
         const int64_t r = base + lane;
-        const bool inr = r < u1;
         int pos = -1;
         double fhj = 0.0;
-        if (inr) {
+        if (r < cur.u1) {
           const int32_t j = fci[r];
           const int ps = lower_bound_i(rc, q + 1, m, j);
           if (ps < m && rc[ps] == j) {
@@ -139,27 +190,14 @@ k_numeric(int64_t n, int64_t nbatch, const int64_t *__restrict__ arp,
             fhj = ld_gpu(&fv[r]);
           }
         }
-        if (base == hd + 1) {
-          if (!wait_vals(&fv[hd], true, &piv, err, row, limit_ns)) {
-            ok = false;
-            break;
-          }
-        }
         if (!wait_vals(&fv[r], pos >= 0, &fhj, err, row, limit_ns)) {
           ok = false;
           break;
         }
-        if (base == hd + 1) {
-          const double fih = __ddiv_rn(rv[q], piv);
-          __syncwarp();
-          if (lane == 0) rv[q] = fih;
-          __syncwarp();
-        }
-        const double fih = rv[q];
         if (pos >= 0) rv[pos] = sub_prod(rv[pos], fih, fhj);
-        if (base + 32 >= u1) break;
       }
       __syncwarp();
+      cur = nxt;
     }
     if (!__all_sync(FULL_MASK, ok)) {
       if (lane == 0 && !earlier_failed(err, row)) set_err(err, row, ILUK_ETIMEOUT);

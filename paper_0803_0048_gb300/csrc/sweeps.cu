@@ -19,6 +19,8 @@
 // The transposed solve (L~U~)^-T p runs the same kernels on an explicit CSR
 // transpose T = F^T: forward with division by t_ii (U~^T), then backward with
 // unit diagonal (L~^T).
+#include <mutex>
+
 #include "internal.h"
 
 namespace iluk {
@@ -127,27 +129,25 @@ k_sweep(const int32_t *__restrict__ order, int64_t len, const int64_t *__restric
         }
       }
       if (__any_sync(FULL_MASK, pend)) {
-        // Wait with little memory traffic: each lane re-reads only its first
-        // pending value per round, and the warp sleeps between rounds, so the
-        // warps that can make progress keep the load pipe.
+        // Re-read every still-pending value each round (they may arrive in any
+        // order), sleeping briefly between rounds so that waiting warps leave
+        // issue slots to the warps that can make progress.
         const uint64_t t0 = globaltimer_ns();
         unsigned backoff = 16;
         for (unsigned it = 0; __any_sync(FULL_MASK, pend); ++it) {
           pend = false;
-          bool polled = false;
 #pragma unroll
           for (int u = 0; u < W; ++u) {
             const int e = q0 + u - off;
             if (e >= 0 && e < mylen && pending(x[u])) {
-              if (!polled) {
-                x[u] = ld_val<GPU_SCOPE>(&out[c[u]]);
-                polled = pending(x[u]);
-              }
+              x[u] = ld_val<GPU_SCOPE>(&out[c[u]]);
               pend |= pending(x[u]);
             }
           }
-          if ((it & 15u) == 15u &&
-              (any_failed(err) || (int64_t)(globaltimer_ns() - t0) > limit_ns)) {
+          // the decision to give up is taken by the whole warp at once
+          const bool stop = (it & 15u) == 15u &&
+                            (any_failed(err) || (int64_t)(globaltimer_ns() - t0) > limit_ns);
+          if (__any_sync(FULL_MASK, stop)) {
             ok = false;
             break;
           }
@@ -182,6 +182,285 @@ k_sweep(const int32_t *__restrict__ order, int64_t len, const int64_t *__restric
   }
 }
 
+// ---------------------------------------------------------------------------
+// Cluster schedule: one thread-block cluster of C CTAs (C up to 16, one per
+// SM).  The sweep's output vector lives in the cluster's distributed shared
+// memory -- x_i in the shared memory of CTA (i mod C), slot i / C -- so a
+// dependency is handed from one SM to another through DSMEM (a few hundred
+// cycles) instead of L2, while the FP64 work spreads over C SMs.  Values are
+// again their own ready flags (kPending until written).  At the end each CTA
+// copies its slice to the global output.  Every CTA reaches the final cluster
+// barrier even after a failure, so no CTA leaves while others may still read
+// its shared memory.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned dsm_addr(unsigned base, int64_t i, int C) {
+  unsigned a;
+  const unsigned rank = (unsigned)(i % C);
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(a) : "r"(base), "r"(rank));
+  return a + (unsigned)((i / C) * 8);
+}
+
+__device__ __forceinline__ double ld_dsm(unsigned a) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.cluster.shared::cluster.b64 %0, [%1];" : "=l"(v) : "r"(a) : "memory");
+  return __longlong_as_double((long long)v);
+}
+
+__device__ __forceinline__ void st_dsm(unsigned a, double x) {
+  asm volatile("st.relaxed.cluster.shared::cluster.b64 [%0], %1;" ::"r"(a),
+               "l"((unsigned long long)__double_as_longlong(x))
+               : "memory");
+}
+
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.aligned;\n\tbarrier.cluster.wait.aligned;" ::: "memory");
+}
+
+template <bool FORWARD, bool DIVIDE, int W>
+__global__ void __launch_bounds__(kCtaThreads, 1)
+k_sweep_cluster(const int32_t *__restrict__ order, int64_t len, int64_t n,
+                const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                const int64_t *__restrict__ dg, const double *__restrict__ v, const double *in,
+                double *out, double *clear, DevErr *err, int64_t limit_ns) {
+  extern __shared__ __align__(16) double xs[];  // this CTA's slice of x
+  __shared__ int sfail;
+  unsigned rank, C;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(C));
+  const int64_t slice = (n + C - 1) / C;
+  for (int64_t j = threadIdx.x; j < slice; j += blockDim.x)
+    xs[j] = __longlong_as_double((long long)kPending);
+  if (threadIdx.x == 0) sfail = 0;
+  const unsigned base = (unsigned)__cvta_generic_to_shared(xs);
+  cluster_sync_all();
+
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = (int64_t)rank * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int64_t nw = (int64_t)C * (blockDim.x >> 5);
+  bool ok = true;
+  for (int64_t slot0 = gw * 32; slot0 < len && ok; slot0 += nw * 32) {
+    const int64_t row = order[slot0 + lane];
+    int64_t first = 0, d = 0;
+    int mylen = 0;
+    double s = 0.0;
+    if (row >= 0) {
+      d = dg[row];
+      if (FORWARD) {
+        first = rp[row];
+        mylen = (int)(d - first);
+      } else {
+        first = rp[row + 1] - 1;
+        mylen = (int)(first - d);
+      }
+      s = in[row];
+      if (clear) clear[row] = __longlong_as_double((long long)kPending);
+    }
+    constexpr int64_t step = FORWARD ? 1 : -1;
+    const int maxlen = __reduce_max_sync(FULL_MASK, mylen);
+    const int off = maxlen - mylen;
+    for (int q0 = 0; q0 < maxlen; q0 += W) {
+      unsigned a[W];
+      double f[W], x[W];
+      bool pend = false;
+#pragma unroll
+      for (int u = 0; u < W; ++u) {
+        const int e = q0 + u - off;
+        if (e >= 0 && e < mylen) {
+          a[u] = dsm_addr(base, ci[first + step * e], (int)C);
+          f[u] = v[first + step * e];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < W; ++u) {
+        const int e = q0 + u - off;
+        if (e >= 0 && e < mylen) {
+          x[u] = ld_dsm(a[u]);
+          pend |= pending(x[u]);
+        }
+      }
+      if (__any_sync(FULL_MASK, pend)) {
+        const uint64_t t0 = globaltimer_ns();
+        unsigned backoff = 8;
+        for (unsigned it = 0; __any_sync(FULL_MASK, pend); ++it) {
+          pend = false;
+#pragma unroll
+          for (int u = 0; u < W; ++u) {
+            const int e = q0 + u - off;
+            if (e >= 0 && e < mylen && pending(x[u])) {
+              x[u] = ld_dsm(a[u]);
+              pend |= pending(x[u]);
+            }
+          }
+          const bool stop = (it & 15u) == 15u &&
+                            (*((volatile int *)&sfail) || any_failed(err) ||
+                             (int64_t)(globaltimer_ns() - t0) > limit_ns);
+          if (__any_sync(FULL_MASK, stop)) {
+            ok = false;
+            break;
+          }
+          if (__any_sync(FULL_MASK, pend) && it >= 2) {
+            __nanosleep(backoff);
+            if (backoff < 64u) backoff <<= 1;
+          }
+        }
+        if (!__all_sync(FULL_MASK, ok)) {
+          ok = false;
+          break;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < W; ++u) {
+        const int e = q0 + u - off;
+        if (e >= 0 && e < mylen) x[u] = __dmul_rn(f[u], x[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < W; ++u) {
+        const int e = q0 + u - off;
+        if (e >= 0 && e < mylen) s = __dsub_rn(s, x[u]);
+      }
+    }
+    if (!ok) {
+      if (lane == 0) {
+        atomicExch(&sfail, 1);
+        if (row >= 0) set_err(err, row, ILUK_ETIMEOUT);
+        else set_err(err, n, ILUK_ETIMEOUT);
+      }
+      break;
+    }
+    if (DIVIDE && row >= 0) s = __ddiv_rn(s, v[d]);
+    if (row >= 0) {
+      if ((unsigned long long)__double_as_longlong(s) == kPending)
+        s = __longlong_as_double((long long)kQuietNaN);
+      st_dsm(dsm_addr(base, row, (int)C), s);
+    }
+  }
+  // Every CTA arrives here, so no shared memory is released while read.
+  cluster_sync_all();
+  for (int64_t j = threadIdx.x; j < slice; j += blockDim.x) {
+    const int64_t i = j * C + rank;
+    if (i < n) out[i] = xs[j];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Warp-per-row schedules.  One warp owns one row (rows taken from the level
+// order, so every dependency lies at an earlier position and is owned by a
+// warp that is already running).  The lanes load and poll up to 32 entries at
+// a time and form their products as soon as their values arrive; the warp
+// then subtracts the longest ready prefix of the chain, in order, and goes
+// back to polling only if the prefix stopped at a still-pending entry.  A row
+// therefore pays, after its last dependency arrives, only for the rest of its
+// own chain.  SCOPE 0: values in global memory, any number of SMs (a
+// co-resident cooperative grid); SCOPE 1: values in the distributed shared
+// memory of one thread-block cluster (as k_sweep_cluster).
+// ---------------------------------------------------------------------------
+template <int SCOPE>
+__device__ __forceinline__ double wpr_load(const double *out, unsigned base, int64_t i, int C) {
+  if (SCOPE == 0) return ld_val<true>(&out[i]);
+  return ld_dsm(dsm_addr(base, i, C));
+}
+
+template <bool FORWARD, bool DIVIDE, int SCOPE>
+__global__ void __launch_bounds__(kCtaThreads, 1)
+k_sweep_wpr(const int32_t *__restrict__ order, int64_t len, int64_t n,
+            const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
+            const int64_t *__restrict__ dg, const double *__restrict__ v, const double *in,
+            double *out, double *clear, DevErr *err, int64_t limit_ns) {
+  extern __shared__ __align__(16) double xs[];
+  unsigned rank = 0, C = 1, base = 0;
+  int64_t slice = 0;
+  if (SCOPE == 1) {
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(C));
+    slice = (n + C - 1) / C;
+    for (int64_t j = threadIdx.x; j < slice; j += blockDim.x)
+      xs[j] = __longlong_as_double((long long)kPending);
+    base = (unsigned)__cvta_generic_to_shared(xs);
+    cluster_sync_all();
+  }
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = SCOPE == 1 ? (int64_t)rank * (blockDim.x >> 5) + (threadIdx.x >> 5)
+                                : ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = SCOPE == 1 ? (int64_t)C * (blockDim.x >> 5)
+                                : ((int64_t)gridDim.x * blockDim.x) >> 5;
+  bool ok = true;
+  for (int64_t slot = gw; slot < len && ok; slot += nw) {
+    const int64_t row = order[slot];
+    if (row < 0) continue;
+    const int64_t d = dg[row];
+    const int64_t first = FORWARD ? rp[row] : rp[row + 1] - 1;
+    const int mylen = (int)(FORWARD ? d - first : first - d);
+    constexpr int64_t step = FORWARD ? 1 : -1;
+    double s = in[row];
+    if (clear && lane == 0) clear[row] = __longlong_as_double((long long)kPending);
+    for (int b = 0; b < mylen && ok; b += 32) {
+      const int e = b + lane;
+      const bool act = e < mylen;
+      const int cnt = (mylen - b) < 32 ? mylen - b : 32;
+      int32_t c = 0;
+      double f = 0.0, x = 0.0, prod = 0.0;
+      bool have = !act;
+      if (act) {
+        c = ci[first + step * e];
+        f = v[first + step * e];
+        x = wpr_load<SCOPE>(out, base, c, (int)C);
+        if (!pending(x)) {
+          prod = __dmul_rn(f, x);
+          have = true;
+        }
+      }
+      int done = 0;
+      const uint64_t t0 = globaltimer_ns();
+      unsigned backoff = 8;
+      for (unsigned it = 0;; ++it) {
+        const unsigned ready = __ballot_sync(FULL_MASK, have);
+        const unsigned rest = ~(ready >> done);  // first not-ready lane at or after `done`
+        const int run = rest == 0u ? 32 - done : __ffs(rest) - 1;
+        const int upto = done + run < cnt ? done + run : cnt;
+        for (int j = done; j < upto; ++j) s = __dsub_rn(s, __shfl_sync(FULL_MASK, prod, j));
+        done = upto;
+        if (done >= cnt) break;
+        const bool stop = (it & 15u) == 15u &&
+                          (any_failed(err) || (int64_t)(globaltimer_ns() - t0) > limit_ns);
+        if (__any_sync(FULL_MASK, stop)) {
+          ok = false;
+          break;
+        }
+        __nanosleep(backoff);
+        if (backoff < (SCOPE == 0 ? 128u : 64u)) backoff <<= 1;
+        if (!have) {
+          x = wpr_load<SCOPE>(out, base, c, (int)C);
+          if (!pending(x)) {
+            prod = __dmul_rn(f, x);
+            have = true;
+          }
+        }
+      }
+    }
+    if (!ok) {
+      if (lane == 0) set_err(err, row, ILUK_ETIMEOUT);
+      break;
+    }
+    if (DIVIDE) s = __ddiv_rn(s, v[d]);
+    if ((unsigned long long)__double_as_longlong(s) == kPending)
+      s = __longlong_as_double((long long)kQuietNaN);
+    if (lane == 0) {
+      if (SCOPE == 0)
+        st_val<true>(&out[row], s);
+      else
+        st_dsm(dsm_addr(base, row, (int)C), s);
+    }
+    __syncwarp();
+  }
+  if (SCOPE == 1) {
+    cluster_sync_all();
+    for (int64_t j = threadIdx.x; j < slice; j += blockDim.x) {
+      const int64_t ii = j * C + rank;
+      if (ii < n) out[ii] = xs[j];
+    }
+  }
+}
+
 __global__ void k_fill_pending(int64_t n, double *x) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
@@ -198,8 +477,86 @@ cudaError_t launch_fill_pending(int64_t n, double *x, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// Cluster width for n rows: the largest of 16, 8, 4, 2 whose slices fit in
+// one CTA's shared memory and that the device can schedule (0 when none).
+template <typename K>
+static int cluster_width(int64_t n, K kern) {
+  static int cached[64][2] = {};
+  static std::mutex mu;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const size_t budget = (size_t)max_smem_optin() - 1024;
+  for (int C : {16, 8, 4, 2}) {
+    const size_t smem = (size_t)((n + C - 1) / C) * sizeof(double);
+    if (smem > budget) continue;
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      // schedulable widths do not depend on n beyond the shared memory size
+      if (dev < 64 && cached[dev][0] == C && (size_t)cached[dev][1] >= smem) return C;
+    }
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+            cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)C);
+    cfg.blockDim = dim3(kCtaThreads);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg) == cudaSuccess && nclusters >= 1) {
+      std::lock_guard<std::mutex> lk(mu);
+      if (dev < 64) {
+        cached[dev][0] = C;
+        cached[dev][1] = (int)smem;
+      }
+      return C;
+    }
+    cudaGetLastError();
+  }
+  return 0;
+}
+
+int cluster_size_for(int64_t n) { return cluster_width(n, k_sweep_cluster<true, false, 4>); }
+
+template <typename K>
+static cudaError_t launch_on_cluster(K kern, int C, size_t smem, cudaStream_t s,
+                                     const int32_t *order, int64_t len, int64_t n,
+                                     const int64_t *rp, const int32_t *ci, const int64_t *dg,
+                                     const double *v, const double *in, double *out,
+                                     double *clear, DevErr *err, int64_t limit) {
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)C);
+  cfg.blockDim = dim3(kCtaThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  e = cudaLaunchKernelEx(&cfg, kern, order, len, n, rp, ci, dg, v, in, out, clear, err, limit);
+  note_launch();
+  return e;
+}
+
 template <bool FORWARD, bool DIVIDE>
-static cudaError_t run_sweep(const LevelOrder &lo, const int64_t *rp, const int32_t *ci,
+static cudaError_t run_sweep(int64_t n, const LevelOrder &lo, const int64_t *rp, const int32_t *ci,
                              const int64_t *dg, const double *v, const double *in, double *out,
                              double *clear, int sched, DevErr *err, cudaStream_t s) {
   ProfScope prof_scope(FORWARD ? ILUK_PROF_SWEEP : ILUK_PROF_SWEEP_BWD, s);
@@ -212,6 +569,35 @@ static cudaError_t run_sweep(const LevelOrder &lo, const int64_t *rp, const int3
                                                                 out, clear, err, limit);
     note_launch();
     return cudaGetLastError();
+  }
+  if (sched == ILUK_SCHED_CLUSTER || sched == ILUK_SCHED_WARP_CLUSTER) {
+    const bool wpr = sched == ILUK_SCHED_WARP_CLUSTER;
+    const int C = wpr ? cluster_width(n, k_sweep_wpr<FORWARD, DIVIDE, 1>)
+                      : cluster_width(n, k_sweep_cluster<FORWARD, DIVIDE, 4>);
+    if (C == 0) return cudaErrorInvalidConfiguration;
+    const size_t smem = (size_t)((n + C - 1) / C) * sizeof(double);
+    if (wpr)
+      return launch_on_cluster(k_sweep_wpr<FORWARD, DIVIDE, 1>, C, smem, s, order, len, n, rp, ci,
+                               dg, v, in, out, clear, err, limit);
+    return launch_on_cluster(k_sweep_cluster<FORWARD, DIVIDE, 4>, C, smem, s, order, len, n, rp,
+                             ci, dg, v, in, out, clear, err, limit);
+  }
+  if (sched == ILUK_SCHED_WARP_GRID) {
+    auto kern = k_sweep_wpr<FORWARD, DIVIDE, 0>;
+    int bps = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, kCtaThreads, 0);
+    if (bps < 1) bps = 1;
+    int64_t grid = (int64_t)bps * num_sms();
+    const int64_t want = (len + (kCtaThreads / 32) - 1) / (kCtaThreads / 32);
+    if (grid > want) grid = want;
+    const int64_t nn = n;
+    void *args[] = {(void *)&order, (void *)&len, (void *)&nn, (void *)&rp, (void *)&ci,
+                    (void *)&dg, (void *)&v, (void *)&in, (void *)&out, (void *)&clear,
+                    (void *)&err, (void *)&limit};
+    cudaError_t e = cudaLaunchCooperativeKernel((const void *)kern, dim3((unsigned)grid),
+                                                dim3(kCtaThreads), args, 0, s);
+    note_launch();
+    return e;
   }
   // Multi-SM: every block must be resident (rows wait on rows of other
   // blocks), so the grid is launched cooperatively and sized by occupancy.
@@ -236,19 +622,29 @@ cudaError_t launch_apply(int64_t n, const int64_t *rp, const int32_t *ci, const 
                          const double *v, const LevelOrder &fwd, const LevelOrder &bwd,
                          const double *p, double *tmp, double *y, int transpose, int sched,
                          DevErr *err, cudaStream_t s) {
-  if (sched != ILUK_SCHED_SINGLE_CTA) sched = ILUK_SCHED_FLAGS;
-  (void)n;
+  // sched packs the forward schedule in bits 0-7 and the backward one in 8-15
+  // (a single value applies to both).
+  int sf = sched & 0xff, sb = (sched >> 8) & 0xff;
+  if (sb == 0) sb = sf;
+  auto fix = [&](int sc) {
+    if ((sc == ILUK_SCHED_CLUSTER || sc == ILUK_SCHED_WARP_CLUSTER) && cluster_size_for(n) == 0)
+      sc = ILUK_SCHED_WARP_GRID;
+    if (sc < ILUK_SCHED_FLAGS || sc > ILUK_SCHED_WARP_CLUSTER) sc = ILUK_SCHED_WARP_GRID;
+    return sc;
+  };
+  sf = fix(sf);
+  sb = fix(sb);
   cudaError_t e;
   // tmp is pending on entry (left so by the previous backward sweep); the
   // forward sweep re-arms y, the backward sweep re-arms tmp.
   if (!transpose) {
-    e = run_sweep<true, false>(fwd, rp, ci, dg, v, p, tmp, y, sched, err, s);
+    e = run_sweep<true, false>(n, fwd, rp, ci, dg, v, p, tmp, y, sf, err, s);
     if (e != cudaSuccess) return e;
-    return run_sweep<false, true>(bwd, rp, ci, dg, v, tmp, y, tmp, sched, err, s);
+    return run_sweep<false, true>(n, bwd, rp, ci, dg, v, tmp, y, tmp, sb, err, s);
   }
-  e = run_sweep<true, true>(fwd, rp, ci, dg, v, p, tmp, y, sched, err, s);
+  e = run_sweep<true, true>(n, fwd, rp, ci, dg, v, p, tmp, y, sf, err, s);
   if (e != cudaSuccess) return e;
-  return run_sweep<false, false>(bwd, rp, ci, dg, v, tmp, y, tmp, sched, err, s);
+  return run_sweep<false, false>(n, bwd, rp, ci, dg, v, tmp, y, tmp, sb, err, s);
 }
 
 // ---------------------------------------------------------------------------

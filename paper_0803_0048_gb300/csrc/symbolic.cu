@@ -75,7 +75,8 @@ k_symbolic_rows(int64_t n, const int64_t *__restrict__ arp, const int32_t *__res
         ucol = aci + s;
         ulen = (int)(b1 - s);
       } else {
-        if (!wait_flag(&ready[i], err, row, limit_ns)) {
+        const bool got = wait_flag(&ready[i], err, row, limit_ns);
+        if (!__all_sync(FULL_MASK, got)) {  // any lane gave up: the warp stops
           if (lane == 0 && !earlier_failed(err, row)) set_err(err, row, ILUK_ETIMEOUT);
           ok = false;
           break;

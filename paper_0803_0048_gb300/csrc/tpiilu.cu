@@ -103,8 +103,9 @@ k_iiluk_build(int64_t n, const int64_t *__restrict__ frp, const int32_t *__restr
               pend = pend_g(gv);
             }
             if (!__any_sync(FULL_MASK, pend)) break;
-            if ((it & 7u) == 7u &&
-                (earlier_failed(err, t) || (int64_t)(globaltimer_ns() - t0) > limit_ns)) {
+            const bool stop = (it & 7u) == 7u && (earlier_failed(err, t) ||
+                                                  (int64_t)(globaltimer_ns() - t0) > limit_ns);
+            if (__any_sync(FULL_MASK, stop)) {  // the whole warp gives up together
               ok = false;
               break;
             }

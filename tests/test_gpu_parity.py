@@ -60,7 +60,7 @@ def test_numeric_bit_exact(name, A, k):
     assert_bits_equal(F.values(), ref["val"], "factor values")
 
 
-@pytest.mark.parametrize("sched", [L.SCHED_FLAGS, L.SCHED_SINGLE_CTA])
+@pytest.mark.parametrize("sched", [L.SCHED_FLAGS, L.SCHED_SINGLE_CTA, L.SCHED_CLUSTER, L.SCHED_WARP_GRID, L.SCHED_WARP_CLUSTER])
 @pytest.mark.parametrize("name,A,k", CASES, ids=IDS)
 def test_apply_bit_exact(name, A, k, sched):
     S, F, ref, _ = factor_both(A, k)
