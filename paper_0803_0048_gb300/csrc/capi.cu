@@ -372,8 +372,7 @@ int iluk_symbolic(const iluk_pattern *A, int k, iluk_sym **out, iluk_info *info,
   dfree(maxrow, s);
   cleanup();
   // level orders of the two sweeps
-  st = build_levels(n, S->rowptr, S->colind, S->diag, true, &S->lord, s);
-  if (st == ILUK_OK) st = build_levels(n, S->rowptr, S->colind, S->diag, false, &S->uord, s);
+  st = build_levels_pair(n, S->rowptr, S->colind, S->diag, &S->lord, &S->uord, s);
   if (st != ILUK_OK) {
     iluk_sym_destroy(S);
     return fail(info, st);
@@ -534,9 +533,7 @@ static int ensure_transpose(iluk_fac *F, cudaStream_t s) {
   dfree(cursor, s);
   dfree(scan_tmp, s);
   if (!F->tlord.order && S->n) {
-    int st = build_levels(S->n, F->trowptr, F->tcolind, F->tdiag, true, &F->tlord, s);
-    if (st == ILUK_OK)
-      st = build_levels(S->n, F->trowptr, F->tcolind, F->tdiag, false, &F->tuord, s);
+    int st = build_levels_pair(S->n, F->trowptr, F->tcolind, F->tdiag, &F->tlord, &F->tuord, s);
     if (st != ILUK_OK) return st;
   }
   return ILUK_OK;

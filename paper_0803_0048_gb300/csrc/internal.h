@@ -99,9 +99,9 @@ cudaError_t launch_symbolic_compact(int64_t n, const SymArena &ar, const int64_t
 cudaError_t launch_a2f(int64_t n, const int64_t *arp, const int32_t *aci, const int64_t *frp,
                        const int32_t *fci, int32_t *a2f, cudaStream_t s);
 
-// Levels (levels.cu): synchronous; allocates lo->order on success.
-int build_levels(int64_t n, const int64_t *rp, const int32_t *ci, const int64_t *dg, bool forward,
-                 LevelOrder *lo, cudaStream_t s);
+// Levels (levels.cu): synchronous; allocates both orders on success.
+int build_levels_pair(int64_t n, const int64_t *rp, const int32_t *ci, const int64_t *dg,
+                      LevelOrder *fwd, LevelOrder *bwd, cudaStream_t s);
 
 // Numeric (numeric.cu)
 // The factor values double as ready flags (numeric.cu); fval is overwritten.

@@ -16,10 +16,9 @@ constexpr int kDepthThreads = 1024;
 // One CTA, one warp per row (rows claimed in sweep order through a shared
 // ticket).  depth[] doubles as the ready flag: 0 until the row is final.
 template <bool FORWARD>
-__global__ void __launch_bounds__(kDepthThreads, 1)
-k_depth_cta(int64_t n, const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
-            const int64_t *__restrict__ dg, int32_t *depth, int32_t *maxdepth, DevErr *err,
-            int64_t limit_ns) {
+__device__ void depth_cta(int64_t n, const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                          const int64_t *__restrict__ dg, int32_t *depth, int32_t *maxdepth,
+                          DevErr *err, int64_t limit_ns) {
   __shared__ unsigned long long sticket;
   __shared__ int sfail;
   if (threadIdx.x == 0) {
@@ -79,6 +78,18 @@ k_depth_cta(int64_t n, const int64_t *__restrict__ rp, const int32_t *__restrict
   if (lane == 0 && dmax_local) atomicMax(maxdepth, dmax_local);
 }
 
+// Block 0 computes the forward depths, block 1 the backward depths; the two
+// DAGs are independent, so the two blocks run side by side on two SMs.
+__global__ void __launch_bounds__(kDepthThreads, 1)
+k_depth_pair(int64_t n, const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
+             const int64_t *__restrict__ dg, int32_t *depth_f, int32_t *depth_b, int32_t *mx,
+             DevErr *err, int64_t limit_ns) {
+  if (blockIdx.x == 0)
+    depth_cta<true>(n, rp, ci, dg, depth_f, mx, err, limit_ns);
+  else
+    depth_cta<false>(n, rp, ci, dg, depth_b, mx + 1, err + 1, limit_ns);
+}
+
 __global__ void k_level_count(int64_t n, const int32_t *__restrict__ depth, int32_t *cnt) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
@@ -108,26 +119,15 @@ static unsigned grid_for(int64_t n) {
   return (unsigned)(b < 1 ? 1 : b);
 }
 
-// Synchronous: computes the depths, then the padded level order.  On success
-// lo->order is a new device allocation of lo->len entries.
-int build_levels(int64_t n, const int64_t *rp, const int32_t *ci, const int64_t *dg, bool forward,
-                 LevelOrder *lo, cudaStream_t s) {
-  ProfScope prof_scope(ILUK_PROF_DEPTH, s);
-  lo->order = nullptr;
-  lo->len = 0;
-  lo->nlev = 0;
-  if (n == 0) return ILUK_OK;
-  int32_t *depth = nullptr, *mx = nullptr, *cnt = nullptr, *cursor = nullptr;
+// Padded level order from depths (synchronous).
+static int order_from_depth(int64_t n, const int32_t *depth, int32_t nlev, LevelOrder *lo,
+                            cudaStream_t s) {
+  int32_t *cnt = nullptr, *cursor = nullptr;
   int64_t *lstart = nullptr, *scan_tmp = nullptr;
-  DevErr *err = nullptr;
-  int st = ILUK_OK;
   auto cleanup = [&]() {
-    if (depth) cudaFreeAsync(depth, s);
-    if (mx) cudaFreeAsync(mx, s);
     if (cnt) cudaFreeAsync(cnt, s);
     if (cursor) cudaFreeAsync(cursor, s);
     if (scan_tmp) cudaFreeAsync(scan_tmp, s);
-    if (err) cudaFreeAsync(err, s);
   };
 #define CKL(call)                              \
   do {                                         \
@@ -137,27 +137,6 @@ int build_levels(int64_t n, const int64_t *rp, const int32_t *ci, const int64_t 
       return ILUK_ECUDA;                       \
     }                                          \
   } while (0)
-  CKL(cudaMallocAsync((void **)&depth, n * sizeof(int32_t), s));
-  CKL(cudaMallocAsync((void **)&mx, sizeof(int32_t), s));
-  CKL(cudaMallocAsync((void **)&err, sizeof(DevErr), s));
-  CKL(cudaMemsetAsync(depth, 0, n * sizeof(int32_t), s));
-  CKL(cudaMemsetAsync(mx, 0, sizeof(int32_t), s));
-  CKL(launch_fill_err(err, s));
-  if (forward)
-    k_depth_cta<true><<<1, kDepthThreads, 0, s>>>(n, rp, ci, dg, depth, mx, err, wait_limit());
-  else
-    k_depth_cta<false><<<1, kDepthThreads, 0, s>>>(n, rp, ci, dg, depth, mx, err, wait_limit());
-  note_launch();
-  CKL(cudaGetLastError());
-  DevErr herr;
-  int32_t nlev = 0;
-  CKL(cudaMemcpyAsync(&herr, err, sizeof(herr), cudaMemcpyDeviceToHost, s));
-  CKL(cudaMemcpyAsync(&nlev, mx, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-  CKL(cudaStreamSynchronize(s));
-  if (herr.key != kNoErr) {
-    cleanup();
-    return (int)(herr.key & 0xff);
-  }
   CKL(cudaMallocAsync((void **)&cnt, (size_t)nlev * sizeof(int32_t), s));
   CKL(cudaMallocAsync((void **)&cursor, (size_t)nlev * sizeof(int32_t), s));
   CKL(cudaMallocAsync((void **)&lstart, ((size_t)nlev + 1) * sizeof(int64_t), s));
@@ -182,6 +161,54 @@ int build_levels(int64_t n, const int64_t *rp, const int32_t *ci, const int64_t 
   lo->lstart = lstart;
   lo->len = len;
   lo->nlev = nlev;
+  return ILUK_OK;
+}
+
+// Synchronous: the depths of both sweep DAGs (one launch, one block each),
+// then the two padded level orders.  On success fwd->order / bwd->order (and
+// their level starts) are new device allocations.
+int build_levels_pair(int64_t n, const int64_t *rp, const int32_t *ci, const int64_t *dg,
+                      LevelOrder *fwd, LevelOrder *bwd, cudaStream_t s) {
+  ProfScope prof_scope(ILUK_PROF_DEPTH, s);
+  *fwd = LevelOrder();
+  *bwd = LevelOrder();
+  if (n == 0) return ILUK_OK;
+  int32_t *depth = nullptr, *mx = nullptr;
+  DevErr *err = nullptr;
+  auto cleanup = [&]() {
+    if (depth) cudaFreeAsync(depth, s);
+    if (mx) cudaFreeAsync(mx, s);
+    if (err) cudaFreeAsync(err, s);
+  };
+  if (cudaMallocAsync((void **)&depth, 2 * n * sizeof(int32_t), s) != cudaSuccess ||
+      cudaMallocAsync((void **)&mx, 2 * sizeof(int32_t), s) != cudaSuccess ||
+      cudaMallocAsync((void **)&err, 2 * sizeof(DevErr), s) != cudaSuccess ||
+      cudaMemsetAsync(depth, 0, 2 * n * sizeof(int32_t), s) != cudaSuccess ||
+      cudaMemsetAsync(mx, 0, 2 * sizeof(int32_t), s) != cudaSuccess ||
+      launch_fill_err(err, s) != cudaSuccess || launch_fill_err(err + 1, s) != cudaSuccess) {
+    cleanup();
+    return ILUK_ECUDA;
+  }
+  k_depth_pair<<<2, kDepthThreads, 0, s>>>(n, rp, ci, dg, depth, depth + n, mx, err,
+                                           wait_limit());
+  note_launch();
+  DevErr herr[2];
+  int32_t nlev[2] = {0, 0};
+  if (cudaGetLastError() != cudaSuccess ||
+      cudaMemcpyAsync(herr, err, sizeof(herr), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemcpyAsync(nlev, mx, sizeof(nlev), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    cleanup();
+    return ILUK_ECUDA;
+  }
+  for (int d = 0; d < 2; ++d)
+    if (herr[d].key != kNoErr) {
+      cleanup();
+      return (int)(herr[d].key & 0xff);
+    }
+  int st = order_from_depth(n, depth, nlev[0], fwd, s);
+  if (st == ILUK_OK) st = order_from_depth(n, depth + n, nlev[1], bwd, s);
+  cleanup();
   return st;
 }
 

@@ -1,0 +1,143 @@
+"""Parity at the full sizes of the synthetic workloads.
+
+* 2D 64^2 (k=2), random band n=160,000 (k=0,1,2) and 3D 64^3 (k=2): pattern,
+  levels, factors, one preconditioner application (the autotuned schedule),
+  TPIILU and GMRES compared with the oracle element by element.
+* Random band n=160,000 with k=3 (87 million factor entries; the oracle needs
+  minutes): properties that hold at any size, on sampled rows -- the level of
+  every entry satisfies Def. 2.3's recurrence over the GPU's own earlier rows,
+  (L~U~)_ij = a_ij on kept positions within the rounding bound, and
+  L~U~y = p for the applied preconditioner.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_0803_0048_gb300 as P
+from paper_0803_0048_gb300 import workloads as W
+
+from gpu_helpers import assert_bits_equal, bits
+
+pytestmark = pytest.mark.gpu
+EPS = np.finfo(np.float64).eps
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+FULL = [("convdiff2d_64", lambda: W.conv_diff_2d_64(), 2),
+        ("band160k_k0", lambda: W.random_band_160k(k=0), 0),
+        ("band160k_k1", lambda: W.random_band_160k(k=1), 1),
+        ("band160k_k2", lambda: W.random_band_160k(k=2), 2),
+        ("convdiff3d_64", lambda: W.conv_diff_3d(), 2)]
+
+
+@pytest.mark.parametrize("name,make,k", FULL, ids=[f[0] for f in FULL])
+def test_full_size_bit_exact(name, make, k):
+    Pb = make()
+    A = Pb.A
+    rp, ci, av, b = dev(A.rowptr), dev(A.colind), dev(A.val), dev(Pb.b)
+    S = P.symbolic(rp, ci, k)
+    F = P.numeric(S, av)
+    ref = oracle.factor(A, k)
+    grp, gci, glev, _ = [t.cpu().numpy() for t in S.pattern()]
+    assert np.array_equal(grp, ref["rowptr"]) and np.array_equal(gci, ref["colind"])
+    assert np.array_equal(glev, ref["level"])
+    assert_bits_equal(F.values(), ref["val"], "factors")
+    p = W.uniform(W.stream_key(3, "fs"), np.arange(A.n), -1.0, 1.0)
+    y = F.apply(dev(p))
+    assert F.status() == 0
+    assert_bits_equal(y, oracle.apply(A.n, ref["rowptr"], ref["colind"], ref["val"], p), "apply")
+    M = P.iiluk_build(F)
+    g = oracle.iiluk_build(A.n, ref["rowptr"], ref["colind"], ref["val"])
+    assert_bits_equal(M.values(), g, "TPIILU")
+    x, info = P.gmres(rp, ci, av, b, F, restart=Pb.restart, rtol=Pb.rtol)
+    st, xo, it, rel, cyc = oracle.gmres(A.n, A.rowptr, A.colind, A.val, Pb.b, oracle.PREC_ILU,
+                                        (ref["rowptr"], ref["colind"], ref["val"]), Pb.restart,
+                                        Pb.rtol, dotmode=oracle.DOT_TREE)
+    assert st == 0 and info.iters == it and bits([info.relres])[0] == bits([rel])[0]
+    assert_bits_equal(x, xo, "gmres x")
+    assert np.abs(x.cpu().numpy() - Pb.xstar).max() < 1e-4
+
+
+def test_largest_case_properties_on_sampled_rows():
+    k = 3
+    Pb = W.random_band_160k(k=k)
+    A = Pb.A
+    rp, ci, av = dev(A.rowptr), dev(A.colind), dev(A.val)
+    S = P.symbolic(rp, ci, k)
+    F = P.numeric(S, av)
+    frp, fci, flev, fdg = [t.cpu().numpy() for t in S.pattern()]
+    fv = F.values().cpu().numpy()
+    n = A.n
+    p = W.uniform(W.stream_key(4, "fs3"), np.arange(n), -1.0, 1.0)
+    y = F.apply(dev(p)).cpu().numpy()
+    assert F.status() == 0
+    rng_rows = W.draws_u64(W.stream_key(5, "rows"), np.arange(24)) % np.uint64(n)
+    rows = sorted(set(int(r) for r in rng_rows) | {0, 1, n - 1, n // 2})
+
+    def row(i):
+        s, e = frp[i], frp[i + 1]
+        return fci[s:e], flev[s:e], fv[s:e], fdg[i] - s
+
+    Ad = {}
+    for i in rows:
+        Ad[i] = dict(zip(A.colind[A.rowptr[i]:A.rowptr[i + 1]].tolist(),
+                         A.val[A.rowptr[i]:A.rowptr[i + 1]].tolist()))
+    Uy = {}
+
+    def uy(h):  # (U~ y)_h, needed for the residual check
+        if h not in Uy:
+            c, _, v, d = row(h)
+            Uy[h] = float(np.dot(v[d:], y[c[d:]]))
+        return Uy[h]
+
+    for j in rows:
+        cj, lj, vj, dj = row(j)
+        # Def. 2.3 recurrence over the GPU's own earlier rows
+        best = {}
+        for q in range(dj):
+            h = int(cj[q])
+            ch, lh, _, dh = row(h)
+            for t, lt in zip(ch[dh + 1:].tolist(), lh[dh + 1:].tolist()):
+                w = int(lj[q]) + lt + 1
+                if w < best.get(t, 10 ** 9):
+                    best[t] = w
+        present = dict(zip(cj.tolist(), lj.tolist()))
+        for t, lev in present.items():
+            if t in Ad[j]:
+                assert lev == 0
+            else:
+                assert best.get(t) == lev, (j, t)
+        for t, w in best.items():
+            if t not in present:
+                assert w > k, (j, t)
+        # (L~U~)_jt = a_jt on kept positions:
+        # sum over h in L(j), h <= t, of l_jh u_ht, plus u_jt when t >= j
+        acc = {t: 0.0 for t in present}
+        bnd = {t: 0.0 for t in present}
+        for qq in range(dj):
+            h = int(cj[qq])
+            ch, _, vh, dh = row(h)
+            for t, u in zip(ch[dh:].tolist(), vh[dh:].tolist()):
+                if t in acc:
+                    acc[t] += vj[qq] * u
+                    bnd[t] += abs(vj[qq] * u)
+        for q in range(dj, len(cj)):
+            acc[int(cj[q])] += vj[q]
+            bnd[int(cj[q])] += abs(vj[q])
+        for t in present:
+            assert abs(acc[t] - Ad[j].get(t, 0.0)) <= 64 * (dj + 2) * EPS * bnd[t] + 1e-300, (j, t)
+        # (L~ U~ y)_j = p_j
+        lhs = uy(j) + sum(vj[q] * uy(int(cj[q])) for q in range(dj))
+        scale = abs(uy(j)) + sum(abs(vj[q] * uy(int(cj[q]))) for q in range(dj))
+        assert abs(lhs - p[j]) <= 1e-8 * max(scale, 1.0)

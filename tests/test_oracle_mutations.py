@@ -1,0 +1,181 @@
+"""The pins must be able to fail: each plausible mistake planted in a copy of
+the oracle's C source (a dropped term, a wrong sign, a wrong index or bound, a
+transposed operation) has to be caught by at least one pin.
+
+The mutants are compiled into a temporary directory and loaded in place of
+the real oracle for the duration of one check; the real oracle is untouched.
+"""
+import math
+import os
+import subprocess
+import tempfile
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+import oracle
+from paper_0803_0048_gb300 import workloads as W
+
+from test_oracle_symbolic import path_levels
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "iluk_oracle.c")
+
+MUTANTS = {
+    "level_sum_drops_plus_one": ("int weight = level[i] + (int)rlev[i][q] + 1;",
+                                 "int weight = level[i] + (int)rlev[i][q];"),
+    "level_uses_max": ("int weight = level[i] + (int)rlev[i][q] + 1;",
+                       "int weight = (level[i] > (int)rlev[i][q] ? level[i] : (int)rlev[i][q]) + 1;"),
+    "fill_bound_strict": ("} else if (weight <= k) {", "} else if (weight < k) {"),
+    "merge_skips_lower_fill": ("if (t <= i) continue;", "if (t <= j) continue;"),
+    "multiplier_times_pivot": ("w[h] = w[h] / piv;", "w[h] = w[h] * piv;"),
+    "update_adds": ("          w[j] = w[j] - prod;", "          w[j] = w[j] + prod;"),
+    "forward_sweep_adds": ("""      double prod = fv[q] * x[fci[q]];
+      s = s - prod;""", """      double prod = fv[q] * x[fci[q]];
+      s = s + prod;"""),
+    "backward_no_divide": ("    y[i] = s / fv[d];", "    y[i] = s;"),
+    "tpiilu_lower_adds": ("""          double prod = lih * b[q];
+          b[pos[t]] = b[pos[t]] - prod;""", """          double prod = lih * b[q];
+          b[pos[t]] = b[pos[t]] + prod;"""),
+    "tpiilu_no_flip": ("g[p] = (p == d) ? fv[p] : -b[p];", "g[p] = (p == d) ? fv[p] : b[p];"),
+    "tpiilu_upper_unscaled": ("      double uih = fv[p] / uii;                     /* u^_ih */",
+                              "      double uih = fv[p];                           /* u^_ih */"),
+    "givens_sign": ("H[(i + 1) * m + j] = t4 - t3;", "H[(i + 1) * m + j] = t4 + t3;"),
+    "tree_dot_skips_partner": ("for (int p = 0; p < w; ++p) part[p] = part[p] + part[p + w];",
+                               "for (int p = 0; p < w; ++p) part[p] = part[p] + part[p];"),
+    "adjoint_sign": ("      gA[p] = -prod;", "      gA[p] = prod;"),
+    "transpose_backward_divides": ("""      double prod = tv[q] * y[tci[q]];
+      s = s - prod;
+    }
+    y[i] = s;""", """      double prod = tv[q] * y[tci[q]];
+      s = s - prod;
+    }
+    y[i] = s / tv[d];"""),
+}
+
+
+def build_mutant(name, tmp):
+    old, new = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) >= 1, f"mutation site for {name} not found"
+    mutated = src.replace(old, new, 1)
+    path_c = os.path.join(tmp, f"{name}.c")
+    path_so = os.path.join(tmp, f"{name}.so")
+    with open(path_c, "w") as f:
+        f.write(mutated)
+    subprocess.run(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-o",
+                    path_so, path_c, "-lm"], check=True)
+    return path_so
+
+
+def pins_pass():
+    """A compact run of the oracle's pins; returns the names that fail."""
+    failed = []
+    try:  # Def. 2.3 against lower-numbered paths
+        for n, dens, seed in [(10, 0.2, 3), (12, 0.15, 4)]:
+            A = W.random_sparse(n, dens, seed, dominance=None)
+            lev = path_levels(A)
+            for k in range(0, 4):
+                st, bad, frp, fci, flev = oracle.symbolic(A.n, A.rowptr, A.colind, k)
+                got = {(i, int(fci[p])): int(flev[p]) for i in range(n)
+                       for p in range(frp[i], frp[i + 1])}
+                want = {(i, j): lev[i][j] for i in range(n) for j in range(n)
+                        if lev[i][j] is not None and lev[i][j] <= k}
+                if got != want:
+                    raise AssertionError
+    except Exception:
+        failed.append("levels")
+    try:  # complete LU when k >= n
+        n = 12
+        key = W.stream_key(3, "m")
+        M = W.uniform(key, np.arange(n * n), -1, 1).reshape(n, n)
+        M[np.arange(n), np.arange(n)] = 2 * (np.abs(M).sum(axis=0) - np.abs(np.diag(M))) + 1
+        A = W.dense_to_csr(M, np.ones_like(M, dtype=bool))
+        F = oracle.factor(A, 250)
+        L = np.eye(n)
+        U = np.zeros((n, n))
+        for i in range(n):
+            for p in range(F["rowptr"][i], F["rowptr"][i + 1]):
+                j = int(F["colind"][p])
+                (L if j < i else U)[i, j] = F["val"][p]
+        _, Lr, Ur = sla.lu(M)
+        if not (np.allclose(L, Lr, atol=1e-13) and np.allclose(U, Ur, atol=1e-12)):
+            raise AssertionError
+    except Exception:
+        failed.append("dense_lu")
+    try:  # sweeps, transposed sweeps, TPIILU on a full pattern
+        n = 15
+        key = W.stream_key(5, "m")
+        M = W.uniform(key, np.arange(n * n), -1, 1).reshape(n, n)
+        M[np.arange(n), np.arange(n)] = 2 * (np.abs(M).sum(axis=0) - np.abs(np.diag(M))) + 1
+        A = W.dense_to_csr(M, np.ones_like(M, dtype=bool))
+        F = oracle.factor(A, 250)
+        p = W.uniform(W.stream_key(6, "p"), np.arange(n), -1, 1)
+        ref = np.linalg.solve(M, p)
+        if not np.allclose(oracle.apply(n, F["rowptr"], F["colind"], F["val"], p), ref, atol=1e-12):
+            raise AssertionError("apply")
+        trp, tci, tv = oracle.transpose(n, F["rowptr"], F["colind"], F["val"])
+        if not np.allclose(oracle.apply_t(n, trp, tci, tv, p), np.linalg.solve(M.T, p), atol=1e-12):
+            raise AssertionError("apply_t")
+        g = oracle.iiluk_build(n, F["rowptr"], F["colind"], F["val"])
+        if not np.allclose(oracle.iiluk_apply(n, F["rowptr"], F["colind"], g, p), ref, atol=1e-11):
+            raise AssertionError("iilu")
+    except Exception:
+        failed.append("solves")
+    try:  # GMRES and the adjoint against dense solves; tree dot vs fsum
+        A = W.conv_diff(8, 2, (20.0, 20.0))
+        n = A.n
+        b = W.uniform(W.stream_key(7, "b"), np.arange(n), -1, 1)
+        F = oracle.factor(A, 1)
+        st, x, *_ = oracle.gmres(n, A.rowptr, A.colind, A.val, b, oracle.PREC_ILU,
+                                 (F["rowptr"], F["colind"], F["val"]), 20, 1e-12,
+                                 dotmode=oracle.DOT_TREE)
+        Ad = W.csr_to_dense(A)
+        if st != 0 or np.linalg.norm(x - np.linalg.solve(Ad, b)) > 1e-9 * np.linalg.norm(x):
+            raise AssertionError("gmres")
+        g = W.uniform(W.stream_key(7, "g"), np.arange(n), -1, 1)
+        st, lam, gA, *_ = oracle.adjoint(n, A.rowptr, A.colind, A.val, F["rowptr"], F["colind"],
+                                         F["val"], x, g, 20, 1e-12)
+        if np.linalg.norm(lam - np.linalg.solve(Ad.T, g)) > 1e-9 * np.linalg.norm(lam):
+            raise AssertionError("adjoint")
+        r = np.repeat(np.arange(n), np.diff(A.rowptr))
+        if not np.array_equal(gA, -(lam[r] * x[A.colind])):
+            raise AssertionError("scatter")
+        # GMRES(m >= n) without preconditioning ends within one cycle
+        B = W.random_sparse(20, 0.25, 9, dominance=0.9)
+        bb = W.uniform(W.stream_key(9, "b"), np.arange(20), -1, 1)
+        st, xb, it, rel, cyc = oracle.gmres(20, B.rowptr, B.colind, B.val, bb, oracle.PREC_NONE,
+                                            None, 20, 1e-10)
+        if st != 0 or cyc != 1 or it > 20:
+            raise AssertionError("gmres one cycle")
+        xs = W.uniform(W.stream_key(8, "x"), np.arange(9000), -1, 1)
+        exact = math.fsum((xs * xs).tolist())
+        if abs(oracle.dot(xs, xs, oracle.DOT_TREE) - exact) > 9000 * 2.3e-16 * exact:
+            raise AssertionError("dot")
+    except Exception:
+        failed.append("krylov")
+    return failed
+
+
+def test_real_oracle_passes_the_compact_pins():
+    assert pins_pass() == []
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_every_planted_mistake_is_caught(name, monkeypatch):
+    import ctypes
+    with tempfile.TemporaryDirectory() as tmp:
+        so = build_mutant(name, tmp)
+        real = oracle._load()
+        mutant = ctypes.CDLL(so)
+        # give the mutant the same signatures as the real library
+        for attr in ("orc_check_pattern", "orc_symbolic", "orc_sym_status", "orc_sym_copy",
+                     "orc_sym_free", "orc_numeric", "orc_lsolve", "orc_usolve", "orc_apply",
+                     "orc_apply_t", "orc_iiluk_apply", "orc_iiluk_build", "orc_transpose",
+                     "orc_dot", "orc_spmv", "orc_gmres", "orc_adjoint"):
+            f_real, f_mut = getattr(real, attr), getattr(mutant, attr)
+            f_mut.argtypes = f_real.argtypes
+            f_mut.restype = f_real.restype
+        monkeypatch.setattr(oracle, "_lib", mutant)
+        failed = pins_pass()
+    assert failed, f"mutant {name} passed every pin"
