@@ -264,6 +264,17 @@ int iluk_spmv(const iluk_pattern *A, const double *A_val, const double *x, doubl
 int iluk_dot(int64_t n, const double *x, const double *y, double *out, void *stream);
 
 /*
+ * Elementwise q_i = a_i / b_i rounded to nearest, computed as the sweeps and
+ * the transposed sweeps divide by the diagonal (Eq. triangleSolve's division
+ * by u_ii): a double-double reciprocal of b_i, then one Markstein correction,
+ * with IEEE division for operands outside [2^-400, 2^401) in magnitude.  The
+ * results must equal IEEE division bit for bit; this call exists so that the
+ * method can be checked against it.  a, b, q: device double[n] (q may alias
+ * neither).  ILUK_EINVAL on n < 0 or a null pointer with n > 0.  Asynchronous.
+ */
+int iluk_div_rn(int64_t n, const double *a, const double *b, double *q, void *stream);
+
+/*
  * a6. Restarted GMRES(m), right preconditioned (the solver works with
  * A M^-1, Sec. 2), x0 = 0, modified Gram-Schmidt with the fixed-order inner
  * product above, Givens rotations.  Stops when |g_{j+1}| / ||b|| <= rtol and

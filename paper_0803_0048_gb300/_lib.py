@@ -77,6 +77,7 @@ SIGNATURES = [
     ("iiluk_destroy", None, [P]),
     ("iluk_spmv", I, [P, P, P, P, P]),
     ("iluk_dot", I, [I64, P, P, P, P]),
+    ("iluk_div_rn", I, [I64, P, P, P, P]),
     ("gmres_solve", I, [P, P, I, P, P, P, I, D, I, I, P, P]),
     ("iluk_adjoint_scatter", I, [P, P, P, P, P]),
     ("iluk_numeric_batched", I, [P, I64, P, P, P, P]),

@@ -222,6 +222,15 @@ def dot(x: torch.Tensor, y: torch.Tensor) -> torch.Tensor:
     return out
 
 
+def div_rn(a: torch.Tensor, b: torch.Tensor) -> torch.Tensor:
+    """a / b elementwise by the sweeps' division (double-double reciprocal
+    plus a Markstein correction); equal to IEEE division bit for bit."""
+    _check_dev(a, b)
+    q = torch.empty_like(a)
+    _call(L.load().iluk_div_rn, a.numel(), _ptr(a), _ptr(b), _ptr(q), C.c_void_p(_stream()))
+    return q
+
+
 def gmres(rowptr, colind, vals, b, prec=None, restart=30, rtol=1e-8, maxit=10000,
           transpose=False, x=None, check=True):
     """a6: right-preconditioned GMRES(m) from x0 = 0.  ``prec`` is None, a

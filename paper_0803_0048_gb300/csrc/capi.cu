@@ -427,6 +427,7 @@ void iluk_fac_destroy(iluk_fac *F) {
   dfree(F->val, s);
   dfree(F->sync, s);
   dfree(F->tmp, s);
+  dfree(F->rdiag, s);
   dfree(F->err, s);
   dfree(F->trowptr, s);
   dfree(F->tcolind, s);
@@ -446,6 +447,7 @@ static int numeric_into(iluk_fac *F, const double *A_val, iluk_info *info, cudaS
   CK(launch_fill_err(F->err, s));
   CK(launch_numeric(S, A_val, F->val, reinterpret_cast<unsigned long long *>(F->sync), F->err,
                     s));
+  CK(launch_recip_diag(S->n, S->diag, F->val, F->rdiag, s));
   int64_t row;
   int st = read_err(F->err, s, &row, nullptr);
   CK(launch_fill_err(F->err, s));
@@ -469,6 +471,7 @@ int iluk_numeric(const iluk_sym *S, const double *A_val, iluk_fac **out, iluk_in
   cudaError_t e = dalloc(&F->val, S->nnz, s);
   if (e == cudaSuccess) e = dalloc(&F->sync, sweep_sync_ints(S->n), s);
   if (e == cudaSuccess) e = dalloc(&F->tmp, S->n, s);
+  if (e == cudaSuccess) e = dalloc(&F->rdiag, S->n, s);
   if (e == cudaSuccess) e = dalloc(&F->err, 2, s);
   if (e == cudaSuccess) e = launch_fill_pending(S->n, F->tmp, s);
   if (e != cudaSuccess) {
@@ -569,11 +572,11 @@ static int pick_schedule(iluk_fac *F, cudaStream_t s) {
       // level orders the real applies use
       LevelOrder none;
       cudaEventRecord(e0, s);
-      launch_apply(S->n, S->rowptr, S->colind, S->diag, F->val, S->lord, none, p, F->tmp, y, 0,
-                   sched, F->err, s);
+      launch_apply(S->n, S->rowptr, S->colind, S->diag, F->val, F->rdiag, S->lord, none, p,
+                   F->tmp, y, 0, sched, F->err, s);
       cudaEventRecord(e1, s);
-      launch_apply(S->n, S->rowptr, S->colind, S->diag, F->val, none, S->uord, p, F->tmp, y, 0,
-                   sched, F->err, s);
+      launch_apply(S->n, S->rowptr, S->colind, S->diag, F->val, F->rdiag, none, S->uord, p,
+                   F->tmp, y, 0, sched, F->err, s);
       cudaEventRecord(e2, s);
       cudaEventSynchronize(e2);
       float a = 0, b = 0;
@@ -616,11 +619,11 @@ int iluk_apply_sched(iluk_fac *F, const double *p, double *y, int transpose, int
   if (transpose) {
     int st = ensure_transpose(F, s);
     if (st != ILUK_OK) return st;
-    CK(launch_apply(S->n, F->trowptr, F->tcolind, F->tdiag, F->tval, F->tlord, F->tuord, p,
-                    F->tmp, y, 1, sched, F->err, s));
+    CK(launch_apply(S->n, F->trowptr, F->tcolind, F->tdiag, F->tval, F->rdiag, F->tlord,
+                    F->tuord, p, F->tmp, y, 1, sched, F->err, s));
   } else {
-    CK(launch_apply(S->n, S->rowptr, S->colind, S->diag, F->val, S->lord, S->uord, p, F->tmp, y,
-                    0, sched, F->err, s));
+    CK(launch_apply(S->n, S->rowptr, S->colind, S->diag, F->val, F->rdiag, S->lord, S->uord, p,
+                    F->tmp, y, 0, sched, F->err, s));
   }
   return ILUK_OK;
 }
@@ -713,6 +716,13 @@ int iluk_spmv(const iluk_pattern *A, const double *A_val, const double *x, doubl
   iluk_info *info = nullptr;
   if (!A) return ILUK_EINVAL;
   CK(launch_spmv(A->n, A->rowptr, A->colind, A_val, x, y, nullptr, (cudaStream_t)stream));
+  return ILUK_OK;
+}
+
+int iluk_div_rn(int64_t n, const double *a, const double *b, double *q, void *stream) {
+  iluk_info *info = nullptr;
+  if (n < 0 || (n > 0 && (!a || !b || !q))) return ILUK_EINVAL;
+  CK(launch_div_check(n, a, b, q, (cudaStream_t)stream));
   return ILUK_OK;
 }
 
@@ -996,10 +1006,10 @@ int gmres_solve(const iluk_pattern *A, const double *A_val, int prec_kind, void 
   auto precond = [&](const double *in, double *outv) -> cudaError_t {
     if (F) {
       if (transpose)
-        return launch_apply(n, F->trowptr, F->tcolind, F->tdiag, F->tval, F->tlord, F->tuord,
-                            in, F->tmp, outv, 1, sched, F->err, s);
-      return launch_apply(n, F->S->rowptr, F->S->colind, F->S->diag, F->val, F->S->lord,
-                          F->S->uord, in, F->tmp, outv, 0, sched, F->err, s);
+        return launch_apply(n, F->trowptr, F->tcolind, F->tdiag, F->tval, F->rdiag, F->tlord,
+                            F->tuord, in, F->tmp, outv, 1, sched, F->err, s);
+      return launch_apply(n, F->S->rowptr, F->S->colind, F->S->diag, F->val, F->rdiag,
+                          F->S->lord, F->S->uord, in, F->tmp, outv, 0, sched, F->err, s);
     }
     if (M) return launch_iiluk_apply(M->S, M->g, in, M->tmp, outv, s);
     return cudaMemcpyAsync(outv, in, n * sizeof(double), cudaMemcpyDeviceToDevice, s);

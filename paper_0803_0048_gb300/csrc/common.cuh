@@ -115,4 +115,39 @@ __device__ __forceinline__ double add_prod(double acc, double a, double b) {
   return __dadd_rn(acc, __dmul_rn(a, b));
 }
 
+// Correctly rounded division from a precomputed reciprocal.
+//
+// recip_dd(b) = (y, t): y = RN(1/b), and t = RN(e*y) with e = 1 - b*y (exact:
+// the residual of a correctly rounded reciprocal is representable), so that
+// y + t = 1/b within a relative 2^-104.  Then for a dividend a
+//   q0 = RN(a*y + RN(a*t))      is within 1/2 ulp + 2^-104 of a/b: faithful,
+//   r  = a - b*q0               is exact (fma) because q0 is faithful,
+//   q  = RN(q0 + r*y)           is RN(a/b) by Markstein's theorem (P. Markstein,
+//                               IBM J. Res. Dev. 34(1), 1990; J.-M. Muller et
+//                               al., Handbook of Floating-Point Arithmetic,
+//                               ch. 4), y being within 1/2 ulp of 1/b.
+// Four dependent FP64 operations instead of a full IEEE division on the
+// critical path.  The argument assumes no intermediate underflows or
+// overflows: both operands must have magnitudes in [2^-400, 2^401), else
+// (zero, subnormal, huge, infinite, NaN) the quotient comes from __ddiv_rn.
+// recip_dd marks such a divisor with y = 0.
+__device__ __forceinline__ bool dd_in_range(double x) {
+  const unsigned ex = ((unsigned)__double2hiint(x) >> 20) & 0x7ffu;
+  return ex - 623u <= 800u;  // biased exponent in [1023-400, 1023+400]
+}
+
+__device__ __forceinline__ double2 recip_dd(double b) {
+  if (!dd_in_range(b)) return make_double2(0.0, 0.0);
+  const double y = __drcp_rn(b);
+  const double e = __fma_rn(-b, y, 1.0);
+  return make_double2(y, __dmul_rn(e, y));
+}
+
+__device__ __forceinline__ double div_rn_recip(double a, double b, double2 rb) {
+  if (rb.x == 0.0 || !dd_in_range(a)) return __ddiv_rn(a, b);
+  const double q0 = __fma_rn(a, rb.x, __dmul_rn(a, rb.y));
+  const double r = __fma_rn(-b, q0, a);
+  return __fma_rn(r, rb.x, q0);
+}
+
 }  // namespace iluk

@@ -35,6 +35,7 @@ struct iluk_fac {
   double *val = nullptr;          // F values
   int *sync = nullptr;            // tickets + flags for sweeps: see sweeps.cu
   double *tmp = nullptr;          // intermediate vector of the two sweeps
+  double2 *rdiag = nullptr;       // double-double reciprocals of the diagonal
   iluk::DevErr *err = nullptr;    // status of asynchronous calls
   // explicit transpose of F for (L~U~)^-T, built on first use
   int64_t *trowptr = nullptr;
@@ -116,10 +117,15 @@ size_t sweep_sync_ints(int64_t n);
 // y = (LU)^-1 p (or ^-T on the transposed arrays).  tmp must hold the pending
 // marker in every entry on entry, and does again on exit.
 cudaError_t launch_apply(int64_t n, const int64_t *rp, const int32_t *ci, const int64_t *dg,
-                         const double *v, const LevelOrder &fwd, const LevelOrder &bwd,
+                         const double *v, const double2 *rd, const LevelOrder &fwd,
+                         const LevelOrder &bwd,
                          const double *p, double *tmp, double *y, int transpose, int sched,
                          DevErr *err, cudaStream_t s);
 cudaError_t launch_fill_pending(int64_t n, double *x, cudaStream_t s);
+cudaError_t launch_recip_diag(int64_t n, const int64_t *dg, const double *v, double2 *rd,
+                              cudaStream_t s);
+cudaError_t launch_div_check(int64_t n, const double *a, const double *b, double *q,
+                             cudaStream_t s);
 cudaError_t launch_transpose(int64_t n, int64_t nnz, const int64_t *rp, const int32_t *ci,
                              const double *v, int64_t *trp, int32_t *tci, double *tv,
                              int64_t *tdiag, int32_t *cursor, int64_t *scan_tmp, cudaStream_t s);

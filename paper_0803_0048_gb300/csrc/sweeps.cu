@@ -75,8 +75,8 @@ template <bool FORWARD, bool DIVIDE, bool GPU_SCOPE, int W>
 __global__ void __launch_bounds__(GPU_SCOPE ? kGridThreads : kCtaThreads)
 k_sweep(const int32_t *__restrict__ order, int64_t len, const int64_t *__restrict__ rp,
         const int32_t *__restrict__ ci, const int64_t *__restrict__ dg,
-        const double *__restrict__ v, const double *in, double *out, double *clear, DevErr *err,
-        int64_t limit_ns) {
+        const double *__restrict__ v, const double2 *__restrict__ rd, const double *in,
+        double *out, double *clear, DevErr *err, int64_t limit_ns) {
   const int lane = threadIdx.x & 31;
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -88,9 +88,14 @@ k_sweep(const int32_t *__restrict__ order, int64_t len, const int64_t *__restric
     // always subtracted last.
     int64_t first = 0, d = 0;
     int mylen = 0;
-    double s = 0.0;
+    double s = 0.0, dv = 1.0;
+    double2 rr = make_double2(0.0, 0.0);
     if (row >= 0) {
       d = dg[row];
+      if (DIVIDE) {  // fetched now, off the chain's critical path
+        dv = v[d];
+        rr = rd[row];
+      }
       if (FORWARD) {
         first = rp[row];
         mylen = (int)(d - first);
@@ -173,7 +178,7 @@ k_sweep(const int32_t *__restrict__ order, int64_t len, const int64_t *__restric
       if (row >= 0) set_err(err, row, ILUK_ETIMEOUT);
       return;
     }
-    if (DIVIDE && row >= 0) s = __ddiv_rn(s, v[d]);
+    if (DIVIDE && row >= 0) s = div_rn_recip(s, dv, rr);
     if (row >= 0) {
       if ((unsigned long long)__double_as_longlong(s) == kPending)
         s = __longlong_as_double((long long)kQuietNaN);
@@ -220,8 +225,9 @@ template <bool FORWARD, bool DIVIDE, int W>
 __global__ void __launch_bounds__(kCtaThreads, 1)
 k_sweep_cluster(const int32_t *__restrict__ order, int64_t len, int64_t n,
                 const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
-                const int64_t *__restrict__ dg, const double *__restrict__ v, const double *in,
-                double *out, double *clear, DevErr *err, int64_t limit_ns) {
+                const int64_t *__restrict__ dg, const double *__restrict__ v,
+                const double2 *__restrict__ rd, const double *in, double *out, double *clear,
+                DevErr *err, int64_t limit_ns) {
   extern __shared__ __align__(16) double xs[];  // this CTA's slice of x
   __shared__ int sfail;
   unsigned rank, C;
@@ -242,9 +248,14 @@ k_sweep_cluster(const int32_t *__restrict__ order, int64_t len, int64_t n,
     const int64_t row = order[slot0 + lane];
     int64_t first = 0, d = 0;
     int mylen = 0;
-    double s = 0.0;
+    double s = 0.0, dv = 1.0;
+    double2 rr = make_double2(0.0, 0.0);
     if (row >= 0) {
       d = dg[row];
+      if (DIVIDE) {  // fetched now, off the chain's critical path
+        dv = v[d];
+        rr = rd[row];
+      }
       if (FORWARD) {
         first = rp[row];
         mylen = (int)(d - first);
@@ -327,7 +338,7 @@ k_sweep_cluster(const int32_t *__restrict__ order, int64_t len, int64_t n,
       }
       break;
     }
-    if (DIVIDE && row >= 0) s = __ddiv_rn(s, v[d]);
+    if (DIVIDE && row >= 0) s = div_rn_recip(s, dv, rr);
     if (row >= 0) {
       if ((unsigned long long)__double_as_longlong(s) == kPending)
         s = __longlong_as_double((long long)kQuietNaN);
@@ -364,8 +375,9 @@ template <bool FORWARD, bool DIVIDE, int SCOPE>
 __global__ void __launch_bounds__(kCtaThreads, 1)
 k_sweep_wpr(const int32_t *__restrict__ order, int64_t len, int64_t n,
             const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
-            const int64_t *__restrict__ dg, const double *__restrict__ v, const double *in,
-            double *out, double *clear, DevErr *err, int64_t limit_ns) {
+            const int64_t *__restrict__ dg, const double *__restrict__ v,
+            const double2 *__restrict__ rd, const double *in, double *out, double *clear,
+            DevErr *err, int64_t limit_ns) {
   extern __shared__ __align__(16) double xs[];
   unsigned rank = 0, C = 1, base = 0;
   int64_t slice = 0;
@@ -388,6 +400,12 @@ k_sweep_wpr(const int32_t *__restrict__ order, int64_t len, int64_t n,
     const int64_t row = order[slot];
     if (row < 0) continue;
     const int64_t d = dg[row];
+    double dv = 1.0;
+    double2 rr = make_double2(0.0, 0.0);
+    if (DIVIDE) {  // fetched now, off the chain's critical path
+      dv = v[d];
+      rr = rd[row];
+    }
     const int64_t first = FORWARD ? rp[row] : rp[row + 1] - 1;
     const int mylen = (int)(FORWARD ? d - first : first - d);
     constexpr int64_t step = FORWARD ? 1 : -1;
@@ -441,7 +459,7 @@ k_sweep_wpr(const int32_t *__restrict__ order, int64_t len, int64_t n,
       if (lane == 0) set_err(err, row, ILUK_ETIMEOUT);
       break;
     }
-    if (DIVIDE) s = __ddiv_rn(s, v[d]);
+    if (DIVIDE) s = div_rn_recip(s, dv, rr);
     if ((unsigned long long)__double_as_longlong(s) == kPending)
       s = __longlong_as_double((long long)kQuietNaN);
     if (lane == 0) {
@@ -473,6 +491,47 @@ cudaError_t launch_fill_pending(int64_t n, double *x, cudaStream_t s) {
   const int64_t cap = (int64_t)num_sms() * 8;
   if (b > cap) b = cap;
   k_fill_pending<<<(unsigned)b, 256, 0, s>>>(n, x);
+  note_launch();
+  return cudaGetLastError();
+}
+
+// Double-double reciprocals of the diagonal, one per row (see recip_dd): the
+// divisions of the sweeps then cost four dependent FP64 operations.  Computed
+// once per set of factor values; the diagonal of row i of F^T is f_ii, so the
+// same array serves the transposed sweeps.
+__global__ void k_recip_diag(int64_t n, const int64_t *__restrict__ dg,
+                             const double *__restrict__ v, double2 *__restrict__ rd) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    rd[i] = recip_dd(v[dg[i]]);
+}
+
+cudaError_t launch_recip_diag(int64_t n, const int64_t *dg, const double *v, double2 *rd,
+                              cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  int64_t b = (n + 255) / 256;
+  const int64_t cap = (int64_t)num_sms() * 8;
+  if (b > cap) b = cap;
+  k_recip_diag<<<(unsigned)b, 256, 0, s>>>(n, dg, v, rd);
+  note_launch();
+  return cudaGetLastError();
+}
+
+// q_i = a_i / b_i through recip_dd + div_rn_recip, the sweeps' division.
+__global__ void k_div_check(int64_t n, const double *__restrict__ a,
+                            const double *__restrict__ b, double *__restrict__ q) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    q[i] = div_rn_recip(a[i], b[i], recip_dd(b[i]));
+}
+
+cudaError_t launch_div_check(int64_t n, const double *a, const double *b, double *q,
+                             cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  int64_t g = (n + 255) / 256;
+  const int64_t cap = (int64_t)num_sms() * 8;
+  if (g > cap) g = cap;
+  k_div_check<<<(unsigned)g, 256, 0, s>>>(n, a, b, q);
   note_launch();
   return cudaGetLastError();
 }
@@ -532,8 +591,8 @@ template <typename K>
 static cudaError_t launch_on_cluster(K kern, int C, size_t smem, cudaStream_t s,
                                      const int32_t *order, int64_t len, int64_t n,
                                      const int64_t *rp, const int32_t *ci, const int64_t *dg,
-                                     const double *v, const double *in, double *out,
-                                     double *clear, DevErr *err, int64_t limit) {
+                                     const double *v, const double2 *rd, const double *in,
+                                     double *out, double *clear, DevErr *err, int64_t limit) {
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
@@ -550,23 +609,25 @@ static cudaError_t launch_on_cluster(K kern, int C, size_t smem, cudaStream_t s,
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  e = cudaLaunchKernelEx(&cfg, kern, order, len, n, rp, ci, dg, v, in, out, clear, err, limit);
+  e = cudaLaunchKernelEx(&cfg, kern, order, len, n, rp, ci, dg, v, rd, in, out, clear, err,
+                         limit);
   note_launch();
   return e;
 }
 
 template <bool FORWARD, bool DIVIDE>
 static cudaError_t run_sweep(int64_t n, const LevelOrder &lo, const int64_t *rp, const int32_t *ci,
-                             const int64_t *dg, const double *v, const double *in, double *out,
-                             double *clear, int sched, DevErr *err, cudaStream_t s) {
+                             const int64_t *dg, const double *v, const double2 *rd,
+                             const double *in, double *out, double *clear, int sched, DevErr *err,
+                             cudaStream_t s) {
   ProfScope prof_scope(FORWARD ? ILUK_PROF_SWEEP : ILUK_PROF_SWEEP_BWD, s);
   if (lo.len == 0) return cudaSuccess;
   int64_t limit = wait_limit();
   const int32_t *order = lo.order;
   int64_t len = lo.len;
   if (sched == ILUK_SCHED_SINGLE_CTA) {
-    k_sweep<FORWARD, DIVIDE, false, 4><<<1, kCtaThreads, 0, s>>>(order, len, rp, ci, dg, v, in,
-                                                                out, clear, err, limit);
+    k_sweep<FORWARD, DIVIDE, false, 4><<<1, kCtaThreads, 0, s>>>(order, len, rp, ci, dg, v, rd,
+                                                                in, out, clear, err, limit);
     note_launch();
     return cudaGetLastError();
   }
@@ -578,9 +639,9 @@ static cudaError_t run_sweep(int64_t n, const LevelOrder &lo, const int64_t *rp,
     const size_t smem = (size_t)((n + C - 1) / C) * sizeof(double);
     if (wpr)
       return launch_on_cluster(k_sweep_wpr<FORWARD, DIVIDE, 1>, C, smem, s, order, len, n, rp, ci,
-                               dg, v, in, out, clear, err, limit);
+                               dg, v, rd, in, out, clear, err, limit);
     return launch_on_cluster(k_sweep_cluster<FORWARD, DIVIDE, 4>, C, smem, s, order, len, n, rp,
-                             ci, dg, v, in, out, clear, err, limit);
+                             ci, dg, v, rd, in, out, clear, err, limit);
   }
   if (sched == ILUK_SCHED_WARP_GRID) {
     auto kern = k_sweep_wpr<FORWARD, DIVIDE, 0>;
@@ -592,8 +653,8 @@ static cudaError_t run_sweep(int64_t n, const LevelOrder &lo, const int64_t *rp,
     if (grid > want) grid = want;
     const int64_t nn = n;
     void *args[] = {(void *)&order, (void *)&len, (void *)&nn, (void *)&rp, (void *)&ci,
-                    (void *)&dg, (void *)&v, (void *)&in, (void *)&out, (void *)&clear,
-                    (void *)&err, (void *)&limit};
+                    (void *)&dg, (void *)&v, (void *)&rd, (void *)&in, (void *)&out,
+                    (void *)&clear, (void *)&err, (void *)&limit};
     cudaError_t e = cudaLaunchCooperativeKernel((const void *)kern, dim3((unsigned)grid),
                                                 dim3(kCtaThreads), args, 0, s);
     note_launch();
@@ -610,8 +671,8 @@ static cudaError_t run_sweep(int64_t n, const LevelOrder &lo, const int64_t *rp,
   const int64_t want = (len + kGridThreads - 1) / kGridThreads;  // one warp per 32 slots
   if (grid > want) grid = want;
   void *args[] = {(void *)&order, (void *)&len, (void *)&rp, (void *)&ci, (void *)&dg,
-                  (void *)&v, (void *)&in, (void *)&out, (void *)&clear, (void *)&err,
-                  (void *)&limit};
+                  (void *)&v, (void *)&rd, (void *)&in, (void *)&out, (void *)&clear,
+                  (void *)&err, (void *)&limit};
   cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_sweep<FORWARD, DIVIDE, true, 8>,
                                               dim3((unsigned)grid), dim3(kGridThreads), args, 0, s);
   note_launch();
@@ -619,7 +680,8 @@ static cudaError_t run_sweep(int64_t n, const LevelOrder &lo, const int64_t *rp,
 }
 
 cudaError_t launch_apply(int64_t n, const int64_t *rp, const int32_t *ci, const int64_t *dg,
-                         const double *v, const LevelOrder &fwd, const LevelOrder &bwd,
+                         const double *v, const double2 *rd, const LevelOrder &fwd,
+                         const LevelOrder &bwd,
                          const double *p, double *tmp, double *y, int transpose, int sched,
                          DevErr *err, cudaStream_t s) {
   // sched packs the forward schedule in bits 0-7 and the backward one in 8-15
@@ -638,13 +700,13 @@ cudaError_t launch_apply(int64_t n, const int64_t *rp, const int32_t *ci, const 
   // tmp is pending on entry (left so by the previous backward sweep); the
   // forward sweep re-arms y, the backward sweep re-arms tmp.
   if (!transpose) {
-    e = run_sweep<true, false>(n, fwd, rp, ci, dg, v, p, tmp, y, sf, err, s);
+    e = run_sweep<true, false>(n, fwd, rp, ci, dg, v, rd, p, tmp, y, sf, err, s);
     if (e != cudaSuccess) return e;
-    return run_sweep<false, true>(n, bwd, rp, ci, dg, v, tmp, y, tmp, sb, err, s);
+    return run_sweep<false, true>(n, bwd, rp, ci, dg, v, rd, tmp, y, tmp, sb, err, s);
   }
-  e = run_sweep<true, true>(n, fwd, rp, ci, dg, v, p, tmp, y, sf, err, s);
+  e = run_sweep<true, true>(n, fwd, rp, ci, dg, v, rd, p, tmp, y, sf, err, s);
   if (e != cudaSuccess) return e;
-  return run_sweep<false, false>(n, bwd, rp, ci, dg, v, tmp, y, tmp, sb, err, s);
+  return run_sweep<false, false>(n, bwd, rp, ci, dg, v, rd, tmp, y, tmp, sb, err, s);
 }
 
 // ---------------------------------------------------------------------------
