@@ -556,7 +556,9 @@ static int pick_schedule(iluk_fac *F, cudaStream_t s) {
     dfree(p, s);
     return ILUK_SCHED_WARP_GRID;
   }
-  cudaMemsetAsync(p, 0, S->n * sizeof(double), s);
+  // a right-hand side of ones: realistic operands for the divisions (zeros
+  // would all take the IEEE fallback of the reciprocal division)
+  launch_fill_value(S->n, p, 1.0, s);
   float best_f = 1e30f, best_b = 1e30f;
   int pick_f = ILUK_SCHED_WARP_GRID, pick_b = ILUK_SCHED_WARP_GRID;
   const bool prof = g_prof.exchange(false);  // the trial runs are not profiled

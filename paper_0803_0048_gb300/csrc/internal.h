@@ -122,6 +122,7 @@ cudaError_t launch_apply(int64_t n, const int64_t *rp, const int32_t *ci, const 
                          const double *p, double *tmp, double *y, int transpose, int sched,
                          DevErr *err, cudaStream_t s);
 cudaError_t launch_fill_pending(int64_t n, double *x, cudaStream_t s);
+cudaError_t launch_fill_value(int64_t n, double *x, double v, cudaStream_t s);
 cudaError_t launch_recip_diag(int64_t n, const int64_t *dg, const double *v, double2 *rd,
                               cudaStream_t s);
 cudaError_t launch_div_check(int64_t n, const double *a, const double *b, double *q,

@@ -19,6 +19,7 @@
 // The transposed solve (L~U~)^-T p runs the same kernels on an explicit CSR
 // transpose T = F^T: forward with division by t_ii (U~^T), then backward with
 // unit diagonal (L~^T).
+#include <cstring>
 #include <mutex>
 
 #include "internal.h"
@@ -198,11 +199,14 @@ k_sweep(const int32_t *__restrict__ order, int64_t len, const int64_t *__restric
 // barrier even after a failure, so no CTA leaves while others may still read
 // its shared memory.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ unsigned dsm_addr(unsigned base, int64_t i, int C) {
+// The cluster width C is a power of two (lg = log2 C), so owner and slot
+// are a mask and a shift: the address is computed once per value, off the
+// polling loop.
+__device__ __forceinline__ unsigned dsm_addr(unsigned base, int64_t i, int lg) {
   unsigned a;
-  const unsigned rank = (unsigned)(i % C);
-  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(a) : "r"(base), "r"(rank));
-  return a + (unsigned)((i / C) * 8);
+  const unsigned rank = (unsigned)i & ((1u << lg) - 1u);
+  asm("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(a) : "r"(base), "r"(rank));
+  return a + ((unsigned)(i >> lg) << 3);
 }
 
 __device__ __forceinline__ double ld_dsm(unsigned a) {
@@ -233,6 +237,7 @@ k_sweep_cluster(const int32_t *__restrict__ order, int64_t len, int64_t n,
   unsigned rank, C;
   asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
   asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(C));
+  const int lg = __ffs((int)C) - 1;  // C is a power of two
   const int64_t slice = (n + C - 1) / C;
   for (int64_t j = threadIdx.x; j < slice; j += blockDim.x)
     xs[j] = __longlong_as_double((long long)kPending);
@@ -277,7 +282,7 @@ k_sweep_cluster(const int32_t *__restrict__ order, int64_t len, int64_t n,
       for (int u = 0; u < W; ++u) {
         const int e = q0 + u - off;
         if (e >= 0 && e < mylen) {
-          a[u] = dsm_addr(base, ci[first + step * e], (int)C);
+          a[u] = dsm_addr(base, ci[first + step * e], lg);
           f[u] = v[first + step * e];
         }
       }
@@ -342,7 +347,7 @@ k_sweep_cluster(const int32_t *__restrict__ order, int64_t len, int64_t n,
     if (row >= 0) {
       if ((unsigned long long)__double_as_longlong(s) == kPending)
         s = __longlong_as_double((long long)kQuietNaN);
-      st_dsm(dsm_addr(base, row, (int)C), s);
+      st_dsm(dsm_addr(base, row, lg), s);
     }
   }
   // Every CTA arrives here, so no shared memory is released while read.
@@ -366,9 +371,9 @@ k_sweep_cluster(const int32_t *__restrict__ order, int64_t len, int64_t n,
 // memory of one thread-block cluster (as k_sweep_cluster).
 // ---------------------------------------------------------------------------
 template <int SCOPE>
-__device__ __forceinline__ double wpr_load(const double *out, unsigned base, int64_t i, int C) {
+__device__ __forceinline__ double wpr_load(const double *out, unsigned da, int64_t i) {
   if (SCOPE == 0) return ld_val<true>(&out[i]);
-  return ld_dsm(dsm_addr(base, i, C));
+  return ld_dsm(da);
 }
 
 template <bool FORWARD, bool DIVIDE, int SCOPE>
@@ -380,10 +385,12 @@ k_sweep_wpr(const int32_t *__restrict__ order, int64_t len, int64_t n,
             DevErr *err, int64_t limit_ns) {
   extern __shared__ __align__(16) double xs[];
   unsigned rank = 0, C = 1, base = 0;
+  int lg = 0;
   int64_t slice = 0;
   if (SCOPE == 1) {
     asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
     asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(C));
+    lg = __ffs((int)C) - 1;  // C is a power of two
     slice = (n + C - 1) / C;
     for (int64_t j = threadIdx.x; j < slice; j += blockDim.x)
       xs[j] = __longlong_as_double((long long)kPending);
@@ -410,18 +417,21 @@ k_sweep_wpr(const int32_t *__restrict__ order, int64_t len, int64_t n,
     const int mylen = (int)(FORWARD ? d - first : first - d);
     constexpr int64_t step = FORWARD ? 1 : -1;
     double s = in[row];
+    const unsigned sa = SCOPE == 1 ? dsm_addr(base, row, lg) : 0u;  // where x_row goes
     if (clear && lane == 0) clear[row] = __longlong_as_double((long long)kPending);
     for (int b = 0; b < mylen && ok; b += 32) {
       const int e = b + lane;
       const bool act = e < mylen;
       const int cnt = (mylen - b) < 32 ? mylen - b : 32;
       int32_t c = 0;
+      unsigned da = 0;
       double f = 0.0, x = 0.0, prod = 0.0;
       bool have = !act;
       if (act) {
         c = ci[first + step * e];
         f = v[first + step * e];
-        x = wpr_load<SCOPE>(out, base, c, (int)C);
+        if (SCOPE == 1) da = dsm_addr(base, c, lg);
+        x = wpr_load<SCOPE>(out, da, c);
         if (!pending(x)) {
           prod = __dmul_rn(f, x);
           have = true;
@@ -444,10 +454,14 @@ k_sweep_wpr(const int32_t *__restrict__ order, int64_t len, int64_t n,
           ok = false;
           break;
         }
-        __nanosleep(backoff);
-        if (backoff < (SCOPE == 0 ? 128u : 64u)) backoff <<= 1;
+        // grid: back off (L2 polls compete with the stores they wait for);
+        // cluster: spin, a DSMEM poll is cheap and sleeping measured slower
+        if (SCOPE == 0) {
+          __nanosleep(backoff);
+          if (backoff < 128u) backoff <<= 1;
+        }
         if (!have) {
-          x = wpr_load<SCOPE>(out, base, c, (int)C);
+          x = wpr_load<SCOPE>(out, da, c);
           if (!pending(x)) {
             prod = __dmul_rn(f, x);
             have = true;
@@ -466,7 +480,7 @@ k_sweep_wpr(const int32_t *__restrict__ order, int64_t len, int64_t n,
       if (SCOPE == 0)
         st_val<true>(&out[row], s);
       else
-        st_dsm(dsm_addr(base, row, (int)C), s);
+        st_dsm(sa, s);
     }
     __syncwarp();
   }
@@ -479,20 +493,30 @@ k_sweep_wpr(const int32_t *__restrict__ order, int64_t len, int64_t n,
   }
 }
 
-__global__ void k_fill_pending(int64_t n, double *x) {
+__global__ void k_fill_pending(int64_t n, double *x, unsigned long long bits) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
-    x[i] = __longlong_as_double((long long)kPending);
+    x[i] = __longlong_as_double((long long)bits);
 }
 
-cudaError_t launch_fill_pending(int64_t n, double *x, cudaStream_t s) {
+static cudaError_t fill_bits(int64_t n, double *x, unsigned long long bits, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   int64_t b = (n + 255) / 256;
   const int64_t cap = (int64_t)num_sms() * 8;
   if (b > cap) b = cap;
-  k_fill_pending<<<(unsigned)b, 256, 0, s>>>(n, x);
+  k_fill_pending<<<(unsigned)b, 256, 0, s>>>(n, x, bits);
   note_launch();
   return cudaGetLastError();
+}
+
+cudaError_t launch_fill_pending(int64_t n, double *x, cudaStream_t s) {
+  return fill_bits(n, x, kPending, s);
+}
+
+cudaError_t launch_fill_value(int64_t n, double *x, double v, cudaStream_t s) {
+  unsigned long long bits;
+  std::memcpy(&bits, &v, sizeof bits);
+  return fill_bits(n, x, bits, s);
 }
 
 // Double-double reciprocals of the diagonal, one per row (see recip_dd): the
