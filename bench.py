@@ -35,8 +35,6 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "ILU(k) factor+apply ms & HBM GB/s (% peak); batched/adjoint vs plain, 1e-8 res"
-SCHED_NAMES = ["auto", "lockstep_grid", "lockstep_cta", "lockstep_cluster", "warp_grid",
-               "warp_cluster"]
 L2_BYTES = 129 * 1024 * 1024
 
 
@@ -273,8 +271,8 @@ def ours(args):
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
         "gmres": {"iters": info.iters, "relres": info.relres,
-                  "sweep_schedule": {"forward": SCHED_NAMES[sched[0] & 0xff],
-                                     "backward": SCHED_NAMES[(sched[0] >> 8) & 0xff]}},
+                  "sweep_schedule": {"forward": L.sched_name(sched[0] & 0xff),
+                                     "backward": L.sched_name((sched[0] >> 8) & 0xff)}},
         "kernels": per_kind,
     }
 

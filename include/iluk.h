@@ -104,11 +104,16 @@ enum { ILUK_PREC_NONE = 0, ILUK_PREC_ILU = 1, ILUK_PREC_IILU = 2 };
 /* Sweep schedules (all give bit-identical results): rows of a level in
  * lockstep warps over all SMs (FLAGS), on one SM (SINGLE_CTA) or on one
  * thread-block cluster (CLUSTER); one warp per row over all SMs (WARP_GRID)
- * or on one cluster (WARP_CLUSTER).  AUTO times them and keeps the fastest. */
+ * or on one cluster (WARP_CLUSTER).  AUTO times them and keeps the fastest.
+ * A schedule byte holds the kind in bits 0-3 and, for the two warp-per-row
+ * kinds, the threads per CTA / 128 in bits 4-7 (0: 1024 threads; for
+ * WARP_GRID a non-zero width also means one CTA per SM), which bounds how
+ * many rows are in flight: ILUK_SCHED_WIDTH(ILUK_SCHED_WARP_CLUSTER, 512). */
 enum {
   ILUK_SCHED_AUTO = 0, ILUK_SCHED_FLAGS = 1, ILUK_SCHED_SINGLE_CTA = 2, ILUK_SCHED_CLUSTER = 3,
   ILUK_SCHED_WARP_GRID = 4, ILUK_SCHED_WARP_CLUSTER = 5
 };
+#define ILUK_SCHED_WIDTH(kind, threads) ((kind) | (((threads) / 128) << 4))
 
 const char *iluk_strerror(int status);
 
@@ -195,7 +200,8 @@ void iluk_fac_destroy(iluk_fac *F);
 /*
  * a4. Preconditioner application (Eq. triangleSolve): y = (L~U~)^-1 p by a
  * forward sweep x_i = p_i - sum_{h<i} f_ih x_h (Eq. forwardsubA, h ascending)
- * and a backward sweep y_i = (x_i - sum_{j>i} f_ij y_j) / f_ii (j ascending).
+ * and a backward sweep y_i = (x_i - sum_{j>i} f_ij y_j) / f_ii (j descending:
+ * each row read right to left, the mirror image of the forward sweep).
  * With transpose != 0: y = (L~U~)^-T p = L~^-T U~^-T p on the explicit
  * transpose of F (built on the first transposed call; make that first call
  * outside any stream capture).  p, y: device double[n]; p and y may alias.
@@ -204,10 +210,12 @@ void iluk_fac_destroy(iluk_fac *F);
 int iluk_apply(iluk_fac *F, const double *p, double *y, int transpose, void *stream);
 int iluk_apply_sched(iluk_fac *F, const double *p, double *y, int transpose, int sched,
                      void *stream);
-/* Fix the sweep schedule of F: one ILUK_SCHED_* value for both sweeps, or
+/* Fix the sweep schedule of F: one schedule byte for both sweeps, or
  * forward | backward << 8.  ILUK_SCHED_AUTO (the default) lets the first
- * application outside a stream capture time every schedule on each sweep and
- * keep the fastest (iluk_get_schedule then returns the packed pair). */
+ * application outside a stream capture time every schedule (and, for the
+ * warp-per-row kinds, several CTA widths) on each sweep and keep the fastest
+ * (iluk_get_schedule then returns the packed pair).  An unknown kind or width
+ * falls back to WARP_GRID or 1024 threads. */
 int iluk_set_schedule(iluk_fac *F, int sched);
 int iluk_get_schedule(const iluk_fac *F);
 

@@ -16,6 +16,20 @@ LIB_PATH = os.path.join(HERE, "_build", "libiluk.so")
 OK, EINVAL, EPATTERN, ENODIAG, EZEROPIVOT, ENONFINITE, ENOMEM, ETIMEOUT, ENOCONV, ECUDA = range(10)
 PREC_NONE, PREC_ILU, PREC_IILU = 0, 1, 2
 SCHED_AUTO, SCHED_FLAGS, SCHED_SINGLE_CTA, SCHED_CLUSTER, SCHED_WARP_GRID, SCHED_WARP_CLUSTER = 0, 1, 2, 3, 4, 5
+_SCHED_NAMES = ["auto", "lockstep_grid", "lockstep_cta", "lockstep_cluster", "warp_grid",
+                "warp_cluster"]
+
+
+def sched_width(kind: int, threads: int) -> int:
+    """Schedule byte of a warp-per-row kind at `threads` per CTA (ILUK_SCHED_WIDTH)."""
+    return kind | ((threads // 128) << 4)
+
+
+def sched_name(byte: int) -> str:
+    """Readable name of one schedule byte, e.g. 'warp_cluster/512'."""
+    kind, w = byte & 0xF, (byte >> 4) & 0xF
+    name = _SCHED_NAMES[kind] if kind < len(_SCHED_NAMES) else f"kind{kind}"
+    return f"{name}/{w * 128}" if w else name
 PROF_KINDS = ["validate", "symbolic", "compact", "depth", "numeric", "sweep", "transpose",
               "iilu_build", "iilu_apply", "spmv", "dot", "vector", "sweep_bwd", "batch"]
 

@@ -242,6 +242,8 @@ void iluk_sym_destroy(iluk_sym *S) {
   dfree(S->a2f, s);
   dfree(S->lord.order, s);
   dfree(S->uord.order, s);
+  dfree(S->lord.corder, s);
+  dfree(S->uord.corder, s);
   dfree(S->lord.lstart, s);
   dfree(S->uord.lstart, s);
   delete S;
@@ -435,6 +437,8 @@ void iluk_fac_destroy(iluk_fac *F) {
   dfree(F->tval, s);
   dfree(F->tlord.order, s);
   dfree(F->tuord.order, s);
+  dfree(F->tlord.corder, s);
+  dfree(F->tuord.corder, s);
   dfree(F->tlord.lstart, s);
   dfree(F->tuord.lstart, s);
   delete F;
@@ -542,9 +546,10 @@ static int ensure_transpose(iluk_fac *F, cudaStream_t s) {
   return ILUK_OK;
 }
 
-// Autotuner: time every sweep schedule once on this factorization, forward
-// and backward sweeps separately, and keep the fastest of each (packed as
-// forward | backward << 8).  Skipped while the stream is being captured.
+// Autotuner: time every sweep schedule (the warp-per-row ones at several CTA
+// widths) on this factorization, forward and backward sweeps separately, and
+// keep the fastest of each (packed as forward | backward << 8).  Skipped
+// while the stream is being captured.
 static int pick_schedule(iluk_fac *F, cudaStream_t s) {
   if (F->sched != ILUK_SCHED_AUTO) return F->sched;
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -566,8 +571,20 @@ static int pick_schedule(iluk_fac *F, cudaStream_t s) {
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   cudaEventCreate(&e2);
-  for (int sched : {ILUK_SCHED_FLAGS, ILUK_SCHED_SINGLE_CTA, ILUK_SCHED_CLUSTER,
-                    ILUK_SCHED_WARP_GRID, ILUK_SCHED_WARP_CLUSTER}) {
+  // the warp-per-row kinds at several CTA widths: fewer warps keep fewer
+  // rows in flight (less polling), more warps start each row earlier
+  const int candidates[] = {ILUK_SCHED_FLAGS,
+                            ILUK_SCHED_SINGLE_CTA,
+                            ILUK_SCHED_CLUSTER,
+                            ILUK_SCHED_WARP_GRID,
+                            ILUK_SCHED_WIDTH(ILUK_SCHED_WARP_GRID, 512),
+                            ILUK_SCHED_WIDTH(ILUK_SCHED_WARP_GRID, 256),
+                            ILUK_SCHED_WARP_CLUSTER,
+                            ILUK_SCHED_WIDTH(ILUK_SCHED_WARP_CLUSTER, 768),
+                            ILUK_SCHED_WIDTH(ILUK_SCHED_WARP_CLUSTER, 512),
+                            ILUK_SCHED_WIDTH(ILUK_SCHED_WARP_CLUSTER, 384),
+                            ILUK_SCHED_WIDTH(ILUK_SCHED_WARP_CLUSTER, 256)};
+  for (int sched : candidates) {
     float mf = 1e30f, mb = 1e30f;
     for (int rep = 0; rep < 3; ++rep) {
       // the forward sweep alone, then the backward sweep alone, on the same
@@ -635,9 +652,15 @@ int iluk_apply(iluk_fac *F, const double *p, double *y, int transpose, void *str
 }
 
 int iluk_set_schedule(iluk_fac *F, int sched) {
-  const int sf = sched & 0xff, sb = (sched >> 8) & 0xff;
-  if (!F || sched < 0 || sched > 0xffff || sf > ILUK_SCHED_WARP_CLUSTER ||
-      sb > ILUK_SCHED_WARP_CLUSTER)
+  // a schedule byte: a kind, plus a width (256..1024 threads) for the
+  // warp-per-row kinds only
+  auto valid = [](int b) {
+    const int kind = b & 0xf, w = (b >> 4) & 0xf;
+    if (kind > ILUK_SCHED_WARP_CLUSTER) return false;
+    return w == 0 || ((kind == ILUK_SCHED_WARP_GRID || kind == ILUK_SCHED_WARP_CLUSTER) &&
+                      w >= 2 && w <= 8);
+  };
+  if (!F || sched < 0 || sched > 0xffff || !valid(sched & 0xff) || !valid((sched >> 8) & 0xff))
     return ILUK_EINVAL;
   F->sched = sched;
   return ILUK_OK;

@@ -9,10 +9,12 @@
 // Rows of one sweep DAG in level order, every level padded with -1 to a
 // multiple of 32 entries (see levels.cu).
 struct LevelOrder {
-  int32_t *order = nullptr;
+  int32_t *order = nullptr;   // levels padded to multiples of 32 slots (-1 fills)
   int64_t *lstart = nullptr;  // int64[nlev+1]: first slot of each level
   int64_t len = 0;
   int32_t nlev = 0;
+  int32_t *corder = nullptr;  // the same rows without padding (clen = rows)
+  int64_t clen = 0;
 };
 
 // Handle layouts (opaque in the public header).

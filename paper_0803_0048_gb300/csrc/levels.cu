@@ -119,14 +119,16 @@ static unsigned grid_for(int64_t n) {
   return (unsigned)(b < 1 ? 1 : b);
 }
 
-// Padded level order from depths (synchronous).
+// Padded level order from depths, and the same order without padding
+// (synchronous).
 static int order_from_depth(int64_t n, const int32_t *depth, int32_t nlev, LevelOrder *lo,
                             cudaStream_t s) {
   int32_t *cnt = nullptr, *cursor = nullptr;
-  int64_t *lstart = nullptr, *scan_tmp = nullptr;
+  int64_t *lstart = nullptr, *scan_tmp = nullptr, *cstart = nullptr;
   auto cleanup = [&]() {
     if (cnt) cudaFreeAsync(cnt, s);
     if (cursor) cudaFreeAsync(cursor, s);
+    if (cstart) cudaFreeAsync(cstart, s);
     if (scan_tmp) cudaFreeAsync(scan_tmp, s);
   };
 #define CKL(call)                              \
@@ -134,6 +136,9 @@ static int order_from_depth(int64_t n, const int32_t *depth, int32_t nlev, Level
     if ((call) != cudaSuccess) {               \
       cleanup();                               \
       if (lstart) cudaFreeAsync(lstart, s);    \
+      if (lo->order) cudaFreeAsync(lo->order, s); \
+      if (lo->corder) cudaFreeAsync(lo->corder, s); \
+      lo->order = lo->corder = nullptr;        \
       return ILUK_ECUDA;                       \
     }                                          \
   } while (0)
@@ -143,8 +148,10 @@ static int order_from_depth(int64_t n, const int32_t *depth, int32_t nlev, Level
   CKL(cudaMallocAsync((void **)&scan_tmp, (size_t)scan_tmp_elems(nlev) * sizeof(int64_t), s));
   CKL(cudaMemsetAsync(cnt, 0, (size_t)nlev * sizeof(int32_t), s));
   CKL(cudaMemsetAsync(cursor, 0, (size_t)nlev * sizeof(int32_t), s));
+  CKL(cudaMallocAsync((void **)&cstart, ((size_t)nlev + 1) * sizeof(int64_t), s));
   k_level_count<<<grid_for(n), 256, 0, s>>>(n, depth, cnt);
   note_launch();
+  CKL(launch_scan_lengths(nlev, cnt, cstart, scan_tmp, s));  // unpadded level starts
   k_level_pad<<<grid_for(nlev), 256, 0, s>>>(nlev, cnt);
   note_launch();
   CKL(launch_scan_lengths(nlev, cnt, lstart, scan_tmp, s));
@@ -155,12 +162,17 @@ static int order_from_depth(int64_t n, const int32_t *depth, int32_t nlev, Level
   CKL(cudaMemsetAsync(lo->order, 0xff, (size_t)len * sizeof(int32_t), s));
   k_level_scatter<<<grid_for(n), 256, 0, s>>>(n, depth, lstart, cursor, lo->order);
   note_launch();
+  CKL(cudaMallocAsync((void **)&lo->corder, (size_t)n * sizeof(int32_t), s));
+  CKL(cudaMemsetAsync(cursor, 0, (size_t)nlev * sizeof(int32_t), s));
+  k_level_scatter<<<grid_for(n), 256, 0, s>>>(n, depth, cstart, cursor, lo->corder);
+  note_launch();
   CKL(cudaGetLastError());
 #undef CKL
   cleanup();
   lo->lstart = lstart;
   lo->len = len;
   lo->nlev = nlev;
+  lo->clen = n;
   return ILUK_OK;
 }
 

@@ -612,7 +612,7 @@ static int cluster_width(int64_t n, K kern) {
 int cluster_size_for(int64_t n) { return cluster_width(n, k_sweep_cluster<true, false, 4>); }
 
 template <typename K>
-static cudaError_t launch_on_cluster(K kern, int C, size_t smem, cudaStream_t s,
+static cudaError_t launch_on_cluster(K kern, int C, int threads, size_t smem, cudaStream_t s,
                                      const int32_t *order, int64_t len, int64_t n,
                                      const int64_t *rp, const int32_t *ci, const int64_t *dg,
                                      const double *v, const double2 *rd, const double *in,
@@ -623,7 +623,7 @@ static cudaError_t launch_on_cluster(K kern, int C, size_t smem, cudaStream_t s,
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)C);
-  cfg.blockDim = dim3(kCtaThreads);
+  cfg.blockDim = dim3((unsigned)threads);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
@@ -649,11 +649,20 @@ static cudaError_t run_sweep(int64_t n, const LevelOrder &lo, const int64_t *rp,
   int64_t limit = wait_limit();
   const int32_t *order = lo.order;
   int64_t len = lo.len;
+  const int w = (sched >> 4) & 0xf;  // CTA width / 128 of the warp-per-row kinds
+  const int threads = w ? w * 128 : kCtaThreads;
+  sched &= 0xf;
   if (sched == ILUK_SCHED_SINGLE_CTA) {
     k_sweep<FORWARD, DIVIDE, false, 4><<<1, kCtaThreads, 0, s>>>(order, len, rp, ci, dg, v, rd,
                                                                 in, out, clear, err, limit);
     note_launch();
     return cudaGetLastError();
+  }
+  if (sched == ILUK_SCHED_WARP_GRID || sched == ILUK_SCHED_WARP_CLUSTER) {
+    // one warp per row needs no warp-aligned levels: the unpadded order keeps
+    // every warp's next row further ahead and wastes no slot loads
+    order = lo.corder;
+    len = lo.clen;
   }
   if (sched == ILUK_SCHED_CLUSTER || sched == ILUK_SCHED_WARP_CLUSTER) {
     const bool wpr = sched == ILUK_SCHED_WARP_CLUSTER;
@@ -662,25 +671,27 @@ static cudaError_t run_sweep(int64_t n, const LevelOrder &lo, const int64_t *rp,
     if (C == 0) return cudaErrorInvalidConfiguration;
     const size_t smem = (size_t)((n + C - 1) / C) * sizeof(double);
     if (wpr)
-      return launch_on_cluster(k_sweep_wpr<FORWARD, DIVIDE, 1>, C, smem, s, order, len, n, rp, ci,
+      return launch_on_cluster(k_sweep_wpr<FORWARD, DIVIDE, 1>, C, threads, smem, s, order, len,
+                               n, rp, ci,
                                dg, v, rd, in, out, clear, err, limit);
-    return launch_on_cluster(k_sweep_cluster<FORWARD, DIVIDE, 4>, C, smem, s, order, len, n, rp,
+    return launch_on_cluster(k_sweep_cluster<FORWARD, DIVIDE, 4>, C, kCtaThreads, smem, s, order,
+                             len, n, rp,
                              ci, dg, v, rd, in, out, clear, err, limit);
   }
   if (sched == ILUK_SCHED_WARP_GRID) {
     auto kern = k_sweep_wpr<FORWARD, DIVIDE, 0>;
-    int bps = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, kCtaThreads, 0);
+    int bps = 1;  // an explicit width means one CTA of that width per SM
+    if (w == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, kCtaThreads, 0);
     if (bps < 1) bps = 1;
     int64_t grid = (int64_t)bps * num_sms();
-    const int64_t want = (len + (kCtaThreads / 32) - 1) / (kCtaThreads / 32);
+    const int64_t want = (len + (threads / 32) - 1) / (threads / 32);
     if (grid > want) grid = want;
     const int64_t nn = n;
     void *args[] = {(void *)&order, (void *)&len, (void *)&nn, (void *)&rp, (void *)&ci,
                     (void *)&dg, (void *)&v, (void *)&rd, (void *)&in, (void *)&out,
                     (void *)&clear, (void *)&err, (void *)&limit};
     cudaError_t e = cudaLaunchCooperativeKernel((const void *)kern, dim3((unsigned)grid),
-                                                dim3(kCtaThreads), args, 0, s);
+                                                dim3((unsigned)threads), args, 0, s);
     note_launch();
     return e;
   }
@@ -713,10 +724,14 @@ cudaError_t launch_apply(int64_t n, const int64_t *rp, const int32_t *ci, const 
   int sf = sched & 0xff, sb = (sched >> 8) & 0xff;
   if (sb == 0) sb = sf;
   auto fix = [&](int sc) {
-    if ((sc == ILUK_SCHED_CLUSTER || sc == ILUK_SCHED_WARP_CLUSTER) && cluster_size_for(n) == 0)
-      sc = ILUK_SCHED_WARP_GRID;
-    if (sc < ILUK_SCHED_FLAGS || sc > ILUK_SCHED_WARP_CLUSTER) sc = ILUK_SCHED_WARP_GRID;
-    return sc;
+    int kind = sc & 0xf, w = (sc >> 4) & 0xf;
+    if (kind < ILUK_SCHED_FLAGS || kind > ILUK_SCHED_WARP_CLUSTER) kind = ILUK_SCHED_WARP_GRID;
+    if ((kind == ILUK_SCHED_CLUSTER || kind == ILUK_SCHED_WARP_CLUSTER) &&
+        cluster_size_for(n) == 0)
+      kind = ILUK_SCHED_WARP_GRID;
+    if ((kind != ILUK_SCHED_WARP_GRID && kind != ILUK_SCHED_WARP_CLUSTER) || w < 2 || w > 8)
+      w = 0;  // widths 256..1024 threads
+    return kind | (w << 4);
   };
   sf = fix(sf);
   sb = fix(sb);

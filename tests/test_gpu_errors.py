@@ -121,3 +121,21 @@ def test_gmres_reports_nonconvergence():
     b = torch.ones(A.n, dtype=torch.float64, device="cuda")
     x, info = P.gmres(rp, ci, av, b, None, restart=5, rtol=1e-12, maxit=12, check=False)
     assert info.status == L.ENOCONV and info.iters == 12
+
+
+def test_schedule_values_checked():
+    A = W.conv_diff(12, 2, (20.0, 20.0))
+    rp, ci, av = to_dev(A)
+    F = P.numeric(P.symbolic(rp, ci, 1), av)
+    good = [L.SCHED_AUTO, L.SCHED_FLAGS, L.sched_width(L.SCHED_WARP_CLUSTER, 256),
+            L.sched_width(L.SCHED_WARP_GRID, 1024),
+            L.SCHED_CLUSTER | (L.sched_width(L.SCHED_WARP_CLUSTER, 768) << 8)]
+    for s in good:
+        F.set_schedule(s)
+        assert F.schedule() == s
+    bad = [6, 0x0F, L.sched_width(L.SCHED_FLAGS, 512),  # width on a lockstep kind
+           L.SCHED_WARP_GRID | (1 << 4), L.SCHED_WARP_GRID | (9 << 4),  # 128 / 1152 threads
+           L.SCHED_WARP_GRID | (6 << 8), -1, 1 << 16]
+    for s in bad:
+        with pytest.raises(P.IlukError):
+            F.set_schedule(s)

@@ -60,7 +60,16 @@ def test_numeric_bit_exact(name, A, k):
     assert_bits_equal(F.values(), ref["val"], "factor values")
 
 
-@pytest.mark.parametrize("sched", [L.SCHED_FLAGS, L.SCHED_SINGLE_CTA, L.SCHED_CLUSTER, L.SCHED_WARP_GRID, L.SCHED_WARP_CLUSTER])
+SCHEDS = [L.SCHED_FLAGS, L.SCHED_SINGLE_CTA, L.SCHED_CLUSTER, L.SCHED_WARP_GRID,
+          L.SCHED_WARP_CLUSTER, L.sched_width(L.SCHED_WARP_GRID, 256),
+          L.sched_width(L.SCHED_WARP_CLUSTER, 384),
+          # forward and backward on different schedules
+          L.SCHED_SINGLE_CTA | (L.sched_width(L.SCHED_WARP_CLUSTER, 256) << 8),
+          # invalid kind and width: fall back to the warp grid
+          0x9F]
+
+
+@pytest.mark.parametrize("sched", SCHEDS)
 @pytest.mark.parametrize("name,A,k", CASES, ids=IDS)
 def test_apply_bit_exact(name, A, k, sched):
     S, F, ref, _ = factor_both(A, k)
