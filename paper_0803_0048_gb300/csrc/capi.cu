@@ -449,9 +449,9 @@ static int numeric_into(iluk_fac *F, const double *A_val, iluk_info *info, cudaS
   // numeric uses the sweep scratch: [0..1] ticket, [4..4+n) ready flags
   CK(cudaMemsetAsync(F->sync, 0, sweep_sync_ints(S->n) * sizeof(int), s));
   CK(launch_fill_err(F->err, s));
-  CK(launch_numeric(S, A_val, F->val, reinterpret_cast<unsigned long long *>(F->sync), F->err,
-                    s));
-  CK(launch_recip_diag(S->n, S->diag, F->val, F->rdiag, s));
+  // the numeric phase also publishes the reciprocals of the diagonal
+  CK(launch_numeric(S, A_val, F->val, F->rdiag, reinterpret_cast<unsigned long long *>(F->sync),
+                    F->err, s));
   int64_t row;
   int st = read_err(F->err, s, &row, nullptr);
   CK(launch_fill_err(F->err, s));

@@ -130,7 +130,8 @@ __device__ __forceinline__ double add_prod(double acc, double a, double b) {
 // critical path.  The argument assumes no intermediate underflows or
 // overflows: both operands must have magnitudes in [2^-400, 2^401), else
 // (zero, subnormal, huge, infinite, NaN) the quotient comes from __ddiv_rn.
-// recip_dd marks such a divisor with y = 0.
+// recip_dd marks such a divisor with y = 0, and any y outside that range
+// (0, NaN) also selects __ddiv_rn.
 __device__ __forceinline__ bool dd_in_range(double x) {
   const unsigned ex = ((unsigned)__double2hiint(x) >> 20) & 0x7ffu;
   return ex - 623u <= 800u;  // biased exponent in [1023-400, 1023+400]
@@ -144,7 +145,7 @@ __device__ __forceinline__ double2 recip_dd(double b) {
 }
 
 __device__ __forceinline__ double div_rn_recip(double a, double b, double2 rb) {
-  if (rb.x == 0.0 || !dd_in_range(a)) return __ddiv_rn(a, b);
+  if (!dd_in_range(rb.x) || !dd_in_range(a)) return __ddiv_rn(a, b);
   const double q0 = __fma_rn(a, rb.x, __dmul_rn(a, rb.y));
   const double r = __fma_rn(-b, q0, a);
   return __fma_rn(r, rb.x, q0);

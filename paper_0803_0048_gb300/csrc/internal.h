@@ -37,7 +37,8 @@ struct iluk_fac {
   double *val = nullptr;          // F values
   int *sync = nullptr;            // tickets + flags for sweeps: see sweeps.cu
   double *tmp = nullptr;          // intermediate vector of the two sweeps
-  double2 *rdiag = nullptr;       // double-double reciprocals of the diagonal
+  double2 *rdiag = nullptr;       // double-double reciprocals of the diagonal (from
+                                  // the numeric phase; used by every sweep division)
   iluk::DevErr *err = nullptr;    // status of asynchronous calls
   // explicit transpose of F for (L~U~)^-T, built on first use
   int64_t *trowptr = nullptr;
@@ -108,7 +109,7 @@ int build_levels_pair(int64_t n, const int64_t *rp, const int32_t *ci, const int
 
 // Numeric (numeric.cu)
 // The factor values double as ready flags (numeric.cu); fval is overwritten.
-cudaError_t launch_numeric(const iluk_sym *S, const double *aval, double *fval,
+cudaError_t launch_numeric(const iluk_sym *S, const double *aval, double *fval, double2 *rdiag,
                            unsigned long long *ticket, DevErr *err, cudaStream_t s);
 cudaError_t launch_numeric_batched(const iluk_sym *S, int64_t nbatch, const double *avals,
                                    double *fvals, unsigned long long *ticket, DevErr *errs,
@@ -125,8 +126,6 @@ cudaError_t launch_apply(int64_t n, const int64_t *rp, const int32_t *ci, const 
                          DevErr *err, cudaStream_t s);
 cudaError_t launch_fill_pending(int64_t n, double *x, cudaStream_t s);
 cudaError_t launch_fill_value(int64_t n, double *x, double v, cudaStream_t s);
-cudaError_t launch_recip_diag(int64_t n, const int64_t *dg, const double *v, double2 *rd,
-                              cudaStream_t s);
 cudaError_t launch_div_check(int64_t n, const double *a, const double *b, double *q,
                              cudaStream_t s);
 cudaError_t launch_transpose(int64_t n, int64_t nnz, const int64_t *rp, const int32_t *ci,

@@ -63,40 +63,89 @@ __device__ __forceinline__ bool wait_vals(const double *p, bool active, double *
 }
 
 // What a warp needs from pivot row h before its values are final: where
-// its first 64 entries j > h fall in the current row (pos, -1 if absent),
-// and loads of those values and of f_hh already issued.
+// its first kPre * 32 entries j > h fall in the current row (pos, -1 if
+// absent), and loads of those values and of f_hh already issued.
+constexpr int kPre = 4;
+constexpr unsigned kPollSleepMax = 64;
+
 struct PivotPre {
   int64_t hd, u1;
-  int pos0, pos1;
-  double piv, f0, f1;
+  int pos[kPre];
+  double piv, f[kPre];
+  double rh, rl;  // the pivot row's published reciprocal of f_hh (may be pending)
 };
 
 __device__ __forceinline__ void prefetch_pivot(PivotPre &pp, int q, const int32_t *rc, int m,
                                                const int64_t *__restrict__ fdiag,
                                                const int64_t *__restrict__ frp,
                                                const int32_t *__restrict__ fci, const double *fv,
-                                               int lane) {
+                                               const double *rdiag, int lane) {
   const int h = rc[q];
   pp.hd = fdiag[h];
   pp.u1 = frp[h + 1];
   pp.piv = ld_gpu(&fv[pp.hd]);
-  pp.pos0 = pp.pos1 = -1;
-  pp.f0 = pp.f1 = 0.0;
-  const int64_t r0 = pp.hd + 1 + lane, r1 = r0 + 32;
-  if (r0 < pp.u1) {
-    const int32_t j = fci[r0];
-    const int ps = lower_bound_i(rc, q + 1, m, j);
-    if (ps < m && rc[ps] == j) {
-      pp.pos0 = ps;
-      pp.f0 = ld_gpu(&fv[r0]);
+  pp.rh = pp.rl = __longlong_as_double((long long)kPendingF);
+  if (rdiag) {
+    pp.rh = ld_gpu(&rdiag[2 * (int64_t)h]);
+    pp.rl = ld_gpu(&rdiag[2 * (int64_t)h + 1]);
+  }
+  int lo = q + 1;  // a lane's columns increase with c: each search starts where the last ended
+#pragma unroll
+  for (int c = 0; c < kPre; ++c) {
+    const int64_t r = pp.hd + 1 + lane + 32 * c;
+    pp.pos[c] = -1;
+    pp.f[c] = 0.0;
+    if (r < pp.u1) {
+      const int32_t j = fci[r];
+      lo = lower_bound_i(rc, lo, m, j);
+      if (lo < m && rc[lo] == j) {
+        pp.pos[c] = lo;
+        pp.f[c] = ld_gpu(&fv[r]);
+      }
     }
   }
-  if (r1 < pp.u1) {
-    const int32_t j = fci[r1];
-    const int ps = lower_bound_i(rc, q + 1, m, j);
-    if (ps < m && rc[ps] == j) {
-      pp.pos1 = ps;
-      pp.f1 = ld_gpu(&fv[r1]);
+}
+
+// Re-issue the loads of the values of a prefetched pivot that were still
+// pending.  The loads are independent, so they travel together: one round
+// trip refreshes the whole pivot.
+__device__ __forceinline__ void refresh_pivot(PivotPre &pp, const double *fv, int lane,
+                                              const double *rdiag, int h) {
+  if (pend_f(pp.piv)) pp.piv = ld_gpu(&fv[pp.hd]);
+  if (rdiag && (pend_f(pp.rh) || pend_f(pp.rl))) {  // optional: never waited for
+    pp.rh = ld_gpu(&rdiag[2 * (int64_t)h]);
+    pp.rl = ld_gpu(&rdiag[2 * (int64_t)h + 1]);
+  }
+#pragma unroll
+  for (int c = 0; c < kPre; ++c)
+    if (pp.pos[c] >= 0 && pend_f(pp.f[c])) pp.f[c] = ld_gpu(&fv[pp.hd + 1 + lane + 32 * c]);
+}
+
+__device__ __forceinline__ bool pivot_pending(const PivotPre &pp) {
+  bool p = pend_f(pp.piv);
+#pragma unroll
+  for (int c = 0; c < kPre; ++c) p |= pp.pos[c] >= 0 && pend_f(pp.f[c]);
+  return p;
+}
+
+// Warp-uniform wait until f_hh and every prefetched f_hj of the pivot are
+// final, polling all of them at once.  False on time-out or when a row
+// before `row` has failed.
+__device__ __forceinline__ bool wait_pivot(PivotPre &pp, const double *fv, int lane,
+                                           const double *rdiag, int h, const DevErr *err,
+                                           int64_t row, int64_t limit_ns) {
+  if (!__any_sync(FULL_MASK, pivot_pending(pp))) return true;
+  const uint64_t t0 = globaltimer_ns();
+  unsigned backoff = 16;
+  for (unsigned it = 0;; ++it) {
+    refresh_pivot(pp, fv, lane, rdiag, h);
+    if (!__any_sync(FULL_MASK, pivot_pending(pp))) return true;
+    const bool stop = (it & 31u) == 31u &&
+                      (earlier_failed(err, row) || (int64_t)(globaltimer_ns() - t0) > limit_ns);
+    if (__any_sync(FULL_MASK, stop)) return false;  // the whole warp gives up together
+    if (it >= 4) {  // a short spin first, then a bounded back-off
+      __nanosleep(backoff);
+      if (backoff < kPollSleepMax) backoff <<= 1;
     }
   }
 }
@@ -111,7 +160,7 @@ __global__ void __launch_bounds__(kNumThreads)
 k_numeric(int64_t n, int64_t nbatch, const int64_t *__restrict__ arp,
           const int32_t *__restrict__ a2f, const double *__restrict__ aval, int64_t astride,
           const int64_t *__restrict__ frp, const int32_t *__restrict__ fci,
-          const int64_t *__restrict__ fdiag, double *fval, int64_t fstride,
+          const int64_t *__restrict__ fdiag, double *fval, int64_t fstride, double *rdiag,
           unsigned long long *ticket, DevErr *errs, int cap, int64_t limit_ns, int64_t hold) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31;
@@ -159,26 +208,38 @@ k_numeric(int64_t n, int64_t nbatch, const int64_t *__restrict__ arp,
     __syncwarp();
 
     // Pivots are software-pipelined: while the values of pivot q are awaited,
-    // the pattern work and the value loads of pivot q+1 are already issued.
-    // A prefetch covers the first 64 entries j > h of the pivot row (two per
-    // lane); longer pivot rows finish their tail inline.
+    // the pattern work and the value loads of pivot q+1 are already issued,
+    // and the loads of its values that were still pending are re-issued as
+    // soon as pivot q's values arrive.  A prefetch covers the first 128
+    // entries j > h of the pivot row (four per lane); longer pivot rows
+    // finish their tail inline.
     bool ok = true;
     PivotPre cur, nxt;
-    if (dp > 0) prefetch_pivot(cur, 0, rc, m, fdiag, frp, fci, fv, lane);
+    if (dp > 0) prefetch_pivot(cur, 0, rc, m, fdiag, frp, fci, fv, rdiag, lane);
     for (int q = 0; q < dp && ok; ++q) {
-      if (q + 1 < dp) prefetch_pivot(nxt, q + 1, rc, m, fdiag, frp, fci, fv, lane);
-      if (!wait_vals(&fv[cur.hd], true, &cur.piv, err, row, limit_ns) ||
-          !wait_vals(&fv[cur.hd + 1 + lane], cur.pos0 >= 0, &cur.f0, err, row, limit_ns) ||
-          !wait_vals(&fv[cur.hd + 33 + lane], cur.pos1 >= 0, &cur.f1, err, row, limit_ns)) {
+      if (q + 1 < dp) prefetch_pivot(nxt, q + 1, rc, m, fdiag, frp, fci, fv, rdiag, lane);
+      if (!wait_pivot(cur, fv, lane, rdiag, rc[q], err, row, limit_ns)) {
         ok = false;
         break;
       }
-      const double fih = __ddiv_rn(rv[q], cur.piv);
+      if (q + 1 < dp) refresh_pivot(nxt, fv, lane, rdiag, rc[q + 1]);
+      // The multiplier f_ih / f_hh: through the pivot row's reciprocal when
+      // it has been published (four FP64 operations), else by IEEE division;
+      // both give the correctly rounded quotient.
+      const bool have_r = __all_sync(FULL_MASK, !pend_f(cur.rh) && !pend_f(cur.rl));
+      const double fih = have_r ? div_rn_recip(rv[q], cur.piv, make_double2(cur.rh, cur.rl))
+                                : __ddiv_rn(rv[q], cur.piv);
       __syncwarp();
       if (lane == 0) rv[q] = fih;
-      if (cur.pos0 >= 0) rv[cur.pos0] = sub_prod(rv[cur.pos0], fih, cur.f0);
-      if (cur.pos1 >= 0) rv[cur.pos1] = sub_prod(rv[cur.pos1], fih, cur.f1);
-      for (int64_t base = cur.hd + 65; base < cur.u1; base += 32) {  // long pivot rows
+      // only the chunks the pivot row has: an FP64 instruction costs its
+      // pipe time even with every lane predicated off
+      const int nch = (int)((cur.u1 - cur.hd - 1 + 31) >> 5);
+#pragma unroll
+      for (int c = 0; c < kPre; ++c) {
+        if (c >= nch) break;
+        if (cur.pos[c] >= 0) rv[cur.pos[c]] = sub_prod(rv[cur.pos[c]], fih, cur.f[c]);
+      }
+      for (int64_t base = cur.hd + 1 + 32 * kPre; base < cur.u1; base += 32) {  // long rows
         const int64_t r = base + lane;
         int pos = -1;
         double fhj = 0.0;
@@ -204,8 +265,20 @@ k_numeric(int64_t n, int64_t nbatch, const int64_t *__restrict__ arp,
       continue;
     }
     if (lane == 0 && rv[dp] == 0.0) set_err(err, row, ILUK_EZEROPIVOT);
-    if (row != hold)
-      for (int q = lane; q < m; q += 32) fv[b0 + q] = svals[q];
+    // write back the diagonal and U part first: that is what later rows wait
+    // for; then the reciprocal of the diagonal, for their multipliers and
+    // for the sweeps' divisions
+    if (row != hold) {
+      for (int t = lane; t < m; t += 32) {
+        const int q = t + dp < m ? t + dp : t + dp - m;
+        fv[b0 + q] = svals[q];
+      }
+      if (rdiag && lane == 0) {
+        const double2 r = recip_dd(svals[dp]);
+        rdiag[2 * row] = r.x;
+        rdiag[2 * row + 1] = r.y;
+      }
+    }
     __syncwarp();
   }
 }
@@ -225,8 +298,8 @@ static int numeric_cap(const iluk_sym *S, int *warps_out, size_t *smem_out) {
 }
 
 static cudaError_t launch_numeric_impl(const iluk_sym *S, int64_t nbatch, const double *avals,
-                                       double *fvals, unsigned long long *ticket, DevErr *errs,
-                                       cudaStream_t s) {
+                                       double *fvals, double *rdiag, unsigned long long *ticket,
+                                       DevErr *errs, cudaStream_t s) {
   ProfScope prof_scope(ILUK_PROF_NUMERIC, s);
   int warps;
   size_t smem;
@@ -239,6 +312,10 @@ static cudaError_t launch_numeric_impl(const iluk_sym *S, int64_t nbatch, const 
     if (b < 1) b = 1;
     k_fill_pending_f<<<(unsigned)b, 256, 0, s>>>(nv, fvals);
     note_launch();
+    if (rdiag) {
+      k_fill_pending_f<<<(unsigned)b, 256, 0, s>>>(2 * S->n, rdiag);
+      note_launch();
+    }
   }
   cudaError_t e = cudaFuncSetAttribute(k_numeric, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
@@ -252,20 +329,21 @@ static cudaError_t launch_numeric_impl(const iluk_sym *S, int64_t nbatch, const 
   if (grid < 1) grid = 1;
   k_numeric<<<(unsigned)grid, warps * 32, smem, s>>>(
       S->n, nbatch, S->arowptr, S->a2f, avals, S->nnzA, S->rowptr, S->colind, S->diag, fvals,
-      S->nnz, ticket, errs, cap, wait_limit(), hold_row());
+      S->nnz, rdiag, ticket, errs, cap, wait_limit(), hold_row());
   note_launch();
   return cudaGetLastError();
 }
 
-cudaError_t launch_numeric(const iluk_sym *S, const double *aval, double *fval,
+cudaError_t launch_numeric(const iluk_sym *S, const double *aval, double *fval, double2 *rdiag,
                            unsigned long long *ticket, DevErr *err, cudaStream_t s) {
-  return launch_numeric_impl(S, 1, aval, fval, ticket, err, s);
+  return launch_numeric_impl(S, 1, aval, fval, reinterpret_cast<double *>(rdiag), ticket, err,
+                             s);
 }
 
 cudaError_t launch_numeric_batched(const iluk_sym *S, int64_t nbatch, const double *avals,
                                    double *fvals, unsigned long long *ticket, DevErr *errs,
                                    cudaStream_t s) {
-  return launch_numeric_impl(S, nbatch, avals, fvals, ticket, errs, s);
+  return launch_numeric_impl(S, nbatch, avals, fvals, nullptr, ticket, errs, s);
 }
 
 }  // namespace iluk

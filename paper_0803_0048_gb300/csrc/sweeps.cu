@@ -519,28 +519,6 @@ cudaError_t launch_fill_value(int64_t n, double *x, double v, cudaStream_t s) {
   return fill_bits(n, x, bits, s);
 }
 
-// Double-double reciprocals of the diagonal, one per row (see recip_dd): the
-// divisions of the sweeps then cost four dependent FP64 operations.  Computed
-// once per set of factor values; the diagonal of row i of F^T is f_ii, so the
-// same array serves the transposed sweeps.
-__global__ void k_recip_diag(int64_t n, const int64_t *__restrict__ dg,
-                             const double *__restrict__ v, double2 *__restrict__ rd) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    rd[i] = recip_dd(v[dg[i]]);
-}
-
-cudaError_t launch_recip_diag(int64_t n, const int64_t *dg, const double *v, double2 *rd,
-                              cudaStream_t s) {
-  if (n == 0) return cudaSuccess;
-  int64_t b = (n + 255) / 256;
-  const int64_t cap = (int64_t)num_sms() * 8;
-  if (b > cap) b = cap;
-  k_recip_diag<<<(unsigned)b, 256, 0, s>>>(n, dg, v, rd);
-  note_launch();
-  return cudaGetLastError();
-}
-
 // q_i = a_i / b_i through recip_dd + div_rn_recip, the sweeps' division.
 __global__ void k_div_check(int64_t n, const double *__restrict__ a,
                             const double *__restrict__ b, double *__restrict__ q) {
