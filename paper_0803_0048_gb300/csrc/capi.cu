@@ -240,6 +240,7 @@ void iluk_sym_destroy(iluk_sym *S) {
   dfree(S->diag, s);
   dfree(S->arowptr, s);
   dfree(S->a2f, s);
+  dfree(S->pinfo, s);
   dfree(S->lord.order, s);
   dfree(S->uord.order, s);
   dfree(S->lord.corder, s);
@@ -366,6 +367,8 @@ int iluk_symbolic(const iluk_pattern *A, int k, iluk_sym **out, iluk_info *info,
   CKS(cudaMemsetAsync(maxrow, 0, sizeof(int32_t), s));
   CKS(launch_symbolic_compact(n, ar, S->rowptr, S->colind, S->level, S->diag, maxrow, s));
   CKS(launch_a2f(n, A->rowptr, A->colind, S->rowptr, S->colind, S->a2f, s));
+  CKS(dalloc(&S->pinfo, nnzF, s));
+  CKS(launch_pivot_info(n, S->rowptr, S->colind, S->diag, S->pinfo, s));
   CKS(cudaMemcpyAsync(S->arowptr, A->rowptr, (n + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
   int32_t mr = 0;
   CKS(cudaMemcpyAsync(&mr, maxrow, sizeof(int32_t), cudaMemcpyDeviceToHost, s));

@@ -27,6 +27,7 @@ struct iluk_sym {
   int64_t *diag = nullptr;
   int64_t *arowptr = nullptr;  // copy of A's row pointers
   int32_t *a2f = nullptr;      // offset of each A entry inside its F row
+  int64_t *pinfo = nullptr;    // per lower entry (i,h): diag position of row h << 24 | |U(h)|
   int32_t max_row = 0;
   int32_t depth_lower = -1, depth_upper = -1;
   LevelOrder lord, uord;       // forward / backward sweep level orders
@@ -109,6 +110,8 @@ int build_levels_pair(int64_t n, const int64_t *rp, const int32_t *ci, const int
 
 // Numeric (numeric.cu)
 // The factor values double as ready flags (numeric.cu); fval is overwritten.
+cudaError_t launch_pivot_info(int64_t n, const int64_t *frp, const int32_t *fci,
+                              const int64_t *fdiag, int64_t *pinfo, cudaStream_t s);
 cudaError_t launch_numeric(const iluk_sym *S, const double *aval, double *fval, double2 *rdiag,
                            unsigned long long *ticket, DevErr *err, cudaStream_t s);
 cudaError_t launch_numeric_batched(const iluk_sym *S, int64_t nbatch, const double *avals,

@@ -62,53 +62,94 @@ __device__ __forceinline__ bool wait_vals(const double *p, bool active, double *
   }
 }
 
-// What a warp needs from pivot row h before its values are final: where
-// its first kPre * 32 entries j > h fall in the current row (pos, -1 if
-// absent), and loads of those values and of f_hh already issued.
+// Pivot row h, as the warp stages it before its values are final.  Stage A
+// issues the loads of f_hh, of the published reciprocal of f_hh and of the
+// columns j of the first kPre * 32 entries j > h; stage B, one pivot later,
+// turns those columns into positions in the current row (pos, -1 if absent)
+// and issues the loads of the matching f_hj; stage C, one more pivot later,
+// waits for whatever is still pending and applies the pivot.  The per-entry
+// pivot facts (where row h's diagonal sits, how long its U part is) come from
+// a table built with the pattern, so no stage waits on a dependent load.
 constexpr int kPre = 4;
 constexpr unsigned kPollSleepMax = 64;
+constexpr int kUlenBits = 24;  // pivot info = diag position << 24 | U length
+
+struct PivotA {
+  int64_t hd;
+  int ulen;
+  int32_t j[kPre];
+  double piv, rh, rl;
+};
 
 struct PivotPre {
-  int64_t hd, u1;
+  int64_t hd;
+  int ulen;
   int pos[kPre];
   double piv, f[kPre];
   double rh, rl;  // the pivot row's published reciprocal of f_hh (may be pending)
 };
 
-__device__ __forceinline__ void prefetch_pivot(PivotPre &pp, int q, const int32_t *rc, int m,
-                                               const int64_t *__restrict__ fdiag,
-                                               const int64_t *__restrict__ frp,
-                                               const int32_t *__restrict__ fci, const double *fv,
-                                               const double *rdiag, int lane) {
-  const int h = rc[q];
-  pp.hd = fdiag[h];
-  pp.u1 = frp[h + 1];
-  pp.piv = ld_gpu(&fv[pp.hd]);
-  pp.rh = pp.rl = __longlong_as_double((long long)kPendingF);
-  if (rdiag) {
-    pp.rh = ld_gpu(&rdiag[2 * (int64_t)h]);
-    pp.rl = ld_gpu(&rdiag[2 * (int64_t)h + 1]);
+// Where column j sits in the current row: a dense map over the row's column
+// span when it fits in shared memory, else a binary search from `lo`.
+struct RowIndex {
+  const int32_t *rc;
+  const int16_t *map;
+  int32_t c0;
+  int span, m;
+  bool use_map;
+  __device__ __forceinline__ int find(int32_t j, int lo) const {
+    if (use_map) {
+      const int d = j - c0;
+      return (d >= 0 && d < span) ? (int)map[d] : -1;
+    }
+    const int ps = lower_bound_i(rc, lo, m, j);
+    return (ps < m && rc[ps] == j) ? ps : -1;
   }
+};
+
+__device__ __forceinline__ void stage_a(PivotA &a, int64_t pinfo, const int32_t *__restrict__ fci,
+                                        const double *fv, const double *rdiag, int h, int lane) {
+  a.hd = pinfo >> kUlenBits;
+  a.ulen = (int)(pinfo & ((1ll << kUlenBits) - 1));
+  a.piv = ld_gpu(&fv[a.hd]);
+  a.rh = a.rl = __longlong_as_double((long long)kPendingF);
+  if (rdiag) {
+    a.rh = ld_gpu(&rdiag[2 * (int64_t)h]);
+    a.rl = ld_gpu(&rdiag[2 * (int64_t)h + 1]);
+  }
+#pragma unroll
+  for (int c = 0; c < kPre; ++c) {
+    const int e = lane + 32 * c;
+    a.j[c] = e < a.ulen ? fci[a.hd + 1 + e] : -1;
+  }
+}
+
+__device__ __forceinline__ void stage_b(PivotPre &pp, const PivotA &a, const RowIndex &ri, int q,
+                                        const double *fv, int lane) {
+  pp.hd = a.hd;
+  pp.ulen = a.ulen;
+  pp.piv = a.piv;
+  pp.rh = a.rh;
+  pp.rl = a.rl;
   int lo = q + 1;  // a lane's columns increase with c: each search starts where the last ended
 #pragma unroll
   for (int c = 0; c < kPre; ++c) {
-    const int64_t r = pp.hd + 1 + lane + 32 * c;
     pp.pos[c] = -1;
     pp.f[c] = 0.0;
-    if (r < pp.u1) {
-      const int32_t j = fci[r];
-      lo = lower_bound_i(rc, lo, m, j);
-      if (lo < m && rc[lo] == j) {
-        pp.pos[c] = lo;
-        pp.f[c] = ld_gpu(&fv[r]);
+    if (a.j[c] >= 0) {
+      const int ps = ri.find(a.j[c], lo);
+      if (ps >= 0) {
+        lo = ps;
+        pp.pos[c] = ps;
+        pp.f[c] = ld_gpu(&fv[pp.hd + 1 + lane + 32 * c]);
       }
     }
   }
 }
 
-// Re-issue the loads of the values of a prefetched pivot that were still
-// pending.  The loads are independent, so they travel together: one round
-// trip refreshes the whole pivot.
+// Re-issue the loads of the values of a staged pivot that are still pending.
+// The loads are independent, so they travel together: one round trip
+// refreshes the whole pivot.
 __device__ __forceinline__ void refresh_pivot(PivotPre &pp, const double *fv, int lane,
                                               const double *rdiag, int h) {
   if (pend_f(pp.piv)) pp.piv = ld_gpu(&fv[pp.hd]);
@@ -128,9 +169,9 @@ __device__ __forceinline__ bool pivot_pending(const PivotPre &pp) {
   return p;
 }
 
-// Warp-uniform wait until f_hh and every prefetched f_hj of the pivot are
-// final, polling all of them at once.  False on time-out or when a row
-// before `row` has failed.
+// Warp-uniform wait until f_hh and every staged f_hj of the pivot are final,
+// polling all of them at once.  False on time-out or when a row before `row`
+// has failed.
 __device__ __forceinline__ bool wait_pivot(PivotPre &pp, const double *fv, int lane,
                                            const double *rdiag, int h, const DevErr *err,
                                            int64_t row, int64_t limit_ns) {
@@ -150,6 +191,34 @@ __device__ __forceinline__ bool wait_pivot(PivotPre &pp, const double *fv, int l
   }
 }
 
+// Pivot facts per lower entry (i, h) of F: position of row h's diagonal and
+// the length of its strictly upper part, packed for the numeric phase.
+__global__ void k_pivot_info(int64_t n, const int64_t *__restrict__ frp,
+                             const int32_t *__restrict__ fci, const int64_t *__restrict__ fdiag,
+                             int64_t *pinfo) {
+  const int lane = threadIdx.x & 31;
+  int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t row = w; row < n; row += nw)
+    for (int64_t p = frp[row] + lane; p < fdiag[row]; p += 32) {
+      const int32_t h = fci[p];
+      const int64_t hd = fdiag[h];
+      pinfo[p] = (hd << kUlenBits) | (frp[h + 1] - hd - 1);
+    }
+}
+
+cudaError_t launch_pivot_info(int64_t n, const int64_t *frp, const int32_t *fci,
+                              const int64_t *fdiag, int64_t *pinfo, cudaStream_t s) {
+  ProfScope prof_scope(ILUK_PROF_COMPACT, s);  // pattern post-processing
+  if (n == 0) return cudaSuccess;
+  int64_t blocks = (n * 32 + 255) / 256;
+  const int64_t cap = (int64_t)num_sms() * 16;
+  if (blocks > cap) blocks = cap;
+  k_pivot_info<<<(unsigned)blocks, 256, 0, s>>>(n, frp, fci, fdiag, pinfo);
+  note_launch();
+  return cudaGetLastError();
+}
+
 __global__ void k_fill_pending_f(int64_t n, double *x) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
@@ -160,14 +229,20 @@ __global__ void __launch_bounds__(kNumThreads)
 k_numeric(int64_t n, int64_t nbatch, const int64_t *__restrict__ arp,
           const int32_t *__restrict__ a2f, const double *__restrict__ aval, int64_t astride,
           const int64_t *__restrict__ frp, const int32_t *__restrict__ fci,
-          const int64_t *__restrict__ fdiag, double *fval, int64_t fstride, double *rdiag,
-          unsigned long long *ticket, DevErr *errs, int cap, int64_t limit_ns, int64_t hold) {
+          const int64_t *__restrict__ fdiag, const int64_t *__restrict__ pinfo, double *fval,
+          int64_t fstride, double *rdiag, unsigned long long *ticket, DevErr *errs, int cap,
+          int map_cap, int64_t limit_ns, int64_t hold) {
+  // per warp: values, pivot infos (cap each), columns, then the column map
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   const int nwarps = blockDim.x >> 5;
   double *svals = reinterpret_cast<double *>(smem) + (size_t)wib * cap;
-  int32_t *scols = reinterpret_cast<int32_t *>(smem + (size_t)nwarps * cap * 8) + (size_t)wib * cap;
+  int64_t *spinfo = reinterpret_cast<int64_t *>(smem + (size_t)nwarps * cap * 8) + (size_t)wib * cap;
+  int32_t *scols =
+      reinterpret_cast<int32_t *>(smem + (size_t)nwarps * cap * 16) + (size_t)wib * cap;
+  int16_t *smap =
+      reinterpret_cast<int16_t *>(smem + (size_t)nwarps * cap * 20) + (size_t)wib * map_cap;
   const int64_t total = n * nbatch;
 
   for (;;) {
@@ -194,6 +269,7 @@ k_numeric(int64_t n, int64_t nbatch, const int64_t *__restrict__ arp,
       scols[q] = fci[b0 + q];
       svals[q] = 0.0;
     }
+    for (int q = lane; q < dp; q += 32) spinfo[q] = pinfo[b0 + q];
     __syncwarp();
     bool bad = false;
     for (int64_t p = arp[row] + lane; p < arp[row + 1]; p += 32) {
@@ -205,24 +281,39 @@ k_numeric(int64_t n, int64_t nbatch, const int64_t *__restrict__ arp,
       if (lane == 0) set_err(err, row, ILUK_ENONFINITE);
       continue;
     }
+    RowIndex ri;
+    ri.rc = rc;
+    ri.map = smap;
+    ri.m = m;
+    ri.c0 = rc[0];
+    ri.span = rc[m - 1] - ri.c0 + 1;
+    ri.use_map = ri.span <= map_cap;
+    if (ri.use_map) {
+      for (int d = lane; d < ri.span; d += 32) smap[d] = -1;
+      __syncwarp();
+      for (int q = lane; q < m; q += 32) smap[rc[q] - ri.c0] = (int16_t)q;
+    }
     __syncwarp();
 
-    // Pivots are software-pipelined: while the values of pivot q are awaited,
-    // the pattern work and the value loads of pivot q+1 are already issued,
-    // and the loads of its values that were still pending are re-issued as
-    // soon as pivot q's values arrive.  A prefetch covers the first 128
-    // entries j > h of the pivot row (four per lane); longer pivot rows
-    // finish their tail inline.
+    // Pivots go through the three stages (see PivotA): in iteration q the
+    // warp applies pivot q, finds the positions of pivot q+1 and issues the
+    // loads of pivot q+2, so the latencies of the later stages overlap the
+    // work and the waits of the earlier ones.
     bool ok = true;
+    PivotA pa;
     PivotPre cur, nxt;
-    if (dp > 0) prefetch_pivot(cur, 0, rc, m, fdiag, frp, fci, fv, rdiag, lane);
+    if (dp > 0) {
+      stage_a(pa, spinfo[0], fci, fv, rdiag, rc[0], lane);
+      stage_b(cur, pa, ri, 0, fv, lane);
+    }
+    if (dp > 1) stage_a(pa, spinfo[1], fci, fv, rdiag, rc[1], lane);
     for (int q = 0; q < dp && ok; ++q) {
-      if (q + 1 < dp) prefetch_pivot(nxt, q + 1, rc, m, fdiag, frp, fci, fv, rdiag, lane);
+      if (q + 1 < dp) stage_b(nxt, pa, ri, q + 1, fv, lane);
+      if (q + 2 < dp) stage_a(pa, spinfo[q + 2], fci, fv, rdiag, rc[q + 2], lane);
       if (!wait_pivot(cur, fv, lane, rdiag, rc[q], err, row, limit_ns)) {
         ok = false;
         break;
       }
-      if (q + 1 < dp) refresh_pivot(nxt, fv, lane, rdiag, rc[q + 1]);
       // The multiplier f_ih / f_hh: through the pivot row's reciprocal when
       // it has been published (four FP64 operations), else by IEEE division;
       // both give the correctly rounded quotient.
@@ -233,23 +324,20 @@ k_numeric(int64_t n, int64_t nbatch, const int64_t *__restrict__ arp,
       if (lane == 0) rv[q] = fih;
       // only the chunks the pivot row has: an FP64 instruction costs its
       // pipe time even with every lane predicated off
-      const int nch = (int)((cur.u1 - cur.hd - 1 + 31) >> 5);
+      const int nch = (cur.ulen + 31) >> 5;
 #pragma unroll
       for (int c = 0; c < kPre; ++c) {
         if (c >= nch) break;
         if (cur.pos[c] >= 0) rv[cur.pos[c]] = sub_prod(rv[cur.pos[c]], fih, cur.f[c]);
       }
-      for (int64_t base = cur.hd + 1 + 32 * kPre; base < cur.u1; base += 32) {  // long rows
+      const int64_t u1 = cur.hd + 1 + cur.ulen;
+      for (int64_t base = cur.hd + 1 + 32 * kPre; base < u1; base += 32) {  // long rows
         const int64_t r = base + lane;
         int pos = -1;
         double fhj = 0.0;
-        if (r < cur.u1) {
-          const int32_t j = fci[r];
-          const int ps = lower_bound_i(rc, q + 1, m, j);
-          if (ps < m && rc[ps] == j) {
-            pos = ps;
-            fhj = ld_gpu(&fv[r]);
-          }
+        if (r < u1) {
+          pos = ri.find(fci[r], q + 1);
+          if (pos >= 0) fhj = ld_gpu(&fv[r]);
         }
         if (!wait_vals(&fv[r], pos >= 0, &fhj, err, row, limit_ns)) {
           ok = false;
@@ -283,27 +371,35 @@ k_numeric(int64_t n, int64_t nbatch, const int64_t *__restrict__ arp,
   }
 }
 
-static int numeric_cap(const iluk_sym *S, int *warps_out, size_t *smem_out) {
-  // Per-warp slice: one row of F (double value + int32 column per entry).
+// Shared memory per warp: a row of F (value, pivot info, column: 20 bytes per
+// entry) and a column map of map_cap int16.  The largest map that lets 8,
+// then 4, 2, 1 warps share a CTA; rows whose column span exceeds the map
+// fall back to binary search.
+static int numeric_cap(const iluk_sym *S, int *warps_out, int *map_out, size_t *smem_out) {
   int cap = S->max_row;
   if (cap < 32) cap = 32;
   cap = (cap + 31) & ~31;
-  int warps = kNumThreads / 32;
   const size_t budget = (size_t)max_smem_optin();
-  while (warps > 1 && (size_t)cap * 12 * warps > budget) warps >>= 1;
-  if ((size_t)cap * 12 * warps > budget) return -1;  // a row of F exceeds shared memory
-  *warps_out = warps;
-  *smem_out = (size_t)cap * 12 * warps;
-  return cap;
+  for (int warps : {8, 4, 2, 1})
+    for (int map : {8192, 4096, 0}) {
+      const size_t need = ((size_t)cap * 20 + (size_t)map * 2) * warps;
+      if (need <= budget) {
+        *warps_out = warps;
+        *map_out = map;
+        *smem_out = need;
+        return cap;
+      }
+    }
+  return -1;  // a row of F exceeds shared memory
 }
 
 static cudaError_t launch_numeric_impl(const iluk_sym *S, int64_t nbatch, const double *avals,
                                        double *fvals, double *rdiag, unsigned long long *ticket,
                                        DevErr *errs, cudaStream_t s) {
   ProfScope prof_scope(ILUK_PROF_NUMERIC, s);
-  int warps;
+  int warps, map_cap;
   size_t smem;
-  const int cap = numeric_cap(S, &warps, &smem);
+  const int cap = numeric_cap(S, &warps, &map_cap, &smem);
   if (cap < 0) return cudaErrorMemoryAllocation;
   {
     const int64_t nv = S->nnz * nbatch;
@@ -328,8 +424,8 @@ static cudaError_t launch_numeric_impl(const iluk_sym *S, int64_t nbatch, const 
   if (grid > want) grid = want;
   if (grid < 1) grid = 1;
   k_numeric<<<(unsigned)grid, warps * 32, smem, s>>>(
-      S->n, nbatch, S->arowptr, S->a2f, avals, S->nnzA, S->rowptr, S->colind, S->diag, fvals,
-      S->nnz, rdiag, ticket, errs, cap, wait_limit(), hold_row());
+      S->n, nbatch, S->arowptr, S->a2f, avals, S->nnzA, S->rowptr, S->colind, S->diag, S->pinfo,
+      fvals, S->nnz, rdiag, ticket, errs, cap, map_cap, wait_limit(), hold_row());
   note_launch();
   return cudaGetLastError();
 }
