@@ -275,7 +275,7 @@ int iluk_symbolic(const iluk_pattern *A, int k, iluk_sym **out, iluk_info *info,
     dfree(ar.row_off, s);
     dfree(ar.row_len, s);
     dfree(ar.row_ust, s);
-    dfree(ar.ready, s);
+    dfree(ar.meta, s);
     dfree(ar.ticket, s);
     dfree(scan_tmp, s);
   };
@@ -293,7 +293,7 @@ int iluk_symbolic(const iluk_pattern *A, int k, iluk_sym **out, iluk_info *info,
   CKS(dalloc(&ar.row_off, n, s));
   CKS(dalloc(&ar.row_len, n, s));
   CKS(dalloc(&ar.row_ust, n, s));
-  CKS(dalloc(&ar.ready, n, s));
+  CKS(dalloc(&ar.meta, n, s));
   CKS(dalloc(&ar.ticket, 1, s));
   CKS(dalloc(&ar.top, 1, s));
 
@@ -313,7 +313,11 @@ int iluk_symbolic(const iluk_pattern *A, int k, iluk_sym **out, iluk_info *info,
       CKS(dalloc(&ar.lev, arena_cap, s));
     }
     ar.cap = arena_cap;
-    CKS(cudaMemsetAsync(ar.ready, 0, n * sizeof(int), s));
+    if (k >= 2) {  // rows wait on rows: announcements and arena start pending
+      CKS(cudaMemsetAsync(ar.meta, 0xff, n * sizeof(unsigned long long), s));
+      CKS(cudaMemsetAsync(ar.col, 0xff, arena_cap * sizeof(int32_t), s));
+      CKS(cudaMemsetAsync(ar.lev, 0xff, arena_cap, s));
+    }
     CKS(cudaMemsetAsync(ar.ticket, 0, sizeof(unsigned long long), s));
     CKS(cudaMemsetAsync(ar.top, 0, sizeof(unsigned long long), s));
     CKS(launch_fill_err(err, s));

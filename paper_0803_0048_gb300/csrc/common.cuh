@@ -1,10 +1,12 @@
 // common.cuh -- device helpers shared by the libiluk kernels.
 //
-// Row-to-row synchronisation: a row publishes its result with a release store
-// to its ready flag; a dependent row spins on the flag with acquire loads.
-// Every wait is bounded by a time limit read from %globaltimer; on running
-// out, or when an earlier row has failed, the wait returns false and the
-// kernel records a status and returns (no trap, no endless loop).
+// Row-to-row synchronisation: every output a later row may read starts out
+// as a pending marker (a signalling-NaN bit pattern for values, an
+// impossible column or level for patterns) and is written exactly once, so a
+// dependent row polls the data itself with relaxed loads: no flags, no
+// fences.  Every wait is bounded by a time limit read from %globaltimer; on
+// running out, or when an earlier row has failed, the wait returns false and
+// the kernel records a status and returns (no trap, no endless loop).
 #pragma once
 
 #include <cstdint>
@@ -47,44 +49,10 @@ __device__ __forceinline__ bool any_failed(const DevErr *e) {
   return ld_volatile_u64(&e->key) != kNoErr;
 }
 
-__device__ __forceinline__ int ld_acquire(const int *p) {
-  int v;
-  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-__device__ __forceinline__ void st_release(int *p, int v) {
-  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
 __device__ __forceinline__ uint64_t globaltimer_ns() {
   uint64_t t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
-}
-
-// Spin until *flag != 0.  Returns false if the limit ran out or a row before
-// `row` failed.  Called by all lanes of a warp that need the flag.
-__device__ __forceinline__ bool wait_flag(const int *flag, const DevErr *err, int64_t row,
-                                          int64_t limit_ns) {
-  if (ld_acquire(flag)) return true;
-  uint64_t t0 = globaltimer_ns();
-  unsigned backoff = 32;
-  for (;;) {
-    if (ld_acquire(flag)) return true;
-    if (earlier_failed(err, row)) return false;
-    if ((int64_t)(globaltimer_ns() - t0) > limit_ns) return false;
-    __nanosleep(backoff);
-    if (backoff < 256) backoff <<= 1;
-  }
-}
-
-// Publish: every lane has finished its stores for the row; make them visible
-// at GPU scope before the flag.
-__device__ __forceinline__ void warp_publish(int *flag, int lane) {
-  __threadfence();
-  __syncwarp();
-  if (lane == 0) st_release(flag, 1);
 }
 
 // Lower bound of `key` in the sorted array a[lo, hi).

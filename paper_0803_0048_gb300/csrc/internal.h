@@ -93,7 +93,7 @@ cudaError_t launch_fill_err(DevErr *err, cudaStream_t s);
 struct SymArena {
   int32_t *col; uint8_t *lev; int64_t cap; unsigned long long *top;
   int64_t *row_off; int32_t *row_len; int32_t *row_ust;
-  int *ready; unsigned long long *ticket;
+  unsigned long long *meta; unsigned long long *ticket;
 };
 cudaError_t launch_symbolic_rows(int64_t n, const int64_t *arp, const int32_t *aci, int k,
                                  const SymArena &ar, DevErr *err, int cap, cudaStream_t s);

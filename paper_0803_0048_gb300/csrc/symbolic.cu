@@ -22,6 +22,60 @@ namespace iluk {
 
 constexpr int kSymThreads = 256;
 
+// Hand-off between rows without fences.  The arena is filled with pending
+// markers (column -1, level 255: levels never exceed k <= 250) before the
+// launch, and each slot is written once, so a reader simply retries while it
+// sees a marker.  A finished row announces itself with one 64-bit word:
+// (offset of its strictly upper part in the arena) << 24 | (its length),
+// kMetaPending until then.
+constexpr unsigned long long kMetaPending = ~0ull;
+constexpr int kMetaLenBits = 24;
+
+__device__ __forceinline__ unsigned long long ld_meta(const unsigned long long *p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p));
+  return v;
+}
+
+__device__ __forceinline__ int32_t ld_col(const int32_t *p) {
+  int32_t v;
+  asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p));
+  return v;
+}
+
+__device__ __forceinline__ int ld_lev(const uint8_t *p) {
+  unsigned v;
+  asm volatile("ld.relaxed.gpu.global.u8 %0, [%1];" : "=r"(v) : "l"(p));
+  return (int)v;
+}
+
+// Warp-uniform poll of a row's announcement; false on time-out or when a
+// row before `row` failed.
+__device__ __forceinline__ bool wait_meta(const unsigned long long *p, unsigned long long *out,
+                                          const DevErr *err, int64_t row, int64_t limit_ns) {
+  unsigned long long v = ld_meta(p);
+  if (__all_sync(FULL_MASK, v != kMetaPending)) {
+    *out = __shfl_sync(FULL_MASK, v, 0);
+    return true;
+  }
+  const uint64_t t0 = globaltimer_ns();
+  unsigned backoff = 16;
+  for (unsigned it = 0;; ++it) {
+    v = ld_meta(p);
+    if (__all_sync(FULL_MASK, v != kMetaPending)) {
+      *out = __shfl_sync(FULL_MASK, v, 0);
+      return true;
+    }
+    const bool stop = (it & 31u) == 31u &&
+                      (earlier_failed(err, row) || (int64_t)(globaltimer_ns() - t0) > limit_ns);
+    if (__any_sync(FULL_MASK, stop)) return false;
+    if (it >= 4) {
+      __nanosleep(backoff);
+      if (backoff < 64u) backoff <<= 1;
+    }
+  }
+}
+
 size_t symbolic_smem_per_warp(int cap) { return (size_t)cap * 5; }
 
 template <bool INDEP>
@@ -29,8 +83,8 @@ __global__ void __launch_bounds__(kSymThreads)
 k_symbolic_rows(int64_t n, const int64_t *__restrict__ arp, const int32_t *__restrict__ aci,
                 int k, int32_t *arena_col, uint8_t *arena_lev, int64_t arena_cap,
                 unsigned long long *arena_top, int64_t *row_off, int32_t *row_len,
-                int32_t *row_ust, int *ready, unsigned long long *ticket, DevErr *err, int cap,
-                int64_t limit_ns) {
+                int32_t *row_ust, unsigned long long *meta, unsigned long long *ticket, DevErr *err,
+                int cap, int64_t limit_ns) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
@@ -75,26 +129,54 @@ k_symbolic_rows(int64_t n, const int64_t *__restrict__ arp, const int32_t *__res
         ucol = aci + s;
         ulen = (int)(b1 - s);
       } else {
-        const bool got = wait_flag(&ready[i], err, row, limit_ns);
-        if (!__all_sync(FULL_MASK, got)) {  // any lane gave up: the warp stops
+        unsigned long long mt = 0;
+        if (!wait_meta(&meta[i], &mt, err, row, limit_ns)) {
           if (lane == 0 && !earlier_failed(err, row)) set_err(err, row, ILUK_ETIMEOUT);
           ok = false;
           break;
         }
-        const int64_t off = *((volatile int64_t *)&row_off[i]);
-        const int len = *((volatile int32_t *)&row_len[i]);
-        const int ust = *((volatile int32_t *)&row_ust[i]);
-        ucol = arena_col + off + ust;
-        ulev = arena_lev + off + ust;
-        ulen = len - ust;
+        const int64_t uoff = (int64_t)(mt >> kMetaLenBits);
+        ucol = arena_col + uoff;
+        ulev = arena_lev + uoff;
+        ulen = (int)(mt & ((1ull << kMetaLenBits) - 1));
       }
       const int limit = k - 1 - lji;  // level(i,t) must not exceed this
       for (int base = 0; base < ulen; base += 32) {
         const int q = base + lane;
         int t = INT_MAX, lt = 255;
         if (q < ulen) {
-          t = ucol[q];
-          lt = INDEP ? 0 : (int)ulev[q];
+          if (INDEP) {
+            t = ucol[q];
+            lt = 0;
+          } else {
+            t = ld_col(&ucol[q]);
+            lt = ld_lev(&ulev[q]);
+          }
+        }
+        if (!INDEP) {  // arena entries of row i not yet visible: retry them
+          bool pend = q < ulen && (t < 0 || lt == 255);
+          if (__any_sync(FULL_MASK, pend)) {
+            const uint64_t t0 = globaltimer_ns();
+            for (unsigned it = 0;; ++it) {
+              if (pend) {
+                t = ld_col(&ucol[q]);
+                lt = ld_lev(&ulev[q]);
+                pend = t < 0 || lt == 255;
+              }
+              if (!__any_sync(FULL_MASK, pend)) break;
+              const bool stop = (it & 31u) == 31u &&
+                                (earlier_failed(err, row) ||
+                                 (int64_t)(globaltimer_ns() - t0) > limit_ns);
+              if (__any_sync(FULL_MASK, stop)) {
+                ok = false;
+                break;
+              }
+            }
+            if (!ok) {
+              if (lane == 0 && !earlier_failed(err, row)) set_err(err, row, ILUK_ETIMEOUT);
+              break;
+            }
+          }
         }
         const bool cand = (q < ulen) && lt <= limit;
         const int w = lji + lt + 1;
@@ -175,8 +257,12 @@ k_symbolic_rows(int64_t n, const int64_t *__restrict__ arp, const int32_t *__res
       row_off[row] = (int64_t)off;
       row_len[row] = m;
       row_ust[row] = ust;
+      if (!INDEP) {  // readers poll the arena entries themselves: no fence needed
+        const unsigned long long mt =
+            ((unsigned long long)(off + ust) << kMetaLenBits) | (unsigned long long)(m - ust);
+        asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(&meta[row]), "l"(mt) : "memory");
+      }
     }
-    if (!INDEP) warp_publish(&ready[row], lane);
     __syncwarp();
   }
 }
@@ -213,11 +299,11 @@ cudaError_t launch_symbolic_rows(int64_t n, const int64_t *arp, const int32_t *a
   if (indep)
     k_symbolic_rows<true><<<(unsigned)grid, threads, smem, s>>>(
         n, arp, aci, k, ar.col, ar.lev, ar.cap, ar.top, ar.row_off, ar.row_len, ar.row_ust,
-        ar.ready, ar.ticket, err, cap, wait_limit());
+        ar.meta, ar.ticket, err, cap, wait_limit());
   else
     k_symbolic_rows<false><<<(unsigned)grid, threads, smem, s>>>(
         n, arp, aci, k, ar.col, ar.lev, ar.cap, ar.top, ar.row_off, ar.row_len, ar.row_ust,
-        ar.ready, ar.ticket, err, cap, wait_limit());
+        ar.meta, ar.ticket, err, cap, wait_limit());
   note_launch();
   return cudaGetLastError();
 }
