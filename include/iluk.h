@@ -91,8 +91,10 @@ typedef struct {
   const int64_t *diag;      /* int64[n], position of (i,i) in colind                */
   const int32_t *a2f;       /* int32[nnz_A], offset of A's entry inside its F row   */
   int32_t max_row;          /* longest row of F                                    */
-  int32_t depth_lower;      /* longest dependency chain of the forward sweep       */
-  int32_t depth_upper;      /* longest dependency chain of the backward sweep      */
+  int32_t depth_lower;      /* longest dependency chain of the forward sweep, or -1 */
+  int32_t depth_upper;      /* ... of the backward sweep, or -1: both are -1 until
+                               the level orders exist (first iluk_numeric on S, or
+                               iluk_sym_depth)                                      */
   int32_t k;
 } iluk_sym_view;
 
@@ -135,12 +137,15 @@ int64_t iluk_launch_count(void);
 /* Kernel timing.  While enabled, every kernel launch of the kinds below is
  * bracketed by CUDA events on its own stream.  iluk_prof_read synchronizes
  * those events and fills ms[kind] (total milliseconds) and count[kind]
- * (launches) for kind < nkinds (host arrays).  Enabling clears the records. */
+ * (launches) for kind < nkinds (host arrays).  Enabling clears the records.
+ * OVERLAPPED collects the work a call runs on a second stream beside its main
+ * kernel (the level orders built during the first numeric phase of a
+ * pattern): its time is hidden, not added, so it is kept apart. */
 enum {
   ILUK_PROF_VALIDATE = 0, ILUK_PROF_SYMBOLIC = 1, ILUK_PROF_COMPACT = 2, ILUK_PROF_DEPTH = 3,
   ILUK_PROF_NUMERIC = 4, ILUK_PROF_SWEEP = 5 /* forward sweeps */, ILUK_PROF_TRANSPOSE = 6, ILUK_PROF_IILU_BUILD = 7,
   ILUK_PROF_IILU_APPLY = 8, ILUK_PROF_SPMV = 9, ILUK_PROF_DOT = 10, ILUK_PROF_VECTOR = 11,
-  ILUK_PROF_SWEEP_BWD = 12, ILUK_PROF_BATCH = 13, ILUK_PROF_KINDS = 14
+  ILUK_PROF_SWEEP_BWD = 12, ILUK_PROF_BATCH = 13, ILUK_PROF_OVERLAPPED = 14, ILUK_PROF_KINDS = 15
 };
 int iluk_prof_enable(int on);
 int iluk_prof_read(double *ms, int64_t *count, int nkinds);
@@ -166,8 +171,10 @@ int iluk_validate(const iluk_pattern *A, iluk_info *info, void *stream);
 int iluk_symbolic(const iluk_pattern *A, int k, iluk_sym **S, iluk_info *info, void *stream);
 int iluk_sym_query(const iluk_sym *S, iluk_sym_view *view);
 /* Longest dependency chains of the forward and backward sweeps over F's
- * pattern (the number of rows on the critical path of each sweep).  Computed
- * on first call (synchronous), cached in S afterwards. */
+ * pattern (the number of rows on the critical path of each sweep).  They come
+ * with the sweeps' level orders, which the first iluk_numeric on S builds on a
+ * second stream while it factorizes; if none has run yet, this call builds
+ * them (synchronous on `stream`).  Cached in S afterwards. */
 int iluk_sym_depth(iluk_sym *S, int32_t *depth_lower, int32_t *depth_upper, void *stream);
 /* Copy S's arrays into caller-owned device buffers (any pointer may be NULL
  * to skip that array).  Asynchronous. */

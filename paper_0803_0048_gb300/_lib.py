@@ -31,7 +31,8 @@ def sched_name(byte: int) -> str:
     name = _SCHED_NAMES[kind] if kind < len(_SCHED_NAMES) else f"kind{kind}"
     return f"{name}/{w * 128}" if w else name
 PROF_KINDS = ["validate", "symbolic", "compact", "depth", "numeric", "sweep", "transpose",
-              "iilu_build", "iilu_apply", "spmv", "dot", "vector", "sweep_bwd", "batch"]
+              "iilu_build", "iilu_apply", "spmv", "dot", "vector", "sweep_bwd", "batch",
+              "overlapped"]
 
 
 class Pattern(C.Structure):

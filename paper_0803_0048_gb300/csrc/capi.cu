@@ -140,6 +140,8 @@ cudaEvent_t prof_event() {
 
 bool prof_on() { return g_prof.load(std::memory_order_relaxed); }
 
+thread_local int prof_override = -1;
+
 int prof_begin(int kind, cudaStream_t s) {
   std::lock_guard<std::mutex> lk(g_prof_mu);
   ProfRec r{kind, prof_event(), prof_event()};
@@ -380,17 +382,26 @@ int iluk_symbolic(const iluk_pattern *A, int k, iluk_sym **out, iluk_info *info,
   S->max_row = mr;
   dfree(maxrow, s);
   cleanup();
-  // level orders of the two sweeps
-  st = build_levels_pair(n, S->rowptr, S->colind, S->diag, &S->lord, &S->uord, s);
-  if (st != ILUK_OK) {
-    iluk_sym_destroy(S);
-    return fail(info, st);
-  }
-  S->depth_lower = S->lord.nlev;
-  S->depth_upper = S->uord.nlev;
+  // The level orders of the two sweeps depend only on the pattern; they are
+  // built by the first numeric phase, on a second stream while the
+  // factorization runs (see ensure_levels).
 #undef CKS
   *out = S;
   return fail(info, ILUK_OK);
+}
+
+// Build the sweeps' level orders of S once (synchronous on `s`).
+static std::mutex g_levels_mu;
+static int ensure_levels(const iluk_sym *Sc, cudaStream_t s) {
+  iluk_sym *S = const_cast<iluk_sym *>(Sc);  // the level orders are a cache of the pattern
+  std::lock_guard<std::mutex> lk(g_levels_mu);
+  if (S->levels_built) return ILUK_OK;
+  const int st = build_levels_pair(S->n, S->rowptr, S->colind, S->diag, &S->lord, &S->uord, s);
+  if (st != ILUK_OK) return st;
+  S->depth_lower = S->lord.nlev;
+  S->depth_upper = S->uord.nlev;
+  S->levels_built = true;
+  return ILUK_OK;
 }
 
 int iluk_sym_query(const iluk_sym *S, iluk_sym_view *v) {
@@ -423,8 +434,9 @@ int iluk_sym_export(const iluk_sym *S, int64_t *rowptr, int32_t *colind, uint8_t
 }
 
 int iluk_sym_depth(iluk_sym *S, int32_t *depth_lower, int32_t *depth_upper, void *stream) {
-  (void)stream;
   if (!S) return ILUK_EINVAL;
+  const int st = ensure_levels(S, (cudaStream_t)stream);
+  if (st != ILUK_OK) return st;
   if (depth_lower) *depth_lower = S->depth_lower;
   if (depth_upper) *depth_upper = S->depth_upper;
   return ILUK_OK;
@@ -459,8 +471,25 @@ static int numeric_into(iluk_fac *F, const double *A_val, iluk_info *info, cudaS
   // the numeric phase also publishes the reciprocals of the diagonal
   CK(launch_numeric(S, A_val, F->val, F->rdiag, reinterpret_cast<unsigned long long *>(F->sync),
                     F->err, s));
+  // First factorization of this pattern: build the sweeps' level orders on a
+  // second stream meanwhile (they read only the pattern; the numeric kernel
+  // leaves room on every SM for the two level-building CTAs).
+  int lst = ILUK_OK;
+  if (!S->levels_built) {
+    cudaStream_t side = nullptr;
+    if (cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking) == cudaSuccess) {
+      prof_override = ILUK_PROF_OVERLAPPED;
+      lst = ensure_levels(S, side);
+      prof_override = -1;
+      cudaStreamDestroy(side);
+    } else {
+      cudaGetLastError();
+      lst = ensure_levels(S, s);
+    }
+  }
   int64_t row;
   int st = read_err(F->err, s, &row, nullptr);
+  if (st == ILUK_OK && lst != ILUK_OK) st = lst;
   CK(launch_fill_err(F->err, s));
   // factor values changed: drop the transpose (its level orders depend only
   // on the pattern and are kept)
@@ -859,6 +888,11 @@ int iluk_batch_create(const iluk_batch_item *items, int64_t nitems, int restart,
     if (!it.S || !it.a_rowptr || !it.b || !it.x || (it.S->nnzA && (!it.a_colind || !it.a_val))) {
       delete B;
       return ILUK_EINVAL;
+    }
+    const int lst = ensure_levels(it.S, s);  // the in-CTA sweeps walk the level orders
+    if (lst != ILUK_OK) {
+      delete B;
+      return lst;
     }
     batch_pack_item(hitems.data() + i * batch_item_bytes(), it.S, it.a_rowptr, it.a_colind,
                     it.a_val, it.b, it.x);

@@ -31,6 +31,7 @@ struct iluk_sym {
   int32_t max_row = 0;
   int32_t depth_lower = -1, depth_upper = -1;
   LevelOrder lord, uord;       // forward / backward sweep level orders
+  bool levels_built = false;   // lord/uord are built by the first numeric phase
 };
 
 struct iluk_fac {
@@ -65,11 +66,15 @@ void note_launch();              // counts kernel launches (iluk_launch_count)
 // (iluk_prof_enable / iluk_prof_read).  Kinds are listed in include/iluk.h.
 bool prof_on();
 int prof_begin(int kind, cudaStream_t s);
+// While >= 0, every scope opened by this thread is counted under this kind.
+extern thread_local int prof_override;
 void prof_end(int slot, cudaStream_t s);
 struct ProfScope {
   int slot;
   cudaStream_t s;
-  ProfScope(int kind, cudaStream_t st) : slot(prof_on() ? prof_begin(kind, st) : -1), s(st) {}
+  ProfScope(int kind, cudaStream_t st)
+      : slot(prof_on() ? prof_begin(prof_override >= 0 ? prof_override : kind, st) : -1),
+        s(st) {}
   ~ProfScope() {
     if (slot >= 0) prof_end(slot, s);
   }
