@@ -135,11 +135,40 @@ def alg_bytes(n, nnzA, nnzF, nnzL):
         "numeric": 12 * nnzA + 16 * (n + 1) + 4 * nnzF + 8 * n + 8 * nnzF,
         # read A pattern, write F pattern + levels via the arena, diagonal
         "symbolic": 8 * (n + 1) + 4 * nnzA + 5 * nnzF,
-        # one sweep: its half of F (cols + vals), row pointers, diagonal, in/out vectors
-        "sweep": (12 * nnzL + 8 * (n + 1) + 8 * n + 24 * n + 12 * nnzU + 8 * (n + 1) + 8 * n
-                  + 24 * n) / 2.0,
+        # forward sweep: F's strictly lower half (cols + vals), row pointers, diagonal
+        # positions, the input read, the output written, the next buffer re-armed
+        "sweep": 12 * nnzL + 8 * (n + 1) + 8 * n + 24 * n,
+        # backward sweep: F's upper half with the diagonal, the same vectors, and the
+        # double-double reciprocals of the diagonal
+        "sweep_bwd": 12 * nnzU + 8 * (n + 1) + 8 * n + 24 * n + 16 * n,
         "spmv": 12 * nnzA + 8 * (n + 1) + 16 * n,
     }
+
+
+def sources_digest():
+    """Digest of the sweep kernels' sources, as stamped on measured traffic."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("sweeps.cu", "common.cuh"):
+        with open(os.path.join(ROOT, "paper_0803_0048_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kind, k):
+    """DRAM bytes per launch of `kind` from the committed ncu summary, or None
+    when there is none or the kernel sources changed since it was captured."""
+    path = os.path.join(ROOT, "profiles", "sweep_band160k_k2.md")
+    if not os.path.exists(path):
+        return None
+    digest = sources_digest()
+    for line in open(path):
+        if not line.startswith("traffic:"):
+            continue
+        f = dict(x.split("=", 1) for x in line.split()[1:])
+        if f.get("kernel") == kind and f.get("k") == str(k) and f.get("sources") == digest:
+            return int(f["bytes"])
+    return None
 
 
 def ours(args):
@@ -236,22 +265,31 @@ def ours(args):
     depth = S.depth()
     ab = alg_bytes(n, nnzA, nnzF, nnzL)
     hbm, peak_src = measured_peaks()
-    kinds = {"numeric": "numeric", "symbolic": "symbolic", "sweep": "sweep", "sweep_bwd": "sweep",
-             "spmv": "spmv"}
+    kinds = {"numeric": "numeric", "symbolic": "symbolic", "sweep": "sweep",
+             "sweep_bwd": "sweep_bwd", "spmv": "spmv"}
     per_kind = {}
     for kname, (tot_ms, cnt) in prof.items():
         if cnt:
             per_kind[kname] = {"ms_total_per_step": tot_ms / args.steps,
                                "launches_per_step": cnt / args.steps,
                                "ms_per_launch": tot_ms / cnt}
+    # per phase: algorithmic GB/s, fraction of the measured HBM peak, and the time
+    # per level of the dependency DAG the phase walks (its critical path)
+    levels_of = {"symbolic": depth[0], "numeric": depth[0], "sweep": depth[0],
+                 "sweep_bwd": depth[1]}
+    for kname, rec in per_kind.items():
+        if kname in kinds:
+            gbps = ab[kinds[kname]] / (rec["ms_per_launch"] / 1e3) / 1e9
+            rec["alg_bytes_per_launch"] = ab[kinds[kname]]
+            rec["alg_GBps"] = round(gbps, 3)
+            rec["hbm_frac"] = round(gbps / hbm, 6)
+        if kname in levels_of and levels_of[kname] > 0:
+            rec["levels"] = levels_of[kname]
+            rec["ns_per_level"] = round(rec["ms_per_launch"] * 1e6 / levels_of[kname], 1)
     dom = max((k for k in per_kind if k in kinds), key=lambda k: per_kind[k]["ms_total_per_step"])
     dur_s = per_kind[dom]["ms_per_launch"] / 1e3
     achieved = ab[kinds[dom]] / dur_s / 1e9
-    traffic = None
-    tpath = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tpath):
-        with open(tpath) as f:
-            traffic = json.load(f).get(f"{dom}_k{Pb.k}")
+    traffic = measured_traffic(dom, Pb.k)
 
     out = {
         "metric": METRIC, "value": round(ms, 4), "unit": "ms", "n_gpus": world,
