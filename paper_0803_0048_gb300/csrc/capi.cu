@@ -303,7 +303,10 @@ int iluk_symbolic(const iluk_pattern *A, int k, iluk_sym **out, iluk_info *info,
   int cap = k <= 1 ? 256 : 1024;
   int64_t mult = (k == 0) ? 1 : (k == 1) ? 8 : (k == 2) ? 17 : 65;
   int64_t arena_cap = nnz * mult + 1024;
-  const int max_cap = max_smem_optin() / 5 / 32 * 32;
+  // level-map window of the symbolic walk (0: sorted lists only)
+  int mapw = symbolic_map_width(n, A->rowptr, A->colind, k, s);
+  if (symbolic_map_per_warp(mapw) + 5 * 1024 > (size_t)max_smem_optin()) mapw = 0;
+  const int max_cap = (int)((max_smem_optin() - symbolic_map_per_warp(mapw)) / 5 / 32 * 32);
   size_t free_b = 0, total_b = 0;
   cudaMemGetInfo(&free_b, &total_b);
   const int64_t arena_max = (int64_t)(free_b / 2 / 5);
@@ -323,7 +326,7 @@ int iluk_symbolic(const iluk_pattern *A, int k, iluk_sym **out, iluk_info *info,
     CKS(cudaMemsetAsync(ar.ticket, 0, sizeof(unsigned long long), s));
     CKS(cudaMemsetAsync(ar.top, 0, sizeof(unsigned long long), s));
     CKS(launch_fill_err(err, s));
-    CKS(launch_symbolic_rows(n, A->rowptr, A->colind, k, ar, err, cap, s));
+    CKS(launch_symbolic_rows(n, A->rowptr, A->colind, k, ar, err, cap, mapw, s));
     int64_t row;
     uint64_t need = 0;
     st = read_err(err, s, &row, &need);

@@ -101,8 +101,11 @@ struct SymArena {
   unsigned long long *meta; unsigned long long *ticket;
 };
 cudaError_t launch_symbolic_rows(int64_t n, const int64_t *arp, const int32_t *aci, int k,
-                                 const SymArena &ar, DevErr *err, int cap, cudaStream_t s);
+                                 const SymArena &ar, DevErr *err, int cap, int mapw,
+                                 cudaStream_t s);
+int symbolic_map_width(int64_t n, const int64_t *arp, const int32_t *aci, int k, cudaStream_t s);
 size_t symbolic_smem_per_warp(int cap);
+size_t symbolic_map_per_warp(int mapw);  // per-warp shared memory of the level map
 cudaError_t launch_symbolic_compact(int64_t n, const SymArena &ar, const int64_t *frp,
                                     int32_t *fci, uint8_t *flev, int64_t *fdiag, int32_t *maxrow,
                                     cudaStream_t s);

@@ -76,7 +76,57 @@ __device__ __forceinline__ bool wait_meta(const unsigned long long *p, unsigned 
   }
 }
 
+// Level map of the row being built (k >= 2): one byte per column over a window
+// that starts at the row's first column of A.  Every column of the final row
+// lies at or above that column: a fill column t comes from the upper part of
+// a pivot i that is itself a column of the row, so t > i >= the first column.
+// Only the upper end can leave the window; a row that does falls back to the
+// sorted list.
+// The window width (a power of two, mapw columns) is chosen per call from the
+// widest row of A: twice its span, at most kMaxMapCols; 0 selects the list.
+// The cap is also an occupancy choice: rows are claimed in index order before
+// any level information exists, so a matrix with wide wavefronts (a 3D grid)
+// needs many warps in flight, which larger maps would crowd out.
+constexpr int kMaxMapCols = 8192;
+
 size_t symbolic_smem_per_warp(int cap) { return (size_t)cap * 5; }
+// per warp: the level bytes, then a presence bitmap and a pivot bitmap (level < k)
+size_t symbolic_map_per_warp(int mapw) { return (size_t)mapw + (size_t)mapw / 4; }
+
+// Window for the level map: twice the widest column span of a row of A,
+// rounded up to a power of two (at least 1024); 0 when that exceeds
+// kMaxMapCols.  Synchronous.
+__global__ void k_row_span(int64_t n, const int64_t *__restrict__ arp,
+                           const int32_t *__restrict__ aci, int32_t *span) {
+  int32_t mx = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    if (arp[i + 1] > arp[i]) {
+      const int32_t w = aci[arp[i + 1] - 1] - aci[arp[i]] + 1;
+      if (w > mx) mx = w;
+    }
+  mx = __reduce_max_sync(FULL_MASK, mx);
+  if ((threadIdx.x & 31) == 0 && mx > 0) atomicMax(span, mx);
+}
+
+int symbolic_map_width(int64_t n, const int64_t *arp, const int32_t *aci, int k,
+                       cudaStream_t s) {
+  if (k < 2 || n == 0) return 0;
+  int32_t *d = nullptr;
+  if (cudaMallocAsync((void **)&d, sizeof(int32_t), s) != cudaSuccess) return 0;
+  int32_t span = 0;
+  cudaMemsetAsync(d, 0, sizeof(int32_t), s);
+  int64_t b = (n + 255) / 256;
+  if (b > (int64_t)num_sms() * 8) b = (int64_t)num_sms() * 8;
+  k_row_span<<<(unsigned)b, 256, 0, s>>>(n, arp, aci, d);
+  note_launch();
+  cudaMemcpyAsync(&span, d, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+  cudaFreeAsync(d, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return 0;
+  int64_t w = 1024;
+  while (w < 2 * (int64_t)span) w <<= 1;
+  return w <= kMaxMapCols ? (int)w : 0;
+}
 
 template <bool INDEP>
 __global__ void __launch_bounds__(kSymThreads)
@@ -84,13 +134,17 @@ k_symbolic_rows(int64_t n, const int64_t *__restrict__ arp, const int32_t *__res
                 int k, int32_t *arena_col, uint8_t *arena_lev, int64_t arena_cap,
                 unsigned long long *arena_top, int64_t *row_off, int32_t *row_len,
                 int32_t *row_ust, unsigned long long *meta, unsigned long long *ticket, DevErr *err,
-                int cap, int64_t limit_ns) {
+                int cap, int mapw, int64_t limit_ns) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   const int nwarps = blockDim.x >> 5;
   int32_t *cols = reinterpret_cast<int32_t *>(smem) + (size_t)wib * cap;
   uint8_t *lev = smem + (size_t)nwarps * cap * 4 + (size_t)wib * cap;
+  uint8_t *map = mapw ? smem + (size_t)nwarps * cap * 5 + (size_t)wib * (mapw + mapw / 4)
+                      : nullptr;
+  uint32_t *pres = mapw ? reinterpret_cast<uint32_t *>(map + mapw) : nullptr;
+  uint32_t *piv = mapw ? pres + mapw / 32 : nullptr;
 
   for (;;) {
     unsigned long long tk = 0;
@@ -115,7 +169,166 @@ k_symbolic_rows(int64_t n, const int64_t *__restrict__ arp, const int32_t *__res
     __syncwarp();
 
     bool ok = true;
-    for (int p = 0; p < m; ++p) {
+    bool built = false;  // row finished by the level map (k >= 2)
+    if (!INDEP && mapw) {
+      // Level-map form of the same walk: map[c - base] = level of column c,
+      // valid where the presence bit is set; a second bitmap marks possible
+      // pivots (level < k).  A candidate is one min-update, the next pivot a
+      // scan of 32 bitmap words at a time, the finished row a popcount
+      // compaction.  The result is the sorted-list walk's: candidates are
+      // distinct columns, each changes only its own entry, and pivots are
+      // still taken in ascending order, inserted ones included.
+      const int32_t base = cols[0];
+      int hi = cols[m - 1] - base;  // highest occupied offset
+      bool fits = hi < mapw;
+      if (fits) {
+        for (int w = lane; w < mapw / 32; w += 32) {
+          pres[w] = 0u;
+          piv[w] = 0u;
+        }
+        __syncwarp();
+        for (int q = lane; q < m; q += 32) {  // A's entries: level 0 < k
+          const int d = cols[q] - base;
+          map[d] = 0;
+          atomicOr(&pres[d >> 5], 1u << (d & 31));
+          atomicOr(&piv[d >> 5], 1u << (d & 31));
+        }
+        __syncwarp();
+        const int jlim = (int)(row - base);  // pivots lie at offsets below the diagonal
+        const int jw = (jlim + 31) >> 5;     // bitmap words holding such offsets
+        int cur = -1;
+        for (;;) {
+          int nxt = -1;
+          const int from = cur + 1;
+          for (int w0 = from >> 5; w0 < jw; w0 += 32) {
+            const int wi = w0 + lane;
+            uint32_t bits = 0u;
+            if (wi < jw) {
+              bits = piv[wi];
+              if (wi == (from >> 5)) bits &= ~0u << (from & 31);
+              const int room = jlim - wi * 32;  // offsets at or beyond jlim are not pivots
+              if (room < 32) bits &= (1u << room) - 1u;
+            }
+            const unsigned b = __ballot_sync(FULL_MASK, bits != 0u);
+            if (b) {
+              const int l = __ffs(b) - 1;
+              const uint32_t wb = __shfl_sync(FULL_MASK, bits, l);
+              nxt = (w0 + l) * 32 + __ffs(wb) - 1;
+              break;
+            }
+          }
+          if (nxt < 0) break;
+          cur = nxt;
+          const int i = base + nxt;
+          const int lji = map[nxt];
+          unsigned long long mt = 0;
+          if (!wait_meta(&meta[i], &mt, err, row, limit_ns)) {
+            if (lane == 0 && !earlier_failed(err, row)) set_err(err, row, ILUK_ETIMEOUT);
+            ok = false;
+            break;
+          }
+          const int64_t uoff = (int64_t)(mt >> kMetaLenBits);
+          const int ulen = (int)(mt & ((1ull << kMetaLenBits) - 1));
+          const int limit = k - 1 - lji;
+          for (int b0 = 0; b0 < ulen; b0 += 32) {
+            const int q = b0 + lane;
+            int t = 0, lt = 255;
+            if (q < ulen) {
+              t = ld_col(&arena_col[uoff + q]);
+              lt = ld_lev(&arena_lev[uoff + q]);
+            }
+            bool pend = q < ulen && (t < 0 || lt == 255);
+            if (__any_sync(FULL_MASK, pend)) {  // entries of row i not yet visible
+              const uint64_t t0 = globaltimer_ns();
+              for (unsigned it = 0;; ++it) {
+                if (pend) {
+                  t = ld_col(&arena_col[uoff + q]);
+                  lt = ld_lev(&arena_lev[uoff + q]);
+                  pend = t < 0 || lt == 255;
+                }
+                if (!__any_sync(FULL_MASK, pend)) break;
+                const bool stop = (it & 31u) == 31u &&
+                                  (earlier_failed(err, row) ||
+                                   (int64_t)(globaltimer_ns() - t0) > limit_ns);
+                if (__any_sync(FULL_MASK, stop)) {
+                  ok = false;
+                  break;
+                }
+              }
+              if (!ok) {
+                if (lane == 0 && !earlier_failed(err, row)) set_err(err, row, ILUK_ETIMEOUT);
+                break;
+              }
+            }
+            if (q < ulen && lt <= limit) {
+              const int d = t - base;
+              if (d >= mapw) {
+                fits = false;
+              } else {
+                const int w = lji + lt + 1;  // <= k
+                const uint32_t bit = 1u << (d & 31);
+                if (!(pres[d >> 5] & bit)) {  // insertion
+                  map[d] = (uint8_t)w;
+                  atomicOr(&pres[d >> 5], bit);
+                  if (w < k) atomicOr(&piv[d >> 5], bit);
+                  if (d > hi) hi = d;
+                } else if (w < (int)map[d]) {  // lower level
+                  if ((int)map[d] >= k && w < k) atomicOr(&piv[d >> 5], bit);
+                  map[d] = (uint8_t)w;
+                }
+              }
+            }
+            __syncwarp();
+          }
+          if (!ok) break;
+          if (!__all_sync(FULL_MASK, fits)) {
+            fits = false;
+            break;
+          }
+        }
+        if (!ok) return;
+      }
+      if (fits) {
+        hi = __reduce_max_sync(FULL_MASK, hi);
+        const int nw = (hi >> 5) + 1;
+        int mm = 0;
+        for (int w0 = 0; w0 < nw; w0 += 32) {
+          const int wi = w0 + lane;
+          uint32_t bits = wi < nw ? pres[wi] : 0u;
+          const int c = __popc(bits);
+          int incl = c;  // inclusive prefix of the counts over the lanes
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(FULL_MASK, incl, o);
+            if (lane >= o) incl += y;
+          }
+          int pos = mm + incl - c;
+          while (bits) {
+            const int d = wi * 32 + __ffs(bits) - 1;
+            bits &= bits - 1u;
+            if (pos < cap) {
+              cols[pos] = base + d;
+              lev[pos] = map[d];
+            }
+            ++pos;
+          }
+          mm += __shfl_sync(FULL_MASK, incl, 31);
+        }
+        if (mm > cap) {
+          if (lane == 0) {
+            set_err(err, row, ILUK_ENOMEM);
+            atomicMax(&err->need, (unsigned long long)mm);
+          }
+          return;
+        }
+        m = mm;
+        built = true;
+        __syncwarp();
+      }
+      // else: the row left the window; cols/lev still hold A's row
+    }
+
+    for (int p = 0; p < m && !built; ++p) {
       const int i = cols[p];
       if (i >= row) break;
       const int lji = lev[p];
@@ -268,9 +481,11 @@ k_symbolic_rows(int64_t n, const int64_t *__restrict__ arp, const int32_t *__res
 }
 
 cudaError_t launch_symbolic_rows(int64_t n, const int64_t *arp, const int32_t *aci, int k,
-                                 const SymArena &ar, DevErr *err, int cap, cudaStream_t s) {
+                                 const SymArena &ar, DevErr *err, int cap, int mapw,
+                                 cudaStream_t s) {
   ProfScope prof_scope(ILUK_PROF_SYMBOLIC, s);
-  const size_t per_warp = symbolic_smem_per_warp(cap);
+  if (k < 2) mapw = 0;
+  const size_t per_warp = symbolic_smem_per_warp(cap) + symbolic_map_per_warp(mapw);
   int warps = kSymThreads / 32;
   while (warps > 1 && per_warp * warps > (size_t)max_smem_optin()) warps >>= 1;
   const size_t smem = per_warp * warps;
@@ -299,11 +514,11 @@ cudaError_t launch_symbolic_rows(int64_t n, const int64_t *arp, const int32_t *a
   if (indep)
     k_symbolic_rows<true><<<(unsigned)grid, threads, smem, s>>>(
         n, arp, aci, k, ar.col, ar.lev, ar.cap, ar.top, ar.row_off, ar.row_len, ar.row_ust,
-        ar.meta, ar.ticket, err, cap, wait_limit());
+        ar.meta, ar.ticket, err, cap, mapw, wait_limit());
   else
     k_symbolic_rows<false><<<(unsigned)grid, threads, smem, s>>>(
         n, arp, aci, k, ar.col, ar.lev, ar.cap, ar.top, ar.row_off, ar.row_len, ar.row_ust,
-        ar.meta, ar.ticket, err, cap, wait_limit());
+        ar.meta, ar.ticket, err, cap, mapw, wait_limit());
   note_launch();
   return cudaGetLastError();
 }
