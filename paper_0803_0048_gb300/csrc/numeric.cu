@@ -230,8 +230,9 @@ k_numeric(int64_t n, int64_t nbatch, const int64_t *__restrict__ arp,
           const int32_t *__restrict__ a2f, const double *__restrict__ aval, int64_t astride,
           const int64_t *__restrict__ frp, const int32_t *__restrict__ fci,
           const int64_t *__restrict__ fdiag, const int64_t *__restrict__ pinfo, double *fval,
-          int64_t fstride, double *rdiag, unsigned long long *ticket, DevErr *errs, int cap,
-          int map_cap, int64_t limit_ns, int64_t hold) {
+          int64_t fstride, double *rdiag, const int32_t *__restrict__ order,
+          unsigned long long *ticket, DevErr *errs, int cap, int map_cap, int64_t limit_ns,
+          int64_t hold) {
   // per warp: values, pivot infos (cap each), columns, then the column map
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31;
@@ -250,8 +251,12 @@ k_numeric(int64_t n, int64_t nbatch, const int64_t *__restrict__ arp,
     if (lane == 0) tk = atomicAdd(ticket, 1ull);
     const int64_t t = (int64_t)__shfl_sync(FULL_MASK, tk, 0);
     if (t >= total) return;
-    const int64_t row = t / nbatch;
-    const int64_t set = t - row * nbatch;
+    // tickets walk the rows in level order when it is known (every row's
+    // pivots then lie at earlier tickets, as in index order), else in index
+    // order
+    const int64_t slot = t / nbatch;
+    const int64_t set = t - slot * nbatch;
+    const int64_t row = order ? (int64_t)order[slot] : slot;
     DevErr *err = errs + set;
     if (earlier_failed(err, row)) continue;
     double *fv = fval + set * fstride;
@@ -396,6 +401,8 @@ static int numeric_cap(const iluk_sym *S, int *warps_out, int *map_out, size_t *
 static cudaError_t launch_numeric_impl(const iluk_sym *S, int64_t nbatch, const double *avals,
                                        double *fvals, double *rdiag, unsigned long long *ticket,
                                        DevErr *errs, cudaStream_t s) {
+  // the forward level order, once built, is a valid and better-spread order
+  const int32_t *order = S->levels_built ? S->lord.corder : nullptr;
   ProfScope prof_scope(ILUK_PROF_NUMERIC, s);
   int warps, map_cap;
   size_t smem;
@@ -425,7 +432,7 @@ static cudaError_t launch_numeric_impl(const iluk_sym *S, int64_t nbatch, const 
   if (grid < 1) grid = 1;
   k_numeric<<<(unsigned)grid, warps * 32, smem, s>>>(
       S->n, nbatch, S->arowptr, S->a2f, avals, S->nnzA, S->rowptr, S->colind, S->diag, S->pinfo,
-      fvals, S->nnz, rdiag, ticket, errs, cap, map_cap, wait_limit(), hold_row());
+      fvals, S->nnz, rdiag, order, ticket, errs, cap, map_cap, wait_limit(), hold_row());
   note_launch();
   return cudaGetLastError();
 }
