@@ -435,7 +435,11 @@ void orc_iiluk_apply(int64_t n, const int64_t *frp, const int32_t *fci, const do
 
 /* ------------------------------------------------------------------------ */
 /* Restarted GMRES(m), right preconditioned (Sec. 2: the solver works with   */
-/* A U~^-1 L~^-1), x0 = 0, modified Gram-Schmidt, Givens rotations.          */
+/* A U~^-1 L~^-1), x0 = 0, modified Gram-Schmidt, Givens rotations.  The     */
+/* preconditioned basis vectors z_j = M^-1 v_j of a cycle are kept, and the  */
+/* cycle ends with x = x + Z y (the flexible-GMRES form of Saad 1993, equal  */
+/* to x + M^-1 V y in exact arithmetic for a fixed M), so no extra           */
+/* application of M is needed.                                               */
 /*                                                                           */
 /* Inner products (Sec. 3.5 keeps them in a fixed order): mode 0 sums        */
 /* x_i*y_i left to right; mode 1 uses a fixed tree: 4096 partial sums, the   */
@@ -509,6 +513,7 @@ int orc_gmres(int64_t n, const int64_t *arp, const int32_t *aci, const double *a
   if (m < 1 || n < 0) return ORC_EINVAL;
   size_t N = (size_t)(n ? n : 1);
   double *V = (double *)malloc(N * (size_t)(m + 1) * sizeof(double));
+  double *Z = (double *)malloc(N * (size_t)m * sizeof(double));
   double *H = (double *)calloc((size_t)(m + 1) * (size_t)m, sizeof(double)); /* H[i*m+j] */
   double *cs = (double *)malloc((size_t)m * sizeof(double));
   double *sn = (double *)malloc((size_t)m * sizeof(double));
@@ -516,7 +521,6 @@ int orc_gmres(int64_t n, const int64_t *arp, const int32_t *aci, const double *a
   double *yv = (double *)malloc((size_t)m * sizeof(double));
   double *r = (double *)malloc(N * sizeof(double));
   double *w = (double *)malloc(N * sizeof(double));
-  double *z = (double *)malloc(N * sizeof(double));
   double *u = (double *)malloc(N * sizeof(double));
   int status = ORC_ENOCONV;
   int iters = 0, cycles = 0;
@@ -540,8 +544,9 @@ int orc_gmres(int64_t n, const int64_t *arp, const int32_t *aci, const double *a
     int jend = -1;
     for (int j = 0; j < m; ++j) {
       double *vj = V + (size_t)j * N;
-      prec_apply(&M, n, vj, z);
-      orc_spmv(n, arp, aci, av, z, w);
+      double *zj = Z + (size_t)j * N;
+      prec_apply(&M, n, vj, zj);
+      orc_spmv(n, arp, aci, av, zj, w);
       for (int i = 0; i <= j; ++i) {                 /* modified Gram-Schmidt */
         double *vi = V + (size_t)i * N;
         double hij = dot_mode(n, w, vi, dotmode);
@@ -574,7 +579,7 @@ int orc_gmres(int64_t n, const int64_t *arp, const int32_t *aci, const double *a
       }
       if (fabs(gv[j + 1]) / bnorm <= rtol || iters >= maxit || breakdown) break;
     }
-    /* y = H^-1 g (back substitution), u = V y, x = x + M^-1 u */
+    /* y = H^-1 g (back substitution), u = Z y, x = x + u */
     for (int i = jend; i >= 0; --i) {
       double s = gv[i];
       for (int l = i + 1; l <= jend; ++l) { double prod = H[i * m + l] * yv[l]; s = s - prod; }
@@ -582,15 +587,14 @@ int orc_gmres(int64_t n, const int64_t *arp, const int32_t *aci, const double *a
     }
     for (int64_t q = 0; q < n; ++q) {
       double s = 0.0;
-      for (int j = 0; j <= jend; ++j) { double prod = yv[j] * V[(size_t)j * N + q]; s = s + prod; }
+      for (int j = 0; j <= jend; ++j) { double prod = yv[j] * Z[(size_t)j * N + q]; s = s + prod; }
       u[q] = s;
     }
-    prec_apply(&M, n, u, z);
-    for (int64_t q = 0; q < n; ++q) x[q] = x[q] + z[q];
+    for (int64_t q = 0; q < n; ++q) x[q] = x[q] + u[q];
   }
 done:
   info_out[0] = iters; info_out[1] = relres; info_out[2] = cycles;
-  free(V); free(H); free(cs); free(sn); free(gv); free(yv); free(r); free(w); free(z); free(u);
+  free(V); free(Z); free(H); free(cs); free(sn); free(gv); free(yv); free(r); free(w); free(u);
   return status;
 }
 

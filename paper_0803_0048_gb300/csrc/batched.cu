@@ -46,7 +46,7 @@ struct BatchResultDev {
 };
 
 struct BatchWork {
-  double *fval, *V, *w, *z, *u, *tmp;
+  double *fval, *V, *w, *z, *u, *tmp;  // z: the m preconditioned basis vectors of a cycle
   int64_t ldv;  // stride between basis vectors
 };
 
@@ -277,8 +277,9 @@ k_batch_solve(const BatchItemDev *items, int64_t nitems, BatchResultDev *results
       int jend = -1;
       for (int j = 0; j < m; ++j) {
         double *vj = wk.V + (size_t)j * wk.ldv;
-        cta_apply<NT>(it, wk.fval, vj, wk.tmp, wk.z);
-        cta_spmv<NT>(it, wk.z, wk.w, nullptr);
+        double *zj = wk.z + (size_t)j * wk.ldv;
+        cta_apply<NT>(it, wk.fval, vj, wk.tmp, zj);
+        cta_spmv<NT>(it, zj, wk.w, nullptr);
         double hval = cta_dot<NT>(n, wk.w, nullptr, 0.0, false, wk.V, sh, false);
         if (threadIdx.x == 0) H[0 * m + j] = hval;
         for (int i = 0; i <= j; ++i) {
@@ -328,15 +329,13 @@ k_batch_solve(const BatchItemDev *items, int64_t nitems, BatchResultDev *results
         }
       }
       __syncthreads();
+      // x += Z y, each entry summed over j in order from +0.0
       for (int64_t q = threadIdx.x; q < n; q += NT) {
         double sacc = 0.0;
         for (int jj = 0; jj <= jend; ++jj)
-          sacc = __dadd_rn(sacc, __dmul_rn(yv[jj], wk.V[(size_t)jj * wk.ldv + q]));
-        wk.u[q] = sacc;
+          sacc = __dadd_rn(sacc, __dmul_rn(yv[jj], wk.z[(size_t)jj * wk.ldv + q]));
+        it.x[q] = __dadd_rn(it.x[q], sacc);
       }
-      __syncthreads();
-      cta_apply<NT>(it, wk.fval, wk.u, wk.tmp, wk.z);
-      for (int64_t i = threadIdx.x; i < n; i += NT) it.x[i] = __dadd_rn(it.x[i], wk.z[i]);
       __syncthreads();
     }
     if (threadIdx.x == 0) {

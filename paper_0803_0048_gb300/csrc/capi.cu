@@ -926,7 +926,7 @@ int iluk_batch_create(const iluk_batch_item *items, int64_t nitems, int restart,
     if (dalloc(&fval, maxf, s) != cudaSuccess || (B->bufs.push_back(fval), false) ||
         dalloc(&V, (size_t)ldv * (restart + 1), s) != cudaSuccess ||
         (B->bufs.push_back(V), false) || dalloc(&vw, ldv, s) != cudaSuccess ||
-        (B->bufs.push_back(vw), false) || dalloc(&z, ldv, s) != cudaSuccess ||
+        (B->bufs.push_back(vw), false) || dalloc(&z, (size_t)ldv * restart, s) != cudaSuccess ||
         (B->bufs.push_back(z), false) || dalloc(&u, ldv, s) != cudaSuccess ||
         (B->bufs.push_back(u), false) || dalloc(&tmp, ldv, s) != cudaSuccess) {
       cleanup();
@@ -1053,12 +1053,14 @@ int gmres_solve(const iluk_pattern *A, const double *A_val, int prec_kind, void 
     ov = tv;
   }
   const int64_t ldv = n > 0 ? n : 1;
-  double *V = nullptr, *w = nullptr, *z = nullptr, *u = nullptr, *Hd = nullptr, *dsc = nullptr,
+  // Z keeps the preconditioned basis z_j = M^-1 v_j of a cycle, which ends
+  // with x += Z y (the flexible-GMRES form: no extra application of M)
+  double *V = nullptr, *Z = nullptr, *w = nullptr, *u = nullptr, *Hd = nullptr, *dsc = nullptr,
          *dy = nullptr;
   DotScratch ds{};
   CK(dalloc(&V, (size_t)ldv * (m + 1), s));
+  CK(dalloc(&Z, (size_t)ldv * m, s));
   CK(dalloc(&w, ldv, s));
-  CK(dalloc(&z, ldv, s));
   CK(dalloc(&u, ldv, s));
   CK(dalloc(&Hd, (size_t)(m + 1) * m, s));
   CK(dalloc(&dsc, 4, s));
@@ -1115,8 +1117,9 @@ int gmres_solve(const iluk_pattern *A, const double *A_val, int prec_kind, void 
       for (int j = 0; j < m; ++j) {
         double *vj = V + (size_t)j * ldv;
         double *hc = Hd + (size_t)j * (m + 1);  // column j of H
-        CK(precond(vj, z));
-        CK(launch_spmv(n, orp, oci, ov, z, w, nullptr, s));
+        double *zj = Z + (size_t)j * ldv;
+        CK(precond(vj, zj));
+        CK(launch_spmv(n, orp, oci, ov, zj, w, nullptr, s));
         CK(launch_dot(n, w, V, hc + 0, 0, ds, s));
         for (int i = 0; i <= j; ++i) {
           const double *vi = V + (size_t)i * ldv;
@@ -1162,9 +1165,8 @@ int gmres_solve(const iluk_pattern *A, const double *A_val, int prec_kind, void 
         yv[i] = sacc / H[(size_t)i * m + i];
       }
       CK(cudaMemcpyAsync(dy, yv.data(), (jend + 1) * sizeof(double), cudaMemcpyHostToDevice, s));
-      CK(launch_combine(n, V, ldv, dy, jend + 1, u, s));
-      CK(precond(u, z));
-      CK(launch_add(n, x, z, s));
+      CK(launch_combine(n, Z, ldv, dy, jend + 1, u, s));
+      CK(launch_add(n, x, u, s));
     }
   }
   CK(cudaStreamSynchronize(s));
@@ -1177,7 +1179,7 @@ int gmres_solve(const iluk_pattern *A, const double *A_val, int prec_kind, void 
       status = pst;
     }
   }
-  dfree(V, s); dfree(w, s); dfree(z, s); dfree(u, s); dfree(Hd, s); dfree(dsc, s); dfree(dy, s);
+  dfree(V, s); dfree(Z, s); dfree(w, s); dfree(u, s); dfree(Hd, s); dfree(dsc, s); dfree(dy, s);
   dfree(ds.partial, s); dfree(ds.counter, s);
   dfree(trp, s); dfree(tci, s); dfree(tv, s);
   if (info) {
