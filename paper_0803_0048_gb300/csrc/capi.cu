@@ -243,6 +243,7 @@ void iluk_sym_destroy(iluk_sym *S) {
   dfree(S->arowptr, s);
   dfree(S->a2f, s);
   dfree(S->pinfo, s);
+  dfree(S->tinfo, s);
   dfree(S->lord.order, s);
   dfree(S->uord.order, s);
   dfree(S->lord.corder, s);
@@ -731,7 +732,12 @@ int iiluk_build(const iluk_fac *F, iiluk **out, iluk_info *info, void *stream) {
   if (e == cudaSuccess) e = dalloc(&err, 2, s);
   if (e == cudaSuccess) e = launch_fill_err(err, s);
   if (e == cudaSuccess) e = launch_fill_err(err + 1, s);
-  if (e == cudaSuccess) e = launch_iiluk_build(S, F->val, M->g, sync, err, s);
+  if (e == cudaSuccess && !S->tinfo) {  // segment table, once per pattern
+    iluk_sym *Sm = const_cast<iluk_sym *>(S);
+    e = dalloc(&Sm->tinfo, S->nnz, s);
+    if (e == cudaSuccess) e = launch_tpiilu_info(S->n, S->rowptr, S->colind, S->diag, Sm->tinfo, s);
+  }
+  if (e == cudaSuccess) e = launch_iiluk_build(S, F->val, F->rdiag, S->tinfo, M->g, sync, err, s);
   int st = ILUK_OK;
   int64_t row = -1;
   if (e == cudaSuccess) {

@@ -28,6 +28,8 @@ struct iluk_sym {
   int64_t *arowptr = nullptr;  // copy of A's row pointers
   int32_t *a2f = nullptr;      // offset of each A entry inside its F row
   int64_t *pinfo = nullptr;    // per lower entry (i,h): diag position of row h << 24 | |U(h)|
+  int64_t *tinfo = nullptr;    // per entry (i,h): row h's TPIILU segment (start << 24 | length),
+                               // built by the first iiluk_build on the pattern
   int32_t max_row = 0;
   int32_t depth_lower = -1, depth_upper = -1;
   LevelOrder lord, uord;       // forward / backward sweep level orders
@@ -144,8 +146,11 @@ cudaError_t launch_transpose(int64_t n, int64_t nnz, const int64_t *rp, const in
                              int64_t *tdiag, int32_t *cursor, int64_t *scan_tmp, cudaStream_t s);
 
 // TPIILU (tpiilu.cu)
-cudaError_t launch_iiluk_build(const iluk_sym *S, const double *fval, double *g, int *sync,
-                               DevErr *err, cudaStream_t s);
+cudaError_t launch_iiluk_build(const iluk_sym *S, const double *fval, const double2 *rdiag,
+                               const int64_t *tinfo, double *g, int *sync, DevErr *err,
+                               cudaStream_t s);
+cudaError_t launch_tpiilu_info(int64_t n, const int64_t *frp, const int32_t *fci,
+                               const int64_t *fdiag, int64_t *tinfo, cudaStream_t s);
 cudaError_t launch_iiluk_apply(const iluk_sym *S, const double *g, const double *p, double *tmp,
                                double *y, cudaStream_t s);
 

@@ -19,24 +19,19 @@ constexpr int kDotThreads = 256;
 constexpr int kDotBlocks = kDotP / kDotThreads;
 
 // y = A x (b_minus == nullptr) or y = b - A x; each row summed left to right
-// from +0.0.  One warp per row, products in parallel, ordered sum.
+// from +0.0.  One thread per row: a row's sum is a chain of dependent FP64
+// additions, so a warp advances 32 rows' chains with each instruction.
 __global__ void __launch_bounds__(256)
 k_spmv(int64_t n, const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
        const double *__restrict__ v, const double *__restrict__ x, double *y,
        const double *b_minus) {
-  const int lane = threadIdx.x & 31;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < n; row += nw) {
+  for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < n;
+       row += (int64_t)gridDim.x * blockDim.x) {
     const int64_t b0 = rp[row], b1 = rp[row + 1];
     double s = 0.0;
-    for (int64_t base = b0; base < b1; base += 32) {
-      const int64_t q = base + lane;
-      double prod = 0.0;
-      if (q < b1) prod = __dmul_rn(v[q], x[ci[q]]);
-      const int cnt = (b1 - base) < 32 ? (int)(b1 - base) : 32;
-      for (int l = 0; l < cnt; ++l) s = __dadd_rn(s, __shfl_sync(FULL_MASK, prod, l));
-    }
-    if (lane == 0) y[row] = b_minus ? __dsub_rn(b_minus[row], s) : s;
+#pragma unroll 4
+    for (int64_t q = b0; q < b1; ++q) s = __dadd_rn(s, __dmul_rn(v[q], x[ci[q]]));
+    y[row] = b_minus ? __dsub_rn(b_minus[row], s) : s;
   }
 }
 
@@ -44,9 +39,7 @@ cudaError_t launch_spmv(int64_t n, const int64_t *rp, const int32_t *ci, const d
                         const double *x, double *y, const double *b_minus, cudaStream_t s) {
   ProfScope prof_scope(ILUK_PROF_SPMV, s);
   if (n == 0) return cudaSuccess;
-  int64_t blocks = (n * 32 + 255) / 256;
-  const int64_t cap = (int64_t)num_sms() * 8;
-  if (blocks > cap) blocks = cap;
+  const int64_t blocks = (n + 255) / 256;
   k_spmv<<<(unsigned)blocks, 256, 0, s>>>(n, rp, ci, v, x, y, b_minus);
   note_launch();
   return cudaGetLastError();

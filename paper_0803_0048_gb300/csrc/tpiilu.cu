@@ -44,101 +44,301 @@ __global__ void k_fill_pending_g(int64_t n, double *x) {
     x[i] = __longlong_as_double((long long)kPendingG);
 }
 
+// Segment table: for a lower entry (i,h) of F, where row h's strictly lower
+// part starts and how long it is; for an upper entry (i,h), h > i, the same
+// for row h's strictly upper part (start << 24 | length).  Built once per
+// pattern, so a warp reaches a pivot row's segment without dependent loads.
+constexpr int kSegBits = 24;
+
+__global__ void k_tpiilu_info(int64_t n, const int64_t *__restrict__ frp,
+                              const int32_t *__restrict__ fci, const int64_t *__restrict__ fdiag,
+                              int64_t *tinfo) {
+  const int lane = threadIdx.x & 31;
+  int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t row = w; row < n; row += nw) {
+    const int64_t d = fdiag[row];
+    for (int64_t p = frp[row] + lane; p < frp[row + 1]; p += 32) {
+      const int32_t h = fci[p];
+      const int64_t hd = fdiag[h];
+      int64_t v = 0;
+      if (p < d) v = (frp[h] << kSegBits) | (hd - frp[h]);
+      else if (p > d) v = ((hd + 1) << kSegBits) | (frp[h + 1] - hd - 1);
+      tinfo[p] = v;
+    }
+  }
+}
+
+cudaError_t launch_tpiilu_info(int64_t n, const int64_t *frp, const int32_t *fci,
+                               const int64_t *fdiag, int64_t *tinfo, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  int64_t blocks = (n * 32 + 255) / 256;
+  const int64_t cap = (int64_t)num_sms() * 16;
+  if (blocks > cap) blocks = cap;
+  k_tpiilu_info<<<(unsigned)blocks, 256, 0, s>>>(n, frp, fci, fdiag, tinfo);
+  note_launch();
+  return cudaGetLastError();
+}
+
+// One pivot h of the current row, staged like the numeric phase's pivots:
+// stage A issues the column loads of the first kIiPre * 32 entries of row h's
+// segment; stage B turns them into positions in the current row's segment and
+// issues the loads of the matching g_ht; stage C waits for whatever is still
+// pending and applies the pivot.
+constexpr int kIiPre = 4;
+
+struct IiStageA {
+  int64_t start;
+  int len;
+  int32_t j[kIiPre];
+};
+
+struct IiStageB {
+  int64_t start;
+  int len;
+  int pos[kIiPre];
+  double gv[kIiPre];
+};
+
+struct IiIndex {  // position of a column in the current row's segment
+  const int32_t *rc;
+  const int16_t *map;
+  int32_t c0;
+  int span;
+  bool use_map;
+  __device__ __forceinline__ int find(int32_t j, int lo, int hi) const {
+    if (use_map) {
+      const int d = j - c0;
+      return (d >= 0 && d < span) ? (int)map[d] : -1;
+    }
+    const int ps = lower_bound_i(rc, lo, hi, j);
+    return (ps < hi && rc[ps] == j) ? ps : -1;
+  }
+};
+
+__device__ __forceinline__ void ii_stage_a(IiStageA &a, int64_t info,
+                                           const int32_t *__restrict__ fci, int lane) {
+  a.start = info >> kSegBits;
+  a.len = (int)(info & ((1ll << kSegBits) - 1));
+#pragma unroll
+  for (int c = 0; c < kIiPre; ++c) {
+    const int e = lane + 32 * c;
+    a.j[c] = e < a.len ? fci[a.start + e] : -1;
+  }
+}
+
 template <bool LOWER>
+__device__ __forceinline__ void ii_stage_b(IiStageB &b, const IiStageA &a, const IiIndex &ix,
+                                           int q, int m, const double *g, int lane) {
+  b.start = a.start;
+  b.len = a.len;
+  // row h's lower entries t < h can only match positions below q; its upper
+  // entries t > h only positions above q
+  int lo = LOWER ? 0 : q + 1;
+  const int hi = LOWER ? q : m;
+#pragma unroll
+  for (int c = 0; c < kIiPre; ++c) {
+    b.pos[c] = -1;
+    b.gv[c] = 0.0;
+    if (a.j[c] >= 0) {
+      const int ps = ix.find(a.j[c], lo, hi);
+      if (ps >= 0) {
+        lo = ps;
+        b.pos[c] = ps;
+        b.gv[c] = ld_gpu_g(&g[b.start + lane + 32 * c]);
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ bool ii_pending(const IiStageB &b) {
+  bool p = false;
+#pragma unroll
+  for (int c = 0; c < kIiPre; ++c) p |= b.pos[c] >= 0 && pend_g(b.gv[c]);
+  return p;
+}
+
+__device__ __forceinline__ bool ii_wait(IiStageB &b, const double *g, int lane, const DevErr *err,
+                                        int64_t key, int64_t limit_ns) {
+  if (!__any_sync(FULL_MASK, ii_pending(b))) return true;
+  const uint64_t t0 = globaltimer_ns();
+  unsigned backoff = 16;
+  for (unsigned it = 0;; ++it) {
+#pragma unroll
+    for (int c = 0; c < kIiPre; ++c)
+      if (b.pos[c] >= 0 && pend_g(b.gv[c])) b.gv[c] = ld_gpu_g(&g[b.start + lane + 32 * c]);
+    if (!__any_sync(FULL_MASK, ii_pending(b))) return true;
+    const bool stop = (it & 31u) == 31u &&
+                      (earlier_failed(err, key) || (int64_t)(globaltimer_ns() - t0) > limit_ns);
+    if (__any_sync(FULL_MASK, stop)) return false;  // the whole warp gives up together
+    if (it >= 4) {
+      __nanosleep(backoff);
+      if (backoff < 64u) backoff <<= 1;
+    }
+  }
+}
+
+// One row of one pass.  key orders the rows of the pass for error reports
+// (row for the lower pass, n-1-row for the upper one, as processed by the
+// sequential algorithm).
+template <bool LOWER>
+__device__ bool ii_row(int64_t n, int64_t row, const int64_t *__restrict__ frp,
+                       const int32_t *__restrict__ fci, const int64_t *__restrict__ fdiag,
+                       const double *__restrict__ fval, const double2 *__restrict__ rdiag,
+                       const int64_t *__restrict__ tinfo, double *g, DevErr *err, double *rv,
+                       int64_t *sinfo, int32_t *rc, int16_t *smap, int map_cap, int64_t limit_ns,
+                       int lane) {
+  const int64_t key = LOWER ? row : n - 1 - row;
+  const int64_t d = fdiag[row];
+  const int64_t s0 = LOWER ? frp[row] : d + 1;  // segment of the row handled here
+  const int m = (int)((LOWER ? d : frp[row + 1]) - s0);
+  const double uii = fval[d];
+  const double2 rr = rdiag ? rdiag[row] : make_double2(0.0, 0.0);
+  for (int q = lane; q < m; q += 32) {
+    rc[q] = fci[s0 + q];
+    sinfo[q] = tinfo[s0 + q];
+    rv[q] = LOWER ? fval[s0 + q] : div_rn_recip(fval[s0 + q], uii, rr);  // u^_it = u_it / u_ii
+  }
+  __syncwarp();
+  IiIndex ix;
+  ix.rc = rc;
+  ix.map = smap;
+  ix.c0 = m > 0 ? rc[0] : 0;
+  ix.span = m > 0 ? rc[m - 1] - ix.c0 + 1 : 0;
+  ix.use_map = ix.span <= map_cap;
+  if (ix.use_map && m > 0) {
+    for (int dd = lane; dd < ix.span; dd += 32) smap[dd] = -1;
+    __syncwarp();
+    for (int q = lane; q < m; q += 32) smap[rc[q] - ix.c0] = (int16_t)q;
+  }
+  __syncwarp();
+  // pivots ascending (lower pass) or descending (upper pass), k-th at qk(k)
+  auto qk = [&](int k) { return LOWER ? k : m - 1 - k; };
+  bool ok = true;
+  IiStageA sa;
+  IiStageB cur, nxt;
+  if (m > 0) {
+    ii_stage_a(sa, sinfo[qk(0)], fci, lane);
+    ii_stage_b<LOWER>(cur, sa, ix, qk(0), m, g, lane);
+  }
+  if (m > 1) ii_stage_a(sa, sinfo[qk(1)], fci, lane);
+  for (int k = 0; k < m && ok; ++k) {
+    const int q = qk(k);
+    if (k + 1 < m) ii_stage_b<LOWER>(nxt, sa, ix, qk(k + 1), m, g, lane);
+    if (k + 2 < m) ii_stage_a(sa, sinfo[qk(k + 2)], fci, lane);
+    if (!ii_wait(cur, g, lane, err, key, limit_ns)) {
+      ok = false;
+      break;
+    }
+    // the coefficient f_ih (lower) or u^_ih (upper): earlier pivots of this
+    // pass never write position q, so rv[q] still holds it
+    const double coef = rv[q];
+    const int nch = (cur.len + 31) >> 5;
+#pragma unroll
+    for (int c = 0; c < kIiPre; ++c) {
+      if (c >= nch) break;
+      // beta_ht = -g_ht (or gamma_ht = -g_ht), an exact negation
+      if (cur.pos[c] >= 0) rv[cur.pos[c]] = sub_prod(rv[cur.pos[c]], coef, -cur.gv[c]);
+    }
+    for (int base = 32 * kIiPre; base < cur.len; base += 32) {  // long segments
+      const int e = base + lane;
+      int pos = -1;
+      double gv = 0.0;
+      if (e < cur.len) {
+        pos = ix.find(fci[cur.start + e], LOWER ? 0 : q + 1, LOWER ? q : m);
+        if (pos >= 0) gv = ld_gpu_g(&g[cur.start + e]);
+      }
+      bool pend = pos >= 0 && pend_g(gv);
+      if (__any_sync(FULL_MASK, pend)) {
+        const uint64_t t0 = globaltimer_ns();
+        for (unsigned it = 0;; ++it) {
+          if (pend) {
+            gv = ld_gpu_g(&g[cur.start + e]);
+            pend = pend_g(gv);
+          }
+          if (!__any_sync(FULL_MASK, pend)) break;
+          const bool stop = (it & 31u) == 31u && (earlier_failed(err, key) ||
+                                                  (int64_t)(globaltimer_ns() - t0) > limit_ns);
+          if (__any_sync(FULL_MASK, stop)) {
+            ok = false;
+            break;
+          }
+        }
+        if (!ok) break;
+      }
+      if (pos >= 0) rv[pos] = sub_prod(rv[pos], coef, -gv);
+    }
+    __syncwarp();
+    cur = nxt;
+  }
+  if (!__all_sync(FULL_MASK, ok)) {
+    if (lane == 0 && !earlier_failed(err, key)) set_err(err, key, ILUK_ETIMEOUT);
+    return false;
+  }
+  for (int q = lane; q < m; q += 32) g[s0 + q] = -rv[q];
+  if (!LOWER && lane == 0) g[d] = uii;
+  __syncwarp();
+  return true;
+}
+
+// Both passes in one launch: even tickets take the next row of the lower
+// pass (forward level order), odd tickets the next row of the upper pass
+// (backward level order).  Each pass's rows depend only on rows of the same
+// pass that sit at smaller tickets, so the launch cannot deadlock.
 __global__ void __launch_bounds__(kIiThreads)
 k_iiluk_build(int64_t n, const int64_t *__restrict__ frp, const int32_t *__restrict__ fci,
-              const int64_t *__restrict__ fdiag, const double *__restrict__ fval, double *g,
-              unsigned long long *ticket, DevErr *err, int cap, int64_t limit_ns) {
+              const int64_t *__restrict__ fdiag, const double *__restrict__ fval,
+              const double2 *__restrict__ rdiag, const int64_t *__restrict__ tinfo,
+              const int32_t *__restrict__ lord, const int32_t *__restrict__ uord, double *g,
+              unsigned long long *ticket, DevErr *err, int cap, int map_cap, int64_t limit_ns) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   const int nwarps = blockDim.x >> 5;
   double *rv = reinterpret_cast<double *>(smem) + (size_t)wib * cap;
-  int32_t *rc = reinterpret_cast<int32_t *>(smem + (size_t)nwarps * cap * 8) + (size_t)wib * cap;
-
+  int64_t *sinfo = reinterpret_cast<int64_t *>(smem + (size_t)nwarps * cap * 8) + (size_t)wib * cap;
+  int32_t *rc = reinterpret_cast<int32_t *>(smem + (size_t)nwarps * cap * 16) + (size_t)wib * cap;
+  int16_t *smap =
+      reinterpret_cast<int16_t *>(smem + (size_t)nwarps * cap * 20) + (size_t)wib * map_cap;
   for (;;) {
     unsigned long long tk = 0;
     if (lane == 0) tk = atomicAdd(ticket, 1ull);
     const int64_t t = (int64_t)__shfl_sync(FULL_MASK, tk, 0);
-    if (t >= n) return;
-    if (earlier_failed(err, t)) continue;
-    const int64_t row = LOWER ? t : n - 1 - t;
-    const int64_t d = fdiag[row];
-    const int64_t s0 = LOWER ? frp[row] : d + 1;  // segment of the row handled here
-    const int m = (int)((LOWER ? d : frp[row + 1]) - s0);
-    const double uii = fval[d];
-    for (int q = lane; q < m; q += 32) {
-      rc[q] = fci[s0 + q];
-      rv[q] = LOWER ? fval[s0 + q] : __ddiv_rn(fval[s0 + q], uii);
+    if (t >= 2 * n) return;
+    const int64_t idx = t >> 1;
+    if ((t & 1) == 0) {
+      const int64_t row = lord ? (int64_t)lord[idx] : idx;
+      if (earlier_failed(err, row)) continue;
+      ii_row<true>(n, row, frp, fci, fdiag, fval, rdiag, tinfo, g, err, rv, sinfo, rc, smap,
+                   map_cap, limit_ns, lane);
+    } else {
+      const int64_t row = uord ? (int64_t)uord[idx] : n - 1 - idx;
+      if (earlier_failed(err + 1, n - 1 - row)) continue;
+      ii_row<false>(n, row, frp, fci, fdiag, fval, rdiag, tinfo, g, err + 1, rv, sinfo, rc,
+                    smap, map_cap, limit_ns, lane);
     }
-    __syncwarp();
-    bool ok = true;
-    for (int qq = 0; qq < m && ok; ++qq) {
-      const int q = LOWER ? qq : m - 1 - qq;  // pivots ascending / descending
-      const int h = rc[q];
-      const double coef = LOWER ? fval[s0 + q] : __ddiv_rn(fval[s0 + q], uii);
-      const int64_t hd = fdiag[h];
-      const int64_t r0 = LOWER ? frp[h] : hd + 1;
-      const int64_t r1 = LOWER ? hd : frp[h + 1];
-      for (int64_t base = r0; base < r1; base += 32) {
-        const int64_t r = base + lane;
-        int pos = -1;
-        double gv = 0.0;
-        if (r < r1) {
-          const int32_t col = fci[r];
-          const int lo = LOWER ? 0 : q + 1, hi = LOWER ? q : m;
-          const int ps = lower_bound_i(rc, lo, hi, col);
-          if (ps < hi && rc[ps] == col) {
-            pos = ps;
-            gv = ld_gpu_g(&g[r]);
-          }
-        }
-        bool pend = pos >= 0 && pend_g(gv);
-        if (__any_sync(FULL_MASK, pend)) {
-          const uint64_t t0 = globaltimer_ns();
-          unsigned backoff = 32;
-          for (unsigned it = 0;; ++it) {
-            if (pend) {
-              gv = ld_gpu_g(&g[r]);
-              pend = pend_g(gv);
-            }
-            if (!__any_sync(FULL_MASK, pend)) break;
-            const bool stop = (it & 7u) == 7u && (earlier_failed(err, t) ||
-                                                  (int64_t)(globaltimer_ns() - t0) > limit_ns);
-            if (__any_sync(FULL_MASK, stop)) {  // the whole warp gives up together
-              ok = false;
-              break;
-            }
-            __nanosleep(backoff);
-            if (backoff < 256u) backoff <<= 1;
-          }
-          if (!__all_sync(FULL_MASK, ok)) break;
-        }
-        // beta_ht = -g_ht (or gamma_ht = -g_ht), an exact negation
-        if (pos >= 0) rv[pos] = sub_prod(rv[pos], coef, -gv);
-      }
-      __syncwarp();
-    }
-    if (!__all_sync(FULL_MASK, ok)) {
-      if (lane == 0 && !earlier_failed(err, t)) set_err(err, t, ILUK_ETIMEOUT);
-      continue;
-    }
-    for (int q = lane; q < m; q += 32) g[s0 + q] = -rv[q];
-    if (!LOWER && lane == 0) g[d] = uii;
-    __syncwarp();
   }
 }
 
-cudaError_t launch_iiluk_build(const iluk_sym *S, const double *fval, double *g, int *sync,
-                               DevErr *err, cudaStream_t s) {
+cudaError_t launch_iiluk_build(const iluk_sym *S, const double *fval, const double2 *rdiag,
+                               const int64_t *tinfo, double *g, int *sync, DevErr *err,
+                               cudaStream_t s) {
   const int64_t n = S->n;
   if (n == 0) return cudaSuccess;
   int cap = S->max_row < 32 ? 32 : ((S->max_row + 31) & ~31);
-  int warps = kIiThreads / 32;
   const size_t budget = (size_t)max_smem_optin();
-  while (warps > 1 && (size_t)cap * 12 * warps > budget) warps >>= 1;
-  if ((size_t)cap * 12 * warps > budget) return cudaErrorMemoryAllocation;
-  const size_t smem = (size_t)cap * 12 * warps;
+  int warps = 0, map_cap = 0;
+  for (int w : {8, 4, 2, 1}) {
+    for (int mc : {8192, 4096, 0})
+      if (((size_t)cap * 20 + (size_t)mc * 2) * w <= budget) {
+        warps = w;
+        map_cap = mc;
+        break;
+      }
+    if (warps) break;
+  }
+  if (!warps) return cudaErrorMemoryAllocation;
+  const size_t smem = ((size_t)cap * 20 + (size_t)map_cap * 2) * warps;
   unsigned long long *tick = reinterpret_cast<unsigned long long *>(sync);
   cudaError_t e = cudaMemsetAsync(sync, 0, 4 * sizeof(int), s);
   if (e != cudaSuccess) return e;
@@ -149,62 +349,47 @@ cudaError_t launch_iiluk_build(const iluk_sym *S, const double *fval, double *g,
     k_fill_pending_g<<<(unsigned)b, 256, 0, s>>>(S->nnz, g);
     note_launch();
   }
+  e = cudaFuncSetAttribute(k_iiluk_build, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
   int bps = 0;
-  e = cudaFuncSetAttribute(k_iiluk_build<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smem);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_iiluk_build<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smem);
-  if (e != cudaSuccess) return e;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_iiluk_build<true>, warps * 32, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_iiluk_build, warps * 32, smem);
   if (bps < 1) bps = 1;
   int64_t grid = (int64_t)bps * num_sms();
-  const int64_t want = (n + warps - 1) / warps;
+  const int64_t want = (2 * n + warps - 1) / warps;
   if (grid > want) grid = want;
-  {
-    ProfScope prof_scope(ILUK_PROF_IILU_BUILD, s);
-    k_iiluk_build<true><<<(unsigned)grid, warps * 32, smem, s>>>(
-        n, S->rowptr, S->colind, S->diag, fval, g, tick, err, cap, wait_limit());
-    note_launch();
-  }
-  {
-    ProfScope prof_scope(ILUK_PROF_IILU_BUILD, s);
-    k_iiluk_build<false><<<(unsigned)grid, warps * 32, smem, s>>>(
-        n, S->rowptr, S->colind, S->diag, fval, g, tick + 1, err + 1, cap, wait_limit());
-    note_launch();
-  }
+  const int32_t *lord = S->levels_built ? S->lord.corder : nullptr;
+  const int32_t *uord = S->levels_built ? S->uord.corder : nullptr;
+  ProfScope prof_scope(ILUK_PROF_IILU_BUILD, s);
+  k_iiluk_build<<<(unsigned)grid, warps * 32, smem, s>>>(n, S->rowptr, S->colind, S->diag, fval,
+                                                         rdiag, tinfo, lord, uord, g, tick, err,
+                                                         cap, map_cap, wait_limit());
+  note_launch();
   return cudaGetLastError();
 }
 
-// Apply: warp per row, products in parallel, ordered left-to-right sum.
+// Apply: one thread per row, each row summed left to right from its first
+// product, the own term added last (Eq. forwardsubB); the sums are chains of
+// dependent FP64 additions, so a warp advances 32 rows with each instruction.
 template <bool LOWER>
 __global__ void __launch_bounds__(256)
 k_iiluk_apply(int64_t n, const int64_t *__restrict__ frp, const int32_t *__restrict__ fci,
               const int64_t *__restrict__ fdiag, const double *__restrict__ g,
               const double *__restrict__ in, double *__restrict__ out) {
-  const int lane = threadIdx.x & 31;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < n; row += nw) {
+  for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < n;
+       row += (int64_t)gridDim.x * blockDim.x) {
     const int64_t d = fdiag[row];
     const int64_t b0 = LOWER ? frp[row] : d + 1;
     const int64_t b1 = LOWER ? d : frp[row + 1];
-    double s = 0.0;
-    bool first = true;
-    for (int64_t base = b0; base < b1; base += 32) {
-      const int64_t q = base + lane;
-      double prod = 0.0;
-      if (q < b1) prod = __dmul_rn(g[q], in[fci[q]]);
-      const int cnt = (b1 - base) < 32 ? (int)(b1 - base) : 32;
-      for (int l = 0; l < cnt; ++l) {
-        const double pr = __shfl_sync(FULL_MASK, prod, l);
-        s = first ? pr : __dadd_rn(s, pr);
-        first = false;
-      }
-    }
     const double own = in[row];
-    double x = (b1 > b0) ? __dadd_rn(s, own) : own;
+    double x = own;
+    if (b1 > b0) {
+      double s = __dmul_rn(g[b0], in[fci[b0]]);
+#pragma unroll 4
+      for (int64_t q = b0 + 1; q < b1; ++q) s = __dadd_rn(s, __dmul_rn(g[q], in[fci[q]]));
+      x = __dadd_rn(s, own);
+    }
     if (LOWER) x = __ddiv_rn(x, g[d]);
-    if (lane == 0) out[row] = x;
+    out[row] = x;
   }
 }
 
@@ -212,9 +397,7 @@ cudaError_t launch_iiluk_apply(const iluk_sym *S, const double *g, const double 
                                double *y, cudaStream_t s) {
   const int64_t n = S->n;
   if (n == 0) return cudaSuccess;
-  int64_t blocks = (n * 32 + 255) / 256;
-  const int64_t cap = (int64_t)num_sms() * 8;
-  if (blocks > cap) blocks = cap;
+  const int64_t blocks = (n + 255) / 256;
   {
     ProfScope prof_scope(ILUK_PROF_IILU_APPLY, s);
     k_iiluk_apply<true><<<(unsigned)blocks, 256, 0, s>>>(n, S->rowptr, S->colind, S->diag, g, p,
