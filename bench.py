@@ -47,9 +47,11 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-steps", type=int, default=2, help="oracle steps for cpu_baseline")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--workload", default="band", choices=["band", "batched", "adjoint"],
+    ap.add_argument("--workload", default="band",
+                    choices=["band", "batched", "adjoint", "suite"],
                     help="band: the n=160,000 headline; batched: 512 value sets on 32^3 plus "
-                         "64 uneven grids in one launch; adjoint: 256^2 differentiable solve")
+                         "64 uneven grids in one launch; adjoint: 256^2 differentiable solve; "
+                         "suite: every phase of every single-system configuration")
     ap.add_argument("--nsets", type=int, default=512)
     ap.add_argument("--ngrids", type=int, default=64)
     return ap.parse_args()
@@ -513,6 +515,151 @@ def adjoint(args):
     print(json.dumps(out), flush=True)
 
 
+def suite(args):
+    """Every phase of every single-system configuration: C1 (2D 64^2, ILU(2)),
+    C2 (random band n=160,000, ILU(k) for k = 0..3), C3 (3D 64^3, ILU(2) and
+    TPIILU(2)).  Per phase: median ms of 20 CUDA-event-timed runs after 5
+    warm-ups, algorithmic GB/s and fraction of the measured HBM peak, ns per
+    level of the DAG the phase walks; per configuration the bit mismatches
+    against the oracle and the oracle's own times on one host core (where it
+    finishes in seconds; C2 k=3 takes minutes and is skipped)."""
+    import torch
+
+    import oracle
+    import paper_0803_0048_gb300 as P
+    from paper_0803_0048_gb300 import workloads as W
+
+    torch.cuda.set_device(0)
+    hbm, peak_src = measured_peaks()
+
+    def med_ms(fn, reps=20, warm=5):
+        for _ in range(warm):
+            fn()
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    def cpu_s(fn):
+        t0 = time.perf_counter()
+        r = fn()
+        return time.perf_counter() - t0, r
+
+    def bits(t):
+        a = t.cpu().numpy() if hasattr(t, "cpu") else np.asarray(t)
+        return np.ascontiguousarray(a).view(np.uint64)
+
+    cases = [("C1 2D 64^2", W.conv_diff_2d_64, 2, False),
+             ("C2 band n=160000", lambda: W.random_band_160k(k=0), 0, False),
+             ("C2 band n=160000", lambda: W.random_band_160k(k=1), 1, False),
+             ("C2 band n=160000", lambda: W.random_band_160k(k=2), 2, True),
+             ("C2 band n=160000", lambda: W.random_band_160k(k=3), 3, False),
+             ("C3 3D 64^3", W.conv_diff_3d, 2, True)]
+    rows = []
+    for name, make, k, with_iilu in cases:
+        Pb = make()
+        A = Pb.A
+        n, nnzA = A.n, A.nnz
+        rp, ci, av, b = (torch.from_numpy(a).cuda() for a in (A.rowptr, A.colind, A.val, Pb.b))
+        S = P.symbolic(rp, ci, k)
+        F = P.numeric(S, av)
+        depth = S.depth()
+        frp, fci, flev, fdg = [t.cpu().numpy() for t in S.pattern()]
+        nnzF = int(frp[-1])
+        nnzL = int(np.sum(fdg - frp[:-1]))
+        nnzU = nnzF - nnzL
+        pvec = torch.from_numpy(W.uniform(W.stream_key(11, "suite"), np.arange(n), -1.0, 1.0)).cuda()
+        y = F.apply(pvec)  # first application: autotunes the sweep schedules
+        by = {  # algorithmic bytes (each array touched once)
+            "symbolic": 8 * (n + 1) + 4 * nnzA + 8 * (n + 1) + 5 * nnzF + 8 * n,
+            "numeric": 12 * nnzA + 16 * (n + 1) + 4 * nnzF + 8 * n + 8 * nnzF,
+            "apply": 12 * nnzF + 16 * (n + 1) + 8 * n + 32 * n + 16 * n,
+            "iilu_build": 12 * nnzF + 8 * nnzF + 16 * (n + 1) + 8 * n,
+            "iilu_apply": 12 * nnzF + 16 * (n + 1) + 8 * n + 40 * n,
+        }
+        ph = {}
+        ph["symbolic"] = med_ms(lambda: P.symbolic(rp, ci, k), reps=5 if k == 3 else 20,
+                                warm=1 if k == 3 else 5)
+        ph["numeric"] = med_ms(lambda: F.refactor(av), reps=5 if k == 3 else 20,
+                               warm=1 if k == 3 else 5)
+        ph["apply"] = med_ms(lambda: F.apply(pvec))
+        x, info = P.gmres(rp, ci, av, b, F, restart=Pb.restart, rtol=Pb.rtol)
+        ph["gmres"] = med_ms(lambda: P.gmres(rp, ci, av, b, F, restart=Pb.restart, rtol=Pb.rtol),
+                             reps=5, warm=1)
+        M = None
+        if with_iilu:
+            M = P.iiluk_build(F)
+            ph["iilu_build"] = med_ms(lambda: P.iiluk_build(F), reps=10, warm=2)
+            ph["iilu_apply"] = med_ms(lambda: M.apply(pvec))
+            xi, info_i = P.gmres(rp, ci, av, b, M, restart=Pb.restart, rtol=Pb.rtol,
+                                 maxit=5000, check=False)
+            ph["gmres_iilu"] = med_ms(lambda: P.gmres(rp, ci, av, b, M, restart=Pb.restart,
+                                                      rtol=Pb.rtol, maxit=5000, check=False),
+                                      reps=3, warm=1)
+        phases = {}
+        lev = {"symbolic": depth[0], "numeric": depth[0], "apply": depth[0] + depth[1],
+               "iilu_build": max(depth)}
+        for key, ms_ in ph.items():
+            rec = {"ms": round(ms_, 4)}
+            if key in by:
+                gbps = by[key] / (ms_ / 1e3) / 1e9
+                rec.update({"alg_bytes": by[key], "alg_GBps": round(gbps, 2),
+                            "hbm_frac": round(gbps / hbm, 6)})
+            if key in lev:
+                rec["ns_per_level"] = round(ms_ * 1e6 / lev[key], 1)
+            phases[key] = rec
+        row = {"config": name, "k": k, "n": n, "nnz_A": nnzA, "nnz_F": nnzF, "nnz_L": nnzL,
+               "nnz_U": nnzU, "depth_forward": depth[0], "depth_backward": depth[1],
+               "sweep_schedule": [L_sched(F.schedule() & 0xff), L_sched((F.schedule() >> 8) & 0xff)],
+               "gmres_iters": info.iters, "gmres_relres": info.relres,
+               "phases": phases}
+        if with_iilu:
+            row["gmres_iilu_iters"] = info_i.iters
+        if k <= 2:
+            t_fac, ref = cpu_s(lambda: oracle.factor(A, k))
+            t_app, yo = cpu_s(lambda: oracle.apply(n, ref["rowptr"], ref["colind"], ref["val"],
+                                                   pvec.cpu().numpy()))
+            par = {"pattern_equal": bool(np.array_equal(frp, ref["rowptr"]) and
+                                         np.array_equal(fci, ref["colind"]) and
+                                         np.array_equal(flev, ref["level"])),
+                   "factor_bit_mismatches": int(np.sum(bits(F.values()) != bits(ref["val"]))),
+                   "apply_bit_mismatches": int(np.sum(bits(y) != bits(yo)))}
+            orc = {"factor_s": round(t_fac, 3), "apply_s": round(t_app, 4)}
+            t_g, (st, xo, it, rel, cyc) = cpu_s(lambda: oracle.gmres(
+                n, A.rowptr, A.colind, A.val, Pb.b, oracle.PREC_ILU,
+                (ref["rowptr"], ref["colind"], ref["val"]), Pb.restart, Pb.rtol,
+                dotmode=oracle.DOT_TREE))
+            orc["gmres_s"] = round(t_g, 3)
+            par["gmres_x_bit_mismatches"] = int(np.sum(bits(x) != bits(xo)))
+            par["gmres_iters_equal"] = it == info.iters
+            if with_iilu:
+                t_ib, go = cpu_s(lambda: oracle.iiluk_build(n, ref["rowptr"], ref["colind"],
+                                                            ref["val"]))
+                orc["iilu_build_s"] = round(t_ib, 3)
+                par["iilu_bit_mismatches"] = int(np.sum(bits(M.values()) != bits(go)))
+            row["parity"] = par
+            row["oracle_one_core"] = orc
+        else:
+            row["parity"] = "oracle skipped: its factorization of this case takes minutes"
+        rows.append(row)
+        print(json.dumps({"progress": name, "k": k}), file=sys.stderr, flush=True)
+    out = {"metric": METRIC, "workload": "suite", "unit": "ms", "dtype": "f64",
+           "data": "synthetic", "peak_GBps": hbm, "peak_source": peak_src,
+           "timing": "CUDA events, median of 20 runs after 5 warm-ups (5 runs for C2 k=3 "
+                     "and for GMRES solves)", "configs": rows}
+    print(json.dumps(out), flush=True)
+
+
+def L_sched(byte):
+    from paper_0803_0048_gb300 import _lib as L
+    return L.sched_name(byte)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -521,6 +668,8 @@ def main():
         batched(args)
     elif args.workload == "adjoint":
         adjoint(args)
+    elif args.workload == "suite":
+        suite(args)
     else:
         ours(args)
 
