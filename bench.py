@@ -591,6 +591,9 @@ def suite(args):
         x, info = P.gmres(rp, ci, av, b, F, restart=Pb.restart, rtol=Pb.rtol)
         ph["gmres"] = med_ms(lambda: P.gmres(rp, ci, av, b, F, restart=Pb.restart, rtol=Pb.rtol),
                              reps=5, warm=1)
+        xb, info_b = P.bicgstab(rp, ci, av, b, F, rtol=Pb.rtol, maxit=5000, check=False)
+        ph["bicgstab"] = med_ms(lambda: P.bicgstab(rp, ci, av, b, F, rtol=Pb.rtol, maxit=5000,
+                                                   check=False), reps=5, warm=1)
         M = None
         if with_iilu:
             M = P.iiluk_build(F)
@@ -601,6 +604,10 @@ def suite(args):
             ph["gmres_iilu"] = med_ms(lambda: P.gmres(rp, ci, av, b, M, restart=Pb.restart,
                                                       rtol=Pb.rtol, maxit=5000, check=False),
                                       reps=3, warm=1)
+            xbi, info_bi = P.bicgstab(rp, ci, av, b, M, rtol=Pb.rtol, maxit=5000, check=False)
+            ph["bicgstab_iilu"] = med_ms(lambda: P.bicgstab(rp, ci, av, b, M, rtol=Pb.rtol,
+                                                            maxit=5000, check=False),
+                                         reps=3, warm=1)
         phases = {}
         lev = {"symbolic": depth[0], "numeric": depth[0], "apply": depth[0] + depth[1],
                "iilu_build": max(depth)}
@@ -617,9 +624,11 @@ def suite(args):
                "nnz_U": nnzU, "depth_forward": depth[0], "depth_backward": depth[1],
                "sweep_schedule": [L_sched(F.schedule() & 0xff), L_sched((F.schedule() >> 8) & 0xff)],
                "gmres_iters": info.iters, "gmres_relres": info.relres,
+               "bicgstab_iters": info_b.iters, "bicgstab_relres": info_b.relres,
                "phases": phases}
         if with_iilu:
             row["gmres_iilu_iters"] = info_i.iters
+            row["bicgstab_iilu_iters"] = info_bi.iters
         if k <= 2:
             t_fac, ref = cpu_s(lambda: oracle.factor(A, k))
             t_app, yo = cpu_s(lambda: oracle.apply(n, ref["rowptr"], ref["colind"], ref["val"],
@@ -637,6 +646,12 @@ def suite(args):
             orc["gmres_s"] = round(t_g, 3)
             par["gmres_x_bit_mismatches"] = int(np.sum(bits(x) != bits(xo)))
             par["gmres_iters_equal"] = it == info.iters
+            t_b, (stb, xbo, itb, relb, _) = cpu_s(lambda: oracle.bicgstab(
+                n, A.rowptr, A.colind, A.val, Pb.b, oracle.PREC_ILU,
+                (ref["rowptr"], ref["colind"], ref["val"]), Pb.rtol, 5000, oracle.DOT_TREE))
+            orc["bicgstab_s"] = round(t_b, 3)
+            par["bicgstab_x_bit_mismatches"] = int(np.sum(bits(xb) != bits(xbo)))
+            par["bicgstab_iters_equal"] = itb == info_b.iters
             if with_iilu:
                 t_ib, go = cpu_s(lambda: oracle.iiluk_build(n, ref["rowptr"], ref["colind"],
                                                             ref["val"]))

@@ -304,6 +304,24 @@ int gmres_solve(const iluk_pattern *A, const double *A_val, int prec_kind, void 
                 int transpose, iluk_info *info, void *stream);
 
 /*
+ * Preconditioned BiCGSTAB (van der Vorst 1992), the solver of the paper's
+ * experiments (Sec. 4), right preconditioned, x0 = 0, shadow residual r^ = b,
+ * inner products in the fixed order above.  Per iteration, each operation
+ * rounded once: rho = (r^,r); p = r + beta (p - omega v) with beta =
+ * (rho/rho_prev)(alpha/omega) (p = r first); p^ = M^-1 p; v = A p^;
+ * alpha = rho / (r^,v); s = r - alpha v; stop with x += alpha p^ when
+ * ||s||/||b|| <= rtol; s^ = M^-1 s; t = A s^; omega = (t,s)/(t,t);
+ * x = (x + alpha p^) + omega s^; r = s - omega t; stop when ||r||/||b|| <= rtol.
+ * info->relres is the true ||b - Ax||/||b|| at exit, info->iters the
+ * iterations.  prec_kind / prec as for gmres_solve (no transpose).  b, x:
+ * device double[n].  Synchronous; ILUK_ENOCONV when maxit is reached,
+ * ILUK_EINVAL on a breakdown (rho, (r^,v), (t,t) or omega exactly zero).
+ */
+int bicgstab_solve(const iluk_pattern *A, const double *A_val, int prec_kind, void *prec,
+                   const double *b, double *x, double rtol, int maxit, iluk_info *info,
+                   void *stream);
+
+/*
  * a8 helper. Gradient of a loss through x = A^-1 b with respect to the stored
  * entries of A: gA[p] = -lambda_i * x_j for entry p = (i, j), where lambda
  * solves A^T lambda = dL/dx.  Asynchronous.

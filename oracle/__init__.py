@@ -66,6 +66,7 @@ def _load():
                                   i32, P]
         lib.orc_adjoint.argtypes = [i64, P, P, P, P, P, P, P, P, P, P, i32, C.c_double, i32,
                                     i32, P]
+        lib.orc_bicgstab.argtypes = [i64, P, P, P, i32, P, P, P, P, P, C.c_double, i32, i32, P]
         _lib = lib
         return lib
 
@@ -222,6 +223,27 @@ def gmres(n, arp, aci, av, b, prec_kind=PREC_NONE, F=None, restart=30, rtol=1e-8
                        _p(fv) if fv is not None else None, _p(b), _p(x), restart, rtol, maxit,
                        dotmode, _p(info))
     return st, x[:n].copy(), int(info[0]), float(info[1]), int(info[2])
+
+
+def bicgstab(n, arp, aci, av, b, prec_kind=PREC_NONE, F=None, rtol=1e-8, maxit=10000,
+             dotmode=DOT_SEQ):
+    """Right-preconditioned BiCGSTAB, x0 = 0 (the iteration written out in
+    iluk_oracle.c).  ``F`` as for gmres (no transpose).
+    Returns (status, x, iterations, true relres, ended_at_half_step)."""
+    lib = _load()
+    arp, aci, av, b = _i64(arp), _i32(aci), _f64(av), _f64(b)
+    x = np.zeros(max(n, 1), dtype=np.float64)
+    info = np.zeros(3, dtype=np.float64)
+    if F is None:
+        frp = fci = fv = None
+    else:
+        frp, fci, fv = _i64(F[0]), _i32(F[1]), _f64(F[2])
+    st = lib.orc_bicgstab(n, _p(arp), _p(aci), _p(av), prec_kind,
+                          _p(frp) if frp is not None else None,
+                          _p(fci) if fci is not None else None,
+                          _p(fv) if fv is not None else None, _p(b), _p(x), rtol, maxit, dotmode,
+                          _p(info))
+    return st, x[:n].copy(), int(info[0]), float(info[1]), bool(info[2])
 
 
 def adjoint(n, arp, aci, av, frp, fci, fv, x, gx, restart=30, rtol=1e-8, maxit=10000,

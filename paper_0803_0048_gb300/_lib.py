@@ -94,6 +94,7 @@ SIGNATURES = [
     ("iluk_dot", I, [I64, P, P, P, P]),
     ("iluk_div_rn", I, [I64, P, P, P, P]),
     ("gmres_solve", I, [P, P, I, P, P, P, I, D, I, I, P, P]),
+    ("bicgstab_solve", I, [P, P, I, P, P, P, D, I, P, P]),
     ("iluk_adjoint_scatter", I, [P, P, P, P, P]),
     ("iluk_numeric_batched", I, [P, I64, P, P, P, P]),
     ("iluk_batch_create", I, [P, I64, I, D, I, PP, P]),

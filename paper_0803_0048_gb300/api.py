@@ -256,6 +256,29 @@ def gmres(rowptr, colind, vals, b, prec=None, restart=30, rtol=1e-8, maxit=10000
     return xo, info
 
 
+def bicgstab(rowptr, colind, vals, b, prec=None, rtol=1e-8, maxit=10000, x=None, check=True):
+    """Right-preconditioned BiCGSTAB from x0 = 0 (the paper's solver, Sec. 4).
+    ``prec`` is None, a Factors or an IncompleteInverse.  Returns (x, info);
+    info.relres is the true relative residual."""
+    A = CsrPattern(rowptr, colind)
+    _check_dev(vals, b)
+    xo = torch.empty_like(b) if x is None else x
+    if prec is None:
+        kind, ph = L.PREC_NONE, None
+    elif isinstance(prec, Factors):
+        kind, ph = L.PREC_ILU, prec.h
+    elif isinstance(prec, IncompleteInverse):
+        kind, ph = L.PREC_IILU, prec.h
+    else:
+        raise TypeError("prec must be None, Factors or IncompleteInverse")
+    info = L.Info()
+    st = L.load().bicgstab_solve(A.ref, _ptr(vals), kind, ph, _ptr(b), _ptr(xo), float(rtol),
+                                 int(maxit), C.byref(info), C.c_void_p(_stream()))
+    if check and st != L.OK:
+        raise IlukError(st, info, "bicgstab_solve")
+    return xo, info
+
+
 def adjoint_scatter(rowptr, colind, lam, x, out=None):
     """gA[p] = -lambda_i x_j on A's pattern."""
     A = CsrPattern(rowptr, colind)

@@ -1198,4 +1198,129 @@ int gmres_solve(const iluk_pattern *A, const double *A_val, int prec_kind, void 
   return status;
 }
 
+int bicgstab_solve(const iluk_pattern *A, const double *A_val, int prec_kind, void *prec,
+                   const double *b, double *x, double rtol, int maxit, iluk_info *info,
+                   void *stream) {
+  info_init(info);
+  if (!A || maxit < 0 || A->n < 0) return fail(info, ILUK_EINVAL);
+  if (prec_kind != ILUK_PREC_NONE && !prec) return fail(info, ILUK_EINVAL);
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t n = A->n;
+  iluk_fac *F = prec_kind == ILUK_PREC_ILU ? (iluk_fac *)prec : nullptr;
+  iiluk *M = prec_kind == ILUK_PREC_IILU ? (iiluk *)prec : nullptr;
+  const int64_t ld = n > 0 ? n : 1;
+  double *r = nullptr, *rh = nullptr, *p = nullptr, *v = nullptr, *ph = nullptr, *sv = nullptr,
+         *sh = nullptr, *t = nullptr, *dsc = nullptr;
+  DotScratch ds{};
+  CK(dalloc(&r, ld, s));
+  CK(dalloc(&rh, ld, s));
+  CK(dalloc(&p, ld, s));
+  CK(dalloc(&v, ld, s));
+  CK(dalloc(&ph, ld, s));
+  CK(dalloc(&sv, ld, s));
+  CK(dalloc(&sh, ld, s));
+  CK(dalloc(&t, ld, s));
+  CK(dalloc(&dsc, 8, s));
+  CK(dalloc(&ds.partial, kDotP, s));
+  CK(dalloc(&ds.counter, 1, s));
+  CK(cudaMemsetAsync(ds.counter, 0, sizeof(unsigned), s));
+  const int sched = F ? pick_schedule(F, s) : 0;
+  auto precond = [&](const double *in, double *outv) -> cudaError_t {
+    if (F)
+      return launch_apply(n, F->S->rowptr, F->S->colind, F->S->diag, F->val, F->rdiag,
+                          F->S->lord, F->S->uord, in, F->tmp, outv, 0, sched, F->err, s);
+    if (M) return launch_iiluk_apply(M->S, M->g, in, M->tmp, outv, s);
+    return cudaMemcpyAsync(outv, in, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  };
+  // scalars come back to the host, as in gmres_solve: dsc[0..k) per sync
+  double hs[4] = {0.0, 0.0, 0.0, 0.0};
+  auto fetch = [&](int cnt) -> cudaError_t {
+    cudaError_t e = cudaMemcpyAsync(hs, dsc, cnt * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return e;
+    return cudaStreamSynchronize(s);
+  };
+  int status = ILUK_ENOCONV, iters = 0;
+  double relres = 0.0;
+  CK(cudaMemsetAsync(x, 0, n * sizeof(double), s));
+  CK(launch_dot(n, b, b, dsc, 1, ds, s));
+  CK(fetch(1));
+  const double bnorm = hs[0];
+  if (bnorm == 0.0) {
+    status = ILUK_OK;
+  } else {
+    CK(cudaMemcpyAsync(r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(rh, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CK(launch_dot(n, rh, r, dsc, 0, ds, s));
+    CK(fetch(1));
+    double rho = hs[0], rho_prev = 1.0, alpha = 1.0, omega = 1.0;
+    for (int it = 1; it <= maxit; ++it) {
+      if (rho == 0.0) { status = ILUK_EINVAL; break; }
+      if (it == 1) {
+        CK(cudaMemcpyAsync(p, r, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      } else {
+        const double b1 = rho / rho_prev, b2 = alpha / omega;
+        CK(launch_bicg_dir(n, p, r, v, b1 * b2, omega, s));
+      }
+      CK(precond(p, ph));
+      CK(launch_spmv(n, A->rowptr, A->colind, A_val, ph, v, nullptr, s));
+      CK(launch_dot(n, rh, v, dsc, 0, ds, s));
+      CK(fetch(1));
+      const double sigma = hs[0];
+      if (sigma == 0.0) { status = ILUK_EINVAL; break; }
+      alpha = rho / sigma;
+      CK(launch_axmy(n, sv, r, alpha, v, s));
+      CK(launch_dot(n, sv, sv, dsc, 1, ds, s));
+      CK(fetch(1));
+      iters = it;
+      if (hs[0] / bnorm <= rtol) {  // converged at the half step
+        CK(launch_bicg_x(n, x, alpha, ph, 0.0, nullptr, s));
+        status = ILUK_OK;
+        break;
+      }
+      CK(precond(sv, sh));
+      CK(launch_spmv(n, A->rowptr, A->colind, A_val, sh, t, nullptr, s));
+      CK(launch_dot(n, t, t, dsc, 0, ds, s));
+      CK(launch_dot(n, t, sv, dsc + 1, 0, ds, s));
+      CK(fetch(2));
+      const double tt = hs[0], ts = hs[1];
+      if (tt == 0.0) { status = ILUK_EINVAL; break; }
+      omega = ts / tt;
+      CK(launch_bicg_x(n, x, alpha, ph, omega, sh, s));
+      CK(launch_axmy(n, r, sv, omega, t, s));
+      CK(launch_dot(n, r, r, dsc, 1, ds, s));
+      CK(launch_dot(n, rh, r, dsc + 1, 0, ds, s));  // the next rho, fetched together
+      CK(fetch(2));
+      if (hs[0] / bnorm <= rtol) { status = ILUK_OK; break; }
+      if (omega == 0.0) { status = ILUK_EINVAL; break; }
+      rho_prev = rho;
+      rho = hs[1];
+    }
+    // the true residual ||b - A x|| / ||b||
+    CK(launch_spmv(n, A->rowptr, A->colind, A_val, x, t, b, s));
+    CK(launch_dot(n, t, t, dsc, 1, ds, s));
+    CK(fetch(1));
+    relres = hs[0] / bnorm;
+  }
+  CK(cudaStreamSynchronize(s));
+  int64_t prow = -1;
+  if (F) {
+    int pst = read_err(F->err, s, &prow, nullptr);
+    if (pst != ILUK_OK) {
+      launch_fill_err(F->err, s);
+      launch_fill_pending(n, F->tmp, s);
+      status = pst;
+    }
+  }
+  dfree(r, s); dfree(rh, s); dfree(p, s); dfree(v, s); dfree(ph, s); dfree(sv, s); dfree(sh, s);
+  dfree(t, s); dfree(dsc, s); dfree(ds.partial, s); dfree(ds.counter, s);
+  if (info) {
+    info->status = status;
+    info->iters = iters;
+    info->relres = relres;
+    info->cycles = 0;
+    info->row = prow;
+  }
+  return status;
+}
+
 }  // extern "C"

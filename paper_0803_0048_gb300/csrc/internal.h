@@ -169,6 +169,12 @@ cudaError_t launch_scale_div(int64_t n, const double *x, const double *den, doub
 cudaError_t launch_combine(int64_t n, const double *V, int64_t ldv, const double *y, int cnt,
                            double *u, cudaStream_t s);
 cudaError_t launch_add(int64_t n, double *x, const double *z, cudaStream_t s);
+cudaError_t launch_bicg_dir(int64_t n, double *p, const double *r, const double *v, double beta,
+                            double omega, cudaStream_t s);
+cudaError_t launch_axmy(int64_t n, double *out, const double *a, double alpha, const double *b,
+                        cudaStream_t s);
+cudaError_t launch_bicg_x(int64_t n, double *x, double alpha, const double *ph, double omega,
+                          const double *sh, cudaStream_t s);
 cudaError_t launch_adjoint_scatter(int64_t n, const int64_t *rp, const int32_t *ci,
                                    const double *lam, const double *x, double *gA,
                                    cudaStream_t s);

@@ -170,6 +170,60 @@ cudaError_t launch_add(int64_t n, double *x, const double *z, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// BiCGSTAB vector updates, each operation rounded once in the oracle's order.
+// p = r + beta * (p - omega * v)
+__global__ void k_bicg_dir(int64_t n, double *p, const double *__restrict__ r,
+                           const double *__restrict__ v, double beta, double omega) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = __dadd_rn(r[i], __dmul_rn(beta, __dsub_rn(p[i], __dmul_rn(omega, v[i]))));
+}
+
+// out = a - alpha * b
+__global__ void k_axmy(int64_t n, double *out, const double *__restrict__ a, double alpha,
+                       const double *__restrict__ b) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = __dsub_rn(a[i], __dmul_rn(alpha, b[i]));
+}
+
+// x = (x + alpha * ph) + omega * sh, or x = x + alpha * ph when sh is null
+__global__ void k_bicg_x(int64_t n, double *x, double alpha, const double *__restrict__ ph,
+                         double omega, const double *__restrict__ sh) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double xa = __dadd_rn(x[i], __dmul_rn(alpha, ph[i]));
+    x[i] = sh ? __dadd_rn(xa, __dmul_rn(omega, sh[i])) : xa;
+  }
+}
+
+cudaError_t launch_bicg_dir(int64_t n, double *p, const double *r, const double *v, double beta,
+                            double omega, cudaStream_t s) {
+  ProfScope prof_scope(ILUK_PROF_VECTOR, s);
+  if (n == 0) return cudaSuccess;
+  k_bicg_dir<<<vec_blocks(n), 256, 0, s>>>(n, p, r, v, beta, omega);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_axmy(int64_t n, double *out, const double *a, double alpha, const double *b,
+                        cudaStream_t s) {
+  ProfScope prof_scope(ILUK_PROF_VECTOR, s);
+  if (n == 0) return cudaSuccess;
+  k_axmy<<<vec_blocks(n), 256, 0, s>>>(n, out, a, alpha, b);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bicg_x(int64_t n, double *x, double alpha, const double *ph, double omega,
+                          const double *sh, cudaStream_t s) {
+  ProfScope prof_scope(ILUK_PROF_VECTOR, s);
+  if (n == 0) return cudaSuccess;
+  k_bicg_x<<<vec_blocks(n), 256, 0, s>>>(n, x, alpha, ph, omega, sh);
+  note_launch();
+  return cudaGetLastError();
+}
+
 // gA[p] = -(lambda_i * x_j) for entry p = (i, j).
 __global__ void k_adjoint_scatter(int64_t n, const int64_t *__restrict__ rp,
                                   const int32_t *__restrict__ ci, const double *__restrict__ lam,

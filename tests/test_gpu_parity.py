@@ -183,3 +183,44 @@ def test_batched_numeric_matches_single():
         assert_bits_equal(Fb[s], F.values(), f"set {s}")
         ref = oracle.factor(W.CSR(Pt.n, Pt.rowptr, Pt.colind, vals[s]), 1)
         assert_bits_equal(Fb[s], ref["val"], f"set {s} vs oracle")
+
+
+@pytest.mark.parametrize("prec", ["none", "ilu", "iilu"])
+@pytest.mark.parametrize("name,A,k,m", GMRES_CASES, ids=[c[0] for c in GMRES_CASES])
+def test_bicgstab_bit_exact_vs_tree_oracle(name, A, k, m, prec):
+    S, F, ref, (rp, ci, av) = factor_both(A, k)
+    b, bd = vec(51, A.n)
+    if prec == "ilu":
+        pr, kind, Fa = F, oracle.PREC_ILU, (ref["rowptr"], ref["colind"], ref["val"])
+    elif prec == "iilu":
+        pr = P.iiluk_build(F)
+        g = oracle.iiluk_build(A.n, ref["rowptr"], ref["colind"], ref["val"])
+        kind, Fa = oracle.PREC_IILU, (ref["rowptr"], ref["colind"], g)
+    else:
+        pr, kind, Fa = None, oracle.PREC_NONE, None
+    maxit = 800
+    x, info = P.bicgstab(rp, ci, av, bd, pr, rtol=1e-8, maxit=maxit, check=False)
+    st, xo, it, rel, half = oracle.bicgstab(A.n, A.rowptr, A.colind, A.val, b, kind, Fa, 1e-8,
+                                            maxit, oracle.DOT_TREE)
+    assert info.status == st and info.iters == it
+    assert bits([info.relres])[0] == bits([rel])[0]
+    assert_bits_equal(x, xo, "bicgstab x")
+    st2, xs, it2, rel2, _ = oracle.bicgstab(A.n, A.rowptr, A.colind, A.val, b, kind, Fa, 1e-8,
+                                            maxit, oracle.DOT_SEQ)
+    if st == oracle.OK and st2 == oracle.OK:
+        rel_diff = np.linalg.norm(x.cpu().numpy() - xs) / np.linalg.norm(xs)
+        if it2 == it:
+            assert rel_diff <= 1e-10
+        else:  # different stopping step: both meet the 1e-8 residual
+            assert rel_diff <= 1e-5
+
+
+def test_bicgstab_zero_rhs_and_breakdown_statuses():
+    A = W.conv_diff(10, 2, (20.0, 20.0))
+    rp, ci, av = to_dev(A)
+    z = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+    x, info = P.bicgstab(rp, ci, av, z)
+    assert info.status == L.OK and info.iters == 0 and not torch.any(x)
+    b, bd = vec(52, A.n)
+    x, info = P.bicgstab(rp, ci, av, bd, rtol=1e-14, maxit=3, check=False)
+    assert info.status == L.ENOCONV and info.iters == 3

@@ -44,6 +44,9 @@ MUTANTS = {
     "tree_dot_skips_partner": ("for (int p = 0; p < w; ++p) part[p] = part[p] + part[p + w];",
                                "for (int p = 0; p < w; ++p) part[p] = part[p] + part[p];"),
     "adjoint_sign": ("      gA[p] = -prod;", "      gA[p] = prod;"),
+    "bicgstab_omega_sign": ("      x[i] = xa + ws;", "      x[i] = xa - ws;"),
+    "bicgstab_beta_inverted": ("double b1 = rho / rho_prev, b2 = alpha / omega;",
+                               "double b1 = rho / rho_prev, b2 = omega / alpha;"),
     "transpose_backward_divides": ("""      double prod = tv[q] * y[tci[q]];
       s = s - prod;
     }
@@ -154,6 +157,21 @@ def pins_pass():
             raise AssertionError("dot")
     except Exception:
         failed.append("krylov")
+    try:  # BiCGSTAB against a dense solve, with and without preconditioning
+        A = W.conv_diff(8, 2, (20.0, 20.0))
+        n = A.n
+        b = W.uniform(W.stream_key(10, "b"), np.arange(n), -1, 1)
+        F = oracle.factor(A, 1)
+        Ad = W.csr_to_dense(A)
+        xd = np.linalg.solve(Ad, b)
+        for kind, Fa in ((oracle.PREC_NONE, None),
+                         (oracle.PREC_ILU, (F["rowptr"], F["colind"], F["val"]))):
+            st, x, it, rel, half = oracle.bicgstab(n, A.rowptr, A.colind, A.val, b, kind, Fa,
+                                                   1e-12, 500, oracle.DOT_TREE)
+            if st != 0 or np.linalg.norm(x - xd) > 1e-9 * np.linalg.norm(xd):
+                raise AssertionError("bicgstab")
+    except Exception:
+        failed.append("bicgstab")
     return failed
 
 
@@ -172,7 +190,7 @@ def test_every_planted_mistake_is_caught(name, monkeypatch):
         for attr in ("orc_check_pattern", "orc_symbolic", "orc_sym_status", "orc_sym_copy",
                      "orc_sym_free", "orc_numeric", "orc_lsolve", "orc_usolve", "orc_apply",
                      "orc_apply_t", "orc_iiluk_apply", "orc_iiluk_build", "orc_transpose",
-                     "orc_dot", "orc_spmv", "orc_gmres", "orc_adjoint"):
+                     "orc_dot", "orc_spmv", "orc_gmres", "orc_adjoint", "orc_bicgstab"):
             f_real, f_mut = getattr(real, attr), getattr(mutant, attr)
             f_mut.argtypes = f_real.argtypes
             f_mut.restype = f_real.restype

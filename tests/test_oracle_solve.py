@@ -170,3 +170,58 @@ def test_adjoint_gradient_matches_finite_differences():
         bm[c] -= h
         fd = (loss(theta0, bp) - loss(theta0, bm)) / (2 * h)
         assert abs(fd - lam[c]) <= 1e-5 * max(abs(fd), 1e-3 * np.abs(lam).max())
+
+
+# --- BiCGSTAB (the paper's solver, Sec. 4) ----------------------------------
+
+def test_bicgstab_identity_is_exact_in_half_a_step():
+    # A = I: p = b, v = b, alpha = (b,b)/(b,b) = 1 exactly, s = 0: x = b bit for bit
+    n = 50
+    A = W.dense_to_csr(np.eye(n), np.eye(n, dtype=bool))
+    b = W.uniform(W.stream_key(21, "b"), np.arange(n), -1, 1)
+    st, x, it, rel, half = oracle.bicgstab(n, A.rowptr, A.colind, A.val, b)
+    assert st == oracle.OK and it == 1 and half and rel == 0.0
+    assert np.array_equal(x, b)
+
+
+def test_bicgstab_exact_preconditioner_converges_in_one_step():
+    A = W.random_sparse(40, 0.1, 3)
+    F = oracle.factor(A, 250)  # complete LU: M = A up to rounding
+    b = W.uniform(W.stream_key(22, "b"), np.arange(A.n), -1, 1)
+    st, x, it, rel, half = oracle.bicgstab(A.n, A.rowptr, A.colind, A.val, b, oracle.PREC_ILU,
+                                           (F["rowptr"], F["colind"], F["val"]), 1e-10)
+    assert st == oracle.OK and it == 1 and half
+
+
+@pytest.mark.parametrize("prec", ["none", "ilu", "iilu"])
+@pytest.mark.parametrize("mode", [oracle.DOT_SEQ, oracle.DOT_TREE])
+def test_bicgstab_matches_dense_solve(prec, mode):
+    A = W.conv_diff(12, 2, (20.0, 20.0))
+    n = A.n
+    b = W.uniform(W.stream_key(23, "b"), np.arange(n), -1, 1)
+    F = oracle.factor(A, 1)
+    if prec == "none":
+        kind, Fa = oracle.PREC_NONE, None
+    elif prec == "ilu":
+        kind, Fa = oracle.PREC_ILU, (F["rowptr"], F["colind"], F["val"])
+    else:
+        g = oracle.iiluk_build(n, F["rowptr"], F["colind"], F["val"])
+        kind, Fa = oracle.PREC_IILU, (F["rowptr"], F["colind"], g)
+    st, x, it, rel, half = oracle.bicgstab(n, A.rowptr, A.colind, A.val, b, kind, Fa, 1e-11,
+                                           2000, mode)
+    assert st == oracle.OK
+    xd = np.linalg.solve(W.csr_to_dense(A), b)
+    assert np.linalg.norm(x - xd) <= 1e-8 * np.linalg.norm(xd)
+    # the reported residual is the true one
+    r = b - W.csr_to_dense(A) @ x
+    assert abs(rel - np.linalg.norm(r) / np.linalg.norm(b)) <= 1e-6 * rel + 1e-15
+
+
+def test_bicgstab_zero_rhs_and_nonconvergence():
+    A = W.conv_diff(10, 2, (20.0, 20.0))
+    st, x, it, rel, half = oracle.bicgstab(A.n, A.rowptr, A.colind, A.val, np.zeros(A.n))
+    assert st == oracle.OK and it == 0 and not np.any(x)
+    b = W.uniform(W.stream_key(24, "b"), np.arange(A.n), -1, 1)
+    st, x, it, rel, half = oracle.bicgstab(A.n, A.rowptr, A.colind, A.val, b, rtol=1e-14,
+                                           maxit=3)
+    assert st == oracle.ENOCONV and it == 3
