@@ -518,7 +518,8 @@ def adjoint(args):
 def suite(args):
     """Every phase of every single-system configuration: C1 (2D 64^2, ILU(2)),
     C2 (random band n=160,000, ILU(k) for k = 0..3), C3 (3D 64^3, ILU(2) and
-    TPIILU(2)).  Per phase: median ms of 20 CUDA-event-timed runs after 5
+    TPIILU(2)), C6 (27-point Poisson on 50^3 and 90^3, k = 0, 1, ILU(k)
+    against TPIILU(k) and the TPILU(k) policy).  Per phase: median ms of 20 CUDA-event-timed runs after 5
     warm-ups, algorithmic GB/s and fraction of the measured HBM peak, ns per
     level of the DAG the phase walks; per configuration the bit mismatches
     against the oracle and the oracle's own times on one host core (where it
@@ -559,7 +560,11 @@ def suite(args):
              ("C2 band n=160000", lambda: W.random_band_160k(k=1), 1, False),
              ("C2 band n=160000", lambda: W.random_band_160k(k=2), 2, True),
              ("C2 band n=160000", lambda: W.random_band_160k(k=3), 3, False),
-             ("C3 3D 64^3", W.conv_diff_3d, 2, True)]
+             ("C3 3D 64^3", W.conv_diff_3d, 2, True),
+             ("C6 27-point Poisson 50^3", lambda: W.poisson27_problem(50, 0), 0, True),
+             ("C6 27-point Poisson 50^3", lambda: W.poisson27_problem(50, 1), 1, True),
+             ("C6 27-point Poisson 90^3", lambda: W.poisson27_problem(90, 0), 0, True),
+             ("C6 27-point Poisson 90^3", lambda: W.poisson27_problem(90, 1), 1, True)]
     rows = []
     for name, make, k, with_iilu in cases:
         Pb = make()
@@ -583,10 +588,11 @@ def suite(args):
             "iilu_apply": 12 * nnzF + 16 * (n + 1) + 8 * n + 40 * n,
         }
         ph = {}
-        ph["symbolic"] = med_ms(lambda: P.symbolic(rp, ci, k), reps=5 if k == 3 else 20,
-                                warm=1 if k == 3 else 5)
-        ph["numeric"] = med_ms(lambda: F.refactor(av), reps=5 if k == 3 else 20,
-                               warm=1 if k == 3 else 5)
+        big = k == 3 or n > 500000
+        ph["symbolic"] = med_ms(lambda: P.symbolic(rp, ci, k), reps=5 if big else 20,
+                                warm=1 if big else 5)
+        ph["numeric"] = med_ms(lambda: F.refactor(av), reps=5 if big else 20,
+                               warm=1 if big else 5)
         ph["apply"] = med_ms(lambda: F.apply(pvec))
         x, info = P.gmres(rp, ci, av, b, F, restart=Pb.restart, rtol=Pb.rtol)
         ph["gmres"] = med_ms(lambda: P.gmres(rp, ci, av, b, F, restart=Pb.restart, rtol=Pb.rtol),
@@ -604,6 +610,12 @@ def suite(args):
             ph["gmres_iilu"] = med_ms(lambda: P.gmres(rp, ci, av, b, M, restart=Pb.restart,
                                                       rtol=Pb.rtol, maxit=5000, check=False),
                                       reps=3, warm=1)
+            # the TPILU(k) policy: TPIILU for at most one GMRES cycle, then ILU(k)
+            xt, info_t, used_t = P.tpilu_solve(rp, ci, av, b, F, M, restart=Pb.restart,
+                                               rtol=Pb.rtol, iilu_maxit=Pb.restart, maxit=5000)
+            ph["tpilu_policy"] = med_ms(lambda: P.tpilu_solve(
+                rp, ci, av, b, F, M, restart=Pb.restart, rtol=Pb.rtol, iilu_maxit=Pb.restart,
+                maxit=5000), reps=3, warm=1)
             xbi, info_bi = P.bicgstab(rp, ci, av, b, M, rtol=Pb.rtol, maxit=5000, check=False)
             ph["bicgstab_iilu"] = med_ms(lambda: P.bicgstab(rp, ci, av, b, M, rtol=Pb.rtol,
                                                             maxit=5000, check=False),
@@ -629,7 +641,9 @@ def suite(args):
         if with_iilu:
             row["gmres_iilu_iters"] = info_i.iters
             row["bicgstab_iilu_iters"] = info_bi.iters
-        if k <= 2:
+            row["tpilu_policy_used"] = used_t
+            row["tpilu_policy_iters"] = info_t.iters
+        if k <= 2 and n <= 300000:
             t_fac, ref = cpu_s(lambda: oracle.factor(A, k))
             t_app, yo = cpu_s(lambda: oracle.apply(n, ref["rowptr"], ref["colind"], ref["val"],
                                                    pvec.cpu().numpy()))
@@ -660,7 +674,7 @@ def suite(args):
             row["parity"] = par
             row["oracle_one_core"] = orc
         else:
-            row["parity"] = "oracle skipped: its factorization of this case takes minutes"
+            row["parity"] = "oracle skipped: too slow on one core for this case"
         rows.append(row)
         print(json.dumps({"progress": name, "k": k}), file=sys.stderr, flush=True)
     out = {"metric": METRIC, "workload": "suite", "unit": "ms", "dtype": "f64",

@@ -322,6 +322,22 @@ int bicgstab_solve(const iluk_pattern *A, const double *A_val, int prec_kind, vo
                    void *stream);
 
 /*
+ * The TPILU(k) solve policy (Sec. 1): first the level-based incomplete
+ * inverse, and when that does not converge fast, revert to the stable ILU(k)
+ * sweeps.  Runs `solver` (ILUK_SOLVER_GMRES with restart `m`, or
+ * ILUK_SOLVER_BICGSTAB) preconditioned by M = TPIILU(F) (built and freed here
+ * when M is null) for at most iilu_maxit iterations; if that solve does not
+ * reach rtol (or breaks down), solves again from x0 = 0 preconditioned by F's
+ * sweeps for at most maxit iterations.  *used receives ILUK_PREC_IILU or
+ * ILUK_PREC_ILU, the preconditioner of the returned x; info describes that
+ * last solve.  Synchronous.
+ */
+enum { ILUK_SOLVER_GMRES = 0, ILUK_SOLVER_BICGSTAB = 1 };
+int tpilu_solve(const iluk_pattern *A, const double *A_val, iluk_fac *F, iiluk *M, int solver,
+                const double *b, double *x, int m, double rtol, int iilu_maxit, int maxit,
+                int *used, iluk_info *info, void *stream);
+
+/*
  * a8 helper. Gradient of a loss through x = A^-1 b with respect to the stored
  * entries of A: gA[p] = -lambda_i * x_j for entry p = (i, j), where lambda
  * solves A^T lambda = dL/dx.  Asynchronous.

@@ -246,6 +246,26 @@ def bicgstab(n, arp, aci, av, b, prec_kind=PREC_NONE, F=None, rtol=1e-8, maxit=1
     return st, x[:n].copy(), int(info[0]), float(info[1]), bool(info[2])
 
 
+def tpilu(n, arp, aci, av, b, F, g, solver="gmres", restart=50, rtol=1e-8, iilu_maxit=50,
+          maxit=10000, dotmode=DOT_SEQ):
+    """The TPILU(k) solve policy of Sec. 1 composed from the solvers above:
+    TPIILU first with at most ``iilu_maxit`` iterations, and if it does not
+    converge (or breaks down), ILU(k) from x0 = 0.  ``F`` = (rowptr, colind,
+    values) of the factors, ``g`` their TPIILU array.
+    Returns (status, x, iterations, relres, used) with used "iilu" or "ilu"."""
+    def run(kind, Fa, its):
+        if solver == "gmres":
+            st, x, it, rel, _ = gmres(n, arp, aci, av, b, kind, Fa, restart, rtol, its, dotmode)
+        else:
+            st, x, it, rel, _ = bicgstab(n, arp, aci, av, b, kind, Fa, rtol, its, dotmode)
+        return st, x, it, rel
+    st, x, it, rel = run(PREC_IILU, (F[0], F[1], g), iilu_maxit)
+    if st == OK:
+        return st, x, it, rel, "iilu"
+    st, x, it, rel = run(PREC_ILU, F, maxit)
+    return st, x, it, rel, "ilu"
+
+
 def adjoint(n, arp, aci, av, frp, fci, fv, x, gx, restart=30, rtol=1e-8, maxit=10000,
             dotmode=DOT_SEQ):
     """A^T lambda = gx with (L~U~)^-T preconditioning; dL/da_ij = -lambda_i x_j.

@@ -15,6 +15,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libiluk.so")
 
 OK, EINVAL, EPATTERN, ENODIAG, EZEROPIVOT, ENONFINITE, ENOMEM, ETIMEOUT, ENOCONV, ECUDA = range(10)
 PREC_NONE, PREC_ILU, PREC_IILU = 0, 1, 2
+SOLVER_GMRES, SOLVER_BICGSTAB = 0, 1
 SCHED_AUTO, SCHED_FLAGS, SCHED_SINGLE_CTA, SCHED_CLUSTER, SCHED_WARP_GRID, SCHED_WARP_CLUSTER = 0, 1, 2, 3, 4, 5
 _SCHED_NAMES = ["auto", "lockstep_grid", "lockstep_cta", "lockstep_cluster", "warp_grid",
                 "warp_cluster"]
@@ -95,6 +96,7 @@ SIGNATURES = [
     ("iluk_div_rn", I, [I64, P, P, P, P]),
     ("gmres_solve", I, [P, P, I, P, P, P, I, D, I, I, P, P]),
     ("bicgstab_solve", I, [P, P, I, P, P, P, D, I, P, P]),
+    ("tpilu_solve", I, [P, P, P, P, I, P, P, I, D, I, I, P, P, P]),
     ("iluk_adjoint_scatter", I, [P, P, P, P, P]),
     ("iluk_numeric_batched", I, [P, I64, P, P, P, P]),
     ("iluk_batch_create", I, [P, I64, I, D, I, PP, P]),

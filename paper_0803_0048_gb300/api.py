@@ -279,6 +279,26 @@ def bicgstab(rowptr, colind, vals, b, prec=None, rtol=1e-8, maxit=10000, x=None,
     return xo, info
 
 
+def tpilu_solve(rowptr, colind, vals, b, F, M=None, solver="gmres", restart=50, rtol=1e-8,
+                iilu_maxit=50, maxit=10000, check=True):
+    """The TPILU(k) policy (Sec. 1): ``solver`` ("gmres" or "bicgstab") with
+    the TPIILU inverses M of F (built when None) for at most ``iilu_maxit``
+    iterations, then, if that does not converge, again from x0 = 0 with F's
+    ILU(k) sweeps.  Returns (x, info, used) with used "iilu" or "ilu"."""
+    A = CsrPattern(rowptr, colind)
+    _check_dev(vals, b)
+    xo = torch.empty_like(b)
+    kind = {"gmres": L.SOLVER_GMRES, "bicgstab": L.SOLVER_BICGSTAB}[solver]
+    info = L.Info()
+    used = C.c_int(-1)
+    st = L.load().tpilu_solve(A.ref, _ptr(vals), F.h, M.h if M is not None else None, kind,
+                              _ptr(b), _ptr(xo), int(restart), float(rtol), int(iilu_maxit),
+                              int(maxit), C.byref(used), C.byref(info), C.c_void_p(_stream()))
+    if check and st != L.OK:
+        raise IlukError(st, info, "tpilu_solve")
+    return xo, info, ("iilu" if used.value == L.PREC_IILU else "ilu")
+
+
 def adjoint_scatter(rowptr, colind, lam, x, out=None):
     """gA[p] = -lambda_i x_j on A's pattern."""
     A = CsrPattern(rowptr, colind)

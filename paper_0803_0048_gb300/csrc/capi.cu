@@ -1323,4 +1323,31 @@ int bicgstab_solve(const iluk_pattern *A, const double *A_val, int prec_kind, vo
   return status;
 }
 
+int tpilu_solve(const iluk_pattern *A, const double *A_val, iluk_fac *F, iiluk *M, int solver,
+                const double *b, double *x, int m, double rtol, int iilu_maxit, int maxit,
+                int *used, iluk_info *info, void *stream) {
+  info_init(info);
+  if (!A || !F || !used || (solver != ILUK_SOLVER_GMRES && solver != ILUK_SOLVER_BICGSTAB) ||
+      iilu_maxit < 0 || maxit < 0 || (solver == ILUK_SOLVER_GMRES && m < 1))
+    return fail(info, ILUK_EINVAL);
+  auto run = [&](int kind, void *prec, int its) {
+    return solver == ILUK_SOLVER_GMRES
+               ? gmres_solve(A, A_val, kind, prec, b, x, m, rtol, its, 0, info, stream)
+               : bicgstab_solve(A, A_val, kind, prec, b, x, rtol, its, info, stream);
+  };
+  iiluk *own = nullptr;
+  if (!M) {
+    const int bst = iiluk_build(F, &own, info, stream);
+    if (bst != ILUK_OK) return bst;
+    M = own;
+  }
+  int st = run(ILUK_PREC_IILU, M, iilu_maxit);
+  iiluk_destroy(own);
+  *used = ILUK_PREC_IILU;
+  // a failed sweep status (time-out) is not a convergence failure: report it
+  if (st == ILUK_OK || (st != ILUK_ENOCONV && st != ILUK_EINVAL)) return st;
+  *used = ILUK_PREC_ILU;
+  return run(ILUK_PREC_ILU, F, maxit);
+}
+
 }  // extern "C"

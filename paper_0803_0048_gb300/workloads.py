@@ -326,6 +326,42 @@ def conv_diff_3d(N: int = 64, k: int = 2, beta=(50.0, 50.0, 50.0)) -> Problem:
     return Problem(f"convdiff3d_{N}^3", A, matvec_rowseq(A, xs), xs, k, 50, 1e-8)
 
 
+def poisson27(N: int) -> CSR:
+    """Poisson's equation on an N^3 interior grid by 27-point central
+    differencing (the paper's Sec. 4 workload, grids 50^3 to 90^3): 26 on the
+    diagonal and -1 for each of the 26 neighbours (face, edge and corner)
+    inside the grid; zero Dirichlet boundary; natural ordering, x fastest.
+    Columns are emitted in ascending order."""
+    n = N ** 3
+    idx = np.arange(n, dtype=np.int64)
+    x, y, z = idx % N, (idx // N) % N, idx // (N * N)
+    cols, vals = [], []
+    # offsets in ascending column order: dz outermost, then dy, then dx
+    for dz in (-1, 0, 1):
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                ok = ((x + dx >= 0) & (x + dx < N) & (y + dy >= 0) & (y + dy < N) &
+                      (z + dz >= 0) & (z + dz < N))
+                c = np.where(ok, idx + dx + N * dy + N * N * dz, -1)
+                v = 26.0 if (dx, dy, dz) == (0, 0, 0) else -1.0
+                cols.append(c)
+                vals.append(np.full(n, v))
+    C = np.stack(cols, axis=1)
+    V = np.stack(vals, axis=1)
+    keep = C >= 0
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    rowptr[1:] = np.cumsum(keep.sum(axis=1))
+    return CSR(n, rowptr, C[keep].astype(np.int32), V[keep].astype(np.float64))
+
+
+def poisson27_problem(N: int = 50, k: int = 0) -> Problem:
+    """27-point Poisson on an N^3 grid, b = A x* for a uniform x*, GMRES(50)."""
+    seed = MASTER_SEED + 6
+    A = poisson27(N)
+    xs = _xstar(seed, A.n)
+    return Problem(f"poisson27_{N}^3", A, matvec_rowseq(A, xs), xs, k, 50, 1e-8)
+
+
 def batched_values(nsets: int = 512, N: int = 32, seed: int = MASTER_SEED + 4):
     """``nsets`` value sets on one N^3 7-point pattern.
 

@@ -224,3 +224,22 @@ def test_bicgstab_zero_rhs_and_breakdown_statuses():
     b, bd = vec(52, A.n)
     x, info = P.bicgstab(rp, ci, av, bd, rtol=1e-14, maxit=3, check=False)
     assert info.status == L.ENOCONV and info.iters == 3
+
+
+@pytest.mark.parametrize("solver", ["gmres", "bicgstab"])
+@pytest.mark.parametrize("budget,expect", [(400, "iilu"), (2, "ilu")])
+def test_tpilu_policy_bit_exact(solver, budget, expect):
+    Pb = W.poisson27_problem(14, k=1)
+    A = Pb.A
+    S, F, ref, (rp, ci, av) = factor_both(A, 1)
+    b, bd = vec(61, A.n)
+    x, info, used = P.tpilu_solve(rp, ci, av, bd, F, solver=solver, restart=30, rtol=1e-8,
+                                  iilu_maxit=budget, maxit=400)
+    g = oracle.iiluk_build(A.n, ref["rowptr"], ref["colind"], ref["val"])
+    st, xo, it, rel, used_o = oracle.tpilu(A.n, A.rowptr, A.colind, A.val, b,
+                                           (ref["rowptr"], ref["colind"], ref["val"]), g, solver,
+                                           30, 1e-8, budget, 400, oracle.DOT_TREE)
+    assert used == used_o == expect
+    assert info.status == st and info.iters == it
+    assert bits([info.relres])[0] == bits([rel])[0]
+    assert_bits_equal(x, xo, "tpilu x")
