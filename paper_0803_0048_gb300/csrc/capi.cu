@@ -244,12 +244,8 @@ void iluk_sym_destroy(iluk_sym *S) {
   dfree(S->a2f, s);
   dfree(S->pinfo, s);
   dfree(S->tinfo, s);
-  dfree(S->lord.order, s);
-  dfree(S->uord.order, s);
-  dfree(S->lord.corder, s);
-  dfree(S->uord.corder, s);
-  dfree(S->lord.lstart, s);
-  dfree(S->uord.lstart, s);
+  level_order_free(S->lord, s);
+  level_order_free(S->uord, s);
   delete S;
 }
 
@@ -458,12 +454,8 @@ void iluk_fac_destroy(iluk_fac *F) {
   dfree(F->tcolind, s);
   dfree(F->tdiag, s);
   dfree(F->tval, s);
-  dfree(F->tlord.order, s);
-  dfree(F->tuord.order, s);
-  dfree(F->tlord.corder, s);
-  dfree(F->tuord.corder, s);
-  dfree(F->tlord.lstart, s);
-  dfree(F->tuord.lstart, s);
+  level_order_free(F->tlord, s);
+  level_order_free(F->tuord, s);
   delete F;
 }
 

@@ -8,6 +8,14 @@
 
 // Rows of one sweep DAG in level order, every level padded with -1 to a
 // multiple of 32 entries (see levels.cu).
+// Where the cluster warp-per-row sweep keeps x_i: in the shared memory of the
+// CTA that computes row i (rank << 26 | slot), which depends on the order,
+// the cluster width and the CTA width; built on first use.
+struct OwnerCode {
+  int C = 0, threads = 0;
+  int32_t *code = nullptr;
+};
+
 struct LevelOrder {
   int32_t *order = nullptr;   // levels padded to multiples of 32 slots (-1 fills)
   int64_t *lstart = nullptr;  // int64[nlev+1]: first slot of each level
@@ -15,7 +23,9 @@ struct LevelOrder {
   int32_t nlev = 0;
   int32_t *corder = nullptr;  // the same rows without padding (clen = rows)
   int64_t clen = 0;
+  OwnerCode owner[8];         // cache, see OwnerCode
 };
+void level_order_free(LevelOrder &lo, cudaStream_t s);
 
 // Handle layouts (opaque in the public header).
 struct iluk_sym {

@@ -225,3 +225,13 @@ int build_levels_pair(int64_t n, const int64_t *rp, const int32_t *ci, const int
 }
 
 }  // namespace iluk
+
+// LevelOrder is declared at global scope (internal.h), and so is this.
+void level_order_free(LevelOrder &lo, cudaStream_t s) {
+  if (lo.order) cudaFreeAsync(lo.order, s);
+  if (lo.corder) cudaFreeAsync(lo.corder, s);
+  if (lo.lstart) cudaFreeAsync(lo.lstart, s);
+  for (OwnerCode &oc : lo.owner)
+    if (oc.code) cudaFreeAsync(oc.code, s);
+  lo = LevelOrder();
+}

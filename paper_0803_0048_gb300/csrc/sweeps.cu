@@ -382,28 +382,34 @@ k_sweep_wpr(const int32_t *__restrict__ order, int64_t len, int64_t n,
             const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
             const int64_t *__restrict__ dg, const double *__restrict__ v,
             const double2 *__restrict__ rd, const double *in, double *out, double *clear,
-            DevErr *err, int64_t limit_ns) {
+            DevErr *err, int64_t limit_ns, const int32_t *__restrict__ owner) {
+  // SCOPE 1: x_i lives in the shared memory of the CTA whose warp computes
+  // row i, at slot (k * wpc + warp) for the warp's k-th row; owner[i] holds
+  // (rank << 26 | slot), so the producer's store stays on its own SM and only
+  // the dependants' polls cross SMs.
   extern __shared__ __align__(16) double xs[];
   unsigned rank = 0, C = 1, base = 0;
-  int lg = 0;
+  const int wpc = blockDim.x >> 5;  // warps per CTA
   int64_t slice = 0;
   if (SCOPE == 1) {
     asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
     asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(C));
-    lg = __ffs((int)C) - 1;  // C is a power of two
-    slice = (n + C - 1) / C;
+    const int64_t nwc = (int64_t)C * wpc;
+    slice = (len + nwc - 1) / nwc * wpc;
     for (int64_t j = threadIdx.x; j < slice; j += blockDim.x)
       xs[j] = __longlong_as_double((long long)kPending);
     base = (unsigned)__cvta_generic_to_shared(xs);
     cluster_sync_all();
   }
   const int lane = threadIdx.x & 31;
-  const int64_t gw = SCOPE == 1 ? (int64_t)rank * (blockDim.x >> 5) + (threadIdx.x >> 5)
+  const int64_t gw = SCOPE == 1 ? (int64_t)rank * wpc + (threadIdx.x >> 5)
                                 : ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = SCOPE == 1 ? (int64_t)C * (blockDim.x >> 5)
-                                : ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t nw = SCOPE == 1 ? (int64_t)C * wpc : ((int64_t)gridDim.x * blockDim.x) >> 5;
+  unsigned own_slot = 0;  // SCOPE 1: the slot of this warp's current row
+  unsigned own_base = 0;
+  if (SCOPE == 1) asm("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(own_base) : "r"(base), "r"(rank));
   bool ok = true;
-  for (int64_t slot = gw; slot < len && ok; slot += nw) {
+  for (int64_t slot = gw; slot < len && ok; slot += nw, own_slot += wpc) {
     const int64_t row = order[slot];
     if (row < 0) continue;
     const int64_t d = dg[row];
@@ -417,7 +423,8 @@ k_sweep_wpr(const int32_t *__restrict__ order, int64_t len, int64_t n,
     const int mylen = (int)(FORWARD ? d - first : first - d);
     constexpr int64_t step = FORWARD ? 1 : -1;
     double s = in[row];
-    const unsigned sa = SCOPE == 1 ? dsm_addr(base, row, lg) : 0u;  // where x_row goes
+    // where x_row goes: this CTA's slot for the warp's current row
+    const unsigned sa = SCOPE == 1 ? own_base + ((own_slot + (threadIdx.x >> 5)) << 3) : 0u;
     if (clear && lane == 0) clear[row] = __longlong_as_double((long long)kPending);
     for (int b = 0; b < mylen && ok; b += 32) {
       const int e = b + lane;
@@ -430,7 +437,12 @@ k_sweep_wpr(const int32_t *__restrict__ order, int64_t len, int64_t n,
       if (act) {
         c = ci[first + step * e];
         f = v[first + step * e];
-        if (SCOPE == 1) da = dsm_addr(base, c, lg);
+        if (SCOPE == 1) {
+          const unsigned oc = (unsigned)owner[c];
+          unsigned a;
+          asm("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(a) : "r"(base), "r"(oc >> 26));
+          da = a + ((oc & ((1u << 26) - 1u)) << 3);
+        }
         x = wpr_load<SCOPE>(out, da, c);
         if (!pending(x)) {
           prod = __dmul_rn(f, x);
@@ -487,10 +499,56 @@ k_sweep_wpr(const int32_t *__restrict__ order, int64_t len, int64_t n,
   if (SCOPE == 1) {
     cluster_sync_all();
     for (int64_t j = threadIdx.x; j < slice; j += blockDim.x) {
-      const int64_t ii = j * C + rank;
-      if (ii < n) out[ii] = xs[j];
+      const int64_t pos = (j / wpc) * nw + (int64_t)rank * wpc + j % wpc;
+      if (pos < len) out[order[pos]] = xs[j];
     }
   }
+}
+
+// owner[order[pos]] = (rank << 26 | slot) for the CTA layout above.
+__global__ void k_owner_codes(const int32_t *__restrict__ order, int64_t len, int C, int wpc,
+                              int32_t *owner) {
+  const int64_t nw = (int64_t)C * wpc;
+  for (int64_t pos = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; pos < len;
+       pos += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t g = pos % nw;
+    const int64_t slot = (pos / nw) * wpc + g % wpc;
+    owner[order[pos]] = (int32_t)(((g / wpc) << 26) | slot);
+  }
+}
+
+// The (cached) owner codes of a level order for one cluster and CTA width.
+static std::mutex g_owner_mu;
+static const int32_t *owner_codes(const LevelOrder &lo_c, int64_t n, int C, int threads,
+                                  cudaStream_t s) {
+  LevelOrder &lo = const_cast<LevelOrder &>(lo_c);  // a cache of the order
+  std::lock_guard<std::mutex> lk(g_owner_mu);
+  for (OwnerCode &oc : lo.owner)
+    if (oc.code && oc.C == C && oc.threads == threads) return oc.code;
+  OwnerCode *slot = nullptr;
+  for (OwnerCode &oc : lo.owner)
+    if (!oc.code) {
+      slot = &oc;
+      break;
+    }
+  if (!slot) {  // full: reuse the first entry (stream order keeps its users safe)
+    slot = &lo.owner[0];
+    cudaFreeAsync(slot->code, s);
+    slot->code = nullptr;
+  }
+  if (cudaMallocAsync((void **)&slot->code, (size_t)(n > 0 ? n : 1) * sizeof(int32_t), s) !=
+      cudaSuccess) {
+    slot->code = nullptr;
+    return nullptr;
+  }
+  int64_t b = (lo.clen + 255) / 256;
+  if (b > (int64_t)num_sms() * 8) b = (int64_t)num_sms() * 8;
+  if (b < 1) b = 1;
+  k_owner_codes<<<(unsigned)b, 256, 0, s>>>(lo.corder, lo.clen, C, threads / 32, slot->code);
+  note_launch();
+  slot->C = C;
+  slot->threads = threads;
+  return slot->code;
 }
 
 __global__ void k_fill_pending(int64_t n, double *x, unsigned long long bits) {
@@ -589,12 +647,9 @@ static int cluster_width(int64_t n, K kern) {
 
 int cluster_size_for(int64_t n) { return cluster_width(n, k_sweep_cluster<true, false, 4>); }
 
-template <typename K>
+template <typename K, typename... Args>
 static cudaError_t launch_on_cluster(K kern, int C, int threads, size_t smem, cudaStream_t s,
-                                     const int32_t *order, int64_t len, int64_t n,
-                                     const int64_t *rp, const int32_t *ci, const int64_t *dg,
-                                     const double *v, const double2 *rd, const double *in,
-                                     double *out, double *clear, DevErr *err, int64_t limit) {
+                                     Args... args) {
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
@@ -611,8 +666,7 @@ static cudaError_t launch_on_cluster(K kern, int C, int threads, size_t smem, cu
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  e = cudaLaunchKernelEx(&cfg, kern, order, len, n, rp, ci, dg, v, rd, in, out, clear, err,
-                         limit);
+  e = cudaLaunchKernelEx(&cfg, kern, args...);
   note_launch();
   return e;
 }
@@ -647,14 +701,19 @@ static cudaError_t run_sweep(int64_t n, const LevelOrder &lo, const int64_t *rp,
     const int C = wpr ? cluster_width(n, k_sweep_wpr<FORWARD, DIVIDE, 1>)
                       : cluster_width(n, k_sweep_cluster<FORWARD, DIVIDE, 4>);
     if (C == 0) return cudaErrorInvalidConfiguration;
+    if (wpr) {
+      const int wpc = threads / 32;
+      const int64_t nwc = (int64_t)C * wpc;
+      const size_t wsmem = (size_t)((len + nwc - 1) / nwc * wpc) * sizeof(double);
+      if (wsmem > (size_t)max_smem_optin()) return cudaErrorInvalidConfiguration;
+      const int32_t *owner = owner_codes(lo, n, C, threads, s);
+      if (!owner) return cudaErrorMemoryAllocation;
+      return launch_on_cluster(k_sweep_wpr<FORWARD, DIVIDE, 1>, C, threads, wsmem, s, order, len,
+                               n, rp, ci, dg, v, rd, in, out, clear, err, limit, owner);
+    }
     const size_t smem = (size_t)((n + C - 1) / C) * sizeof(double);
-    if (wpr)
-      return launch_on_cluster(k_sweep_wpr<FORWARD, DIVIDE, 1>, C, threads, smem, s, order, len,
-                               n, rp, ci,
-                               dg, v, rd, in, out, clear, err, limit);
     return launch_on_cluster(k_sweep_cluster<FORWARD, DIVIDE, 4>, C, kCtaThreads, smem, s, order,
-                             len, n, rp,
-                             ci, dg, v, rd, in, out, clear, err, limit);
+                             len, n, rp, ci, dg, v, rd, in, out, clear, err, limit);
   }
   if (sched == ILUK_SCHED_WARP_GRID) {
     auto kern = k_sweep_wpr<FORWARD, DIVIDE, 0>;
@@ -665,9 +724,10 @@ static cudaError_t run_sweep(int64_t n, const LevelOrder &lo, const int64_t *rp,
     const int64_t want = (len + (threads / 32) - 1) / (threads / 32);
     if (grid > want) grid = want;
     const int64_t nn = n;
+    const int32_t *no_owner = nullptr;
     void *args[] = {(void *)&order, (void *)&len, (void *)&nn, (void *)&rp, (void *)&ci,
                     (void *)&dg, (void *)&v, (void *)&rd, (void *)&in, (void *)&out,
-                    (void *)&clear, (void *)&err, (void *)&limit};
+                    (void *)&clear, (void *)&err, (void *)&limit, (void *)&no_owner};
     cudaError_t e = cudaLaunchCooperativeKernel((const void *)kern, dim3((unsigned)grid),
                                                 dim3((unsigned)threads), args, 0, s);
     note_launch();
