@@ -461,7 +461,7 @@ void iluk_fac_destroy(iluk_fac *F) {
 
 static int numeric_into(iluk_fac *F, const double *A_val, iluk_info *info, cudaStream_t s) {
   const iluk_sym *S = F->S;
-  // numeric uses the sweep scratch: [0..1] ticket, [4..4+n) ready flags
+  // the numeric phase's row ticket lives in the handle's scratch
   CK(cudaMemsetAsync(F->sync, 0, sweep_sync_ints(S->n) * sizeof(int), s));
   CK(launch_fill_err(F->err, s));
   // the numeric phase also publishes the reciprocals of the diagonal
@@ -720,7 +720,7 @@ int iiluk_build(const iluk_fac *F, iiluk **out, iluk_info *info, void *stream) {
   DevErr *err = nullptr;
   cudaError_t e = dalloc(&M->g, S->nnz, s);
   if (e == cudaSuccess) e = dalloc(&M->tmp, S->n, s);
-  if (e == cudaSuccess) e = dalloc(&sync, 4 + 2 * S->n, s);
+  if (e == cudaSuccess) e = dalloc(&sync, 4, s);  // the build's row ticket
   if (e == cudaSuccess) e = dalloc(&err, 2, s);
   if (e == cudaSuccess) e = launch_fill_err(err, s);
   if (e == cudaSuccess) e = launch_fill_err(err + 1, s);

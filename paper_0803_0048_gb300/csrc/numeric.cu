@@ -4,11 +4,14 @@
 // Row i is scattered from A onto F's pattern in the warp's shared-memory
 // slice (fill positions +0.0).  For each h in L(i), ascending, the warp finds
 // where row h's entries j > h fall in row i (pattern only, before row h is
-// final), waits for the values of row h, forms the multiplier
-// f_ih <- f_ih / f_hh (IEEE division) and applies f_ij <- f_ij - f_ih * f_hj
-// (one rounding for the product, one for the difference).  Lanes own
-// distinct j, so each entry sees its updates in ascending h, exactly as the
-// sequential algorithm does.  The finished row is then written back.
+// final), waits for the values of row h, forms the multiplier f_ih / f_hh
+// (IEEE's quotient: through row h's published reciprocal when it is there,
+// else by IEEE division) and applies f_ij <- f_ij - f_ih * f_hj (one rounding
+// for the product, one for the difference).  Lanes own distinct j, so each
+// entry sees its updates in ascending h, exactly as the sequential algorithm
+// does.  The finished row is written back, diagonal and upper part first.
+// Pivots are pipelined three deep (see PivotA); rows are claimed in index
+// order, or in forward level order once that is known.
 //
 // The batched form runs `nbatch` value sets on the same pattern in the same
 // persistent launch: tickets are handed out row-major over (row, set), so

@@ -3,18 +3,26 @@
 //
 // Forward (Eq. forwardsubA): x_i = p_i - sum_{h<i} f_ih x_h, h ascending.
 // Backward: y_i = (x_i - sum_{j>i} f_ij y_j) / f_ii, j descending (the mirror
-// image: rows last to first, each row right to left).
-// Each row's subtraction chain keeps the sequential order (one rounding per
-// product, one per difference) and is run by one thread.
+// image: rows last to first, each row right to left).  Each row's
+// subtraction chain keeps the sequential order (one rounding per product, one
+// per difference); the division uses the factor's double-double reciprocal
+// of f_ii and one Markstein correction, which gives IEEE's quotient
+// (common.cuh).
 //
-// Two schedules of the same row task:
-//  * FLAGS (multi-SM): a co-resident grid over all SMs, one thread per row;
-//    a dependency crosses SMs through L2 (relaxed GPU-scope loads and
-//    stores).  Suits wide dependency DAGs, which need the FP64 throughput of
-//    many SMs.
-//  * SINGLE_CTA: one 1024-thread block on one SM; a dependency is handed over
-//    through the SM's L1 within a couple of hundred cycles.  Suits deep,
-//    narrow DAGs, where the chain of row-to-row hand-offs sets the time.
+// Five schedules of the same row task, all bit-identical; the factor handle
+// times them (the warp-per-row ones at several CTA widths) on its first
+// application and keeps the fastest for each direction:
+//  * WARP_CLUSTER: one warp per row in one 16-CTA thread-block cluster, x in
+//    the cluster's distributed shared memory on the producer's SM; the warp
+//    subtracts the longest ready prefix of its chain as values arrive.
+//    Suits deep, narrow DAGs, where the hand-off latency sets the time.
+//  * WARP_GRID: the same over all SMs with x in global memory (L2 hand-offs);
+//    suits wide DAGs, which need many SMs in flight.
+//  * FLAGS / SINGLE_CTA / CLUSTER: 32 rows of one level per warp in lockstep
+//    (all SMs through L2, one SM, or one cluster); they pack the FP64 work
+//    of 32 rows into each instruction but couple the rows of a warp.
+// Rows are taken in level order (padded to warps for the lockstep kernels);
+// every wait is bounded.
 //
 // The transposed solve (L~U~)^-T p runs the same kernels on an explicit CSR
 // transpose T = F^T: forward with division by t_ii (U~^T), then backward with
@@ -26,8 +34,12 @@
 
 namespace iluk {
 
-// Scratch ints kept per factor handle for the factorization's ready flags.
-size_t sweep_sync_ints(int64_t n) { return 4 + 2 * (size_t)n; }
+// Scratch ints kept per factor handle: the numeric phase's row ticket (rows
+// hand their results over through the values themselves, so no flags).
+size_t sweep_sync_ints(int64_t n) {
+  (void)n;
+  return 4;
+}
 
 constexpr int kCtaThreads = 1024;
 constexpr int kGridThreads = 256;

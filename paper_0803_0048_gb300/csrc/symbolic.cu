@@ -1,16 +1,19 @@
 // symbolic.cu -- a2: symbolic ILU(k) factorization (Algorithm 1, Sec. 2.2)
 // with the level of fill of Def. 2.3, one warp per row.
 //
-// Row j's permitted set is kept sorted in the warp's slice of shared memory
-// (columns int32 + levels uint8).  Its entries below the diagonal are walked
-// in ascending order, including those inserted during the walk; for each
-// such i with level(j,i) < k the warp waits for row i to be final, then
-// merges row i's entries t > i: weight = level(j,i) + level(i,t) + 1, a
-// min-update when t is present, an insertion when weight <= k.  Entries with
-// level(j,i) >= k, or with weight > k, cannot change anything and are
-// skipped.  Finished rows go to a bump arena (the device analogue of the
-// paper's thread-private allocation arenas, Sec. 3.3) and are compacted into
-// CSR afterwards (Sec. 3.4).
+// Row j's permitted set starts as A's row (level 0).  Its entries below the
+// diagonal are walked in ascending order, including those inserted during
+// the walk; for each such i with level(j,i) < k the warp waits for row i to be
+// final, then merges row i's entries t > i: weight = level(j,i) + level(i,t)
+// + 1, a min-update when t is present, an insertion when weight <= k.
+// Entries with level(j,i) >= k, or with weight > k, cannot change anything
+// and are skipped.  For k >= 2 the row is kept as a level map over a window
+// of columns in shared memory (one byte per column plus presence and pivot
+// bitmaps); a row that leaves the window, and every row of a matrix too wide
+// for one, is kept as a sorted list with parallel insertion instead.
+// Finished rows go to a bump arena (the device analogue of the paper's
+// thread-private allocation arenas, Sec. 3.3) and announce their upper part
+// in one word; they are compacted into CSR afterwards (Sec. 3.4).
 //
 // With k <= 1 rows are independent (Sec. 3.3: only level-0 entries can cause
 // fill), so the warp reads the pivot rows straight from A and never waits.
