@@ -427,6 +427,22 @@ def batched(args):
         torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1) / args.steps
     res = B.results()
+    chosen = (B.width(), B.spin())
+    # every schedule the autotuner chooses from, one timed run each
+    sched_ms = {}
+    for sp in (False, True):
+        for w in (512, 1024):
+            B.set_schedule(w, sp)
+            B.solve()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            B.solve()
+            e1.record()
+            torch.cuda.synchronize()
+            sched_ms[f"{w}/{'spin' if sp else 'level'}"] = round(e0.elapsed_time(e1), 3)
+    B.set_schedule(*chosen)
+    B.solve()
+    res = B.results()
     # the same items, one at a time through the single-instance path
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
@@ -445,7 +461,9 @@ def batched(args):
            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic",
            "config": {"workload": f"batched_{args.nsets}x32^3_plus_{args.ngrids}_uneven_k1_gmres30",
-                      "items": len(items), "width": B.width()},
+                      "items": len(items), "width": chosen[0],
+                      "sweeps": "spin" if chosen[1] else "level"},
+           "schedules_ms": sched_ms,
            "loop_single_path_ms": round(loop_ms, 3),
            "speedup_vs_loop": round(loop_ms / ms, 2),
            "bit_mismatches_vs_single": mism,

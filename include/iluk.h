@@ -389,8 +389,16 @@ int iluk_batch_create(const iluk_batch_item *items, int64_t nitems, int restart,
                       int maxit, iluk_batch **B, void *stream);
 int iluk_batch_solve(iluk_batch *B, void *stream);
 int iluk_batch_results(iluk_batch *B, iluk_info *infos, void *stream);
-/* Threads per item chosen by the autotuner (0 until the first solve). */
+/* The first solve outside a stream capture times the whole batch at 512
+ * and 1024 threads per item, each with level-barrier sweeps (every level of
+ * the in-CTA sweeps ends at a barrier) and with spinning sweeps (each warp
+ * polls the values its rows need, no barriers), and keeps the fastest; the
+ * results do not depend on the choice.  Threads per item chosen (0 until the
+ * first solve) and whether the sweeps spin (1) or use level barriers (0). */
 int iluk_batch_width(const iluk_batch *B);
+int iluk_batch_spin(const iluk_batch *B);
+/* Fix the schedule instead (width 512 or 1024; ILUK_EINVAL otherwise). */
+int iluk_batch_set_schedule(iluk_batch *B, int width, int spin);
 void iluk_batch_destroy(iluk_batch *B);
 
 #ifdef __cplusplus

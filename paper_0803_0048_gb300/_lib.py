@@ -103,6 +103,8 @@ SIGNATURES = [
     ("iluk_batch_solve", I, [P, P]),
     ("iluk_batch_results", I, [P, P, P]),
     ("iluk_batch_width", I, [P]),
+    ("iluk_batch_spin", I, [P]),
+    ("iluk_batch_set_schedule", I, [P, I, I]),
     ("iluk_batch_destroy", None, [P]),
 ]
 

@@ -383,3 +383,11 @@ class BatchSolve:
 
     def width(self) -> int:
         return L.load().iluk_batch_width(self.h)
+
+    def spin(self) -> bool:
+        """True when the autotuned (or fixed) in-CTA sweeps spin instead of
+        ending every level at a barrier."""
+        return bool(L.load().iluk_batch_spin(self.h))
+
+    def set_schedule(self, width: int, spin: bool) -> None:
+        _call(L.load().iluk_batch_set_schedule, self.h, int(width), int(bool(spin)))

@@ -134,6 +134,102 @@ __device__ void cta_sweep(const BatchItemDev &it, const double *fv, const double
   }
 }
 
+// The same sweep without level barriers: the output starts as a pending
+// marker (a signalling-NaN pattern no arithmetic produces) and each warp,
+// taking its 32 rows from the level order, polls the values its lanes need
+// with CTA-scope loads, so a row starts as soon as its own inputs are final.
+// Each chain keeps the level form's order, so the results are identical.
+// Bounded: false when a wait runs out.
+constexpr unsigned long long kSpinPending = 0x7FF0DEADBEEFCAFEull;
+
+__device__ __forceinline__ double ld_cta_f64(const double *p) {
+  double v;
+  asm volatile("ld.relaxed.cta.global.f64 %0, [%1];" : "=d"(v) : "l"(p));
+  return v;
+}
+
+__device__ __forceinline__ void st_cta_f64(double *p, double v) {
+  asm volatile("st.relaxed.cta.global.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
+}
+
+__device__ __forceinline__ bool spin_pending(double v) {
+  return (unsigned long long)__double_as_longlong(v) == kSpinPending;
+}
+
+template <int NT, bool FORWARD>
+__device__ bool cta_sweep_spin(const BatchItemDev &it, const double *fv, const double *in,
+                               double *out, int64_t limit_ns) {
+  const int32_t *order = FORWARD ? it.lord : it.uord;
+  const int64_t len = FORWARD ? it.lstart[it.nlev_l] : it.ustart[it.nlev_u];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __shared__ int s_fail;
+  if (threadIdx.x == 0) s_fail = 0;
+  for (int64_t i = threadIdx.x; i < it.n; i += NT)
+    out[i] = __longlong_as_double((long long)kSpinPending);
+  __syncthreads();
+  bool ok = true;
+  for (int64_t s0 = (int64_t)wid * 32; s0 < len && ok; s0 += NT) {
+    const int64_t row = order[s0 + lane];
+    int64_t first = 0, d = 0;
+    int mylen = 0;
+    double s = 0.0;
+    if (row >= 0) {
+      d = it.fdiag[row];
+      if (FORWARD) {
+        first = it.frp[row];
+        mylen = (int)(d - first);
+      } else {
+        first = it.frp[row + 1] - 1;
+        mylen = (int)(first - d);
+      }
+      s = in[row];
+    }
+    const int maxlen = __reduce_max_sync(FULL_MASK, mylen);
+    const int off = maxlen - mylen;
+    for (int q = 0; q < maxlen; ++q) {
+      const int e = q - off;
+      const bool act = e >= 0;
+      int64_t pq = 0;
+      double x = 0.0;
+      if (act) {
+        pq = FORWARD ? first + e : first - e;
+        x = ld_cta_f64(&out[it.fci[pq]]);
+      }
+      bool pend = act && spin_pending(x);
+      if (__any_sync(FULL_MASK, pend)) {
+        const uint64_t t0 = globaltimer_ns();
+        for (unsigned k = 0; __any_sync(FULL_MASK, pend); ++k) {
+          if (pend) {
+            x = ld_cta_f64(&out[it.fci[pq]]);
+            pend = spin_pending(x);
+          }
+          const bool stop = (k & 31u) == 31u &&
+                            (*((volatile int *)&s_fail) ||
+                             (int64_t)(globaltimer_ns() - t0) > limit_ns);
+          if (__any_sync(FULL_MASK, stop)) {  // the whole warp gives up together
+            ok = false;
+            break;
+          }
+        }
+        if (!ok) break;
+      }
+      if (act) s = __dsub_rn(s, __dmul_rn(fv[pq], x));
+    }
+    if (!ok) {
+      if (lane == 0) atomicExch(&s_fail, 1);
+      break;
+    }
+    if (row >= 0) {
+      double y = FORWARD ? s : __ddiv_rn(s, fv[d]);
+      if ((unsigned long long)__double_as_longlong(y) == kSpinPending)
+        y = __longlong_as_double(0x7FF8000000000000ll);  // never the marker
+      st_cta_f64(&out[row], y);
+    }
+  }
+  __syncthreads();
+  return s_fail == 0;
+}
+
 // Numeric factorization, level by level over the forward level sets; one
 // warp per row, the row in the warp's shared slice, pivots ascending.
 template <int NT>
@@ -206,11 +302,15 @@ __device__ bool cta_numeric(const BatchItemDev &it, double *fv, double *svals, i
   return s_bad == 0;
 }
 
-template <int NT>
-__device__ void cta_apply(const BatchItemDev &it, const double *fv, const double *p, double *tmp,
-                          double *y) {
+template <int NT, bool SPIN>
+__device__ bool cta_apply(const BatchItemDev &it, const double *fv, const double *p, double *tmp,
+                          double *y, int64_t limit_ns) {
+  if (SPIN)
+    return cta_sweep_spin<NT, true>(it, fv, p, tmp, limit_ns) &&
+           cta_sweep_spin<NT, false>(it, fv, tmp, y, limit_ns);
   cta_sweep<NT, true>(it, fv, p, tmp);
   cta_sweep<NT, false>(it, fv, tmp, y);
+  return true;
 }
 
 template <int NT>
@@ -222,11 +322,11 @@ __device__ void cta_vec_div(int64_t n, const double *x, double den, double *y) {
 
 // --- the persistent kernel ---------------------------------------------------
 
-template <int NT>
+template <int NT, bool SPIN>
 __global__ void __launch_bounds__(NT, 1024 / NT)
 k_batch_solve(const BatchItemDev *items, int64_t nitems, BatchResultDev *results,
               BatchWork *work, unsigned long long *ticket, int m, double rtol, int maxit,
-              int cap) {
+              int cap, int64_t limit_ns) {
   constexpr int kBWarps = NT / 32;
   extern __shared__ __align__(16) unsigned char smem[];
   double *sh = reinterpret_cast<double *>(smem);                 // kDotP doubles
@@ -278,7 +378,11 @@ k_batch_solve(const BatchItemDev *items, int64_t nitems, BatchResultDev *results
       for (int j = 0; j < m; ++j) {
         double *vj = wk.V + (size_t)j * wk.ldv;
         double *zj = wk.z + (size_t)j * wk.ldv;
-        cta_apply<NT>(it, wk.fval, vj, wk.tmp, zj);
+        if (!cta_apply<NT, SPIN>(it, wk.fval, vj, wk.tmp, zj, limit_ns)) {
+          if (threadIdx.x == 0) s_stop = 3;  // a bounded wait ran out
+          __syncthreads();
+          break;
+        }
         cta_spmv<NT>(it, zj, wk.w, nullptr);
         double hval = cta_dot<NT>(n, wk.w, nullptr, 0.0, false, wk.V, sh, false);
         if (threadIdx.x == 0) H[0 * m + j] = hval;
@@ -321,6 +425,7 @@ k_batch_solve(const BatchItemDev *items, int64_t nitems, BatchResultDev *results
         if (s_stop == 1) break;
       }
       if (s_stop == 2) { status = ILUK_EINVAL; break; }
+      if (s_stop == 3) { status = ILUK_ETIMEOUT; break; }
       if (threadIdx.x == 0) {
         for (int i = jend; i >= 0; --i) {
           double sacc = gv[i];
@@ -357,28 +462,32 @@ int batch_max_restart() { return kBMaxRestart; }
 template <int NT>
 static cudaError_t launch_bs(const void *items, int64_t nitems, void *results, void *work,
                              int64_t nwork, unsigned long long *ticket, int m, double rtol,
-                             int maxit, int cap, cudaStream_t s) {
+                             int maxit, int cap, bool spin, cudaStream_t s) {
   const size_t smem = batch_smem_bytes(NT, cap);
-  cudaError_t e = cudaFuncSetAttribute(k_batch_solve<NT>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  auto kern = spin ? k_batch_solve<NT, true> : k_batch_solve<NT, false>;
+  cudaError_t e =
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_batch_solve<NT><<<(unsigned)nwork, NT, smem, s>>>(
-      (const BatchItemDev *)items, nitems, (BatchResultDev *)results, (BatchWork *)work, ticket, m,
-      rtol, maxit, cap);
+  kern<<<(unsigned)nwork, NT, smem, s>>>((const BatchItemDev *)items, nitems,
+                                         (BatchResultDev *)results, (BatchWork *)work, ticket, m,
+                                         rtol, maxit, cap, wait_limit());
   note_launch();
   return cudaGetLastError();
 }
 
 // nt = threads per instance (512 or 1024); nwork CTAs (<= the work slots).
-cudaError_t launch_batch_solve(int nt, const void *items, int64_t nitems, void *results,
-                               void *work, int64_t nwork, unsigned long long *ticket, int m,
-                               double rtol, int maxit, int cap, cudaStream_t s) {
+cudaError_t launch_batch_solve(int nt, bool spin, const void *items, int64_t nitems,
+                               void *results, void *work, int64_t nwork,
+                               unsigned long long *ticket, int m, double rtol, int maxit, int cap,
+                               cudaStream_t s) {
   ProfScope prof_scope(ILUK_PROF_BATCH, s);
   cudaError_t e = cudaMemsetAsync(ticket, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
   if (nt == 512)
-    return launch_bs<512>(items, nitems, results, work, nwork, ticket, m, rtol, maxit, cap, s);
-  return launch_bs<1024>(items, nitems, results, work, nwork, ticket, m, rtol, maxit, cap, s);
+    return launch_bs<512>(items, nitems, results, work, nwork, ticket, m, rtol, maxit, cap, spin,
+                          s);
+  return launch_bs<1024>(items, nitems, results, work, nwork, ticket, m, rtol, maxit, cap, spin,
+                         s);
 }
 
 size_t batch_item_bytes() { return sizeof(BatchItemDev); }

@@ -848,6 +848,7 @@ int iluk_numeric_batched(const iluk_sym *S, int64_t nbatch, const double *A_vals
 struct iluk_batch {
   int64_t nitems = 0;
   int restart = 30, maxit = 10000, cap = 32, width = 0;
+  bool spin = false;  // in-CTA sweeps polling values instead of level barriers
   double rtol = 1e-8;
   int64_t nwork = 0;  // work slots (CTAs of the widest grid)
   void *items = nullptr, *results = nullptr, *work = nullptr;
@@ -940,10 +941,10 @@ int iluk_batch_create(const iluk_batch_item *items, int64_t nitems, int restart,
   return ILUK_OK;
 }
 
-static cudaError_t batch_launch(iluk_batch *B, int width, cudaStream_t s) {
+static cudaError_t batch_launch(iluk_batch *B, int width, bool spin, cudaStream_t s) {
   const int64_t grid = (width == 512 ? 2 : 1) * (int64_t)num_sms();
-  return launch_batch_solve(width, B->items, B->nitems, B->results, B->work, grid, B->ticket,
-                            B->restart, B->rtol, B->maxit, B->cap, s);
+  return launch_batch_solve(width, spin, B->items, B->nitems, B->results, B->work, grid,
+                            B->ticket, B->restart, B->rtol, B->maxit, B->cap, s);
 }
 
 int iluk_batch_solve(iluk_batch *B, void *stream) {
@@ -957,33 +958,46 @@ int iluk_batch_solve(iluk_batch *B, void *stream) {
     if (cs != cudaStreamCaptureStatusNone) {
       B->width = 1024;
     } else {
-      // Autotuner: run the whole batch at both widths, keep the faster.
+      // Autotuner: run the whole batch at both widths, with level-barrier
+      // sweeps and with spinning sweeps, and keep the fastest.
       cudaEvent_t e0, e1;
       cudaEventCreate(&e0);
       cudaEventCreate(&e1);
       float best = 1e30f;
-      for (int w : {512, 1024}) {
-        cudaEventRecord(e0, s);
-        CK(batch_launch(B, w, s));
-        cudaEventRecord(e1, s);
-        cudaEventSynchronize(e1);
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < best) {
-          best = ms;
-          B->width = w;
+      for (bool sp : {false, true})
+        for (int w : {512, 1024}) {
+          cudaEventRecord(e0, s);
+          CK(batch_launch(B, w, sp, s));
+          cudaEventRecord(e1, s);
+          cudaEventSynchronize(e1);
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, e0, e1);
+          if (ms < best) {
+            best = ms;
+            B->width = w;
+            B->spin = sp;
+          }
         }
-      }
       cudaEventDestroy(e0);
       cudaEventDestroy(e1);
-      return ILUK_OK;  // results do not depend on the width: the last run holds them
+      // results do not depend on the width or the schedule: the last run holds them
+      return ILUK_OK;
     }
   }
-  CK(batch_launch(B, B->width, s));
+  CK(batch_launch(B, B->width, B->spin, s));
   return ILUK_OK;
 }
 
 int iluk_batch_width(const iluk_batch *B) { return B ? B->width : 0; }
+
+int iluk_batch_spin(const iluk_batch *B) { return B && B->spin ? 1 : 0; }
+
+int iluk_batch_set_schedule(iluk_batch *B, int width, int spin) {
+  if (!B || (width != 512 && width != 1024)) return ILUK_EINVAL;
+  B->width = width;
+  B->spin = spin != 0;
+  return ILUK_OK;
+}
 
 int iluk_batch_results(iluk_batch *B, iluk_info *infos, void *stream) {
   iluk_info *info = nullptr;

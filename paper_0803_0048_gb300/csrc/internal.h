@@ -201,8 +201,9 @@ void batch_pack_work(void *dst, double *fval, double *V, double *w, double *z, d
                      double *tmp, int64_t ldv);
 void batch_unpack_result(const void *src, int32_t *status, int32_t *iters, int32_t *cycles,
                          int64_t *row, double *relres);
-cudaError_t launch_batch_solve(int nt, const void *items, int64_t nitems, void *results,
-                               void *work, int64_t nwork, unsigned long long *ticket, int m,
-                               double rtol, int maxit, int cap, cudaStream_t s);
+cudaError_t launch_batch_solve(int nt, bool spin, const void *items, int64_t nitems,
+                               void *results, void *work, int64_t nwork,
+                               unsigned long long *ticket, int m, double rtol, int maxit, int cap,
+                               cudaStream_t s);
 
 }  // namespace iluk

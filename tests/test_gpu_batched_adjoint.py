@@ -187,3 +187,18 @@ def test_adjoint_matches_central_finite_differences():
         bm[c] -= h
         fd = (loss_of(theta0, bp) - loss_of(theta0, bm)) / (2 * h)
         assert abs(fd - gb[c]) <= 1e-5 * max(abs(fd), 1e-3 * np.abs(gb).max())
+
+
+@pytest.mark.parametrize("width", [512, 1024])
+@pytest.mark.parametrize("spin", [False, True])
+def test_batched_every_schedule_bit_exact_vs_single(width, spin):
+    items, host = build_batch()
+    B = P.BatchSolve(items, restart=30, rtol=1e-8)
+    B.set_schedule(width, spin)
+    B.solve()
+    res = B.results()
+    assert B.width() == width and B.spin() == spin
+    for (S, vals, b, x), (rp, ci), r in zip(items, host, res):
+        xs, info = single_solve(S, rp, ci, vals, b, 30, 1e-8)
+        assert r.status == info.status == 0 and r.iters == info.iters
+        assert_bits_equal(x, xs, "batched x")
