@@ -9,14 +9,33 @@
 // fixed order for the same reason).
 //
 // The modified Gram-Schmidt step w <- w - h_ij v_i is fused with the next
-// inner product: the thread that updates w_q is the one that owns index q in
-// the reduction, so no other thread needs the updated value first.
+// inner product: the thread that updates w_q also forms w_q * vnext_q, so no
+// other thread needs the updated value.
 #include "internal.h"
 
 namespace iluk {
 
-constexpr int kDotThreads = 256;
-constexpr int kDotBlocks = kDotP / kDotThreads;
+// A CTA owns 32 consecutive partials (128 CTAs).  The element operations
+// (products, and the Gram-Schmidt update) are independent; only the additions
+// into a partial form a chain.  FP64 issue is what limits these kernels on
+// this part: one warp instruction occupies an SM sub-partition's FP64 pipe
+// for ~66 clocks, and a dependent addition waits as long.  So warp 0 runs the
+// CTA's 32 chains (one per lane) from products staged in shared memory, alone
+// on its sub-partition, while the warps of the other three sub-partitions
+// (warp % 4 != 0) evaluate the products.
+constexpr int kRedWarps = 8;
+constexpr int kRedThreads = kRedWarps * 32;
+constexpr int kRedBlocks = kDotP / 32;
+constexpr int kRowsPerWarp = 8;                          // rows m per compute warp per chunk
+constexpr int kComputeWarps = kRedWarps * 3 / 4;
+constexpr int kChunk = kComputeWarps * kRowsPerWarp;     // rows m per chunk
+static_assert(2 * kChunk * 32 <= kDotP, "chunk buffers reuse the reduction array");
+static_assert(kDotP % kRedThreads == 0, "the finishing CTA holds kDotP / kRedThreads partials");
+
+// Index of a compute warp, or -1 for the warps of sub-partition 0.
+__device__ __forceinline__ int compute_index(int warp) {
+  return (warp & 3) ? warp - (warp >> 2) - 1 : -1;
+}
 
 // y = A x (b_minus == nullptr) or y = b - A x; each row summed left to right
 // from +0.0.  One thread per row: a row's sum is a chain of dependent FP64
@@ -45,68 +64,174 @@ cudaError_t launch_spmv(int64_t n, const int64_t *rp, const int32_t *ci, const d
   return cudaGetLastError();
 }
 
-// Last-block tree reduction of the 4096 partials.
-__device__ void dot_finish(double *partial, unsigned *counter, double *out, int take_sqrt) {
-  __shared__ double sh[kDotP];
+// Last-CTA tree reduction of the 4096 partials (sh: at least kRedThreads
+// doubles).  Thread t holds s[t + 256 k], k < 16, so the levels w = 2048..256
+// pair two values of one thread and run in registers; w = 128..32 go through
+// shared memory and w = 16..1 are shuffles of warp 0.
+__device__ void dot_finish(double *partial, unsigned *counter, double *out, int take_sqrt,
+                           double *sh) {
   __shared__ bool last;
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) last = atomicAdd(counter, 1u) == (unsigned)(gridDim.x - 1);
   __syncthreads();
   if (!last) return;
-  for (int p = threadIdx.x; p < kDotP; p += blockDim.x) sh[p] = __ldcg(&partial[p]);
+  __threadfence();
+  constexpr int K = kDotP / kRedThreads;
+  const int t = threadIdx.x;
+  double v[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) v[k] = __ldcg(&partial[t + kRedThreads * k]);
+#pragma unroll
+  for (int h = K / 2; h >= 1; h >>= 1)
+#pragma unroll
+    for (int k = 0; k < h; ++k) v[k] = __dadd_rn(v[k], v[k + h]);
+  sh[t] = v[0];
   __syncthreads();
-  for (int w = kDotP / 2; w >= 1; w >>= 1) {
-    for (int p = threadIdx.x; p < w; p += blockDim.x) sh[p] = __dadd_rn(sh[p], sh[p + w]);
+  for (int w = kRedThreads / 2; w >= 32; w >>= 1) {
+    if (t < w) sh[t] = __dadd_rn(sh[t], sh[t + w]);
     __syncthreads();
   }
-  if (threadIdx.x == 0) {
-    out[0] = take_sqrt ? __dsqrt_rn(sh[0]) : sh[0];
-    *counter = 0u;
+  if (t < 32) {
+    double x = sh[t];
+#pragma unroll
+    for (int w = 16; w >= 1; w >>= 1) {
+      const double o = __shfl_down_sync(0xffffffffu, x, w);
+      if (t < w) x = __dadd_rn(x, o);
+    }
+    if (t == 0) {
+      out[0] = take_sqrt ? __dsqrt_rn(x) : x;
+      *counter = 0u;
+    }
   }
 }
 
-__global__ void __launch_bounds__(kDotThreads)
-k_dot(int64_t n, const double *__restrict__ x, const double *__restrict__ y, double *partial,
-      unsigned *counter, double *out, int take_sqrt) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+// The CTA's 32 partials: partial p = 32 blockIdx.x + lane sums prod(i) for
+// i = p, p + 4096, ... (row m of the partial is i = p + 4096 m) left to right
+// from +0.0.  Rows are taken kChunk at a time: warps 1..7 evaluate chunk c
+// into one half of sh, with the operands of chunk c+1 already loading, while
+// warp 0 adds chunk c-1 from the other half.  Returns the partial in warp 0's
+// lanes.  Op::load fetches the operands of kRowsPerWarp rows i0, i0 + 4096,
+// ... (those < n) and Op::eval turns them into the rows' products.
+template <class Op>
+__device__ double chained_partials(int64_t n, const Op &op, double *sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t p = (int64_t)blockIdx.x * 32 + lane;
+  const int64_t rows = (n + kDotP - 1) / kDotP;
+  const int64_t lane_rows = p < n ? (n - p + kDotP - 1) / kDotP : 0;  // i = p + 4096 m < n
+  const int64_t nchunks = (rows + kChunk - 1) / kChunk;
+  const int cw = compute_index(warp);
+  const int r0 = cw * kRowsPerWarp;
+  auto first = [&](int64_t c) { return p + (c * kChunk + r0) * (int64_t)kDotP; };
+  typename Op::Regs cur, nxt;
+  if (cw >= 0 && nchunks > 0) op.load(first(0), n, cur);
   double s = 0.0;
-  for (int64_t i = p; i < n; i += kDotP) s = __dadd_rn(s, __dmul_rn(x[i], y[i]));
-  partial[p] = s;
-  dot_finish(partial, counter, out, take_sqrt);
+  for (int64_t c = 0; c <= nchunks; ++c) {
+    if (cw >= 0) {
+      if (c < nchunks) {
+        if (c + 1 < nchunks) op.load(first(c + 1), n, nxt);
+        double *buf = sh + (c & 1) * (kChunk * 32);
+        double pr[kRowsPerWarp];
+        op.eval(first(c), n, cur, pr);
+#pragma unroll
+        for (int u = 0; u < kRowsPerWarp; ++u) buf[(r0 + u) * 32 + lane] = pr[u];
+        if (c + 1 < nchunks) cur = nxt;
+      }
+    } else if (warp == 0 && c > 0) {
+      const double *buf = sh + ((c - 1) & 1) * (kChunk * 32) + lane;
+      const int64_t left = lane_rows - (c - 1) * kChunk;  // this lane's rows from the chunk on
+      if (left >= kChunk) {
+#pragma unroll 16
+        for (int r = 0; r < kChunk; ++r) s = __dadd_rn(s, buf[r * 32]);
+      } else {
+        for (int r = 0; r < (int)left; ++r) s = __dadd_rn(s, buf[r * 32]);
+      }
+    }
+    __syncthreads();
+  }
+  return s;
+}
+
+struct DotOp {
+  const double *x, *y;
+  struct Regs { double x[kRowsPerWarp], y[kRowsPerWarp]; };
+  __device__ void load(int64_t i0, int64_t n, Regs &r) const {
+#pragma unroll
+    for (int u = 0; u < kRowsPerWarp; ++u) {
+      const int64_t i = i0 + (int64_t)u * kDotP;
+      r.x[u] = i < n ? x[i] : 0.0;
+      r.y[u] = i < n ? y[i] : 0.0;
+    }
+  }
+  __device__ void eval(int64_t, int64_t, const Regs &r, double *pr) const {
+#pragma unroll
+    for (int u = 0; u < kRowsPerWarp; ++u) pr[u] = __dmul_rn(r.x[u], r.y[u]);
+  }
+};
+
+// w_i <- w_i - h v_i, product w_i * vnext_i (vnext == w: w_i * w_i of the
+// updated w).  Each w_i is read and written by the one thread that owns it.
+struct MgsOp {
+  double *w;
+  const double *vi, *vnext;
+  double h;
+  bool self;
+  struct Regs { double w[kRowsPerWarp], v[kRowsPerWarp], nx[kRowsPerWarp]; };
+  __device__ void load(int64_t i0, int64_t n, Regs &r) const {
+#pragma unroll
+    for (int u = 0; u < kRowsPerWarp; ++u) {
+      const int64_t i = i0 + (int64_t)u * kDotP;
+      r.w[u] = i < n ? w[i] : 0.0;
+      r.v[u] = i < n ? vi[i] : 0.0;
+      r.nx[u] = (i < n && !self) ? vnext[i] : 0.0;
+    }
+  }
+  __device__ void eval(int64_t i0, int64_t n, const Regs &r, double *pr) const {
+#pragma unroll
+    for (int u = 0; u < kRowsPerWarp; ++u) {
+      const int64_t i = i0 + (int64_t)u * kDotP;
+      const double wi = __dsub_rn(r.w[u], __dmul_rn(h, r.v[u]));
+      if (i < n) w[i] = wi;
+      pr[u] = __dmul_rn(wi, self ? wi : r.nx[u]);
+    }
+  }
+};
+
+__global__ void __launch_bounds__(kRedThreads)
+k_dot(int64_t n, const double *x, const double *y, double *partial, unsigned *counter,
+      double *out, int take_sqrt) {
+  __shared__ double sh[kDotP];
+  const double s = chained_partials(n, DotOp{x, y}, sh);
+  if (threadIdx.x < 32) partial[blockIdx.x * 32 + threadIdx.x] = s;
+  dot_finish(partial, counter, out, take_sqrt, sh);
+}
+
+// w <- w - h * v_i (h read from device memory), then the fixed-shape inner
+// product of the new w with vnext (vnext == w gives ||w||^2).
+__global__ void __launch_bounds__(kRedThreads)
+k_mgs_step(int64_t n, double *w, const double *vi, const double *hij, const double *vnext,
+           double *partial, unsigned *counter, double *out, int take_sqrt) {
+  __shared__ double sh[kDotP];
+  const double s =
+      chained_partials(n, MgsOp{w, vi, vnext, *hij, vnext == w}, sh);
+  if (threadIdx.x < 32) partial[blockIdx.x * 32 + threadIdx.x] = s;
+  dot_finish(partial, counter, out, take_sqrt, sh);
 }
 
 cudaError_t launch_dot(int64_t n, const double *x, const double *y, double *out, int take_sqrt,
                        const DotScratch &ds, cudaStream_t s) {
   ProfScope prof_scope(ILUK_PROF_DOT, s);
-  k_dot<<<kDotBlocks, kDotThreads, 0, s>>>(n, x, y, ds.partial, ds.counter, out, take_sqrt);
+  k_dot<<<kRedBlocks, kRedThreads, 0, s>>>(n, x, y, ds.partial, ds.counter, out, take_sqrt);
   note_launch();
   return cudaGetLastError();
-}
-
-// w <- w - h * v_i (h read from device memory), then the fixed-shape inner
-// product of the new w with vnext (vnext == w gives ||w||^2).
-__global__ void __launch_bounds__(kDotThreads)
-k_mgs_step(int64_t n, double *w, const double *__restrict__ vi, const double *hij,
-           const double *vnext, double *partial, unsigned *counter, double *out, int take_sqrt) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  const double h = *hij;
-  double s = 0.0;
-  for (int64_t i = p; i < n; i += kDotP) {
-    const double wi = __dsub_rn(w[i], __dmul_rn(h, vi[i]));
-    w[i] = wi;
-    s = __dadd_rn(s, __dmul_rn(wi, vnext[i]));
-  }
-  partial[p] = s;
-  dot_finish(partial, counter, out, take_sqrt);
 }
 
 cudaError_t launch_mgs_step(int64_t n, double *w, const double *vi, const double *hij,
                             const double *vnext, double *out, int take_sqrt,
                             const DotScratch &ds, cudaStream_t s) {
   ProfScope prof_scope(ILUK_PROF_DOT, s);
-  k_mgs_step<<<kDotBlocks, kDotThreads, 0, s>>>(n, w, vi, hij, vnext, ds.partial, ds.counter, out,
-                                                take_sqrt);
+  k_mgs_step<<<kRedBlocks, kRedThreads, 0, s>>>(n, w, vi, hij, vnext, ds.partial, ds.counter,
+                                                out, take_sqrt);
   note_launch();
   return cudaGetLastError();
 }
