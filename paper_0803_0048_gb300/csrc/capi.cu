@@ -464,7 +464,7 @@ static int numeric_into(iluk_fac *F, const double *A_val, iluk_info *info, cudaS
   // the numeric phase's row ticket lives in the handle's scratch
   CK(cudaMemsetAsync(F->sync, 0, sweep_sync_ints(S->n) * sizeof(int), s));
   CK(launch_fill_err(F->err, s));
-  // the numeric phase also publishes the reciprocals of the diagonal
+  // the numeric phase also fills the reciprocals of the diagonal (after the factorization)
   CK(launch_numeric(S, A_val, F->val, F->rdiag, reinterpret_cast<unsigned long long *>(F->sync),
                     F->err, s));
   // First factorization of this pattern: build the sweeps' level orders on a

@@ -4,10 +4,9 @@
 // Row i is scattered from A onto F's pattern in the warp's shared-memory
 // slice (fill positions +0.0).  For each h in L(i), ascending, the warp finds
 // where row h's entries j > h fall in row i (pattern only, before row h is
-// final), waits for the values of row h, forms the multiplier f_ih / f_hh
-// (IEEE's quotient: through row h's published reciprocal when it is there,
-// else by IEEE division) and applies f_ij <- f_ij - f_ih * f_hj (one rounding
-// for the product, one for the difference).  Lanes own distinct j, so each
+// final), waits for the values of row h, forms the multiplier f_ih / f_hh by
+// IEEE division and applies f_ij <- f_ij - f_ih * f_hj (one rounding for the
+// product, one for the difference).  Lanes own distinct j, so each
 // entry sees its updates in ascending h, exactly as the sequential algorithm
 // does.  The finished row is written back, diagonal and upper part first.
 // Pivots are pipelined three deep (see PivotA); rows are claimed in index
@@ -66,8 +65,8 @@ __device__ __forceinline__ bool wait_vals(const double *p, bool active, double *
 }
 
 // Pivot row h, as the warp stages it before its values are final.  Stage A
-// issues the loads of f_hh, of the published reciprocal of f_hh and of the
-// columns j of the first kPre * 32 entries j > h; stage B, one pivot later,
+// issues the loads of f_hh and of the columns j of the first kPre * 32
+// entries j > h; stage B, one pivot later,
 // turns those columns into positions in the current row (pos, -1 if absent)
 // and issues the loads of the matching f_hj; stage C, one more pivot later,
 // waits for whatever is still pending and applies the pivot.  The per-entry
@@ -81,7 +80,7 @@ struct PivotA {
   int64_t hd;
   int ulen;
   int32_t j[kPre];
-  double piv, rh, rl;
+  double piv;
 };
 
 struct PivotPre {
@@ -89,7 +88,6 @@ struct PivotPre {
   int ulen;
   int pos[kPre];
   double piv, f[kPre];
-  double rh, rl;  // the pivot row's published reciprocal of f_hh (may be pending)
 };
 
 // Where column j sits in the current row: a dense map over the row's column
@@ -111,15 +109,10 @@ struct RowIndex {
 };
 
 __device__ __forceinline__ void stage_a(PivotA &a, int64_t pinfo, const int32_t *__restrict__ fci,
-                                        const double *fv, const double *rdiag, int h, int lane) {
+                                        const double *fv, int lane) {
   a.hd = pinfo >> kUlenBits;
   a.ulen = (int)(pinfo & ((1ll << kUlenBits) - 1));
   a.piv = ld_gpu(&fv[a.hd]);
-  a.rh = a.rl = __longlong_as_double((long long)kPendingF);
-  if (rdiag) {
-    a.rh = ld_gpu(&rdiag[2 * (int64_t)h]);
-    a.rl = ld_gpu(&rdiag[2 * (int64_t)h + 1]);
-  }
 #pragma unroll
   for (int c = 0; c < kPre; ++c) {
     const int e = lane + 32 * c;
@@ -132,8 +125,6 @@ __device__ __forceinline__ void stage_b(PivotPre &pp, const PivotA &a, const Row
   pp.hd = a.hd;
   pp.ulen = a.ulen;
   pp.piv = a.piv;
-  pp.rh = a.rh;
-  pp.rl = a.rl;
   int lo = q + 1;  // a lane's columns increase with c: each search starts where the last ended
 #pragma unroll
   for (int c = 0; c < kPre; ++c) {
@@ -153,13 +144,8 @@ __device__ __forceinline__ void stage_b(PivotPre &pp, const PivotA &a, const Row
 // Re-issue the loads of the values of a staged pivot that are still pending.
 // The loads are independent, so they travel together: one round trip
 // refreshes the whole pivot.
-__device__ __forceinline__ void refresh_pivot(PivotPre &pp, const double *fv, int lane,
-                                              const double *rdiag, int h) {
+__device__ __forceinline__ void refresh_pivot(PivotPre &pp, const double *fv, int lane) {
   if (pend_f(pp.piv)) pp.piv = ld_gpu(&fv[pp.hd]);
-  if (rdiag && (pend_f(pp.rh) || pend_f(pp.rl))) {  // optional: never waited for
-    pp.rh = ld_gpu(&rdiag[2 * (int64_t)h]);
-    pp.rl = ld_gpu(&rdiag[2 * (int64_t)h + 1]);
-  }
 #pragma unroll
   for (int c = 0; c < kPre; ++c)
     if (pp.pos[c] >= 0 && pend_f(pp.f[c])) pp.f[c] = ld_gpu(&fv[pp.hd + 1 + lane + 32 * c]);
@@ -176,13 +162,12 @@ __device__ __forceinline__ bool pivot_pending(const PivotPre &pp) {
 // polling all of them at once.  False on time-out or when a row before `row`
 // has failed.
 __device__ __forceinline__ bool wait_pivot(PivotPre &pp, const double *fv, int lane,
-                                           const double *rdiag, int h, const DevErr *err,
-                                           int64_t row, int64_t limit_ns) {
+                                           const DevErr *err, int64_t row, int64_t limit_ns) {
   if (!__any_sync(FULL_MASK, pivot_pending(pp))) return true;
   const uint64_t t0 = globaltimer_ns();
   unsigned backoff = 16;
   for (unsigned it = 0;; ++it) {
-    refresh_pivot(pp, fv, lane, rdiag, h);
+    refresh_pivot(pp, fv, lane);
     if (!__any_sync(FULL_MASK, pivot_pending(pp))) return true;
     const bool stop = (it & 31u) == 31u &&
                       (earlier_failed(err, row) || (int64_t)(globaltimer_ns() - t0) > limit_ns);
@@ -233,7 +218,7 @@ k_numeric(int64_t n, int64_t nbatch, const int64_t *__restrict__ arp,
           const int32_t *__restrict__ a2f, const double *__restrict__ aval, int64_t astride,
           const int64_t *__restrict__ frp, const int32_t *__restrict__ fci,
           const int64_t *__restrict__ fdiag, const int64_t *__restrict__ pinfo, double *fval,
-          int64_t fstride, double *rdiag, const int32_t *__restrict__ order,
+          int64_t fstride, const int32_t *__restrict__ order,
           unsigned long long *ticket, DevErr *errs, int cap, int map_cap, int64_t limit_ns,
           int64_t hold) {
   // per warp: values, pivot infos (cap each), columns, then the column map
@@ -311,23 +296,22 @@ k_numeric(int64_t n, int64_t nbatch, const int64_t *__restrict__ arp,
     PivotA pa;
     PivotPre cur, nxt;
     if (dp > 0) {
-      stage_a(pa, spinfo[0], fci, fv, rdiag, rc[0], lane);
+      stage_a(pa, spinfo[0], fci, fv, lane);
       stage_b(cur, pa, ri, 0, fv, lane);
     }
-    if (dp > 1) stage_a(pa, spinfo[1], fci, fv, rdiag, rc[1], lane);
+    if (dp > 1) stage_a(pa, spinfo[1], fci, fv, lane);
     for (int q = 0; q < dp && ok; ++q) {
       if (q + 1 < dp) stage_b(nxt, pa, ri, q + 1, fv, lane);
-      if (q + 2 < dp) stage_a(pa, spinfo[q + 2], fci, fv, rdiag, rc[q + 2], lane);
-      if (!wait_pivot(cur, fv, lane, rdiag, rc[q], err, row, limit_ns)) {
+      if (q + 2 < dp) stage_a(pa, spinfo[q + 2], fci, fv, lane);
+      if (!wait_pivot(cur, fv, lane, err, row, limit_ns)) {
         ok = false;
         break;
       }
-      // The multiplier f_ih / f_hh: through the pivot row's reciprocal when
-      // it has been published (four FP64 operations), else by IEEE division;
-      // both give the correctly rounded quotient.
-      const bool have_r = __all_sync(FULL_MASK, !pend_f(cur.rh) && !pend_f(cur.rl));
-      const double fih = have_r ? div_rn_recip(rv[q], cur.piv, make_double2(cur.rh, cur.rl))
-                                : __ddiv_rn(rv[q], cur.piv);
+      // The multiplier f_ih / f_hh by IEEE division.  (A reciprocal
+      // published by the pivot row, with a Markstein correction, measured
+      // slower here: it is rarely there yet for the pivot that just arrived,
+      // and its loads and polls cost more than the divisions it saves.)
+      const double fih = __ddiv_rn(rv[q], cur.piv);
       __syncwarp();
       if (lane == 0) rv[q] = fih;
       // only the chunks the pivot row has: an FP64 instruction costs its
@@ -362,17 +346,11 @@ k_numeric(int64_t n, int64_t nbatch, const int64_t *__restrict__ arp,
     }
     if (lane == 0 && rv[dp] == 0.0) set_err(err, row, ILUK_EZEROPIVOT);
     // write back the diagonal and U part first: that is what later rows wait
-    // for; then the reciprocal of the diagonal, for their multipliers and
-    // for the sweeps' divisions
+    // for
     if (row != hold) {
       for (int t = lane; t < m; t += 32) {
         const int q = t + dp < m ? t + dp : t + dp - m;
         fv[b0 + q] = svals[q];
-      }
-      if (rdiag && lane == 0) {
-        const double2 r = recip_dd(svals[dp]);
-        rdiag[2 * row] = r.x;
-        rdiag[2 * row + 1] = r.y;
       }
     }
     __syncwarp();
@@ -401,8 +379,18 @@ static int numeric_cap(const iluk_sym *S, int *warps_out, int *map_out, size_t *
   return -1;  // a row of F exceeds shared memory
 }
 
+// rdiag[i] = recip_dd(f_ii): the double-double reciprocal of each diagonal
+// entry, for the backward sweep's division.  A row that did not finish leaves
+// its diagonal pending, whose reciprocal comes out as (0, 0): no fast path.
+__global__ void k_recip_diag(int64_t n, const int64_t *__restrict__ fdiag,
+                             const double *__restrict__ fval, double2 *rdiag) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    rdiag[i] = recip_dd(fval[fdiag[i]]);
+}
+
 static cudaError_t launch_numeric_impl(const iluk_sym *S, int64_t nbatch, const double *avals,
-                                       double *fvals, double *rdiag, unsigned long long *ticket,
+                                       double *fvals, double2 *rdiag, unsigned long long *ticket,
                                        DevErr *errs, cudaStream_t s) {
   // the forward level order, once built, is a valid and better-spread order
   const int32_t *order = S->levels_built ? S->lord.corder : nullptr;
@@ -418,10 +406,6 @@ static cudaError_t launch_numeric_impl(const iluk_sym *S, int64_t nbatch, const 
     if (b < 1) b = 1;
     k_fill_pending_f<<<(unsigned)b, 256, 0, s>>>(nv, fvals);
     note_launch();
-    if (rdiag) {
-      k_fill_pending_f<<<(unsigned)b, 256, 0, s>>>(2 * S->n, rdiag);
-      note_launch();
-    }
   }
   cudaError_t e = cudaFuncSetAttribute(k_numeric, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
@@ -435,15 +419,21 @@ static cudaError_t launch_numeric_impl(const iluk_sym *S, int64_t nbatch, const 
   if (grid < 1) grid = 1;
   k_numeric<<<(unsigned)grid, warps * 32, smem, s>>>(
       S->n, nbatch, S->arowptr, S->a2f, avals, S->nnzA, S->rowptr, S->colind, S->diag, S->pinfo,
-      fvals, S->nnz, rdiag, order, ticket, errs, cap, map_cap, wait_limit(), hold_row());
+      fvals, S->nnz, order, ticket, errs, cap, map_cap, wait_limit(), hold_row());
   note_launch();
+  if (rdiag) {  // the sweeps' reciprocals of the diagonal, row-parallel
+    int64_t rb = (S->n + 255) / 256;
+    if (rb > (int64_t)num_sms() * 8) rb = (int64_t)num_sms() * 8;
+    if (rb < 1) rb = 1;
+    k_recip_diag<<<(unsigned)rb, 256, 0, s>>>(S->n, S->diag, fvals, rdiag);
+    note_launch();
+  }
   return cudaGetLastError();
 }
 
 cudaError_t launch_numeric(const iluk_sym *S, const double *aval, double *fval, double2 *rdiag,
                            unsigned long long *ticket, DevErr *err, cudaStream_t s) {
-  return launch_numeric_impl(S, 1, aval, fval, reinterpret_cast<double *>(rdiag), ticket, err,
-                             s);
+  return launch_numeric_impl(S, 1, aval, fval, rdiag, ticket, err, s);
 }
 
 cudaError_t launch_numeric_batched(const iluk_sym *S, int64_t nbatch, const double *avals,
