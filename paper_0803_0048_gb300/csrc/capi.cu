@@ -307,9 +307,24 @@ int iluk_symbolic(const iluk_pattern *A, int k, iluk_sym **out, iluk_info *info,
   size_t free_b = 0, total_b = 0;
   cudaMemGetInfo(&free_b, &total_b);
   const int64_t arena_max = (int64_t)(free_b / 2 / 5);
+  // room for the fill estimate plus what the per-warp chunks may leave unused
+  int64_t floor_cap = -1, arena_floor = 0;
+  auto floor_for_cap = [&]() {
+    if (floor_cap != cap) {
+      arena_floor = nnz * mult + 1024 + symbolic_arena_slack(n, k, cap, mapw, nnz * mult);
+      floor_cap = cap;
+    }
+    return arena_floor;
+  };
+  arena_cap = floor_for_cap();
   if (arena_cap > arena_max) arena_cap = arena_max;
 
   for (int attempt = 0;; ++attempt) {
+    if (ar.col && arena_cap < floor_for_cap() && floor_for_cap() <= arena_max) {  // cap grew
+      dfree(ar.col, s);
+      dfree(ar.lev, s);
+      arena_cap = floor_for_cap();
+    }
     if (!ar.col) {
       CKS(dalloc(&ar.col, arena_cap, s));
       CKS(dalloc(&ar.lev, arena_cap, s));

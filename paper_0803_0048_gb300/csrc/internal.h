@@ -118,6 +118,8 @@ cudaError_t launch_symbolic_rows(int64_t n, const int64_t *arp, const int32_t *a
 int symbolic_map_width(int64_t n, const int64_t *arp, const int32_t *aci, int k, cudaStream_t s);
 size_t symbolic_smem_per_warp(int cap);
 size_t symbolic_map_per_warp(int mapw);  // per-warp shared memory of the level map
+// arena entries the per-warp chunks may leave unused, for this shape
+int64_t symbolic_arena_slack(int64_t n, int k, int cap, int mapw, int64_t rows_est);
 cudaError_t launch_symbolic_compact(int64_t n, const SymArena &ar, const int64_t *frp,
                                     int32_t *fci, uint8_t *flev, int64_t *fdiag, int32_t *maxrow,
                                     cudaStream_t s);

@@ -11,9 +11,11 @@
 // of columns in shared memory (one byte per column plus presence and pivot
 // bitmaps); a row that leaves the window, and every row of a matrix too wide
 // for one, is kept as a sorted list with parallel insertion instead.
-// Finished rows go to a bump arena (the device analogue of the paper's
-// thread-private allocation arenas, Sec. 3.3) and announce their upper part
-// in one word; they are compacted into CSR afterwards (Sec. 3.4).
+// Finished rows go to an arena carved into per-warp chunks (the device
+// analogue of the paper's thread-private allocation arenas, Sec. 3.3): a warp
+// reserves its next chunk right after announcing a row, so no global atomic
+// lies between a row's last pivot and its announcement.  A row announces its
+// upper part in one word; rows are compacted into CSR afterwards (Sec. 3.4).
 //
 // With k <= 1 rows are independent (Sec. 3.3: only level-0 entries can cause
 // fill), so the warp reads the pivot rows straight from A and never waits.
@@ -137,7 +139,7 @@ k_symbolic_rows(int64_t n, const int64_t *__restrict__ arp, const int32_t *__res
                 int k, int32_t *arena_col, uint8_t *arena_lev, int64_t arena_cap,
                 unsigned long long *arena_top, int64_t *row_off, int32_t *row_len,
                 int32_t *row_ust, unsigned long long *meta, unsigned long long *ticket, DevErr *err,
-                int cap, int mapw, int64_t limit_ns) {
+                int cap, int mapw, int64_t chunk, int64_t limit_ns) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
@@ -148,6 +150,8 @@ k_symbolic_rows(int64_t n, const int64_t *__restrict__ arp, const int32_t *__res
                       : nullptr;
   uint32_t *pres = mapw ? reinterpret_cast<uint32_t *>(map + mapw) : nullptr;
   uint32_t *piv = mapw ? pres + mapw / 32 : nullptr;
+  // this warp's arena chunk [ch_off, ch_end) (warp-uniform)
+  unsigned long long ch_off = 0, ch_end = 0;
 
   for (;;) {
     unsigned long long tk = 0;
@@ -458,9 +462,15 @@ k_symbolic_rows(int64_t n, const int64_t *__restrict__ arp, const int32_t *__res
     const int ust = has_diag ? dpos + 1 : dpos;
     if (!has_diag && lane == 0) set_err(err, row, ILUK_ENODIAG);
 
-    unsigned long long off = 0;
-    if (lane == 0) off = atomicAdd(arena_top, (unsigned long long)m);
-    off = __shfl_sync(FULL_MASK, off, 0);
+    if (ch_off + (unsigned long long)m > ch_end) {  // a longer row than the chunk has left
+      unsigned long long c0 = 0;
+      const unsigned long long sz = (unsigned long long)(m > chunk ? m : chunk);
+      if (lane == 0) c0 = atomicAdd(arena_top, sz);
+      ch_off = __shfl_sync(FULL_MASK, c0, 0);
+      ch_end = ch_off + sz;
+    }
+    const unsigned long long off = ch_off;
+    ch_off += (unsigned long long)m;
     if ((int64_t)(off + m) > arena_cap) {
       if (lane == 0) set_err(err, row, ILUK_ENOMEM);
       return;
@@ -479,8 +489,65 @@ k_symbolic_rows(int64_t n, const int64_t *__restrict__ arp, const int32_t *__res
         asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(&meta[row]), "l"(mt) : "memory");
       }
     }
+    // the next chunk, now that the row is announced, if this one runs low
+    if (chunk > 0 && ch_end - ch_off < (unsigned long long)(cap / 2)) {
+      unsigned long long c0 = 0;
+      if (lane == 0) c0 = atomicAdd(arena_top, (unsigned long long)chunk);
+      ch_off = __shfl_sync(FULL_MASK, c0, 0);
+      ch_end = ch_off + (unsigned long long)chunk;
+    }
     __syncwarp();
   }
+}
+
+// Chunk size: room for two of the longest rows, so that a warp that renews
+// its chunk whenever less than half a row is left never waits on the
+// allocation with a row in hand unless that row is longer than half the
+// capacity.  Rows that never wait on other rows (k <= 1) allocate per row.
+int64_t symbolic_chunk(int k, int cap) { return k <= 1 ? 0 : 2 * (int64_t)cap; }
+
+// Warps per CTA and CTAs of the symbolic launch for this row capacity and map.
+static cudaError_t symbolic_shape(int k, int cap, int mapw, int *warps_out, size_t *smem_out,
+                                  int *blocks_per_sm_out) {
+  if (k < 2) mapw = 0;
+  const size_t per_warp = symbolic_smem_per_warp(cap) + symbolic_map_per_warp(mapw);
+  int warps = kSymThreads / 32;
+  while (warps > 1 && per_warp * warps > (size_t)max_smem_optin()) warps >>= 1;
+  const size_t smem = per_warp * warps;
+  int bps = 0;
+  cudaError_t e;
+  if (k <= 1) {
+    e = cudaFuncSetAttribute(k_symbolic_rows<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    if (e == cudaSuccess)
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_symbolic_rows<true>, warps * 32, smem);
+  } else {
+    e = cudaFuncSetAttribute(k_symbolic_rows<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    if (e == cudaSuccess)
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_symbolic_rows<false>, warps * 32,
+                                                    smem);
+  }
+  *warps_out = warps;
+  *smem_out = smem;
+  *blocks_per_sm_out = bps < 1 ? 1 : bps;
+  return e;
+}
+
+// Arena entries the chunked allocation may leave unused, beyond the rows
+// themselves: every warp's open chunk, plus what chunk changes leave behind
+// (less than cap/2 entries when a warp renews after a row, less than the row
+// when a row does not fit: at most a quarter of what the chunk held), given
+// an estimate `rows_est` of the rows' entries.
+int64_t symbolic_arena_slack(int64_t n, int k, int cap, int mapw, int64_t rows_est) {
+  if (k <= 1) return 0;
+  int warps, bps;
+  size_t smem;
+  if (symbolic_shape(k, cap, mapw, &warps, &smem, &bps) != cudaSuccess) return 0;
+  int64_t grid = (int64_t)bps * num_sms();
+  const int64_t want = (n + warps - 1) / warps;
+  if (grid > want) grid = want;
+  return grid * warps * symbolic_chunk(k, cap) + rows_est / 4;
 }
 
 cudaError_t launch_symbolic_rows(int64_t n, const int64_t *arp, const int32_t *aci, int k,
@@ -488,28 +555,13 @@ cudaError_t launch_symbolic_rows(int64_t n, const int64_t *arp, const int32_t *a
                                  cudaStream_t s) {
   ProfScope prof_scope(ILUK_PROF_SYMBOLIC, s);
   if (k < 2) mapw = 0;
-  const size_t per_warp = symbolic_smem_per_warp(cap) + symbolic_map_per_warp(mapw);
-  int warps = kSymThreads / 32;
-  while (warps > 1 && per_warp * warps > (size_t)max_smem_optin()) warps >>= 1;
-  const size_t smem = per_warp * warps;
+  int warps, blocks_per_sm;
+  size_t smem;
+  cudaError_t e = symbolic_shape(k, cap, mapw, &warps, &smem, &blocks_per_sm);
+  if (e != cudaSuccess) return e;
   const int threads = warps * 32;
   const bool indep = k <= 1;
-  cudaError_t e;
-  int blocks_per_sm = 0;
-  if (indep) {
-    e = cudaFuncSetAttribute(k_symbolic_rows<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-    if (e != cudaSuccess) return e;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_symbolic_rows<true>, threads,
-                                                  smem);
-  } else {
-    e = cudaFuncSetAttribute(k_symbolic_rows<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-    if (e != cudaSuccess) return e;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_symbolic_rows<false>,
-                                                  threads, smem);
-  }
-  if (blocks_per_sm < 1) blocks_per_sm = 1;
+  const int64_t chunk = symbolic_chunk(k, cap);
   int64_t want = (n + warps - 1) / warps;
   int64_t grid = (int64_t)blocks_per_sm * num_sms();
   if (grid > want) grid = want;
@@ -517,11 +569,11 @@ cudaError_t launch_symbolic_rows(int64_t n, const int64_t *arp, const int32_t *a
   if (indep)
     k_symbolic_rows<true><<<(unsigned)grid, threads, smem, s>>>(
         n, arp, aci, k, ar.col, ar.lev, ar.cap, ar.top, ar.row_off, ar.row_len, ar.row_ust,
-        ar.meta, ar.ticket, err, cap, mapw, wait_limit());
+        ar.meta, ar.ticket, err, cap, mapw, chunk, wait_limit());
   else
     k_symbolic_rows<false><<<(unsigned)grid, threads, smem, s>>>(
         n, arp, aci, k, ar.col, ar.lev, ar.cap, ar.top, ar.row_off, ar.row_len, ar.row_ust,
-        ar.meta, ar.ticket, err, cap, mapw, wait_limit());
+        ar.meta, ar.ticket, err, cap, mapw, chunk, wait_limit());
   note_launch();
   return cudaGetLastError();
 }
