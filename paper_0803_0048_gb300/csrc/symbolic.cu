@@ -11,11 +11,13 @@
 // of columns in shared memory (one byte per column plus presence and pivot
 // bitmaps); a row that leaves the window, and every row of a matrix too wide
 // for one, is kept as a sorted list with parallel insertion instead.
-// Finished rows go to an arena carved into per-warp chunks (the device
-// analogue of the paper's thread-private allocation arenas, Sec. 3.3): a warp
-// reserves its next chunk right after announcing a row, so no global atomic
-// lies between a row's last pivot and its announcement.  A row announces its
-// upper part in one word; rows are compacted into CSR afterwards (Sec. 3.4).
+// Rows go to an arena carved into per-warp chunks (the device analogue of the
+// paper's thread-private allocation arenas, Sec. 3.3).  A warp that claims a
+// row fixes the row's slot at once (its chunk always has room for the longest
+// row) and announces the slot; the finished row is written upper part first,
+// closed by an end marker, so a row that needs it polls those entries
+// directly, one round trip after they land.  Rows are compacted into CSR
+// afterwards (Sec. 3.4).
 //
 // With k <= 1 rows are independent (Sec. 3.3: only level-0 entries can cause
 // fill), so the warp reads the pivot rows straight from A and never waits.
@@ -29,12 +31,13 @@ constexpr int kSymThreads = 256;
 
 // Hand-off between rows without fences.  The arena is filled with pending
 // markers (column -1, level 255: levels never exceed k <= 250) before the
-// launch, and each slot is written once, so a reader simply retries while it
-// sees a marker.  A finished row announces itself with one 64-bit word:
-// (offset of its strictly upper part in the arena) << 24 | (its length),
-// kMetaPending until then.
+// launch, and each entry is written once, so a reader simply retries while it
+// sees a marker.  A claimed row announces its arena slot in one 64-bit word
+// (kMetaPending until then).  The slot holds the row's strictly upper part in
+// ascending order, then an entry with column kEndCol, then the lower part and
+// the diagonal.
 constexpr unsigned long long kMetaPending = ~0ull;
-constexpr int kMetaLenBits = 24;
+constexpr int32_t kEndCol = INT_MAX;
 
 __device__ __forceinline__ unsigned long long ld_meta(const unsigned long long *p) {
   unsigned long long v;
@@ -77,6 +80,48 @@ __device__ __forceinline__ bool wait_meta(const unsigned long long *p, unsigned 
     if (it >= 4) {
       __nanosleep(backoff);
       if (backoff < 64u) backoff <<= 1;
+    }
+  }
+}
+
+// Loads entry b0 + lane of the upper part of the row whose slot starts at
+// `slot` into (t, lt) and waits until every entry of this chunk up to the end
+// marker is visible (entries past the marker are not waited for).  Returns how
+// many entries of the chunk belong to the upper part (32 when the marker lies
+// beyond the chunk), or -1 on time-out or an earlier row's failure.
+__device__ __forceinline__ int load_upper_chunk(const int32_t *acol, const uint8_t *alev,
+                                                int64_t arena_cap, int64_t slot, int b0,
+                                                int lane, int &t, int &lt, const DevErr *err,
+                                                int64_t row, int64_t limit_ns) {
+  const int64_t a = slot + b0 + lane;
+  const bool in = a < arena_cap;  // the row ends before the arena does
+  t = kEndCol;
+  lt = 0;
+  if (in) {
+    t = ld_col(&acol[a]);
+    lt = ld_lev(&alev[a]);
+  }
+  bool pend = t < 0 || lt == 255;
+  uint64_t t0 = 0;
+  unsigned backoff = 16;
+  for (unsigned it = 0;; ++it) {
+    const unsigned endm = __ballot_sync(FULL_MASK, !pend && t == kEndCol);
+    const unsigned pm = __ballot_sync(FULL_MASK, pend);
+    const int e = endm ? __ffs(endm) - 1 : 32;  // first visible end marker
+    const unsigned before = e >= 32 ? ~0u : ((1u << e) - 1u);
+    if ((pm & before) == 0u) return e;
+    if (it == 0) t0 = globaltimer_ns();
+    const bool stop = (it & 31u) == 31u &&
+                      (earlier_failed(err, row) || (int64_t)(globaltimer_ns() - t0) > limit_ns);
+    if (__any_sync(FULL_MASK, stop)) return -1;
+    if (it >= 4) {  // a row far from finishing: poll gently
+      __nanosleep(backoff);
+      if (backoff < 64u) backoff <<= 1;
+    }
+    if (pend) {
+      t = ld_col(&acol[a]);
+      lt = ld_lev(&alev[a]);
+      pend = t < 0 || lt == 255;
     }
   }
 }
@@ -160,6 +205,20 @@ k_symbolic_rows(int64_t n, const int64_t *__restrict__ arp, const int32_t *__res
     if (row >= n) return;
     if (earlier_failed(err, row)) return;
 
+    // The row's slot: k >= 2 rows announce it now; the warp's chunk always
+    // has room for cap + 1 entries here.
+    unsigned long long slot = 0;
+    if (!INDEP && chunk > 0) {
+      if (ch_end - ch_off < (unsigned long long)cap + 1) {  // first row of the warp
+        unsigned long long c0 = 0;
+        if (lane == 0) c0 = atomicAdd(arena_top, (unsigned long long)chunk);
+        ch_off = __shfl_sync(FULL_MASK, c0, 0);
+        ch_end = ch_off + (unsigned long long)chunk;
+      }
+      slot = ch_off;
+      if (lane == 0)
+        asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(&meta[row]), "l"(slot) : "memory");
+    }
     const int64_t a0 = arp[row], a1 = arp[row + 1];
     int m = (int)(a1 - a0);
     if (a1 - a0 > cap) {
@@ -228,46 +287,23 @@ k_symbolic_rows(int64_t n, const int64_t *__restrict__ arp, const int32_t *__res
           cur = nxt;
           const int i = base + nxt;
           const int lji = map[nxt];
-          unsigned long long mt = 0;
-          if (!wait_meta(&meta[i], &mt, err, row, limit_ns)) {
+          unsigned long long islot = 0;
+          if (!wait_meta(&meta[i], &islot, err, row, limit_ns)) {
             if (lane == 0 && !earlier_failed(err, row)) set_err(err, row, ILUK_ETIMEOUT);
             ok = false;
             break;
           }
-          const int64_t uoff = (int64_t)(mt >> kMetaLenBits);
-          const int ulen = (int)(mt & ((1ull << kMetaLenBits) - 1));
           const int limit = k - 1 - lji;
-          for (int b0 = 0; b0 < ulen; b0 += 32) {
-            const int q = b0 + lane;
-            int t = 0, lt = 255;
-            if (q < ulen) {
-              t = ld_col(&arena_col[uoff + q]);
-              lt = ld_lev(&arena_lev[uoff + q]);
+          for (int b0 = 0;; b0 += 32) {
+            int t, lt;
+            const int cnt = load_upper_chunk(arena_col, arena_lev, arena_cap, (int64_t)islot, b0,
+                                             lane, t, lt, err, row, limit_ns);
+            if (cnt < 0) {
+              if (lane == 0 && !earlier_failed(err, row)) set_err(err, row, ILUK_ETIMEOUT);
+              ok = false;
+              break;
             }
-            bool pend = q < ulen && (t < 0 || lt == 255);
-            if (__any_sync(FULL_MASK, pend)) {  // entries of row i not yet visible
-              const uint64_t t0 = globaltimer_ns();
-              for (unsigned it = 0;; ++it) {
-                if (pend) {
-                  t = ld_col(&arena_col[uoff + q]);
-                  lt = ld_lev(&arena_lev[uoff + q]);
-                  pend = t < 0 || lt == 255;
-                }
-                if (!__any_sync(FULL_MASK, pend)) break;
-                const bool stop = (it & 31u) == 31u &&
-                                  (earlier_failed(err, row) ||
-                                   (int64_t)(globaltimer_ns() - t0) > limit_ns);
-                if (__any_sync(FULL_MASK, stop)) {
-                  ok = false;
-                  break;
-                }
-              }
-              if (!ok) {
-                if (lane == 0 && !earlier_failed(err, row)) set_err(err, row, ILUK_ETIMEOUT);
-                break;
-              }
-            }
-            if (q < ulen && lt <= limit) {
+            if (lane < cnt && lt <= limit) {
               const int d = t - base;
               if (d >= mapw) {
                 fits = false;
@@ -286,6 +322,7 @@ k_symbolic_rows(int64_t n, const int64_t *__restrict__ arp, const int32_t *__res
               }
             }
             __syncwarp();
+            if (cnt < 32) break;
           }
           if (!ok) break;
           if (!__all_sync(FULL_MASK, fits)) {
@@ -340,65 +377,43 @@ k_symbolic_rows(int64_t n, const int64_t *__restrict__ arp, const int32_t *__res
       if (i >= row) break;
       const int lji = lev[p];
       if (lji >= k) continue;  // weight would exceed k for every t
-      const int32_t *ucol;
-      const uint8_t *ulev = nullptr;
-      int ulen;
+      // row i's upper part: from A (k <= 1), else from row i's arena slot,
+      // a chunk of 32 at a time up to its end marker
+      const int32_t *ucol = nullptr;
+      int ulen = INT_MAX;
+      unsigned long long islot = 0;
       if (INDEP) {
         const int64_t b0 = arp[i], b1 = arp[i + 1];
         const int64_t s = lower_bound_l(aci, b0, b1, (int32_t)(i + 1));
         ucol = aci + s;
         ulen = (int)(b1 - s);
-      } else {
-        unsigned long long mt = 0;
-        if (!wait_meta(&meta[i], &mt, err, row, limit_ns)) {
-          if (lane == 0 && !earlier_failed(err, row)) set_err(err, row, ILUK_ETIMEOUT);
-          ok = false;
-          break;
-        }
-        const int64_t uoff = (int64_t)(mt >> kMetaLenBits);
-        ucol = arena_col + uoff;
-        ulev = arena_lev + uoff;
-        ulen = (int)(mt & ((1ull << kMetaLenBits) - 1));
+      } else if (!wait_meta(&meta[i], &islot, err, row, limit_ns)) {
+        if (lane == 0 && !earlier_failed(err, row)) set_err(err, row, ILUK_ETIMEOUT);
+        ok = false;
+        break;
       }
       const int limit = k - 1 - lji;  // level(i,t) must not exceed this
       for (int base = 0; base < ulen; base += 32) {
         const int q = base + lane;
         int t = INT_MAX, lt = 255;
-        if (q < ulen) {
-          if (INDEP) {
+        int cnt = 32;  // entries of this chunk in row i's upper part
+        if (INDEP) {
+          if (q < ulen) {
             t = ucol[q];
             lt = 0;
-          } else {
-            t = ld_col(&ucol[q]);
-            lt = ld_lev(&ulev[q]);
           }
-        }
-        if (!INDEP) {  // arena entries of row i not yet visible: retry them
-          bool pend = q < ulen && (t < 0 || lt == 255);
-          if (__any_sync(FULL_MASK, pend)) {
-            const uint64_t t0 = globaltimer_ns();
-            for (unsigned it = 0;; ++it) {
-              if (pend) {
-                t = ld_col(&ucol[q]);
-                lt = ld_lev(&ulev[q]);
-                pend = t < 0 || lt == 255;
-              }
-              if (!__any_sync(FULL_MASK, pend)) break;
-              const bool stop = (it & 31u) == 31u &&
-                                (earlier_failed(err, row) ||
-                                 (int64_t)(globaltimer_ns() - t0) > limit_ns);
-              if (__any_sync(FULL_MASK, stop)) {
-                ok = false;
-                break;
-              }
-            }
-            if (!ok) {
-              if (lane == 0 && !earlier_failed(err, row)) set_err(err, row, ILUK_ETIMEOUT);
-              break;
-            }
+          cnt = ulen - base < 32 ? ulen - base : 32;
+        } else {
+          cnt = load_upper_chunk(arena_col, arena_lev, arena_cap, (int64_t)islot, base, lane, t,
+                                 lt, err, row, limit_ns);
+          if (cnt < 0) {
+            if (lane == 0 && !earlier_failed(err, row)) set_err(err, row, ILUK_ETIMEOUT);
+            ok = false;
+            break;
           }
+          if (cnt < 32) ulen = base + cnt;  // the last chunk
         }
-        const bool cand = (q < ulen) && lt <= limit;
+        const bool cand = lane < cnt && lt <= limit;
         const int w = lji + lt + 1;
         int pos = 0;
         bool found = false;
@@ -462,35 +477,33 @@ k_symbolic_rows(int64_t n, const int64_t *__restrict__ arp, const int32_t *__res
     const int ust = has_diag ? dpos + 1 : dpos;
     if (!has_diag && lane == 0) set_err(err, row, ILUK_ENODIAG);
 
-    if (ch_off + (unsigned long long)m > ch_end) {  // a longer row than the chunk has left
+    // The slot: upper part, end marker, then lower part and diagonal (m + 1
+    // entries).  k <= 1 rows allocate theirs now.
+    const int mu = m - ust;
+    if (INDEP || chunk == 0) {
       unsigned long long c0 = 0;
-      const unsigned long long sz = (unsigned long long)(m > chunk ? m : chunk);
-      if (lane == 0) c0 = atomicAdd(arena_top, sz);
-      ch_off = __shfl_sync(FULL_MASK, c0, 0);
-      ch_end = ch_off + sz;
+      if (lane == 0) c0 = atomicAdd(arena_top, (unsigned long long)(m + 1));
+      slot = __shfl_sync(FULL_MASK, c0, 0);
+    } else {
+      ch_off = slot + (unsigned long long)(m + 1);
     }
-    const unsigned long long off = ch_off;
-    ch_off += (unsigned long long)m;
-    if ((int64_t)(off + m) > arena_cap) {
+    if ((int64_t)(slot + m + 1) > arena_cap) {
       if (lane == 0) set_err(err, row, ILUK_ENOMEM);
       return;
     }
-    for (int q = lane; q < m; q += 32) {
-      arena_col[off + q] = cols[q];
-      arena_lev[off + q] = lev[q];
+    for (int q = lane; q <= m; q += 32) {
+      const int src = q < mu ? ust + q : q - mu - 1;  // q == mu: the end marker
+      arena_col[slot + q] = q == mu ? kEndCol : cols[src];
+      arena_lev[slot + q] = q == mu ? (uint8_t)0 : lev[src];
     }
     if (lane == 0) {
-      row_off[row] = (int64_t)off;
+      row_off[row] = (int64_t)slot;
       row_len[row] = m;
       row_ust[row] = ust;
-      if (!INDEP) {  // readers poll the arena entries themselves: no fence needed
-        const unsigned long long mt =
-            ((unsigned long long)(off + ust) << kMetaLenBits) | (unsigned long long)(m - ust);
-        asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(&meta[row]), "l"(mt) : "memory");
-      }
     }
-    // the next chunk, now that the row is announced, if this one runs low
-    if (chunk > 0 && ch_end - ch_off < (unsigned long long)(cap / 2)) {
+    // the next chunk, now that the row is written, if this one cannot take
+    // the longest row
+    if (!INDEP && chunk > 0 && ch_end - ch_off < (unsigned long long)cap + 1) {
       unsigned long long c0 = 0;
       if (lane == 0) c0 = atomicAdd(arena_top, (unsigned long long)chunk);
       ch_off = __shfl_sync(FULL_MASK, c0, 0);
@@ -500,11 +513,11 @@ k_symbolic_rows(int64_t n, const int64_t *__restrict__ arp, const int32_t *__res
   }
 }
 
-// Chunk size: room for two of the longest rows, so that a warp that renews
-// its chunk whenever less than half a row is left never waits on the
-// allocation with a row in hand unless that row is longer than half the
-// capacity.  Rows that never wait on other rows (k <= 1) allocate per row.
-int64_t symbolic_chunk(int k, int cap) { return k <= 1 ? 0 : 2 * (int64_t)cap; }
+// Chunk size: room for four of the longest rows (with their end markers); a
+// warp renews its chunk after a row whenever the longest row would no longer
+// fit, so every claimed row has its slot at once.  Rows that never wait on
+// other rows (k <= 1) allocate per row.
+int64_t symbolic_chunk(int k, int cap) { return k <= 1 ? 0 : 4 * ((int64_t)cap + 1); }
 
 // Warps per CTA and CTAs of the symbolic launch for this row capacity and map.
 static cudaError_t symbolic_shape(int k, int cap, int mapw, int *warps_out, size_t *smem_out,
@@ -536,18 +549,18 @@ static cudaError_t symbolic_shape(int k, int cap, int mapw, int *warps_out, size
 
 // Arena entries the chunked allocation may leave unused, beyond the rows
 // themselves: every warp's open chunk, plus what chunk changes leave behind
-// (less than cap/2 entries when a warp renews after a row, less than the row
-// when a row does not fit: at most a quarter of what the chunk held), given
-// an estimate `rows_est` of the rows' entries.
+// (at most cap entries of each chunk of 4 (cap + 1): a third of what the
+// chunk held), given an estimate `rows_est` of the rows' entries.  The end
+// markers (one per row) come on top.
 int64_t symbolic_arena_slack(int64_t n, int k, int cap, int mapw, int64_t rows_est) {
-  if (k <= 1) return 0;
+  if (k <= 1) return n;  // per-row allocation: only the end markers
   int warps, bps;
   size_t smem;
   if (symbolic_shape(k, cap, mapw, &warps, &smem, &bps) != cudaSuccess) return 0;
   int64_t grid = (int64_t)bps * num_sms();
   const int64_t want = (n + warps - 1) / warps;
   if (grid > want) grid = want;
-  return grid * warps * symbolic_chunk(k, cap) + rows_est / 4;
+  return grid * warps * symbolic_chunk(k, cap) + rows_est / 3 + n;
 }
 
 cudaError_t launch_symbolic_rows(int64_t n, const int64_t *arp, const int32_t *aci, int k,
@@ -591,14 +604,17 @@ __global__ void k_symbolic_compact(int64_t n, const int32_t *__restrict__ acol,
   int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t row = w; row < n; row += nw) {
+    // the slot holds the upper part, an end marker, then the lower part and
+    // the diagonal; CSR wants lower, diagonal, upper
     const int64_t off = row_off[row], dst = frp[row];
-    const int len = row_len[row];
+    const int len = row_len[row], ust = row_ust[row], mu = len - ust;
     for (int q = lane; q < len; q += 32) {
-      fci[dst + q] = acol[off + q];
-      flev[dst + q] = alev[off + q];
+      const int64_t src = q < ust ? off + mu + 1 + q : off + (q - ust);
+      fci[dst + q] = acol[src];
+      flev[dst + q] = alev[src];
     }
     if (lane == 0) {
-      fdiag[row] = dst + row_ust[row] - 1;
+      fdiag[row] = dst + ust - 1;
       atomicMax(maxrow, len);
     }
   }
