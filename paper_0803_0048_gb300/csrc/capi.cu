@@ -638,16 +638,21 @@ static int pick_schedule(iluk_fac *F, cudaStream_t s) {
       // level orders the real applies use
       LevelOrder none;
       cudaEventRecord(e0, s);
-      launch_apply(S->n, S->rowptr, S->colind, S->diag, F->val, F->rdiag, S->lord, none, p,
-                   F->tmp, y, 0, sched, F->err, s);
+      const cudaError_t ef = launch_apply(S->n, S->rowptr, S->colind, S->diag, F->val, F->rdiag,
+                                          S->lord, none, p, F->tmp, y, 0, sched, F->err, s);
       cudaEventRecord(e1, s);
-      launch_apply(S->n, S->rowptr, S->colind, S->diag, F->val, F->rdiag, none, S->uord, p,
-                   F->tmp, y, 0, sched, F->err, s);
+      const cudaError_t eb = launch_apply(S->n, S->rowptr, S->colind, S->diag, F->val, F->rdiag,
+                                          none, S->uord, p, F->tmp, y, 0, sched, F->err, s);
       cudaEventRecord(e2, s);
       cudaEventSynchronize(e2);
       float a = 0, b = 0;
       cudaEventElapsedTime(&a, e0, e1);
       cudaEventElapsedTime(&b, e1, e2);
+      // a schedule this matrix cannot use (a launch that was refused) is not
+      // a candidate
+      if (ef != cudaSuccess) a = 1e30f;
+      if (eb != cudaSuccess) b = 1e30f;
+      if (ef != cudaSuccess || eb != cudaSuccess) cudaGetLastError();
       if (rep > 0) {
         if (a < mf) mf = a;
         if (b < mb) mb = b;
