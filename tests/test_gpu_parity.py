@@ -100,11 +100,28 @@ def test_spmv_and_dot_bit_exact():
     rp, ci, av = to_dev(A)
     x, xd = vec(5, A.n)
     assert_bits_equal(P.spmv(rp, ci, av, xd), oracle.spmv(A.n, A.rowptr, A.colind, A.val, x))
-    for n in (0, 1, 4095, 4096, 4097, 100003):
+    # the GPU reduction takes rows of 4096 in chunks of 48 rows (196,608
+    # elements): sizes below, at and across chunk boundaries, ragged tails
+    for n in (0, 1, 4095, 4096, 4097, 100003, 196608, 196609, 393216 + 4095, 600011):
         a, ad = vec(6, n)
         b, bd = vec(7, n)
         got = P.dot(ad, bd).item()
         assert bits([got])[0] == bits([oracle.dot(a, b, oracle.DOT_TREE)])[0]
+
+
+def test_gmres_bit_exact_multi_chunk():
+    # n spans three chunks of the reduction kernels (w <- w - h v fused with
+    # the next inner product, and ||w|| on the last step): a fixed budget of
+    # iterations without a preconditioner, compared bit for bit
+    A = W.random_band(420011, 5, 40, 9)
+    rp, ci, av = to_dev(A)
+    b, bd = vec(33, A.n)
+    x, info = P.gmres(rp, ci, av, bd, None, restart=8, rtol=1e-14, maxit=20, check=False)
+    st, xo, it, rel, cyc = oracle.gmres(A.n, A.rowptr, A.colind, A.val, b, oracle.PREC_NONE,
+                                        None, 8, 1e-14, maxit=20, dotmode=oracle.DOT_TREE)
+    assert info.status == st and info.iters == it == 20 and info.cycles == cyc
+    assert bits([info.relres])[0] == bits([rel])[0]
+    assert_bits_equal(x, xo, "gmres x")
 
 
 GMRES_CASES = [
