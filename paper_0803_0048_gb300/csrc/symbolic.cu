@@ -263,8 +263,12 @@ k_symbolic_rows(int64_t n, const int64_t *__restrict__ arp, const int32_t *__res
         const int jlim = (int)(row - base);  // pivots lie at offsets below the diagonal
         const int jw = (jlim + 31) >> 5;     // bitmap words holding such offsets
         int cur = -1;
+        // the slot of the pivot expected next, loaded one pivot ahead (a fill
+        // inserted in between only wastes the load)
+        int pf_i = -1;
+        unsigned long long pf_slot = kMetaPending;
         for (;;) {
-          int nxt = -1;
+          int nxt = -1, nxt2 = -1;
           const int from = cur + 1;
           for (int w0 = from >> 5; w0 < jw; w0 += 32) {
             const int wi = w0 + lane;
@@ -280,6 +284,15 @@ k_symbolic_rows(int64_t n, const int64_t *__restrict__ arp, const int32_t *__res
               const int l = __ffs(b) - 1;
               const uint32_t wb = __shfl_sync(FULL_MASK, bits, l);
               nxt = (w0 + l) * 32 + __ffs(wb) - 1;
+              // and the pivot after it, if this window shows it
+              const uint32_t wb2 = wb & (wb - 1u);
+              const unsigned b2 = b & ~((2u << l) - 1u);
+              if (wb2) {
+                nxt2 = (w0 + l) * 32 + __ffs(wb2) - 1;
+              } else if (b2) {
+                const int l2 = __ffs(b2) - 1;
+                nxt2 = (w0 + l2) * 32 + __ffs(__shfl_sync(FULL_MASK, bits, l2)) - 1;
+              }
               break;
             }
           }
@@ -288,11 +301,15 @@ k_symbolic_rows(int64_t n, const int64_t *__restrict__ arp, const int32_t *__res
           const int i = base + nxt;
           const int lji = map[nxt];
           unsigned long long islot = 0;
-          if (!wait_meta(&meta[i], &islot, err, row, limit_ns)) {
+          if (pf_i == i && __all_sync(FULL_MASK, pf_slot != kMetaPending)) {
+            islot = pf_slot;
+          } else if (!wait_meta(&meta[i], &islot, err, row, limit_ns)) {
             if (lane == 0 && !earlier_failed(err, row)) set_err(err, row, ILUK_ETIMEOUT);
             ok = false;
             break;
           }
+          pf_i = nxt2 >= 0 ? base + nxt2 : -1;
+          pf_slot = nxt2 >= 0 ? ld_meta(&meta[pf_i]) : kMetaPending;
           const int limit = k - 1 - lji;
           for (int b0 = 0;; b0 += 32) {
             int t, lt;
