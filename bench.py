@@ -5,8 +5,8 @@ Workload (default): the random banded non-symmetric system with n = 160,000
 rows, 9 off-diagonals per row inside |j - i| <= 2000, values uniform in
 [-1, 1] and diagonal 1.2 * sum |a_ij|, b = A x* for a uniform x*.  One step is
 one pass of the whole hot path on it: pattern check + symbolic ILU(2) +
-numeric ILU(2) + right-preconditioned GMRES(50) with the ILU(2) sweeps to a
-1e-8 relative residual, all in libiluk's kernels.
+numeric ILU(2) (one launch, iluk_factor) + right-preconditioned GMRES(50) with
+the ILU(2) sweeps to a 1e-8 relative residual, all in libiluk's kernels.
 
 Printed: one JSON line with ms per step (device-timed, inputs resident in
 HBM), the same measured end to end from pinned host buffers, the roofline of
@@ -144,6 +144,9 @@ def alg_bytes(n, nnzA, nnzF, nnzL):
         # double-double reciprocals of the diagonal
         "sweep_bwd": 12 * nnzU + 8 * (n + 1) + 8 * n + 24 * n + 16 * n,
         "spmv": 12 * nnzA + 8 * (n + 1) + 16 * n,
+        # symbolic and numeric in one launch: the two phases' bytes
+        "factor": (8 * (n + 1) + 4 * nnzA + 5 * nnzF)
+        + (12 * nnzA + 16 * (n + 1) + 4 * nnzF + 8 * n + 8 * nnzF),
     }
 
 
@@ -202,8 +205,9 @@ def ours(args):
     def step(rp_, ci_, av_, b_):
         st, row = P.validate(rp_, ci_)
         assert st == 0
-        S = P.symbolic(rp_, ci_, Pb.k)
-        F = P.numeric(S, av_)
+        # symbolic and numeric phases in one launch (the numeric rows start as
+        # soon as their patterns are final)
+        S, F = P.factor(rp_, ci_, av_, Pb.k)
         F.set_schedule(sched[0])
         x, info = P.gmres(rp_, ci_, av_, b_, F, restart=Pb.restart, rtol=Pb.rtol)
         return S, F, x, info
@@ -268,7 +272,7 @@ def ours(args):
     ab = alg_bytes(n, nnzA, nnzF, nnzL)
     hbm, peak_src = measured_peaks()
     kinds = {"numeric": "numeric", "symbolic": "symbolic", "sweep": "sweep",
-             "sweep_bwd": "sweep_bwd", "spmv": "spmv"}
+             "sweep_bwd": "sweep_bwd", "spmv": "spmv", "factor": "factor"}
     per_kind = {}
     for kname, (tot_ms, cnt) in prof.items():
         if cnt:
@@ -278,7 +282,7 @@ def ours(args):
     # per phase: algorithmic GB/s, fraction of the measured HBM peak, and the time
     # per level of the dependency DAG the phase walks (its critical path)
     levels_of = {"symbolic": depth[0], "numeric": depth[0], "sweep": depth[0],
-                 "sweep_bwd": depth[1]}
+                 "sweep_bwd": depth[1], "factor": depth[0]}
     for kname, rec in per_kind.items():
         if kname in kinds:
             gbps = ab[kinds[kname]] / (rec["ms_per_launch"] / 1e3) / 1e9
@@ -612,6 +616,8 @@ def suite(args):
         ph["numeric"] = med_ms(lambda: F.refactor(av), reps=5 if big else 20,
                                warm=1 if big else 5)
         ph["apply"] = med_ms(lambda: F.apply(pvec))
+        ph["factor"] = med_ms(lambda: P.factor(rp, ci, av, k), reps=5 if big else 20,
+                              warm=1 if big else 5)
         x, info = P.gmres(rp, ci, av, b, F, restart=Pb.restart, rtol=Pb.rtol)
         ph["gmres"] = med_ms(lambda: P.gmres(rp, ci, av, b, F, restart=Pb.restart, rtol=Pb.rtol),
                              reps=5, warm=1)

@@ -145,7 +145,8 @@ enum {
   ILUK_PROF_VALIDATE = 0, ILUK_PROF_SYMBOLIC = 1, ILUK_PROF_COMPACT = 2, ILUK_PROF_DEPTH = 3,
   ILUK_PROF_NUMERIC = 4, ILUK_PROF_SWEEP = 5 /* forward sweeps */, ILUK_PROF_TRANSPOSE = 6, ILUK_PROF_IILU_BUILD = 7,
   ILUK_PROF_IILU_APPLY = 8, ILUK_PROF_SPMV = 9, ILUK_PROF_DOT = 10, ILUK_PROF_VECTOR = 11,
-  ILUK_PROF_SWEEP_BWD = 12, ILUK_PROF_BATCH = 13, ILUK_PROF_OVERLAPPED = 14, ILUK_PROF_KINDS = 15
+  ILUK_PROF_SWEEP_BWD = 12, ILUK_PROF_BATCH = 13, ILUK_PROF_OVERLAPPED = 14,
+  ILUK_PROF_FACTOR = 15 /* symbolic and numeric in one launch (iluk_factor) */, ILUK_PROF_KINDS = 16
 };
 int iluk_prof_enable(int on);
 int iluk_prof_read(double *ms, int64_t *count, int nkinds);
@@ -195,6 +196,22 @@ int iluk_numeric(const iluk_sym *S, const double *A_val, iluk_fac **F, iluk_info
                  void *stream);
 /* Re-run the numeric phase into an existing handle with new values. */
 int iluk_refactor(iluk_fac *F, const double *A_val, iluk_info *info, void *stream);
+/*
+ * a2 + a3 together: iluk_symbolic(A, k) then iluk_numeric, with the numeric
+ * phase running beside the symbolic one (k >= 2: one launch in which each row
+ * is factored as soon as its pattern is final, its values kept in an arena
+ * laid out like the symbolic one until both phases end).  *S and *F receive
+ * handles equal, bit for bit, to those of the two calls, except that the
+ * level orders of the sweeps are not built: the sweeps walk rows in index
+ * order (ascending forward, descending backward; any order that puts every
+ * dependency first gives the same bits) until a later iluk_numeric or
+ * iluk_refactor on S, or iluk_sym_depth, builds them.  Falls back to the two
+ * calls for k <= 1, for rows of F longer than 512 entries, and whenever the
+ * combined launch reports an error (the two calls then report it).
+ * Synchronous; errors as iluk_symbolic and iluk_numeric.
+ */
+int iluk_factor(const iluk_pattern *A, const double *A_val, int k, iluk_sym **S, iluk_fac **F,
+                iluk_info *info, void *stream);
 /* Device pointer to the factor values (double[nnz_F], F's pattern order). */
 int iluk_fac_values(const iluk_fac *F, const double **val);
 /* Copy the factor values into a caller-owned device buffer double[nnz_F].

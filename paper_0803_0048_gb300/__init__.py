@@ -9,11 +9,11 @@ from . import _lib
 from .autograd import IlukSolve, IlukSolver
 from .api import (BatchSolve, CsrPattern, Factors, IlukError, IncompleteInverse, Symbolic, adjoint_scatter,
                   bicgstab,
-                  debug_hold_row, div_rn, dot, gmres, iiluk_build, launch_count, numeric,
+                  debug_hold_row, div_rn, dot, factor, gmres, iiluk_build, launch_count, numeric,
                   numeric_batched, prof_enable, prof_read, set_wait_limit, spmv, symbolic,
                   tpilu_solve, validate)
 
 __all__ = ["IlukSolve", "IlukSolver", "BatchSolve", "CsrPattern", "Factors", "IlukError", "IncompleteInverse", "Symbolic",
-           "adjoint_scatter", "bicgstab", "debug_hold_row", "div_rn", "dot", "gmres", "iiluk_build", "launch_count",
+           "adjoint_scatter", "bicgstab", "debug_hold_row", "div_rn", "dot", "factor", "gmres", "iiluk_build", "launch_count",
            "numeric", "numeric_batched", "prof_enable", "prof_read", "set_wait_limit", "spmv",
            "symbolic", "tpilu_solve", "validate"]

@@ -33,7 +33,7 @@ def sched_name(byte: int) -> str:
     return f"{name}/{w * 128}" if w else name
 PROF_KINDS = ["validate", "symbolic", "compact", "depth", "numeric", "sweep", "transpose",
               "iilu_build", "iilu_apply", "spmv", "dot", "vector", "sweep_bwd", "batch",
-              "overlapped"]
+              "overlapped", "factor"]
 
 
 class Pattern(C.Structure):
@@ -77,6 +77,7 @@ SIGNATURES = [
     ("iluk_sym_destroy", None, [P]),
     ("iluk_numeric", I, [P, P, PP, P, P]),
     ("iluk_refactor", I, [P, P, P, P]),
+    ("iluk_factor", I, [P, P, I, PP, PP, P, P]),
     ("iluk_fac_values", I, [P, PP]),
     ("iluk_fac_export", I, [P, P, P]),
     ("iluk_fac_status", I, [P, P, P]),

@@ -172,6 +172,21 @@ def numeric(S: Symbolic, vals: torch.Tensor) -> Factors:
     return Factors(h, S)
 
 
+def factor(rowptr: torch.Tensor, colind: torch.Tensor, vals: torch.Tensor, k: int):
+    """a2 + a3 with the numeric phase running beside the symbolic one (k >= 2);
+    the same (Symbolic, Factors) as ``symbolic`` then ``numeric``, bit for bit.
+    The sweeps walk index orders until level orders are built."""
+    A = CsrPattern(rowptr, colind)
+    _check_dev(vals)
+    assert vals.dtype == torch.float64 and vals.numel() == A.nnz
+    hs, hf = C.c_void_p(), C.c_void_p()
+    info = L.Info()
+    _call(L.load().iluk_factor, A.ref, _ptr(vals), int(k), C.byref(hs), C.byref(hf),
+          C.byref(info), C.c_void_p(_stream()), info=info, what="iluk_factor")
+    S = Symbolic(hs, A, k)
+    return S, Factors(hf, S)
+
+
 class IncompleteInverse:
     """TPIILU level-based incomplete inverses (Sec. 3.5)."""
 

@@ -246,6 +246,8 @@ void iluk_sym_destroy(iluk_sym *S) {
   dfree(S->tinfo, s);
   level_order_free(S->lord, s);
   level_order_free(S->uord, s);
+  level_order_free(S->xlord, s);
+  level_order_free(S->xuord, s);
   delete S;
 }
 
@@ -538,6 +540,168 @@ int iluk_numeric(const iluk_sym *S, const double *A_val, iluk_fac **out, iluk_in
   return ILUK_OK;
 }
 
+// iluk_symbolic + iluk_numeric with the two phases overlapped (k >= 2): one
+// cooperative launch in which some CTAs walk the symbolic rows and the others
+// factor each row as soon as its pattern is final (see k_factor_fused).  The
+// results are those of the two calls bit for bit.  The sweeps of the returned
+// factorization walk index orders until level orders are built (by a later
+// iluk_numeric/iluk_refactor on S, or iluk_sym_depth).  Falls back to the two
+// calls for k <= 1 (rows need no other rows' patterns) and whenever the fused
+// launch cannot run or reports an error (the two calls then report it).
+int iluk_factor(const iluk_pattern *A, const double *A_val, int k, iluk_sym **S_out,
+                iluk_fac **F_out, iluk_info *info, void *stream) {
+  info_init(info);
+  if (!S_out || !F_out || !A || (!A_val && A->nnz > 0)) return fail(info, ILUK_EINVAL);
+  *S_out = nullptr;
+  *F_out = nullptr;
+  if (k < 0 || k > 250) return fail(info, ILUK_EINVAL);
+  auto two_phase = [&]() -> int {
+    iluk_sym *S2 = nullptr;
+    int st2 = iluk_symbolic(A, k, &S2, info, stream);
+    if (st2 != ILUK_OK) return st2;
+    iluk_fac *F2 = nullptr;
+    st2 = iluk_numeric(S2, A_val, &F2, info, stream);
+    if (st2 != ILUK_OK) {
+      iluk_sym_destroy(S2);
+      return st2;
+    }
+    *S_out = S2;
+    *F_out = F2;
+    return ILUK_OK;
+  };
+  if (k <= 1 || A->n == 0) return two_phase();
+  int st = iluk_validate(A, info, stream);
+  if (st != ILUK_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t n = A->n, nnz = A->nnz;
+
+  SymArena ar{};
+  DevErr *err = nullptr;
+  unsigned long long *rinfo = nullptr, *nticket = nullptr;
+  double *aval_arena = nullptr;
+  int64_t *scan_tmp = nullptr;
+  int32_t *maxrow = nullptr;
+  iluk_sym *S = nullptr;
+  iluk_fac *F = nullptr;
+  auto cleanup = [&]() {
+    dfree(err, s);
+    dfree(ar.col, s);
+    dfree(ar.lev, s);
+    dfree(ar.top, s);
+    dfree(ar.row_off, s);
+    dfree(ar.row_len, s);
+    dfree(ar.row_ust, s);
+    dfree(ar.meta, s);
+    dfree(ar.ticket, s);
+    dfree(rinfo, s);
+    dfree(nticket, s);
+    dfree(aval_arena, s);
+    dfree(scan_tmp, s);
+    dfree(maxrow, s);
+  };
+  // any failure of the fused path: the two separate phases instead
+  auto fallback = [&]() -> int {
+    cudaGetLastError();
+    cleanup();
+    if (F) iluk_fac_destroy(F);
+    if (S) iluk_sym_destroy(S);
+    F = nullptr;
+    S = nullptr;
+    return two_phase();
+  };
+#define CKF(call)                              \
+  do {                                         \
+    if ((call) != cudaSuccess) return fallback(); \
+  } while (0)
+
+  const int cap = 1024;  // symbolic row capacity, as iluk_symbolic starts with
+  const int ncap = 512;  // numeric row capacity (longer rows of F: the two phases)
+  const int64_t mult = k == 2 ? 17 : 65;
+  int mapw = symbolic_map_width(n, A->rowptr, A->colind, k, s);
+  if (symbolic_map_per_warp(mapw) + 5 * 1024 > (size_t)max_smem_optin()) mapw = 0;
+  size_t free_b = 0, total_b = 0;
+  cudaMemGetInfo(&free_b, &total_b);
+  int64_t arena_cap = nnz * mult + 1024 + symbolic_arena_slack(n, k, cap, mapw, nnz * mult);
+  if (arena_cap > (int64_t)(free_b / 2 / 13)) return fallback();  // 13 bytes an entry
+
+  CKF(dalloc(&err, 1, s));
+  CKF(dalloc(&ar.row_off, n, s));
+  CKF(dalloc(&ar.row_len, n, s));
+  CKF(dalloc(&ar.row_ust, n, s));
+  CKF(dalloc(&ar.meta, n, s));
+  CKF(dalloc(&ar.ticket, 1, s));
+  CKF(dalloc(&ar.top, 1, s));
+  CKF(dalloc(&ar.col, arena_cap, s));
+  CKF(dalloc(&ar.lev, arena_cap, s));
+  CKF(dalloc(&rinfo, n, s));
+  CKF(dalloc(&nticket, 1, s));
+  CKF(dalloc(&aval_arena, arena_cap, s));
+  ar.cap = arena_cap;
+  CKF(cudaMemsetAsync(ar.meta, 0xff, n * sizeof(unsigned long long), s));
+  CKF(cudaMemsetAsync(rinfo, 0xff, n * sizeof(unsigned long long), s));
+  CKF(cudaMemsetAsync(ar.col, 0xff, arena_cap * sizeof(int32_t), s));
+  CKF(cudaMemsetAsync(ar.lev, 0xff, arena_cap, s));
+  CKF(launch_fill_pending(arena_cap, aval_arena, s));
+  CKF(cudaMemsetAsync(ar.ticket, 0, sizeof(unsigned long long), s));
+  CKF(cudaMemsetAsync(nticket, 0, sizeof(unsigned long long), s));
+  CKF(cudaMemsetAsync(ar.top, 0, sizeof(unsigned long long), s));
+  CKF(launch_fill_err(err, s));
+  CKF(launch_factor_fused(n, A->rowptr, A->colind, A_val, k, ar, aval_arena, rinfo, nticket, err,
+                          cap, mapw, ncap, s));
+  {
+    int64_t row = -1;
+    uint64_t need = 0;
+    if (read_err(err, s, &row, &need) != ILUK_OK) return fallback();
+  }
+
+  // the pattern into CSR, as iluk_symbolic does, and the values beside it
+  S = new iluk_sym();
+  S->n = n;
+  S->nnzA = nnz;
+  S->k = k;
+  CKF(dalloc(&S->rowptr, n + 1, s));
+  CKF(dalloc(&scan_tmp, scan_tmp_elems(n), s));
+  CKF(launch_scan_lengths(n, ar.row_len, S->rowptr, scan_tmp, s));
+  int64_t nnzF = 0;
+  CKF(cudaMemcpyAsync(&nnzF, S->rowptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  CKF(cudaStreamSynchronize(s));
+  S->nnz = nnzF;
+  CKF(dalloc(&S->colind, nnzF, s));
+  CKF(dalloc(&S->level, nnzF, s));
+  CKF(dalloc(&S->diag, n, s));
+  CKF(dalloc(&S->a2f, nnz, s));
+  CKF(dalloc(&S->arowptr, n + 1, s));
+  CKF(dalloc(&maxrow, 1, s));
+  CKF(cudaMemsetAsync(maxrow, 0, sizeof(int32_t), s));
+  CKF(launch_symbolic_compact(n, ar, S->rowptr, S->colind, S->level, S->diag, maxrow, s));
+  CKF(launch_a2f(n, A->rowptr, A->colind, S->rowptr, S->colind, S->a2f, s));
+  CKF(dalloc(&S->pinfo, nnzF, s));
+  CKF(launch_pivot_info(n, S->rowptr, S->colind, S->diag, S->pinfo, s));
+  CKF(cudaMemcpyAsync(S->arowptr, A->rowptr, (n + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice,
+                      s));
+  CKF(build_index_orders(n, &S->xlord, &S->xuord, s));
+  F = new iluk_fac();
+  F->S = S;
+  CKF(dalloc(&F->val, nnzF, s));
+  CKF(dalloc(&F->sync, sweep_sync_ints(n), s));
+  CKF(dalloc(&F->tmp, n, s));
+  CKF(dalloc(&F->rdiag, n, s));
+  CKF(dalloc(&F->err, 2, s));
+  CKF(launch_fill_pending(n, F->tmp, s));
+  CKF(launch_compact_values(n, ar, aval_arena, S->rowptr, F->val, s));
+  CKF(launch_recip_diag(n, S->diag, F->val, F->rdiag, s));
+  CKF(launch_fill_err(F->err, s));
+  int32_t mr = 0;
+  CKF(cudaMemcpyAsync(&mr, maxrow, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  CKF(cudaStreamSynchronize(s));
+  S->max_row = mr;
+#undef CKF
+  cleanup();
+  *S_out = S;
+  *F_out = F;
+  return fail(info, ILUK_OK);
+}
+
 int iluk_refactor(iluk_fac *F, const double *A_val, iluk_info *info, void *stream) {
   info_init(info);
   if (!F || (!A_val && F->S->nnzA > 0)) return fail(info, ILUK_EINVAL);
@@ -639,10 +803,10 @@ static int pick_schedule(iluk_fac *F, cudaStream_t s) {
       LevelOrder none;
       cudaEventRecord(e0, s);
       const cudaError_t ef = launch_apply(S->n, S->rowptr, S->colind, S->diag, F->val, F->rdiag,
-                                          S->lord, none, p, F->tmp, y, 0, sched, F->err, s);
+                                          sweep_fwd(S), none, p, F->tmp, y, 0, sched, F->err, s);
       cudaEventRecord(e1, s);
       const cudaError_t eb = launch_apply(S->n, S->rowptr, S->colind, S->diag, F->val, F->rdiag,
-                                          none, S->uord, p, F->tmp, y, 0, sched, F->err, s);
+                                          none, sweep_bwd(S), p, F->tmp, y, 0, sched, F->err, s);
       cudaEventRecord(e2, s);
       cudaEventSynchronize(e2);
       float a = 0, b = 0;
@@ -693,7 +857,8 @@ int iluk_apply_sched(iluk_fac *F, const double *p, double *y, int transpose, int
     CK(launch_apply(S->n, F->trowptr, F->tcolind, F->tdiag, F->tval, F->rdiag, F->tlord,
                     F->tuord, p, F->tmp, y, 1, sched, F->err, s));
   } else {
-    CK(launch_apply(S->n, S->rowptr, S->colind, S->diag, F->val, F->rdiag, S->lord, S->uord, p,
+    CK(launch_apply(S->n, S->rowptr, S->colind, S->diag, F->val, F->rdiag, sweep_fwd(S),
+                    sweep_bwd(S), p,
                     F->tmp, y, 0, sched, F->err, s));
   }
   return ILUK_OK;
@@ -1112,7 +1277,7 @@ int gmres_solve(const iluk_pattern *A, const double *A_val, int prec_kind, void 
         return launch_apply(n, F->trowptr, F->tcolind, F->tdiag, F->tval, F->rdiag, F->tlord,
                             F->tuord, in, F->tmp, outv, 1, sched, F->err, s);
       return launch_apply(n, F->S->rowptr, F->S->colind, F->S->diag, F->val, F->rdiag,
-                          F->S->lord, F->S->uord, in, F->tmp, outv, 0, sched, F->err, s);
+                          sweep_fwd(F->S), sweep_bwd(F->S), in, F->tmp, outv, 0, sched, F->err, s);
     }
     if (M) return launch_iiluk_apply(M->S, M->g, in, M->tmp, outv, s);
     return cudaMemcpyAsync(outv, in, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
@@ -1254,7 +1419,7 @@ int bicgstab_solve(const iluk_pattern *A, const double *A_val, int prec_kind, vo
   auto precond = [&](const double *in, double *outv) -> cudaError_t {
     if (F)
       return launch_apply(n, F->S->rowptr, F->S->colind, F->S->diag, F->val, F->rdiag,
-                          F->S->lord, F->S->uord, in, F->tmp, outv, 0, sched, F->err, s);
+                          sweep_fwd(F->S), sweep_bwd(F->S), in, F->tmp, outv, 0, sched, F->err, s);
     if (M) return launch_iiluk_apply(M->S, M->g, in, M->tmp, outv, s);
     return cudaMemcpyAsync(outv, in, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
   };

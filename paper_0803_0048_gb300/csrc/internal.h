@@ -44,7 +44,13 @@ struct iluk_sym {
   int32_t depth_lower = -1, depth_upper = -1;
   LevelOrder lord, uord;       // forward / backward sweep level orders
   bool levels_built = false;   // lord/uord are built by the first numeric phase
+  LevelOrder xlord, xuord;     // index orders (iluk_factor), for the sweeps until lord/uord exist
 };
+
+// The orders the sweeps of S walk: the level orders once built, else the
+// index orders of a factorization that skipped them.
+inline const LevelOrder &sweep_fwd(const iluk_sym *S) { return S->levels_built ? S->lord : S->xlord; }
+inline const LevelOrder &sweep_bwd(const iluk_sym *S) { return S->levels_built ? S->uord : S->xuord; }
 
 struct iluk_fac {
   const iluk_sym *S = nullptr;
@@ -120,6 +126,16 @@ size_t symbolic_smem_per_warp(int cap);
 size_t symbolic_map_per_warp(int mapw);  // per-warp shared memory of the level map
 // arena entries the per-warp chunks may leave unused, for this shape
 int64_t symbolic_arena_slack(int64_t n, int k, int cap, int mapw, int64_t rows_est);
+int64_t symbolic_chunk(int k, int cap);
+cudaError_t launch_compact_values(int64_t n, const SymArena &ar, const double *aval,
+                                  const int64_t *frp, double *fval, cudaStream_t s);
+cudaError_t launch_factor_fused(int64_t n, const int64_t *arp, const int32_t *aci,
+                                const double *aval, int k, const SymArena &ar, double *arena_val,
+                                unsigned long long *rinfo, unsigned long long *num_ticket,
+                                DevErr *err, int scap, int mapw, int ncap, cudaStream_t s);
+cudaError_t launch_recip_diag(int64_t n, const int64_t *diag, const double *fval, double2 *rdiag,
+                              cudaStream_t s);
+cudaError_t build_index_orders(int64_t n, LevelOrder *fwd, LevelOrder *bwd, cudaStream_t s);
 cudaError_t launch_symbolic_compact(int64_t n, const SymArena &ar, const int64_t *frp,
                                     int32_t *fci, uint8_t *flev, int64_t *fdiag, int32_t *maxrow,
                                     cudaStream_t s);

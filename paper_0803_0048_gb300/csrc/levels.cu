@@ -224,6 +224,31 @@ int build_levels_pair(int64_t n, const int64_t *rp, const int32_t *ci, const int
   return st;
 }
 
+// Index orders for the warp-per-row sweeps of a factorization whose level
+// orders are not built: rows ascending (forward) and descending (backward),
+// valid since every dependency lies at a smaller (forward) or larger
+// (backward) index.  Only corder/clen are set.
+__global__ void k_index_orders(int64_t n, int32_t *fwd, int32_t *bwd) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    fwd[i] = (int32_t)i;
+    bwd[i] = (int32_t)(n - 1 - i);
+  }
+}
+
+cudaError_t build_index_orders(int64_t n, LevelOrder *fwd, LevelOrder *bwd, cudaStream_t s) {
+  *fwd = LevelOrder();
+  *bwd = LevelOrder();
+  if (n == 0) return cudaSuccess;
+  cudaError_t e = cudaMallocAsync((void **)&fwd->corder, (size_t)n * sizeof(int32_t), s);
+  if (e == cudaSuccess) e = cudaMallocAsync((void **)&bwd->corder, (size_t)n * sizeof(int32_t), s);
+  if (e != cudaSuccess) return e;
+  k_index_orders<<<grid_for(n), 256, 0, s>>>(n, fwd->corder, bwd->corder);
+  note_launch();
+  fwd->clen = bwd->clen = n;
+  return cudaGetLastError();
+}
+
 }  // namespace iluk
 
 // LevelOrder is declared at global scope (internal.h), and so is this.

@@ -17,10 +17,13 @@
 // every set advances through the rows together and the sets' independent
 // rows fill the GPU while each set's dependency chain is walked.
 #include "internal.h"
+#include "symbolic_body.cuh"
 
 namespace iluk {
 
 constexpr int kNumThreads = 256;
+// Sixteenths of the fused factorization's CTAs that run the symbolic walk.
+constexpr int kFusedSymPart = 6;
 
 // Factor values double as ready flags: the output array is filled with
 // kPendingF before the launch, and a row's entries change from kPendingF to
@@ -179,6 +182,70 @@ __device__ __forceinline__ bool wait_pivot(PivotPre &pp, const double *fv, int l
   }
 }
 
+// Row i's pivots, ascending: the staged pipeline (see PivotA) applied to the
+// row in shared memory.  fci and fv hold the pivot rows' columns and values
+// at their diagonal position hd and the upper part after it (CSR, or a slot of
+// the factorization arena); spinfo[q] = hd << 24 | |U(h)| for the row's q-th
+// lower entry h.  Warp-uniform; false on time-out or an earlier row's failure.
+__device__ __forceinline__ bool apply_pivots(int dp, double *rv, const int64_t *spinfo,
+                                             const RowIndex &ri, const int32_t *__restrict__ fci,
+                                             const double *fv, const DevErr *err, int64_t row,
+                                             int64_t limit_ns, int lane) {
+  // Pivots go through the three stages (see PivotA): in iteration q the
+  // warp applies pivot q, finds the positions of pivot q+1 and issues the
+  // loads of pivot q+2, so the latencies of the later stages overlap the
+  // work and the waits of the earlier ones.
+  bool ok = true;
+  PivotA pa;
+  PivotPre cur, nxt;
+  if (dp > 0) {
+    stage_a(pa, spinfo[0], fci, fv, lane);
+    stage_b(cur, pa, ri, 0, fv, lane);
+  }
+  if (dp > 1) stage_a(pa, spinfo[1], fci, fv, lane);
+  for (int q = 0; q < dp && ok; ++q) {
+    if (q + 1 < dp) stage_b(nxt, pa, ri, q + 1, fv, lane);
+    if (q + 2 < dp) stage_a(pa, spinfo[q + 2], fci, fv, lane);
+    if (!wait_pivot(cur, fv, lane, err, row, limit_ns)) {
+      ok = false;
+      break;
+    }
+    // The multiplier f_ih / f_hh by IEEE division.  (A reciprocal
+    // published by the pivot row, with a Markstein correction, measured
+    // slower here: it is rarely there yet for the pivot that just arrived,
+    // and its loads and polls cost more than the divisions it saves.)
+    const double fih = __ddiv_rn(rv[q], cur.piv);
+    __syncwarp();
+    if (lane == 0) rv[q] = fih;
+    // only the chunks the pivot row has: an FP64 instruction costs its
+    // pipe time even with every lane predicated off
+    const int nch = (cur.ulen + 31) >> 5;
+#pragma unroll
+    for (int c = 0; c < kPre; ++c) {
+      if (c >= nch) break;
+      if (cur.pos[c] >= 0) rv[cur.pos[c]] = sub_prod(rv[cur.pos[c]], fih, cur.f[c]);
+    }
+    const int64_t u1 = cur.hd + 1 + cur.ulen;
+    for (int64_t base = cur.hd + 1 + 32 * kPre; base < u1; base += 32) {  // long rows
+      const int64_t r = base + lane;
+      int pos = -1;
+      double fhj = 0.0;
+      if (r < u1) {
+        pos = ri.find(fci[r], q + 1);
+        if (pos >= 0) fhj = ld_gpu(&fv[r]);
+      }
+      if (!wait_vals(&fv[r], pos >= 0, &fhj, err, row, limit_ns)) {
+        ok = false;
+        break;
+      }
+      if (pos >= 0) rv[pos] = sub_prod(rv[pos], fih, fhj);
+    }
+    __syncwarp();
+    cur = nxt;
+  }
+  return __all_sync(FULL_MASK, ok);
+}
+
 // Pivot facts per lower entry (i, h) of F: position of row h's diagonal and
 // the length of its strictly upper part, packed for the numeric phase.
 __global__ void k_pivot_info(int64_t n, const int64_t *__restrict__ frp,
@@ -288,59 +355,8 @@ k_numeric(int64_t n, int64_t nbatch, const int64_t *__restrict__ arp,
     }
     __syncwarp();
 
-    // Pivots go through the three stages (see PivotA): in iteration q the
-    // warp applies pivot q, finds the positions of pivot q+1 and issues the
-    // loads of pivot q+2, so the latencies of the later stages overlap the
-    // work and the waits of the earlier ones.
-    bool ok = true;
-    PivotA pa;
-    PivotPre cur, nxt;
-    if (dp > 0) {
-      stage_a(pa, spinfo[0], fci, fv, lane);
-      stage_b(cur, pa, ri, 0, fv, lane);
-    }
-    if (dp > 1) stage_a(pa, spinfo[1], fci, fv, lane);
-    for (int q = 0; q < dp && ok; ++q) {
-      if (q + 1 < dp) stage_b(nxt, pa, ri, q + 1, fv, lane);
-      if (q + 2 < dp) stage_a(pa, spinfo[q + 2], fci, fv, lane);
-      if (!wait_pivot(cur, fv, lane, err, row, limit_ns)) {
-        ok = false;
-        break;
-      }
-      // The multiplier f_ih / f_hh by IEEE division.  (A reciprocal
-      // published by the pivot row, with a Markstein correction, measured
-      // slower here: it is rarely there yet for the pivot that just arrived,
-      // and its loads and polls cost more than the divisions it saves.)
-      const double fih = __ddiv_rn(rv[q], cur.piv);
-      __syncwarp();
-      if (lane == 0) rv[q] = fih;
-      // only the chunks the pivot row has: an FP64 instruction costs its
-      // pipe time even with every lane predicated off
-      const int nch = (cur.ulen + 31) >> 5;
-#pragma unroll
-      for (int c = 0; c < kPre; ++c) {
-        if (c >= nch) break;
-        if (cur.pos[c] >= 0) rv[cur.pos[c]] = sub_prod(rv[cur.pos[c]], fih, cur.f[c]);
-      }
-      const int64_t u1 = cur.hd + 1 + cur.ulen;
-      for (int64_t base = cur.hd + 1 + 32 * kPre; base < u1; base += 32) {  // long rows
-        const int64_t r = base + lane;
-        int pos = -1;
-        double fhj = 0.0;
-        if (r < u1) {
-          pos = ri.find(fci[r], q + 1);
-          if (pos >= 0) fhj = ld_gpu(&fv[r]);
-        }
-        if (!wait_vals(&fv[r], pos >= 0, &fhj, err, row, limit_ns)) {
-          ok = false;
-          break;
-        }
-        if (pos >= 0) rv[pos] = sub_prod(rv[pos], fih, fhj);
-      }
-      __syncwarp();
-      cur = nxt;
-    }
-    if (!__all_sync(FULL_MASK, ok)) {
+    const bool ok = apply_pivots(dp, rv, spinfo, ri, fci, fv, err, row, limit_ns, lane);
+    if (!ok) {
       if (lane == 0 && !earlier_failed(err, row)) set_err(err, row, ILUK_ETIMEOUT);
       continue;
     }
@@ -355,6 +371,177 @@ k_numeric(int64_t n, int64_t nbatch, const int64_t *__restrict__ arp,
     }
     __syncwarp();
   }
+}
+
+// ---------------------------------------------------------------------------
+// Symbolic and numeric phases in one launch (k >= 2).  The CTAs below g_sym
+// run the symbolic row walk; the others factor rows as soon as the walk has
+// finished them.  A numeric row waits for its own pattern (the symbolic row
+// publishes (length << 32 | upper start) in rinfo once its slot is written)
+// and for the values of its pivot rows, which live in a value arena laid out
+// like the column arena: row h's slot holds the diagonal, the strictly upper
+// part, an end marker and the strictly lower part, so the pivot pipeline above
+// reads a pivot row at its slot exactly as it reads a CSR row at its diagonal
+// position.  Both phases only wait for rows that come earlier in their own
+// order (index order), and every CTA of the cooperative launch is resident,
+// so the numeric CTAs' waits on the symbolic ones always end.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long ld_u64_gpu(const unsigned long long *p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p));
+  return v;
+}
+
+// Warp-uniform wait until *p is no longer ~0; false on time-out or failure.
+__device__ __forceinline__ bool wait_word(const unsigned long long *p, unsigned long long *out,
+                                          const DevErr *err, int64_t row, int64_t limit_ns) {
+  unsigned long long v = ld_u64_gpu(p);
+  if (v != ~0ull) {
+    *out = v;
+    return true;
+  }
+  const uint64_t t0 = globaltimer_ns();
+  unsigned backoff = 16;
+  for (unsigned it = 0;; ++it) {
+    v = ld_u64_gpu(p);
+    if (v != ~0ull) {
+      *out = v;
+      return true;
+    }
+    const bool stop = (it & 31u) == 31u &&
+                      (earlier_failed(err, row) || (int64_t)(globaltimer_ns() - t0) > limit_ns);
+    if (stop) return false;
+    if (it >= 4) {
+      __nanosleep(backoff);
+      if (backoff < kPollSleepMax) backoff <<= 1;
+    }
+  }
+}
+
+__device__ void numeric_arena_rows(int64_t n, const int64_t *__restrict__ arp,
+                                   const int32_t *__restrict__ aci,
+                                   const double *__restrict__ aval, const int32_t *acol,
+                                   double *vals, const unsigned long long *meta,
+                                   const unsigned long long *rinfo, unsigned long long *ticket,
+                                   DevErr *err, int cap, int map_cap, int64_t limit_ns,
+                                   unsigned char *smem) {
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  const int nwarps = blockDim.x >> 5;
+  double *svals = reinterpret_cast<double *>(smem) + (size_t)wib * cap;
+  int64_t *spinfo = reinterpret_cast<int64_t *>(smem + (size_t)nwarps * cap * 8) + (size_t)wib * cap;
+  int32_t *scols =
+      reinterpret_cast<int32_t *>(smem + (size_t)nwarps * cap * 16) + (size_t)wib * cap;
+  int16_t *smap =
+      reinterpret_cast<int16_t *>(smem + (size_t)nwarps * cap * 20) + (size_t)wib * map_cap;
+  for (;;) {
+    unsigned long long tk = 0;
+    if (lane == 0) tk = atomicAdd(ticket, 1ull);
+    const int64_t row = (int64_t)__shfl_sync(FULL_MASK, tk, 0);
+    if (row >= n) return;
+    if (earlier_failed(err, row)) continue;
+    // the row's pattern, once the symbolic walk has written it
+    unsigned long long ri_w = 0;
+    bool ok = lane == 0 ? wait_word(&rinfo[row], &ri_w, err, row, limit_ns) : true;
+    ok = __shfl_sync(FULL_MASK, ok ? 1 : 0, 0) != 0;
+    ri_w = __shfl_sync(FULL_MASK, ri_w, 0);
+    if (!ok) {
+      if (lane == 0 && !earlier_failed(err, row)) set_err(err, row, ILUK_ETIMEOUT);
+      continue;
+    }
+    __threadfence();  // the row's slot entries were written before rinfo
+    const int m = (int)(ri_w >> 32), ust = (int)(ri_w & 0xffffffffu);
+    const int mu = m - ust, dp = ust - 1;
+    if (m > cap) {  // longer than this launch's numeric slice: the host redoes it apart
+      if (lane == 0) {
+        set_err(err, row, ILUK_ENOMEM);
+        atomicMax(&err->need, (unsigned long long)m);
+      }
+      continue;
+    }
+    const int64_t slot = (int64_t)ld_u64_gpu(&meta[row]);
+    // columns in CSR order: lower part, diagonal, upper part
+    for (int q = lane; q < m; q += 32) {
+      const int64_t src = q < dp ? slot + mu + 2 + q : slot + (q - dp);
+      int32_t c;
+      asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(c) : "l"(acol + src));
+      scols[q] = c;
+      svals[q] = 0.0;
+    }
+    __syncwarp();
+    // pivot facts: row h's slot (its diagonal) and upper length
+    for (int q = lane; q < dp; q += 32) {
+      const int32_t h = scols[q];
+      unsigned long long rh = 0;
+      if (!wait_word(&rinfo[h], &rh, err, row, limit_ns)) {
+        ok = false;
+      } else {
+        const int64_t sh = (int64_t)ld_u64_gpu(&meta[h]);
+        const int64_t muh = (int64_t)(rh >> 32) - (int64_t)(rh & 0xffffffffu);
+        spinfo[q] = (sh << kUlenBits) | muh;
+      }
+    }
+    if (!__all_sync(FULL_MASK, ok)) {
+      if (lane == 0 && !earlier_failed(err, row)) set_err(err, row, ILUK_ETIMEOUT);
+      continue;
+    }
+    __threadfence();  // the pivot rows' slot columns were written before their rinfo
+    // A's row onto the pattern (A's columns are a subset of the row's)
+    bool bad = false;
+    for (int64_t p = arp[row] + lane; p < arp[row + 1]; p += 32) {
+      const double a = aval[p];
+      if (!isfinite(a)) bad = true;
+      svals[lower_bound_i(scols, 0, m, aci[p])] = a;
+    }
+    if (__any_sync(FULL_MASK, bad)) {
+      if (lane == 0) set_err(err, row, ILUK_ENONFINITE);
+      continue;
+    }
+    RowIndex ri;
+    ri.rc = scols;
+    ri.map = smap;
+    ri.m = m;
+    ri.c0 = scols[0];
+    ri.span = scols[m - 1] - ri.c0 + 1;
+    ri.use_map = ri.span <= map_cap;
+    if (ri.use_map) {
+      for (int d = lane; d < ri.span; d += 32) smap[d] = -1;
+      __syncwarp();
+      for (int q = lane; q < m; q += 32) smap[scols[q] - ri.c0] = (int16_t)q;
+    }
+    __syncwarp();
+    if (!apply_pivots(dp, svals, spinfo, ri, acol, vals, err, row, limit_ns, lane)) {
+      if (lane == 0 && !earlier_failed(err, row)) set_err(err, row, ILUK_ETIMEOUT);
+      continue;
+    }
+    if (lane == 0 && svals[dp] == 0.0) set_err(err, row, ILUK_EZEROPIVOT);
+    // diagonal and upper part first (what later rows wait for), then the
+    // lower part, into the row's slot
+    for (int t = lane; t < m; t += 32) {
+      const int q = t + dp < m ? t + dp : t + dp - m;
+      const int64_t dst = q < dp ? slot + mu + 2 + q : slot + (q - dp);
+      vals[dst] = svals[q];
+    }
+    __syncwarp();
+  }
+}
+
+__global__ void __launch_bounds__(kNumThreads)
+k_factor_fused(int64_t n, const int64_t *__restrict__ arp, const int32_t *__restrict__ aci,
+               const double *__restrict__ aval, int k, int32_t *arena_col, uint8_t *arena_lev,
+               double *arena_val, int64_t arena_cap, unsigned long long *arena_top,
+               int64_t *row_off, int32_t *row_len, int32_t *row_ust, unsigned long long *meta,
+               unsigned long long *rinfo, unsigned long long *sym_ticket,
+               unsigned long long *num_ticket, DevErr *err, int scap, int mapw, int64_t chunk,
+               int ncap, int nmap, int g_sym, int64_t limit_ns) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  if ((int)blockIdx.x < g_sym)
+    symbolic_rows_body<false, true>(n, arp, aci, k, arena_col, arena_lev, arena_cap, arena_top,
+                                    row_off, row_len, row_ust, meta, sym_ticket, err, scap, mapw,
+                                    chunk, limit_ns, rinfo, smem);
+  else
+    numeric_arena_rows(n, arp, aci, aval, arena_col, arena_val, meta, rinfo, num_ticket, err,
+                       ncap, nmap, limit_ns, smem);
 }
 
 // Shared memory per warp: a row of F (value, pivot info, column: 20 bytes per
@@ -389,6 +576,17 @@ __global__ void k_recip_diag(int64_t n, const int64_t *__restrict__ fdiag,
     rdiag[i] = recip_dd(fval[fdiag[i]]);
 }
 
+cudaError_t launch_recip_diag(int64_t n, const int64_t *diag, const double *fval, double2 *rdiag,
+                              cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  int64_t rb = (n + 255) / 256;
+  if (rb > (int64_t)num_sms() * 8) rb = (int64_t)num_sms() * 8;
+  if (rb < 1) rb = 1;
+  k_recip_diag<<<(unsigned)rb, 256, 0, s>>>(n, diag, fval, rdiag);
+  note_launch();
+  return cudaGetLastError();
+}
+
 static cudaError_t launch_numeric_impl(const iluk_sym *S, int64_t nbatch, const double *avals,
                                        double *fvals, double2 *rdiag, unsigned long long *ticket,
                                        DevErr *errs, cudaStream_t s) {
@@ -421,14 +619,57 @@ static cudaError_t launch_numeric_impl(const iluk_sym *S, int64_t nbatch, const 
       S->n, nbatch, S->arowptr, S->a2f, avals, S->nnzA, S->rowptr, S->colind, S->diag, S->pinfo,
       fvals, S->nnz, order, ticket, errs, cap, map_cap, wait_limit(), hold_row());
   note_launch();
-  if (rdiag) {  // the sweeps' reciprocals of the diagonal, row-parallel
-    int64_t rb = (S->n + 255) / 256;
-    if (rb > (int64_t)num_sms() * 8) rb = (int64_t)num_sms() * 8;
-    if (rb < 1) rb = 1;
-    k_recip_diag<<<(unsigned)rb, 256, 0, s>>>(S->n, S->diag, fvals, rdiag);
-    note_launch();
-  }
+  if (rdiag) return launch_recip_diag(S->n, S->diag, fvals, rdiag, s);
   return cudaGetLastError();
+}
+
+// Symbolic (k >= 2) and numeric phases in one cooperative launch.  The symbolic
+// CTAs use the symbolic kernel's per-warp layout (scap, mapw); the numeric
+// CTAs hold rows of at most ncap entries.  Fails (cudaErrorInvalidConfiguration)
+// when the two layouts do not fit one CTA's shared memory or the grid has room
+// for fewer than two CTAs.
+cudaError_t launch_factor_fused(int64_t n, const int64_t *arp, const int32_t *aci,
+                                const double *aval, int k, const SymArena &ar, double *arena_val,
+                                unsigned long long *rinfo, unsigned long long *num_ticket,
+                                DevErr *err, int scap, int mapw, int ncap, cudaStream_t s) {
+  ProfScope prof_scope(ILUK_PROF_FACTOR, s);
+  const int warps = kNumThreads / 32;
+  const size_t sym_smem = (symbolic_smem_per_warp(scap) + symbolic_map_per_warp(mapw)) * warps;
+  int nmap = 0;
+  size_t num_smem = 0;
+  for (int map : {8192, 4096, 0}) {
+    num_smem = ((size_t)ncap * 20 + (size_t)map * 2) * warps;
+    nmap = map;
+    if (num_smem <= (size_t)max_smem_optin()) break;
+  }
+  const size_t smem = sym_smem > num_smem ? sym_smem : num_smem;
+  if (smem > (size_t)max_smem_optin()) return cudaErrorInvalidConfiguration;
+  cudaError_t e = cudaFuncSetAttribute(k_factor_fused, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  int bps = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_factor_fused, kNumThreads, smem);
+  if (bps < 1) return cudaErrorInvalidConfiguration;
+  int grid = bps * num_sms();
+  if (grid < 2) return cudaErrorInvalidConfiguration;
+  // the symbolic walk runs ahead of the numeric one with far fewer warps
+  int g_sym = (int)((int64_t)grid * kFusedSymPart / 16);
+  if (g_sym < 1) g_sym = 1;
+  if (g_sym > grid - 1) g_sym = grid - 1;
+  const int64_t chunk = symbolic_chunk(k, scap);
+  int64_t limit = wait_limit();
+  int kk = k, sc = scap, mw = mapw, nc = ncap, nm = nmap, gs = g_sym;
+  int64_t nn = n, acap = ar.cap, ch = chunk;
+  void *args[] = {(void *)&nn, (void *)&arp, (void *)&aci, (void *)&aval, (void *)&kk,
+                  (void *)&ar.col, (void *)&ar.lev, (void *)&arena_val, (void *)&acap,
+                  (void *)&ar.top, (void *)&ar.row_off, (void *)&ar.row_len, (void *)&ar.row_ust,
+                  (void *)&ar.meta, (void *)&rinfo, (void *)&ar.ticket, (void *)&num_ticket,
+                  (void *)&err, (void *)&sc, (void *)&mw, (void *)&ch, (void *)&nc, (void *)&nm,
+                  (void *)&gs, (void *)&limit};
+  e = cudaLaunchCooperativeKernel((const void *)k_factor_fused, dim3((unsigned)grid),
+                                  dim3(kNumThreads), args, smem, s);
+  note_launch();
+  return e;
 }
 
 cudaError_t launch_numeric(const iluk_sym *S, const double *aval, double *fval, double2 *rdiag,

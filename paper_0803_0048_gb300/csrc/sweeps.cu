@@ -689,7 +689,14 @@ static cudaError_t run_sweep(int64_t n, const LevelOrder &lo, const int64_t *rp,
                              const double *in, double *out, double *clear, int sched, DevErr *err,
                              cudaStream_t s) {
   ProfScope prof_scope(FORWARD ? ILUK_PROF_SWEEP : ILUK_PROF_SWEEP_BWD, s);
-  if (lo.len == 0) return cudaSuccess;
+  // an empty order: nothing to sweep (n = 0, or a direction the caller skips)
+  if (n == 0 || (!lo.order && !lo.corder)) return cudaSuccess;
+  // the lockstep kinds walk the padded level order; an index order (a
+  // factorization that has not built its level orders) has only the plain one
+  const int kind0 = sched & 0xf;
+  const bool padded = kind0 != ILUK_SCHED_WARP_GRID && kind0 != ILUK_SCHED_WARP_CLUSTER;
+  if (padded && !lo.order) return cudaErrorInvalidValue;
+  if (!padded && !lo.corder) return cudaErrorInvalidValue;
   int64_t limit = wait_limit();
   const int32_t *order = lo.order;
   int64_t len = lo.len;
