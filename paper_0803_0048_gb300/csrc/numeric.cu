@@ -22,8 +22,13 @@
 namespace iluk {
 
 constexpr int kNumThreads = 256;
-// Sixteenths of the fused factorization's CTAs that run the symbolic walk.
-constexpr int kFusedSymPart = 6;
+// Sixteenths of the fused factorization's CTAs that run the symbolic walk:
+// few with the level-map walk, which keeps ahead of the numeric rows easily;
+// more with the sorted-list walk of wide matrices, which is slower per row.
+// (At the headline band size 3-10/16 time alike; the 3D 64^3 grid: 58 ms at
+// 3/16, 23 ms at 8/16, 37 ms at 12/16.)
+constexpr int kFusedSymPartMap = 4;
+constexpr int kFusedSymPartList = 8;
 
 // Factor values double as ready flags: the output array is filled with
 // kPendingF before the launch, and a row's entries change from kPendingF to
@@ -653,7 +658,7 @@ cudaError_t launch_factor_fused(int64_t n, const int64_t *arp, const int32_t *ac
   int grid = bps * num_sms();
   if (grid < 2) return cudaErrorInvalidConfiguration;
   // the symbolic walk runs ahead of the numeric one with far fewer warps
-  int g_sym = (int)((int64_t)grid * kFusedSymPart / 16);
+  int g_sym = (int)((int64_t)grid * (mapw ? kFusedSymPartMap : kFusedSymPartList) / 16);
   if (g_sym < 1) g_sym = 1;
   if (g_sym > grid - 1) g_sym = grid - 1;
   const int64_t chunk = symbolic_chunk(k, scap);
