@@ -205,9 +205,12 @@ int iluk_refactor(iluk_fac *F, const double *A_val, iluk_info *info, void *strea
  * level orders of the sweeps are not built: the sweeps walk rows in index
  * order (ascending forward, descending backward; any order that puts every
  * dependency first gives the same bits) until a later iluk_numeric or
- * iluk_refactor on S, or iluk_sym_depth, builds them.  Falls back to the two
- * calls for k <= 1, for rows of F longer than 512 entries, and whenever the
- * combined launch reports an error (the two calls then report it).
+ * iluk_refactor on S, or iluk_sym_depth, builds them (on wide DAGs, such as 3D
+ * grids, level orders give much faster sweeps: call iluk_sym_depth first, or
+ * the two calls).  For k <= 1 the two phases run one after the other (rows
+ * need no other rows' patterns), also without level orders.  Falls back to the
+ * two calls for rows of F longer than 512 entries and whenever the combined
+ * launch reports an error (the two calls then report it).
  * Synchronous; errors as iluk_symbolic and iluk_numeric.
  */
 int iluk_factor(const iluk_pattern *A, const double *A_val, int k, iluk_sym **S, iluk_fac **F,

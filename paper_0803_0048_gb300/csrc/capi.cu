@@ -476,7 +476,8 @@ void iluk_fac_destroy(iluk_fac *F) {
   delete F;
 }
 
-static int numeric_into(iluk_fac *F, const double *A_val, iluk_info *info, cudaStream_t s) {
+static int numeric_into(iluk_fac *F, const double *A_val, iluk_info *info, cudaStream_t s,
+                        bool build_levels = true) {
   const iluk_sym *S = F->S;
   // the numeric phase's row ticket lives in the handle's scratch
   CK(cudaMemsetAsync(F->sync, 0, sweep_sync_ints(S->n) * sizeof(int), s));
@@ -488,7 +489,7 @@ static int numeric_into(iluk_fac *F, const double *A_val, iluk_info *info, cudaS
   // second stream meanwhile (they read only the pattern; the numeric kernel
   // leaves room on every SM for the two level-building CTAs).
   int lst = ILUK_OK;
-  if (!S->levels_built) {
+  if (build_levels && !S->levels_built) {
     cudaStream_t side = nullptr;
     if (cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking) == cudaSuccess) {
       prof_override = ILUK_PROF_OVERLAPPED;
@@ -569,7 +570,38 @@ int iluk_factor(const iluk_pattern *A, const double *A_val, int k, iluk_sym **S_
     *F_out = F2;
     return ILUK_OK;
   };
-  if (k <= 1 || A->n == 0) return two_phase();
+  // k <= 1: rows need no other rows' patterns, so the two phases simply run
+  // one after the other, without the level orders (index orders instead)
+  auto serial = [&]() -> int {
+    cudaStream_t s2 = (cudaStream_t)stream;
+    iluk_sym *S2 = nullptr;
+    int st2 = iluk_symbolic(A, k, &S2, info, stream);
+    if (st2 != ILUK_OK) return st2;
+    iluk_fac *F2 = new iluk_fac();
+    F2->S = S2;
+    cudaError_t e2 = build_index_orders(S2->n, &S2->xlord, &S2->xuord, s2);
+    if (e2 == cudaSuccess) e2 = dalloc(&F2->val, S2->nnz, s2);
+    if (e2 == cudaSuccess) e2 = dalloc(&F2->sync, sweep_sync_ints(S2->n), s2);
+    if (e2 == cudaSuccess) e2 = dalloc(&F2->tmp, S2->n, s2);
+    if (e2 == cudaSuccess) e2 = dalloc(&F2->rdiag, S2->n, s2);
+    if (e2 == cudaSuccess) e2 = dalloc(&F2->err, 2, s2);
+    if (e2 == cudaSuccess) e2 = launch_fill_pending(S2->n, F2->tmp, s2);
+    if (e2 != cudaSuccess) {
+      iluk_fac_destroy(F2);
+      iluk_sym_destroy(S2);
+      return fail(info, e2 == cudaErrorMemoryAllocation ? ILUK_ENOMEM : ILUK_ECUDA);
+    }
+    st2 = numeric_into(F2, A_val, info, s2, false);
+    if (st2 != ILUK_OK) {
+      iluk_fac_destroy(F2);
+      iluk_sym_destroy(S2);
+      return st2;
+    }
+    *S_out = S2;
+    *F_out = F2;
+    return ILUK_OK;
+  };
+  if (k <= 1 || A->n == 0) return serial();
   int st = iluk_validate(A, info, stream);
   if (st != ILUK_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
