@@ -81,3 +81,16 @@ def test_factor_errors_as_the_two_calls():
     with pytest.raises(P.IlukError) as e:
         P.factor(rp, ci, av, 2)
     assert e.value.status == L.EZEROPIVOT and e.value.row == 2
+
+
+def test_factor_rows_longer_than_the_numeric_slice():
+    # full fill: every row of F holds 600 entries, more than the combined
+    # launch's numeric rows take, so the two separate calls run instead
+    A = W.random_sparse(600, 0.02, 21)
+    rp, ci, av = to_dev(A)
+    S, F = P.factor(rp, ci, av, 250)
+    assert S.max_row > 512
+    ref = oracle.factor(A, 250)
+    grp, gci, _, _ = [t.cpu().numpy() for t in S.pattern()]
+    assert np.array_equal(grp, ref["rowptr"]) and np.array_equal(gci, ref["colind"])
+    assert_bits_equal(F.values(), ref["val"], "factor values")
