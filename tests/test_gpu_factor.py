@@ -94,3 +94,19 @@ def test_factor_rows_longer_than_the_numeric_slice():
     grp, gci, _, _ = [t.cpu().numpy() for t in S.pattern()]
     assert np.array_equal(grp, ref["rowptr"]) and np.array_equal(gci, ref["colind"])
     assert_bits_equal(F.values(), ref["val"], "factor values")
+
+
+def test_factor_sorted_list_walk():
+    # a 3D grid too wide for the symbolic level map (row span 2 * 48^2): the
+    # symbolic rows of the combined launch take the sorted-list walk
+    A = W.conv_diff(48, 3, (50.0, 50.0, 50.0))
+    rp, ci, av = to_dev(A)
+    S, F = P.factor(rp, ci, av, 2)
+    ref = oracle.factor(A, 2)
+    grp, gci, glev, _ = [t.cpu().numpy() for t in S.pattern()]
+    assert np.array_equal(grp, ref["rowptr"]) and np.array_equal(gci, ref["colind"])
+    assert np.array_equal(glev, ref["level"])
+    assert_bits_equal(F.values(), ref["val"], "factor values")
+    p, pd = vec(23, A.n)
+    assert_bits_equal(F.apply(pd), oracle.apply(A.n, ref["rowptr"], ref["colind"], ref["val"], p),
+                      "apply")
