@@ -16,6 +16,9 @@
 // persistent launch: tickets are handed out row-major over (row, set), so
 // every set advances through the rows together and the sets' independent
 // rows fill the GPU while each set's dependency chain is walked.
+//
+// k_factor_fused runs this phase beside the symbolic one in one launch, each
+// row starting as soon as its pattern is final (see the section below).
 #include "internal.h"
 #include "symbolic_body.cuh"
 
@@ -25,8 +28,9 @@ constexpr int kNumThreads = 256;
 // Sixteenths of the fused factorization's CTAs that run the symbolic walk:
 // few with the level-map walk, which keeps ahead of the numeric rows easily;
 // more with the sorted-list walk of wide matrices, which is slower per row.
-// (At the headline band size 3-10/16 time alike; the 3D 64^3 grid: 58 ms at
-// 3/16, 23 ms at 8/16, 37 ms at 12/16.)
+// (On the random band matrix with n = 160,000, k = 2, 3-10/16 time alike; on
+// the 7-point 3D 64^3 grid, k = 2: 58 ms at 3/16, 23 ms at 8/16, 37 ms at
+// 12/16.)
 constexpr int kFusedSymPartMap = 4;
 constexpr int kFusedSymPartList = 8;
 
