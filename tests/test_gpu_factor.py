@@ -48,7 +48,7 @@ def test_factor_equals_oracle(name, A, k):
     assert F.status() == L.OK
 
 
-def test_factor_equals_two_calls_headline_band():
+def test_factor_equals_two_calls_band_160k():
     pr = W.random_band_160k(2)
     rp, ci, av = to_dev(pr.A)
     S, F = P.factor(rp, ci, av, 2)
