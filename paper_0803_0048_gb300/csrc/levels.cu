@@ -11,26 +11,24 @@
 
 namespace iluk {
 
-constexpr int kDepthThreads = 1024;
+constexpr int kDepthThreads = 512;
 
-// One CTA, one warp per row (rows claimed in sweep order through a shared
-// ticket).  depth[] doubles as the ready flag: 0 until the row is final.
+// One warp per row, rows claimed in sweep order through a global ticket per
+// direction; depth[] doubles as the ready flag (0 until the row is final),
+// handed over through L2.  A warp claims a row only while it runs, and every
+// row it reads holds an earlier ticket, so the waits end whether or not all
+// CTAs are resident: the launch can share the GPU with the numeric phase, and
+// wide DAGs (thousands of rows per level) get thousands of warps.
 template <bool FORWARD>
-__device__ void depth_cta(int64_t n, const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
-                          const int64_t *__restrict__ dg, int32_t *depth, int32_t *maxdepth,
-                          DevErr *err, int64_t limit_ns) {
-  __shared__ unsigned long long sticket;
-  __shared__ int sfail;
-  if (threadIdx.x == 0) {
-    sticket = 0;
-    sfail = 0;
-  }
-  __syncthreads();
+__device__ void depth_rows(int64_t n, const int64_t *__restrict__ rp,
+                           const int32_t *__restrict__ ci, const int64_t *__restrict__ dg,
+                           int32_t *depth, int32_t *maxdepth, DevErr *err, int64_t limit_ns,
+                           unsigned long long *ticket, int *fail) {
   const int lane = threadIdx.x & 31;
   int dmax_local = 0;
   for (;;) {
     unsigned long long tk = 0;
-    if (lane == 0) tk = atomicAdd(&sticket, 1ull);
+    if (lane == 0) tk = atomicAdd(ticket, 1ull);
     const int64_t t = (int64_t)__shfl_sync(FULL_MASK, tk, 0);
     if (t >= n) break;
     const int64_t row = FORWARD ? t : n - 1 - t;
@@ -45,17 +43,22 @@ __device__ void depth_cta(int64_t n, const int64_t *__restrict__ rp, const int32
       const int32_t *src = nullptr;
       if (q < b1) {
         src = &depth[ci[q]];
-        asm volatile("ld.relaxed.cta.global.b32 %0, [%1];" : "=r"(v) : "l"(src));
+        asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(src));
       }
       if (__any_sync(FULL_MASK, v == 0)) {
         const uint64_t t0 = globaltimer_ns();
-        while (__any_sync(FULL_MASK, v == 0)) {
-          if (v == 0) asm volatile("ld.relaxed.cta.global.b32 %0, [%1];" : "=r"(v) : "l"(src));
-          const bool stop =
-              *((volatile int *)&sfail) || (int64_t)(globaltimer_ns() - t0) > limit_ns;
+        unsigned backoff = 16;
+        for (unsigned it = 0; __any_sync(FULL_MASK, v == 0); ++it) {
+          if (v == 0) asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(src));
+          const bool stop = (it & 15u) == 15u &&
+                            (*((volatile int *)fail) || (int64_t)(globaltimer_ns() - t0) > limit_ns);
           if (__any_sync(FULL_MASK, stop)) {  // the whole warp gives up together
             ok = false;
             break;
+          }
+          if (it >= 4) {
+            __nanosleep(backoff);
+            if (backoff < 64u) backoff <<= 1;
           }
         }
       }
@@ -64,30 +67,31 @@ __device__ void depth_cta(int64_t n, const int64_t *__restrict__ rp, const int32
     }
     if (!__all_sync(FULL_MASK, ok)) {
       if (lane == 0) {
-        atomicExch(&sfail, 1);
+        atomicExch(fail, 1);
         set_err(err, t, ILUK_ETIMEOUT);
       }
       return;
     }
     dm = __reduce_max_sync(FULL_MASK, dm) + 1;
     if (lane == 0) {
-      asm volatile("st.relaxed.cta.global.b32 [%0], %1;" ::"l"(&depth[row]), "r"(dm) : "memory");
+      asm volatile("st.relaxed.gpu.global.b32 [%0], %1;" ::"l"(&depth[row]), "r"(dm) : "memory");
       if (dm > dmax_local) dmax_local = dm;
     }
   }
   if (lane == 0 && dmax_local) atomicMax(maxdepth, dmax_local);
 }
 
-// Block 0 computes the forward depths, block 1 the backward depths; the two
-// DAGs are independent, so the two blocks run side by side on two SMs.
-__global__ void __launch_bounds__(kDepthThreads, 1)
+// Even CTAs compute the forward depths, odd CTAs the backward depths (the two
+// DAGs are independent).  ctl: two tickets, then two failure flags.
+__global__ void __launch_bounds__(kDepthThreads)
 k_depth_pair(int64_t n, const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
              const int64_t *__restrict__ dg, int32_t *depth_f, int32_t *depth_b, int32_t *mx,
-             DevErr *err, int64_t limit_ns) {
-  if (blockIdx.x == 0)
-    depth_cta<true>(n, rp, ci, dg, depth_f, mx, err, limit_ns);
+             DevErr *err, unsigned long long *ctl, int64_t limit_ns) {
+  int *fail = reinterpret_cast<int *>(ctl + 2);
+  if ((blockIdx.x & 1) == 0)
+    depth_rows<true>(n, rp, ci, dg, depth_f, mx, err, limit_ns, ctl, fail);
   else
-    depth_cta<false>(n, rp, ci, dg, depth_b, mx + 1, err + 1, limit_ns);
+    depth_rows<false>(n, rp, ci, dg, depth_b, mx + 1, err + 1, limit_ns, ctl + 1, fail + 1);
 }
 
 __global__ void k_level_count(int64_t n, const int32_t *__restrict__ depth, int32_t *cnt) {
@@ -187,22 +191,32 @@ int build_levels_pair(int64_t n, const int64_t *rp, const int32_t *ci, const int
   if (n == 0) return ILUK_OK;
   int32_t *depth = nullptr, *mx = nullptr;
   DevErr *err = nullptr;
+  unsigned long long *ctl = nullptr;  // two tickets, two failure flags
   auto cleanup = [&]() {
     if (depth) cudaFreeAsync(depth, s);
     if (mx) cudaFreeAsync(mx, s);
     if (err) cudaFreeAsync(err, s);
+    if (ctl) cudaFreeAsync(ctl, s);
   };
   if (cudaMallocAsync((void **)&depth, 2 * n * sizeof(int32_t), s) != cudaSuccess ||
       cudaMallocAsync((void **)&mx, 2 * sizeof(int32_t), s) != cudaSuccess ||
       cudaMallocAsync((void **)&err, 2 * sizeof(DevErr), s) != cudaSuccess ||
+      cudaMallocAsync((void **)&ctl, 3 * sizeof(unsigned long long), s) != cudaSuccess ||
       cudaMemsetAsync(depth, 0, 2 * n * sizeof(int32_t), s) != cudaSuccess ||
       cudaMemsetAsync(mx, 0, 2 * sizeof(int32_t), s) != cudaSuccess ||
+      cudaMemsetAsync(ctl, 0, 3 * sizeof(unsigned long long), s) != cudaSuccess ||
       launch_fill_err(err, s) != cudaSuccess || launch_fill_err(err + 1, s) != cudaSuccess) {
     cleanup();
     return ILUK_ECUDA;
   }
-  k_depth_pair<<<2, kDepthThreads, 0, s>>>(n, rp, ci, dg, depth, depth + n, mx, err,
-                                           wait_limit());
+  // one forward and one backward CTA per SM: 1024 threads, which leaves room
+  // beside the numeric phase's 256-thread CTA when both run at once
+  int64_t grid = 2 * (int64_t)num_sms();
+  const int64_t want = 2 * ((n * 32 + kDepthThreads - 1) / kDepthThreads);
+  if (grid > want) grid = want;
+  if (grid < 2) grid = 2;
+  k_depth_pair<<<(unsigned)grid, kDepthThreads, 0, s>>>(n, rp, ci, dg, depth, depth + n, mx, err,
+                                                        ctl, wait_limit());
   note_launch();
   DevErr herr[2];
   int32_t nlev[2] = {0, 0};
