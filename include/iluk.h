@@ -10,6 +10,12 @@
  * every iteration of a Krylov solver, and the optional level-based incomplete
  * inverse (TPIILU, Sec. 3.5) that turns that solve into two sparse mat-vecs.
  *
+ * The steps are numbered the same way here and in the library's sources:
+ *   a1 pattern check            a5 TPIILU build and apply
+ *   a2 symbolic phase           a6 restarted GMRES(m)
+ *   a3 numeric phase            a7 many systems on one pattern (batched)
+ *   a4 triangular sweeps        a8 gradient of a solve (adjoint)
+ *
  * General conventions (all entry points):
  *  - Matrices are CSR, 0-based: rowptr int64[n+1] (rowptr[0] = 0,
  *    non-decreasing), colind int32[nnz] strictly ascending inside each row,

@@ -3,7 +3,8 @@
 PyTorch provides device memory and the current CUDA stream; every step of
 the method runs in the library's kernels.  All tensors must live on the
 current CUDA device: CSR row pointers int64, column indices int32, values and
-vectors float64.
+vectors float64.  The step labels a1-a8 in the docstrings are those of the
+C header (include/iluk.h).
 """
 from __future__ import annotations
 

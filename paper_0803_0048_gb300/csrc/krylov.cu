@@ -1,4 +1,4 @@
-// krylov.cu -- a6 building blocks of right-preconditioned GMRES(m).
+// krylov.cu -- a6: building blocks of right-preconditioned GMRES(m).
 //
 // Inner products use one fixed reduction shape, independent of the GPU:
 // 4096 partial sums, partial p summing indices p, p+4096, ... left to right
@@ -19,7 +19,7 @@ namespace iluk {
 // (products, and the Gram-Schmidt update) are independent; only the additions
 // into a partial form a chain.  FP64 issue is what limits these kernels on
 // this part: one warp instruction occupies an SM sub-partition's FP64 pipe
-// for ~66 clocks, and a dependent addition waits as long.  So warp 0 runs the
+// for ~75 clocks, and a dependent addition waits ~64.  So warp 0 runs the
 // CTA's 32 chains (one per lane) from products staged in shared memory, alone
 // on its sub-partition, while the warps of the other three sub-partitions
 // (warp % 4 != 0) evaluate the products.
