@@ -176,6 +176,19 @@ def measured_traffic(kind, k):
     return None
 
 
+def ranks_max(values, dev, world):
+    """Each value's maximum over the ranks of the process group (a plain copy
+    when world == 1).  Backend-agnostic: dev is the device the backend reduces
+    on (cuda for NCCL, cpu for gloo)."""
+    if world <= 1:
+        return [float(v) for v in values]
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
 def ours(args):
     import torch
     import torch.distributed as dist
@@ -238,10 +251,6 @@ def ours(args):
     prof = P.prof_read()
     P.prof_enable(False)
     launches = (P.launch_count() - launches0) // args.steps
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
 
     # end to end through the public API from pinned host buffers
     h_rp = torch.from_numpy(A.rowptr).pin_memory()
@@ -261,6 +270,8 @@ def ours(args):
     e1.record(stream)
     barrier()
     ms_e2e = e0.elapsed_time(e1) / args.steps
+    # every replica runs the same step: the slowest one sets both times
+    ms, ms_e2e = ranks_max([ms, ms_e2e], dev, world)
     h2d = h_rp.numel() * 8 + h_ci.numel() * 4 + h_av.numel() * 8 + h_b.numel() * 8
     d2h = n * 8
 
