@@ -37,10 +37,27 @@ def _ptr(t: Optional[torch.Tensor]):
 
 def _check_dev(*ts):
     for t in ts:
-        if t is not None and not t.is_cuda:
-            raise ValueError("tensors must be on a CUDA device")
-        if t is not None and not t.is_contiguous():
+        if t is None:
+            continue
+        if not t.is_cuda or t.get_device() != torch.cuda.current_device():
+            raise ValueError("tensors must be on the current CUDA device")
+        if not t.is_contiguous():
             raise ValueError("tensors must be contiguous")
+
+
+def _vecs(*specs) -> None:
+    """Check float64 tensors before their pointers cross the C ABI, which takes
+    lengths from the handle or the pattern: the kernels trust dtype and size.
+    Each spec is (tensor or None, expected number of elements, name); dtypes and
+    sizes of all are checked before devices."""
+    for t, n, what in specs:
+        if t is None:
+            continue
+        if t.dtype != torch.float64:
+            raise ValueError(f"{what}: expected torch.float64, got {t.dtype}")
+        if t.numel() != n:
+            raise ValueError(f"{what}: expected {n} elements, got {t.numel()}")
+    _check_dev(*(t for t, _, _ in specs))
 
 
 def _call(fn, *args, info=None, what=""):
@@ -54,8 +71,11 @@ class CsrPattern:
     """A CSR pattern on the device, plus the C struct that points at it."""
 
     def __init__(self, rowptr: torch.Tensor, colind: torch.Tensor):
+        if rowptr.dtype != torch.int64 or colind.dtype != torch.int32:
+            raise ValueError("CSR pattern: rowptr must be int64 and colind int32")
+        if rowptr.dim() != 1 or colind.dim() != 1 or rowptr.numel() < 1:
+            raise ValueError("CSR pattern: rowptr [n+1] and colind [nnz] must be 1-D")
         _check_dev(rowptr, colind)
-        assert rowptr.dtype == torch.int64 and colind.dtype == torch.int32
         self.rowptr, self.colind = rowptr, colind
         self.n = rowptr.numel() - 1
         self.nnz = colind.numel()
@@ -137,7 +157,7 @@ class Factors:
         return out
 
     def refactor(self, vals: torch.Tensor) -> None:
-        _check_dev(vals)
+        _vecs((vals, self.S.A.nnz, "values of A"))
         info = L.Info()
         _call(L.load().iluk_refactor, self.h, _ptr(vals), C.byref(info), C.c_void_p(_stream()),
               info=info, what="iluk_refactor")
@@ -145,7 +165,8 @@ class Factors:
     def apply(self, p: torch.Tensor, out: Optional[torch.Tensor] = None, transpose: bool = False,
               sched: int = L.SCHED_AUTO) -> torch.Tensor:
         """a4: y = (L~U~)^-1 p (or ^-T)."""
-        _check_dev(p)
+        _vecs((p, self.S.n, "p"),
+              (out, self.S.n, "out"))
         y = torch.empty_like(p) if out is None else out
         _call(L.load().iluk_apply_sched, self.h, _ptr(p), _ptr(y), int(transpose), int(sched),
               C.c_void_p(_stream()))
@@ -164,8 +185,7 @@ class Factors:
 
 def numeric(S: Symbolic, vals: torch.Tensor) -> Factors:
     """a3: numeric IKJ factorization (Eq. 1)."""
-    _check_dev(vals)
-    assert vals.dtype == torch.float64 and vals.numel() == S.A.nnz
+    _vecs((vals, S.A.nnz, "values of A"))
     h = C.c_void_p()
     info = L.Info()
     _call(L.load().iluk_numeric, S.h, _ptr(vals), C.byref(h), C.byref(info),
@@ -178,8 +198,7 @@ def factor(rowptr: torch.Tensor, colind: torch.Tensor, vals: torch.Tensor, k: in
     the same (Symbolic, Factors) as ``symbolic`` then ``numeric``, bit for bit.
     The sweeps walk index orders until level orders are built."""
     A = CsrPattern(rowptr, colind)
-    _check_dev(vals)
-    assert vals.dtype == torch.float64 and vals.numel() == A.nnz
+    _vecs((vals, A.nnz, "values of A"))
     hs, hf = C.c_void_p(), C.c_void_p()
     info = L.Info()
     _call(L.load().iluk_factor, A.ref, _ptr(vals), int(k), C.byref(hs), C.byref(hf),
@@ -207,7 +226,8 @@ class IncompleteInverse:
         return out
 
     def apply(self, p: torch.Tensor, out: Optional[torch.Tensor] = None) -> torch.Tensor:
-        _check_dev(p)
+        _vecs((p, self.F.S.n, "p"),
+              (out, self.F.S.n, "out"))
         y = torch.empty_like(p) if out is None else out
         _call(L.load().iiluk_apply, self.h, _ptr(p), _ptr(y), C.c_void_p(_stream()))
         return y
@@ -224,7 +244,9 @@ def iiluk_build(F: Factors) -> IncompleteInverse:
 
 def spmv(rowptr, colind, vals, x, out=None):
     A = CsrPattern(rowptr, colind)
-    _check_dev(vals, x)
+    _vecs((vals, A.nnz, "values of A"),
+          (x, A.n, "x"),
+          (out, A.n, "out"))
     y = torch.empty_like(x) if out is None else out
     _call(L.load().iluk_spmv, A.ref, _ptr(vals), _ptr(x), _ptr(y), C.c_void_p(_stream()))
     return y
@@ -232,7 +254,8 @@ def spmv(rowptr, colind, vals, x, out=None):
 
 def dot(x: torch.Tensor, y: torch.Tensor) -> torch.Tensor:
     """Fixed-shape inner product (4096 strided partials, pairwise tree)."""
-    _check_dev(x, y)
+    _vecs((x, x.numel(), "x"),
+          (y, x.numel(), "y"))
     out = torch.empty(1, dtype=torch.float64, device=x.device)
     _call(L.load().iluk_dot, x.numel(), _ptr(x), _ptr(y), _ptr(out), C.c_void_p(_stream()))
     return out
@@ -241,7 +264,8 @@ def dot(x: torch.Tensor, y: torch.Tensor) -> torch.Tensor:
 def div_rn(a: torch.Tensor, b: torch.Tensor) -> torch.Tensor:
     """a / b elementwise by the sweeps' division (double-double reciprocal
     plus a Markstein correction); equal to IEEE division bit for bit."""
-    _check_dev(a, b)
+    _vecs((a, a.numel(), "a"),
+          (b, a.numel(), "b"))
     q = torch.empty_like(a)
     _call(L.load().iluk_div_rn, a.numel(), _ptr(a), _ptr(b), _ptr(q), C.c_void_p(_stream()))
     return q
@@ -253,7 +277,9 @@ def gmres(rowptr, colind, vals, b, prec=None, restart=30, rtol=1e-8, maxit=10000
     Factors (ILU(k) sweeps) or an IncompleteInverse (TPIILU).
     Returns (x, info)."""
     A = CsrPattern(rowptr, colind)
-    _check_dev(vals, b)
+    _vecs((vals, A.nnz, "values of A"),
+          (b, A.n, "b"),
+          (x, A.n, "x"))
     xo = torch.empty_like(b) if x is None else x
     if prec is None:
         kind, ph = L.PREC_NONE, None
@@ -277,7 +303,9 @@ def bicgstab(rowptr, colind, vals, b, prec=None, rtol=1e-8, maxit=10000, x=None,
     ``prec`` is None, a Factors or an IncompleteInverse.  Returns (x, info);
     info.relres is the true relative residual."""
     A = CsrPattern(rowptr, colind)
-    _check_dev(vals, b)
+    _vecs((vals, A.nnz, "values of A"),
+          (b, A.n, "b"),
+          (x, A.n, "x"))
     xo = torch.empty_like(b) if x is None else x
     if prec is None:
         kind, ph = L.PREC_NONE, None
@@ -302,7 +330,8 @@ def tpilu_solve(rowptr, colind, vals, b, F, M=None, solver="gmres", restart=50, 
     iterations, then, if that does not converge, again from x0 = 0 with F's
     ILU(k) sweeps.  Returns (x, info, used) with used "iilu" or "ilu"."""
     A = CsrPattern(rowptr, colind)
-    _check_dev(vals, b)
+    _vecs((vals, A.nnz, "values of A"),
+          (b, A.n, "b"))
     xo = torch.empty_like(b)
     kind = {"gmres": L.SOLVER_GMRES, "bicgstab": L.SOLVER_BICGSTAB}[solver]
     info = L.Info()
@@ -318,7 +347,9 @@ def tpilu_solve(rowptr, colind, vals, b, F, M=None, solver="gmres", restart=50, 
 def adjoint_scatter(rowptr, colind, lam, x, out=None):
     """gA[p] = -lambda_i x_j on A's pattern."""
     A = CsrPattern(rowptr, colind)
-    _check_dev(lam, x)
+    _vecs((lam, A.n, "lambda"),
+          (x, A.n, "x"),
+          (out, A.nnz, "out"))
     g = torch.empty(A.nnz, dtype=torch.float64, device=x.device) if out is None else out
     _call(L.load().iluk_adjoint_scatter, A.ref, _ptr(lam), _ptr(x), _ptr(g),
           C.c_void_p(_stream()))
@@ -328,8 +359,11 @@ def adjoint_scatter(rowptr, colind, lam, x, out=None):
 def numeric_batched(S: Symbolic, vals: torch.Tensor, out: Optional[torch.Tensor] = None):
     """a7: factor ``vals`` [nbatch, nnz_A] on one pattern in one launch.
     Returns (F values [nbatch, nnz_F], per-set statuses)."""
-    _check_dev(vals)
+    if vals.dim() != 2:
+        raise ValueError("values: expected [nbatch, nnz_A]")
     nb = vals.shape[0]
+    _vecs((vals, nb * S.A.nnz, "values [nbatch, nnz_A]"),
+          (out, nb * S.nnz, "out [nbatch, nnz_F]"))
     F = torch.empty(nb, S.nnz, dtype=torch.float64, device=vals.device) if out is None else out
     infos = (L.Info * max(nb, 1))()
     L.load().iluk_numeric_batched(S.h, nb, _ptr(vals), _ptr(F), infos, C.c_void_p(_stream()))
@@ -372,9 +406,11 @@ class BatchSolve:
 
     def __init__(self, items, restart=30, rtol=1e-8, maxit=10000):
         self.items = list(items)  # keep the tensors alive
+        _vecs(*(spec for i, (S, vals, b, x) in enumerate(self.items)
+                for spec in ((vals, S.A.nnz, f"item {i}: values of A"),
+                             (b, S.n, f"item {i}: b"), (x, S.n, f"item {i}: x"))))
         arr = (L.BatchItem * max(len(self.items), 1))()
         for i, (S, vals, b, x) in enumerate(self.items):
-            _check_dev(vals, b, x)
             arr[i] = L.BatchItem(S.h.value if isinstance(S.h, C.c_void_p) else S.h,
                                  S.A.rowptr.data_ptr(), S.A.colind.data_ptr(), vals.data_ptr(),
                                  b.data_ptr(), x.data_ptr())
