@@ -82,6 +82,14 @@ void info_init(iluk_info *info) {
   }
 }
 
+// Sizes and pointers of a pattern that the kernels may index: n and nnz not
+// negative (n within int32 column indices), rowptr always present, colind
+// present when nnz > 0.  Its contents are iluk_validate's business.
+bool pattern_args_ok(const iluk_pattern *A) {
+  return A && A->n >= 0 && A->n <= INT32_MAX && A->nnz >= 0 && A->rowptr &&
+         (A->nnz == 0 || A->colind);
+}
+
 #define CK(call)                                        \
   do {                                                  \
     cudaError_t _e = (call);                            \
@@ -219,9 +227,7 @@ int iluk_prof_read(double *ms, int64_t *count, int nkinds) {
 
 int iluk_validate(const iluk_pattern *A, iluk_info *info, void *stream) {
   info_init(info);
-  if (!A || A->n < 0 || A->nnz < 0 || !A->rowptr || (A->nnz > 0 && !A->colind))
-    return fail(info, ILUK_EINVAL);
-  if (A->n > INT32_MAX) return fail(info, ILUK_EINVAL);
+  if (!pattern_args_ok(A)) return fail(info, ILUK_EINVAL);
   cudaStream_t s = (cudaStream_t)stream;
   DevErr *err = nullptr;
   CK(dalloc(&err, 1, s));
@@ -985,7 +991,7 @@ int iiluk_export(const iiluk *M, double *g, void *stream) {
 
 int iiluk_apply(const iiluk *M, const double *p, double *y, void *stream) {
   iluk_info *info = nullptr;
-  if (!M) return ILUK_EINVAL;
+  if (!M || (M->S->n > 0 && (!p || !y))) return ILUK_EINVAL;
   CK(launch_iiluk_apply(M->S, M->g, p, M->tmp, y, (cudaStream_t)stream));
   return ILUK_OK;
 }
@@ -993,7 +999,8 @@ int iiluk_apply(const iiluk *M, const double *p, double *y, void *stream) {
 int iluk_spmv(const iluk_pattern *A, const double *A_val, const double *x, double *y,
               void *stream) {
   iluk_info *info = nullptr;
-  if (!A) return ILUK_EINVAL;
+  if (!pattern_args_ok(A) || (A->n > 0 && (!x || !y)) || (A->nnz > 0 && !A_val))
+    return ILUK_EINVAL;
   CK(launch_spmv(A->n, A->rowptr, A->colind, A_val, x, y, nullptr, (cudaStream_t)stream));
   return ILUK_OK;
 }
@@ -1007,6 +1014,7 @@ int iluk_div_rn(int64_t n, const double *a, const double *b, double *q, void *st
 
 int iluk_dot(int64_t n, const double *x, const double *y, double *out, void *stream) {
   iluk_info *info = nullptr;
+  if (n < 0 || !out || (n > 0 && (!x || !y))) return ILUK_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   DotScratch ds{};
   CK(dalloc(&ds.partial, kDotP, s));
@@ -1021,7 +1029,8 @@ int iluk_dot(int64_t n, const double *x, const double *y, double *out, void *str
 int iluk_adjoint_scatter(const iluk_pattern *A, const double *lambda, const double *x, double *gA,
                          void *stream) {
   iluk_info *info = nullptr;
-  if (!A) return ILUK_EINVAL;
+  if (!pattern_args_ok(A) || (A->n > 0 && (!lambda || !x)) || (A->nnz > 0 && !gA))
+    return ILUK_EINVAL;
   CK(launch_adjoint_scatter(A->n, A->rowptr, A->colind, lambda, x, gA, (cudaStream_t)stream));
   return ILUK_OK;
 }
@@ -1031,6 +1040,7 @@ int iluk_numeric_batched(const iluk_sym *S, int64_t nbatch, const double *A_vals
   iluk_info *info = nullptr;
   if (!S || nbatch < 0) return ILUK_EINVAL;
   if (nbatch == 0) return ILUK_OK;
+  if ((S->nnzA > 0 && !A_vals) || (S->nnz > 0 && !F_vals)) return ILUK_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   unsigned long long *ticket = nullptr;
   DevErr *errs = nullptr;
@@ -1250,7 +1260,8 @@ int gmres_solve(const iluk_pattern *A, const double *A_val, int prec_kind, void 
                 const double *b, double *x, int m, double rtol, int maxit, int transpose,
                 iluk_info *info, void *stream) {
   info_init(info);
-  if (!A || m < 1 || maxit < 0 || A->n < 0) return fail(info, ILUK_EINVAL);
+  if (!pattern_args_ok(A) || m < 1 || maxit < 0) return fail(info, ILUK_EINVAL);
+  if ((A->n > 0 && (!b || !x)) || (A->nnz > 0 && !A_val)) return fail(info, ILUK_EINVAL);
   if (prec_kind != ILUK_PREC_NONE && !prec) return fail(info, ILUK_EINVAL);
   if (transpose && prec_kind == ILUK_PREC_IILU) return fail(info, ILUK_EINVAL);
   cudaStream_t s = (cudaStream_t)stream;
@@ -1425,7 +1436,8 @@ int bicgstab_solve(const iluk_pattern *A, const double *A_val, int prec_kind, vo
                    const double *b, double *x, double rtol, int maxit, iluk_info *info,
                    void *stream) {
   info_init(info);
-  if (!A || maxit < 0 || A->n < 0) return fail(info, ILUK_EINVAL);
+  if (!pattern_args_ok(A) || maxit < 0) return fail(info, ILUK_EINVAL);
+  if ((A->n > 0 && (!b || !x)) || (A->nnz > 0 && !A_val)) return fail(info, ILUK_EINVAL);
   if (prec_kind != ILUK_PREC_NONE && !prec) return fail(info, ILUK_EINVAL);
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t n = A->n;
@@ -1550,9 +1562,11 @@ int tpilu_solve(const iluk_pattern *A, const double *A_val, iluk_fac *F, iiluk *
                 const double *b, double *x, int m, double rtol, int iilu_maxit, int maxit,
                 int *used, iluk_info *info, void *stream) {
   info_init(info);
-  if (!A || !F || !used || (solver != ILUK_SOLVER_GMRES && solver != ILUK_SOLVER_BICGSTAB) ||
-      iilu_maxit < 0 || maxit < 0 || (solver == ILUK_SOLVER_GMRES && m < 1))
+  if (!pattern_args_ok(A) || !F || !used ||
+      (solver != ILUK_SOLVER_GMRES && solver != ILUK_SOLVER_BICGSTAB) || iilu_maxit < 0 ||
+      maxit < 0 || (solver == ILUK_SOLVER_GMRES && m < 1))
     return fail(info, ILUK_EINVAL);
+  if ((A->n > 0 && (!b || !x)) || (A->nnz > 0 && !A_val)) return fail(info, ILUK_EINVAL);
   auto run = [&](int kind, void *prec, int its) {
     return solver == ILUK_SOLVER_GMRES
                ? gmres_solve(A, A_val, kind, prec, b, x, m, rtol, its, 0, info, stream)
