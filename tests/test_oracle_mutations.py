@@ -47,6 +47,43 @@ MUTANTS = {
     "bicgstab_omega_sign": ("      x[i] = xa + ws;", "      x[i] = xa - ws;"),
     "bicgstab_beta_inverted": ("double b1 = rho / rho_prev, b2 = alpha / omega;",
                                "double b1 = rho / rho_prev, b2 = omega / alpha;"),
+    "pattern_allows_duplicates": ("if (p > rp[i] && ci[p] <= ci[p - 1])",
+                                  "if (p > rp[i] && ci[p] < ci[p - 1])"),
+    "pattern_allows_column_n": ("if (ci[p] < 0 || ci[p] >= n)", "if (ci[p] < 0 || ci[p] > n)"),
+    "initial_level_one": ("level[t] = 0; in[t] = 1; next[t] = END;",
+                          "level[t] = 1; in[t] = 1; next[t] = END;"),
+    "level_keeps_larger": ("if (weight < level[t]) level[t] = weight;",
+                           "if (weight > level[t]) level[t] = weight;"),
+    "numeric_update_from_diagonal": ("for (int64_t q = diag[h] + 1; q < frp[h + 1]; ++q) {",
+                                     "for (int64_t q = diag[h]; q < frp[h + 1]; ++q) {"),
+    "forward_sweep_takes_diagonal": ("q < frp[i + 1] && fci[q] < i; ++q) {",
+                                     "q < frp[i + 1] && fci[q] <= i; ++q) {"),
+    "backward_sweep_skips_last": ("""    for (int64_t q = frp[i + 1] - 1; q > d; --q) {
+      double prod = fv[q] * y[fci[q]];""", """    for (int64_t q = frp[i + 1] - 2; q > d; --q) {
+      double prod = fv[q] * y[fci[q]];"""),
+    "transpose_copies_wrong_value": ("if (v && tv) tv[dst] = v[p];",
+                                     "if (v && tv) tv[dst] = v[dst];"),
+    "transpose_forward_no_divide": ("    z[i] = s / tv[d];", "    z[i] = s;"),
+    "iilu_apply_drops_own_term": ("      x = s + p[i];", "      x = s;"),
+    "iilu_apply_no_diagonal": ("    z[i] = x / g[d];", "    z[i] = x;"),
+    "spmv_reads_row_index": ("{ double prod = v[p] * x[ci[p]]; s = s + prod; }",
+                             "{ double prod = v[p] * x[i]; s = s + prod; }"),
+    "residual_sign": ("r[i] = b[i] - w[i];", "r[i] = w[i] - b[i];"),
+    "mgs_adds": ("double prod = hij * vi[q]; w[q] = w[q] - prod;",
+                 "double prod = hij * vi[q]; w[q] = w[q] + prod;"),
+    "update_forgets_preconditioner": ("double prod = yv[j] * Z[(size_t)j * N + q];",
+                                      "double prod = yv[j] * V[(size_t)j * N + q];"),
+    "back_substitution_transposed": ("double prod = H[i * m + l] * yv[l];",
+                                     "double prod = H[l * m + i] * yv[l];"),
+    "givens_cos_sin_swapped": ("cs[j] = a / rr; sn[j] = c / rr;", "cs[j] = c / rr; sn[j] = a / rr;"),
+    "tree_dot_wrong_stride": ("for (int64_t i = p; i < n; i += ORC_TREE_P)",
+                              "for (int64_t i = p; i < n; i += ORC_TREE_P / 2)"),
+    "sequential_dot_drops_last": ("for (int64_t i = 0; i < n; ++i) { double prod = x[i] * y[i];",
+                                  "for (int64_t i = 0; i + 1 < n; ++i) { double prod = x[i] * y[i];"),
+    "adjoint_scatter_transposed": ("double prod = lambda[i] * x[aci[p]];",
+                                   "double prod = lambda[aci[p]] * x[i];"),
+    "adjoint_solves_untransposed": ("int st = orc_gmres(n, atrp, atci, atv, ORC_PREC_ILU, 1,",
+                                    "int st = orc_gmres(n, arp, aci, av, ORC_PREC_ILU, 1,"),
     "transpose_backward_divides": ("""      double prod = tv[q] * y[tci[q]];
       s = s - prod;
     }
@@ -74,6 +111,16 @@ def build_mutant(name, tmp):
 def pins_pass():
     """A compact run of the oracle's pins; returns the names that fail."""
     failed = []
+    try:  # sparse storage (Sec. 2.1): each defect reported with its row
+        bad = [([0, 2, 3], [1, 0, 1], 0), ([0, 2, 3], [0, 0, 1], 0), ([0, 1, 3], [0, 0, 2], 1),
+               ([0, 2, 1, 3], [0, 1, 1], 1)]
+        for rp, ci, row in bad:
+            if oracle.check_pattern(len(rp) - 1, rp, ci) != (oracle.EPATTERN, row):
+                raise AssertionError
+        if oracle.check_pattern(3, [0, 2, 3, 5], [0, 2, 1, 0, 2])[0] != 0:
+            raise AssertionError
+    except Exception:
+        failed.append("pattern")
     try:  # Def. 2.3 against lower-numbered paths
         for n, dens, seed in [(10, 0.2, 3), (12, 0.15, 4)]:
             A = W.random_sparse(n, dens, seed, dominance=None)
@@ -153,8 +200,9 @@ def pins_pass():
             raise AssertionError("gmres one cycle")
         xs = W.uniform(W.stream_key(8, "x"), np.arange(9000), -1, 1)
         exact = math.fsum((xs * xs).tolist())
-        if abs(oracle.dot(xs, xs, oracle.DOT_TREE) - exact) > 9000 * 2.3e-16 * exact:
-            raise AssertionError("dot")
+        for mode in (oracle.DOT_TREE, oracle.DOT_SEQ):
+            if abs(oracle.dot(xs, xs, mode) - exact) > 9000 * 2.3e-16 * exact:
+                raise AssertionError("dot")
     except Exception:
         failed.append("krylov")
     try:  # BiCGSTAB against a dense solve, with and without preconditioning
