@@ -6,14 +6,14 @@ Memory" (arXiv 0803.0048).  The work runs in libiluk.so (CUDA, sm_103a,
 declared in include/iluk.h); this package is its thin Python binding.
 """
 from . import _lib
+from .api import (BatchSolve, CsrPattern, Factors, IlukError, IncompleteInverse, Symbolic,
+                  adjoint_scatter, bicgstab, debug_hold_row, div_rn, dot, factor, gmres,
+                  iiluk_build, launch_count, numeric, numeric_batched, prof_enable, prof_read,
+                  set_wait_limit, solve, spmv, symbolic, tpilu_solve, validate)
 from .autograd import IlukSolve, IlukSolver
-from .api import (BatchSolve, CsrPattern, Factors, IlukError, IncompleteInverse, Symbolic, adjoint_scatter,
-                  bicgstab,
-                  debug_hold_row, div_rn, dot, factor, gmres, iiluk_build, launch_count, numeric,
-                  numeric_batched, prof_enable, prof_read, set_wait_limit, spmv, symbolic,
-                  tpilu_solve, validate)
 
-__all__ = ["IlukSolve", "IlukSolver", "BatchSolve", "CsrPattern", "Factors", "IlukError", "IncompleteInverse", "Symbolic",
-           "adjoint_scatter", "bicgstab", "debug_hold_row", "div_rn", "dot", "factor", "gmres", "iiluk_build", "launch_count",
-           "numeric", "numeric_batched", "prof_enable", "prof_read", "set_wait_limit", "spmv",
+__all__ = ["BatchSolve", "CsrPattern", "Factors", "IlukError", "IlukSolve", "IlukSolver",
+           "IncompleteInverse", "Symbolic", "adjoint_scatter", "bicgstab", "debug_hold_row",
+           "div_rn", "dot", "factor", "gmres", "iiluk_build", "launch_count", "numeric",
+           "numeric_batched", "prof_enable", "prof_read", "set_wait_limit", "solve", "spmv",
            "symbolic", "tpilu_solve", "validate"]

@@ -207,6 +207,24 @@ def factor(rowptr: torch.Tensor, colind: torch.Tensor, vals: torch.Tensor, k: in
     return S, Factors(hf, S)
 
 
+def solve(rowptr: torch.Tensor, colind: torch.Tensor, vals: torch.Tensor, b: torch.Tensor,
+          k: int = 2, restart: int = 30, rtol: float = 1e-8, maxit: int = 10000,
+          precond: str = "ilu", check: bool = True):
+    """Solve A x = b in one call: the level-k factorization of A (``factor``),
+    then right-preconditioned GMRES(restart) from x0 = 0 with the ILU(k) sweeps
+    (precond "ilu"), the TPIILU inverses built from the same factors ("iilu"),
+    or no preconditioner ("none").  Returns (x, info)."""
+    if precond not in ("ilu", "iilu", "none"):
+        raise ValueError("precond must be 'ilu', 'iilu' or 'none'")
+    prec = None
+    if precond != "none":
+        _, prec = factor(rowptr, colind, vals, k)
+        if precond == "iilu":
+            prec = iiluk_build(prec)
+    return gmres(rowptr, colind, vals, b, prec, restart=restart, rtol=rtol, maxit=maxit,
+                 check=check)
+
+
 class IncompleteInverse:
     """TPIILU level-based incomplete inverses (Sec. 3.5)."""
 

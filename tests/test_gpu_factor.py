@@ -110,3 +110,25 @@ def test_factor_sorted_list_walk():
     p, pd = vec(23, A.n)
     assert_bits_equal(F.apply(pd), oracle.apply(A.n, ref["rowptr"], ref["colind"], ref["val"], p),
                       "apply")
+
+
+@pytest.mark.parametrize("precond", ["none", "ilu", "iilu"])
+def test_one_call_solve_bit_exact(precond):
+    # solve(): factor (one launch for k = 2), optional TPIILU, then GMRES,
+    # against the oracle's factorization and GMRES with the fixed-tree dots
+    A = W.conv_diff(40, 2, (20.0, 20.0))
+    rp, ci, av = to_dev(A)
+    b, bd = vec(44, A.n)
+    x, info = P.solve(rp, ci, av, bd, k=2, restart=30, rtol=1e-10, precond=precond)
+    ref = oracle.factor(A, 2)
+    if precond == "ilu":
+        kind, Fa = oracle.PREC_ILU, (ref["rowptr"], ref["colind"], ref["val"])
+    elif precond == "iilu":
+        g = oracle.iiluk_build(A.n, ref["rowptr"], ref["colind"], ref["val"])
+        kind, Fa = oracle.PREC_IILU, (ref["rowptr"], ref["colind"], g)
+    else:
+        kind, Fa = oracle.PREC_NONE, None
+    st, xo, it, rel, cyc = oracle.gmres(A.n, A.rowptr, A.colind, A.val, b, kind, Fa, 30, 1e-10,
+                                        dotmode=oracle.DOT_TREE)
+    assert st == oracle.OK and info.status == st and info.iters == it and info.cycles == cyc
+    assert_bits_equal(x, xo, "solve x")
