@@ -66,6 +66,19 @@ void dfree(T *&p, cudaStream_t s) {
   p = nullptr;
 }
 
+// Calls fn when the scope ends, whichever return leaves it, so that scratch
+// buffers freed there with dfree do not leak when a CUDA call fails part-way
+// (dfree nulls what it frees, so buffers freed earlier are skipped).
+template <typename Fn>
+struct ScopeExit {
+  Fn fn;
+  ~ScopeExit() { fn(); }
+};
+template <typename Fn>
+ScopeExit<Fn> at_scope_exit(Fn fn) {
+  return ScopeExit<Fn>{fn};
+}
+
 int fail(iluk_info *info, int st, int64_t row = -1, int64_t need = 0) {
   if (info) {
     info->status = st;
@@ -230,6 +243,7 @@ int iluk_validate(const iluk_pattern *A, iluk_info *info, void *stream) {
   if (!pattern_args_ok(A)) return fail(info, ILUK_EINVAL);
   cudaStream_t s = (cudaStream_t)stream;
   DevErr *err = nullptr;
+  auto scratch = at_scope_exit([&] { dfree(err, s); });
   CK(dalloc(&err, 1, s));
   CK(launch_fill_err(err, s));
   CK(launch_validate(A->n, A->nnz, A->rowptr, A->colind, err, s));
@@ -778,6 +792,17 @@ static int ensure_transpose(iluk_fac *F, cudaStream_t s) {
   const iluk_sym *S = F->S;
   int32_t *cursor = nullptr;
   int64_t *scan_tmp = nullptr;
+  bool built = false;
+  auto scratch = at_scope_exit([&] {
+    dfree(cursor, s);
+    dfree(scan_tmp, s);
+    if (!built) {  // a failed build leaves no half-made transpose in F
+      dfree(F->trowptr, s);
+      dfree(F->tcolind, s);
+      dfree(F->tdiag, s);
+      dfree(F->tval, s);
+    }
+  });
   CK(dalloc(&F->trowptr, S->n + 1, s));
   CK(dalloc(&F->tcolind, S->nnz, s));
   CK(dalloc(&F->tdiag, S->n, s));
@@ -786,6 +811,7 @@ static int ensure_transpose(iluk_fac *F, cudaStream_t s) {
   CK(dalloc(&scan_tmp, scan_tmp_elems(S->n), s));
   CK(launch_transpose(S->n, S->nnz, S->rowptr, S->colind, F->val, F->trowptr, F->tcolind,
                       F->tval, F->tdiag, cursor, scan_tmp, s));
+  built = true;
   dfree(cursor, s);
   dfree(scan_tmp, s);
   if (!F->tlord.order && S->n) {
@@ -1017,6 +1043,10 @@ int iluk_dot(int64_t n, const double *x, const double *y, double *out, void *str
   if (n < 0 || !out || (n > 0 && (!x || !y))) return ILUK_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   DotScratch ds{};
+  auto scratch = at_scope_exit([&] {
+    dfree(ds.partial, s);
+    dfree(ds.counter, s);
+  });
   CK(dalloc(&ds.partial, kDotP, s));
   CK(dalloc(&ds.counter, 1, s));
   CK(cudaMemsetAsync(ds.counter, 0, sizeof(unsigned), s));
@@ -1044,6 +1074,10 @@ int iluk_numeric_batched(const iluk_sym *S, int64_t nbatch, const double *A_vals
   cudaStream_t s = (cudaStream_t)stream;
   unsigned long long *ticket = nullptr;
   DevErr *errs = nullptr;
+  auto scratch = at_scope_exit([&] {
+    dfree(ticket, s);
+    dfree(errs, s);
+  });
   CK(dalloc(&ticket, 1, s));
   CK(dalloc(&errs, nbatch, s));
   CK(cudaMemsetAsync(ticket, 0, sizeof(unsigned long long), s));
@@ -1276,9 +1310,19 @@ int gmres_solve(const iluk_pattern *A, const double *A_val, int prec_kind, void 
   int64_t *trp = nullptr;
   int32_t *tci = nullptr;
   double *tv = nullptr;
+  int32_t *cursor = nullptr;
+  int64_t *scan_tmp = nullptr;
+  // Z keeps the preconditioned basis z_j = M^-1 v_j of a cycle, which ends
+  // with x += Z y (the flexible-GMRES form: no extra application of M)
+  double *V = nullptr, *Z = nullptr, *w = nullptr, *u = nullptr, *Hd = nullptr, *dsc = nullptr,
+         *dy = nullptr;
+  DotScratch ds{};
+  auto scratch = at_scope_exit([&] {
+    dfree(cursor, s); dfree(scan_tmp, s); dfree(trp, s); dfree(tci, s); dfree(tv, s);
+    dfree(V, s); dfree(Z, s); dfree(w, s); dfree(u, s); dfree(Hd, s); dfree(dsc, s);
+    dfree(dy, s); dfree(ds.partial, s); dfree(ds.counter, s);
+  });
   if (transpose) {
-    int32_t *cursor = nullptr;
-    int64_t *scan_tmp = nullptr;
     CK(dalloc(&trp, n + 1, s));
     CK(dalloc(&tci, A->nnz, s));
     CK(dalloc(&tv, A->nnz, s));
@@ -1293,11 +1337,6 @@ int gmres_solve(const iluk_pattern *A, const double *A_val, int prec_kind, void 
     ov = tv;
   }
   const int64_t ldv = n > 0 ? n : 1;
-  // Z keeps the preconditioned basis z_j = M^-1 v_j of a cycle, which ends
-  // with x += Z y (the flexible-GMRES form: no extra application of M)
-  double *V = nullptr, *Z = nullptr, *w = nullptr, *u = nullptr, *Hd = nullptr, *dsc = nullptr,
-         *dy = nullptr;
-  DotScratch ds{};
   CK(dalloc(&V, (size_t)ldv * (m + 1), s));
   CK(dalloc(&Z, (size_t)ldv * m, s));
   CK(dalloc(&w, ldv, s));
@@ -1447,6 +1486,10 @@ int bicgstab_solve(const iluk_pattern *A, const double *A_val, int prec_kind, vo
   double *r = nullptr, *rh = nullptr, *p = nullptr, *v = nullptr, *ph = nullptr, *sv = nullptr,
          *sh = nullptr, *t = nullptr, *dsc = nullptr;
   DotScratch ds{};
+  auto scratch = at_scope_exit([&] {
+    dfree(r, s); dfree(rh, s); dfree(p, s); dfree(v, s); dfree(ph, s); dfree(sv, s);
+    dfree(sh, s); dfree(t, s); dfree(dsc, s); dfree(ds.partial, s); dfree(ds.counter, s);
+  });
   CK(dalloc(&r, ld, s));
   CK(dalloc(&rh, ld, s));
   CK(dalloc(&p, ld, s));

@@ -4,7 +4,9 @@ Every call below is refused by its argument checks with ILUK_EINVAL (or the
 documented status) before it touches CUDA, so the library runs here without a
 GPU.  The non-NULL pointers handed over point at host memory that the refused
 calls never read: each case is one where a check on sizes, handles or NULL
-pointers returns first.
+pointers returns first.  The last test alone passes the checks, and runs only
+where no GPU is present: there the first CUDA call fails and the entry point
+must return ILUK_ECUDA through its cleanup path.
 """
 import ctypes as C
 
@@ -147,3 +149,28 @@ def test_prof_read_and_strerror(lib):
     einval(lib.iluk_prof_read(None, None, 3))
     msgs = [lib.iluk_strerror(s) for s in range(10)]
     assert all(msgs) and len(set(msgs)) == 10
+
+
+def _cuda_available():
+    import torch
+    return torch.cuda.is_available()
+
+
+@pytest.mark.skipif(_cuda_available(), reason="host-only: with a GPU these calls would launch "
+                    "kernels on host pointers")
+def test_failing_cuda_calls_surface_as_ecuda(lib):
+    """Without a GPU the first CUDA call of each entry point fails; the call
+    returns ILUK_ECUDA through its cleanup path instead of crashing."""
+    A = pat()
+    info = L.Info()
+    assert lib.iluk_validate(C.byref(A), C.byref(info), None) == L.ECUDA
+    assert info.status == L.ECUDA
+    assert lib.iluk_dot(4, DUMMY, DUMMY, DUMMY, None) == L.ECUDA
+    for transpose in (0, 1):
+        assert lib.gmres_solve(C.byref(A), DUMMY, L.PREC_NONE, None, DUMMY, DUMMY, 30, 1e-8, 10,
+                               transpose, C.byref(info), None) == L.ECUDA
+    assert lib.bicgstab_solve(C.byref(A), DUMMY, L.PREC_NONE, None, DUMMY, DUMMY, 1e-8, 10,
+                              C.byref(info), None) == L.ECUDA
+    h = C.c_void_p()
+    assert lib.iluk_symbolic(C.byref(A), 2, C.byref(h), C.byref(info), None) == L.ECUDA
+    assert h.value is None
