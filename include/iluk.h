@@ -7,8 +7,9 @@
  * The calls follow the paper's statement of the problem (Sec. 2): a symbolic
  * phase that fixes the level-k pattern, a numeric phase that fills in the
  * values of the incomplete factors, a triangular solve L~U~y = p applied in
- * every iteration of a Krylov solver, and the optional level-based incomplete
- * inverse (TPIILU, Sec. 3.5) that turns that solve into two sparse mat-vecs.
+ * every iteration of a Krylov solver, and, as an option, the level-based
+ * incomplete inverse (TPIILU, Sec. 3.5) that turns that solve into two sparse
+ * mat-vecs.
  *
  * The steps are numbered the same way here and in the library's sources:
  *   a1 pattern check            a5 TPIILU build and apply

@@ -62,7 +62,7 @@ int orc_check_pattern(int64_t n, const int64_t *rp, const int32_t *ci, int64_t *
 /* Phase I: symbolic factorization, Algorithm 1 (Sec. 2.2) with the level    */
 /* of Def. 2.3.  permitted(j) is kept as a sorted singly linked list over    */
 /* column numbers; finished rows are stored in growable row-major arrays and */
-/* converted to CSR at the end (Sec. 3.4, "Efficient Matrix Storage").       */
+/* converted to CSR at the end (the row storage of Sec. 3.4).               */
 /* ------------------------------------------------------------------------ */
 typedef struct {
   int status;
@@ -335,8 +335,8 @@ void orc_apply_t(int64_t n, const int64_t *trp, const int32_t *tci, const double
 /* the stored value is -beta_it (Eq. flipfactor), taken after every row is   */
 /* done so the recurrence always reads unflipped beta.                       */
 /*                                                                           */
-/* Upper part, the mirror image ("reverse order from last row to first and   */
-/* from right to left within a row"): with u^_it = u_it / u_ii,              */
+/* Upper part, the mirror image (Sec. 3.5 runs it backwards: rows from the  */
+/* last to the first, each row read right to left): with u^_it = u_it/u_ii, */
 /*   gamma_it = u^_it - sum_{i<h<t} u^_ih gamma_ht,                          */
 /* rows n-1..0, pivots h descending; stored value -gamma_it.                 */
 /*                                                                           */
