@@ -7,6 +7,9 @@
   residual; without preconditioning GMRES(m >= n) terminates within n steps.
 * Adjoint: lambda solves A^T lambda = g (dense check), and the chain rule
   through the matrix assembly matches central finite differences.
+* Mat-vec and transpose: exact on integer values against the dense product;
+  the CSR transpose equals the dense transpose and, applied twice, gives the
+  matrix back.
 """
 import math
 
@@ -225,3 +228,32 @@ def test_bicgstab_zero_rhs_and_nonconvergence():
     st, x, it, rel, half = oracle.bicgstab(A.n, A.rowptr, A.colind, A.val, b, rtol=1e-14,
                                            maxit=3)
     assert st == oracle.ENOCONV and it == 3
+
+
+def test_spmv_exact_on_integers():
+    """y = A x with small integer entries: every product and partial sum is
+    exact, so the result equals the dense product exactly, whatever the
+    order."""
+    A = W.random_sparse(300, 0.05, 21, dominance=None)
+    key = W.stream_key(21, "int")
+    ival = np.floor(W.uniform(key, np.arange(A.nnz), -50, 50))
+    x = np.floor(W.uniform(W.stream_key(22, "int"), np.arange(A.n), -50, 50))
+    B = W.CSR(A.n, A.rowptr, A.colind, ival)
+    y = oracle.spmv(A.n, B.rowptr, B.colind, B.val, x)
+    assert np.array_equal(y, W.csr_to_dense(B) @ x)
+    # an empty row gives +0.0
+    E = W.CSR(2, np.array([0, 0, 1]), np.array([1], np.int32), np.array([3.0]))
+    assert np.array_equal(oracle.spmv(2, E.rowptr, E.colind, E.val, np.array([2.0, 5.0])),
+                          np.array([0.0, 15.0]))
+
+
+def test_transpose_is_exact_and_involutive():
+    A = W.random_sparse(200, 0.07, 23, dominance=None)
+    trp, tci, tv = oracle.transpose(A.n, A.rowptr, A.colind, A.val)
+    T = W.CSR(A.n, trp, tci, tv)
+    assert np.array_equal(W.csr_to_dense(T), W.csr_to_dense(A).T)
+    for i in range(A.n):  # rows of the transpose sorted by original row
+        assert np.all(np.diff(tci[trp[i]:trp[i + 1]]) > 0)
+    rrp, rci, rv = oracle.transpose(A.n, trp, tci, tv)
+    assert np.array_equal(rrp, A.rowptr) and np.array_equal(rci, A.colind)
+    assert np.array_equal(rv, A.val)
