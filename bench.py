@@ -36,6 +36,25 @@ sys.path.insert(0, ROOT)
 
 METRIC = "ILU(k) factor+apply ms & HBM GB/s (% peak); batched/adjoint vs plain, 1e-8 res"
 L2_BYTES = 129 * 1024 * 1024
+HBM_NOMINAL_GBS = 7900.0  # GB300 HBM3e, nominal
+
+
+def host_cpu(cpuinfo="/proc/cpuinfo"):
+    """The host the CPU baseline ran on: architecture, CPU model (when
+    /proc/cpuinfo names one) and the number of cores."""
+    import platform
+    fields = {}
+    try:
+        with open(cpuinfo) as f:
+            for line in f:
+                key, _, val = line.partition(":")
+                fields.setdefault(key.strip().lower(), val.strip())
+    except OSError:
+        pass
+    model = fields.get("model name") or fields.get("cpu model")
+    if not model and "cpu part" in fields:  # Arm: implementer and part numbers
+        model = f"implementer {fields.get('cpu implementer', '?')} part {fields['cpu part']}"
+    return {"arch": platform.machine(), "model": model or None, "nproc": os.cpu_count()}
 
 
 def parse():
@@ -320,7 +339,9 @@ def ours(args):
                    "parallelism": "replicas" if world > 1 else "single"},
         "roofline": {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 3), "peak": hbm,
                      "unit": "GB/s", "frac": round(achieved / hbm, 6), "traffic": traffic,
-                     "alg_bytes_per_launch": ab[kinds[dom]], "peak_source": peak_src},
+                     "alg_bytes_per_launch": ab[kinds[dom]], "peak_source": peak_src,
+                     "nominal_peak": HBM_NOMINAL_GBS,
+                     "nominal_frac": round(achieved / HBM_NOMINAL_GBS, 6)},
         "e2e": {"value": round(ms_e2e, 4), "unit": "ms", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
@@ -370,7 +391,8 @@ def cpu_baseline(Pb, steps, fv_gpu=None, x_gpu=None):
                   "oracle_iters": it}
     return ({"value": round(ms, 2), "unit": "ms", "cores": 1, "kind": "oracle",
              "sample": f"{len(ts)} full steps (pattern check + symbolic + numeric + GMRES, "
-                       f"fixed-tree dots) of the same workload, median"}, parity)
+                       f"fixed-tree dots) of the same workload, median",
+             "host": host_cpu()}, parity)
 
 
 def reference(args):
@@ -393,7 +415,8 @@ def reference(args):
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": f"random_band_n{Pb.A.n}_hw2000_k{Pb.k}_gmres{Pb.restart}_rtol1e-8"},
            "cpu_baseline": {"value": round(ms, 3), "unit": "ms", "cores": 1, "kind": "oracle",
-                            "sample": "each step one full oracle pass of the workload"},
+                            "sample": "each step one full oracle pass of the workload",
+                            "host": host_cpu()},
            "e2e": {"value": round(ms, 3), "unit": "ms", "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)

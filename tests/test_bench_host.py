@@ -1,0 +1,37 @@
+"""Host-side parts of the benchmark on CPU: the oracle baseline it prints
+(timed steps, parity fields, host description) and the CPU description read
+from /proc/cpuinfo on both kinds of host."""
+import json
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def test_host_cpu_names_x86_and_arm_models(tmp_path):
+    x86 = tmp_path / "x86"
+    x86.write_text("processor\t: 0\nvendor_id\t: GenuineIntel\nmodel name\t: Some Xeon\n")
+    assert bench.host_cpu(str(x86))["model"] == "Some Xeon"
+    arm = tmp_path / "arm"
+    arm.write_text("processor\t: 0\nBogoMIPS\t: 2000.00\nCPU implementer\t: 0x41\n"
+                   "CPU architecture: 8\nCPU part\t: 0xd4f\n")
+    assert bench.host_cpu(str(arm))["model"] == "implementer 0x41 part 0xd4f"
+    h = bench.host_cpu(str(tmp_path / "missing"))
+    assert h["model"] is None and h["nproc"] >= 1 and h["arch"]
+
+
+def test_cpu_baseline_on_the_headline_workload():
+    """One oracle step of the n = 160,000 band matrix, as the bench line's
+    cpu_baseline reports it, with the parity fields filled from the oracle's
+    own results (so both mismatch counts are 0)."""
+    Pb = bench.workload(2)
+    F, x, it = bench.oracle_step(Pb)
+    cb, parity = bench.cpu_baseline(Pb, 1, F["val"], x)
+    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["unit"] == "ms"
+    assert cb["value"] > 0 and cb["host"]["nproc"] >= 1
+    assert parity == {"factor_ulp_mismatches": 0, "x_bit_mismatches": 0, "oracle_iters": it}
+    assert it == 4  # GMRES(50) with ILU(2) on this matrix
+    json.dumps({"cpu_baseline": cb, "parity": parity})

@@ -91,4 +91,5 @@ def test_reference_arm_under_torchrun_two_ranks():
     assert out["impl"] == "reference" and out["n_gpus"] == 2
     assert out["higher_is_better"] is False and out["value"] > 0
     assert out["cpu_baseline"]["kind"] == "oracle" and out["cpu_baseline"]["value"] == out["value"]
+    assert out["cpu_baseline"]["host"]["nproc"] >= 1
     assert out["e2e"]["h2d_bytes_per_step"] == 0 and out["e2e"]["d2h_bytes_per_step"] == 0
