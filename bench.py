@@ -169,6 +169,21 @@ def alg_bytes(n, nnzA, nnzF, nnzL):
     }
 
 
+def operand_stream_bytes(frp, fci, fdg):
+    """Bytes of pivot rows the numeric phase streams, re-reads included: for
+    every lower entry (i, h) of F, row h's strictly upper part (a 4-byte column
+    and an 8-byte value per entry).  Against the compulsory bytes it shows how
+    much of the pivot-row traffic L2 has to absorb."""
+    frp = np.asarray(frp, dtype=np.int64)
+    fci = np.asarray(fci, dtype=np.int64)
+    fdg = np.asarray(fdg, dtype=np.int64)
+    n = fdg.size
+    ustrict = frp[1:] - fdg - 1
+    rows = np.repeat(np.arange(n, dtype=np.int64), np.diff(frp))
+    lower = fci < rows
+    return int(12 * ustrict[fci[lower]].sum())
+
+
 def sources_digest():
     """Digest of the sweep kernels' sources, as stamped on measured traffic."""
     import hashlib
@@ -326,6 +341,8 @@ def ours(args):
     dur_s = per_kind[dom]["ms_per_launch"] / 1e3
     achieved = ab[kinds[dom]] / dur_s / 1e9
     traffic = measured_traffic(dom, Pb.k)
+    ob = operand_stream_bytes(frp, fci, fdg)
+    kn = "factor" if "factor" in per_kind else "numeric" if "numeric" in per_kind else None
 
     out = {
         "metric": METRIC, "value": round(ms, 4), "unit": "ms", "n_gpus": world,
@@ -344,6 +361,9 @@ def ours(args):
                      "nominal_frac": round(achieved / HBM_NOMINAL_GBS, 6)},
         "e2e": {"value": round(ms_e2e, 4), "unit": "ms", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
+        "operand_stream": {"kernel": kn, "bytes_per_launch": ob,
+                           "GBps": (round(ob / (per_kind[kn]["ms_per_launch"] / 1e3) / 1e9, 3)
+                                    if kn else None)},
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
         "gmres": {"iters": info.iters, "relres": info.relres,

@@ -35,3 +35,22 @@ def test_cpu_baseline_on_the_headline_workload():
     assert parity == {"factor_ulp_mismatches": 0, "x_bit_mismatches": 0, "oracle_iters": it}
     assert it == 4  # GMRES(50) with ILU(2) on this matrix
     json.dumps({"cpu_baseline": cb, "parity": parity})
+
+
+def test_operand_stream_bytes_against_a_loop():
+    import numpy as np
+
+    import oracle
+    from paper_0803_0048_gb300 import workloads as W
+    A = W.random_sparse(120, 0.05, 5)
+    F = oracle.factor(A, 2)
+    frp, fci, n = F["rowptr"], F["colind"], A.n
+    fdg = np.array([frp[i] + np.searchsorted(fci[frp[i]:frp[i + 1]], i) for i in range(n)],
+                   dtype=np.int64)
+    want = 0
+    for i in range(n):
+        for p in range(frp[i], fdg[i]):  # lower entries (i, h): row h's strictly upper part
+            h = fci[p]
+            want += 12 * (frp[h + 1] - fdg[h] - 1)
+    assert want > 0
+    assert bench.operand_stream_bytes(frp, fci.astype(np.int32), fdg) == want
