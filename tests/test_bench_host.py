@@ -54,3 +54,33 @@ def test_operand_stream_bytes_against_a_loop():
             want += 12 * (frp[h + 1] - fdg[h] - 1)
     assert want > 0
     assert bench.operand_stream_bytes(frp, fci.astype(np.int32), fdg) == want
+
+
+def test_bench_line_contract_with_stand_ins():
+    """bench.ours() end to end on CPU, the CUDA runtime and libiluk replaced
+    by stand-ins (tests/stand_in_bench.py): the one JSON line carries every
+    key of the contract, and the derived numbers follow from the inputs."""
+    import subprocess
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "tests", "stand_in_bench.py")],
+                       cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-3000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
+                "roofline", "e2e", "gpu_launches", "clocks", "operand_stream", "kernels"):
+        assert key in d, key
+    assert d["value"] == 119.0 and d["n_gpus"] == 1 and d["steps"] == 3
+    assert d["higher_is_better"] is False and d["dtype"] == "f64"
+    assert d["config"]["workload"].startswith("random_band_n160000")
+    assert d["gpu_launches"] == 59
+    rf = d["roofline"]
+    assert rf["kernel"] == "sweep_bwd" and rf["bound"] == "hbm" and rf["unit"] == "GB/s"
+    assert abs(rf["achieved"] - rf["alg_bytes_per_launch"] / 11.25e-3 / 1e9) < 1e-3
+    assert abs(rf["frac"] - rf["achieved"] / rf["peak"]) < 1e-5
+    assert abs(rf["nominal_frac"] - rf["achieved"] / 7900.0) < 1e-5
+    assert d["e2e"]["h2d_bytes_per_step"] == 160001 * 8 + 1_600_000 * 12 + 160000 * 8
+    assert d["e2e"]["d2h_bytes_per_step"] == 160000 * 8
+    assert d["operand_stream"]["kernel"] == "factor"
+    assert d["operand_stream"]["bytes_per_launch"] > 10 * d["kernels"]["factor"]["alg_bytes_per_launch"]
