@@ -27,6 +27,7 @@ _lib = None
 OK, EINVAL, EPATTERN, ENODIAG, EZEROPIVOT, ENONFINITE, ENOMEM, ENOCONV = 0, 1, 2, 3, 4, 5, 6, 8
 PREC_NONE, PREC_ILU, PREC_IILU = 0, 1, 2
 DOT_SEQ, DOT_TREE = 0, 1
+UPDATE_Z, UPDATE_MVY = 0, 1  # how a GMRES cycle ends: x += Z y, or x += M^-1 (V y)
 
 
 def build(force: bool = False) -> str:
@@ -64,6 +65,8 @@ def _load():
         lib.orc_spmv.argtypes = [i64, P, P, P, P, P]
         lib.orc_gmres.argtypes = [i64, P, P, P, i32, i32, P, P, P, P, P, i32, C.c_double, i32,
                                   i32, P]
+        lib.orc_gmres_update.argtypes = [i64, P, P, P, i32, i32, P, P, P, P, P, i32, C.c_double,
+                                         i32, i32, i32, P]
         lib.orc_adjoint.argtypes = [i64, P, P, P, P, P, P, P, P, P, P, i32, C.c_double, i32,
                                     i32, P]
         lib.orc_bicgstab.argtypes = [i64, P, P, P, i32, P, P, P, P, P, C.c_double, i32, i32, P]
@@ -204,11 +207,14 @@ def spmv(n, rp, ci, v, x):
 
 
 def gmres(n, arp, aci, av, b, prec_kind=PREC_NONE, F=None, restart=30, rtol=1e-8, maxit=10000,
-          dotmode=DOT_SEQ, prec_transpose=False):
+          dotmode=DOT_SEQ, prec_transpose=False, update=UPDATE_Z):
     """Right-preconditioned restarted GMRES(m), x0 = 0.
 
     ``F`` is (rowptr, colind, values) of the factors (ILU), their transpose
-    (ILU with prec_transpose), or the TPIILU array g (IILU).
+    (ILU with prec_transpose), or the TPIILU array g (IILU).  ``update``:
+    UPDATE_Z ends a cycle with x += Z y on the kept preconditioned basis (the
+    flexible form); UPDATE_MVY with x += M^-1 (V y) (the textbook form of
+    right preconditioning, Sec. 2's A U~^-1 L~^-1).
     Returns (status, x, iterations, relres, cycles)."""
     lib = _load()
     arp, aci, av, b = _i64(arp), _i32(aci), _f64(av), _f64(b)
@@ -218,10 +224,11 @@ def gmres(n, arp, aci, av, b, prec_kind=PREC_NONE, F=None, restart=30, rtol=1e-8
         frp = fci = fv = None
     else:
         frp, fci, fv = _i64(F[0]), _i32(F[1]), _f64(F[2])
-    st = lib.orc_gmres(n, _p(arp), _p(aci), _p(av), prec_kind, int(prec_transpose),
-                       _p(frp) if frp is not None else None, _p(fci) if fci is not None else None,
-                       _p(fv) if fv is not None else None, _p(b), _p(x), restart, rtol, maxit,
-                       dotmode, _p(info))
+    st = lib.orc_gmres_update(n, _p(arp), _p(aci), _p(av), prec_kind, int(prec_transpose),
+                              _p(frp) if frp is not None else None,
+                              _p(fci) if fci is not None else None,
+                              _p(fv) if fv is not None else None, _p(b), _p(x), restart, rtol,
+                              maxit, dotmode, int(update), _p(info))
     return st, x[:n].copy(), int(info[0]), float(info[1]), int(info[2])
 
 

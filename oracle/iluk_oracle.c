@@ -503,11 +503,21 @@ static void prec_apply(const orc_prec *M, int64_t n, const double *v, double *z)
 }
 
 /* info_out: [0] iterations, [1] true relative residual, [2] cycles.        */
-int orc_gmres(int64_t n, const int64_t *arp, const int32_t *aci, const double *av,
-              int prec_kind, int prec_transpose,
-              const int64_t *frp, const int32_t *fci, const double *fv,
-              const double *b, double *x, int m, double rtol, int maxit, int dotmode,
-              double *info_out)
+/* update selects how a cycle ends (both are right-preconditioned GMRES,    */
+/* equal in exact arithmetic for a fixed M; they round differently):        */
+/*   ORC_UPDATE_Z:   x = x + Z y, Z = the preconditioned basis z_j = M^-1 v_j */
+/*                   kept during the cycle (the flexible form, Saad 1993);   */
+/*   ORC_UPDATE_MVY: x = x + M^-1 (V y), only V kept (the textbook form of   */
+/*                   right preconditioning, Saad & Schultz 1986).            */
+/* In both, each entry of the combination is summed over j in order from    */
+/* +0.0, one rounding per product and per addition.                          */
+#define ORC_UPDATE_Z 0
+#define ORC_UPDATE_MVY 1
+int orc_gmres_update(int64_t n, const int64_t *arp, const int32_t *aci, const double *av,
+                     int prec_kind, int prec_transpose,
+                     const int64_t *frp, const int32_t *fci, const double *fv,
+                     const double *b, double *x, int m, double rtol, int maxit, int dotmode,
+                     int update, double *info_out)
 {
   orc_prec M = { prec_kind, prec_transpose, frp, fci, fv };
   if (m < 1 || n < 0) return ORC_EINVAL;
@@ -579,23 +589,40 @@ int orc_gmres(int64_t n, const int64_t *arp, const int32_t *aci, const double *a
       }
       if (fabs(gv[j + 1]) / bnorm <= rtol || iters >= maxit || breakdown) break;
     }
-    /* y = H^-1 g (back substitution), u = Z y, x = x + u */
+    /* y = H^-1 g (back substitution), then u = Z y and x = x + u, or      */
+    /* u = V y and x = x + M^-1 u                                          */
     for (int i = jend; i >= 0; --i) {
       double s = gv[i];
       for (int l = i + 1; l <= jend; ++l) { double prod = H[i * m + l] * yv[l]; s = s - prod; }
       yv[i] = s / H[i * m + i];
     }
+    const double *Bas = update == ORC_UPDATE_MVY ? V : Z;
     for (int64_t q = 0; q < n; ++q) {
       double s = 0.0;
-      for (int j = 0; j <= jend; ++j) { double prod = yv[j] * Z[(size_t)j * N + q]; s = s + prod; }
+      for (int j = 0; j <= jend; ++j) { double prod = yv[j] * Bas[(size_t)j * N + q]; s = s + prod; }
       u[q] = s;
     }
-    for (int64_t q = 0; q < n; ++q) x[q] = x[q] + u[q];
+    if (update == ORC_UPDATE_MVY) {
+      prec_apply(&M, n, u, w);
+      for (int64_t q = 0; q < n; ++q) x[q] = x[q] + w[q];
+    } else {
+      for (int64_t q = 0; q < n; ++q) x[q] = x[q] + u[q];
+    }
   }
 done:
   info_out[0] = iters; info_out[1] = relres; info_out[2] = cycles;
   free(V); free(Z); free(H); free(cs); free(sn); free(gv); free(yv); free(r); free(w); free(u);
   return status;
+}
+
+int orc_gmres(int64_t n, const int64_t *arp, const int32_t *aci, const double *av,
+              int prec_kind, int prec_transpose,
+              const int64_t *frp, const int32_t *fci, const double *fv,
+              const double *b, double *x, int m, double rtol, int maxit, int dotmode,
+              double *info_out)
+{
+  return orc_gmres_update(n, arp, aci, av, prec_kind, prec_transpose, frp, fci, fv, b, x, m,
+                          rtol, maxit, dotmode, ORC_UPDATE_Z, info_out);
 }
 
 /* ------------------------------------------------------------------------ */

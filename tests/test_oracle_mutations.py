@@ -71,8 +71,13 @@ MUTANTS = {
     "residual_sign": ("r[i] = b[i] - w[i];", "r[i] = w[i] - b[i];"),
     "mgs_adds": ("double prod = hij * vi[q]; w[q] = w[q] - prod;",
                  "double prod = hij * vi[q]; w[q] = w[q] + prod;"),
-    "update_forgets_preconditioner": ("double prod = yv[j] * Z[(size_t)j * N + q];",
-                                      "double prod = yv[j] * V[(size_t)j * N + q];"),
+    "update_forgets_preconditioner": ("const double *Bas = update == ORC_UPDATE_MVY ? V : Z;",
+                                      "const double *Bas = V;"),
+    "mvy_update_combines_z": ("const double *Bas = update == ORC_UPDATE_MVY ? V : Z;",
+                              "const double *Bas = Z;"),
+    "mvy_update_skips_preconditioner": ("""      prec_apply(&M, n, u, w);
+      for (int64_t q = 0; q < n; ++q) x[q] = x[q] + w[q];""",
+                                        """      for (int64_t q = 0; q < n; ++q) x[q] = x[q] + u[q];"""),
     "back_substitution_transposed": ("double prod = H[i * m + l] * yv[l];",
                                      "double prod = H[l * m + i] * yv[l];"),
     "givens_cos_sin_swapped": ("cs[j] = a / rr; sn[j] = c / rr;", "cs[j] = c / rr; sn[j] = a / rr;"),
@@ -183,6 +188,16 @@ def pins_pass():
         Ad = W.csr_to_dense(A)
         if st != 0 or np.linalg.norm(x - np.linalg.solve(Ad, b)) > 1e-9 * np.linalg.norm(x):
             raise AssertionError("gmres")
+        # the textbook update x += M^-1 (V y), over several restart cycles:
+        # the same iterates as x += Z y in exact arithmetic, so the same
+        # iteration counts and the same x to rounding level
+        runs = [oracle.gmres(n, A.rowptr, A.colind, A.val, b, oracle.PREC_ILU,
+                             (F["rowptr"], F["colind"], F["val"]), 4, 1e-12, update=u)
+                for u in (oracle.UPDATE_Z, oracle.UPDATE_MVY)]
+        (stz, xz, itz, _, cycz), (st2, x2, it2, _, cyc2) = runs
+        if st2 != 0 or cyc2 < 2 or (it2, cyc2) != (itz, cycz) or \
+                np.linalg.norm(x2 - xz) > 1e-10 * np.linalg.norm(xz):
+            raise AssertionError("gmres mvy")
         g = W.uniform(W.stream_key(7, "g"), np.arange(n), -1, 1)
         st, lam, gA, *_ = oracle.adjoint(n, A.rowptr, A.colind, A.val, F["rowptr"], F["colind"],
                                          F["val"], x, g, 20, 1e-12)
@@ -238,7 +253,8 @@ def test_every_planted_mistake_is_caught(name, monkeypatch):
         for attr in ("orc_check_pattern", "orc_symbolic", "orc_sym_status", "orc_sym_copy",
                      "orc_sym_free", "orc_numeric", "orc_lsolve", "orc_usolve", "orc_apply",
                      "orc_apply_t", "orc_iiluk_apply", "orc_iiluk_build", "orc_transpose",
-                     "orc_dot", "orc_spmv", "orc_gmres", "orc_adjoint", "orc_bicgstab"):
+                     "orc_dot", "orc_spmv", "orc_gmres", "orc_gmres_update", "orc_adjoint",
+                     "orc_bicgstab"):
             f_real, f_mut = getattr(real, attr), getattr(mutant, attr)
             f_mut.argtypes = f_real.argtypes
             f_mut.restype = f_real.restype

@@ -53,7 +53,8 @@ def test_exact_preconditioner_converges_in_one_step():
 
 @pytest.mark.parametrize("prec", ["none", "ilu", "iilu"])
 @pytest.mark.parametrize("mode", [oracle.DOT_SEQ, oracle.DOT_TREE])
-def test_gmres_matches_dense_solve(prec, mode):
+@pytest.mark.parametrize("update", [oracle.UPDATE_Z, oracle.UPDATE_MVY])
+def test_gmres_matches_dense_solve(prec, mode, update):
     A = W.conv_diff(12, 2, (20.0, 20.0))
     n = A.n
     b = W.uniform(W.stream_key(3, "b"), np.arange(n), -1, 1)
@@ -66,7 +67,7 @@ def test_gmres_matches_dense_solve(prec, mode):
         g = oracle.iiluk_build(n, F["rowptr"], F["colind"], F["val"])
         kind, Fa = oracle.PREC_IILU, (F["rowptr"], F["colind"], g)
     st, x, it, rel, cyc = oracle.gmres(n, A.rowptr, A.colind, A.val, b, kind, Fa, 20, 1e-12,
-                                       dotmode=mode)
+                                       dotmode=mode, update=update)
     assert st == oracle.OK
     Ad = W.csr_to_dense(A)
     ref = np.linalg.solve(Ad, b)
@@ -74,6 +75,44 @@ def test_gmres_matches_dense_solve(prec, mode):
     true_rel = np.linalg.norm(b - Ad @ x) / np.linalg.norm(b)
     assert rel <= 1e-12
     assert abs(rel - true_rel) <= 1e-3 * true_rel + 1e-15
+
+
+def test_update_forms_bit_identical_without_preconditioner():
+    # M = I: z_j = v_j, so x += Z y and x += M^-1 (V y) perform the same
+    # operations in the same order
+    A = W.conv_diff(10, 2, (20.0, 20.0))
+    b = W.uniform(W.stream_key(11, "b"), np.arange(A.n), -1, 1)
+    runs = [oracle.gmres(A.n, A.rowptr, A.colind, A.val, b, oracle.PREC_NONE, None, 7, 1e-10,
+                         update=u) for u in (oracle.UPDATE_Z, oracle.UPDATE_MVY)]
+    assert runs[0][0] == runs[1][0] == oracle.OK and runs[0][4] > 1
+    assert runs[0][2:] == runs[1][2:]
+    assert np.array_equal(runs[0][1].view(np.int64), runs[1][1].view(np.int64))
+
+
+@pytest.mark.parametrize("prec", ["ilu", "iilu"])
+def test_update_forms_agree_over_restarts(prec):
+    # With a fixed preconditioner both cycle ends give the same iterate in
+    # exact arithmetic; across several restarts they agree to rounding level
+    # and with the dense solve.
+    A = W.conv_diff(16, 2, (20.0, 20.0))
+    n = A.n
+    b = W.uniform(W.stream_key(12, "b"), np.arange(n), -1, 1)
+    F = oracle.factor(A, 1)
+    if prec == "ilu":
+        kind, Fa = oracle.PREC_ILU, (F["rowptr"], F["colind"], F["val"])
+    else:
+        g = oracle.iiluk_build(n, F["rowptr"], F["colind"], F["val"])
+        kind, Fa = oracle.PREC_IILU, (F["rowptr"], F["colind"], g)
+    out = {}
+    for u in (oracle.UPDATE_Z, oracle.UPDATE_MVY):
+        st, x, it, rel, cyc = oracle.gmres(n, A.rowptr, A.colind, A.val, b, kind, Fa, 6, 1e-12,
+                                           update=u)
+        assert st == oracle.OK and cyc >= 3
+        out[u] = x
+    ref = np.linalg.solve(W.csr_to_dense(A), b)
+    for x in out.values():
+        assert np.linalg.norm(x - ref) <= 1e-10 * np.linalg.norm(ref)
+    assert np.linalg.norm(out[oracle.UPDATE_Z] - out[oracle.UPDATE_MVY]) <= 1e-10 * np.linalg.norm(ref)
 
 
 def test_preconditioning_reduces_iterations():
