@@ -4,7 +4,11 @@
   levels, factors, one preconditioner application (the autotuned schedule),
   TPIILU and GMRES compared with the oracle element by element.
 * Random band n=160,000 with k=3 (87 million factor entries; the oracle needs
-  minutes): properties that hold at any size, on sampled rows -- the level of
+  minutes): bit for bit against SHA-256 digests of the oracle's pattern,
+  levels, factors, one application, TPIILU and GMRES, written by
+  tests/golden/make_band160k_k3.py (which calls only the oracle), through both
+  the two separate phases and the one-call factorization; and, as a second
+  check, properties that hold at any size, on sampled rows -- the level of
   every entry satisfies Def. 2.3's recurrence over the GPU's own earlier rows,
   (L~U~)_ij = a_ij on kept positions within the rounding bound, and
   L~U~y = p for the applied preconditioner.
@@ -141,3 +145,51 @@ def test_largest_case_properties_on_sampled_rows():
         lhs = uy(j) + sum(vj[q] * uy(int(cj[q])) for q in range(dj))
         scale = abs(uy(j)) + sum(abs(vj[q] * uy(int(cj[q]))) for q in range(dj))
         assert abs(lhs - p[j]) <= 1e-8 * max(scale, 1.0)
+
+
+def _sha(*arrays) -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for a in arrays:
+        a = a.detach().cpu().numpy() if isinstance(a, torch.Tensor) else a
+        h.update(np.ascontiguousarray(a).view(np.uint8).tobytes())
+    return h.hexdigest()
+
+
+@pytest.mark.parametrize("path", ["symbolic+numeric", "factor"])
+def test_band160k_k3_bit_exact_against_oracle_digests(path):
+    """Random band n=160,000 at k=3 (87 M factor entries) against the digests
+    the oracle wrote (tests/golden/make_band160k_k3.py): pattern, levels,
+    factors, one application of the preconditioner, TPIILU and GMRES, bit for
+    bit.  "factor" is the one-call iluk_factor, whose rows longer than its
+    combined launch's numeric slice send it through the two separate phases."""
+    import json
+    import os
+    import sys
+    gold_dir = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    want = json.load(open(os.path.join(gold_dir, "band160k_k3.json")))
+    sys.path.insert(0, gold_dir)
+    import make_band160k_k3 as G
+    Pb = W.random_band_160k(k=3)
+    A = Pb.A
+    rp, ci, av, b = dev(A.rowptr), dev(A.colind), dev(A.val), dev(Pb.b)
+    if path == "factor":
+        S, F = P.factor(rp, ci, av, 3)
+    else:
+        S = P.symbolic(rp, ci, 3)
+        F = P.numeric(S, av)
+    grp, gci, glev, _ = S.pattern()
+    assert int(grp[-1]) == want["nnz_F"]
+    assert _sha(grp, gci) == want["pattern"]
+    assert _sha(glev) == want["levels"]
+    assert _sha(F.values()) == want["values"]
+    y = F.apply(dev(G.apply_input(A.n)))
+    assert F.status() == 0
+    assert _sha(y) == want["apply"]
+    M = P.iiluk_build(F)
+    assert _sha(M.values()) == want["tpiilu"]
+    del M
+    x, info = P.gmres(rp, ci, av, b, F, restart=Pb.restart, rtol=Pb.rtol)
+    assert (info.iters, info.cycles) == (want["gmres_iters"], want["gmres_cycles"])
+    assert int(bits([info.relres])[0]) == want["gmres_relres_bits"]
+    assert _sha(x) == want["gmres_x"]
