@@ -148,6 +148,15 @@ def workload(k):
     return W.random_band_160k(k=k)
 
 
+def workload_config(Pb, nnzF, world):
+    """The config dict both arms print: the workload and its sizes."""
+    return {"workload": f"random_band_n{Pb.A.n}_hw2000_k{Pb.k}_gmres{Pb.restart}_rtol1e-8",
+            "n": Pb.A.n, "nnz_A": Pb.A.nnz, "nnz_F": int(nnzF), "k": Pb.k,
+            "restart": Pb.restart, "rtol": Pb.rtol,
+            "l2": f"inputs larger than L2: F is {(12 * nnzF) / 2**20:.0f} MiB > 129 MiB",
+            "parallelism": "replicas" if world > 1 else "single"}
+
+
 def alg_bytes(n, nnzA, nnzF, nnzL):
     """Compulsory bytes per launch of each kernel kind (each array touched once)."""
     nnzU = nnzF - nnzL
@@ -160,7 +169,7 @@ def alg_bytes(n, nnzA, nnzF, nnzL):
         # positions, the input read, the output written, the next buffer re-armed
         "sweep": 12 * nnzL + 8 * (n + 1) + 8 * n + 24 * n,
         # backward sweep: F's upper half with the diagonal, the same vectors, and the
-        # double-double reciprocals of the diagonal
+        # diagonal with its fixed-point reciprocals (16 bytes per row)
         "sweep_bwd": 12 * nnzU + 8 * (n + 1) + 8 * n + 24 * n + 16 * n,
         "spmv": 12 * nnzA + 8 * (n + 1) + 16 * n,
         # symbolic and numeric in one launch: the two phases' bytes
@@ -286,24 +295,24 @@ def ours(args):
     P.prof_enable(False)
     launches = (P.launch_count() - launches0) // args.steps
 
-    # end to end through the public API from pinned host buffers
+    # end to end through the C ABI's host-buffer call (iluk_solve_host): the
+    # inputs cross from pinned host memory and x comes back inside each call
     h_rp = torch.from_numpy(A.rowptr).pin_memory()
     h_ci = torch.from_numpy(A.colind).pin_memory()
     h_av = torch.from_numpy(A.val).pin_memory()
     h_b = torch.from_numpy(Pb.b).pin_memory()
     h_x = torch.empty(n, dtype=torch.float64).pin_memory()
-    d_rp, d_ci, d_av, d_b = (torch.empty_like(t, device=dev) for t in (h_rp, h_ci, h_av, h_b))
+    P.solve_host(h_rp, h_ci, h_av, h_b, Pb.k, Pb.restart, Pb.rtol, sched=sched[0], x=h_x)
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
-        for d, h in ((d_rp, h_rp), (d_ci, h_ci), (d_av, h_av), (d_b, h_b)):
-            d.copy_(h, non_blocking=True)
-        S2, F2, x2, info2 = step(d_rp, d_ci, d_av, d_b)
-        h_x.copy_(x2, non_blocking=True)
+        _, info2 = P.solve_host(h_rp, h_ci, h_av, h_b, Pb.k, Pb.restart, Pb.rtol,
+                                sched=sched[0], x=h_x)
     e1.record(stream)
     barrier()
     ms_e2e = e0.elapsed_time(e1) / args.steps
+    e2e_bits_equal = bool(torch.equal(h_x.view(torch.int64), x.cpu().view(torch.int64)))
     # every replica runs the same step: the slowest one sets both times
     ms, ms_e2e = ranks_max([ms, ms_e2e], dev, world)
     h2d = h_rp.numel() * 8 + h_ci.numel() * 4 + h_av.numel() * 8 + h_b.numel() * 8
@@ -349,18 +358,16 @@ def ours(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": f"random_band_n{n}_hw2000_k{Pb.k}_gmres{Pb.restart}_rtol1e-8",
-                   "n": n, "nnz_A": nnzA, "nnz_F": nnzF, "k": Pb.k, "restart": Pb.restart,
-                   "rtol": Pb.rtol, "depth_lower": depth[0], "depth_upper": depth[1],
-                   "l2": f"inputs larger than L2: F is {(12 * nnzF) / 2**20:.0f} MiB > 129 MiB",
-                   "parallelism": "replicas" if world > 1 else "single"},
+        "config": workload_config(Pb, nnzF, world),
+        "dag": {"depth_lower": depth[0], "depth_upper": depth[1]},
         "roofline": {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 3), "peak": hbm,
                      "unit": "GB/s", "frac": round(achieved / hbm, 6), "traffic": traffic,
                      "alg_bytes_per_launch": ab[kinds[dom]], "peak_source": peak_src,
                      "nominal_peak": HBM_NOMINAL_GBS,
                      "nominal_frac": round(achieved / HBM_NOMINAL_GBS, 6)},
         "e2e": {"value": round(ms_e2e, 4), "unit": "ms", "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h},
+                "d2h_bytes_per_step": d2h, "call": "iluk_solve_host (host buffers)",
+                "x_bits_equal_device_run": e2e_bits_equal},
         "operand_stream": {"kernel": kn, "bytes_per_launch": ob,
                            "GBps": (round(ob / (per_kind[kn]["ms_per_launch"] / 1e3) / 1e9, 3)
                                     if kn else None)},
@@ -422,18 +429,18 @@ def reference(args):
         return
     Pb = workload(args.k)
     for _ in range(args.warmup):
-        oracle_step(Pb)
+        F, _, _ = oracle_step(Pb)
     ts = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        oracle_step(Pb)
+        F, _, _ = oracle_step(Pb)
         ts.append(time.perf_counter() - t0)
     ms = 1e3 * sum(ts) / len(ts)
     out = {"impl": "reference", "metric": METRIC, "value": round(ms, 3), "unit": "ms",
            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": round(ms, 3), "higher_is_better": False, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": f"random_band_n{Pb.A.n}_hw2000_k{Pb.k}_gmres{Pb.restart}_rtol1e-8"},
+           "config": workload_config(Pb, F["rowptr"][-1], world),
            "cpu_baseline": {"value": round(ms, 3), "unit": "ms", "cores": 1, "kind": "oracle",
                             "sample": "each step one full oracle pass of the workload",
                             "host": host_cpu()},
@@ -501,19 +508,23 @@ def batched(args):
     B.set_schedule(*chosen)
     B.solve()
     res = B.results()
-    # the same items, one at a time through the single-instance path
+    # the same items, one at a time through the single-instance path; the
+    # results are compared after the timed loop
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
+    loop_out = []
     t0.record()
-    mism = 0
-    for (S, r, c, v, b), (_, _, _, xb), rr in zip(plain, items, res):
+    for (S, r, c, v, b) in plain:
         F = P.numeric(S, v)
         x, info = P.gmres(r, c, v, b, F, restart=30, rtol=1e-8, check=False)
-        mism += int((x.view(torch.int64) != xb.view(torch.int64)).sum().item())
-        mism += int(info.iters != rr.iters)
+        loop_out.append((x, info.iters))
     t1.record()
     torch.cuda.synchronize()
     loop_ms = t0.elapsed_time(t1)
+    mism = 0
+    for (x, iters), (_, _, _, xb), rr in zip(loop_out, items, res):
+        mism += int((x.view(torch.int64) != xb.view(torch.int64)).sum().item())
+        mism += int(iters != rr.iters)
     out = {"metric": METRIC, "value": round(ms, 3), "unit": "ms", "n_gpus": 1,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -533,7 +544,18 @@ def batched(args):
 
 def adjoint(args):
     """2D 256^2 diffusion-convection with per-cell theta: x = A(theta)^-1 b by
-    ILU(2)-GMRES(30), L = ||x - x_t||^2, dL/dtheta and dL/db by the adjoint."""
+    ILU(2)-GMRES(30) to 1e-8, L = ||x - x_t||^2, dL/dtheta and dL/db by the
+    adjoint (the forward's factors reused, transposed).
+
+    Two arms of the plain single-instance path on the same GPU, both timed:
+    * plain gradient: the same gradient by plain calls without factor reuse --
+      numeric ILU(2) of A, GMRES for x, then the explicit A^T (iluk_transpose),
+      its own numeric ILU(2) (its symbolic phase cached outside the timing,
+      the most favourable case for the plain path), GMRES for lambda, the
+      -lambda_i x_j scatter and autograd through the assembly;
+    * finite-difference loop: central differences need 2 n_theta plain
+      solves (numeric + GMRES); a sample of them is timed and the loop's time
+      is extrapolated from the measured mean (labelled as such)."""
     import torch
 
     import paper_0803_0048_gb300 as P
@@ -560,34 +582,99 @@ def adjoint(args):
         with torch.no_grad():
             return solver.solve(W.fd_values(Pt, th0, beta), bd)
 
+    # the plain path: A^T's pattern and symbolic phase fixed once
+    v0 = W.fd_values(Pt, th0, beta).detach()
+    trp, tci, _ = P.transpose(rp, ci, v0)
+    St = P.symbolic(trp, tci, 2)
+    plain_info = {}
+
+    def plain_gradient():
+        th = th0.clone().requires_grad_(True)
+        vals = W.fd_values(Pt, th, beta)
+        v = vals.detach()
+        F = P.numeric(solver.S, v)
+        x, info = P.gmres(rp, ci, v, bd, F, restart=30, rtol=1e-8)
+        _, _, tv = P.transpose(rp, ci, v)
+        Ft = P.numeric(St, tv)
+        lam, info_t = P.gmres(trp, tci, tv, 2.0 * (x - xtd), Ft, restart=30, rtol=1e-8)
+        gA = P.adjoint_scatter(rp, ci, lam, x)
+        (gth,) = torch.autograd.grad(vals, th, grad_outputs=gA)
+        plain_info["iters"] = (info.iters, info_t.iters)
+        return gth, lam
+
+    def plain_solve(th):
+        v = W.fd_values(Pt, th, beta)
+        F = P.numeric(solver.S, v)
+        return P.gmres(rp, ci, v, bd, F, restart=30, rtol=1e-8)[0]
+
     for _ in range(max(args.warmup, 1)):
         fwd_bwd()
         fwd_only()
+        plain_gradient()
     torch.cuda.synchronize()
     e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-    e[0].record()
-    for _ in range(args.steps):
-        fwd_bwd()
-    e[1].record()
-    for _ in range(args.steps):
-        fwd_only()
-    e[2].record()
-    torch.cuda.synchronize()
+    with ClockSampler(0) as clk:
+        e[0].record()
+        for _ in range(args.steps):
+            fwd_bwd()
+        e[1].record()
+        for _ in range(args.steps):
+            fwd_only()
+        e[2].record()
+        for _ in range(args.steps):
+            plain_gradient()
+        e[3].record()
+        torch.cuda.synchronize()
     ms_fb = e[0].elapsed_time(e[1]) / args.steps
     ms_f = e[1].elapsed_time(e[2]) / args.steps
+    ms_plain = e[2].elapsed_time(e[3]) / args.steps
+    # agreement of the two gradients (different preconditioners for A^T,
+    # both solved to 1e-8)
+    g_ours, lam_ours = fwd_bwd()
+    g_plain, lam_plain = plain_gradient()
+    rel_theta = float((g_ours - g_plain).norm() / g_plain.norm())
+    rel_lam = float((lam_ours - lam_plain).norm() / lam_plain.norm())
+    # finite differences: time a sample of the 2 n_theta plain solves
     n_theta = Pt.n
+    cells = [int(c) for c in np.linspace(0, n_theta - 1, 4)]
+    sample = []
+    for c in cells:
+        for sgn in (1.0, -1.0):
+            th = th0.clone()
+            th[c] += sgn * 1e-6 * th[c]
+            sample.append(th)
+    plain_solve(sample[0])
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record()
+    for th in sample:
+        plain_solve(th)
+    f1.record()
+    torch.cuda.synchronize()
+    ms_solve = f0.elapsed_time(f1) / len(sample)
+    fd_ms = 2 * n_theta * ms_solve
     out = {"metric": METRIC, "value": round(ms_fb, 3), "unit": "ms", "n_gpus": 1,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_fb, 3),
            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic",
            "config": {"workload": "adjoint_2d_256^2_k2_gmres30", "n": Pt.n,
-                      "n_theta": n_theta},
+                      "n_theta": n_theta, "rtol": 1e-8},
            "forward_only_ms": round(ms_f, 3),
            "backward_over_forward": round((ms_fb - ms_f) / ms_f, 3),
            "forward_iters": solver.last_forward.iters,
            "adjoint_iters": solver.last_backward.iters if solver.last_backward else None,
-           "loop_plain_gradient_ms_estimate": round(2 * n_theta * ms_f, 1),
-           "speedup_vs_loop": round(2 * n_theta * ms_f / ms_fb, 1)}
+           "plain_gradient": {"ms": round(ms_plain, 3), "measured": True,
+                              "what": "numeric ILU(2) of A + GMRES, explicit A^T + its own "
+                                      "numeric ILU(2) (symbolic cached) + GMRES, scatter, "
+                                      "autograd through the assembly",
+                              "iters_forward_adjoint": list(plain_info.get("iters", ())),
+                              "rel_diff_dtheta": rel_theta, "rel_diff_lambda": rel_lam},
+           "speedup_vs_plain_gradient": round(ms_plain / ms_fb, 3),
+           "fd_loop": {"solves": 2 * n_theta, "sampled_solves": len(sample),
+                       "ms_per_solve_measured": round(ms_solve, 3),
+                       "ms_extrapolated": round(fd_ms, 1), "extrapolated": True},
+           "speedup_vs_fd_loop_extrapolated": round(fd_ms / ms_fb, 1),
+           "clocks": clk.summary()}
     print(json.dumps(out), flush=True)
 
 

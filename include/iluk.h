@@ -306,10 +306,12 @@ int iluk_spmv(const iluk_pattern *A, const double *A_val, const double *x, doubl
 int iluk_dot(int64_t n, const double *x, const double *y, double *out, void *stream);
 
 /*
- * Elementwise q_i = a_i / b_i rounded to nearest, computed as the sweeps and
- * the transposed sweeps divide by the diagonal (Eq. triangleSolve's division
- * by u_ii): a double-double reciprocal of b_i, then one Markstein correction,
- * with IEEE division for operands outside [2^-400, 2^401) in magnitude.  The
+ * Elementwise q_i = a_i / b_i rounded to nearest, computed as the numeric
+ * phase forms its multipliers f_ih / f_hh (Eq. lufactor2) and as the sweeps
+ * divide by u_ii (Eq. triangleSolve): on the integer pipes, from a 64-bit
+ * fixed-point reciprocal of b_i (an fp32 seed refined by two Newton steps)
+ * and an exact remainder correction, with IEEE division for zero, subnormal,
+ * infinite and NaN operands and for quotients outside the normal range.  The
  * results must equal IEEE division bit for bit; this call exists so that the
  * method can be checked against it.  a, b, q: device double[n] (q may alias
  * neither).  ILUK_EINVAL on n < 0 or a null pointer with n > 0.  Asynchronous.
@@ -329,6 +331,33 @@ int iluk_div_rn(int64_t n, const double *a, const double *b, double *q, void *st
 int gmres_solve(const iluk_pattern *A, const double *A_val, int prec_kind, void *prec,
                 const double *b, double *x, int restart, double rtol, int maxit,
                 int transpose, iluk_info *info, void *stream);
+
+/*
+ * a6, a8. The same GMRES(m) with a choice of what a restart cycle keeps for
+ * its final update (the memory of the Krylov bases).  gmres_solve is
+ * gmres_solve_ex with ILUK_BASIS_AUTO.
+ *  ILUK_BASIS_STORE      keeps the preconditioned basis z_j = M^-1 v_j
+ *                        (m more vectors of n doubles) and ends a cycle with
+ *                        x += Z y (the flexible form, Saad 1993).
+ *  ILUK_BASIS_RECOMPUTE  keeps only V and, at the end of a cycle, applies M to
+ *                        each v_j again and accumulates Z y term by term in
+ *                        the same order: bit-identical to STORE, at the cost
+ *                        of up to m more applications of M per cycle.
+ *  ILUK_BASIS_AUTO       STORE when the m vectors take at most half of the
+ *                        device's free memory, else RECOMPUTE (same bits).
+ *  ILUK_BASIS_MINV_VY    keeps only V and ends a cycle with x += M^-1 (V y),
+ *                        the textbook form of right preconditioning (Sec. 2's
+ *                        A U~^-1 L~^-1): one more application of M per cycle;
+ *                        equal to the forms above in exact arithmetic, not in
+ *                        rounding.
+ * Other arguments, results and errors as gmres_solve (ILUK_EINVAL for an
+ * unknown basis).  Synchronous.
+ */
+enum { ILUK_BASIS_AUTO = 0, ILUK_BASIS_STORE = 1, ILUK_BASIS_RECOMPUTE = 2,
+       ILUK_BASIS_MINV_VY = 3 };
+int gmres_solve_ex(const iluk_pattern *A, const double *A_val, int prec_kind, void *prec,
+                   const double *b, double *x, int restart, double rtol, int maxit,
+                   int transpose, int basis, iluk_info *info, void *stream);
 
 /*
  * Preconditioned BiCGSTAB (van der Vorst 1992), the solver of the paper's
@@ -363,6 +392,33 @@ enum { ILUK_SOLVER_GMRES = 0, ILUK_SOLVER_BICGSTAB = 1 };
 int tpilu_solve(const iluk_pattern *A, const double *A_val, iluk_fac *F, iiluk *M, int solver,
                 const double *b, double *x, int m, double rtol, int iilu_maxit, int maxit,
                 int *used, iluk_info *info, void *stream);
+
+/*
+ * Explicit CSR transpose: t_rowptr (int64[n+1]), t_colind (int32[nnz]) and
+ * t_val (double[nnz]) receive A^T, columns ascending inside each row, values
+ * moved exactly.  The transposed solves build the same transposes internally
+ * (for A^T lambda = g, and of F for the (L~U~)^-T sweeps); this call gives
+ * them to a caller, e.g. to factor A^T on its own.  Caller-owned device
+ * buffers; A is not validated.  Asynchronous.
+ */
+int iluk_transpose(const iluk_pattern *A, const double *A_val, int64_t *t_rowptr,
+                   int32_t *t_colind, double *t_val, void *stream);
+
+/*
+ * a1-a6 in one call, from HOST buffers: rowptr (int64[n+1]), colind
+ * (int32[nnz]), val (double[nnz]) and b (double[n]) are host arrays (pinned
+ * memory lets the copies run at full speed; pageable memory works too), x
+ * (double[n]) is a host array that receives the solution.  The call copies
+ * the inputs to the device on `stream`, runs iluk_validate, iluk_factor(k)
+ * and gmres_solve(restart, rtol, maxit) preconditioned by the ILU(k) sweeps
+ * with sweep schedule `sched` (as iluk_set_schedule; ILUK_SCHED_AUTO times
+ * the schedules inside the call), copies x back and frees its device memory.
+ * Synchronous; statuses and info as the calls it makes (x is written even
+ * when GMRES returns ILUK_ENOCONV).
+ */
+int iluk_solve_host(int64_t n, int64_t nnz, const int64_t *rowptr, const int32_t *colind,
+                    const double *val, const double *b, double *x, int k, int restart,
+                    double rtol, int maxit, int sched, iluk_info *info, void *stream);
 
 /*
  * a8 helper. Gradient of a loss through x = A^-1 b with respect to the stored

@@ -15,6 +15,8 @@ LIB_PATH = os.path.join(HERE, "_build", "libiluk.so")
 
 OK, EINVAL, EPATTERN, ENODIAG, EZEROPIVOT, ENONFINITE, ENOMEM, ETIMEOUT, ENOCONV, ECUDA = range(10)
 PREC_NONE, PREC_ILU, PREC_IILU = 0, 1, 2
+# what a GMRES cycle keeps for its final update (gmres_solve_ex)
+BASIS = {"auto": 0, "store": 1, "recompute": 2, "minv_vy": 3}
 SOLVER_GMRES, SOLVER_BICGSTAB = 0, 1
 SCHED_AUTO, SCHED_FLAGS, SCHED_SINGLE_CTA, SCHED_CLUSTER, SCHED_WARP_GRID, SCHED_WARP_CLUSTER = 0, 1, 2, 3, 4, 5
 _SCHED_NAMES = ["auto", "lockstep_grid", "lockstep_cta", "lockstep_cluster", "warp_grid",
@@ -96,6 +98,9 @@ SIGNATURES = [
     ("iluk_dot", I, [I64, P, P, P, P]),
     ("iluk_div_rn", I, [I64, P, P, P, P]),
     ("gmres_solve", I, [P, P, I, P, P, P, I, D, I, I, P, P]),
+    ("gmres_solve_ex", I, [P, P, I, P, P, P, I, D, I, I, I, P, P]),
+    ("iluk_transpose", I, [P, P, P, P, P, P]),
+    ("iluk_solve_host", I, [I64, I64, P, P, P, P, P, I, I, D, I, I, P, P]),
     ("bicgstab_solve", I, [P, P, I, P, P, P, D, I, P, P]),
     ("tpilu_solve", I, [P, P, P, P, I, P, P, I, D, I, I, P, P, P]),
     ("iluk_adjoint_scatter", I, [P, P, P, P, P]),

@@ -280,8 +280,9 @@ def dot(x: torch.Tensor, y: torch.Tensor) -> torch.Tensor:
 
 
 def div_rn(a: torch.Tensor, b: torch.Tensor) -> torch.Tensor:
-    """a / b elementwise by the sweeps' division (double-double reciprocal
-    plus a Markstein correction); equal to IEEE division bit for bit."""
+    """a / b elementwise by the library's division (integer pipes: a
+    fixed-point reciprocal and an exact remainder correction), as the
+    numeric phase and the sweeps divide; equal to IEEE division bit for bit."""
     _vecs((a, a.numel(), "a"),
           (b, a.numel(), "b"))
     q = torch.empty_like(a)
@@ -290,10 +291,16 @@ def div_rn(a: torch.Tensor, b: torch.Tensor) -> torch.Tensor:
 
 
 def gmres(rowptr, colind, vals, b, prec=None, restart=30, rtol=1e-8, maxit=10000,
-          transpose=False, x=None, check=True):
+          transpose=False, x=None, check=True, basis="auto"):
     """a6: right-preconditioned GMRES(m) from x0 = 0.  ``prec`` is None, a
-    Factors (ILU(k) sweeps) or an IncompleteInverse (TPIILU).
-    Returns (x, info)."""
+    Factors (ILU(k) sweeps) or an IncompleteInverse (TPIILU).  ``basis``:
+    "store" keeps the preconditioned basis and ends a cycle with x += Z y;
+    "recompute" keeps only V and applies the preconditioner again at the end
+    of a cycle (same bits, less memory); "auto" (default) stores when the
+    basis takes at most half of the free device memory; "minv_vy" ends a
+    cycle with x += M^-1 (V y).  Returns (x, info)."""
+    if basis not in L.BASIS:
+        raise ValueError(f"basis must be one of {sorted(L.BASIS)}")
     A = CsrPattern(rowptr, colind)
     _vecs((vals, A.nnz, "values of A"),
           (b, A.n, "b"),
@@ -308,9 +315,9 @@ def gmres(rowptr, colind, vals, b, prec=None, restart=30, rtol=1e-8, maxit=10000
     else:
         raise TypeError("prec must be None, Factors or IncompleteInverse")
     info = L.Info()
-    st = L.load().gmres_solve(A.ref, _ptr(vals), kind, ph, _ptr(b), _ptr(xo), int(restart),
-                              float(rtol), int(maxit), int(transpose), C.byref(info),
-                              C.c_void_p(_stream()))
+    st = L.load().gmres_solve_ex(A.ref, _ptr(vals), kind, ph, _ptr(b), _ptr(xo), int(restart),
+                                 float(rtol), int(maxit), int(transpose), L.BASIS[basis],
+                                 C.byref(info), C.c_void_p(_stream()))
     if check and st != L.OK:
         raise IlukError(st, info, "gmres_solve")
     return xo, info
@@ -360,6 +367,45 @@ def tpilu_solve(rowptr, colind, vals, b, F, M=None, solver="gmres", restart=50, 
     if check and st != L.OK:
         raise IlukError(st, info, "tpilu_solve")
     return xo, info, ("iilu" if used.value == L.PREC_IILU else "ilu")
+
+
+def solve_host(rowptr, colind, vals, b, k, restart=30, rtol=1e-8, maxit=10000, sched=0,
+               x=None, check=True):
+    """a1-a6 from host memory in one C call (iluk_solve_host): CPU tensors in
+    (pinned memory copies fastest), x out on the host.  ``sched`` is a sweep
+    schedule (Factors.schedule() of an earlier solve, or 0 to autotune).
+    Returns (x, info)."""
+    n = rowptr.numel() - 1
+    nnz = colind.numel()
+    for t, dt, cnt, what in ((rowptr, torch.int64, n + 1, "rowptr"),
+                             (colind, torch.int32, nnz, "colind"),
+                             (vals, torch.float64, nnz, "values of A"),
+                             (b, torch.float64, n, "b"), (x, torch.float64, n, "x")):
+        if t is None:
+            continue
+        if t.device.type != "cpu" or t.dtype != dt or t.numel() != cnt or not t.is_contiguous():
+            raise ValueError(f"{what}: need a contiguous host {dt} tensor of {cnt} elements")
+    xo = torch.empty(n, dtype=torch.float64, pin_memory=b.is_pinned()) if x is None else x
+    info = L.Info()
+    st = L.load().iluk_solve_host(n, nnz, _ptr(rowptr), _ptr(colind), _ptr(vals), _ptr(b),
+                                  _ptr(xo), int(k), int(restart), float(rtol), int(maxit),
+                                  int(sched), C.byref(info), C.c_void_p(_stream()))
+    if check and st != L.OK:
+        raise IlukError(st, info, "iluk_solve_host")
+    return xo, info
+
+
+def transpose(rowptr, colind, vals):
+    """Explicit CSR transpose of A: (rowptr, colind, vals) of A^T on the
+    device, columns ascending in each row, values moved exactly."""
+    A = CsrPattern(rowptr, colind)
+    _vecs((vals, A.nnz, "values of A"))
+    trp = torch.empty(A.n + 1, dtype=torch.int64, device=rowptr.device)
+    tci = torch.empty(A.nnz, dtype=torch.int32, device=rowptr.device)
+    tv = torch.empty(A.nnz, dtype=torch.float64, device=rowptr.device)
+    _call(L.load().iluk_transpose, A.ref, _ptr(vals), _ptr(trp), _ptr(tci), _ptr(tv),
+          C.c_void_p(_stream()), what="iluk_transpose")
+    return trp, tci, tv
 
 
 def adjoint_scatter(rowptr, colind, lam, x, out=None):

@@ -20,9 +20,15 @@ class IlukSolver:
     """A fixed pattern and the solver settings; the symbolic phase runs once."""
 
     def __init__(self, rowptr: torch.Tensor, colind: torch.Tensor, k: int, restart: int = 30,
-                 rtol: float = 1e-8, maxit: int = 10000):
+                 rtol: float = 1e-8, maxit: int = 10000, basis: str = "auto"):
+        # basis: what each GMRES cycle (forward and adjoint) keeps for its
+        # final update.  "store" keeps the m preconditioned basis vectors;
+        # "recompute" keeps only the Krylov basis and applies the factors
+        # again at the end of a cycle (same bits, m vectors less memory);
+        # "auto" stores them when they fit in half of the free device memory.
         self.rowptr, self.colind = rowptr, colind
         self.k, self.restart, self.rtol, self.maxit = k, restart, rtol, maxit
+        self.basis = basis
         self.S = api.symbolic(rowptr, colind, k)
         self.last_forward = None
         self.last_backward = None
@@ -38,7 +44,7 @@ class IlukSolve(torch.autograd.Function):
         b_d = b.detach().contiguous()
         F = api.numeric(solver.S, vals_d)
         x, info = api.gmres(solver.rowptr, solver.colind, vals_d, b_d, F, restart=solver.restart,
-                            rtol=solver.rtol, maxit=solver.maxit)
+                            rtol=solver.rtol, maxit=solver.maxit, basis=solver.basis)
         solver.last_forward = info
         ctx.solver = solver
         ctx.F = F
@@ -50,7 +56,8 @@ class IlukSolve(torch.autograd.Function):
         vals_d, x = ctx.saved_tensors
         s = ctx.solver
         lam, info = api.gmres(s.rowptr, s.colind, vals_d, gx.detach().contiguous(), ctx.F,
-                              restart=s.restart, rtol=s.rtol, maxit=s.maxit, transpose=True)
+                              restart=s.restart, rtol=s.rtol, maxit=s.maxit, transpose=True,
+                              basis=s.basis)
         s.last_backward = info
         gA = api.adjoint_scatter(s.rowptr, s.colind, lam, x)
         return gA, lam, None

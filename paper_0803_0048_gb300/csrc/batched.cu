@@ -128,7 +128,7 @@ __device__ void cta_sweep(const BatchItemDev &it, const double *fv, const double
           s = __dsub_rn(s, __dmul_rn(fv[pq], out[it.fci[pq]]));
         }
       }
-      if (row >= 0) out[row] = FORWARD ? s : __ddiv_rn(s, fv[d]);
+      if (row >= 0) out[row] = FORWARD ? s : div_int(s, fv[d]);
     }
     __syncthreads();
   }
@@ -220,7 +220,7 @@ __device__ bool cta_sweep_spin(const BatchItemDev &it, const double *fv, const d
       break;
     }
     if (row >= 0) {
-      double y = FORWARD ? s : __ddiv_rn(s, fv[d]);
+      double y = FORWARD ? s : div_int(s, fv[d]);
       if ((unsigned long long)__double_as_longlong(y) == kSpinPending)
         y = __longlong_as_double(0x7FF8000000000000ll);  // never the marker
       st_cta_f64(&out[row], y);
@@ -274,7 +274,7 @@ __device__ bool cta_numeric(const BatchItemDev &it, double *fv, double *svals, i
       for (int q = 0; q < dp; ++q) {
         const int h = rc[q];
         const int64_t hd = it.fdiag[h];
-        const double fih = __ddiv_rn(rv[q], fv[hd]);
+        const double fih = div_int(rv[q], fv[hd]);
         __syncwarp();
         if (lane == 0) rv[q] = fih;
         __syncwarp();
@@ -315,8 +315,10 @@ __device__ bool cta_apply(const BatchItemDev &it, const double *fv, const double
 
 template <int NT>
 __device__ void cta_vec_div(int64_t n, const double *x, double den, double *y) {
-  if (den != 0.0)
-    for (int64_t i = threadIdx.x; i < n; i += NT) y[i] = __ddiv_rn(x[i], den);
+  if (den != 0.0) {
+    const DivPrep pd = div_prep(den);  // one reciprocal, n quotients
+    for (int64_t i = threadIdx.x; i < n; i += NT) y[i] = div_fin(x[i], pd);
+  }
   __syncthreads();
 }
 

@@ -1056,6 +1056,24 @@ int iluk_dot(int64_t n, const double *x, const double *y, double *out, void *str
   return ILUK_OK;
 }
 
+int iluk_transpose(const iluk_pattern *A, const double *A_val, int64_t *t_rowptr,
+                   int32_t *t_colind, double *t_val, void *stream) {
+  iluk_info *info = nullptr;
+  if (!pattern_args_ok(A) || !t_rowptr || (A->nnz > 0 && (!A_val || !t_colind || !t_val)))
+    return ILUK_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  int32_t *cursor = nullptr;
+  int64_t *scan_tmp = nullptr;
+  auto scratch = at_scope_exit([&] { dfree(cursor, s); dfree(scan_tmp, s); });
+  if (A->n > 0) {
+    CK(dalloc(&cursor, A->n, s));
+    CK(dalloc(&scan_tmp, scan_tmp_elems(A->n), s));
+  }
+  CK(launch_transpose(A->n, A->nnz, A->rowptr, A->colind, A_val, t_rowptr, t_colind, t_val,
+                      nullptr, cursor, scan_tmp, s));
+  return ILUK_OK;
+}
+
 int iluk_adjoint_scatter(const iluk_pattern *A, const double *lambda, const double *x, double *gA,
                          void *stream) {
   iluk_info *info = nullptr;
@@ -1293,8 +1311,16 @@ int iluk_batch_results(iluk_batch *B, iluk_info *infos, void *stream) {
 int gmres_solve(const iluk_pattern *A, const double *A_val, int prec_kind, void *prec,
                 const double *b, double *x, int m, double rtol, int maxit, int transpose,
                 iluk_info *info, void *stream) {
+  return gmres_solve_ex(A, A_val, prec_kind, prec, b, x, m, rtol, maxit, transpose,
+                        ILUK_BASIS_AUTO, info, stream);
+}
+
+int gmres_solve_ex(const iluk_pattern *A, const double *A_val, int prec_kind, void *prec,
+                   const double *b, double *x, int m, double rtol, int maxit, int transpose,
+                   int basis, iluk_info *info, void *stream) {
   info_init(info);
   if (!pattern_args_ok(A) || m < 1 || maxit < 0) return fail(info, ILUK_EINVAL);
+  if (basis < ILUK_BASIS_AUTO || basis > ILUK_BASIS_MINV_VY) return fail(info, ILUK_EINVAL);
   if ((A->n > 0 && (!b || !x)) || (A->nnz > 0 && !A_val)) return fail(info, ILUK_EINVAL);
   if (prec_kind != ILUK_PREC_NONE && !prec) return fail(info, ILUK_EINVAL);
   if (transpose && prec_kind == ILUK_PREC_IILU) return fail(info, ILUK_EINVAL);
@@ -1312,8 +1338,11 @@ int gmres_solve(const iluk_pattern *A, const double *A_val, int prec_kind, void 
   double *tv = nullptr;
   int32_t *cursor = nullptr;
   int64_t *scan_tmp = nullptr;
-  // Z keeps the preconditioned basis z_j = M^-1 v_j of a cycle, which ends
-  // with x += Z y (the flexible-GMRES form: no extra application of M)
+  // With ILUK_BASIS_STORE, Z keeps the preconditioned basis z_j = M^-1 v_j
+  // of a cycle, which ends with x += Z y (the flexible-GMRES form: no extra
+  // application of M).  Without it only V is kept: RECOMPUTE applies M to
+  // each v_j again at the end of the cycle and accumulates Z y in the same
+  // order (the same bits, m more applications), MINV_VY forms x += M^-1 (V y).
   double *V = nullptr, *Z = nullptr, *w = nullptr, *u = nullptr, *Hd = nullptr, *dsc = nullptr,
          *dy = nullptr;
   DotScratch ds{};
@@ -1337,8 +1366,16 @@ int gmres_solve(const iluk_pattern *A, const double *A_val, int prec_kind, void 
     ov = tv;
   }
   const int64_t ldv = n > 0 ? n : 1;
+  if (basis == ILUK_BASIS_AUTO) {
+    // keep Z only when its m vectors take at most half of the free memory
+    size_t free_b = 0, total_b = 0;
+    CK(cudaMemGetInfo(&free_b, &total_b));
+    const double need = (double)ldv * (double)m * sizeof(double);
+    basis = need <= 0.5 * (double)free_b ? ILUK_BASIS_STORE : ILUK_BASIS_RECOMPUTE;
+  }
+  const bool store_z = basis == ILUK_BASIS_STORE;
   CK(dalloc(&V, (size_t)ldv * (m + 1), s));
-  CK(dalloc(&Z, (size_t)ldv * m, s));
+  CK(dalloc(&Z, store_z ? (size_t)ldv * m : (size_t)ldv, s));
   CK(dalloc(&w, ldv, s));
   CK(dalloc(&u, ldv, s));
   CK(dalloc(&Hd, (size_t)(m + 1) * m, s));
@@ -1396,7 +1433,7 @@ int gmres_solve(const iluk_pattern *A, const double *A_val, int prec_kind, void 
       for (int j = 0; j < m; ++j) {
         double *vj = V + (size_t)j * ldv;
         double *hc = Hd + (size_t)j * (m + 1);  // column j of H
-        double *zj = Z + (size_t)j * ldv;
+        double *zj = store_z ? Z + (size_t)j * ldv : Z;
         CK(precond(vj, zj));
         CK(launch_spmv(n, orp, oci, ov, zj, w, nullptr, s));
         CK(launch_dot(n, w, V, hc + 0, 0, ds, s));
@@ -1444,8 +1481,22 @@ int gmres_solve(const iluk_pattern *A, const double *A_val, int prec_kind, void 
         yv[i] = sacc / H[(size_t)i * m + i];
       }
       CK(cudaMemcpyAsync(dy, yv.data(), (jend + 1) * sizeof(double), cudaMemcpyHostToDevice, s));
-      CK(launch_combine(n, Z, ldv, dy, jend + 1, u, s));
-      CK(launch_add(n, x, u, s));
+      if (store_z) {
+        CK(launch_combine(n, Z, ldv, dy, jend + 1, u, s));
+        CK(launch_add(n, x, u, s));
+      } else if (basis == ILUK_BASIS_RECOMPUTE) {
+        // u = sum_j y_j z_j from +0.0, one term at a time, z_j recomputed
+        CK(cudaMemsetAsync(u, 0, n * sizeof(double), s));
+        for (int j = 0; j <= jend; ++j) {
+          CK(precond(V + (size_t)j * ldv, Z));
+          CK(launch_acc_scaled(n, u, dy + j, Z, s));
+        }
+        CK(launch_add(n, x, u, s));
+      } else {  // ILUK_BASIS_MINV_VY
+        CK(launch_combine(n, V, ldv, dy, jend + 1, u, s));
+        CK(precond(u, Z));
+        CK(launch_add(n, x, Z, s));
+      }
     }
   }
   CK(cudaStreamSynchronize(s));
@@ -1599,6 +1650,52 @@ int bicgstab_solve(const iluk_pattern *A, const double *A_val, int prec_kind, vo
     info->row = prow;
   }
   return status;
+}
+
+// One solve from host buffers: the arrays cross to the device and x comes
+// back inside the call, around the same device calls a caller would make
+// (pattern check, symbolic + numeric, GMRES with the ILU(k) sweeps).
+int iluk_solve_host(int64_t n, int64_t nnz, const int64_t *rowptr, const int32_t *colind,
+                    const double *val, const double *b, double *x, int k, int restart,
+                    double rtol, int maxit, int sched, iluk_info *info, void *stream) {
+  info_init(info);
+  if (n < 0 || nnz < 0 || !rowptr || (nnz > 0 && (!colind || !val)) || (n > 0 && (!b || !x)) ||
+      k < 0 || k > 250 || restart < 1 || maxit < 0)
+    return fail(info, ILUK_EINVAL);
+  cudaStream_t s = (cudaStream_t)stream;
+  int64_t *d_rp = nullptr;
+  int32_t *d_ci = nullptr;
+  double *d_v = nullptr, *d_b = nullptr, *d_x = nullptr;
+  iluk_sym *S = nullptr;
+  iluk_fac *F = nullptr;
+  auto scratch = at_scope_exit([&] {
+    if (F) iluk_fac_destroy(F);
+    if (S) iluk_sym_destroy(S);
+    dfree(d_rp, s); dfree(d_ci, s); dfree(d_v, s); dfree(d_b, s); dfree(d_x, s);
+  });
+  const size_t nn = n > 0 ? (size_t)n : 1, nz = nnz > 0 ? (size_t)nnz : 1;
+  CK(dalloc(&d_rp, (size_t)n + 1, s));
+  CK(dalloc(&d_ci, nz, s));
+  CK(dalloc(&d_v, nz, s));
+  CK(dalloc(&d_b, nn, s));
+  CK(dalloc(&d_x, nn, s));
+  CK(cudaMemcpyAsync(d_rp, rowptr, ((size_t)n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  if (nnz > 0) {
+    CK(cudaMemcpyAsync(d_ci, colind, (size_t)nnz * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(d_v, val, (size_t)nnz * sizeof(double), cudaMemcpyHostToDevice, s));
+  }
+  if (n > 0) CK(cudaMemcpyAsync(d_b, b, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, s));
+  const iluk_pattern A{n, nnz, d_rp, d_ci};
+  int st = iluk_validate(&A, info, stream);
+  if (st != ILUK_OK) return st;
+  st = iluk_factor(&A, d_v, k, &S, &F, info, stream);
+  if (st != ILUK_OK) return st;
+  st = iluk_set_schedule(F, sched);
+  if (st != ILUK_OK) return fail(info, st);
+  st = gmres_solve(&A, d_v, ILUK_PREC_ILU, F, d_b, d_x, restart, rtol, maxit, 0, info, stream);
+  if (n > 0) CK(cudaMemcpyAsync(x, d_x, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return st;
 }
 
 int tpilu_solve(const iluk_pattern *A, const double *A_val, iluk_fac *F, iiluk *M, int solver,

@@ -57,7 +57,7 @@ struct iluk_fac {
   double *val = nullptr;          // F values
   int *sync = nullptr;            // tickets + flags for sweeps: see sweeps.cu
   double *tmp = nullptr;          // intermediate vector of the two sweeps
-  double2 *rdiag = nullptr;       // double-double reciprocals of the diagonal (from
+  iluk::DivPrep *rdiag = nullptr; // the diagonal with its fixed-point reciprocals (from
                                   // the numeric phase; used by every sweep division)
   iluk::DevErr *err = nullptr;    // status of asynchronous calls
   // explicit transpose of F for (L~U~)^-T, built on first use
@@ -133,7 +133,7 @@ cudaError_t launch_factor_fused(int64_t n, const int64_t *arp, const int32_t *ac
                                 const double *aval, int k, const SymArena &ar, double *arena_val,
                                 unsigned long long *rinfo, unsigned long long *num_ticket,
                                 DevErr *err, int scap, int mapw, int ncap, cudaStream_t s);
-cudaError_t launch_recip_diag(int64_t n, const int64_t *diag, const double *fval, double2 *rdiag,
+cudaError_t launch_recip_diag(int64_t n, const int64_t *diag, const double *fval, DivPrep *rdiag,
                               cudaStream_t s);
 cudaError_t build_index_orders(int64_t n, LevelOrder *fwd, LevelOrder *bwd, cudaStream_t s);
 cudaError_t launch_symbolic_compact(int64_t n, const SymArena &ar, const int64_t *frp,
@@ -150,7 +150,7 @@ int build_levels_pair(int64_t n, const int64_t *rp, const int32_t *ci, const int
 // The factor values double as ready flags (numeric.cu); fval is overwritten.
 cudaError_t launch_pivot_info(int64_t n, const int64_t *frp, const int32_t *fci,
                               const int64_t *fdiag, int64_t *pinfo, cudaStream_t s);
-cudaError_t launch_numeric(const iluk_sym *S, const double *aval, double *fval, double2 *rdiag,
+cudaError_t launch_numeric(const iluk_sym *S, const double *aval, double *fval, DivPrep *rdiag,
                            unsigned long long *ticket, DevErr *err, cudaStream_t s);
 cudaError_t launch_numeric_batched(const iluk_sym *S, int64_t nbatch, const double *avals,
                                    double *fvals, unsigned long long *ticket, DevErr *errs,
@@ -161,7 +161,7 @@ size_t sweep_sync_ints(int64_t n);
 // y = (LU)^-1 p (or ^-T on the transposed arrays).  tmp must hold the pending
 // marker in every entry on entry, and does again on exit.
 cudaError_t launch_apply(int64_t n, const int64_t *rp, const int32_t *ci, const int64_t *dg,
-                         const double *v, const double2 *rd, const LevelOrder &fwd,
+                         const double *v, const DivPrep *rd, const LevelOrder &fwd,
                          const LevelOrder &bwd,
                          const double *p, double *tmp, double *y, int transpose, int sched,
                          DevErr *err, cudaStream_t s);
@@ -174,7 +174,7 @@ cudaError_t launch_transpose(int64_t n, int64_t nnz, const int64_t *rp, const in
                              int64_t *tdiag, int32_t *cursor, int64_t *scan_tmp, cudaStream_t s);
 
 // TPIILU (tpiilu.cu)
-cudaError_t launch_iiluk_build(const iluk_sym *S, const double *fval, const double2 *rdiag,
+cudaError_t launch_iiluk_build(const iluk_sym *S, const double *fval, const DivPrep *rdiag,
                                const int64_t *tinfo, double *g, int *sync, DevErr *err,
                                cudaStream_t s);
 cudaError_t launch_tpiilu_info(int64_t n, const int64_t *frp, const int32_t *fci,
@@ -197,6 +197,8 @@ cudaError_t launch_scale_div(int64_t n, const double *x, const double *den, doub
 cudaError_t launch_combine(int64_t n, const double *V, int64_t ldv, const double *y, int cnt,
                            double *u, cudaStream_t s);
 cudaError_t launch_add(int64_t n, double *x, const double *z, cudaStream_t s);
+cudaError_t launch_acc_scaled(int64_t n, double *u, const double *y, const double *z,
+                              cudaStream_t s);
 cudaError_t launch_bicg_dir(int64_t n, double *p, const double *r, const double *v, double beta,
                             double omega, cudaStream_t s);
 cudaError_t launch_axmy(int64_t n, double *out, const double *a, double alpha, const double *b,

@@ -240,9 +240,10 @@ cudaError_t launch_mgs_step(int64_t n, double *w, const double *vi, const double
 __global__ void k_scale_div(int64_t n, const double *__restrict__ x, const double *den, double *y) {
   const double d = *den;
   if (d == 0.0) return;
+  const DivPrep pd = div_prep(d);  // one reciprocal, n quotients
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
-    y[i] = __ddiv_rn(x[i], d);
+    y[i] = div_fin(x[i], pd);
 }
 
 static unsigned vec_blocks(int64_t n) {
@@ -277,6 +278,25 @@ cudaError_t launch_combine(int64_t n, const double *V, int64_t ldv, const double
   ProfScope prof_scope(ILUK_PROF_VECTOR, s);
   if (n == 0) return cudaSuccess;
   k_combine<<<vec_blocks(n), 256, 0, s>>>(n, V, ldv, y, cnt, u);
+  note_launch();
+  return cudaGetLastError();
+}
+
+// u_i = u_i + y * z_i (y read on the device), one rounding each: one term
+// of k_combine's sum at a time, in the same order.
+__global__ void k_acc_scaled(int64_t n, double *u, const double *__restrict__ y,
+                             const double *__restrict__ z) {
+  const double yj = *y;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    u[i] = __dadd_rn(u[i], __dmul_rn(yj, z[i]));
+}
+
+cudaError_t launch_acc_scaled(int64_t n, double *u, const double *y, const double *z,
+                              cudaStream_t s) {
+  ProfScope prof_scope(ILUK_PROF_VECTOR, s);
+  if (n == 0) return cudaSuccess;
+  k_acc_scaled<<<vec_blocks(n), 256, 0, s>>>(n, u, y, z);
   note_launch();
   return cudaGetLastError();
 }

@@ -219,11 +219,12 @@ __device__ __forceinline__ bool apply_pivots(int dp, double *rv, const int64_t *
       ok = false;
       break;
     }
-    // The multiplier f_ih / f_hh by IEEE division.  (A reciprocal
-    // published by the pivot row, with a Markstein correction, measured
-    // slower here: it is rarely there yet for the pivot that just arrived,
-    // and its loads and polls cost more than the divisions it saves.)
-    const double fih = __ddiv_rn(rv[q], cur.piv);
+    // The multiplier f_ih / f_hh, correctly rounded, on the integer pipes
+    // (div_int): a fraction of the latency of an FP64 division, and it
+    // leaves the FP64 pipe to the updates.  (A reciprocal published by the
+    // pivot row measured slower: it is rarely there yet for the pivot that
+    // just arrived, and its loads and polls cost more than they save.)
+    const double fih = div_int(rv[q], cur.piv);
     __syncwarp();
     if (lane == 0) rv[q] = fih;
     // only the chunks the pivot row has: an FP64 instruction costs its
@@ -575,17 +576,17 @@ static int numeric_cap(const iluk_sym *S, int *warps_out, int *map_out, size_t *
   return -1;  // a row of F exceeds shared memory
 }
 
-// rdiag[i] = recip_dd(f_ii): the double-double reciprocal of each diagonal
-// entry, for the backward sweep's division.  A row that did not finish leaves
-// its diagonal pending, whose reciprocal comes out as (0, 0): no fast path.
+// rdiag[i] = div_prep(f_ii): each diagonal entry with its fixed-point
+// reciprocal, for the backward sweep's division.  A row that did not finish
+// leaves its diagonal pending (a NaN), which div_fin hands to IEEE division.
 __global__ void k_recip_diag(int64_t n, const int64_t *__restrict__ fdiag,
-                             const double *__restrict__ fval, double2 *rdiag) {
+                             const double *__restrict__ fval, DivPrep *rdiag) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
-    rdiag[i] = recip_dd(fval[fdiag[i]]);
+    rdiag[i] = div_prep(fval[fdiag[i]]);
 }
 
-cudaError_t launch_recip_diag(int64_t n, const int64_t *diag, const double *fval, double2 *rdiag,
+cudaError_t launch_recip_diag(int64_t n, const int64_t *diag, const double *fval, DivPrep *rdiag,
                               cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   int64_t rb = (n + 255) / 256;
@@ -597,7 +598,7 @@ cudaError_t launch_recip_diag(int64_t n, const int64_t *diag, const double *fval
 }
 
 static cudaError_t launch_numeric_impl(const iluk_sym *S, int64_t nbatch, const double *avals,
-                                       double *fvals, double2 *rdiag, unsigned long long *ticket,
+                                       double *fvals, DivPrep *rdiag, unsigned long long *ticket,
                                        DevErr *errs, cudaStream_t s) {
   // the forward level order, once built, is a valid and better-spread order
   const int32_t *order = S->levels_built ? S->lord.corder : nullptr;
@@ -681,7 +682,7 @@ cudaError_t launch_factor_fused(int64_t n, const int64_t *arp, const int32_t *ac
   return e;
 }
 
-cudaError_t launch_numeric(const iluk_sym *S, const double *aval, double *fval, double2 *rdiag,
+cudaError_t launch_numeric(const iluk_sym *S, const double *aval, double *fval, DivPrep *rdiag,
                            unsigned long long *ticket, DevErr *err, cudaStream_t s) {
   return launch_numeric_impl(S, 1, aval, fval, rdiag, ticket, err, s);
 }

@@ -5,9 +5,9 @@
 // Backward: y_i = (x_i - sum_{j>i} f_ij y_j) / f_ii, j descending (the mirror
 // image: rows last to first, each row right to left).  Each row's
 // subtraction chain keeps the sequential order (one rounding per product, one
-// per difference); the division uses the factor's double-double reciprocal
-// of f_ii and one Markstein correction, which gives IEEE's quotient
-// (common.cuh).
+// per difference); the division by f_ii runs on the integer pipes from the
+// factor's fixed-point reciprocal of f_ii and gives IEEE's quotient
+// (div_fin, common.cuh).
 //
 // Five schedules of the same row task, all bit-identical; the factor handle
 // times them (the warp-per-row ones at several CTA widths) on its first
@@ -88,7 +88,7 @@ template <bool FORWARD, bool DIVIDE, bool GPU_SCOPE, int W>
 __global__ void __launch_bounds__(GPU_SCOPE ? kGridThreads : kCtaThreads)
 k_sweep(const int32_t *__restrict__ order, int64_t len, const int64_t *__restrict__ rp,
         const int32_t *__restrict__ ci, const int64_t *__restrict__ dg,
-        const double *__restrict__ v, const double2 *__restrict__ rd, const double *in,
+        const double *__restrict__ v, const DivPrep *__restrict__ rd, const double *in,
         double *out, double *clear, DevErr *err, int64_t limit_ns) {
   const int lane = threadIdx.x & 31;
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -101,14 +101,11 @@ k_sweep(const int32_t *__restrict__ order, int64_t len, const int64_t *__restric
     // always subtracted last.
     int64_t first = 0, d = 0;
     int mylen = 0;
-    double s = 0.0, dv = 1.0;
-    double2 rr = make_double2(0.0, 0.0);
+    double s = 0.0;
+    DivPrep rr{0ull, 1.0};
     if (row >= 0) {
       d = dg[row];
-      if (DIVIDE) {  // fetched now, off the chain's critical path
-        dv = v[d];
-        rr = rd[row];
-      }
+      if (DIVIDE) rr = rd[row];  // u_ii and its reciprocal, fetched off the chain
       if (FORWARD) {
         first = rp[row];
         mylen = (int)(d - first);
@@ -191,7 +188,7 @@ k_sweep(const int32_t *__restrict__ order, int64_t len, const int64_t *__restric
       if (row >= 0) set_err(err, row, ILUK_ETIMEOUT);
       return;
     }
-    if (DIVIDE && row >= 0) s = div_rn_recip(s, dv, rr);
+    if (DIVIDE && row >= 0) s = div_fin(s, rr);
     if (row >= 0) {
       if ((unsigned long long)__double_as_longlong(s) == kPending)
         s = __longlong_as_double((long long)kQuietNaN);
@@ -242,7 +239,7 @@ __global__ void __launch_bounds__(kCtaThreads, 1)
 k_sweep_cluster(const int32_t *__restrict__ order, int64_t len, int64_t n,
                 const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
                 const int64_t *__restrict__ dg, const double *__restrict__ v,
-                const double2 *__restrict__ rd, const double *in, double *out, double *clear,
+                const DivPrep *__restrict__ rd, const double *in, double *out, double *clear,
                 DevErr *err, int64_t limit_ns) {
   extern __shared__ __align__(16) double xs[];  // this CTA's slice of x
   __shared__ int sfail;
@@ -265,14 +262,11 @@ k_sweep_cluster(const int32_t *__restrict__ order, int64_t len, int64_t n,
     const int64_t row = order[slot0 + lane];
     int64_t first = 0, d = 0;
     int mylen = 0;
-    double s = 0.0, dv = 1.0;
-    double2 rr = make_double2(0.0, 0.0);
+    double s = 0.0;
+    DivPrep rr{0ull, 1.0};
     if (row >= 0) {
       d = dg[row];
-      if (DIVIDE) {  // fetched now, off the chain's critical path
-        dv = v[d];
-        rr = rd[row];
-      }
+      if (DIVIDE) rr = rd[row];  // u_ii and its reciprocal, fetched off the chain
       if (FORWARD) {
         first = rp[row];
         mylen = (int)(d - first);
@@ -355,7 +349,7 @@ k_sweep_cluster(const int32_t *__restrict__ order, int64_t len, int64_t n,
       }
       break;
     }
-    if (DIVIDE && row >= 0) s = div_rn_recip(s, dv, rr);
+    if (DIVIDE && row >= 0) s = div_fin(s, rr);
     if (row >= 0) {
       if ((unsigned long long)__double_as_longlong(s) == kPending)
         s = __longlong_as_double((long long)kQuietNaN);
@@ -393,7 +387,7 @@ __global__ void __launch_bounds__(kCtaThreads, 1)
 k_sweep_wpr(const int32_t *__restrict__ order, int64_t len, int64_t n,
             const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
             const int64_t *__restrict__ dg, const double *__restrict__ v,
-            const double2 *__restrict__ rd, const double *in, double *out, double *clear,
+            const DivPrep *__restrict__ rd, const double *in, double *out, double *clear,
             DevErr *err, int64_t limit_ns, const int32_t *__restrict__ owner) {
   // SCOPE 1: x_i lives in the shared memory of the CTA whose warp computes
   // row i, at slot (k * wpc + warp) for the warp's k-th row; owner[i] holds
@@ -425,12 +419,8 @@ k_sweep_wpr(const int32_t *__restrict__ order, int64_t len, int64_t n,
     const int64_t row = order[slot];
     if (row < 0) continue;
     const int64_t d = dg[row];
-    double dv = 1.0;
-    double2 rr = make_double2(0.0, 0.0);
-    if (DIVIDE) {  // fetched now, off the chain's critical path
-      dv = v[d];
-      rr = rd[row];
-    }
+    DivPrep rr{0ull, 1.0};
+    if (DIVIDE) rr = rd[row];  // u_ii and its reciprocal, fetched off the chain
     const int64_t first = FORWARD ? rp[row] : rp[row + 1] - 1;
     const int mylen = (int)(FORWARD ? d - first : first - d);
     constexpr int64_t step = FORWARD ? 1 : -1;
@@ -497,7 +487,7 @@ k_sweep_wpr(const int32_t *__restrict__ order, int64_t len, int64_t n,
       if (lane == 0) set_err(err, row, ILUK_ETIMEOUT);
       break;
     }
-    if (DIVIDE) s = div_rn_recip(s, dv, rr);
+    if (DIVIDE) s = div_fin(s, rr);
     if ((unsigned long long)__double_as_longlong(s) == kPending)
       s = __longlong_as_double((long long)kQuietNaN);
     if (lane == 0) {
@@ -589,12 +579,13 @@ cudaError_t launch_fill_value(int64_t n, double *x, double v, cudaStream_t s) {
   return fill_bits(n, x, bits, s);
 }
 
-// q_i = a_i / b_i through recip_dd + div_rn_recip, the sweeps' division.
+// q_i = a_i / b_i through div_prep + div_fin, the division of the numeric
+// phase's multipliers and of the sweeps.
 __global__ void k_div_check(int64_t n, const double *__restrict__ a,
                             const double *__restrict__ b, double *__restrict__ q) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
-    q[i] = div_rn_recip(a[i], b[i], recip_dd(b[i]));
+    q[i] = div_int(a[i], b[i]);
 }
 
 cudaError_t launch_div_check(int64_t n, const double *a, const double *b, double *q,
@@ -685,7 +676,7 @@ static cudaError_t launch_on_cluster(K kern, int C, int threads, size_t smem, cu
 
 template <bool FORWARD, bool DIVIDE>
 static cudaError_t run_sweep(int64_t n, const LevelOrder &lo, const int64_t *rp, const int32_t *ci,
-                             const int64_t *dg, const double *v, const double2 *rd,
+                             const int64_t *dg, const double *v, const DivPrep *rd,
                              const double *in, double *out, double *clear, int sched, DevErr *err,
                              cudaStream_t s) {
   ProfScope prof_scope(FORWARD ? ILUK_PROF_SWEEP : ILUK_PROF_SWEEP_BWD, s);
@@ -772,7 +763,7 @@ static cudaError_t run_sweep(int64_t n, const LevelOrder &lo, const int64_t *rp,
 }
 
 cudaError_t launch_apply(int64_t n, const int64_t *rp, const int32_t *ci, const int64_t *dg,
-                         const double *v, const double2 *rd, const LevelOrder &fwd,
+                         const double *v, const DivPrep *rd, const LevelOrder &fwd,
                          const LevelOrder &bwd,
                          const double *p, double *tmp, double *y, int transpose, int sched,
                          DevErr *err, cudaStream_t s) {

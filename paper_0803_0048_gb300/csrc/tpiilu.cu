@@ -184,7 +184,7 @@ __device__ __forceinline__ bool ii_wait(IiStageB &b, const double *g, int lane, 
 template <bool LOWER>
 __device__ bool ii_row(int64_t n, int64_t row, const int64_t *__restrict__ frp,
                        const int32_t *__restrict__ fci, const int64_t *__restrict__ fdiag,
-                       const double *__restrict__ fval, const double2 *__restrict__ rdiag,
+                       const double *__restrict__ fval, const DivPrep *__restrict__ rdiag,
                        const int64_t *__restrict__ tinfo, double *g, DevErr *err, double *rv,
                        int64_t *sinfo, int32_t *rc, int16_t *smap, int map_cap, int64_t limit_ns,
                        int lane) {
@@ -193,11 +193,11 @@ __device__ bool ii_row(int64_t n, int64_t row, const int64_t *__restrict__ frp,
   const int64_t s0 = LOWER ? frp[row] : d + 1;  // segment of the row handled here
   const int m = (int)((LOWER ? d : frp[row + 1]) - s0);
   const double uii = fval[d];
-  const double2 rr = rdiag ? rdiag[row] : make_double2(0.0, 0.0);
+  const DivPrep rr = rdiag ? rdiag[row] : div_prep(uii);
   for (int q = lane; q < m; q += 32) {
     rc[q] = fci[s0 + q];
     sinfo[q] = tinfo[s0 + q];
-    rv[q] = LOWER ? fval[s0 + q] : div_rn_recip(fval[s0 + q], uii, rr);  // u^_it = u_it / u_ii
+    rv[q] = LOWER ? fval[s0 + q] : div_fin(fval[s0 + q], rr);  // u^_it = u_it / u_ii
   }
   __syncwarp();
   IiIndex ix;
@@ -288,7 +288,7 @@ __device__ bool ii_row(int64_t n, int64_t row, const int64_t *__restrict__ frp,
 __global__ void __launch_bounds__(kIiThreads)
 k_iiluk_build(int64_t n, const int64_t *__restrict__ frp, const int32_t *__restrict__ fci,
               const int64_t *__restrict__ fdiag, const double *__restrict__ fval,
-              const double2 *__restrict__ rdiag, const int64_t *__restrict__ tinfo,
+              const DivPrep *__restrict__ rdiag, const int64_t *__restrict__ tinfo,
               const int32_t *__restrict__ lord, const int32_t *__restrict__ uord, double *g,
               unsigned long long *ticket, DevErr *err, int cap, int map_cap, int64_t limit_ns) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -320,7 +320,7 @@ k_iiluk_build(int64_t n, const int64_t *__restrict__ frp, const int32_t *__restr
   }
 }
 
-cudaError_t launch_iiluk_build(const iluk_sym *S, const double *fval, const double2 *rdiag,
+cudaError_t launch_iiluk_build(const iluk_sym *S, const double *fval, const DivPrep *rdiag,
                                const int64_t *tinfo, double *g, int *sync, DevErr *err,
                                cudaStream_t s) {
   const int64_t n = S->n;
@@ -454,14 +454,23 @@ extern "C" int iiluk_apply_noalloc(int64_t n, const int64_t *rowptr, const int32
     z = g_noalloc_ptr[dev];
   }
   cudaStream_t s = (cudaStream_t)stream;
-  int64_t blocks = (n * 32 + 255) / 256;
-  const int64_t cap = (int64_t)num_sms() * 8;
-  if (blocks > cap) blocks = cap;
+  // one thread per row, as in iiluk_apply
+  const unsigned blocks = (unsigned)((n + 255) / 256);
   // The lower pass writes every z_i before the upper pass reads it, so the
-  // array needs no clearing between calls.
-  k_iiluk_apply<true><<<(unsigned)blocks, 256, 0, s>>>(n, rowptr, colind, diag, g, p, z);
+  // array needs no clearing between calls.  cudaLaunchKernel reports the
+  // error of each launch itself, not an earlier launch's pending one.
+  const double *zin = z;
+  void *lower[] = {(void *)&n, (void *)&rowptr, (void *)&colind, (void *)&diag, (void *)&g,
+                   (void *)&p, (void *)&z};
+  void *upper[] = {(void *)&n, (void *)&rowptr, (void *)&colind, (void *)&diag, (void *)&g,
+                   (void *)&zin, (void *)&y};
+  if (cudaLaunchKernel((const void *)k_iiluk_apply<true>, dim3(blocks), dim3(256), lower, 0, s) !=
+      cudaSuccess)
+    return ILUK_ECUDA;
   note_launch();
-  k_iiluk_apply<false><<<(unsigned)blocks, 256, 0, s>>>(n, rowptr, colind, diag, g, z, y);
+  if (cudaLaunchKernel((const void *)k_iiluk_apply<false>, dim3(blocks), dim3(256), upper, 0, s) !=
+      cudaSuccess)
+    return ILUK_ECUDA;
   note_launch();
-  return cudaGetLastError() == cudaSuccess ? ILUK_OK : ILUK_ECUDA;
+  return ILUK_OK;
 }

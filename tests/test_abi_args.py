@@ -95,6 +95,19 @@ def test_vector_calls_reject_missing_vectors(lib):
     einval(lib.iluk_dot(-1, DUMMY, DUMMY, DUMMY, None))
     einval(lib.iluk_dot(5, None, DUMMY, DUMMY, None))
     einval(lib.iluk_dot(0, None, None, None, None))
+    for args in ((-1, 4, DUMMY, DUMMY, DUMMY, DUMMY, DUMMY, 2, 30, 1e-8, 10, 0),
+                 (4, 4, None, DUMMY, DUMMY, DUMMY, DUMMY, 2, 30, 1e-8, 10, 0),
+                 (4, 4, DUMMY, None, DUMMY, DUMMY, DUMMY, 2, 30, 1e-8, 10, 0),
+                 (4, 4, DUMMY, DUMMY, DUMMY, None, DUMMY, 2, 30, 1e-8, 10, 0),
+                 (4, 4, DUMMY, DUMMY, DUMMY, DUMMY, None, 2, 30, 1e-8, 10, 0),
+                 (4, 4, DUMMY, DUMMY, DUMMY, DUMMY, DUMMY, 251, 30, 1e-8, 10, 0),
+                 (4, 4, DUMMY, DUMMY, DUMMY, DUMMY, DUMMY, 2, 0, 1e-8, 10, 0)):
+        info = L.Info()
+        einval(lib.iluk_solve_host(*args, C.byref(info), None), info)
+    einval(lib.iluk_transpose(C.byref(pat(n=-1)), DUMMY, DUMMY, DUMMY, DUMMY, None))
+    for args in ((None, DUMMY, DUMMY, DUMMY), (DUMMY, None, DUMMY, DUMMY),
+                 (DUMMY, DUMMY, None, DUMMY), (DUMMY, DUMMY, DUMMY, None)):
+        einval(lib.iluk_transpose(C.byref(pat()), *args, None))
     einval(lib.iluk_div_rn(-1, DUMMY, DUMMY, DUMMY, None))
     einval(lib.iluk_div_rn(3, DUMMY, None, DUMMY, None))
     einval(lib.iiluk_apply_noalloc(-1, DUMMY, DUMMY, DUMMY, DUMMY, DUMMY, DUMMY, None))
@@ -120,6 +133,13 @@ def test_solvers_reject_bad_arguments(lib):
     for args in cases:
         info = L.Info()
         einval(gm(*args, C.byref(info), None), info)
+    for args in cases:
+        info = L.Info()
+        einval(lib.gmres_solve_ex(*args, L.BASIS["auto"], C.byref(info), None), info)
+    for basis in (-1, 4):  # unknown basis mode
+        info = L.Info()
+        einval(lib.gmres_solve_ex(C.byref(A), DUMMY, L.PREC_NONE, None, DUMMY, DUMMY, 30, 1e-8,
+                                  10, 0, basis, C.byref(info), None), info)
     for b, x, vals in ((None, DUMMY, DUMMY), (DUMMY, None, DUMMY), (DUMMY, DUMMY, None)):
         info = L.Info()
         einval(lib.bicgstab_solve(C.byref(A), vals, L.PREC_NONE, None, b, x, 1e-8, 10,
@@ -169,6 +189,9 @@ def test_failing_cuda_calls_surface_as_ecuda(lib):
     for transpose in (0, 1):
         assert lib.gmres_solve(C.byref(A), DUMMY, L.PREC_NONE, None, DUMMY, DUMMY, 30, 1e-8, 10,
                                transpose, C.byref(info), None) == L.ECUDA
+        for basis in L.BASIS.values():
+            assert lib.gmres_solve_ex(C.byref(A), DUMMY, L.PREC_NONE, None, DUMMY, DUMMY, 30,
+                                      1e-8, 10, transpose, basis, C.byref(info), None) == L.ECUDA
     assert lib.bicgstab_solve(C.byref(A), DUMMY, L.PREC_NONE, None, DUMMY, DUMMY, 1e-8, 10,
                               C.byref(info), None) == L.ECUDA
     h = C.c_void_p()

@@ -82,5 +82,9 @@ def test_bench_line_contract_with_stand_ins():
     assert abs(rf["nominal_frac"] - rf["achieved"] / 7900.0) < 1e-5
     assert d["e2e"]["h2d_bytes_per_step"] == 160001 * 8 + 1_600_000 * 12 + 160000 * 8
     assert d["e2e"]["d2h_bytes_per_step"] == 160000 * 8
+    assert d["e2e"]["call"].startswith("iluk_solve_host")
+    assert d["dag"] == {"depth_lower": 15777, "depth_upper": 15629}
+    assert set(d["config"]) == {"workload", "n", "nnz_A", "nnz_F", "k", "restart", "rtol", "l2",
+                                "parallelism"}
     assert d["operand_stream"]["kernel"] == "factor"
     assert d["operand_stream"]["bytes_per_launch"] > 10 * d["kernels"]["factor"]["alg_bytes_per_launch"]

@@ -1,10 +1,16 @@
-"""The sweeps divide by the diagonal with a precomputed double-double
-reciprocal and one Markstein correction instead of an IEEE division.  The
-method is exact only if the correction always lands on the correctly rounded
-quotient, so it is pinned here against the host's IEEE division (numpy),
-bit for bit, on inputs chosen to stress it: random operands over the whole
-exponent range, operands inside the fast path's range, quotients next to a
-rounding midpoint, the edges of the fast path's range, and special values.
+"""The numeric phase's multipliers and the sweeps' division by u_ii are
+computed on the integer pipes (a fixed-point reciprocal of the divisor from
+an fp32 seed and two Newton steps, then an exact remainder correction)
+instead of by the FP64 division.  The method is exact only if the quotient
+always comes out as IEEE's correctly rounded one, so it is pinned here
+against the host's IEEE division (numpy), bit for bit, through iluk_div_rn
+(the same device functions), on inputs chosen to stress it: random operands
+over the whole exponent range, random normal operands with normal
+quotients (the integer path), quotients next to a rounding midpoint, extreme
+significands (reciprocal seeds at both ends of their range, rounding carries
+into the exponent), quotients at the edges of the normal range (overflow to
+infinity, underflow to subnormals, which fall back to IEEE division), and
+special values.
 """
 import numpy as np
 import pytest
@@ -59,11 +65,25 @@ def test_random_operands_whole_range():
     _check(a, b)
 
 
-def test_random_operands_fast_path_range():
+def test_random_operands_normal_quotients():
     n = 1 << 23
     ra, rb = _draws("fa", n), _draws("fb", n)
-    ea = np.uint64(623) + (ra >> np.uint64(52)) % np.uint64(801)
-    eb = np.uint64(623) + (rb >> np.uint64(52)) % np.uint64(801)
+    ea = np.uint64(523) + (ra >> np.uint64(52)) % np.uint64(1001)
+    eb = np.uint64(523) + (rb >> np.uint64(52)) % np.uint64(1001)
+    _check(_from_parts(ra >> np.uint64(63), ea, ra), _from_parts(rb >> np.uint64(63), eb, rb))
+
+
+def test_quotients_at_the_edges_of_the_normal_range():
+    # biased quotient exponents -2..3 and 2043..2048 around the subnormal and
+    # overflow boundaries, with random significands (some round up across
+    # the boundary)
+    n = 1 << 20
+    ra, rb, rs = _draws("ea", n), _draws("eb", n), _draws("es", n)
+    eb = np.uint64(1000) + rb % np.uint64(47)
+    shift = rs % np.uint64(12)  # target exponent offset
+    lo = (eb.astype(np.int64) - 1023 + 1 + (shift.astype(np.int64) - 3)).clip(1, 2046)
+    hi = (eb.astype(np.int64) - 1023 + 2046 + (shift.astype(np.int64) - 8)).clip(1, 2046)
+    ea = np.where(rs & np.uint64(1 << 40), lo, hi).astype(np.uint64)
     _check(_from_parts(ra >> np.uint64(63), ea, ra), _from_parts(rb >> np.uint64(63), eb, rb))
 
 
@@ -95,7 +115,7 @@ def test_extreme_mantissas():
 
 def test_range_edges_and_special_values():
     edges = []
-    for e in (622, 623, 624, 1022, 1023, 1024, 1422, 1423, 1424):
+    for e in (1, 2, 3, 622, 623, 624, 1022, 1023, 1024, 1422, 1423, 1424, 2044, 2045, 2046):
         for m in (0, 1, (1 << 52) - 1, 0x8000000000000):
             edges.append(_from_parts(np.zeros(1, np.uint64), np.array([e], np.uint64),
                                      np.array([m], np.uint64))[0])

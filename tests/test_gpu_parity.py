@@ -260,3 +260,36 @@ def test_tpilu_policy_bit_exact(solver, budget, expect):
     assert info.status == st and info.iters == it
     assert bits([info.relres])[0] == bits([rel])[0]
     assert_bits_equal(x, xo, "tpilu x")
+
+
+@pytest.mark.parametrize("name,A", [("rand301", W.random_sparse(301, 0.02, 5)),
+                                    ("convdiff3d_9", W.conv_diff(9, 3, (50.0, 50.0, 50.0))),
+                                    ("band3000", W.random_band(3000, 9, 100, 11))],
+                         ids=["rand301", "convdiff3d_9", "band3000"])
+def test_transpose_matches_oracle(name, A):
+    rp, ci, av = to_dev(A)
+    trp, tci, tv = P.transpose(rp, ci, av)
+    orp, oci, ov = oracle.transpose(A.n, A.rowptr, A.colind, A.val)
+    assert np.array_equal(trp.cpu().numpy(), orp) and np.array_equal(tci.cpu().numpy(), oci)
+    assert_bits_equal(tv, ov, "transposed values")
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_solve_host_matches_oracle(k):
+    """The host-buffer call (iluk_solve_host): host arrays in, x out on the
+    host, bit-identical to the oracle's factor + GMRES with fixed-tree dots."""
+    A = W.conv_diff(20, 2, (20.0, 20.0))
+    b = W.uniform(W.stream_key(41, "host"), np.arange(A.n), -1.0, 1.0)
+    t = [torch.from_numpy(a).pin_memory() for a in (A.rowptr, A.colind, A.val, b)]
+    x, info = P.solve_host(*t, k, restart=30, rtol=1e-10)
+    assert x.device.type == "cpu" and info.status == 0
+    ref = oracle.factor(A, k)
+    st, xo, it, rel, cyc = oracle.gmres(A.n, A.rowptr, A.colind, A.val, b, oracle.PREC_ILU,
+                                        (ref["rowptr"], ref["colind"], ref["val"]), 30, 1e-10,
+                                        dotmode=oracle.DOT_TREE)
+    assert (info.iters, info.cycles) == (it, cyc) and bits([info.relres])[0] == bits([rel])[0]
+    assert_bits_equal(x, xo, "host-buffer solve")
+    # pageable host memory works too
+    x2, _ = P.solve_host(*[torch.from_numpy(a) for a in (A.rowptr, A.colind, A.val, b)], k,
+                         restart=30, rtol=1e-10)
+    assert_bits_equal(x2, xo, "host-buffer solve, pageable")

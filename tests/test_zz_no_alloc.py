@@ -31,14 +31,17 @@ def _ptr(t):
     return C.c_void_p(t.data_ptr())
 
 
-def test_noalloc_apply_matches_regular_apply_twice():
+@pytest.mark.parametrize("side,k", [(40, 2), (700, 1)], ids=["2d_40x40_k2", "2d_700x700_k1"])
+def test_noalloc_apply_matches_regular_apply_twice(side, k):
+    """n = 1,600 (a few CTAs) and n = 490,000 (near half the scratch's
+    2^20 rows, thousands of CTAs)."""
     lib = L.load()
     stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
-    A = W.conv_diff(40, 2, (20.0, 20.0))
+    A = W.conv_diff(side, 2, (20.0, 20.0))
     rp = torch.from_numpy(A.rowptr).cuda()
     ci = torch.from_numpy(A.colind).cuda()
     av = torch.from_numpy(A.val).cuda()
-    S = P.symbolic(rp, ci, 2)
+    S = P.symbolic(rp, ci, k)
     M = P.iiluk_build(P.numeric(S, av))
     frp, fci, _, fdg = S.pattern()
     g = M.values()
