@@ -67,7 +67,7 @@ def parse():
     ap.add_argument("--cpu-steps", type=int, default=2, help="oracle steps for cpu_baseline")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--workload", default="band",
-                    choices=["band", "batched", "adjoint", "suite"],
+                    choices=["band", "batched", "adjoint", "suite", "ratio"],
                     help="band: the n=160,000 headline; batched: 512 value sets on 32^3 plus "
                          "64 uneven grids in one launch; adjoint: 256^2 differentiable solve; "
                          "suite: every phase of every single-system configuration")
@@ -453,44 +453,68 @@ def batched(args):
     """512 value sets on one 32^3 7-point pattern + 64 uneven grids 16^3-40^3,
     ILU(1) factor + GMRES(30) to 1e-8, all in one persistent launch; against
     looping the single-instance path (iluk_numeric + gmres_solve) over the same
-    items on the same GPU."""
+    items on the same GPU.  Under torchrun the items are partitioned across
+    the ranks by estimated work (shard.partition): each GPU solves its share
+    in its own launch, nothing crosses GPUs, the per-item results are
+    gathered on rank 0, and the time is the slowest rank's (strong scaling:
+    the batch is fixed)."""
     import torch
+    import torch.distributed as dist
 
     import paper_0803_0048_gb300 as P
+    from paper_0803_0048_gb300 import shard
     from paper_0803_0048_gb300 import workloads as W
-    torch.cuda.set_device(0)
-    dev = torch.device("cuda", 0)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
     A0, vals, bs, _ = W.batched_values(args.nsets, 32)
     grids = W.uneven_grids(args.ngrids)
     rp = torch.from_numpy(A0.rowptr).to(dev)
     ci = torch.from_numpy(A0.colind).to(dev)
     S0 = P.symbolic(rp, ci, 1)
-    items, plain = [], []
-    for sidx in range(args.nsets):
-        v = torch.from_numpy(vals[sidx]).to(dev)
-        b = torch.from_numpy(bs[sidx]).to(dev)
-        items.append((S0, v, b, torch.empty(A0.n, dtype=torch.float64, device=dev)))
-        plain.append((S0, rp, ci, v, b))
+    # every rank builds every pattern's symbolic handle (cheap) to cost the items
+    pats = [(S0, rp, ci)] * args.nsets
     for g in grids:
         r = torch.from_numpy(g.A.rowptr).to(dev)
         c = torch.from_numpy(g.A.colind).to(dev)
-        S = P.symbolic(r, c, 1)
-        v = torch.from_numpy(g.A.val).to(dev)
-        b = torch.from_numpy(g.b).to(dev)
-        items.append((S, v, b, torch.empty(g.A.n, dtype=torch.float64, device=dev)))
+        pats.append((P.symbolic(r, c, 1), r, c))
+    costs = [shard.item_cost(S.n, *S.depth()) for S, _, _ in pats]
+    parts = shard.partition(costs, world)
+    mine = parts[rank]
+    items, plain = [], []
+    for idx in mine:
+        S, r, c = pats[idx]
+        if idx < args.nsets:
+            v = torch.from_numpy(vals[idx]).to(dev)
+            b = torch.from_numpy(bs[idx]).to(dev)
+        else:
+            g = grids[idx - args.nsets]
+            v = torch.from_numpy(g.A.val).to(dev)
+            b = torch.from_numpy(g.b).to(dev)
+        items.append((S, v, b, torch.empty(S.n, dtype=torch.float64, device=dev)))
         plain.append((S, r, c, v, b))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
     B = P.BatchSolve(items, restart=30, rtol=1e-8)
     for _ in range(max(args.warmup, 1)):
         B.solve()
-    torch.cuda.synchronize()
+    barrier()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(0) as clk:
+    with ClockSampler(local) as clk:
         ev0.record()
         for _ in range(args.steps):
             B.solve()
         ev1.record()
-        torch.cuda.synchronize()
-    ms = ev0.elapsed_time(ev1) / args.steps
+        barrier()
+    ms_local = ev0.elapsed_time(ev1) / args.steps
     res = B.results()
     chosen = (B.width(), B.spin())
     # every schedule the autotuner chooses from, one timed run each
@@ -510,6 +534,7 @@ def batched(args):
     res = B.results()
     # the same items, one at a time through the single-instance path; the
     # results are compared after the timed loop
+    barrier()
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     loop_out = []
@@ -519,25 +544,38 @@ def batched(args):
         x, info = P.gmres(r, c, v, b, F, restart=30, rtol=1e-8, check=False)
         loop_out.append((x, info.iters))
     t1.record()
-    torch.cuda.synchronize()
-    loop_ms = t0.elapsed_time(t1)
+    barrier()
+    loop_local = t0.elapsed_time(t1)
     mism = 0
     for (x, iters), (_, _, _, xb), rr in zip(loop_out, items, res):
         mism += int((x.view(torch.int64) != xb.view(torch.int64)).sum().item())
         mism += int(iters != rr.iters)
-    out = {"metric": METRIC, "value": round(ms, 3), "unit": "ms", "n_gpus": 1,
+    ms, loop_ms, mism_max = ranks_max([ms_local, loop_local, mism], dev, world)
+    merged = shard.gather_results(
+        [(idx, (r.status, r.iters, r.cycles, r.relres)) for idx, r in zip(mine, res)],
+        len(pats), rank, world)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank != 0:
+        return
+    out = {"metric": METRIC, "value": round(ms, 3), "unit": "ms", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
-           "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "higher_is_better": False, "scaling": "strong", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic",
            "config": {"workload": f"batched_{args.nsets}x32^3_plus_{args.ngrids}_uneven_k1_gmres30",
-                      "items": len(items), "width": chosen[0],
-                      "sweeps": "spin" if chosen[1] else "level"},
+                      "items": len(pats), "width": chosen[0],
+                      "sweeps": "spin" if chosen[1] else "level",
+                      "parallelism": f"items partitioned over {world} GPU(s)" if world > 1
+                      else "single"},
+           "partition": {"items_per_rank": [len(p) for p in parts],
+                         "est_work_per_rank": shard.loads(costs, parts)},
            "schedules_ms": sched_ms,
            "loop_single_path_ms": round(loop_ms, 3),
            "speedup_vs_loop": round(loop_ms / ms, 2),
-           "bit_mismatches_vs_single": mism,
-           "max_iters": max(r.iters for r in res),
-           "all_converged": all(r.status == 0 for r in res),
+           "bit_mismatches_vs_single": int(mism_max),
+           "max_iters": max(r[1] for r in merged),
+           "all_converged": all(r[0] == 0 for r in merged),
            "clocks": clk.summary()}
     print(json.dumps(out), flush=True)
 
@@ -849,6 +887,103 @@ def suite(args):
     print(json.dumps(out), flush=True)
 
 
+def ratio(args):
+    """Symbolic against numeric time for k = 1..5, the experiment of the
+    paper's Sec. 4.6 (the sequential symbolic phase's share grows with k and
+    passes the numeric phase's for large k).  The paper's matgen matrices are
+    not available; seeded random sparse matrices of its sizes and densities
+    (1,000-4,000 rows, 0.01-0.002) stand in, beside the random band matrix
+    (n = 160,000) and the 27-point Poisson matrix (50^3).  Per case and k: the
+    sizes (nnz_F, longest row, DAG depths), the GPU symbolic phase and the GPU
+    numeric phase (a refactorization on level orders; both median ms), their
+    ratio, and where the oracle finishes in seconds its own two phases on one
+    host core, their ratio, and the GPU's bit parity against it.  For k = 1
+    the three symbolic walks (iluk_set_symbolic_variant) are timed too."""
+    import torch
+
+    import oracle
+    import paper_0803_0048_gb300 as P
+    from paper_0803_0048_gb300 import workloads as W
+    torch.cuda.set_device(0)
+
+    def med_ms(fn, reps, warm=2):
+        for _ in range(warm):
+            fn()
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    def u64(a):
+        a = a.cpu().numpy() if hasattr(a, "cpu") else np.asarray(a)
+        return np.ascontiguousarray(a).view(np.uint64)
+
+    cases = [("random n=1000 density 0.01", lambda: W.random_sparse(1000, 0.01, 77), range(1, 6),
+              True),
+             ("random n=2000 density 0.004", lambda: W.random_sparse(2000, 0.004, 77),
+              range(1, 6), True),
+             ("random n=4000 density 0.002", lambda: W.random_sparse(4000, 0.002, 77),
+              range(1, 6), True),
+             ("27-point Poisson 50^3", lambda: W.poisson27(50), range(0, 4), False),
+             ("random band n=160000", lambda: W.random_band_160k(k=1).A, range(1, 5), False)]
+    rows = []
+    for name, make, ks, with_oracle in cases:
+        A = make()
+        rp, ci, av = (torch.from_numpy(a).cuda() for a in (A.rowptr, A.colind, A.val))
+        for k in ks:
+            S = P.symbolic(rp, ci, k)
+            F = P.numeric(S, av)
+            depth = S.depth()
+            frp = S.pattern()[0].cpu().numpy()
+            nnzF = int(frp[-1])
+            big = nnzF > 50_000_000
+            reps = 3 if big else 10
+            t_sym = med_ms(lambda: P.symbolic(rp, ci, k), reps, 1 if big else 2)
+            t_num = med_ms(lambda: F.refactor(av), reps, 1 if big else 2)
+            row = {"case": name, "k": k, "n": A.n, "nnz_A": A.nnz, "nnz_F": nnzF,
+                   "max_row": int(np.diff(frp).max()), "depth": list(depth),
+                   "gpu_symbolic_ms": round(t_sym, 4), "gpu_numeric_ms": round(t_num, 4),
+                   "gpu_ratio": round(t_sym / t_num, 3)}
+            if k == 1:
+                var = {}
+                for v in (0, 1, 2):
+                    prev = P.set_symbolic_variant(v)
+                    try:
+                        var[["ascending", "descending", "general_walk"][v]] = round(
+                            med_ms(lambda: P.symbolic(rp, ci, k), reps), 4)
+                    finally:
+                        P.set_symbolic_variant(prev)
+                row["k1_symbolic_variants_ms"] = var
+            if with_oracle:
+                t0 = time.perf_counter()
+                st, bad, orp, oci, olev = oracle.symbolic(A.n, A.rowptr, A.colind, k)
+                t1 = time.perf_counter()
+                st2, bad2, ov = oracle.numeric(A.n, A.rowptr, A.colind, A.val, orp, oci)
+                t2 = time.perf_counter()
+                grp, gci, glev, _ = [t.cpu().numpy() for t in S.pattern()]
+                row["oracle_one_core"] = {"symbolic_s": round(t1 - t0, 4),
+                                          "numeric_s": round(t2 - t1, 4),
+                                          "ratio": round((t1 - t0) / max(t2 - t1, 1e-9), 3)}
+                row["parity"] = {
+                    "pattern_equal": bool(np.array_equal(grp, orp) and np.array_equal(gci, oci)
+                                          and np.array_equal(glev, olev)),
+                    "factor_bit_mismatches": int(np.sum(u64(F.values()) != u64(ov)))}
+            rows.append(row)
+            print(json.dumps({"progress": name, "k": k}), file=sys.stderr, flush=True)
+            del S, F
+            torch.cuda.empty_cache()
+    out = {"metric": METRIC, "workload": "ratio", "unit": "ms", "dtype": "f64",
+           "data": "synthetic", "timing": "CUDA events, median of 10 runs (3 above 50 M "
+           "factor entries); oracle: one run on one host core", "host": host_cpu(),
+           "cases": rows}
+    print(json.dumps(out), flush=True)
+
+
 def L_sched(byte):
     from paper_0803_0048_gb300 import _lib as L
     return L.sched_name(byte)
@@ -862,6 +997,8 @@ def main():
         batched(args)
     elif args.workload == "adjoint":
         adjoint(args)
+    elif args.workload == "ratio":
+        ratio(args)
     elif args.workload == "suite":
         suite(args)
     else:

@@ -137,6 +137,16 @@ int64_t iluk_set_wait_limit(int64_t ns);
  * the previous value.  Host-side, whole process. */
 int64_t iluk_debug_hold_row(int64_t row);
 
+/* The symbolic phase for k <= 1, where rows need no other row's pattern
+ * (Sec. 3.3): 0 (default) each warp takes the next row in ascending order and
+ * reads its pivot rows from A without waiting; 1 the same, last row first
+ * (the order Sec. 3.3 found fastest on a CPU); 2 the general walk of k >= 2
+ * (rows announce their arena slots and dependants wait for them).  All three
+ * give the same pattern and levels; the setting exists to compare them.
+ * Host-side, whole process; returns the previous variant, or -1 (and changes
+ * nothing) for an unknown one. */
+int iluk_set_symbolic_variant(int variant);
+
 /* Number of CUDA kernels this library has launched in the process so far
  * (memsets and copies are not counted). */
 int64_t iluk_launch_count(void);

@@ -9,12 +9,13 @@ from . import _lib
 from .api import (BatchSolve, CsrPattern, Factors, IlukError, IncompleteInverse, Symbolic,
                   adjoint_scatter, bicgstab, debug_hold_row, div_rn, dot, factor, gmres,
                   iiluk_build, launch_count, numeric, numeric_batched, prof_enable, prof_read,
-                  set_wait_limit, solve, solve_host, spmv, symbolic, tpilu_solve, transpose,
-                  validate)
+                  set_symbolic_variant, set_wait_limit, solve, solve_host, spmv, symbolic,
+                  tpilu_solve, transpose, validate)
 from .autograd import IlukSolve, IlukSolver
 
 __all__ = ["BatchSolve", "CsrPattern", "Factors", "IlukError", "IlukSolve", "IlukSolver",
            "IncompleteInverse", "Symbolic", "adjoint_scatter", "bicgstab", "debug_hold_row",
            "div_rn", "dot", "factor", "gmres", "iiluk_build", "launch_count", "numeric",
-           "numeric_batched", "prof_enable", "prof_read", "set_wait_limit", "solve", "solve_host",
-           "spmv", "symbolic", "tpilu_solve", "transpose", "validate"]
+           "numeric_batched", "prof_enable", "prof_read", "set_symbolic_variant",
+           "set_wait_limit", "solve", "solve_host", "spmv", "symbolic", "tpilu_solve",
+           "transpose", "validate"]

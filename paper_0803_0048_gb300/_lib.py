@@ -68,6 +68,7 @@ SIGNATURES = [
     ("iluk_strerror", C.c_char_p, [I]),
     ("iluk_set_wait_limit", I64, [I64]),
     ("iluk_debug_hold_row", I64, [I64]),
+    ("iluk_set_symbolic_variant", I, [I]),
     ("iluk_launch_count", I64, []),
     ("iluk_prof_enable", I, [I]),
     ("iluk_prof_read", I, [P, P, I]),

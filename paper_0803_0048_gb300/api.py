@@ -438,6 +438,16 @@ def set_wait_limit(ns: int) -> int:
     return L.load().iluk_set_wait_limit(int(ns))
 
 
+def set_symbolic_variant(variant: int) -> int:
+    """The symbolic walk for k <= 1: 0 rows ascending without waits (the
+    default), 1 the same last row first, 2 the general walk with waits.  The
+    results do not depend on it.  Returns the previous variant."""
+    prev = L.load().iluk_set_symbolic_variant(int(variant))
+    if prev < 0:
+        raise ValueError("variant must be 0, 1 or 2")
+    return prev
+
+
 def debug_hold_row(row: int) -> int:
     return L.load().iluk_debug_hold_row(int(row))
 

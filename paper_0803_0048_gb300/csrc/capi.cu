@@ -30,6 +30,7 @@ int64_t initial_wait_limit() {
 }
 std::atomic<int64_t> g_wait_limit_ns{initial_wait_limit()};
 std::atomic<int64_t> g_hold_row{-1};
+std::atomic<int> g_sym_variant{0};
 std::atomic<int64_t> g_launches{0};
 
 struct DevCache {
@@ -135,6 +136,7 @@ int64_t next_pow2(int64_t v) {
 namespace iluk {
 int64_t wait_limit() { return g_wait_limit_ns.load(); }
 int64_t hold_row() { return g_hold_row.load(); }
+int symbolic_variant() { return g_sym_variant.load(); }
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 namespace {
@@ -203,6 +205,11 @@ int64_t iluk_set_wait_limit(int64_t ns) {
 }
 
 int64_t iluk_debug_hold_row(int64_t row) { return g_hold_row.exchange(row); }
+
+int iluk_set_symbolic_variant(int variant) {
+  if (variant < 0 || variant > 2) return -1;
+  return g_sym_variant.exchange(variant);
+}
 
 int64_t iluk_launch_count(void) { return g_launches.load(); }
 
@@ -352,7 +359,7 @@ int iluk_symbolic(const iluk_pattern *A, int k, iluk_sym **out, iluk_info *info,
       CKS(dalloc(&ar.lev, arena_cap, s));
     }
     ar.cap = arena_cap;
-    if (k >= 2) {  // rows wait on rows: announcements and arena start pending
+    if (!symbolic_indep(k)) {  // rows wait on rows: announcements and arena start pending
       CKS(cudaMemsetAsync(ar.meta, 0xff, n * sizeof(unsigned long long), s));
       CKS(cudaMemsetAsync(ar.col, 0xff, arena_cap * sizeof(int32_t), s));
       CKS(cudaMemsetAsync(ar.lev, 0xff, arena_cap, s));

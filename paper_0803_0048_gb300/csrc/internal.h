@@ -97,7 +97,12 @@ struct ProfScope {
     if (slot >= 0) prof_end(slot, s);
   }
 };
-int64_t hold_row();              // test hook: a row whose flag is never published
+int64_t hold_row();
+// The symbolic walk for k <= 1 (iluk_set_symbolic_variant): 0 independent
+// rows in ascending order, 1 independent rows in descending order, 2 the
+// general walk with waits (as for k >= 2).
+int symbolic_variant();
+inline bool symbolic_indep(int k) { return k <= 1 && symbolic_variant() != 2; }              // test hook: a row whose flag is never published
 
 // Sizes of the persistent grids (filled on first use per device).
 int num_sms();

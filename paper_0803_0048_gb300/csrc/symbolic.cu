@@ -20,7 +20,11 @@
 // afterwards (Sec. 3.4).
 //
 // With k <= 1 rows are independent (Sec. 3.3: only level-0 entries can cause
-// fill), so the warp reads the pivot rows straight from A and never waits.
+// fill), so the warp reads the pivot rows straight from A and never waits;
+// rows are claimed in ascending order, or last row first (the order Sec. 3.3
+// found fastest on a CPU), or they take the general walk with waits
+// (iluk_set_symbolic_variant, a study of the three: the results are the
+// same).
 #include "symbolic_body.cuh"
 
 namespace iluk {
@@ -70,18 +74,18 @@ k_symbolic_rows(int64_t n, const int64_t *__restrict__ arp, const int32_t *__res
                 int k, int32_t *arena_col, uint8_t *arena_lev, int64_t arena_cap,
                 unsigned long long *arena_top, int64_t *row_off, int32_t *row_len,
                 int32_t *row_ust, unsigned long long *meta, unsigned long long *ticket, DevErr *err,
-                int cap, int mapw, int64_t chunk, int64_t limit_ns) {
+                int cap, int mapw, int64_t chunk, int64_t limit_ns, int rev) {
   extern __shared__ __align__(16) unsigned char smem[];
   symbolic_rows_body<INDEP, false>(n, arp, aci, k, arena_col, arena_lev, arena_cap, arena_top, row_off,
                             row_len, row_ust, meta, ticket, err, cap, mapw, chunk, limit_ns,
-                            nullptr, smem);
+                            nullptr, smem, rev != 0);
 }
 
 // Chunk size: room for four of the longest rows (with their end markers); a
 // warp renews its chunk after a row whenever the longest row would no longer
 // fit, so every claimed row has its slot at once.  Rows that never wait on
 // other rows (k <= 1) allocate per row.
-int64_t symbolic_chunk(int k, int cap) { return k <= 1 ? 0 : 4 * ((int64_t)cap + 1); }
+int64_t symbolic_chunk(int k, int cap) { return symbolic_indep(k) ? 0 : 4 * ((int64_t)cap + 1); }
 
 // Warps per CTA and CTAs of the symbolic launch for this row capacity and map.
 static cudaError_t symbolic_shape(int k, int cap, int mapw, int *warps_out, size_t *smem_out,
@@ -93,7 +97,7 @@ static cudaError_t symbolic_shape(int k, int cap, int mapw, int *warps_out, size
   const size_t smem = per_warp * warps;
   int bps = 0;
   cudaError_t e;
-  if (k <= 1) {
+  if (symbolic_indep(k)) {
     e = cudaFuncSetAttribute(k_symbolic_rows<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
     if (e == cudaSuccess)
@@ -117,7 +121,7 @@ static cudaError_t symbolic_shape(int k, int cap, int mapw, int *warps_out, size
 // chunk held), given an estimate `rows_est` of the rows' entries.  The end
 // markers (one per row) come on top.
 int64_t symbolic_arena_slack(int64_t n, int k, int cap, int mapw, int64_t rows_est) {
-  if (k <= 1) return n;  // per-row allocation: only the end markers
+  if (symbolic_indep(k)) return n;  // per-row allocation: only the end markers
   int warps, bps;
   size_t smem;
   if (symbolic_shape(k, cap, mapw, &warps, &smem, &bps) != cudaSuccess) return 0;
@@ -137,7 +141,8 @@ cudaError_t launch_symbolic_rows(int64_t n, const int64_t *arp, const int32_t *a
   cudaError_t e = symbolic_shape(k, cap, mapw, &warps, &smem, &blocks_per_sm);
   if (e != cudaSuccess) return e;
   const int threads = warps * 32;
-  const bool indep = k <= 1;
+  const bool indep = symbolic_indep(k);
+  const int rev = indep && symbolic_variant() == 1;  // independent rows, last row first
   const int64_t chunk = symbolic_chunk(k, cap);
   int64_t want = (n + warps - 1) / warps;
   int64_t grid = (int64_t)blocks_per_sm * num_sms();
@@ -146,11 +151,11 @@ cudaError_t launch_symbolic_rows(int64_t n, const int64_t *arp, const int32_t *a
   if (indep)
     k_symbolic_rows<true><<<(unsigned)grid, threads, smem, s>>>(
         n, arp, aci, k, ar.col, ar.lev, ar.cap, ar.top, ar.row_off, ar.row_len, ar.row_ust,
-        ar.meta, ar.ticket, err, cap, mapw, chunk, wait_limit());
+        ar.meta, ar.ticket, err, cap, mapw, chunk, wait_limit(), rev);
   else
     k_symbolic_rows<false><<<(unsigned)grid, threads, smem, s>>>(
         n, arp, aci, k, ar.col, ar.lev, ar.cap, ar.top, ar.row_off, ar.row_len, ar.row_ust,
-        ar.meta, ar.ticket, err, cap, mapw, chunk, wait_limit());
+        ar.meta, ar.ticket, err, cap, mapw, chunk, wait_limit(), 0);
   note_launch();
   return cudaGetLastError();
 }

@@ -129,7 +129,7 @@ __device__ __forceinline__ void symbolic_rows_body(int64_t n, const int64_t *__r
                 unsigned long long *arena_top, int64_t *row_off, int32_t *row_len,
                 int32_t *row_ust, unsigned long long *meta, unsigned long long *ticket, DevErr *err,
                 int cap, int mapw, int64_t chunk, int64_t limit_ns,
-                unsigned long long *rinfo, unsigned char *smem) {
+                unsigned long long *rinfo, unsigned char *smem, bool rev = false) {
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   const int nwarps = blockDim.x >> 5;
@@ -145,8 +145,10 @@ __device__ __forceinline__ void symbolic_rows_body(int64_t n, const int64_t *__r
   for (;;) {
     unsigned long long tk = 0;
     if (lane == 0) tk = atomicAdd(ticket, 1ull);
-    const int64_t row = (int64_t)__shfl_sync(FULL_MASK, tk, 0);
-    if (row >= n) return;
+    const int64_t tkt = (int64_t)__shfl_sync(FULL_MASK, tk, 0);
+    if (tkt >= n) return;
+    // independent rows may go last row first (rev); waiting rows never do
+    const int64_t row = (INDEP && rev) ? n - 1 - tkt : tkt;
     if (earlier_failed(err, row)) return;
 
     // The row's slot: k >= 2 rows announce it now; the warp's chunk always

@@ -293,3 +293,50 @@ def test_solve_host_matches_oracle(k):
     x2, _ = P.solve_host(*[torch.from_numpy(a) for a in (A.rowptr, A.colind, A.val, b)], k,
                          restart=30, rtol=1e-10)
     assert_bits_equal(x2, xo, "host-buffer solve, pageable")
+
+
+@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("k", [0, 1])
+def test_symbolic_variants_for_k_le_1_match_oracle(variant, k):
+    """The k <= 1 walks (last row first; the general walk with waits) give
+    the oracle's pattern and levels, through iluk_symbolic and iluk_factor."""
+    cases = [W.random_sparse(301, 0.02, 5), W.conv_diff(9, 3, (50.0, 50.0, 50.0)),
+             W.random_band(3000, 9, 100, 11)]
+    prev = P.set_symbolic_variant(variant)
+    try:
+        for A in cases:
+            rp, ci, av = to_dev(A)
+            ref = oracle.factor(A, k)
+            S = P.symbolic(rp, ci, k)
+            S2, F2 = P.factor(rp, ci, av, k)
+            for SS in (S, S2):
+                grp, gci, glev, _ = [t.cpu().numpy() for t in SS.pattern()]
+                assert np.array_equal(grp, ref["rowptr"]) and np.array_equal(gci, ref["colind"])
+                assert np.array_equal(glev, ref["level"])
+            assert_bits_equal(F2.values(), ref["val"], "factors")
+    finally:
+        P.set_symbolic_variant(prev)
+
+
+@pytest.mark.parametrize("n,dens,k", [(1000, 0.01, 2), (1000, 0.01, 4), (2000, 0.004, 3),
+                                      (2000, 0.004, 5)])
+def test_long_rows_bit_exact(n, dens, k):
+    """Random matrices that fill in to rows of hundreds to ~1,500 entries
+    (the shapes of the paper's symbolic/numeric experiment): pattern, levels,
+    factors and one application against the oracle, through the two phases
+    and the one-call factorization."""
+    A = W.random_sparse(n, dens, 77)
+    rp, ci, av = to_dev(A)
+    ref = oracle.factor(A, k)
+    assert int(np.diff(ref["rowptr"]).max()) > 400
+    S = P.symbolic(rp, ci, k)
+    F = P.numeric(S, av)
+    S2, F2 = P.factor(rp, ci, av, k)
+    for SS, FF in ((S, F), (S2, F2)):
+        grp, gci, glev, _ = [t.cpu().numpy() for t in SS.pattern()]
+        assert np.array_equal(grp, ref["rowptr"]) and np.array_equal(gci, ref["colind"])
+        assert np.array_equal(glev, ref["level"])
+        assert_bits_equal(FF.values(), ref["val"], "factors")
+    p, pd = vec(13, n)
+    assert_bits_equal(F.apply(pd), oracle.apply(n, ref["rowptr"], ref["colind"], ref["val"], p),
+                      "apply")
