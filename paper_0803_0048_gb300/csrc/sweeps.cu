@@ -14,7 +14,9 @@
 // application and keeps the fastest for each direction:
 //  * WARP_CLUSTER: one warp per row in one 16-CTA thread-block cluster, x in
 //    the cluster's distributed shared memory on the producer's SM; the warp
-//    subtracts the longest ready prefix of its chain as values arrive.
+//    subtracts the longest ready prefix of its chain as values arrive, and
+//    when only the last entry is missing, the lane that owns it finishes the
+//    row alone (poll, multiply, subtract, divide, store).
 //    Suits deep, narrow DAGs, where the hand-off latency sets the time.
 //  * WARP_GRID: the same over all SMs with x in global memory (L2 hand-offs);
 //    suits wide DAGs, which need many SMs in flight.
@@ -428,10 +430,12 @@ k_sweep_wpr(const int32_t *__restrict__ order, int64_t len, int64_t n,
     // where x_row goes: this CTA's slot for the warp's current row
     const unsigned sa = SCOPE == 1 ? own_base + ((own_slot + (threadIdx.x >> 5)) << 3) : 0u;
     if (clear && lane == 0) clear[row] = __longlong_as_double((long long)kPending);
+    bool stored = false;  // the last-entry path below stored x_row already
     for (int b = 0; b < mylen && ok; b += 32) {
       const int e = b + lane;
       const bool act = e < mylen;
       const int cnt = (mylen - b) < 32 ? mylen - b : 32;
+      const bool last_batch = b + 32 >= mylen;
       int32_t c = 0;
       unsigned da = 0;
       double f = 0.0, x = 0.0, prod = 0.0;
@@ -462,6 +466,43 @@ k_sweep_wpr(const int32_t *__restrict__ order, int64_t len, int64_t n,
         for (int j = done; j < upto; ++j) s = __dsub_rn(s, __shfl_sync(FULL_MASK, prod, j));
         done = upto;
         if (done >= cnt) break;
+        if (last_batch && done == cnt - 1) {
+          // Only the row's last entry is missing (most often the one from
+          // the row that finished last): the lane that owns it polls alone,
+          // then subtracts, divides and stores, with no warp vote or shuffle
+          // between the value's arrival and the store.  Same operations,
+          // same order.
+          bool gave_up = false;
+          if (lane == done) {
+            for (unsigned jt = 0; !have; ++jt) {
+              x = wpr_load<SCOPE>(out, da, c);
+              if (!pending(x)) {
+                prod = __dmul_rn(f, x);
+                have = true;
+              } else if ((jt & 15u) == 15u &&
+                         (any_failed(err) || (int64_t)(globaltimer_ns() - t0) > limit_ns)) {
+                gave_up = true;
+                break;
+              } else if (SCOPE == 0) {
+                __nanosleep(backoff);
+                if (backoff < 128u) backoff <<= 1;
+              }
+            }
+            if (!gave_up) {
+              double r = __dsub_rn(s, prod);
+              if (DIVIDE) r = div_fin(r, rr);
+              if ((unsigned long long)__double_as_longlong(r) == kPending)
+                r = __longlong_as_double((long long)kQuietNaN);
+              if (SCOPE == 0)
+                st_val<true>(&out[row], r);
+              else
+                st_dsm(sa, r);
+            }
+          }
+          ok = __shfl_sync(FULL_MASK, gave_up ? 0 : 1, done) != 0;
+          stored = ok;
+          break;
+        }
         const bool stop = (it & 15u) == 15u &&
                           (any_failed(err) || (int64_t)(globaltimer_ns() - t0) > limit_ns);
         if (__any_sync(FULL_MASK, stop)) {
@@ -486,6 +527,10 @@ k_sweep_wpr(const int32_t *__restrict__ order, int64_t len, int64_t n,
     if (!ok) {
       if (lane == 0) set_err(err, row, ILUK_ETIMEOUT);
       break;
+    }
+    if (stored) {
+      __syncwarp();
+      continue;
     }
     if (DIVIDE) s = div_fin(s, rr);
     if ((unsigned long long)__double_as_longlong(s) == kPending)
