@@ -520,7 +520,7 @@ def batched(args):
     # every schedule the autotuner chooses from, one timed run each
     sched_ms = {}
     for sp in (False, True):
-        for w in (512, 1024):
+        for w in (256, 512, 1024):
             B.set_schedule(w, sp)
             B.solve()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

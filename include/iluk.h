@@ -462,8 +462,8 @@ int iluk_numeric_batched(const iluk_sym *S, int64_t nbatch, const double *A_vals
  * restart <= 64.
  * iluk_batch_solve: asynchronous, no host round trip and no allocation, so it
  * can be recorded in a CUDA graph by stream capture; the first call outside a
- * capture times the two CTA widths (512 and 1024 threads per item) and keeps
- * the faster (autotuner).  New values written into the same a_val / b buffers
+ * capture times the CTA widths (256, 512 and 1024 threads per item) and keeps
+ * the fastest (autotuner).  New values written into the same a_val / b buffers
  * are picked up by the next call.
  * iluk_batch_results: synchronous; infos (host, may be NULL) gets one entry per
  * item; returns the first item's non-OK status, if any.
@@ -482,15 +482,16 @@ int iluk_batch_create(const iluk_batch_item *items, int64_t nitems, int restart,
                       int maxit, iluk_batch **B, void *stream);
 int iluk_batch_solve(iluk_batch *B, void *stream);
 int iluk_batch_results(iluk_batch *B, iluk_info *infos, void *stream);
-/* The first solve outside a stream capture times the whole batch at 512
- * and 1024 threads per item, each with level-barrier sweeps (every level of
- * the in-CTA sweeps ends at a barrier) and with spinning sweeps (each warp
- * polls the values its rows need, no barriers), and keeps the fastest; the
- * results do not depend on the choice.  Threads per item chosen (0 until the
- * first solve) and whether the sweeps spin (1) or use level barriers (0). */
+/* The first solve outside a stream capture times the whole batch at 256,
+ * 512 and 1024 threads per item (as many items at once as fit on each SM:
+ * up to four, two, one), each with level-barrier sweeps (every level of the
+ * in-CTA sweeps ends at a barrier) and with spinning sweeps (each warp polls
+ * the values its rows need, no barriers), and keeps the fastest; the results
+ * do not depend on the choice.  Threads per item chosen (0 until the first
+ * solve) and whether the sweeps spin (1) or use level barriers (0). */
 int iluk_batch_width(const iluk_batch *B);
 int iluk_batch_spin(const iluk_batch *B);
-/* Fix the schedule instead (width 512 or 1024; ILUK_EINVAL otherwise). */
+/* Fix the schedule instead (width 256, 512 or 1024; ILUK_EINVAL otherwise). */
 int iluk_batch_set_schedule(iluk_batch *B, int width, int spin);
 void iluk_batch_destroy(iluk_batch *B);
 

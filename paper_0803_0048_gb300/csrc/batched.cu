@@ -330,12 +330,17 @@ k_batch_solve(const BatchItemDev *items, int64_t nitems, BatchResultDev *results
               BatchWork *work, unsigned long long *ticket, int m, double rtol, int maxit,
               int cap, int64_t limit_ns) {
   constexpr int kBWarps = NT / 32;
+  // dynamic shared memory: the inner-product partials, the Hessenberg matrix
+  // and rotations of a cycle (sized by m), then each warp's row slice
   extern __shared__ __align__(16) unsigned char smem[];
   double *sh = reinterpret_cast<double *>(smem);                 // kDotP doubles
-  double *svals = sh + kDotP;                                    // kBWarps * cap
+  double *H = sh + kDotP;                                        // (m + 1) * m
+  double *cs = H + (size_t)(m + 1) * m;                          // m
+  double *sn = cs + m;                                           // m
+  double *gv = sn + m;                                           // m + 1
+  double *yv = gv + m + 1;                                       // m
+  double *svals = yv + m;                                        // kBWarps * cap
   int32_t *scols = reinterpret_cast<int32_t *>(svals + (size_t)kBWarps * cap);
-  __shared__ double H[(kBMaxRestart + 1) * kBMaxRestart];
-  __shared__ double cs[kBMaxRestart], sn[kBMaxRestart], gv[kBMaxRestart + 1], yv[kBMaxRestart];
   __shared__ unsigned long long s_item;
   __shared__ int s_stop;
   const BatchWork wk = work[blockIdx.x];
@@ -455,8 +460,9 @@ k_batch_solve(const BatchItemDev *items, int64_t nitems, BatchResultDev *results
   }
 }
 
-size_t batch_smem_bytes(int nt, int cap) {
-  return (size_t)kDotP * 8 + (size_t)(nt / 32) * cap * 12;
+size_t batch_smem_bytes(int nt, int cap, int m) {
+  return (size_t)kDotP * 8 + ((size_t)(m + 1) * m + 4 * (size_t)m + 1) * 8 +
+         (size_t)(nt / 32) * cap * 12;
 }
 
 int batch_max_restart() { return kBMaxRestart; }
@@ -465,19 +471,27 @@ template <int NT>
 static cudaError_t launch_bs(const void *items, int64_t nitems, void *results, void *work,
                              int64_t nwork, unsigned long long *ticket, int m, double rtol,
                              int maxit, int cap, bool spin, cudaStream_t s) {
-  const size_t smem = batch_smem_bytes(NT, cap);
+  const size_t smem = batch_smem_bytes(NT, cap, m);
   auto kern = spin ? k_batch_solve<NT, true> : k_batch_solve<NT, false>;
   cudaError_t e =
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kern<<<(unsigned)nwork, NT, smem, s>>>((const BatchItemDev *)items, nitems,
+  // as many CTAs as fit on the GPU at once, within the work slots
+  int bps = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, NT, smem);
+  if (e != cudaSuccess) return e;
+  if (bps < 1) return cudaErrorInvalidConfiguration;
+  int64_t grid = (int64_t)bps * num_sms();
+  if (grid > nwork) grid = nwork;
+  kern<<<(unsigned)grid, NT, smem, s>>>((const BatchItemDev *)items, nitems,
                                          (BatchResultDev *)results, (BatchWork *)work, ticket, m,
                                          rtol, maxit, cap, wait_limit());
   note_launch();
   return cudaGetLastError();
 }
 
-// nt = threads per instance (512 or 1024); nwork CTAs (<= the work slots).
+// nt = threads per instance (256, 512 or 1024); at most nwork CTAs (the work
+// slots), as many as fit on the GPU at once.
 cudaError_t launch_batch_solve(int nt, bool spin, const void *items, int64_t nitems,
                                void *results, void *work, int64_t nwork,
                                unsigned long long *ticket, int m, double rtol, int maxit, int cap,
@@ -485,6 +499,9 @@ cudaError_t launch_batch_solve(int nt, bool spin, const void *items, int64_t nit
   ProfScope prof_scope(ILUK_PROF_BATCH, s);
   cudaError_t e = cudaMemsetAsync(ticket, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
+  if (nt == 256)
+    return launch_bs<256>(items, nitems, results, work, nwork, ticket, m, rtol, maxit, cap, spin,
+                          s);
   if (nt == 512)
     return launch_bs<512>(items, nitems, results, work, nwork, ticket, m, rtol, maxit, cap, spin,
                           s);

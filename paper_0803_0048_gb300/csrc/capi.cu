@@ -1189,12 +1189,12 @@ int iluk_batch_create(const iluk_batch_item *items, int64_t nitems, int restart,
     if (it.S->max_row > maxrow) maxrow = it.S->max_row;
   }
   B->cap = (maxrow + 31) & ~31;
-  if (batch_smem_bytes(1024, B->cap) + 40 * 1024 > (size_t)max_smem_optin()) {
+  if (batch_smem_bytes(1024, B->cap, restart) + 8 * 1024 > (size_t)max_smem_optin()) {
     delete B;
     return ILUK_ENOMEM;  // a row of F too long for the per-warp slices
   }
-  // Work slots: enough for the widest grid (two 512-thread CTAs per SM).
-  B->nwork = 2 * (int64_t)num_sms();
+  // Work slots: enough for the widest grid (up to four 256-thread CTAs per SM).
+  B->nwork = 4 * (int64_t)num_sms();
   const int64_t ldv = maxn;
   auto cleanup = [&]() { iluk_batch_destroy(B); };
   if (dalloc((unsigned char **)&B->items, hitems.size(), s) != cudaSuccess ||
@@ -1228,8 +1228,7 @@ int iluk_batch_create(const iluk_batch_item *items, int64_t nitems, int restart,
 }
 
 static cudaError_t batch_launch(iluk_batch *B, int width, bool spin, cudaStream_t s) {
-  const int64_t grid = (width == 512 ? 2 : 1) * (int64_t)num_sms();
-  return launch_batch_solve(width, spin, B->items, B->nitems, B->results, B->work, grid,
+  return launch_batch_solve(width, spin, B->items, B->nitems, B->results, B->work, B->nwork,
                             B->ticket, B->restart, B->rtol, B->maxit, B->cap, s);
 }
 
@@ -1244,14 +1243,14 @@ int iluk_batch_solve(iluk_batch *B, void *stream) {
     if (cs != cudaStreamCaptureStatusNone) {
       B->width = 1024;
     } else {
-      // Autotuner: run the whole batch at both widths, with level-barrier
+      // Autotuner: run the whole batch at each width, with level-barrier
       // sweeps and with spinning sweeps, and keep the fastest.
       cudaEvent_t e0, e1;
       cudaEventCreate(&e0);
       cudaEventCreate(&e1);
       float best = 1e30f;
       for (bool sp : {false, true})
-        for (int w : {512, 1024}) {
+        for (int w : {256, 512, 1024}) {
           cudaEventRecord(e0, s);
           CK(batch_launch(B, w, sp, s));
           cudaEventRecord(e1, s);
@@ -1279,7 +1278,7 @@ int iluk_batch_width(const iluk_batch *B) { return B ? B->width : 0; }
 int iluk_batch_spin(const iluk_batch *B) { return B && B->spin ? 1 : 0; }
 
 int iluk_batch_set_schedule(iluk_batch *B, int width, int spin) {
-  if (!B || (width != 512 && width != 1024)) return ILUK_EINVAL;
+  if (!B || (width != 256 && width != 512 && width != 1024)) return ILUK_EINVAL;
   B->width = width;
   B->spin = spin != 0;
   return ILUK_OK;

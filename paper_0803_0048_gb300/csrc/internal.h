@@ -218,7 +218,7 @@ cudaError_t launch_adjoint_scatter(int64_t n, const int64_t *rp, const int32_t *
 size_t batch_item_bytes();
 size_t batch_result_bytes();
 size_t batch_work_bytes();
-size_t batch_smem_bytes(int nt, int cap);
+size_t batch_smem_bytes(int nt, int cap, int m);
 int batch_max_restart();
 void batch_pack_item(void *dst, const iluk_sym *S, const int64_t *arp, const int32_t *aci,
                      const double *aval, const double *b, double *x);

@@ -11,8 +11,8 @@ through the single-instance path.
 Two batch shapes:
 * a small batch (three value sets on one 9^3 pattern and uneven grids of side
   6, 11, 13 and 33, the last one 35,937 rows), under every in-CTA schedule
-  (512/1024 threads per item, level-barrier or spinning sweeps) and under the
-  autotuner's choice;
+  (256/512/1024 threads per item, level-barrier or spinning sweeps) and under
+  the autotuner's choice;
 * the full batched workload (512 value sets on one 32^3 7-point pattern plus
   64 uneven grids with sides in [16, 40]), one launch, of which a seeded
   sample of items, always including the largest grid (40^3 = 64,000 rows)
@@ -96,8 +96,10 @@ def small():
     return items, host, ref
 
 
-@pytest.mark.parametrize("sched", ["auto", (512, False), (512, True), (1024, False), (1024, True)],
-                         ids=["auto", "512-level", "512-spin", "1024-level", "1024-spin"])
+@pytest.mark.parametrize("sched", ["auto", (256, False), (256, True), (512, False), (512, True),
+                                   (1024, False), (1024, True)],
+                         ids=["auto", "256-level", "256-spin", "512-level", "512-spin", "1024-level",
+                              "1024-spin"])
 def test_batched_items_bit_exact_vs_oracle(small, sched):
     items, host, ref = small
     for _, _, _, x in items:

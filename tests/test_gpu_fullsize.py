@@ -193,3 +193,33 @@ def test_band160k_k3_bit_exact_against_oracle_digests(path):
     assert (info.iters, info.cycles) == (want["gmres_iters"], want["gmres_cycles"])
     assert int(bits([info.relres])[0]) == want["gmres_relres_bits"]
     assert _sha(x) == want["gmres_x"]
+
+
+def test_adjoint_256_full_size_bit_exact_against_oracle():
+    """The differentiable solve at its full size (2D 256^2, n = 65,536,
+    ILU(2)-GMRES(30) to 1e-8): x of the forward solve and lambda = dL/db of
+    the adjoint solve bit for bit against the oracle (fixed-tree inner
+    products); dL/dA from the scatter exactly -lambda_i x_j."""
+    Pt, theta, beta, b, xt = W.adjoint_problem(256)
+    rp = torch.from_numpy(Pt.rowptr).cuda()
+    ci = torch.from_numpy(Pt.colind).cuda()
+    vals0 = W.fd_values(Pt, torch.from_numpy(theta), beta)
+    solver = P.IlukSolver(rp, ci, k=2, restart=30, rtol=1e-8)
+    vals = vals0.cuda().requires_grad_(True)
+    bd = torch.from_numpy(b).cuda().requires_grad_(True)
+    x = solver.solve(vals, bd)
+    ((x - torch.from_numpy(xt).cuda()) ** 2).sum().backward()
+    v = vals0.numpy()
+    A = W.CSR(Pt.n, Pt.rowptr, Pt.colind, v)
+    F = oracle.factor(A, 2)
+    st, xo, it, rel, cyc = oracle.gmres(A.n, A.rowptr, A.colind, v, b, oracle.PREC_ILU,
+                                        (F["rowptr"], F["colind"], F["val"]), 30, 1e-8,
+                                        dotmode=oracle.DOT_TREE)
+    assert st == 0 and solver.last_forward.iters == it
+    assert_bits_equal(x.detach(), xo, "forward x")
+    st, lam, gA, it2, rel2 = oracle.adjoint(A.n, A.rowptr, A.colind, v, F["rowptr"], F["colind"],
+                                            F["val"], xo, 2.0 * (xo - xt), 30, 1e-8,
+                                            dotmode=oracle.DOT_TREE)
+    assert st == 0 and solver.last_backward.iters == it2
+    assert_bits_equal(bd.grad, lam, "dL/db")
+    assert_bits_equal(vals.grad, gA, "dL/dA")
