@@ -259,13 +259,13 @@ def ours(args):
     sched = [L.SCHED_AUTO]
 
     def step(rp_, ci_, av_, b_):
-        st, row = P.validate(rp_, ci_)
-        assert st == 0
-        # symbolic and numeric phases in one launch (the numeric rows start as
-        # soon as their patterns are final)
-        S, F = P.factor(rp_, ci_, av_, Pb.k)
-        F.set_schedule(sched[0])
-        x, info = P.gmres(rp_, ci_, av_, b_, F, restart=Pb.restart, rtol=Pb.rtol)
+        # one C call (iluk_solve): pattern check; v_1 = b / ||b||; symbolic and
+        # numeric phases in one launch (the numeric rows start as soon as
+        # their patterns are final, and each factored row also takes its
+        # entry of L^-1 v_1); GMRES, whose first application then needs only
+        # the backward sweep
+        x, info, (S, F) = P.solve(rp_, ci_, av_, b_, k=Pb.k, restart=Pb.restart, rtol=Pb.rtol,
+                                  sched=sched[0], return_factors=True)
         return S, F, x, info
 
     # warm-up (the first apply times both sweep schedules; keep its choice)

@@ -415,14 +415,39 @@ int iluk_transpose(const iluk_pattern *A, const double *A_val, int64_t *t_rowptr
                    int32_t *t_colind, double *t_val, void *stream);
 
 /*
+ * iluk_factor(k) followed by gmres_solve(m, rtol, maxit) preconditioned by
+ * the factors, in one call and with the same results bit for bit (x,
+ * iterations, cycles, relres; x0 = 0, basis ILUK_BASIS_AUTO), device buffers
+ * as those calls take them.  What the one call adds is overlap: the first
+ * GMRES vector v_1 = b / ||b|| does not depend on the factors, so it is
+ * formed first and the one-launch factorization (k >= 2) solves L x = v_1
+ * beside its numeric phase, each row's entry of x computed by the warp that
+ * has just factored the row (the forward substitution of Eq. forwardsubA, in the
+ * same order and roundings as the forward sweep); the first application of
+ * the preconditioner then runs only its backward sweep.  When the one-launch
+ * path is not taken (k <= 1, a fallback to the two separate phases) the first
+ * application runs both sweeps, as gmres_solve does.  sched is the sweep
+ * schedule (as iluk_set_schedule; ILUK_SCHED_AUTO times them once F exists).
+ * The factorization is returned through S_out and F_out when both are
+ * non-NULL (the caller destroys them), else freed.  A failure of the
+ * factorization is reported as iluk_factor reports it (x then holds 0 or is
+ * unwritten); the factorization runs even when GMRES needs no iteration.
+ * Synchronous.
+ */
+int iluk_solve(const iluk_pattern *A, const double *A_val, int k, const double *b, double *x,
+               int m, double rtol, int maxit, int sched, iluk_sym **S_out, iluk_fac **F_out,
+               iluk_info *info, void *stream);
+
+/*
  * a1-a6 in one call, from HOST buffers: rowptr (int64[n+1]), colind
  * (int32[nnz]), val (double[nnz]) and b (double[n]) are host arrays (pinned
  * memory lets the copies run at full speed; pageable memory works too), x
  * (double[n]) is a host array that receives the solution.  The call copies
- * the inputs to the device on `stream`, runs iluk_validate, iluk_factor(k)
- * and gmres_solve(restart, rtol, maxit) preconditioned by the ILU(k) sweeps
- * with sweep schedule `sched` (as iluk_set_schedule; ILUK_SCHED_AUTO times
- * the schedules inside the call), copies x back and frees its device memory.
+ * the inputs to the device on `stream`, runs iluk_solve(k, restart, rtol,
+ * maxit, sched) on them (iluk_factor(k) and gmres_solve preconditioned by the
+ * ILU(k) sweeps, the first forward sweep inside the factorization; with
+ * ILUK_SCHED_AUTO the schedules are timed inside the call), copies x back
+ * and frees its device memory.
  * Synchronous; statuses and info as the calls it makes (x is written even
  * when GMRES returns ILUK_ENOCONV).
  */

@@ -101,6 +101,7 @@ SIGNATURES = [
     ("gmres_solve", I, [P, P, I, P, P, P, I, D, I, I, P, P]),
     ("gmres_solve_ex", I, [P, P, I, P, P, P, I, D, I, I, I, P, P]),
     ("iluk_transpose", I, [P, P, P, P, P, P]),
+    ("iluk_solve", I, [P, P, I, P, P, I, D, I, I, P, P, P, P]),
     ("iluk_solve_host", I, [I64, I64, P, P, P, P, P, I, I, D, I, I, P, P]),
     ("bicgstab_solve", I, [P, P, I, P, P, P, D, I, P, P]),
     ("tpilu_solve", I, [P, P, P, P, I, P, P, I, D, I, I, P, P, P]),

@@ -209,13 +209,43 @@ def factor(rowptr: torch.Tensor, colind: torch.Tensor, vals: torch.Tensor, k: in
 
 def solve(rowptr: torch.Tensor, colind: torch.Tensor, vals: torch.Tensor, b: torch.Tensor,
           k: int = 2, restart: int = 30, rtol: float = 1e-8, maxit: int = 10000,
-          precond: str = "ilu", check: bool = True):
+          precond: str = "ilu", check: bool = True, sched: int = 0, x=None,
+          return_factors: bool = False):
     """Solve A x = b in one call: the level-k factorization of A (``factor``),
     then right-preconditioned GMRES(restart) from x0 = 0 with the ILU(k) sweeps
     (precond "ilu"), the TPIILU inverses built from the same factors ("iilu"),
-    or no preconditioner ("none").  Returns (x, info)."""
+    or no preconditioner ("none").  Returns (x, info), plus (Symbolic,
+    Factors) with ``return_factors`` (precond "ilu" only).
+
+    With "ilu" this is one C call (iluk_solve): GMRES forms v_1 = b / ||b||
+    first, the one-launch factorization (k >= 2) solves L x = v_1 beside its
+    numeric phase, and the first preconditioner application runs only its
+    backward sweep; the results are those of ``factor`` then ``gmres`` bit
+    for bit.  ``sched`` is the sweep schedule (0: autotune once F exists)."""
     if precond not in ("ilu", "iilu", "none"):
         raise ValueError("precond must be 'ilu', 'iilu' or 'none'")
+    if return_factors and precond != "ilu":
+        raise ValueError("return_factors needs precond 'ilu'")
+    if precond == "ilu":
+        A = CsrPattern(rowptr, colind)
+        _vecs((vals, A.nnz, "values of A"),
+              (b, A.n, "b"),
+              (x, A.n, "x"))
+        xo = torch.empty_like(b) if x is None else x
+        hs, hf = C.c_void_p(), C.c_void_p()
+        info = L.Info()
+        st = L.load().iluk_solve(A.ref, _ptr(vals), int(k), _ptr(b), _ptr(xo), int(restart),
+                                 float(rtol), int(maxit), int(sched),
+                                 C.byref(hs) if return_factors else None,
+                                 C.byref(hf) if return_factors else None, C.byref(info),
+                                 C.c_void_p(_stream()))
+        facs = None
+        if return_factors and hf.value:
+            S = Symbolic(hs, A, k)
+            facs = (S, Factors(hf, S))
+        if check and st != L.OK:
+            raise IlukError(st, info, "iluk_solve")
+        return (xo, info, facs) if return_factors else (xo, info)
     prec = None
     if precond != "none":
         _, prec = factor(rowptr, colind, vals, k)

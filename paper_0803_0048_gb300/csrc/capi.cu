@@ -576,9 +576,20 @@ int iluk_numeric(const iluk_sym *S, const double *A_val, iluk_fac **out, iluk_in
 // iluk_numeric/iluk_refactor on S, or iluk_sym_depth).  Falls back to the two
 // calls for k <= 1 (rows need no other rows' patterns) and whenever the fused
 // launch cannot run or reports an error (the two calls then report it).
-int iluk_factor(const iluk_pattern *A, const double *A_val, int k, iluk_sym **S_out,
-                iluk_fac **F_out, iluk_info *info, void *stream) {
+}  // extern "C"
+
+// iluk_factor, with two additions for iluk_solve: `validated` skips the
+// pattern check the caller has made, and a non-null v0 asks the one-launch
+// path to solve L x = v0 beside its numeric phase (each row's entry of x as
+// soon as the row is factored).  Then *fwd_done tells whether it did: F->tmp
+// holds x and must be consumed by a backward sweep before any other apply.
+// The fallbacks (k <= 1, the two separate phases) leave *fwd_done false and
+// F->tmp pending, as iluk_factor does.
+static int factor_impl(const iluk_pattern *A, const double *A_val, int k, iluk_sym **S_out,
+                       iluk_fac **F_out, iluk_info *info, void *stream, bool validated,
+                       const double *v0, bool *fwd_done) {
   info_init(info);
+  if (fwd_done) *fwd_done = false;
   if (!S_out || !F_out || !A || (!A_val && A->nnz > 0)) return fail(info, ILUK_EINVAL);
   *S_out = nullptr;
   *F_out = nullptr;
@@ -629,8 +640,10 @@ int iluk_factor(const iluk_pattern *A, const double *A_val, int k, iluk_sym **S_
     return ILUK_OK;
   };
   if (k <= 1 || A->n == 0) return serial();
-  int st = iluk_validate(A, info, stream);
-  if (st != ILUK_OK) return st;
+  if (!validated) {
+    int st = iluk_validate(A, info, stream);
+    if (st != ILUK_OK) return st;
+  }
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t n = A->n, nnz = A->nnz;
 
@@ -640,9 +653,11 @@ int iluk_factor(const iluk_pattern *A, const double *A_val, int k, iluk_sym **S_
   double *aval_arena = nullptr;
   int64_t *scan_tmp = nullptr;
   int32_t *maxrow = nullptr;
+  double *xf = nullptr;  // L^-1 v0, when asked for; becomes F->tmp
   iluk_sym *S = nullptr;
   iluk_fac *F = nullptr;
   auto cleanup = [&]() {
+    dfree(xf, s);
     dfree(err, s);
     dfree(ar.col, s);
     dfree(ar.lev, s);
@@ -705,8 +720,12 @@ int iluk_factor(const iluk_pattern *A, const double *A_val, int k, iluk_sym **S_
   CKF(cudaMemsetAsync(nticket, 0, sizeof(unsigned long long), s));
   CKF(cudaMemsetAsync(ar.top, 0, sizeof(unsigned long long), s));
   CKF(launch_fill_err(err, s));
+  if (v0) {
+    CKF(dalloc(&xf, n, s));
+    CKF(launch_fill_pending(n, xf, s));
+  }
   CKF(launch_factor_fused(n, A->rowptr, A->colind, A_val, k, ar, aval_arena, rinfo, nticket, err,
-                          cap, mapw, ncap, s));
+                          cap, mapw, ncap, v0, xf, s));
   {
     int64_t row = -1;
     uint64_t need = 0;
@@ -743,10 +762,15 @@ int iluk_factor(const iluk_pattern *A, const double *A_val, int k, iluk_sym **S_
   F->S = S;
   CKF(dalloc(&F->val, nnzF, s));
   CKF(dalloc(&F->sync, sweep_sync_ints(n), s));
-  CKF(dalloc(&F->tmp, n, s));
+  if (xf) {
+    F->tmp = xf;
+    xf = nullptr;
+  } else {
+    CKF(dalloc(&F->tmp, n, s));
+    CKF(launch_fill_pending(n, F->tmp, s));
+  }
   CKF(dalloc(&F->rdiag, n, s));
   CKF(dalloc(&F->err, 2, s));
-  CKF(launch_fill_pending(n, F->tmp, s));
   CKF(launch_compact_values(n, ar, aval_arena, S->rowptr, F->val, s));
   CKF(launch_recip_diag(n, S->diag, F->val, F->rdiag, s));
   CKF(launch_fill_err(F->err, s));
@@ -758,7 +782,15 @@ int iluk_factor(const iluk_pattern *A, const double *A_val, int k, iluk_sym **S_
   cleanup();
   *S_out = S;
   *F_out = F;
+  if (fwd_done) *fwd_done = v0 != nullptr;
   return fail(info, ILUK_OK);
+}
+
+extern "C" {
+
+int iluk_factor(const iluk_pattern *A, const double *A_val, int k, iluk_sym **S_out,
+                iluk_fac **F_out, iluk_info *info, void *stream) {
+  return factor_impl(A, A_val, k, S_out, F_out, info, stream, false, nullptr, nullptr);
 }
 
 int iluk_refactor(iluk_fac *F, const double *A_val, iluk_info *info, void *stream) {
@@ -838,14 +870,19 @@ static int pick_schedule(iluk_fac *F, cudaStream_t s) {
   cudaStreamIsCapturing(s, &cs);
   if (cs != cudaStreamCaptureStatusNone) return ILUK_SCHED_WARP_GRID;
   const iluk_sym *S = F->S;
-  double *p = nullptr, *y = nullptr;
-  if (dalloc(&p, S->n, s) != cudaSuccess || dalloc(&y, S->n, s) != cudaSuccess) {
+  // the trial sweeps use their own intermediate vector: F->tmp may hold a
+  // forward sweep's result that a backward sweep has yet to consume
+  double *p = nullptr, *y = nullptr, *t = nullptr;
+  if (dalloc(&p, S->n, s) != cudaSuccess || dalloc(&y, S->n, s) != cudaSuccess ||
+      dalloc(&t, S->n, s) != cudaSuccess) {
     dfree(p, s);
+    dfree(y, s);
     return ILUK_SCHED_WARP_GRID;
   }
   // a right-hand side of ones: realistic operands for the divisions (zeros
   // would all take the IEEE fallback of the reciprocal division)
   launch_fill_value(S->n, p, 1.0, s);
+  launch_fill_pending(S->n, t, s);
   float best_f = 1e30f, best_b = 1e30f;
   int pick_f = ILUK_SCHED_WARP_GRID, pick_b = ILUK_SCHED_WARP_GRID;
   const bool prof = g_prof.exchange(false);  // the trial runs are not profiled
@@ -874,10 +911,10 @@ static int pick_schedule(iluk_fac *F, cudaStream_t s) {
       LevelOrder none;
       cudaEventRecord(e0, s);
       const cudaError_t ef = launch_apply(S->n, S->rowptr, S->colind, S->diag, F->val, F->rdiag,
-                                          sweep_fwd(S), none, p, F->tmp, y, 0, sched, F->err, s);
+                                          sweep_fwd(S), none, p, t, y, 0, sched, F->err, s);
       cudaEventRecord(e1, s);
       const cudaError_t eb = launch_apply(S->n, S->rowptr, S->colind, S->diag, F->val, F->rdiag,
-                                          none, sweep_bwd(S), p, F->tmp, y, 0, sched, F->err, s);
+                                          none, sweep_bwd(S), p, t, y, 0, sched, F->err, s);
       cudaEventRecord(e2, s);
       cudaEventSynchronize(e2);
       float a = 0, b = 0;
@@ -905,14 +942,27 @@ static int pick_schedule(iluk_fac *F, cudaStream_t s) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaEventDestroy(e2);
-  // the timing runs may leave tmp partly armed: restore the invariant
-  launch_fill_pending(S->n, F->tmp, s);
   launch_fill_err(F->err, s);
   g_prof.store(prof);
   dfree(p, s);
   dfree(y, s);
+  dfree(t, s);
   F->sched = pick_f | (pick_b << 8);
   return F->sched;
+}
+
+// The lockstep kinds (flags, single CTA, cluster) walk the padded level
+// orders; a factorization from iluk_factor has only index orders until they
+// are built, which happens here the first time such a schedule is used.
+static int orders_for(iluk_fac *F, int sched, cudaStream_t s) {
+  auto padded = [](int b) {
+    const int kind = b & 0xf;
+    return kind == ILUK_SCHED_FLAGS || kind == ILUK_SCHED_SINGLE_CTA ||
+           kind == ILUK_SCHED_CLUSTER;
+  };
+  if (F->S->levels_built || !(padded(sched & 0xff) || padded((sched >> 8) & 0xff)))
+    return ILUK_OK;
+  return ensure_levels(F->S, s);
 }
 
 int iluk_apply_sched(iluk_fac *F, const double *p, double *y, int transpose, int sched,
@@ -922,6 +972,10 @@ int iluk_apply_sched(iluk_fac *F, const double *p, double *y, int transpose, int
   cudaStream_t s = (cudaStream_t)stream;
   const iluk_sym *S = F->S;
   if (sched == ILUK_SCHED_AUTO) sched = pick_schedule(F, s);
+  if (!transpose) {
+    const int st = orders_for(F, sched, s);
+    if (st != ILUK_OK) return st;
+  }
   if (transpose) {
     int st = ensure_transpose(F, s);
     if (st != ILUK_OK) return st;
@@ -939,17 +993,25 @@ int iluk_apply(iluk_fac *F, const double *p, double *y, int transpose, void *str
   return iluk_apply_sched(F, p, y, transpose, ILUK_SCHED_AUTO, stream);
 }
 
-int iluk_set_schedule(iluk_fac *F, int sched) {
-  // a schedule byte: a kind, plus a width (256..1024 threads) for the
-  // warp-per-row kinds only
+}  // extern "C"
+
+// A packed schedule (forward | backward << 8) that iluk_set_schedule takes:
+// each byte a kind, plus a width (256..1024 threads) for the warp-per-row
+// kinds only.
+static bool sched_valid(int sched) {
   auto valid = [](int b) {
     const int kind = b & 0xf, w = (b >> 4) & 0xf;
     if (kind > ILUK_SCHED_WARP_CLUSTER) return false;
     return w == 0 || ((kind == ILUK_SCHED_WARP_GRID || kind == ILUK_SCHED_WARP_CLUSTER) &&
                       w >= 2 && w <= 8);
   };
-  if (!F || sched < 0 || sched > 0xffff || !valid(sched & 0xff) || !valid((sched >> 8) & 0xff))
-    return ILUK_EINVAL;
+  return sched >= 0 && sched <= 0xffff && valid(sched & 0xff) && valid((sched >> 8) & 0xff);
+}
+
+extern "C" {
+
+int iluk_set_schedule(iluk_fac *F, int sched) {
+  if (!F || !sched_valid(sched)) return ILUK_EINVAL;
   F->sched = sched;
   return ILUK_OK;
 }
@@ -1321,15 +1383,28 @@ int gmres_solve(const iluk_pattern *A, const double *A_val, int prec_kind, void 
                         ILUK_BASIS_AUTO, info, stream);
 }
 
-int gmres_solve_ex(const iluk_pattern *A, const double *A_val, int prec_kind, void *prec,
-                   const double *b, double *x, int m, double rtol, int maxit, int transpose,
-                   int basis, iluk_info *info, void *stream) {
+}  // extern "C"
+
+// The ILU(k) factorization made inside GMRES once v_1 = r_0 / ||r_0|| is
+// known (iluk_solve): it may solve L x = v_1 beside its numeric phase, which
+// saves the first application its forward sweep.  Returns an iluk status;
+// on success *F is the factorization and *fwd_done whether F->tmp holds
+// L^-1 v_1; on failure finfo describes it.
+struct FactorHook {
+  virtual int operator()(const double *v1, iluk_fac **F, bool *fwd_done, iluk_info *finfo) = 0;
+  virtual ~FactorHook() = default;
+};
+
+static int gmres_impl(const iluk_pattern *A, const double *A_val, int prec_kind, void *prec,
+                      const double *b, double *x, int m, double rtol, int maxit, int transpose,
+                      int basis, iluk_info *info, void *stream, FactorHook *hook) {
   info_init(info);
   if (!pattern_args_ok(A) || m < 1 || maxit < 0) return fail(info, ILUK_EINVAL);
   if (basis < ILUK_BASIS_AUTO || basis > ILUK_BASIS_MINV_VY) return fail(info, ILUK_EINVAL);
   if ((A->n > 0 && (!b || !x)) || (A->nnz > 0 && !A_val)) return fail(info, ILUK_EINVAL);
-  if (prec_kind != ILUK_PREC_NONE && !prec) return fail(info, ILUK_EINVAL);
+  if (prec_kind != ILUK_PREC_NONE && !prec && !hook) return fail(info, ILUK_EINVAL);
   if (transpose && prec_kind == ILUK_PREC_IILU) return fail(info, ILUK_EINVAL);
+  if (hook && (transpose || prec_kind != ILUK_PREC_ILU)) return fail(info, ILUK_EINVAL);
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t n = A->n;
   iluk_fac *F = prec_kind == ILUK_PREC_ILU ? (iluk_fac *)prec : nullptr;
@@ -1394,7 +1469,12 @@ int gmres_solve_ex(const iluk_pattern *A, const double *A_val, int prec_kind, vo
     int st = ensure_transpose(F, s);
     if (st != ILUK_OK) return fail(info, st);
   }
-  const int sched = F ? pick_schedule(F, s) : 0;
+  int sched = F ? pick_schedule(F, s) : 0;
+  if (F && !transpose) {
+    const int st = orders_for(F, sched, s);
+    if (st != ILUK_OK) return fail(info, st);
+  }
+  bool fwd_ready = false;  // F->tmp holds L^-1 v_1 (made by the factorization)
 
   auto precond = [&](const double *in, double *outv) -> cudaError_t {
     if (F) {
@@ -1433,6 +1513,17 @@ int gmres_solve_ex(const iluk_pattern *A, const double *A_val, int prec_kind, vo
       if (iters >= maxit) { status = ILUK_ENOCONV; break; }
       ++cycles;
       CK(launch_scale_div(n, w, dsc + 1, V, s));
+      if (hook && !F) {
+        iluk_info finfo;
+        const int hst = (*hook)(V, &F, &fwd_ready, &finfo);
+        if (hst != ILUK_OK) {
+          if (info) *info = finfo;
+          return hst;
+        }
+        sched = pick_schedule(F, s);
+        const int ost = orders_for(F, sched, s);
+        if (ost != ILUK_OK) return fail(info, ost);
+      }
       gv[0] = beta;
       int jend = -1;
       bool bad = false;
@@ -1440,7 +1531,13 @@ int gmres_solve_ex(const iluk_pattern *A, const double *A_val, int prec_kind, vo
         double *vj = V + (size_t)j * ldv;
         double *hc = Hd + (size_t)j * (m + 1);  // column j of H
         double *zj = store_z ? Z + (size_t)j * ldv : Z;
-        CK(precond(vj, zj));
+        if (fwd_ready) {  // z_1 from the forward sweep the factorization made
+          fwd_ready = false;
+          CK(launch_apply_backward(n, F->S->rowptr, F->S->colind, F->S->diag, F->val, F->rdiag,
+                                   sweep_bwd(F->S), F->tmp, zj, sched, F->err, s));
+        } else {
+          CK(precond(vj, zj));
+        }
         CK(launch_spmv(n, orp, oci, ov, zj, w, nullptr, s));
         CK(launch_dot(n, w, V, hc + 0, 0, ds, s));
         for (int i = 0; i <= j; ++i) {
@@ -1528,6 +1625,77 @@ int gmres_solve_ex(const iluk_pattern *A, const double *A_val, int prec_kind, vo
   return status;
 }
 
+extern "C" {
+
+int gmres_solve_ex(const iluk_pattern *A, const double *A_val, int prec_kind, void *prec,
+                   const double *b, double *x, int m, double rtol, int maxit, int transpose,
+                   int basis, iluk_info *info, void *stream) {
+  return gmres_impl(A, A_val, prec_kind, prec, b, x, m, rtol, maxit, transpose, basis, info,
+                    stream, nullptr);
+}
+
+int iluk_solve(const iluk_pattern *A, const double *A_val, int k, const double *b, double *x,
+               int m, double rtol, int maxit, int sched, iluk_sym **S_out, iluk_fac **F_out,
+               iluk_info *info, void *stream) {
+  info_init(info);
+  if (S_out) *S_out = nullptr;
+  if (F_out) *F_out = nullptr;
+  if (!pattern_args_ok(A) || (A->nnz > 0 && !A_val) || (A->n > 0 && (!b || !x)) || k < 0 ||
+      k > 250 || m < 1 || maxit < 0 || !sched_valid(sched))
+    return fail(info, ILUK_EINVAL);
+  int st = iluk_validate(A, info, stream);
+  if (st != ILUK_OK) return st;
+  struct Hook : FactorHook {
+    const iluk_pattern *A;
+    const double *A_val;
+    int k, sched;
+    void *stream;
+    iluk_sym *S = nullptr;
+    iluk_fac *F = nullptr;
+    int operator()(const double *v1, iluk_fac **Fo, bool *fwd_done, iluk_info *finfo) override {
+      int st2 = factor_impl(A, A_val, k, &S, &F, finfo, stream, true, v1, fwd_done);
+      if (st2 == ILUK_OK) st2 = iluk_set_schedule(F, sched);
+      if (st2 != ILUK_OK) {
+        if (F) iluk_fac_destroy(F);
+        if (S) iluk_sym_destroy(S);
+        F = nullptr;
+        S = nullptr;
+        *fwd_done = false;
+        return st2;
+      }
+      *Fo = F;
+      return ILUK_OK;
+    }
+  } hook;
+  hook.A = A;
+  hook.A_val = A_val;
+  hook.k = k;
+  hook.sched = sched;
+  hook.stream = stream;
+  st = gmres_impl(A, A_val, ILUK_PREC_ILU, nullptr, b, x, m, rtol, maxit, 0, ILUK_BASIS_AUTO,
+                  info, stream, &hook);
+  if (!hook.F && st == ILUK_OK) {
+    // GMRES ended before its first application (b = 0, or x = 0 already
+    // within rtol): the factorization still runs, and its failures count
+    iluk_info finfo;
+    const int fst = factor_impl(A, A_val, k, &hook.S, &hook.F, &finfo, stream, true, nullptr,
+                                nullptr);
+    if (fst != ILUK_OK) {
+      if (info) *info = finfo;
+      return fst;
+    }
+    iluk_set_schedule(hook.F, sched);
+  }
+  if (F_out && S_out && hook.F) {
+    *S_out = hook.S;
+    *F_out = hook.F;
+  } else {
+    if (hook.F) iluk_fac_destroy(hook.F);
+    if (hook.S) iluk_sym_destroy(hook.S);
+  }
+  return st;
+}
+
 int bicgstab_solve(const iluk_pattern *A, const double *A_val, int prec_kind, void *prec,
                    const double *b, double *x, double rtol, int maxit, iluk_info *info,
                    void *stream) {
@@ -1560,6 +1728,10 @@ int bicgstab_solve(const iluk_pattern *A, const double *A_val, int prec_kind, vo
   CK(dalloc(&ds.counter, 1, s));
   CK(cudaMemsetAsync(ds.counter, 0, sizeof(unsigned), s));
   const int sched = F ? pick_schedule(F, s) : 0;
+  if (F) {
+    const int st = orders_for(F, sched, s);
+    if (st != ILUK_OK) return fail(info, st);
+  }
   auto precond = [&](const double *in, double *outv) -> cudaError_t {
     if (F)
       return launch_apply(n, F->S->rowptr, F->S->colind, F->S->diag, F->val, F->rdiag,
@@ -1692,13 +1864,9 @@ int iluk_solve_host(int64_t n, int64_t nnz, const int64_t *rowptr, const int32_t
   }
   if (n > 0) CK(cudaMemcpyAsync(d_b, b, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, s));
   const iluk_pattern A{n, nnz, d_rp, d_ci};
-  int st = iluk_validate(&A, info, stream);
-  if (st != ILUK_OK) return st;
-  st = iluk_factor(&A, d_v, k, &S, &F, info, stream);
-  if (st != ILUK_OK) return st;
-  st = iluk_set_schedule(F, sched);
-  if (st != ILUK_OK) return fail(info, st);
-  st = gmres_solve(&A, d_v, ILUK_PREC_ILU, F, d_b, d_x, restart, rtol, maxit, 0, info, stream);
+  const int st = iluk_solve(&A, d_v, k, d_b, d_x, restart, rtol, maxit, sched, nullptr, nullptr,
+                            info, stream);
+  if (st != ILUK_OK && st != ILUK_ENOCONV) return st;
   if (n > 0) CK(cudaMemcpyAsync(x, d_x, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   return st;

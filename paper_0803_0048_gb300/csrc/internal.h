@@ -137,7 +137,8 @@ cudaError_t launch_compact_values(int64_t n, const SymArena &ar, const double *a
 cudaError_t launch_factor_fused(int64_t n, const int64_t *arp, const int32_t *aci,
                                 const double *aval, int k, const SymArena &ar, double *arena_val,
                                 unsigned long long *rinfo, unsigned long long *num_ticket,
-                                DevErr *err, int scap, int mapw, int ncap, cudaStream_t s);
+                                DevErr *err, int scap, int mapw, int ncap, const double *v0,
+                                double *xf, cudaStream_t s);
 cudaError_t launch_recip_diag(int64_t n, const int64_t *diag, const double *fval, DivPrep *rdiag,
                               cudaStream_t s);
 cudaError_t build_index_orders(int64_t n, LevelOrder *fwd, LevelOrder *bwd, cudaStream_t s);
@@ -163,6 +164,12 @@ cudaError_t launch_numeric_batched(const iluk_sym *S, int64_t nbatch, const doub
 
 // Sweeps (sweeps.cu)
 size_t sweep_sync_ints(int64_t n);
+// The backward half of launch_apply alone, for a tmp that already holds
+// L^-1 p (the factorization computed it beside the numeric phase).
+cudaError_t launch_apply_backward(int64_t n, const int64_t *rp, const int32_t *ci,
+                                  const int64_t *dg, const double *v, const DivPrep *rd,
+                                  const LevelOrder &bwd, double *tmp, double *y, int sched,
+                                  DevErr *err, cudaStream_t s);
 // y = (LU)^-1 p (or ^-T on the transposed arrays).  tmp must hold the pending
 // marker in every entry on entry, and does again on exit.
 cudaError_t launch_apply(int64_t n, const int64_t *rp, const int32_t *ci, const int64_t *dg,

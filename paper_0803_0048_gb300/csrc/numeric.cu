@@ -428,13 +428,76 @@ __device__ __forceinline__ bool wait_word(const unsigned long long *p, unsigned 
   }
 }
 
+// The forward substitution L x = v0 (L unit lower triangular, its strictly
+// lower part the multipliers f_ih of Eq. 1) for one row, taken by the warp that
+// has just factored that row: x_i = v0_i - sum over h in L(i), ascending, of
+// f_ih * x_h, each product and each difference rounded once, in the order of
+// the stand-alone forward sweep, so the result is bit for bit the sweep's.
+// The row's multipliers and columns are still in the warp's shared memory.
+// x lives in global memory, filled with kPendingF before the launch; x_h is
+// polled until it leaves that state (the rows that own x_h were claimed
+// earlier and are resident, so every wait ends).  A value that would equal
+// the marker is stored as a quiet NaN, as the sweep does.  Warp-uniform;
+// false on time-out or when a row before `row` has failed.
+__device__ __forceinline__ bool forward_entry(int64_t row, int dp, const double *lmul,
+                                              const int32_t *lcol, const double *v0, double *x,
+                                              const DevErr *err, int64_t limit_ns, int lane) {
+  double s = v0[row];
+  for (int b = 0; b < dp; b += 32) {
+    const int e = b + lane;
+    const bool act = e < dp;
+    const int cnt = dp - b < 32 ? dp - b : 32;
+    double f = 0.0, prod = 0.0;
+    int32_t c = 0;
+    bool have = !act;
+    if (act) {
+      c = lcol[e];
+      f = lmul[e];
+      const double xh = ld_gpu(&x[c]);
+      if (!pend_f(xh)) {
+        prod = __dmul_rn(f, xh);
+        have = true;
+      }
+    }
+    int done = 0;
+    const uint64_t t0 = globaltimer_ns();
+    unsigned backoff = 16;
+    for (unsigned it = 0;; ++it) {
+      // subtract the ready products in order, up to the first missing one
+      const unsigned ready = __ballot_sync(FULL_MASK, have);
+      const unsigned rest = ~(ready >> done);
+      const int run = rest == 0u ? 32 - done : __ffs(rest) - 1;
+      const int upto = done + run < cnt ? done + run : cnt;
+      for (int j = done; j < upto; ++j) s = __dsub_rn(s, __shfl_sync(FULL_MASK, prod, j));
+      done = upto;
+      if (done >= cnt) break;
+      const bool stop = (it & 15u) == 15u &&
+                        (earlier_failed(err, row) || (int64_t)(globaltimer_ns() - t0) > limit_ns);
+      if (__any_sync(FULL_MASK, stop)) return false;
+      __nanosleep(backoff);
+      if (backoff < 128u) backoff <<= 1;
+      if (!have) {
+        const double xh = ld_gpu(&x[c]);
+        if (!pend_f(xh)) {
+          prod = __dmul_rn(f, xh);
+          have = true;
+        }
+      }
+    }
+  }
+  if ((unsigned long long)__double_as_longlong(s) == kPendingF)
+    s = __longlong_as_double((long long)0x7FF8000000000000ll);
+  if (lane == 0) asm volatile("st.relaxed.gpu.global.f64 [%0], %1;" ::"l"(x + row), "d"(s) : "memory");
+  return true;
+}
+
 __device__ void numeric_arena_rows(int64_t n, const int64_t *__restrict__ arp,
                                    const int32_t *__restrict__ aci,
                                    const double *__restrict__ aval, const int32_t *acol,
                                    double *vals, const unsigned long long *meta,
                                    const unsigned long long *rinfo, unsigned long long *ticket,
                                    DevErr *err, int cap, int map_cap, int64_t limit_ns,
-                                   unsigned char *smem) {
+                                   const double *v0, double *xf, unsigned char *smem) {
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   const int nwarps = blockDim.x >> 5;
@@ -533,6 +596,12 @@ __device__ void numeric_arena_rows(int64_t n, const int64_t *__restrict__ arp,
       vals[dst] = svals[q];
     }
     __syncwarp();
+    // the row's entry of L x = v0, when the launch carries the first
+    // right-hand side
+    if (xf && !forward_entry(row, dp, svals, scols, v0, xf, err, limit_ns, lane)) {
+      if (lane == 0 && !earlier_failed(err, row)) set_err(err, row, ILUK_ETIMEOUT);
+    }
+    __syncwarp();
   }
 }
 
@@ -543,7 +612,7 @@ k_factor_fused(int64_t n, const int64_t *__restrict__ arp, const int32_t *__rest
                int64_t *row_off, int32_t *row_len, int32_t *row_ust, unsigned long long *meta,
                unsigned long long *rinfo, unsigned long long *sym_ticket,
                unsigned long long *num_ticket, DevErr *err, int scap, int mapw, int64_t chunk,
-               int ncap, int nmap, int g_sym, int64_t limit_ns) {
+               int ncap, int nmap, int g_sym, int64_t limit_ns, const double *v0, double *xf) {
   extern __shared__ __align__(16) unsigned char smem[];
   if ((int)blockIdx.x < g_sym)
     symbolic_rows_body<false, true>(n, arp, aci, k, arena_col, arena_lev, arena_cap, arena_top,
@@ -551,7 +620,7 @@ k_factor_fused(int64_t n, const int64_t *__restrict__ arp, const int32_t *__rest
                                     chunk, limit_ns, rinfo, smem);
   else
     numeric_arena_rows(n, arp, aci, aval, arena_col, arena_val, meta, rinfo, num_ticket, err,
-                       ncap, nmap, limit_ns, smem);
+                       ncap, nmap, limit_ns, v0, xf, smem);
 }
 
 // Shared memory per warp: a row of F (value, pivot info, column: 20 bytes per
@@ -641,7 +710,8 @@ static cudaError_t launch_numeric_impl(const iluk_sym *S, int64_t nbatch, const 
 cudaError_t launch_factor_fused(int64_t n, const int64_t *arp, const int32_t *aci,
                                 const double *aval, int k, const SymArena &ar, double *arena_val,
                                 unsigned long long *rinfo, unsigned long long *num_ticket,
-                                DevErr *err, int scap, int mapw, int ncap, cudaStream_t s) {
+                                DevErr *err, int scap, int mapw, int ncap, const double *v0,
+                                double *xf, cudaStream_t s) {
   ProfScope prof_scope(ILUK_PROF_FACTOR, s);
   const int warps = kNumThreads / 32;
   const size_t sym_smem = (symbolic_smem_per_warp(scap) + symbolic_map_per_warp(mapw)) * warps;
@@ -675,7 +745,7 @@ cudaError_t launch_factor_fused(int64_t n, const int64_t *arp, const int32_t *ac
                   (void *)&ar.top, (void *)&ar.row_off, (void *)&ar.row_len, (void *)&ar.row_ust,
                   (void *)&ar.meta, (void *)&rinfo, (void *)&ar.ticket, (void *)&num_ticket,
                   (void *)&err, (void *)&sc, (void *)&mw, (void *)&ch, (void *)&nc, (void *)&nm,
-                  (void *)&gs, (void *)&limit};
+                  (void *)&gs, (void *)&limit, (void *)&v0, (void *)&xf};
   e = cudaLaunchCooperativeKernel((const void *)k_factor_fused, dim3((unsigned)grid),
                                   dim3(kNumThreads), args, smem, s);
   note_launch();

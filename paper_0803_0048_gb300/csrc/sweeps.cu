@@ -807,6 +807,32 @@ static cudaError_t run_sweep(int64_t n, const LevelOrder &lo, const int64_t *rp,
   return e;
 }
 
+// One schedule byte made usable for n rows: an unknown kind becomes the
+// warp-per-row grid, a cluster kind without a usable cluster likewise, and a
+// width only stays with the warp-per-row kinds (256..1024 threads).
+static int usable_sched(int64_t n, int sc) {
+  int kind = sc & 0xf, w = (sc >> 4) & 0xf;
+  if (kind < ILUK_SCHED_FLAGS || kind > ILUK_SCHED_WARP_CLUSTER) kind = ILUK_SCHED_WARP_GRID;
+  if ((kind == ILUK_SCHED_CLUSTER || kind == ILUK_SCHED_WARP_CLUSTER) && cluster_size_for(n) == 0)
+    kind = ILUK_SCHED_WARP_GRID;
+  if ((kind != ILUK_SCHED_WARP_GRID && kind != ILUK_SCHED_WARP_CLUSTER) || w < 2 || w > 8) w = 0;
+  return kind | (w << 4);
+}
+
+cudaError_t launch_apply_backward(int64_t n, const int64_t *rp, const int32_t *ci,
+                                  const int64_t *dg, const double *v, const DivPrep *rd,
+                                  const LevelOrder &bwd, double *tmp, double *y, int sched,
+                                  DevErr *err, cudaStream_t s) {
+  // tmp already holds L^-1 p; y is armed here as the forward sweep would
+  // have armed it, and the backward sweep re-arms tmp as usual
+  int sb = (sched >> 8) & 0xff;
+  if (sb == 0) sb = sched & 0xff;
+  cudaError_t e = launch_fill_pending(n, y, s);
+  if (e != cudaSuccess) return e;
+  return run_sweep<false, true>(n, bwd, rp, ci, dg, v, rd, tmp, y, tmp, usable_sched(n, sb), err,
+                                s);
+}
+
 cudaError_t launch_apply(int64_t n, const int64_t *rp, const int32_t *ci, const int64_t *dg,
                          const double *v, const DivPrep *rd, const LevelOrder &fwd,
                          const LevelOrder &bwd,
@@ -816,18 +842,8 @@ cudaError_t launch_apply(int64_t n, const int64_t *rp, const int32_t *ci, const 
   // (a single value applies to both).
   int sf = sched & 0xff, sb = (sched >> 8) & 0xff;
   if (sb == 0) sb = sf;
-  auto fix = [&](int sc) {
-    int kind = sc & 0xf, w = (sc >> 4) & 0xf;
-    if (kind < ILUK_SCHED_FLAGS || kind > ILUK_SCHED_WARP_CLUSTER) kind = ILUK_SCHED_WARP_GRID;
-    if ((kind == ILUK_SCHED_CLUSTER || kind == ILUK_SCHED_WARP_CLUSTER) &&
-        cluster_size_for(n) == 0)
-      kind = ILUK_SCHED_WARP_GRID;
-    if ((kind != ILUK_SCHED_WARP_GRID && kind != ILUK_SCHED_WARP_CLUSTER) || w < 2 || w > 8)
-      w = 0;  // widths 256..1024 threads
-    return kind | (w << 4);
-  };
-  sf = fix(sf);
-  sb = fix(sb);
+  sf = usable_sched(n, sf);
+  sb = usable_sched(n, sb);
   cudaError_t e;
   // tmp is pending on entry (left so by the previous backward sweep); the
   // forward sweep re-arms y, the backward sweep re-arms tmp.

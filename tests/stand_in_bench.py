@@ -82,6 +82,14 @@ P.factor = lambda rp, ci, av, k: (Sym(), Fac())
 P.gmres = lambda *a, **k: (torch.zeros(n, dtype=torch.float64), info)
 
 
+def solve(rp, ci, av, b, k=2, restart=30, rtol=1e-8, sched=0, return_factors=False, **kw):
+    assert return_factors
+    return torch.zeros(n, dtype=torch.float64), info, (Sym(), Fac())
+
+
+P.solve = solve
+
+
 def solve_host(rp, ci, av, b, k, restart, rtol, sched=0, x=None):
     assert rp.device.type == "cpu" and x is not None and x.device.type == "cpu"
     x.zero_()

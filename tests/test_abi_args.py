@@ -104,6 +104,24 @@ def test_vector_calls_reject_missing_vectors(lib):
                  (4, 4, DUMMY, DUMMY, DUMMY, DUMMY, DUMMY, 2, 0, 1e-8, 10, 0)):
         info = L.Info()
         einval(lib.iluk_solve_host(*args, C.byref(info), None), info)
+    # iluk_solve: A, values, k, b, x, m, rtol, maxit, sched, S_out, F_out
+    A4 = pat()
+    for args in ((C.byref(pat(n=-1)), DUMMY, 2, DUMMY, DUMMY, 30, 1e-8, 10, 0),
+                 (None, DUMMY, 2, DUMMY, DUMMY, 30, 1e-8, 10, 0),
+                 (C.byref(A4), None, 2, DUMMY, DUMMY, 30, 1e-8, 10, 0),    # values
+                 (C.byref(A4), DUMMY, -1, DUMMY, DUMMY, 30, 1e-8, 10, 0),  # k
+                 (C.byref(A4), DUMMY, 251, DUMMY, DUMMY, 30, 1e-8, 10, 0),
+                 (C.byref(A4), DUMMY, 2, None, DUMMY, 30, 1e-8, 10, 0),    # b
+                 (C.byref(A4), DUMMY, 2, DUMMY, None, 30, 1e-8, 10, 0),    # x
+                 (C.byref(A4), DUMMY, 2, DUMMY, DUMMY, 0, 1e-8, 10, 0),    # m
+                 (C.byref(A4), DUMMY, 2, DUMMY, DUMMY, 30, 1e-8, -1, 0),   # maxit
+                 (C.byref(A4), DUMMY, 2, DUMMY, DUMMY, 30, 1e-8, 10, -1),  # sched
+                 (C.byref(A4), DUMMY, 2, DUMMY, DUMMY, 30, 1e-8, 10, 0x10000),
+                 (C.byref(A4), DUMMY, 2, DUMMY, DUMMY, 30, 1e-8, 10, 0x9F)):  # no such kind
+        info = L.Info()
+        hs, hf = C.c_void_p(123), C.c_void_p(456)
+        einval(lib.iluk_solve(*args, C.byref(hs), C.byref(hf), C.byref(info), None), info)
+        assert hs.value is None and hf.value is None  # outputs cleared first
     einval(lib.iluk_transpose(C.byref(pat(n=-1)), DUMMY, DUMMY, DUMMY, DUMMY, None))
     for args in ((None, DUMMY, DUMMY, DUMMY), (DUMMY, None, DUMMY, DUMMY),
                  (DUMMY, DUMMY, None, DUMMY), (DUMMY, DUMMY, DUMMY, None)):

@@ -71,6 +71,13 @@ def test_full_size_bit_exact(name, make, k):
     assert st == 0 and info.iters == it and bits([info.relres])[0] == bits([rel])[0]
     assert_bits_equal(x, xo, "gmres x")
     assert np.abs(x.cpu().numpy() - Pb.xstar).max() < 1e-4
+    # the one-call solve (for k >= 2 the first forward sweep runs inside the
+    # factorization), on the schedule the apply above picked
+    x1, info1 = P.solve(rp, ci, av, b, k=k, restart=Pb.restart, rtol=Pb.rtol,
+                        sched=F.schedule())
+    assert (info1.iters, info1.cycles) == (it, cyc)
+    assert bits([info1.relres])[0] == bits([rel])[0]
+    assert_bits_equal(x1, xo, "one-call solve x")
 
 
 def test_largest_case_properties_on_sampled_rows():
@@ -156,13 +163,15 @@ def _sha(*arrays) -> str:
     return h.hexdigest()
 
 
-@pytest.mark.parametrize("path", ["symbolic+numeric", "factor"])
+@pytest.mark.parametrize("path", ["symbolic+numeric", "factor", "solve"])
 def test_band160k_k3_bit_exact_against_oracle_digests(path):
     """Random band n=160,000 at k=3 (87 M factor entries) against the digests
     the oracle wrote (tests/golden/make_band160k_k3.py): pattern, levels,
     factors, one application of the preconditioner, TPIILU and GMRES, bit for
     bit.  "factor" is the one-call iluk_factor, whose rows longer than its
-    combined launch's numeric slice send it through the two separate phases."""
+    combined launch's numeric slice send it through the two separate phases;
+    "solve" is iluk_solve (factorization and GMRES in one call), whose
+    factors are then checked the same way."""
     import json
     import os
     import sys
@@ -173,7 +182,13 @@ def test_band160k_k3_bit_exact_against_oracle_digests(path):
     Pb = W.random_band_160k(k=3)
     A = Pb.A
     rp, ci, av, b = dev(A.rowptr), dev(A.colind), dev(A.val), dev(Pb.b)
-    if path == "factor":
+    if path == "solve":
+        x, info, (S, F) = P.solve(rp, ci, av, b, k=3, restart=Pb.restart, rtol=Pb.rtol,
+                                  return_factors=True)
+        assert (info.iters, info.cycles) == (want["gmres_iters"], want["gmres_cycles"])
+        assert int(bits([info.relres])[0]) == want["gmres_relres_bits"]
+        assert _sha(x) == want["gmres_x"]
+    elif path == "factor":
         S, F = P.factor(rp, ci, av, 3)
     else:
         S = P.symbolic(rp, ci, 3)
