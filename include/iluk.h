@@ -114,13 +114,21 @@ enum { ILUK_PREC_NONE = 0, ILUK_PREC_ILU = 1, ILUK_PREC_IILU = 2 };
  * lockstep warps over all SMs (FLAGS), on one SM (SINGLE_CTA) or on one
  * thread-block cluster (CLUSTER); one warp per row over all SMs (WARP_GRID)
  * or on one cluster (WARP_CLUSTER).  AUTO times them and keeps the fastest.
- * A schedule byte holds the kind in bits 0-3 and, for the two warp-per-row
+ * A schedule byte holds the kind in bits 0-3 and, for the warp-per-row
  * kinds, the threads per CTA / 128 in bits 4-7 (0: 1024 threads; for
  * WARP_GRID a non-zero width also means one CTA per SM), which bounds how
  * many rows are in flight: ILUK_SCHED_WIDTH(ILUK_SCHED_WARP_CLUSTER, 512). */
+/* WARP_CLUSTER_HELP is WARP_CLUSTER plus a second 16-CTA cluster of prefix
+ * helpers in the same cooperative launch: for each row, shortly before its
+ * warp takes it, a helper warp on another SM subtracts the products of the
+ * row's leading entries whose x is already final and hands the partial
+ * difference over, so most of each subtraction chain runs off the SMs of the
+ * critical path (same operations in the same order: same bits).  It keeps
+ * per-row scratch in F (16 bytes a row) and runs as WARP_CLUSTER when the
+ * GPU cannot hold both clusters at once.  Widths as for WARP_CLUSTER. */
 enum {
   ILUK_SCHED_AUTO = 0, ILUK_SCHED_FLAGS = 1, ILUK_SCHED_SINGLE_CTA = 2, ILUK_SCHED_CLUSTER = 3,
-  ILUK_SCHED_WARP_GRID = 4, ILUK_SCHED_WARP_CLUSTER = 5
+  ILUK_SCHED_WARP_GRID = 4, ILUK_SCHED_WARP_CLUSTER = 5, ILUK_SCHED_WARP_CLUSTER_HELP = 6
 };
 #define ILUK_SCHED_WIDTH(kind, threads) ((kind) | (((threads) / 128) << 4))
 

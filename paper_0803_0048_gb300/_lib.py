@@ -19,8 +19,9 @@ PREC_NONE, PREC_ILU, PREC_IILU = 0, 1, 2
 BASIS = {"auto": 0, "store": 1, "recompute": 2, "minv_vy": 3}
 SOLVER_GMRES, SOLVER_BICGSTAB = 0, 1
 SCHED_AUTO, SCHED_FLAGS, SCHED_SINGLE_CTA, SCHED_CLUSTER, SCHED_WARP_GRID, SCHED_WARP_CLUSTER = 0, 1, 2, 3, 4, 5
+SCHED_WARP_CLUSTER_HELP = 6
 _SCHED_NAMES = ["auto", "lockstep_grid", "lockstep_cta", "lockstep_cluster", "warp_grid",
-                "warp_cluster"]
+                "warp_cluster", "warp_cluster_help"]
 
 
 def sched_width(kind: int, threads: int) -> int:

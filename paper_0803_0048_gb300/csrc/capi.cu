@@ -500,6 +500,9 @@ void iluk_fac_destroy(iluk_fac *F) {
   dfree(F->tval, s);
   level_order_free(F->tlord, s);
   level_order_free(F->tuord, s);
+  dfree(F->aux.pre_s, s);
+  dfree(F->aux.pre_k, s);
+  dfree(F->aux.words, s);
   delete F;
 }
 
@@ -860,6 +863,36 @@ static int ensure_transpose(iluk_fac *F, cudaStream_t s) {
   return ILUK_OK;
 }
 
+// The helped sweeps' scratch (SweepAux), made the first time a schedule of F
+// asks for ILUK_SCHED_WARP_CLUSTER_HELP; null while a stream capture runs
+// (the helped kind then runs as WARP_CLUSTER) or if the memory is missing.
+static const SweepAux *sweep_aux(iluk_fac *F, int sched, cudaStream_t s) {
+  const bool want = (sched & 0xf) == ILUK_SCHED_WARP_CLUSTER_HELP ||
+                    ((sched >> 8) & 0xf) == ILUK_SCHED_WARP_CLUSTER_HELP;
+  if (!want) return nullptr;
+  if (F->aux.pre_s) return &F->aux;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(s, &cs);
+  if (cs != cudaStreamCaptureStatusNone) return nullptr;
+  const int64_t n = F->S->n;
+  SweepAux a;
+  if (dalloc(&a.pre_s, n, s) != cudaSuccess || dalloc(&a.pre_k, n, s) != cudaSuccess ||
+      dalloc(&a.words, 2, s) != cudaSuccess ||
+      // no prefix carries epoch 0xffffffff, which the epochs never reach
+      cudaMemsetAsync(a.pre_k, 0xff, (size_t)(n > 0 ? n : 1) * sizeof(unsigned long long), s) !=
+          cudaSuccess ||
+      cudaMemsetAsync(a.words, 0, 2 * sizeof(unsigned), s) != cudaSuccess) {
+    cudaGetLastError();
+    dfree(a.pre_s, s);
+    dfree(a.pre_k, s);
+    dfree(a.words, s);
+    return nullptr;
+  }
+  a.n = n;
+  F->aux = a;
+  return &F->aux;
+}
+
 // Autotuner: time every sweep schedule (the warp-per-row ones at several CTA
 // widths) on this factorization, forward and backward sweeps separately, and
 // keep the fastest of each (packed as forward | backward << 8).  Skipped
@@ -902,7 +935,9 @@ static int pick_schedule(iluk_fac *F, cudaStream_t s) {
                             ILUK_SCHED_WIDTH(ILUK_SCHED_WARP_CLUSTER, 768),
                             ILUK_SCHED_WIDTH(ILUK_SCHED_WARP_CLUSTER, 512),
                             ILUK_SCHED_WIDTH(ILUK_SCHED_WARP_CLUSTER, 384),
-                            ILUK_SCHED_WIDTH(ILUK_SCHED_WARP_CLUSTER, 256)};
+                            ILUK_SCHED_WIDTH(ILUK_SCHED_WARP_CLUSTER, 256),
+                            ILUK_SCHED_WIDTH(ILUK_SCHED_WARP_CLUSTER_HELP, 512),
+                            ILUK_SCHED_WIDTH(ILUK_SCHED_WARP_CLUSTER_HELP, 384)};
   for (int sched : candidates) {
     float mf = 1e30f, mb = 1e30f;
     for (int rep = 0; rep < 3; ++rep) {
@@ -910,11 +945,12 @@ static int pick_schedule(iluk_fac *F, cudaStream_t s) {
       // level orders the real applies use
       LevelOrder none;
       cudaEventRecord(e0, s);
+      const SweepAux *aux = sweep_aux(F, sched, s);
       const cudaError_t ef = launch_apply(S->n, S->rowptr, S->colind, S->diag, F->val, F->rdiag,
-                                          sweep_fwd(S), none, p, t, y, 0, sched, F->err, s);
+                                          sweep_fwd(S), none, p, t, y, 0, sched, F->err, aux, s);
       cudaEventRecord(e1, s);
       const cudaError_t eb = launch_apply(S->n, S->rowptr, S->colind, S->diag, F->val, F->rdiag,
-                                          none, sweep_bwd(S), p, t, y, 0, sched, F->err, s);
+                                          none, sweep_bwd(S), p, t, y, 0, sched, F->err, aux, s);
       cudaEventRecord(e2, s);
       cudaEventSynchronize(e2);
       float a = 0, b = 0;
@@ -980,11 +1016,10 @@ int iluk_apply_sched(iluk_fac *F, const double *p, double *y, int transpose, int
     int st = ensure_transpose(F, s);
     if (st != ILUK_OK) return st;
     CK(launch_apply(S->n, F->trowptr, F->tcolind, F->tdiag, F->tval, F->rdiag, F->tlord,
-                    F->tuord, p, F->tmp, y, 1, sched, F->err, s));
+                    F->tuord, p, F->tmp, y, 1, sched, F->err, sweep_aux(F, sched, s), s));
   } else {
     CK(launch_apply(S->n, S->rowptr, S->colind, S->diag, F->val, F->rdiag, sweep_fwd(S),
-                    sweep_bwd(S), p,
-                    F->tmp, y, 0, sched, F->err, s));
+                    sweep_bwd(S), p, F->tmp, y, 0, sched, F->err, sweep_aux(F, sched, s), s));
   }
   return ILUK_OK;
 }
@@ -1001,8 +1036,9 @@ int iluk_apply(iluk_fac *F, const double *p, double *y, int transpose, void *str
 static bool sched_valid(int sched) {
   auto valid = [](int b) {
     const int kind = b & 0xf, w = (b >> 4) & 0xf;
-    if (kind > ILUK_SCHED_WARP_CLUSTER) return false;
-    return w == 0 || ((kind == ILUK_SCHED_WARP_GRID || kind == ILUK_SCHED_WARP_CLUSTER) &&
+    if (kind > ILUK_SCHED_WARP_CLUSTER_HELP) return false;
+    return w == 0 || ((kind == ILUK_SCHED_WARP_GRID || kind == ILUK_SCHED_WARP_CLUSTER ||
+                       kind == ILUK_SCHED_WARP_CLUSTER_HELP) &&
                       w >= 2 && w <= 8);
   };
   return sched >= 0 && sched <= 0xffff && valid(sched & 0xff) && valid((sched >> 8) & 0xff);
@@ -1480,9 +1516,11 @@ static int gmres_impl(const iluk_pattern *A, const double *A_val, int prec_kind,
     if (F) {
       if (transpose)
         return launch_apply(n, F->trowptr, F->tcolind, F->tdiag, F->tval, F->rdiag, F->tlord,
-                            F->tuord, in, F->tmp, outv, 1, sched, F->err, s);
+                            F->tuord, in, F->tmp, outv, 1, sched, F->err, sweep_aux(F, sched, s),
+                            s);
       return launch_apply(n, F->S->rowptr, F->S->colind, F->S->diag, F->val, F->rdiag,
-                          sweep_fwd(F->S), sweep_bwd(F->S), in, F->tmp, outv, 0, sched, F->err, s);
+                          sweep_fwd(F->S), sweep_bwd(F->S), in, F->tmp, outv, 0, sched, F->err,
+                          sweep_aux(F, sched, s), s);
     }
     if (M) return launch_iiluk_apply(M->S, M->g, in, M->tmp, outv, s);
     return cudaMemcpyAsync(outv, in, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
@@ -1534,7 +1572,8 @@ static int gmres_impl(const iluk_pattern *A, const double *A_val, int prec_kind,
         if (fwd_ready) {  // z_1 from the forward sweep the factorization made
           fwd_ready = false;
           CK(launch_apply_backward(n, F->S->rowptr, F->S->colind, F->S->diag, F->val, F->rdiag,
-                                   sweep_bwd(F->S), F->tmp, zj, sched, F->err, s));
+                                   sweep_bwd(F->S), F->tmp, zj, sched, F->err,
+                                   sweep_aux(F, sched, s), s));
         } else {
           CK(precond(vj, zj));
         }
@@ -1735,7 +1774,8 @@ int bicgstab_solve(const iluk_pattern *A, const double *A_val, int prec_kind, vo
   auto precond = [&](const double *in, double *outv) -> cudaError_t {
     if (F)
       return launch_apply(n, F->S->rowptr, F->S->colind, F->S->diag, F->val, F->rdiag,
-                          sweep_fwd(F->S), sweep_bwd(F->S), in, F->tmp, outv, 0, sched, F->err, s);
+                          sweep_fwd(F->S), sweep_bwd(F->S), in, F->tmp, outv, 0, sched, F->err,
+                          sweep_aux(F, sched, s), s);
     if (M) return launch_iiluk_apply(M->S, M->g, in, M->tmp, outv, s);
     return cudaMemcpyAsync(outv, in, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
   };

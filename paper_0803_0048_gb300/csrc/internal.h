@@ -52,6 +52,20 @@ struct iluk_sym {
 inline const LevelOrder &sweep_fwd(const iluk_sym *S) { return S->levels_built ? S->lord : S->xlord; }
 inline const LevelOrder &sweep_bwd(const iluk_sym *S) { return S->levels_built ? S->uord : S->xuord; }
 
+namespace iluk {
+// Scratch of the helped warp-per-row sweeps (ILUK_SCHED_WARP_CLUSTER_HELP):
+// per row the prefix a helper published (the partial difference, and the
+// launch's epoch << 32 | the number of entries it covers), then two words:
+// the current epoch (starts at 1) and the count of CTAs of the running launch
+// that have finished.
+struct SweepAux {
+  double *pre_s = nullptr;
+  unsigned long long *pre_k = nullptr;
+  unsigned *words = nullptr;
+  int64_t n = 0;
+};
+}  // namespace iluk
+
 struct iluk_fac {
   const iluk_sym *S = nullptr;
   double *val = nullptr;          // F values
@@ -67,6 +81,7 @@ struct iluk_fac {
   double *tval = nullptr;
   LevelOrder tlord, tuord;        // level orders of the transposed sweeps
   int sched = 0;                  // schedule picked for the sweeps (ILUK_SCHED_*)
+  iluk::SweepAux aux;             // helped sweeps' scratch, made on first use
 };
 
 struct iiluk {
@@ -169,14 +184,14 @@ size_t sweep_sync_ints(int64_t n);
 cudaError_t launch_apply_backward(int64_t n, const int64_t *rp, const int32_t *ci,
                                   const int64_t *dg, const double *v, const DivPrep *rd,
                                   const LevelOrder &bwd, double *tmp, double *y, int sched,
-                                  DevErr *err, cudaStream_t s);
+                                  DevErr *err, const SweepAux *aux, cudaStream_t s);
 // y = (LU)^-1 p (or ^-T on the transposed arrays).  tmp must hold the pending
 // marker in every entry on entry, and does again on exit.
 cudaError_t launch_apply(int64_t n, const int64_t *rp, const int32_t *ci, const int64_t *dg,
                          const double *v, const DivPrep *rd, const LevelOrder &fwd,
                          const LevelOrder &bwd,
                          const double *p, double *tmp, double *y, int transpose, int sched,
-                         DevErr *err, cudaStream_t s);
+                         DevErr *err, const SweepAux *aux, cudaStream_t s);
 cudaError_t launch_fill_pending(int64_t n, double *x, cudaStream_t s);
 cudaError_t launch_fill_value(int64_t n, double *x, double v, cudaStream_t s);
 cudaError_t launch_div_check(int64_t n, const double *a, const double *b, double *q,

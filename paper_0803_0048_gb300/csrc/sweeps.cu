@@ -384,20 +384,106 @@ __device__ __forceinline__ double wpr_load(const double *out, unsigned da, int64
   return ld_dsm(da);
 }
 
+// Prefix helpers (ILUK_SCHED_WARP_CLUSTER_HELP).  The FP64 pipes of the
+// cluster's SMs are kept busy by the rows' subtraction chains (one warp
+// instruction per entry, however few lanes it serves), and that queueing
+// delays the few FP64 operations on the critical path.  A second cluster of
+// the same cooperative launch therefore takes most of each chain: its warps
+// walk the slots in order, one row per warp, and for slot s, once the row at
+// slot s - lag is final, subtract the products of the row's leading entries
+// whose x is already final (read from a global copy of x that the row warps
+// keep), stopping at the first one that is not, and publish the partial
+// difference with the number of entries it covers.  The row's own warp,
+// when it takes the row, starts from there.  Same products, same
+// differences, same order: the result does not change.  A prefix is tagged
+// with the launch's epoch (a device word the last CTA of the launch advances),
+// so one left over from an earlier launch is never used; a row whose prefix
+// is not published in time is simply done in full by its warp, which never
+// waits for a helper.
+template <bool FORWARD>
+__device__ void sweep_prefixes(const int32_t *__restrict__ order, int64_t len,
+                               const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                               const int64_t *__restrict__ dg, const double *__restrict__ v,
+                               const double *in, const double *xg, double *pre_s,
+                               unsigned long long *pre_k, unsigned epoch, int64_t hid,
+                               int64_t hp, int64_t lag, const DevErr *err, int64_t limit_ns,
+                               int lane) {
+  for (int64_t slot = hid; slot < len; slot += hp) {
+    const int64_t ps = slot - lag;
+    if (ps >= 0) {  // pace: start once the row at slot ps is final
+      bool ok = true;
+      if (lane == 0) {
+        const double *pa = &xg[order[ps]];
+        const uint64_t t0 = globaltimer_ns();
+        for (unsigned it = 0;; ++it) {
+          if (!pending(ld_val<true>(pa))) break;
+          if ((it & 15u) == 15u &&
+              (any_failed(err) || (int64_t)(globaltimer_ns() - t0) > limit_ns)) {
+            ok = false;
+            break;
+          }
+          __nanosleep(128);
+        }
+      }
+      if (!__shfl_sync(FULL_MASK, ok ? 1 : 0, 0)) return;  // stop helping
+    }
+    const int64_t row = order[slot];
+    if (!pending(ld_val<true>(&xg[row]))) continue;  // the row is done already
+    const int64_t d = dg[row];
+    const int64_t first = FORWARD ? rp[row] : rp[row + 1] - 1;
+    const int mylen = (int)(FORWARD ? d - first : first - d);
+    constexpr int64_t step = FORWARD ? 1 : -1;
+    double s = in[row];
+    int covered = 0;
+    for (int b = 0; b < mylen; b += 32) {
+      const int e = b + lane;
+      const int cnt = mylen - b < 32 ? mylen - b : 32;
+      double prod = 0.0;
+      bool have = e >= mylen;
+      if (e < mylen) {
+        const double x = ld_val<true>(&xg[ci[first + step * e]]);
+        if (!pending(x)) {
+          prod = __dmul_rn(v[first + step * e], x);
+          have = true;
+        }
+      }
+      const unsigned ready = __ballot_sync(FULL_MASK, have);
+      const int run = ready == FULL_MASK ? 32 : __ffs(~ready) - 1;
+      const int upto = run < cnt ? run : cnt;
+      for (int j = 0; j < upto; ++j) s = __dsub_rn(s, __shfl_sync(FULL_MASK, prod, j));
+      covered += upto;
+      if (upto < cnt) break;
+    }
+    if (covered > 0 && lane == 0) {
+      pre_s[row] = s;
+      __threadfence();  // the difference before the count that publishes it
+      asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(pre_k + row),
+                   "l"(((unsigned long long)epoch << 32) | (unsigned)covered)
+                   : "memory");
+    }
+    __syncwarp();
+  }
+}
+
 template <bool FORWARD, bool DIVIDE, int SCOPE>
 __global__ void __launch_bounds__(kCtaThreads, 1)
 k_sweep_wpr(const int32_t *__restrict__ order, int64_t len, int64_t n,
             const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
             const int64_t *__restrict__ dg, const double *__restrict__ v,
             const DivPrep *__restrict__ rd, const double *in, double *out, double *clear,
-            DevErr *err, int64_t limit_ns, const int32_t *__restrict__ owner) {
+            DevErr *err, int64_t limit_ns, const int32_t *__restrict__ owner, double *pre_s,
+            unsigned long long *pre_k, unsigned *aux_words, int64_t lag) {
   // SCOPE 1: x_i lives in the shared memory of the CTA whose warp computes
   // row i, at slot (k * wpc + warp) for the warp's k-th row; owner[i] holds
   // (rank << 26 | slot), so the producer's store stays on its own SM and only
-  // the dependants' polls cross SMs.
+  // the dependants' polls cross SMs.  With prefix helpers (pre_s non-null) the
+  // launch holds a second cluster of helper CTAs (blockIdx.x >= C), and the
+  // row warps also keep x in `out` (armed with kPending on entry) for them.
   extern __shared__ __align__(16) double xs[];
   unsigned rank = 0, C = 1, base = 0;
   const int wpc = blockDim.x >> 5;  // warps per CTA
+  const bool help = SCOPE == 1 && pre_s != nullptr;
+  const unsigned epoch = help ? *((volatile unsigned *)aux_words) : 0u;
   int64_t slice = 0;
   if (SCOPE == 1) {
     asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
@@ -417,6 +503,13 @@ k_sweep_wpr(const int32_t *__restrict__ order, int64_t len, int64_t n,
   unsigned own_base = 0;
   if (SCOPE == 1) asm("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(own_base) : "r"(base), "r"(rank));
   bool ok = true;
+  if (help && blockIdx.x >= C) {  // a helper CTA: no rows of its own
+    const int hw = (int)(blockDim.x >> 5);
+    sweep_prefixes<FORWARD>(order, len, rp, ci, dg, v, in, out, pre_s, pre_k, epoch,
+                            (int64_t)(blockIdx.x - C) * hw + (threadIdx.x >> 5),
+                            (int64_t)(gridDim.x - C) * hw, lag, err, limit_ns, lane);
+    ok = false;
+  }
   for (int64_t slot = gw; slot < len && ok; slot += nw, own_slot += wpc) {
     const int64_t row = order[slot];
     if (row < 0) continue;
@@ -427,11 +520,23 @@ k_sweep_wpr(const int32_t *__restrict__ order, int64_t len, int64_t n,
     const int mylen = (int)(FORWARD ? d - first : first - d);
     constexpr int64_t step = FORWARD ? 1 : -1;
     double s = in[row];
+    int k0 = 0;  // leading entries a helper has subtracted already
+    if (help) {
+      unsigned long long pk = 0;
+      if (lane == 0)
+        asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(pk) : "l"(pre_k + row));
+      pk = __shfl_sync(FULL_MASK, pk, 0);
+      if ((unsigned)(pk >> 32) == epoch) {
+        __threadfence();  // the difference was written before the count
+        k0 = (int)(pk & 0xffffffffu);
+        s = ld_val<true>(&pre_s[row]);
+      }
+    }
     // where x_row goes: this CTA's slot for the warp's current row
     const unsigned sa = SCOPE == 1 ? own_base + ((own_slot + (threadIdx.x >> 5)) << 3) : 0u;
     if (clear && lane == 0) clear[row] = __longlong_as_double((long long)kPending);
     bool stored = false;  // the last-entry path below stored x_row already
-    for (int b = 0; b < mylen && ok; b += 32) {
+    for (int b = k0; b < mylen && ok; b += 32) {
       const int e = b + lane;
       const bool act = e < mylen;
       const int cnt = (mylen - b) < 32 ? mylen - b : 32;
@@ -493,10 +598,12 @@ k_sweep_wpr(const int32_t *__restrict__ order, int64_t len, int64_t n,
               if (DIVIDE) r = div_fin(r, rr);
               if ((unsigned long long)__double_as_longlong(r) == kPending)
                 r = __longlong_as_double((long long)kQuietNaN);
-              if (SCOPE == 0)
+              if (SCOPE == 0) {
                 st_val<true>(&out[row], r);
-              else
+              } else {
                 st_dsm(sa, r);
+                if (help) st_val<true>(&out[row], r);  // the helpers' copy
+              }
             }
           }
           ok = __shfl_sync(FULL_MASK, gave_up ? 0 : 1, done) != 0;
@@ -536,18 +643,34 @@ k_sweep_wpr(const int32_t *__restrict__ order, int64_t len, int64_t n,
     if ((unsigned long long)__double_as_longlong(s) == kPending)
       s = __longlong_as_double((long long)kQuietNaN);
     if (lane == 0) {
-      if (SCOPE == 0)
+      if (SCOPE == 0) {
         st_val<true>(&out[row], s);
-      else
+      } else {
         st_dsm(sa, s);
+        if (help) st_val<true>(&out[row], s);  // the helpers' copy
+      }
     }
     __syncwarp();
   }
   if (SCOPE == 1) {
     cluster_sync_all();
-    for (int64_t j = threadIdx.x; j < slice; j += blockDim.x) {
-      const int64_t pos = (j / wpc) * nw + (int64_t)rank * wpc + j % wpc;
-      if (pos < len) out[order[pos]] = xs[j];
+    if (!help)  // with helpers every row already wrote its x to out
+      for (int64_t j = threadIdx.x; j < slice; j += blockDim.x) {
+        const int64_t pos = (j / wpc) * nw + (int64_t)rank * wpc + j % wpc;
+        if (pos < len) out[order[pos]] = xs[j];
+      }
+    if (help) {
+      // the last CTA to finish advances the epoch: every CTA read it at its
+      // start and published its last prefix before arriving here
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&aux_words[1], 1u) == gridDim.x - 1) {
+          aux_words[1] = 0u;
+          __threadfence();
+          aux_words[0] = epoch + 1u == 0xffffffffu ? 0u : epoch + 1u;
+        }
+      }
     }
   }
 }
@@ -695,38 +818,62 @@ static int cluster_width(int64_t n, K kern) {
 
 int cluster_size_for(int64_t n) { return cluster_width(n, k_sweep_cluster<true, false, 4>); }
 
+// `clusters` clusters of C CTAs; more than one only as a cooperative launch
+// (every CTA resident at once, or the launch fails), because the CTAs of the
+// later clusters wait on the first one.
 template <typename K, typename... Args>
-static cudaError_t launch_on_cluster(K kern, int C, int threads, size_t smem, cudaStream_t s,
-                                     Args... args) {
+static cudaError_t launch_clusters(K kern, int C, int clusters, int threads, size_t smem,
+                                   cudaStream_t s, Args... args) {
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)C);
+  cfg.gridDim = dim3((unsigned)(C * clusters));
   cfg.blockDim = dim3((unsigned)threads);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
-  cudaLaunchAttribute attr[1];
+  cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = (unsigned)C;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeCooperative;
+  attr[1].val.cooperative = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = clusters > 1 ? 2 : 1;
   e = cudaLaunchKernelEx(&cfg, kern, args...);
   note_launch();
   return e;
 }
 
+template <typename K, typename... Args>
+static cudaError_t launch_on_cluster(K kern, int C, int threads, size_t smem, cudaStream_t s,
+                                     Args... args) {
+  return launch_clusters(kern, C, 1, threads, smem, s, args...);
+}
+
+// Slots beyond the row warps' own span at which a prefix helper starts a row
+// (it waits until the row `lag` slots earlier is final): late enough that
+// most of the row's leading entries are final, early enough to publish before
+// the row's warp takes the row.  Measured on the random band matrix with
+// n = 160,000, k = 2: forward best at 384-512, backward at 256.
+constexpr int64_t kHelpLagFwd = 448;
+constexpr int64_t kHelpLagBwd = 256;
+
 template <bool FORWARD, bool DIVIDE>
 static cudaError_t run_sweep(int64_t n, const LevelOrder &lo, const int64_t *rp, const int32_t *ci,
                              const int64_t *dg, const double *v, const DivPrep *rd,
                              const double *in, double *out, double *clear, int sched, DevErr *err,
-                             cudaStream_t s) {
+                             const SweepAux *aux, cudaStream_t s) {
   ProfScope prof_scope(FORWARD ? ILUK_PROF_SWEEP : ILUK_PROF_SWEEP_BWD, s);
   // an empty order: nothing to sweep (n = 0, or a direction the caller skips)
   if (n == 0 || (!lo.order && !lo.corder)) return cudaSuccess;
+  // the helped kind needs its scratch; without it, the plain cluster kind
+  if ((sched & 0xf) == ILUK_SCHED_WARP_CLUSTER_HELP && (!aux || !aux->pre_s || aux->n < n))
+    sched = (sched & ~0xf) | ILUK_SCHED_WARP_CLUSTER;
+  const bool helped = (sched & 0xf) == ILUK_SCHED_WARP_CLUSTER_HELP;
+  if (helped) sched = (sched & ~0xf) | ILUK_SCHED_WARP_CLUSTER;
   // the lockstep kinds walk the padded level order; an index order (a
   // factorization that has not built its level orders) has only the plain one
   const int kind0 = sched & 0xf;
@@ -763,8 +910,21 @@ static cudaError_t run_sweep(int64_t n, const LevelOrder &lo, const int64_t *rp,
       if (wsmem > (size_t)max_smem_optin()) return cudaErrorInvalidConfiguration;
       const int32_t *owner = owner_codes(lo, n, C, threads, s);
       if (!owner) return cudaErrorMemoryAllocation;
+      double *no_ps = nullptr;
+      unsigned long long *no_pk = nullptr;
+      unsigned *no_words = nullptr;
+      if (helped) {  // a second cluster of prefix helpers
+        const int64_t lag = (FORWARD ? kHelpLagFwd : kHelpLagBwd) + nwc;
+        const cudaError_t e =
+            launch_clusters(k_sweep_wpr<FORWARD, DIVIDE, 1>, C, 2, threads, wsmem, s, order, len,
+                            n, rp, ci, dg, v, rd, in, out, clear, err, limit, owner, aux->pre_s,
+                            aux->pre_k, aux->words, lag);
+        if (e == cudaSuccess) return e;
+        cudaGetLastError();  // cannot hold both clusters at once: the plain kind
+      }
       return launch_on_cluster(k_sweep_wpr<FORWARD, DIVIDE, 1>, C, threads, wsmem, s, order, len,
-                               n, rp, ci, dg, v, rd, in, out, clear, err, limit, owner);
+                               n, rp, ci, dg, v, rd, in, out, clear, err, limit, owner, no_ps,
+                               no_pk, no_words, (int64_t)0);
     }
     const size_t smem = (size_t)((n + C - 1) / C) * sizeof(double);
     return launch_on_cluster(k_sweep_cluster<FORWARD, DIVIDE, 4>, C, kCtaThreads, smem, s, order,
@@ -780,9 +940,14 @@ static cudaError_t run_sweep(int64_t n, const LevelOrder &lo, const int64_t *rp,
     if (grid > want) grid = want;
     const int64_t nn = n;
     const int32_t *no_owner = nullptr;
+    double *no_ps = nullptr;
+    unsigned long long *no_pk = nullptr;
+    unsigned *no_words = nullptr;
+    int64_t no_lag = 0;
     void *args[] = {(void *)&order, (void *)&len, (void *)&nn, (void *)&rp, (void *)&ci,
                     (void *)&dg, (void *)&v, (void *)&rd, (void *)&in, (void *)&out,
-                    (void *)&clear, (void *)&err, (void *)&limit, (void *)&no_owner};
+                    (void *)&clear, (void *)&err, (void *)&limit, (void *)&no_owner,
+                    (void *)&no_ps, (void *)&no_pk, (void *)&no_words, (void *)&no_lag};
     cudaError_t e = cudaLaunchCooperativeKernel((const void *)kern, dim3((unsigned)grid),
                                                 dim3((unsigned)threads), args, 0, s);
     note_launch();
@@ -812,17 +977,20 @@ static cudaError_t run_sweep(int64_t n, const LevelOrder &lo, const int64_t *rp,
 // width only stays with the warp-per-row kinds (256..1024 threads).
 static int usable_sched(int64_t n, int sc) {
   int kind = sc & 0xf, w = (sc >> 4) & 0xf;
-  if (kind < ILUK_SCHED_FLAGS || kind > ILUK_SCHED_WARP_CLUSTER) kind = ILUK_SCHED_WARP_GRID;
-  if ((kind == ILUK_SCHED_CLUSTER || kind == ILUK_SCHED_WARP_CLUSTER) && cluster_size_for(n) == 0)
-    kind = ILUK_SCHED_WARP_GRID;
-  if ((kind != ILUK_SCHED_WARP_GRID && kind != ILUK_SCHED_WARP_CLUSTER) || w < 2 || w > 8) w = 0;
+  if (kind < ILUK_SCHED_FLAGS || kind > ILUK_SCHED_WARP_CLUSTER_HELP) kind = ILUK_SCHED_WARP_GRID;
+  const bool clustered = kind == ILUK_SCHED_CLUSTER || kind == ILUK_SCHED_WARP_CLUSTER ||
+                         kind == ILUK_SCHED_WARP_CLUSTER_HELP;
+  if (clustered && cluster_size_for(n) == 0) kind = ILUK_SCHED_WARP_GRID;
+  const bool per_row = kind == ILUK_SCHED_WARP_GRID || kind == ILUK_SCHED_WARP_CLUSTER ||
+                       kind == ILUK_SCHED_WARP_CLUSTER_HELP;
+  if (!per_row || w < 2 || w > 8) w = 0;
   return kind | (w << 4);
 }
 
 cudaError_t launch_apply_backward(int64_t n, const int64_t *rp, const int32_t *ci,
                                   const int64_t *dg, const double *v, const DivPrep *rd,
                                   const LevelOrder &bwd, double *tmp, double *y, int sched,
-                                  DevErr *err, cudaStream_t s) {
+                                  DevErr *err, const SweepAux *aux, cudaStream_t s) {
   // tmp already holds L^-1 p; y is armed here as the forward sweep would
   // have armed it, and the backward sweep re-arms tmp as usual
   int sb = (sched >> 8) & 0xff;
@@ -830,14 +998,14 @@ cudaError_t launch_apply_backward(int64_t n, const int64_t *rp, const int32_t *c
   cudaError_t e = launch_fill_pending(n, y, s);
   if (e != cudaSuccess) return e;
   return run_sweep<false, true>(n, bwd, rp, ci, dg, v, rd, tmp, y, tmp, usable_sched(n, sb), err,
-                                s);
+                                aux, s);
 }
 
 cudaError_t launch_apply(int64_t n, const int64_t *rp, const int32_t *ci, const int64_t *dg,
                          const double *v, const DivPrep *rd, const LevelOrder &fwd,
                          const LevelOrder &bwd,
                          const double *p, double *tmp, double *y, int transpose, int sched,
-                         DevErr *err, cudaStream_t s) {
+                         DevErr *err, const SweepAux *aux, cudaStream_t s) {
   // sched packs the forward schedule in bits 0-7 and the backward one in 8-15
   // (a single value applies to both).
   int sf = sched & 0xff, sb = (sched >> 8) & 0xff;
@@ -848,13 +1016,13 @@ cudaError_t launch_apply(int64_t n, const int64_t *rp, const int32_t *ci, const 
   // tmp is pending on entry (left so by the previous backward sweep); the
   // forward sweep re-arms y, the backward sweep re-arms tmp.
   if (!transpose) {
-    e = run_sweep<true, false>(n, fwd, rp, ci, dg, v, rd, p, tmp, y, sf, err, s);
+    e = run_sweep<true, false>(n, fwd, rp, ci, dg, v, rd, p, tmp, y, sf, err, aux, s);
     if (e != cudaSuccess) return e;
-    return run_sweep<false, true>(n, bwd, rp, ci, dg, v, rd, tmp, y, tmp, sb, err, s);
+    return run_sweep<false, true>(n, bwd, rp, ci, dg, v, rd, tmp, y, tmp, sb, err, aux, s);
   }
-  e = run_sweep<true, true>(n, fwd, rp, ci, dg, v, rd, p, tmp, y, sf, err, s);
+  e = run_sweep<true, true>(n, fwd, rp, ci, dg, v, rd, p, tmp, y, sf, err, aux, s);
   if (e != cudaSuccess) return e;
-  return run_sweep<false, false>(n, bwd, rp, ci, dg, v, rd, tmp, y, tmp, sb, err, s);
+  return run_sweep<false, false>(n, bwd, rp, ci, dg, v, rd, tmp, y, tmp, sb, err, aux, s);
 }
 
 // ---------------------------------------------------------------------------

@@ -129,13 +129,15 @@ def test_schedule_values_checked():
     F = P.numeric(P.symbolic(rp, ci, 1), av)
     good = [L.SCHED_AUTO, L.SCHED_FLAGS, L.sched_width(L.SCHED_WARP_CLUSTER, 256),
             L.sched_width(L.SCHED_WARP_GRID, 1024),
-            L.SCHED_CLUSTER | (L.sched_width(L.SCHED_WARP_CLUSTER, 768) << 8)]
+            L.SCHED_CLUSTER | (L.sched_width(L.SCHED_WARP_CLUSTER, 768) << 8),
+            L.SCHED_WARP_CLUSTER_HELP, L.sched_width(L.SCHED_WARP_CLUSTER_HELP, 384)]
     for s in good:
         F.set_schedule(s)
         assert F.schedule() == s
-    bad = [6, 0x0F, L.sched_width(L.SCHED_FLAGS, 512),  # width on a lockstep kind
+    bad = [7, 0x0F, L.sched_width(L.SCHED_FLAGS, 512),  # width on a lockstep kind
            L.SCHED_WARP_GRID | (1 << 4), L.SCHED_WARP_GRID | (9 << 4),  # 128 / 1152 threads
-           L.SCHED_WARP_GRID | (6 << 8), -1, 1 << 16]
+           L.SCHED_WARP_CLUSTER_HELP | (9 << 4),
+           L.SCHED_WARP_GRID | (7 << 8), -1, 1 << 16]
     for s in bad:
         with pytest.raises(P.IlukError):
             F.set_schedule(s)

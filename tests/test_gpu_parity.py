@@ -65,6 +65,9 @@ SCHEDS = [L.SCHED_FLAGS, L.SCHED_SINGLE_CTA, L.SCHED_CLUSTER, L.SCHED_WARP_GRID,
           L.sched_width(L.SCHED_WARP_CLUSTER, 384),
           # forward and backward on different schedules
           L.SCHED_SINGLE_CTA | (L.sched_width(L.SCHED_WARP_CLUSTER, 256) << 8),
+          # with the prefix-helper cluster
+          L.SCHED_WARP_CLUSTER_HELP, L.sched_width(L.SCHED_WARP_CLUSTER_HELP, 384),
+          L.sched_width(L.SCHED_WARP_CLUSTER_HELP, 512) | (L.SCHED_WARP_GRID << 8),
           # invalid kind and width: fall back to the warp grid
           0x9F]
 

@@ -87,7 +87,9 @@ SCHEDS = [L.SCHED_FLAGS, L.SCHED_SINGLE_CTA, L.SCHED_CLUSTER, L.SCHED_WARP_GRID,
           L.SCHED_WARP_CLUSTER, L.sched_width(L.SCHED_WARP_GRID, 256),
           L.sched_width(L.SCHED_WARP_CLUSTER, 512),
           L.SCHED_SINGLE_CTA | (L.sched_width(L.SCHED_WARP_CLUSTER, 256) << 8),
-          L.sched_width(L.SCHED_WARP_CLUSTER, 384) | (L.SCHED_FLAGS << 8)]
+          L.sched_width(L.SCHED_WARP_CLUSTER, 384) | (L.SCHED_FLAGS << 8),
+          L.sched_width(L.SCHED_WARP_CLUSTER_HELP, 512),
+          L.sched_width(L.SCHED_WARP_CLUSTER_HELP, 384) | (L.SCHED_WARP_CLUSTER << 8)]
 
 
 @pytest.mark.parametrize("sched", SCHEDS)
