@@ -236,13 +236,28 @@ __device__ __forceinline__ void cluster_sync_all() {
   asm volatile("barrier.cluster.arrive.aligned;\n\tbarrier.cluster.wait.aligned;" ::: "memory");
 }
 
+// The launch shape a cluster kernel finds, checked against the one its host
+// side sized the shared memory for (cluster width, grid, dynamic shared
+// memory): a launch that arrives otherwise records an error (row = width << 16
+// | grid) and does nothing, rather than index past its shared memory.  The
+// decision is the same in every CTA, so no CTA is left at a cluster barrier.
+__device__ __forceinline__ bool cluster_launch_ok(unsigned C, int expect_c, int expect_grid,
+                                                  uint64_t smem_need, DevErr *err) {
+  unsigned dyn;
+  asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
+  const bool ok = (int)C == expect_c && (int)gridDim.x == expect_grid && smem_need <= dyn;
+  if (!ok && threadIdx.x == 0 && blockIdx.x == 0)
+    set_err(err, ((int64_t)C << 16) | (int64_t)gridDim.x, ILUK_ECUDA);
+  return ok;
+}
+
 template <bool FORWARD, bool DIVIDE, int W>
 __global__ void __launch_bounds__(kCtaThreads, 1)
 k_sweep_cluster(const int32_t *__restrict__ order, int64_t len, int64_t n,
                 const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
                 const int64_t *__restrict__ dg, const double *__restrict__ v,
                 const DivPrep *__restrict__ rd, const double *in, double *out, double *clear,
-                DevErr *err, int64_t limit_ns) {
+                DevErr *err, int64_t limit_ns, int expect_c) {
   extern __shared__ __align__(16) double xs[];  // this CTA's slice of x
   __shared__ int sfail;
   unsigned rank, C;
@@ -250,6 +265,7 @@ k_sweep_cluster(const int32_t *__restrict__ order, int64_t len, int64_t n,
   asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(C));
   const int lg = __ffs((int)C) - 1;  // C is a power of two
   const int64_t slice = (n + C - 1) / C;
+  if (!cluster_launch_ok(C, expect_c, expect_c, (uint64_t)slice * sizeof(double), err)) return;
   for (int64_t j = threadIdx.x; j < slice; j += blockDim.x)
     xs[j] = __longlong_as_double((long long)kPending);
   if (threadIdx.x == 0) sfail = 0;
@@ -466,13 +482,14 @@ __device__ void sweep_prefixes(const int32_t *__restrict__ order, int64_t len,
 }
 
 template <bool FORWARD, bool DIVIDE, int SCOPE>
-__global__ void __launch_bounds__(kCtaThreads, 1)
-k_sweep_wpr(const int32_t *__restrict__ order, int64_t len, int64_t n,
-            const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
-            const int64_t *__restrict__ dg, const double *__restrict__ v,
-            const DivPrep *__restrict__ rd, const double *in, double *out, double *clear,
-            DevErr *err, int64_t limit_ns, const int32_t *__restrict__ owner, double *pre_s,
-            unsigned long long *pre_k, unsigned *aux_words, int64_t lag) {
+__device__ __forceinline__ void
+sweep_wpr_body(const int32_t *__restrict__ order, int64_t len, int64_t n,
+               const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
+               const int64_t *__restrict__ dg, const double *__restrict__ v,
+               const DivPrep *__restrict__ rd, const double *in, double *out, double *clear,
+               DevErr *err, int64_t limit_ns, const int32_t *__restrict__ owner, double *pre_s,
+               unsigned long long *pre_k, unsigned *aux_words, int64_t lag, int expect_c,
+               int expect_grid) {
   // SCOPE 1: x_i lives in the shared memory of the CTA whose warp computes
   // row i, at slot (k * wpc + warp) for the warp's k-th row; owner[i] holds
   // (rank << 26 | slot), so the producer's store stays on its own SM and only
@@ -490,6 +507,8 @@ k_sweep_wpr(const int32_t *__restrict__ order, int64_t len, int64_t n,
     asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(C));
     const int64_t nwc = (int64_t)C * wpc;
     slice = (len + nwc - 1) / nwc * wpc;
+    if (!cluster_launch_ok(C, expect_c, expect_grid, (uint64_t)slice * sizeof(double), err))
+      return;
     for (int64_t j = threadIdx.x; j < slice; j += blockDim.x)
       xs[j] = __longlong_as_double((long long)kPending);
     base = (unsigned)__cvta_generic_to_shared(xs);
@@ -675,6 +694,36 @@ k_sweep_wpr(const int32_t *__restrict__ order, int64_t len, int64_t n,
   }
 }
 
+#define ILUK_WPR_PARAMS                                                                     \
+  const int32_t *__restrict__ order, int64_t len, int64_t n, const int64_t *__restrict__ rp,  \
+      const int32_t *__restrict__ ci, const int64_t *__restrict__ dg,                         \
+      const double *__restrict__ v, const DivPrep *__restrict__ rd, const double *in,         \
+      double *out, double *clear, DevErr *err, int64_t limit_ns,                              \
+      const int32_t *__restrict__ owner, double *pre_s, unsigned long long *pre_k,            \
+      unsigned *aux_words, int64_t lag, int expect_c, int expect_grid
+#define ILUK_WPR_ARGS                                                                      \
+  order, len, n, rp, ci, dg, v, rd, in, out, clear, err, limit_ns, owner, pre_s, pre_k,     \
+      aux_words, lag, expect_c, expect_grid
+
+// Warp-per-row sweeps: SCOPE 0 on a grid, SCOPE 1 on one cluster whose width
+// the launch gives.
+template <bool FORWARD, bool DIVIDE, int SCOPE>
+__global__ void __launch_bounds__(kCtaThreads, 1) k_sweep_wpr(ILUK_WPR_PARAMS) {
+  sweep_wpr_body<FORWARD, DIVIDE, SCOPE>(ILUK_WPR_ARGS);
+}
+
+// The helped form: a cooperative launch of two clusters of kHelpCluster CTAs,
+// the sweep's and the helpers'.  The cluster width is part of the kernel
+// (not an attribute of the launch), so every path that launches it gets it.
+constexpr int kHelpCluster = 16;
+template <bool FORWARD, bool DIVIDE>
+__global__ void __cluster_dims__(kHelpCluster, 1, 1) __launch_bounds__(kCtaThreads, 1)
+    k_sweep_wpr_help(ILUK_WPR_PARAMS) {
+  sweep_wpr_body<FORWARD, DIVIDE, 1>(ILUK_WPR_ARGS);
+}
+#undef ILUK_WPR_PARAMS
+#undef ILUK_WPR_ARGS
+
 // owner[order[pos]] = (rank << 26 | slot) for the CTA layout above.
 __global__ void k_owner_codes(const int32_t *__restrict__ order, int64_t len, int C, int wpc,
                               int32_t *owner) {
@@ -818,39 +867,52 @@ static int cluster_width(int64_t n, K kern) {
 
 int cluster_size_for(int64_t n) { return cluster_width(n, k_sweep_cluster<true, false, 4>); }
 
-// `clusters` clusters of C CTAs; more than one only as a cooperative launch
-// (every CTA resident at once, or the launch fails), because the CTAs of the
-// later clusters wait on the first one.
 template <typename K, typename... Args>
-static cudaError_t launch_clusters(K kern, int C, int clusters, int threads, size_t smem,
-                                   cudaStream_t s, Args... args) {
+static cudaError_t launch_on_cluster(K kern, int C, int threads, size_t smem, cudaStream_t s,
+                                     Args... args) {
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(C * clusters));
+  cfg.gridDim = dim3((unsigned)C);
   cfg.blockDim = dim3((unsigned)threads);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
-  cudaLaunchAttribute attr[2];
+  cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = (unsigned)C;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
-  attr[1].id = cudaLaunchAttributeCooperative;
-  attr[1].val.cooperative = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = clusters > 1 ? 2 : 1;
+  cfg.numAttrs = 1;
   e = cudaLaunchKernelEx(&cfg, kern, args...);
   note_launch();
   return e;
 }
 
+// The helped sweep: two clusters (width from the kernel), launched
+// cooperatively, so every CTA is resident at once or the launch fails: the
+// helper CTAs wait on the sweep's.
 template <typename K, typename... Args>
-static cudaError_t launch_on_cluster(K kern, int C, int threads, size_t smem, cudaStream_t s,
-                                     Args... args) {
-  return launch_clusters(kern, C, 1, threads, smem, s, args...);
+static cudaError_t launch_help(K kern, int threads, size_t smem, cudaStream_t s, Args... args) {
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(2 * kHelpCluster));
+  cfg.blockDim = dim3((unsigned)threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  e = cudaLaunchKernelEx(&cfg, kern, args...);
+  note_launch();
+  return e;
 }
 
 // Slots beyond the row warps' own span at which a prefix helper starts a row
@@ -913,22 +975,22 @@ static cudaError_t run_sweep(int64_t n, const LevelOrder &lo, const int64_t *rp,
       double *no_ps = nullptr;
       unsigned long long *no_pk = nullptr;
       unsigned *no_words = nullptr;
-      if (helped) {  // a second cluster of prefix helpers
+      if (helped && C == kHelpCluster) {  // a second cluster of prefix helpers
         const int64_t lag = (FORWARD ? kHelpLagFwd : kHelpLagBwd) + nwc;
         const cudaError_t e =
-            launch_clusters(k_sweep_wpr<FORWARD, DIVIDE, 1>, C, 2, threads, wsmem, s, order, len,
-                            n, rp, ci, dg, v, rd, in, out, clear, err, limit, owner, aux->pre_s,
-                            aux->pre_k, aux->words, lag);
+            launch_help(k_sweep_wpr_help<FORWARD, DIVIDE>, threads, wsmem, s, order, len, n, rp,
+                        ci, dg, v, rd, in, out, clear, err, limit, owner, aux->pre_s, aux->pre_k,
+                        aux->words, lag, C, 2 * C);
         if (e == cudaSuccess) return e;
         cudaGetLastError();  // cannot hold both clusters at once: the plain kind
       }
       return launch_on_cluster(k_sweep_wpr<FORWARD, DIVIDE, 1>, C, threads, wsmem, s, order, len,
                                n, rp, ci, dg, v, rd, in, out, clear, err, limit, owner, no_ps,
-                               no_pk, no_words, (int64_t)0);
+                               no_pk, no_words, (int64_t)0, C, C);
     }
     const size_t smem = (size_t)((n + C - 1) / C) * sizeof(double);
     return launch_on_cluster(k_sweep_cluster<FORWARD, DIVIDE, 4>, C, kCtaThreads, smem, s, order,
-                             len, n, rp, ci, dg, v, rd, in, out, clear, err, limit);
+                             len, n, rp, ci, dg, v, rd, in, out, clear, err, limit, C);
   }
   if (sched == ILUK_SCHED_WARP_GRID) {
     auto kern = k_sweep_wpr<FORWARD, DIVIDE, 0>;
@@ -944,10 +1006,12 @@ static cudaError_t run_sweep(int64_t n, const LevelOrder &lo, const int64_t *rp,
     unsigned long long *no_pk = nullptr;
     unsigned *no_words = nullptr;
     int64_t no_lag = 0;
+    int no_c = 0;
     void *args[] = {(void *)&order, (void *)&len, (void *)&nn, (void *)&rp, (void *)&ci,
                     (void *)&dg, (void *)&v, (void *)&rd, (void *)&in, (void *)&out,
                     (void *)&clear, (void *)&err, (void *)&limit, (void *)&no_owner,
-                    (void *)&no_ps, (void *)&no_pk, (void *)&no_words, (void *)&no_lag};
+                    (void *)&no_ps, (void *)&no_pk, (void *)&no_words, (void *)&no_lag,
+                    (void *)&no_c, (void *)&no_c};
     cudaError_t e = cudaLaunchCooperativeKernel((const void *)kern, dim3((unsigned)grid),
                                                 dim3((unsigned)threads), args, 0, s);
     note_launch();
