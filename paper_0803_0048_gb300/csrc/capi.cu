@@ -50,6 +50,20 @@ const DevCache &dev() {
     cudaDeviceGetAttribute(&c.smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, d);
     if (c.sms <= 0) c.sms = 1;
     if (c.smem <= 0) c.smem = 48 * 1024;
+    // The stream-ordered allocations (arenas, CSR arrays, Krylov vectors)
+    // come from the device's default pool, which by default hands freed
+    // memory back to the driver at every synchronisation, so each call maps
+    // its hundreds of MB again.  Keep up to an eighth of the device's memory
+    // (at most 16 GiB) cached in the pool instead; this process's pool only.
+    cudaMemPool_t pool;
+    size_t free_b = 0, total_b = 0;
+    if (cudaDeviceGetDefaultMemPool(&pool, d) == cudaSuccess &&
+        cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
+      uint64_t keep = total_b / 8;
+      if (keep > (16ull << 30)) keep = 16ull << 30;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    cudaGetLastError();
   }
   return c;
 }
