@@ -25,6 +25,10 @@
 namespace iluk {
 
 constexpr int kNumThreads = 256;
+// Static shared memory of the numeric kernels (apply_pivots' per-warp
+// bitmaps), left out of the dynamic shared memory's budget.
+constexpr int kTouchedWords = 16;  // bitmap words per warp: rows of up to 512 entries
+constexpr size_t kStaticSmem = (kNumThreads / 32) * kTouchedWords * sizeof(unsigned);
 // Sixteenths of the fused factorization's CTAs that run the symbolic walk:
 // few with the level-map walk, which keeps ahead of the numeric rows easily;
 // more with the sorted-list walk of wide matrices, which is slower per row.
@@ -191,15 +195,42 @@ __device__ __forceinline__ bool wait_pivot(PivotPre &pp, const double *fv, int l
   }
 }
 
+// Where the row's finished entries go (position q of the row, diagonal at
+// dp): out[at(q)].  `out` null: nowhere, the caller writes the row back.
+struct CsrOut {
+  double *out;
+  int64_t b0;
+  __device__ __forceinline__ int64_t at(int q) const { return b0 + q; }
+};
+struct ArenaOut {  // a slot: diagonal, upper part, end marker, lower part
+  double *out;
+  int64_t slot;
+  int dp, mu;
+  __device__ __forceinline__ int64_t at(int q) const {
+    return q < dp ? slot + mu + 2 + q : slot + (q - dp);
+  }
+};
+
 // Row i's pivots, ascending: the staged pipeline (see PivotA) applied to the
 // row in shared memory.  fci and fv hold the pivot rows' columns and values
 // at their diagonal position hd and the upper part after it (CSR, or a slot of
 // the factorization arena); spinfo[q] = hd << 24 | |U(h)| for the row's q-th
 // lower entry h.  Warp-uniform; false on time-out or an earlier row's failure.
+//
+// The diagonal and upper part are what later rows wait for, so they leave as
+// soon as they are final.  The last pivot's positions in the row are known
+// (stage B) before its values arrive: every diagonal/upper entry it does not
+// touch is final already and goes out before the wait (`touched`, a 16-word
+// per-warp bitmap over the row's positions); the entries it does touch go
+// out from registers as each update completes.  Then *upper_sent is true and
+// the caller writes only the lower part.  (A row longer than the bitmap, or a
+// last pivot row longer than the staged chunks, leaves it all to the caller.)
+template <typename Out>
 __device__ __forceinline__ bool apply_pivots(int dp, double *rv, const int64_t *spinfo,
                                              const RowIndex &ri, const int32_t *__restrict__ fci,
                                              const double *fv, const DevErr *err, int64_t row,
-                                             int64_t limit_ns, int lane) {
+                                             int64_t limit_ns, int lane, const Out &out, int m,
+                                             unsigned *touched, bool *upper_sent) {
   // Pivots go through the three stages (see PivotA): in iteration q the
   // warp applies pivot q, finds the positions of pivot q+1 and issues the
   // loads of pivot q+2, so the latencies of the later stages overlap the
@@ -215,6 +246,19 @@ __device__ __forceinline__ bool apply_pivots(int dp, double *rv, const int64_t *
   for (int q = 0; q < dp && ok; ++q) {
     if (q + 1 < dp) stage_b(nxt, pa, ri, q + 1, fv, lane);
     if (q + 2 < dp) stage_a(pa, spinfo[q + 2], fci, fv, lane);
+    const bool early =
+        out.out != nullptr && q + 1 == dp && cur.ulen <= 32 * kPre && m <= 32 * kTouchedWords;
+    if (early) {
+      if (lane < kTouchedWords) touched[lane] = 0u;
+      __syncwarp();
+#pragma unroll
+      for (int c = 0; c < kPre; ++c)
+        if (cur.pos[c] >= 0) atomicOr(&touched[cur.pos[c] >> 5], 1u << (cur.pos[c] & 31));
+      __syncwarp();
+      for (int t = dp + lane; t < m; t += 32)
+        if (!((touched[t >> 5] >> (t & 31)) & 1u)) out.out[out.at(t)] = rv[t];
+      *upper_sent = true;
+    }
     if (!wait_pivot(cur, fv, lane, err, row, limit_ns)) {
       ok = false;
       break;
@@ -233,7 +277,11 @@ __device__ __forceinline__ bool apply_pivots(int dp, double *rv, const int64_t *
 #pragma unroll
     for (int c = 0; c < kPre; ++c) {
       if (c >= nch) break;
-      if (cur.pos[c] >= 0) rv[cur.pos[c]] = sub_prod(rv[cur.pos[c]], fih, cur.f[c]);
+      if (cur.pos[c] >= 0) {
+        const double nv = sub_prod(rv[cur.pos[c]], fih, cur.f[c]);
+        rv[cur.pos[c]] = nv;
+        if (early && cur.pos[c] >= dp) out.out[out.at(cur.pos[c])] = nv;  // final: out now
+      }
     }
     const int64_t u1 = cur.hd + 1 + cur.ulen;
     for (int64_t base = cur.hd + 1 + 32 * kPre; base < u1; base += 32) {  // long rows
@@ -309,6 +357,7 @@ k_numeric(int64_t n, int64_t nbatch, const int64_t *__restrict__ arp,
       reinterpret_cast<int32_t *>(smem + (size_t)nwarps * cap * 16) + (size_t)wib * cap;
   int16_t *smap =
       reinterpret_cast<int16_t *>(smem + (size_t)nwarps * cap * 20) + (size_t)wib * map_cap;
+  __shared__ unsigned touched[kNumThreads / 32][kTouchedWords];  // see apply_pivots
   const int64_t total = n * nbatch;
 
   for (;;) {
@@ -365,18 +414,25 @@ k_numeric(int64_t n, int64_t nbatch, const int64_t *__restrict__ arp,
     }
     __syncwarp();
 
-    const bool ok = apply_pivots(dp, rv, spinfo, ri, fci, fv, err, row, limit_ns, lane);
+    bool upper_sent = false;
+    const CsrOut out{row != hold ? fv : nullptr, b0};
+    const bool ok = apply_pivots(dp, rv, spinfo, ri, fci, fv, err, row, limit_ns, lane, out, m,
+                                 touched[wib], &upper_sent);
     if (!ok) {
       if (lane == 0 && !earlier_failed(err, row)) set_err(err, row, ILUK_ETIMEOUT);
       continue;
     }
     if (lane == 0 && rv[dp] == 0.0) set_err(err, row, ILUK_EZEROPIVOT);
-    // write back the diagonal and U part first: that is what later rows wait
-    // for
+    // the rest of the row: the diagonal and U part first (what later rows
+    // wait for) unless they are out already, then the lower part
     if (row != hold) {
-      for (int t = lane; t < m; t += 32) {
-        const int q = t + dp < m ? t + dp : t + dp - m;
-        fv[b0 + q] = svals[q];
+      if (upper_sent) {
+        for (int q = lane; q < dp; q += 32) fv[b0 + q] = svals[q];
+      } else {
+        for (int t = lane; t < m; t += 32) {
+          const int q = t + dp < m ? t + dp : t + dp - m;
+          fv[b0 + q] = svals[q];
+        }
       }
     }
     __syncwarp();
@@ -507,6 +563,7 @@ __device__ void numeric_arena_rows(int64_t n, const int64_t *__restrict__ arp,
       reinterpret_cast<int32_t *>(smem + (size_t)nwarps * cap * 16) + (size_t)wib * cap;
   int16_t *smap =
       reinterpret_cast<int16_t *>(smem + (size_t)nwarps * cap * 20) + (size_t)wib * map_cap;
+  __shared__ unsigned touched[kNumThreads / 32][kTouchedWords];  // see apply_pivots
   for (;;) {
     unsigned long long tk = 0;
     if (lane == 0) tk = atomicAdd(ticket, 1ull);
@@ -583,17 +640,24 @@ __device__ void numeric_arena_rows(int64_t n, const int64_t *__restrict__ arp,
       for (int q = lane; q < m; q += 32) smap[scols[q] - ri.c0] = (int16_t)q;
     }
     __syncwarp();
-    if (!apply_pivots(dp, svals, spinfo, ri, acol, vals, err, row, limit_ns, lane)) {
+    bool upper_sent = false;
+    const ArenaOut out{vals, slot, dp, mu};
+    if (!apply_pivots(dp, svals, spinfo, ri, acol, vals, err, row, limit_ns, lane, out, m,
+                      touched[wib], &upper_sent)) {
       if (lane == 0 && !earlier_failed(err, row)) set_err(err, row, ILUK_ETIMEOUT);
       continue;
     }
     if (lane == 0 && svals[dp] == 0.0) set_err(err, row, ILUK_EZEROPIVOT);
-    // diagonal and upper part first (what later rows wait for), then the
-    // lower part, into the row's slot
-    for (int t = lane; t < m; t += 32) {
-      const int q = t + dp < m ? t + dp : t + dp - m;
-      const int64_t dst = q < dp ? slot + mu + 2 + q : slot + (q - dp);
-      vals[dst] = svals[q];
+    // the rest of the row into its slot: the diagonal and upper part first
+    // (what later rows wait for) unless they are out already, then the lower
+    // part
+    if (upper_sent) {
+      for (int q = lane; q < dp; q += 32) vals[out.at(q)] = svals[q];
+    } else {
+      for (int t = lane; t < m; t += 32) {
+        const int q = t + dp < m ? t + dp : t + dp - m;
+        vals[out.at(q)] = svals[q];
+      }
     }
     __syncwarp();
     // the row's entry of L x = v0, when the launch carries the first
@@ -631,7 +695,7 @@ static int numeric_cap(const iluk_sym *S, int *warps_out, int *map_out, size_t *
   int cap = S->max_row;
   if (cap < 32) cap = 32;
   cap = (cap + 31) & ~31;
-  const size_t budget = (size_t)max_smem_optin();
+  const size_t budget = (size_t)max_smem_optin() - kStaticSmem;
   for (int warps : {8, 4, 2, 1})
     for (int map : {8192, 4096, 0}) {
       const size_t need = ((size_t)cap * 20 + (size_t)map * 2) * warps;
@@ -720,10 +784,10 @@ cudaError_t launch_factor_fused(int64_t n, const int64_t *arp, const int32_t *ac
   for (int map : {8192, 4096, 0}) {
     num_smem = ((size_t)ncap * 20 + (size_t)map * 2) * warps;
     nmap = map;
-    if (num_smem <= (size_t)max_smem_optin()) break;
+    if (num_smem + kStaticSmem <= (size_t)max_smem_optin()) break;
   }
   const size_t smem = sym_smem > num_smem ? sym_smem : num_smem;
-  if (smem > (size_t)max_smem_optin()) return cudaErrorInvalidConfiguration;
+  if (smem + kStaticSmem > (size_t)max_smem_optin()) return cudaErrorInvalidConfiguration;
   cudaError_t e = cudaFuncSetAttribute(k_factor_fused, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
