@@ -741,8 +741,8 @@ static int factor_impl(const iluk_pattern *A, const double *A_val, int k, iluk_s
     CKF(dalloc(&xf, n, s));
     CKF(launch_fill_pending(n, xf, s));
   }
-  CKF(launch_factor_fused(n, A->rowptr, A->colind, A_val, k, ar, aval_arena, rinfo, nticket, err,
-                          cap, mapw, ncap, v0, xf, s));
+  CKF(launch_factor_fused(n, nnz, A->rowptr, A->colind, A_val, k, ar, aval_arena, rinfo, nticket,
+                          err, cap, mapw, ncap, v0, xf, s));
   {
     int64_t row = -1;
     uint64_t need = 0;

@@ -149,11 +149,11 @@ int64_t symbolic_arena_slack(int64_t n, int k, int cap, int mapw, int64_t rows_e
 int64_t symbolic_chunk(int k, int cap);
 cudaError_t launch_compact_values(int64_t n, const SymArena &ar, const double *aval,
                                   const int64_t *frp, double *fval, cudaStream_t s);
-cudaError_t launch_factor_fused(int64_t n, const int64_t *arp, const int32_t *aci,
-                                const double *aval, int k, const SymArena &ar, double *arena_val,
-                                unsigned long long *rinfo, unsigned long long *num_ticket,
-                                DevErr *err, int scap, int mapw, int ncap, const double *v0,
-                                double *xf, cudaStream_t s);
+cudaError_t launch_factor_fused(int64_t n, int64_t nnz_a, const int64_t *arp,
+                                const int32_t *aci, const double *aval, int k, const SymArena &ar,
+                                double *arena_val, unsigned long long *rinfo,
+                                unsigned long long *num_ticket, DevErr *err, int scap, int mapw,
+                                int ncap, const double *v0, double *xf, cudaStream_t s);
 cudaError_t launch_recip_diag(int64_t n, const int64_t *diag, const double *fval, DivPrep *rdiag,
                               cudaStream_t s);
 cudaError_t build_index_orders(int64_t n, LevelOrder *fwd, LevelOrder *bwd, cudaStream_t s);

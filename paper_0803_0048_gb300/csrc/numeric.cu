@@ -32,10 +32,17 @@ constexpr size_t kStaticSmem = (kNumThreads / 32) * kTouchedWords * sizeof(unsig
 // Sixteenths of the fused factorization's CTAs that run the symbolic walk:
 // few with the level-map walk, which keeps ahead of the numeric rows easily;
 // more with the sorted-list walk of wide matrices, which is slower per row.
-// (On the random band matrix with n = 160,000, k = 2, 3-10/16 time alike; on
-// the 7-point 3D 64^3 grid, k = 2: 58 ms at 3/16, 23 ms at 8/16, 37 ms at
-// 12/16.)
+// (On the 7-point 3D 64^3 grid, k = 2: 58 ms at 3/16, 23 ms at 8/16, 37 ms
+// at 12/16.)  With the level map, how far ahead the walk must run depends on
+// how long the numeric rows take: where A has long rows (they fill in to
+// long rows of F, each numeric row is slow) a smaller share leaves more SMs
+// to the numeric rows (random band, n = 160,000, 10 entries a row, k = 2:
+// 30.3 ms at 4/16, 29.1 ms at 3/16 and 2/16); where rows are short the walk
+// needs its 4/16 (2D 256^2 grid, 5 a row: 32.5 ms at 4/16, 40.6 at 3/16,
+// 50.5 at 2/16).
 constexpr int kFusedSymPartMap = 4;
+constexpr int kFusedSymPartMapLongRows = 3;
+constexpr int64_t kLongRowsOfA = 8;  // entries per row of A, on average
 constexpr int kFusedSymPartList = 8;
 
 // Factor values double as ready flags: the output array is filled with
@@ -771,9 +778,9 @@ static cudaError_t launch_numeric_impl(const iluk_sym *S, int64_t nbatch, const 
 // CTAs hold rows of at most ncap entries.  Fails (cudaErrorInvalidConfiguration)
 // when the two layouts do not fit one CTA's shared memory or the grid has room
 // for fewer than two CTAs.
-cudaError_t launch_factor_fused(int64_t n, const int64_t *arp, const int32_t *aci,
-                                const double *aval, int k, const SymArena &ar, double *arena_val,
-                                unsigned long long *rinfo, unsigned long long *num_ticket,
+cudaError_t launch_factor_fused(int64_t n, int64_t nnz_a, const int64_t *arp,
+                                const int32_t *aci, const double *aval, int k, const SymArena &ar,
+                                double *arena_val, unsigned long long *rinfo, unsigned long long *num_ticket,
                                 DevErr *err, int scap, int mapw, int ncap, const double *v0,
                                 double *xf, cudaStream_t s) {
   ProfScope prof_scope(ILUK_PROF_FACTOR, s);
@@ -797,7 +804,10 @@ cudaError_t launch_factor_fused(int64_t n, const int64_t *arp, const int32_t *ac
   int grid = bps * num_sms();
   if (grid < 2) return cudaErrorInvalidConfiguration;
   // the symbolic walk runs ahead of the numeric one with far fewer warps
-  int g_sym = (int)((int64_t)grid * (mapw ? kFusedSymPartMap : kFusedSymPartList) / 16);
+  const int part = !mapw ? kFusedSymPartList
+                   : nnz_a >= kLongRowsOfA * n ? kFusedSymPartMapLongRows
+                                                : kFusedSymPartMap;
+  int g_sym = (int)((int64_t)grid * part / 16);
   if (g_sym < 1) g_sym = 1;
   if (g_sym > grid - 1) g_sym = grid - 1;
   const int64_t chunk = symbolic_chunk(k, scap);
