@@ -780,9 +780,9 @@ static cudaError_t launch_numeric_impl(const iluk_sym *S, int64_t nbatch, const 
 // for fewer than two CTAs.
 cudaError_t launch_factor_fused(int64_t n, int64_t nnz_a, const int64_t *arp,
                                 const int32_t *aci, const double *aval, int k, const SymArena &ar,
-                                double *arena_val, unsigned long long *rinfo, unsigned long long *num_ticket,
-                                DevErr *err, int scap, int mapw, int ncap, const double *v0,
-                                double *xf, cudaStream_t s) {
+                                double *arena_val, unsigned long long *rinfo,
+                                unsigned long long *num_ticket, DevErr *err, int scap, int mapw,
+                                int ncap, const double *v0, double *xf, cudaStream_t s) {
   ProfScope prof_scope(ILUK_PROF_FACTOR, s);
   const int warps = kNumThreads / 32;
   const size_t sym_smem = (symbolic_smem_per_warp(scap) + symbolic_map_per_warp(mapw)) * warps;
