@@ -1525,6 +1525,11 @@ static int gmres_impl(const iluk_pattern *A, const double *A_val, int prec_kind,
     if (st != ILUK_OK) return fail(info, st);
   }
   bool fwd_ready = false;  // F->tmp holds L^-1 v_1 (made by the factorization)
+  // an exit before the backward sweep consumed it leaves F->tmp armed again,
+  // as every later application expects
+  auto rearm = at_scope_exit([&] {
+    if (fwd_ready && F) launch_fill_pending(n, F->tmp, s);
+  });
 
   auto precond = [&](const double *in, double *outv) -> cudaError_t {
     if (F) {
