@@ -29,6 +29,10 @@ constexpr int kNumThreads = 256;
 // bitmaps), left out of the dynamic shared memory's budget.
 constexpr int kTouchedWords = 16;  // bitmap words per warp: rows of up to 512 entries
 constexpr size_t kStaticSmem = (kNumThreads / 32) * kTouchedWords * sizeof(unsigned);
+// Average entries per row of F from which the refactorization publishes
+// entries early (random band, k = 2, 119 a row: 30.6 -> 25.8 ms; grids of 9 to
+// 61 a row lost 5-10 %).
+constexpr int64_t kEarlyRowLen = 80;
 // Sixteenths of the fused factorization's CTAs that run the symbolic walk:
 // few with the level-map walk, which keeps ahead of the numeric rows easily;
 // more with the sorted-list walk of wide matrices, which is slower per row.
@@ -232,7 +236,7 @@ struct ArenaOut {  // a slot: diagonal, upper part, end marker, lower part
 // out from registers as each update completes.  Then *upper_sent is true and
 // the caller writes only the lower part.  (A row longer than the bitmap, or a
 // last pivot row longer than the staged chunks, leaves it all to the caller.)
-template <typename Out>
+template <bool EARLY, typename Out>
 __device__ __forceinline__ bool apply_pivots(int dp, double *rv, const int64_t *spinfo,
                                              const RowIndex &ri, const int32_t *__restrict__ fci,
                                              const double *fv, const DevErr *err, int64_t row,
@@ -253,8 +257,8 @@ __device__ __forceinline__ bool apply_pivots(int dp, double *rv, const int64_t *
   for (int q = 0; q < dp && ok; ++q) {
     if (q + 1 < dp) stage_b(nxt, pa, ri, q + 1, fv, lane);
     if (q + 2 < dp) stage_a(pa, spinfo[q + 2], fci, fv, lane);
-    const bool early =
-        out.out != nullptr && q + 1 == dp && cur.ulen <= 32 * kPre && m <= 32 * kTouchedWords;
+    const bool early = EARLY && out.out != nullptr && q + 1 == dp && cur.ulen <= 32 * kPre &&
+                       m <= 32 * kTouchedWords;
     if (early) {
       if (lane < kTouchedWords) touched[lane] = 0u;
       __syncwarp();
@@ -345,6 +349,7 @@ __global__ void k_fill_pending_f(int64_t n, double *x) {
     x[i] = __longlong_as_double((long long)kPendingF);
 }
 
+template <bool EARLY>
 __global__ void __launch_bounds__(kNumThreads)
 k_numeric(int64_t n, int64_t nbatch, const int64_t *__restrict__ arp,
           const int32_t *__restrict__ a2f, const double *__restrict__ aval, int64_t astride,
@@ -364,7 +369,11 @@ k_numeric(int64_t n, int64_t nbatch, const int64_t *__restrict__ arp,
       reinterpret_cast<int32_t *>(smem + (size_t)nwarps * cap * 16) + (size_t)wib * cap;
   int16_t *smap =
       reinterpret_cast<int16_t *>(smem + (size_t)nwarps * cap * 20) + (size_t)wib * map_cap;
-  __shared__ unsigned touched[kNumThreads / 32][kTouchedWords];  // see apply_pivots
+  unsigned *touched_w = nullptr;  // see apply_pivots
+  if constexpr (EARLY) {
+    __shared__ unsigned touched[kNumThreads / 32][kTouchedWords];
+    touched_w = touched[wib];
+  }
   const int64_t total = n * nbatch;
 
   for (;;) {
@@ -423,8 +432,8 @@ k_numeric(int64_t n, int64_t nbatch, const int64_t *__restrict__ arp,
 
     bool upper_sent = false;
     const CsrOut out{row != hold ? fv : nullptr, b0};
-    const bool ok = apply_pivots(dp, rv, spinfo, ri, fci, fv, err, row, limit_ns, lane, out, m,
-                                 touched[wib], &upper_sent);
+    const bool ok = apply_pivots<EARLY>(dp, rv, spinfo, ri, fci, fv, err, row, limit_ns, lane,
+                                        out, m, touched_w, &upper_sent);
     if (!ok) {
       if (lane == 0 && !earlier_failed(err, row)) set_err(err, row, ILUK_ETIMEOUT);
       continue;
@@ -649,8 +658,8 @@ __device__ void numeric_arena_rows(int64_t n, const int64_t *__restrict__ arp,
     __syncwarp();
     bool upper_sent = false;
     const ArenaOut out{vals, slot, dp, mu};
-    if (!apply_pivots(dp, svals, spinfo, ri, acol, vals, err, row, limit_ns, lane, out, m,
-                      touched[wib], &upper_sent)) {
+    if (!apply_pivots<true>(dp, svals, spinfo, ri, acol, vals, err, row, limit_ns, lane, out, m,
+                            touched[wib], &upper_sent)) {
       if (lane == 0 && !earlier_failed(err, row)) set_err(err, row, ILUK_ETIMEOUT);
       continue;
     }
@@ -698,11 +707,12 @@ k_factor_fused(int64_t n, const int64_t *__restrict__ arp, const int32_t *__rest
 // entry) and a column map of map_cap int16.  The largest map that lets 8,
 // then 4, 2, 1 warps share a CTA; rows whose column span exceeds the map
 // fall back to binary search.
-static int numeric_cap(const iluk_sym *S, int *warps_out, int *map_out, size_t *smem_out) {
+static int numeric_cap(const iluk_sym *S, size_t static_smem, int *warps_out, int *map_out,
+                       size_t *smem_out) {
   int cap = S->max_row;
   if (cap < 32) cap = 32;
   cap = (cap + 31) & ~31;
-  const size_t budget = (size_t)max_smem_optin() - kStaticSmem;
+  const size_t budget = (size_t)max_smem_optin() - static_smem;
   for (int warps : {8, 4, 2, 1})
     for (int map : {8192, 4096, 0}) {
       const size_t need = ((size_t)cap * 20 + (size_t)map * 2) * warps;
@@ -743,9 +753,13 @@ static cudaError_t launch_numeric_impl(const iluk_sym *S, int64_t nbatch, const 
   // the forward level order, once built, is a valid and better-spread order
   const int32_t *order = S->levels_built ? S->lord.corder : nullptr;
   ProfScope prof_scope(ILUK_PROF_NUMERIC, s);
+  // rows publish their entries as soon as final (see apply_pivots) where F's
+  // rows are long; on short rows (grids) that measured slower
+  const bool early = S->nnz >= kEarlyRowLen * S->n;
+  const auto kern = early ? k_numeric<true> : k_numeric<false>;
   int warps, map_cap;
   size_t smem;
-  const int cap = numeric_cap(S, &warps, &map_cap, &smem);
+  const int cap = numeric_cap(S, early ? kStaticSmem : 0, &warps, &map_cap, &smem);
   if (cap < 0) return cudaErrorMemoryAllocation;
   {
     const int64_t nv = S->nnz * nbatch;
@@ -755,17 +769,17 @@ static cudaError_t launch_numeric_impl(const iluk_sym *S, int64_t nbatch, const 
     k_fill_pending_f<<<(unsigned)b, 256, 0, s>>>(nv, fvals);
     note_launch();
   }
-  cudaError_t e = cudaFuncSetAttribute(k_numeric, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
   int bps = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_numeric, warps * 32, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, warps * 32, smem);
   if (bps < 1) bps = 1;
   int64_t grid = (int64_t)bps * num_sms();
   const int64_t want = (S->n * nbatch + warps - 1) / warps;
   if (grid > want) grid = want;
   if (grid < 1) grid = 1;
-  k_numeric<<<(unsigned)grid, warps * 32, smem, s>>>(
+  kern<<<(unsigned)grid, warps * 32, smem, s>>>(
       S->n, nbatch, S->arowptr, S->a2f, avals, S->nnzA, S->rowptr, S->colind, S->diag, S->pinfo,
       fvals, S->nnz, order, ticket, errs, cap, map_cap, wait_limit(), hold_row());
   note_launch();
