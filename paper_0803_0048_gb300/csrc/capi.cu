@@ -671,10 +671,12 @@ static int factor_impl(const iluk_pattern *A, const double *A_val, int k, iluk_s
   int64_t *scan_tmp = nullptr;
   int32_t *maxrow = nullptr;
   double *xf = nullptr;  // L^-1 v0, when asked for; becomes F->tmp
+  DivPrep *rdiag = nullptr;  // the diagonal's reciprocals; becomes F->rdiag
   iluk_sym *S = nullptr;
   iluk_fac *F = nullptr;
   auto cleanup = [&]() {
     dfree(xf, s);
+    dfree(rdiag, s);
     dfree(err, s);
     dfree(ar.col, s);
     dfree(ar.lev, s);
@@ -741,8 +743,10 @@ static int factor_impl(const iluk_pattern *A, const double *A_val, int k, iluk_s
     CKF(dalloc(&xf, n, s));
     CKF(launch_fill_pending(n, xf, s));
   }
+  CKF(dalloc(&rdiag, n, s));  // every row writes its own entry; ~0 marks the others
+  CKF(cudaMemsetAsync(rdiag, 0xff, n * sizeof(DivPrep), s));
   CKF(launch_factor_fused(n, nnz, A->rowptr, A->colind, A_val, k, ar, aval_arena, rinfo, nticket,
-                          err, cap, mapw, ncap, v0, xf, s));
+                          err, cap, mapw, ncap, v0, xf, rdiag, s));
   {
     int64_t row = -1;
     uint64_t need = 0;
@@ -786,10 +790,10 @@ static int factor_impl(const iluk_pattern *A, const double *A_val, int k, iluk_s
     CKF(dalloc(&F->tmp, n, s));
     CKF(launch_fill_pending(n, F->tmp, s));
   }
-  CKF(dalloc(&F->rdiag, n, s));
+  F->rdiag = rdiag;  // written by the launch, row by row
+  rdiag = nullptr;
   CKF(dalloc(&F->err, 2, s));
   CKF(launch_compact_values(n, ar, aval_arena, S->rowptr, F->val, s));
-  CKF(launch_recip_diag(n, S->diag, F->val, F->rdiag, s));
   CKF(launch_fill_err(F->err, s));
   int32_t mr = 0;
   CKF(cudaMemcpyAsync(&mr, maxrow, sizeof(int32_t), cudaMemcpyDeviceToHost, s));

@@ -153,9 +153,8 @@ cudaError_t launch_factor_fused(int64_t n, int64_t nnz_a, const int64_t *arp,
                                 const int32_t *aci, const double *aval, int k, const SymArena &ar,
                                 double *arena_val, unsigned long long *rinfo,
                                 unsigned long long *num_ticket, DevErr *err, int scap, int mapw,
-                                int ncap, const double *v0, double *xf, cudaStream_t s);
-cudaError_t launch_recip_diag(int64_t n, const int64_t *diag, const double *fval, DivPrep *rdiag,
-                              cudaStream_t s);
+                                int ncap, const double *v0, double *xf, DivPrep *rdiag,
+                                cudaStream_t s);
 cudaError_t build_index_orders(int64_t n, LevelOrder *fwd, LevelOrder *bwd, cudaStream_t s);
 cudaError_t launch_symbolic_compact(int64_t n, const SymArena &ar, const int64_t *frp,
                                     int32_t *fci, uint8_t *flev, int64_t *fdiag, int32_t *maxrow,

@@ -108,6 +108,7 @@ struct PivotA {
   int ulen;
   int32_t j[kPre];
   double piv;
+  unsigned long long xr;  // the pivot row's published reciprocal of f_hh, or ~0
 };
 
 struct PivotPre {
@@ -115,6 +116,7 @@ struct PivotPre {
   int ulen;
   int pos[kPre];
   double piv, f[kPre];
+  unsigned long long xr;
 };
 
 // Where column j sits in the current row: a dense map over the row's column
@@ -136,10 +138,12 @@ struct RowIndex {
 };
 
 __device__ __forceinline__ void stage_a(PivotA &a, int64_t pinfo, const int32_t *__restrict__ fci,
-                                        const double *fv, int lane) {
+                                        const double *fv, int lane, const DivPrep *rdp, int32_t h) {
   a.hd = pinfo >> kUlenBits;
   a.ulen = (int)(pinfo & ((1ll << kUlenBits) - 1));
   a.piv = ld_gpu(&fv[a.hd]);
+  a.xr = ~0ull;
+  if (rdp) asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(a.xr) : "l"(&rdp[h].x));
 #pragma unroll
   for (int c = 0; c < kPre; ++c) {
     const int e = lane + 32 * c;
@@ -152,6 +156,7 @@ __device__ __forceinline__ void stage_b(PivotPre &pp, const PivotA &a, const Row
   pp.hd = a.hd;
   pp.ulen = a.ulen;
   pp.piv = a.piv;
+  pp.xr = a.xr;
   int lo = q + 1;  // a lane's columns increase with c: each search starts where the last ended
 #pragma unroll
   for (int c = 0; c < kPre; ++c) {
@@ -206,6 +211,15 @@ __device__ __forceinline__ bool wait_pivot(PivotPre &pp, const double *fv, int l
   }
 }
 
+// The row's diagonal with its fixed-point reciprocal, for the later rows
+// that divide by it (the x word, ~0 until written, is what they look for)
+// and for the sweeps.
+__device__ __forceinline__ void publish_recip(DivPrep *d, double fii) {
+  const DivPrep p = div_prep(fii);
+  d->b = p.b;
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(&d->x), "l"(p.x) : "memory");
+}
+
 // Where the row's finished entries go (position q of the row, diagonal at
 // dp): out[at(q)].  `out` null: nowhere, the caller writes the row back.
 struct CsrOut {
@@ -241,7 +255,8 @@ __device__ __forceinline__ bool apply_pivots(int dp, double *rv, const int64_t *
                                              const RowIndex &ri, const int32_t *__restrict__ fci,
                                              const double *fv, const DevErr *err, int64_t row,
                                              int64_t limit_ns, int lane, const Out &out, int m,
-                                             unsigned *touched, bool *upper_sent) {
+                                             unsigned *touched, bool *upper_sent,
+                                             const DivPrep *rdp) {
   // Pivots go through the three stages (see PivotA): in iteration q the
   // warp applies pivot q, finds the positions of pivot q+1 and issues the
   // loads of pivot q+2, so the latencies of the later stages overlap the
@@ -250,13 +265,13 @@ __device__ __forceinline__ bool apply_pivots(int dp, double *rv, const int64_t *
   PivotA pa;
   PivotPre cur, nxt;
   if (dp > 0) {
-    stage_a(pa, spinfo[0], fci, fv, lane);
+    stage_a(pa, spinfo[0], fci, fv, lane, rdp, ri.rc[0]);
     stage_b(cur, pa, ri, 0, fv, lane);
   }
-  if (dp > 1) stage_a(pa, spinfo[1], fci, fv, lane);
+  if (dp > 1) stage_a(pa, spinfo[1], fci, fv, lane, rdp, ri.rc[1]);
   for (int q = 0; q < dp && ok; ++q) {
     if (q + 1 < dp) stage_b(nxt, pa, ri, q + 1, fv, lane);
-    if (q + 2 < dp) stage_a(pa, spinfo[q + 2], fci, fv, lane);
+    if (q + 2 < dp) stage_a(pa, spinfo[q + 2], fci, fv, lane, rdp, ri.rc[q + 2]);
     const bool early = EARLY && out.out != nullptr && q + 1 == dp && cur.ulen <= 32 * kPre &&
                        m <= 32 * kTouchedWords;
     if (early) {
@@ -276,10 +291,13 @@ __device__ __forceinline__ bool apply_pivots(int dp, double *rv, const int64_t *
     }
     // The multiplier f_ih / f_hh, correctly rounded, on the integer pipes
     // (div_int): a fraction of the latency of an FP64 division, and it
-    // leaves the FP64 pipe to the updates.  (A reciprocal published by the
-    // pivot row measured slower: it is rarely there yet for the pivot that
-    // just arrived, and its loads and polls cost more than they save.)
-    const double fih = div_int(rv[q], cur.piv);
+    // leaves the FP64 pipe to the updates.  A pivot row publishes the
+    // fixed-point reciprocal of its diagonal (rdp[h].x) once it has written
+    // itself back; when that is already there at staging, only the remainder
+    // half of the division is left (div_fin).  Same quotient either way.
+    const unsigned long long xr = __shfl_sync(FULL_MASK, cur.xr, 0);
+    const double fih =
+        xr != ~0ull ? div_fin(rv[q], DivPrep{xr, cur.piv}) : div_int(rv[q], cur.piv);
     __syncwarp();
     if (lane == 0) rv[q] = fih;
     // only the chunks the pivot row has: an FP64 instruction costs its
@@ -357,7 +375,7 @@ k_numeric(int64_t n, int64_t nbatch, const int64_t *__restrict__ arp,
           const int64_t *__restrict__ fdiag, const int64_t *__restrict__ pinfo, double *fval,
           int64_t fstride, const int32_t *__restrict__ order,
           unsigned long long *ticket, DevErr *errs, int cap, int map_cap, int64_t limit_ns,
-          int64_t hold) {
+          int64_t hold, DivPrep *rdiag) {
   // per warp: values, pivot infos (cap each), columns, then the column map
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31;
@@ -433,7 +451,7 @@ k_numeric(int64_t n, int64_t nbatch, const int64_t *__restrict__ arp,
     bool upper_sent = false;
     const CsrOut out{row != hold ? fv : nullptr, b0};
     const bool ok = apply_pivots<EARLY>(dp, rv, spinfo, ri, fci, fv, err, row, limit_ns, lane,
-                                        out, m, touched_w, &upper_sent);
+                                        out, m, touched_w, &upper_sent, rdiag);
     if (!ok) {
       if (lane == 0 && !earlier_failed(err, row)) set_err(err, row, ILUK_ETIMEOUT);
       continue;
@@ -450,6 +468,7 @@ k_numeric(int64_t n, int64_t nbatch, const int64_t *__restrict__ arp,
           fv[b0 + q] = svals[q];
         }
       }
+      if (rdiag && lane == 0) publish_recip(&rdiag[row], svals[dp]);
     }
     __syncwarp();
   }
@@ -569,7 +588,8 @@ __device__ void numeric_arena_rows(int64_t n, const int64_t *__restrict__ arp,
                                    double *vals, const unsigned long long *meta,
                                    const unsigned long long *rinfo, unsigned long long *ticket,
                                    DevErr *err, int cap, int map_cap, int64_t limit_ns,
-                                   const double *v0, double *xf, unsigned char *smem) {
+                                   const double *v0, double *xf, DivPrep *rdiag,
+                                   unsigned char *smem) {
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   const int nwarps = blockDim.x >> 5;
@@ -659,7 +679,7 @@ __device__ void numeric_arena_rows(int64_t n, const int64_t *__restrict__ arp,
     bool upper_sent = false;
     const ArenaOut out{vals, slot, dp, mu};
     if (!apply_pivots<true>(dp, svals, spinfo, ri, acol, vals, err, row, limit_ns, lane, out, m,
-                            touched[wib], &upper_sent)) {
+                            touched[wib], &upper_sent, rdiag)) {
       if (lane == 0 && !earlier_failed(err, row)) set_err(err, row, ILUK_ETIMEOUT);
       continue;
     }
@@ -675,6 +695,7 @@ __device__ void numeric_arena_rows(int64_t n, const int64_t *__restrict__ arp,
         vals[out.at(q)] = svals[q];
       }
     }
+    if (rdiag && lane == 0) publish_recip(&rdiag[row], svals[dp]);
     __syncwarp();
     // the row's entry of L x = v0, when the launch carries the first
     // right-hand side
@@ -692,7 +713,8 @@ k_factor_fused(int64_t n, const int64_t *__restrict__ arp, const int32_t *__rest
                int64_t *row_off, int32_t *row_len, int32_t *row_ust, unsigned long long *meta,
                unsigned long long *rinfo, unsigned long long *sym_ticket,
                unsigned long long *num_ticket, DevErr *err, int scap, int mapw, int64_t chunk,
-               int ncap, int nmap, int g_sym, int64_t limit_ns, const double *v0, double *xf) {
+               int ncap, int nmap, int g_sym, int64_t limit_ns, const double *v0, double *xf,
+               DivPrep *rdiag) {
   extern __shared__ __align__(16) unsigned char smem[];
   if ((int)blockIdx.x < g_sym)
     symbolic_rows_body<false, true>(n, arp, aci, k, arena_col, arena_lev, arena_cap, arena_top,
@@ -700,7 +722,7 @@ k_factor_fused(int64_t n, const int64_t *__restrict__ arp, const int32_t *__rest
                                     chunk, limit_ns, rinfo, smem);
   else
     numeric_arena_rows(n, arp, aci, aval, arena_col, arena_val, meta, rinfo, num_ticket, err,
-                       ncap, nmap, limit_ns, v0, xf, smem);
+                       ncap, nmap, limit_ns, v0, xf, rdiag, smem);
 }
 
 // Shared memory per warp: a row of F (value, pivot info, column: 20 bytes per
@@ -724,27 +746,6 @@ static int numeric_cap(const iluk_sym *S, size_t static_smem, int *warps_out, in
       }
     }
   return -1;  // a row of F exceeds shared memory
-}
-
-// rdiag[i] = div_prep(f_ii): each diagonal entry with its fixed-point
-// reciprocal, for the backward sweep's division.  A row that did not finish
-// leaves its diagonal pending (a NaN), which div_fin hands to IEEE division.
-__global__ void k_recip_diag(int64_t n, const int64_t *__restrict__ fdiag,
-                             const double *__restrict__ fval, DivPrep *rdiag) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    rdiag[i] = div_prep(fval[fdiag[i]]);
-}
-
-cudaError_t launch_recip_diag(int64_t n, const int64_t *diag, const double *fval, DivPrep *rdiag,
-                              cudaStream_t s) {
-  if (n == 0) return cudaSuccess;
-  int64_t rb = (n + 255) / 256;
-  if (rb > (int64_t)num_sms() * 8) rb = (int64_t)num_sms() * 8;
-  if (rb < 1) rb = 1;
-  k_recip_diag<<<(unsigned)rb, 256, 0, s>>>(n, diag, fval, rdiag);
-  note_launch();
-  return cudaGetLastError();
 }
 
 static cudaError_t launch_numeric_impl(const iluk_sym *S, int64_t nbatch, const double *avals,
@@ -779,11 +780,14 @@ static cudaError_t launch_numeric_impl(const iluk_sym *S, int64_t nbatch, const 
   const int64_t want = (S->n * nbatch + warps - 1) / warps;
   if (grid > want) grid = want;
   if (grid < 1) grid = 1;
+  if (rdiag) {  // every row writes its own entry; ~0 marks the ones not written yet
+    e = cudaMemsetAsync(rdiag, 0xff, (size_t)S->n * sizeof(DivPrep), s);
+    if (e != cudaSuccess) return e;
+  }
   kern<<<(unsigned)grid, warps * 32, smem, s>>>(
       S->n, nbatch, S->arowptr, S->a2f, avals, S->nnzA, S->rowptr, S->colind, S->diag, S->pinfo,
-      fvals, S->nnz, order, ticket, errs, cap, map_cap, wait_limit(), hold_row());
+      fvals, S->nnz, order, ticket, errs, cap, map_cap, wait_limit(), hold_row(), rdiag);
   note_launch();
-  if (rdiag) return launch_recip_diag(S->n, S->diag, fvals, rdiag, s);
   return cudaGetLastError();
 }
 
@@ -796,7 +800,8 @@ cudaError_t launch_factor_fused(int64_t n, int64_t nnz_a, const int64_t *arp,
                                 const int32_t *aci, const double *aval, int k, const SymArena &ar,
                                 double *arena_val, unsigned long long *rinfo,
                                 unsigned long long *num_ticket, DevErr *err, int scap, int mapw,
-                                int ncap, const double *v0, double *xf, cudaStream_t s) {
+                                int ncap, const double *v0, double *xf, DivPrep *rdiag,
+                                cudaStream_t s) {
   ProfScope prof_scope(ILUK_PROF_FACTOR, s);
   const int warps = kNumThreads / 32;
   const size_t sym_smem = (symbolic_smem_per_warp(scap) + symbolic_map_per_warp(mapw)) * warps;
@@ -833,7 +838,7 @@ cudaError_t launch_factor_fused(int64_t n, int64_t nnz_a, const int64_t *arp,
                   (void *)&ar.top, (void *)&ar.row_off, (void *)&ar.row_len, (void *)&ar.row_ust,
                   (void *)&ar.meta, (void *)&rinfo, (void *)&ar.ticket, (void *)&num_ticket,
                   (void *)&err, (void *)&sc, (void *)&mw, (void *)&ch, (void *)&nc, (void *)&nm,
-                  (void *)&gs, (void *)&limit, (void *)&v0, (void *)&xf};
+                  (void *)&gs, (void *)&limit, (void *)&v0, (void *)&xf, (void *)&rdiag};
   e = cudaLaunchCooperativeKernel((const void *)k_factor_fused, dim3((unsigned)grid),
                                   dim3(kNumThreads), args, smem, s);
   note_launch();
