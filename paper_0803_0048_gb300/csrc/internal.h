@@ -92,6 +92,10 @@ struct iiluk {
 
 namespace iluk {
 
+// Average rows per forward level from which the row kernels (numeric phase,
+// TPIILU build) walking level order leave out the column map for more warps.
+constexpr int64_t kWideLevelRows = 300;
+
 int64_t wait_limit();
 void note_launch();              // counts kernel launches (iluk_launch_count)
 

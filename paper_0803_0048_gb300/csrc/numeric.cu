@@ -729,13 +729,11 @@ k_factor_fused(int64_t n, const int64_t *__restrict__ arp, const int32_t *__rest
 // entry) and a column map of map_cap int16.  The largest map that lets 8,
 // then 4, 2, 1 warps share a CTA; rows whose column span exceeds the map
 // fall back to binary search.
-// Rows per forward level (on average) from which the numeric phase, walking
-// level order, goes without the column map: the map's shared memory holds
-// the launch to one CTA per SM, and on DAGs this wide more rows in flight
-// matter more than the map (refactorization of the 27-point 90^3 grid, 1,168
-// rows a level: 10.1 -> 5.9 ms; C3, 378 a level: 3.46 -> 2.71 ms; 196 and 64
-// a level lost 2-3 %).
-constexpr int64_t kWideLevel = 300;
+// kWideLevelRows (internal.h): on level orders this wide the numeric phase
+// goes without the column map: the map's shared memory holds the launch to
+// one CTA per SM, and here more rows in flight matter more than the map
+// (refactorization of the 27-point 90^3 grid, 1,168 rows a level: 10.1 ->
+// 5.9 ms; C3, 378 a level: 3.46 -> 2.71 ms; 196 and 64 a level lost 2-3 %).
 
 static int numeric_cap(const iluk_sym *S, size_t static_smem, bool wide, int *warps_out,
                        int *map_out, size_t *smem_out) {
@@ -769,7 +767,7 @@ static cudaError_t launch_numeric_impl(const iluk_sym *S, int64_t nbatch, const 
   const auto kern = early ? k_numeric<true> : k_numeric<false>;
   int warps, map_cap;
   size_t smem;
-  const bool wide = order != nullptr && S->n >= kWideLevel * (int64_t)S->lord.nlev;
+  const bool wide = order != nullptr && S->n >= kWideLevelRows * (int64_t)S->lord.nlev;
   const int cap = numeric_cap(S, early ? kStaticSmem : 0, wide, &warps, &map_cap, &smem);
   if (cap < 0) return cudaErrorMemoryAllocation;
   {

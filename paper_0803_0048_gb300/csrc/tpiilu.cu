@@ -327,10 +327,13 @@ cudaError_t launch_iiluk_build(const iluk_sym *S, const double *fval, const DivP
   if (n == 0) return cudaSuccess;
   int cap = S->max_row < 32 ? 32 : ((S->max_row + 31) & ~31);
   const size_t budget = (size_t)max_smem_optin();
+  // on wide level orders more rows in flight matter more than the column
+  // map, as in the numeric phase
+  const bool wide = S->levels_built && n >= kWideLevelRows * (int64_t)S->lord.nlev;
   int warps = 0, map_cap = 0;
   for (int w : {8, 4, 2, 1}) {
     for (int mc : {8192, 4096, 0})
-      if (((size_t)cap * 20 + (size_t)mc * 2) * w <= budget) {
+      if ((!wide || mc == 0) && ((size_t)cap * 20 + (size_t)mc * 2) * w <= budget) {
         warps = w;
         map_cap = mc;
         break;
