@@ -521,14 +521,15 @@ void iluk_fac_destroy(iluk_fac *F) {
 }
 
 static int numeric_into(iluk_fac *F, const double *A_val, iluk_info *info, cudaStream_t s,
-                        bool build_levels = true) {
+                        bool build_levels = true, int32_t *depth = nullptr,
+                        unsigned *maxdepth = nullptr) {
   const iluk_sym *S = F->S;
   // the numeric phase's row ticket lives in the handle's scratch
   CK(cudaMemsetAsync(F->sync, 0, sweep_sync_ints(S->n) * sizeof(int), s));
   CK(launch_fill_err(F->err, s));
   // the numeric phase also fills the reciprocals of the diagonal (after the factorization)
   CK(launch_numeric(S, A_val, F->val, F->rdiag, reinterpret_cast<unsigned long long *>(F->sync),
-                    F->err, s));
+                    F->err, depth, maxdepth, s));
   // First factorization of this pattern: build the sweeps' level orders on a
   // second stream meanwhile (they read only the pattern; the numeric kernel
   // leaves room on every SM for the two level-building CTAs).
@@ -595,6 +596,18 @@ int iluk_numeric(const iluk_sym *S, const double *A_val, iluk_fac **out, iluk_in
 // launch cannot run or reports an error (the two calls then report it).
 }  // extern "C"
 
+// A factorization made without level orders (iluk_factor) measured the
+// forward DAG's depth as it went: on a wide DAG the sweeps need level orders,
+// so they are built now (on a narrow one index order is as fast).
+static int levels_if_wide(const iluk_sym *S, const unsigned *maxdepth, iluk_info *info,
+                          cudaStream_t s) {
+  unsigned d = 0;
+  CK(cudaMemcpyAsync(&d, maxdepth, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (d == 0 || S->n < kWideSweepRows * (int64_t)d) return ILUK_OK;
+  return ensure_levels(S, s);
+}
+
 // iluk_factor, with two additions for iluk_solve: `validated` skips the
 // pattern check the caller has made, and a non-null v0 asks the one-launch
 // path to solve L x = v0 beside its numeric phase (each row's entry of x as
@@ -641,12 +654,20 @@ static int factor_impl(const iluk_pattern *A, const double *A_val, int k, iluk_s
     if (e2 == cudaSuccess) e2 = dalloc(&F2->rdiag, S2->n, s2);
     if (e2 == cudaSuccess) e2 = dalloc(&F2->err, 2, s2);
     if (e2 == cudaSuccess) e2 = launch_fill_pending(S2->n, F2->tmp, s2);
+    int32_t *depth = nullptr;
+    unsigned *maxdepth = nullptr;
+    auto depth_bufs = at_scope_exit([&] { dfree(depth, s2); dfree(maxdepth, s2); });
+    if (e2 == cudaSuccess) e2 = dalloc(&depth, S2->n, s2);
+    if (e2 == cudaSuccess) e2 = dalloc(&maxdepth, 1, s2);
+    if (e2 == cudaSuccess) e2 = cudaMemsetAsync(depth, 0, (size_t)S2->n * sizeof(int32_t), s2);
+    if (e2 == cudaSuccess) e2 = cudaMemsetAsync(maxdepth, 0, sizeof(unsigned), s2);
     if (e2 != cudaSuccess) {
       iluk_fac_destroy(F2);
       iluk_sym_destroy(S2);
       return fail(info, e2 == cudaErrorMemoryAllocation ? ILUK_ENOMEM : ILUK_ECUDA);
     }
-    st2 = numeric_into(F2, A_val, info, s2, false);
+    st2 = numeric_into(F2, A_val, info, s2, false, depth, maxdepth);
+    if (st2 == ILUK_OK) st2 = levels_if_wide(S2, maxdepth, info, s2);
     if (st2 != ILUK_OK) {
       iluk_fac_destroy(F2);
       iluk_sym_destroy(S2);
@@ -672,11 +693,15 @@ static int factor_impl(const iluk_pattern *A, const double *A_val, int k, iluk_s
   int32_t *maxrow = nullptr;
   double *xf = nullptr;  // L^-1 v0, when asked for; becomes F->tmp
   DivPrep *rdiag = nullptr;  // the diagonal's reciprocals; becomes F->rdiag
+  int32_t *fdepth = nullptr;  // each row's forward depth, and the DAG's
+  unsigned *maxdepth = nullptr;
   iluk_sym *S = nullptr;
   iluk_fac *F = nullptr;
   auto cleanup = [&]() {
     dfree(xf, s);
     dfree(rdiag, s);
+    dfree(fdepth, s);
+    dfree(maxdepth, s);
     dfree(err, s);
     dfree(ar.col, s);
     dfree(ar.lev, s);
@@ -745,8 +770,12 @@ static int factor_impl(const iluk_pattern *A, const double *A_val, int k, iluk_s
   }
   CKF(dalloc(&rdiag, n, s));  // every row writes its own entry; ~0 marks the others
   CKF(cudaMemsetAsync(rdiag, 0xff, n * sizeof(DivPrep), s));
+  CKF(dalloc(&fdepth, n, s));
+  CKF(dalloc(&maxdepth, 1, s));
+  CKF(cudaMemsetAsync(fdepth, 0, n * sizeof(int32_t), s));
+  CKF(cudaMemsetAsync(maxdepth, 0, sizeof(unsigned), s));
   CKF(launch_factor_fused(n, nnz, A->rowptr, A->colind, A_val, k, ar, aval_arena, rinfo, nticket,
-                          err, cap, mapw, ncap, v0, xf, rdiag, s));
+                          err, cap, mapw, ncap, v0, xf, rdiag, fdepth, maxdepth, s));
   {
     int64_t row = -1;
     uint64_t need = 0;
@@ -799,6 +828,10 @@ static int factor_impl(const iluk_pattern *A, const double *A_val, int k, iluk_s
   CKF(cudaMemcpyAsync(&mr, maxrow, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   CKF(cudaStreamSynchronize(s));
   S->max_row = mr;
+  {
+    iluk_info linfo;
+    if (levels_if_wide(S, maxdepth, &linfo, s) != ILUK_OK) return fallback();
+  }
 #undef CKF
   cleanup();
   *S_out = S;

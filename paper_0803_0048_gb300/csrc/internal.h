@@ -95,6 +95,13 @@ namespace iluk {
 // Average rows per forward level from which the row kernels (numeric phase,
 // TPIILU build) walking level order leave out the column map for more warps.
 constexpr int64_t kWideLevelRows = 300;
+// Average rows per forward level from which a factorization made without
+// level orders builds them for its sweeps: on DAGs this wide the sweeps in
+// index order starve (C3, 378 rows a level: one application 8.7 ms in index
+// order, 1.5 ms in level order; 27-point 90^3, 1,168 a level: 22.1 / 2.2 ms),
+// on narrower ones index order is as fast or faster (2D 256^2, 64 a level:
+// 1.06 / 1.35 ms; the random band, 10 a level: 15.1 / 15.3 ms).
+constexpr int64_t kWideSweepRows = 128;
 
 int64_t wait_limit();
 void note_launch();              // counts kernel launches (iluk_launch_count)
@@ -158,7 +165,7 @@ cudaError_t launch_factor_fused(int64_t n, int64_t nnz_a, const int64_t *arp,
                                 double *arena_val, unsigned long long *rinfo,
                                 unsigned long long *num_ticket, DevErr *err, int scap, int mapw,
                                 int ncap, const double *v0, double *xf, DivPrep *rdiag,
-                                cudaStream_t s);
+                                int32_t *depth, unsigned *maxdepth, cudaStream_t s);
 cudaError_t build_index_orders(int64_t n, LevelOrder *fwd, LevelOrder *bwd, cudaStream_t s);
 cudaError_t launch_symbolic_compact(int64_t n, const SymArena &ar, const int64_t *frp,
                                     int32_t *fci, uint8_t *flev, int64_t *fdiag, int32_t *maxrow,
@@ -174,8 +181,11 @@ int build_levels_pair(int64_t n, const int64_t *rp, const int32_t *ci, const int
 // The factor values double as ready flags (numeric.cu); fval is overwritten.
 cudaError_t launch_pivot_info(int64_t n, const int64_t *frp, const int32_t *fci,
                               const int64_t *fdiag, int64_t *pinfo, cudaStream_t s);
+// depth/maxdepth (may be null): each row's forward depth and the DAG's
+// depth, zeroed by the caller.
 cudaError_t launch_numeric(const iluk_sym *S, const double *aval, double *fval, DivPrep *rdiag,
-                           unsigned long long *ticket, DevErr *err, cudaStream_t s);
+                           unsigned long long *ticket, DevErr *err, int32_t *depth,
+                           unsigned *maxdepth, cudaStream_t s);
 cudaError_t launch_numeric_batched(const iluk_sym *S, int64_t nbatch, const double *avals,
                                    double *fvals, unsigned long long *ticket, DevErr *errs,
                                    cudaStream_t s);

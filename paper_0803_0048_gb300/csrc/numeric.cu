@@ -220,6 +220,42 @@ __device__ __forceinline__ void publish_recip(DivPrep *d, double fii) {
   asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(&d->x), "l"(p.x) : "memory");
 }
 
+// The row's depth in the forward DAG (Sec. 3.6's level sets): 1 + the
+// deepest of its pivot rows (cols[0..dp)), written once the row is written
+// back.  Those rows are written back already and set their own depth right
+// after, so each wait is short; depth 0 means not yet.  maxdepth collects
+// the DAG's depth, from which the factorization judges the DAG's width.
+// Warp-uniform; gives up (no depth) on time-out or an earlier row's failure.
+__device__ __forceinline__ void note_depth(int64_t row, int dp, const int32_t *cols,
+                                           int32_t *depth, unsigned *maxdepth, const DevErr *err,
+                                           int64_t limit_ns, int lane) {
+  int dm = 0;
+  bool ok = true;
+  for (int q = lane; q < dp; q += 32) {
+    const int32_t *p = &depth[cols[q]];
+    int d;
+    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(d) : "l"(p));
+    if (d == 0) {
+      const uint64_t t0 = globaltimer_ns();
+      for (unsigned it = 0; d == 0; ++it) {
+        __nanosleep(64);
+        asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(d) : "l"(p));
+        if ((it & 15u) == 15u &&
+            (earlier_failed(err, row) || (int64_t)(globaltimer_ns() - t0) > limit_ns)) {
+          ok = false;
+          break;
+        }
+      }
+    }
+    if (d > dm) dm = d;
+  }
+  dm = __reduce_max_sync(FULL_MASK, dm) + 1;
+  if (__all_sync(FULL_MASK, ok) && lane == 0) {
+    asm volatile("st.relaxed.gpu.global.s32 [%0], %1;" ::"l"(depth + row), "r"(dm) : "memory");
+    atomicMax(maxdepth, (unsigned)dm);
+  }
+}
+
 // Where the row's finished entries go (position q of the row, diagonal at
 // dp): out[at(q)].  `out` null: nowhere, the caller writes the row back.
 struct CsrOut {
@@ -375,7 +411,7 @@ k_numeric(int64_t n, int64_t nbatch, const int64_t *__restrict__ arp,
           const int64_t *__restrict__ fdiag, const int64_t *__restrict__ pinfo, double *fval,
           int64_t fstride, const int32_t *__restrict__ order,
           unsigned long long *ticket, DevErr *errs, int cap, int map_cap, int64_t limit_ns,
-          int64_t hold, DivPrep *rdiag) {
+          int64_t hold, DivPrep *rdiag, int32_t *depth, unsigned *maxdepth) {
   // per warp: values, pivot infos (cap each), columns, then the column map
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31;
@@ -469,6 +505,7 @@ k_numeric(int64_t n, int64_t nbatch, const int64_t *__restrict__ arp,
         }
       }
       if (rdiag && lane == 0) publish_recip(&rdiag[row], svals[dp]);
+      if (depth) note_depth(row, dp, rc, depth, maxdepth, err, limit_ns, lane);
     }
     __syncwarp();
   }
@@ -589,7 +626,7 @@ __device__ void numeric_arena_rows(int64_t n, const int64_t *__restrict__ arp,
                                    const unsigned long long *rinfo, unsigned long long *ticket,
                                    DevErr *err, int cap, int map_cap, int64_t limit_ns,
                                    const double *v0, double *xf, DivPrep *rdiag,
-                                   unsigned char *smem) {
+                                   int32_t *depth, unsigned *maxdepth, unsigned char *smem) {
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   const int nwarps = blockDim.x >> 5;
@@ -702,6 +739,7 @@ __device__ void numeric_arena_rows(int64_t n, const int64_t *__restrict__ arp,
     if (xf && !forward_entry(row, dp, svals, scols, v0, xf, err, limit_ns, lane)) {
       if (lane == 0 && !earlier_failed(err, row)) set_err(err, row, ILUK_ETIMEOUT);
     }
+    if (depth) note_depth(row, dp, scols, depth, maxdepth, err, limit_ns, lane);
     __syncwarp();
   }
 }
@@ -714,7 +752,7 @@ k_factor_fused(int64_t n, const int64_t *__restrict__ arp, const int32_t *__rest
                unsigned long long *rinfo, unsigned long long *sym_ticket,
                unsigned long long *num_ticket, DevErr *err, int scap, int mapw, int64_t chunk,
                int ncap, int nmap, int g_sym, int64_t limit_ns, const double *v0, double *xf,
-               DivPrep *rdiag) {
+               DivPrep *rdiag, int32_t *depth, unsigned *maxdepth) {
   extern __shared__ __align__(16) unsigned char smem[];
   if ((int)blockIdx.x < g_sym)
     symbolic_rows_body<false, true>(n, arp, aci, k, arena_col, arena_lev, arena_cap, arena_top,
@@ -722,7 +760,7 @@ k_factor_fused(int64_t n, const int64_t *__restrict__ arp, const int32_t *__rest
                                     chunk, limit_ns, rinfo, smem);
   else
     numeric_arena_rows(n, arp, aci, aval, arena_col, arena_val, meta, rinfo, num_ticket, err,
-                       ncap, nmap, limit_ns, v0, xf, rdiag, smem);
+                       ncap, nmap, limit_ns, v0, xf, rdiag, depth, maxdepth, smem);
 }
 
 // Shared memory per warp: a row of F (value, pivot info, column: 20 bytes per
@@ -757,7 +795,8 @@ static int numeric_cap(const iluk_sym *S, size_t static_smem, bool wide, int *wa
 
 static cudaError_t launch_numeric_impl(const iluk_sym *S, int64_t nbatch, const double *avals,
                                        double *fvals, DivPrep *rdiag, unsigned long long *ticket,
-                                       DevErr *errs, cudaStream_t s) {
+                                       DevErr *errs, int32_t *depth, unsigned *maxdepth,
+                                       cudaStream_t s) {
   // the forward level order, once built, is a valid and better-spread order
   const int32_t *order = S->levels_built ? S->lord.corder : nullptr;
   ProfScope prof_scope(ILUK_PROF_NUMERIC, s);
@@ -794,7 +833,8 @@ static cudaError_t launch_numeric_impl(const iluk_sym *S, int64_t nbatch, const 
   }
   kern<<<(unsigned)grid, warps * 32, smem, s>>>(
       S->n, nbatch, S->arowptr, S->a2f, avals, S->nnzA, S->rowptr, S->colind, S->diag, S->pinfo,
-      fvals, S->nnz, order, ticket, errs, cap, map_cap, wait_limit(), hold_row(), rdiag);
+      fvals, S->nnz, order, ticket, errs, cap, map_cap, wait_limit(), hold_row(), rdiag, depth,
+      maxdepth);
   note_launch();
   return cudaGetLastError();
 }
@@ -809,7 +849,7 @@ cudaError_t launch_factor_fused(int64_t n, int64_t nnz_a, const int64_t *arp,
                                 double *arena_val, unsigned long long *rinfo,
                                 unsigned long long *num_ticket, DevErr *err, int scap, int mapw,
                                 int ncap, const double *v0, double *xf, DivPrep *rdiag,
-                                cudaStream_t s) {
+                                int32_t *depth, unsigned *maxdepth, cudaStream_t s) {
   ProfScope prof_scope(ILUK_PROF_FACTOR, s);
   const int warps = kNumThreads / 32;
   const size_t sym_smem = (symbolic_smem_per_warp(scap) + symbolic_map_per_warp(mapw)) * warps;
@@ -846,7 +886,8 @@ cudaError_t launch_factor_fused(int64_t n, int64_t nnz_a, const int64_t *arp,
                   (void *)&ar.top, (void *)&ar.row_off, (void *)&ar.row_len, (void *)&ar.row_ust,
                   (void *)&ar.meta, (void *)&rinfo, (void *)&ar.ticket, (void *)&num_ticket,
                   (void *)&err, (void *)&sc, (void *)&mw, (void *)&ch, (void *)&nc, (void *)&nm,
-                  (void *)&gs, (void *)&limit, (void *)&v0, (void *)&xf, (void *)&rdiag};
+                  (void *)&gs, (void *)&limit, (void *)&v0, (void *)&xf, (void *)&rdiag,
+                  (void *)&depth, (void *)&maxdepth};
   e = cudaLaunchCooperativeKernel((const void *)k_factor_fused, dim3((unsigned)grid),
                                   dim3(kNumThreads), args, smem, s);
   note_launch();
@@ -854,14 +895,15 @@ cudaError_t launch_factor_fused(int64_t n, int64_t nnz_a, const int64_t *arp,
 }
 
 cudaError_t launch_numeric(const iluk_sym *S, const double *aval, double *fval, DivPrep *rdiag,
-                           unsigned long long *ticket, DevErr *err, cudaStream_t s) {
-  return launch_numeric_impl(S, 1, aval, fval, rdiag, ticket, err, s);
+                           unsigned long long *ticket, DevErr *err, int32_t *depth,
+                           unsigned *maxdepth, cudaStream_t s) {
+  return launch_numeric_impl(S, 1, aval, fval, rdiag, ticket, err, depth, maxdepth, s);
 }
 
 cudaError_t launch_numeric_batched(const iluk_sym *S, int64_t nbatch, const double *avals,
                                    double *fvals, unsigned long long *ticket, DevErr *errs,
                                    cudaStream_t s) {
-  return launch_numeric_impl(S, nbatch, avals, fvals, nullptr, ticket, errs, s);
+  return launch_numeric_impl(S, nbatch, avals, fvals, nullptr, ticket, errs, nullptr, nullptr, s);
 }
 
 }  // namespace iluk
