@@ -167,3 +167,50 @@ def test_one_call_solve_reports_factorization_failures():
     with pytest.raises(P.IlukError) as e:
         P.solve(rp, ci, av, bd, k=2)
     assert e.value.status == L.EPATTERN
+
+
+def _forward_depth(ref):
+    """Longest chain of the forward DAG of F's lower pattern (levels from 1)."""
+    rp, ci = ref["rowptr"], ref["colind"]
+    n = len(rp) - 1
+    depth = np.zeros(n, dtype=np.int64)
+    for i in range(n):
+        lo = ci[rp[i]:rp[i + 1]]
+        lo = lo[lo < i]
+        depth[i] = 1 + (depth[lo].max() if lo.size else 0)
+    return int(depth.max())
+
+
+def _levels_built(S):
+    import ctypes as C
+    v = L.SymView()
+    L.load().iluk_sym_query(S.h, C.byref(v))
+    return v.depth_lower
+
+
+@pytest.mark.parametrize("name,make,k", [
+    ("convdiff3d_32_k1", lambda: W.conv_diff(32, 3, (50.0, 50.0, 50.0)), 1),   # 175 rows a level
+    ("convdiff3d_40_k2", lambda: W.conv_diff(40, 3, (50.0, 50.0, 50.0)), 2),   # 149 rows a level
+    ("convdiff3d_24_k2", lambda: W.conv_diff(24, 3, (50.0, 50.0, 50.0)), 2),   # 54 rows a level
+    ("band20000_k2", lambda: W.random_band(20000, 9, 400, 3), 2)],            # 3 rows a level
+    ids=["3d32_k1", "3d40_k2", "3d24_k2", "band20000_k2"])
+def test_factorization_leaves_level_orders_on_wide_dags(name, make, k):
+    """A factorization made without level orders measures the forward DAG's
+    depth and builds the level orders when the DAG is wide (n >= 128 depth),
+    as the one-call solve then needs; the results stay the oracle's."""
+    A = make()
+    rp, ci, av = to_dev(A)
+    b, bd = vec(78, A.n)
+    ref, (st, xo, it, rel, cyc) = oracle_solve(A, b, k, 30, 1e-10)
+    depth = _forward_depth(ref)
+    wide = A.n >= 128 * depth
+    S, F = P.factor(rp, ci, av, k)
+    got = _levels_built(S)
+    if wide:
+        assert got == depth, (got, depth)
+    else:
+        assert got == -1
+    assert_bits_equal(F.values(), ref["val"], f"{name}: factors")
+    x, info = P.solve(rp, ci, av, bd, k=k, restart=30, rtol=1e-10)
+    assert (info.iters, info.cycles) == (it, cyc)
+    assert_bits_equal(x, xo, f"{name}: one-call solve")
