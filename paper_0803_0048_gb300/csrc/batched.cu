@@ -55,21 +55,48 @@ struct BatchWork {
 // Fixed-shape inner product (same shape as k_dot): partial p sums i = p,
 // p + 4096, ... from +0.0; pairwise tree.  If `upd` is set, first applies
 // w_i <- w_i - h * v_i to the indices the partial owns.  Result broadcast.
+// A thread owns kDotP / NT partials and advances four of them side by side,
+// one element each per round: all loads of a round are issued before its
+// arithmetic and stores (a store to w could otherwise alias the next
+// partial's loads and serialise them), and the four chains are independent.
+// Each partial still sums its own elements in order.
 template <int NT>
 __device__ double cta_dot(int64_t n, double *w, const double *v, double h, bool upd,
                           const double *y, double *sh, bool take_sqrt) {
-  for (int k = 0; k < kDotP / NT; ++k) {
-    const int p = threadIdx.x + k * NT;
-    double s = 0.0;
-    for (int64_t i = p; i < n; i += kDotP) {
-      double wi = w[i];
-      if (upd) {
-        wi = __dsub_rn(wi, __dmul_rn(h, v[i]));
-        w[i] = wi;
+  constexpr int kPer = kDotP / NT;
+  constexpr int kG = kPer < 4 ? kPer : 4;
+  static_assert(kPer % kG == 0, "partials per thread");
+  for (int k0 = 0; k0 < kPer; k0 += kG) {
+    double s[kG];
+#pragma unroll
+    for (int g = 0; g < kG; ++g) s[g] = 0.0;
+    for (int64_t i0 = threadIdx.x + (int64_t)k0 * NT; i0 < n; i0 += kDotP) {
+      double wv[kG], vv[kG], yv[kG];
+#pragma unroll
+      for (int g = 0; g < kG; ++g) {
+        const int64_t i = i0 + (int64_t)g * NT;
+        wv[g] = vv[g] = yv[g] = 0.0;
+        if (i < n) {
+          wv[g] = w[i];
+          if (upd) vv[g] = v[i];
+          if (y != nullptr) yv[g] = y[i];
+        }
       }
-      s = __dadd_rn(s, __dmul_rn(wi, y == nullptr ? wi : y[i]));
+#pragma unroll
+      for (int g = 0; g < kG; ++g) {
+        const int64_t i = i0 + (int64_t)g * NT;
+        if (i < n) {
+          double wi = wv[g];
+          if (upd) {
+            wi = __dsub_rn(wi, __dmul_rn(h, vv[g]));
+            w[i] = wi;
+          }
+          s[g] = __dadd_rn(s[g], __dmul_rn(wi, y == nullptr ? wi : yv[g]));
+        }
+      }
     }
-    sh[p] = s;
+#pragma unroll
+    for (int g = 0; g < kG; ++g) sh[threadIdx.x + (k0 + g) * NT] = s[g];
   }
   __syncthreads();
   for (int wdt = kDotP / 2; wdt >= 1; wdt >>= 1) {
@@ -94,42 +121,110 @@ __device__ void cta_spmv(const BatchItemDev &it, const double *x, double *y, con
 }
 
 // One sweep, level by level; the 32 rows a warp takes from a level run their
-// chains in lockstep (right-aligned), forward left to right, backward right
-// to left, exactly the order of the single-instance kernels.
+// chains in lockstep, forward left to right, backward right to left, each row
+// exactly in the order of the single-instance kernels.  Nothing a row's chain
+// reads from F depends on the level before, so a warp loads its next level's
+// rows (position, right-hand side, the first kSweepPf coefficients and their
+// columns) before the barrier that ends the current level; after it, only the
+// gather of the values just computed is left.  The backward division uses the
+// reciprocal of u_ii published by the numeric phase (rdx).
+constexpr int kSweepPf = 4;
+
+struct SweepChunk {
+  int64_t first;      // position of the chain's first coefficient
+  int32_t row, len;   // row (-1: padding) and chain length
+  double s;           // right-hand side entry
+  double cv[kSweepPf];
+  int32_t ci[kSweepPf];
+};
+
+// `active` false (no chunk for this warp): an empty chunk, every field set,
+// so that nothing of an earlier chunk stays live.
+template <bool FORWARD>
+__device__ __forceinline__ void sweep_chunk_load(const BatchItemDev &it, const double *fv,
+                                                 const int32_t *order, int64_t slot, bool active,
+                                                 const double *in, SweepChunk &c) {
+  c.row = active ? order[slot] : -1;
+  c.len = 0;
+  c.first = 0;
+  c.s = 0.0;
+  if (c.row >= 0) {
+    const int64_t d = it.fdiag[c.row];
+    if (FORWARD) {
+      c.first = it.frp[c.row];
+      c.len = (int)(d - c.first);
+    } else {
+      c.first = it.frp[c.row + 1] - 1;
+      c.len = (int)(c.first - d);
+    }
+    c.s = in[c.row];
+  }
+#pragma unroll
+  for (int q = 0; q < kSweepPf; ++q) {
+    c.cv[q] = 0.0;
+    c.ci[q] = 0;
+    if (q < c.len) {
+      const int64_t pq = FORWARD ? c.first + q : c.first - q;
+      c.cv[q] = fv[pq];
+      c.ci[q] = it.fci[pq];
+    }
+  }
+}
+
+template <bool FORWARD>
+__device__ __forceinline__ void sweep_chunk_run(const BatchItemDev &it, const double *fv,
+                                                const unsigned long long *rdx,
+                                                const SweepChunk &c, double *out) {
+  const int maxlen = __reduce_max_sync(FULL_MASK, c.len);
+  double xv[kSweepPf];
+#pragma unroll
+  for (int q = 0; q < kSweepPf; ++q)
+    if (q < c.len) xv[q] = out[c.ci[q]];
+  double sacc = c.s;
+#pragma unroll
+  for (int q = 0; q < kSweepPf; ++q)
+    if (q < c.len) sacc = __dsub_rn(sacc, __dmul_rn(c.cv[q], xv[q]));
+  for (int q = kSweepPf; q < maxlen; ++q) {
+    if (q < c.len) {
+      const int64_t pq = FORWARD ? c.first + q : c.first - q;
+      sacc = __dsub_rn(sacc, __dmul_rn(fv[pq], out[it.fci[pq]]));
+    }
+  }
+  if (c.row >= 0) {
+    if (FORWARD) {
+      out[c.row] = sacc;
+    } else {
+      const int64_t d = c.first - c.len;
+      out[c.row] = div_fin(sacc, DivPrep{rdx[c.row], fv[d]});
+    }
+  }
+}
+
 template <int NT, bool FORWARD>
-__device__ void cta_sweep(const BatchItemDev &it, const double *fv, const double *in, double *out) {
+__device__ void cta_sweep(const BatchItemDev &it, const double *fv, const unsigned long long *rdx,
+                          const double *in, double *out) {
   const int32_t *order = FORWARD ? it.lord : it.uord;
   const int64_t *start = FORWARD ? it.lstart : it.ustart;
   const int nlev = FORWARD ? it.nlev_l : it.nlev_u;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  SweepChunk nx;
+  int64_t lbeg = nlev > 0 ? start[0] : 0;
+  int64_t lend = nlev > 0 ? start[1] : 0;
+  sweep_chunk_load<FORWARD>(it, fv, order, lbeg + wid * 32 + lane, lbeg + wid * 32 < lend, in,
+                            nx);
   for (int l = 0; l < nlev; ++l) {
-    for (int64_t s0 = start[l] + (int64_t)wid * 32; s0 < start[l + 1]; s0 += NT) {
-      const int64_t row = order[s0 + lane];
-      int64_t first = 0, d = 0;
-      int mylen = 0;
-      double s = 0.0;
-      if (row >= 0) {
-        d = it.fdiag[row];
-        if (FORWARD) {
-          first = it.frp[row];
-          mylen = (int)(d - first);
-        } else {
-          first = it.frp[row + 1] - 1;
-          mylen = (int)(first - d);
-        }
-        s = in[row];
-      }
-      const int maxlen = __reduce_max_sync(FULL_MASK, mylen);
-      const int off = maxlen - mylen;
-      for (int q = 0; q < maxlen; ++q) {
-        const int e = q - off;
-        if (e >= 0) {
-          const int64_t pq = FORWARD ? first + e : first - e;
-          s = __dsub_rn(s, __dmul_rn(fv[pq], out[it.fci[pq]]));
-        }
-      }
-      if (row >= 0) out[row] = FORWARD ? s : div_int(s, fv[d]);
+    const int64_t nend = l + 1 < nlev ? start[l + 2] : 0;
+    if (lbeg + wid * 32 < lend) sweep_chunk_run<FORWARD>(it, fv, rdx, nx, out);
+    for (int64_t s0 = lbeg + (int64_t)wid * 32 + NT; s0 < lend; s0 += NT) {  // wide levels
+      SweepChunk c;
+      sweep_chunk_load<FORWARD>(it, fv, order, s0 + lane, true, in, c);
+      sweep_chunk_run<FORWARD>(it, fv, rdx, c, out);
     }
+    // the next level's first chunk of this warp, before the barrier
+    sweep_chunk_load<FORWARD>(it, fv, order, lend + wid * 32 + lane, lend + wid * 32 < nend, in,
+                              nx);
+    lbeg = lend;
+    lend = nend;
     __syncthreads();
   }
 }
@@ -157,8 +252,9 @@ __device__ __forceinline__ bool spin_pending(double v) {
 }
 
 template <int NT, bool FORWARD>
-__device__ bool cta_sweep_spin(const BatchItemDev &it, const double *fv, const double *in,
-                               double *out, int64_t limit_ns) {
+__device__ bool cta_sweep_spin(const BatchItemDev &it, const double *fv,
+                               const unsigned long long *rdx, const double *in, double *out,
+                               int64_t limit_ns) {
   const int32_t *order = FORWARD ? it.lord : it.uord;
   const int64_t len = FORWARD ? it.lstart[it.nlev_l] : it.ustart[it.nlev_u];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -220,7 +316,7 @@ __device__ bool cta_sweep_spin(const BatchItemDev &it, const double *fv, const d
       break;
     }
     if (row >= 0) {
-      double y = FORWARD ? s : div_int(s, fv[d]);
+      double y = FORWARD ? s : div_fin(s, DivPrep{rdx[row], fv[d]});
       if ((unsigned long long)__double_as_longlong(y) == kSpinPending)
         y = __longlong_as_double(0x7FF8000000000000ll);  // never the marker
       st_cta_f64(&out[row], y);
@@ -231,14 +327,49 @@ __device__ bool cta_sweep_spin(const BatchItemDev &it, const double *fv, const d
 }
 
 // Numeric factorization, level by level over the forward level sets; one
-// warp per row, the row in the warp's shared slice, pivots ascending.
+// warp per row, the row in the warp's shared slice, pivots ascending (the IKJ
+// order of Eq. lufactor2).  Under the level schedule every pivot row of a
+// row is final before the row starts, so the warp first stages all of them at
+// once: for each pivot h its diagonal f_hh and the reciprocal published when
+// row h finished (rdx[h], see div_prep), and for each entry f_hj, j > h, its
+// value and the position of column j in row i (-1 when (i, j) is not in the
+// pattern).  The loads of all pivots overlap, and the pivot loop is left with
+// the multiplier (div_fin) and the row's updates, all from shared memory.
+// Rows with more pivots or pivot entries than a warp's staging area holds
+// load each pivot row in turn.  A finished row publishes the reciprocal of
+// its diagonal for the rows and backward sweeps after it.  The staging areas
+// take the inner-product partials' shared memory, idle during this phase.
 template <int NT>
-__device__ bool cta_numeric(const BatchItemDev &it, double *fv, double *svals, int32_t *scols,
-                            int cap, BatchResultDev *res) {
+struct WarpStage {
+  static constexpr int kBytes = 8 * kDotP / (NT / 32);    // one warp's share of the partials
+  static constexpr int kPiv = kBytes >= 2048 ? 32 : 16;   // pivots staged
+  static constexpr int kPairs = (kBytes - 24 * kPiv - 4 * (kPiv + 1)) / 12;  // pivot entries
+  static_assert(8 * kPairs + 24 * kPiv + 4 * kPairs + 4 * (kPiv + 1) <= kBytes, "stage size");
+  double *v;                // f_hj of the staged entries
+  unsigned long long *x;    // rdx[h]
+  double *piv;              // f_hh
+  int64_t *hd;              // position of f_hh
+  int32_t *pos;             // position of column j in the row, or -1
+  int32_t *off;             // first staged entry of each pivot, then the total
+  __device__ explicit WarpStage(double *base)
+      : v(base),
+        x(reinterpret_cast<unsigned long long *>(base + kPairs)),
+        piv(reinterpret_cast<double *>(x + kPiv)),
+        hd(reinterpret_cast<int64_t *>(piv + kPiv)),
+        pos(reinterpret_cast<int32_t *>(hd + kPiv)),
+        off(pos + kPairs) {}
+};
+
+template <int NT>
+__device__ bool cta_numeric(const BatchItemDev &it, double *fv, unsigned long long *rdx,
+                            double *svals, int32_t *scols, double *stage_base, int cap,
+                            BatchResultDev *res) {
   constexpr int kBWarps = NT / 32;
+  constexpr int kStagePiv = WarpStage<NT>::kPiv, kStagePairs = WarpStage<NT>::kPairs;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   double *rv = svals + (size_t)wid * cap;
   int32_t *rc = scols + (size_t)wid * cap;
+  const WarpStage<NT> st(stage_base + (size_t)wid * (kDotP / kBWarps));
   __shared__ int s_bad;
   __shared__ long long s_badrow;
   if (threadIdx.x == 0) {
@@ -270,25 +401,74 @@ __device__ bool cta_numeric(const BatchItemDev &it, double *fv, double *svals, i
           atomicMin(&s_badrow, (long long)row);
         }
       }
-      __syncwarp();
-      for (int q = 0; q < dp; ++q) {
-        const int h = rc[q];
+      // stage the pivots: lane q takes pivot q
+      int len = 0;
+      if (dp <= kStagePiv && lane < dp) {
+        const int h = rc[lane];
         const int64_t hd = it.fdiag[h];
-        const double fih = div_int(rv[q], fv[hd]);
+        len = (int)(it.frp[h + 1] - hd - 1);
+        st.hd[lane] = hd;
+        st.x[lane] = rdx[h];
+        st.piv[lane] = fv[hd];
+      }
+      int incl = len;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(FULL_MASK, incl, o);
+        if (lane >= o) incl += t;
+      }
+      const int total = __shfl_sync(FULL_MASK, incl, 31);
+      if (dp <= kStagePiv && total <= kStagePairs) {
+        if (lane < dp) st.off[lane] = incl - len;
+        if (lane == 0) st.off[dp] = total;
         __syncwarp();
-        if (lane == 0) rv[q] = fih;
-        __syncwarp();
-        for (int64_t r = hd + 1 + lane; r < it.frp[h + 1]; r += 32) {
+        for (int t = lane; t < total; t += 32) {
+          int q = 0;  // the pivot of entry t: the last q with off[q] <= t
+          for (int lo = 0, hi = dp; lo < hi;) {
+            const int mid = (lo + hi) >> 1;
+            if (st.off[mid] <= t) { q = mid; lo = mid + 1; } else { hi = mid; }
+          }
+          const int64_t r = st.hd[q] + 1 + (t - st.off[q]);
           const int32_t j = it.fci[r];
+          st.v[t] = fv[r];
           const int pos = lower_bound_i(rc, q + 1, m, j);
-          if (pos < m && rc[pos] == j) rv[pos] = sub_prod(rv[pos], fih, fv[r]);
+          st.pos[t] = (pos < m && rc[pos] == j) ? pos : -1;
         }
         __syncwarp();
+        for (int q = 0; q < dp; ++q) {
+          const double fih = div_fin(rv[q], DivPrep{st.x[q], st.piv[q]});
+          for (int t = st.off[q] + lane; t < st.off[q + 1]; t += 32) {
+            const int pos = st.pos[t];
+            if (pos >= 0) rv[pos] = sub_prod(rv[pos], fih, st.v[t]);
+          }
+          __syncwarp();  // every lane has read rv[q] and applied this pivot
+          if (lane == 0) rv[q] = fih;
+        }
+      } else {
+        for (int q = 0; q < dp; ++q) {
+          const int h = rc[q];
+          const int64_t hd = it.fdiag[h];
+          const double fih = div_fin(rv[q], DivPrep{rdx[h], fv[hd]});
+          __syncwarp();
+          if (lane == 0) rv[q] = fih;
+          __syncwarp();
+          for (int64_t r = hd + 1 + lane; r < it.frp[h + 1]; r += 32) {
+            const int32_t j = it.fci[r];
+            const int pos = lower_bound_i(rc, q + 1, m, j);
+            if (pos < m && rc[pos] == j) rv[pos] = sub_prod(rv[pos], fih, fv[r]);
+          }
+          __syncwarp();
+        }
       }
+      __syncwarp();
       for (int q = lane; q < m; q += 32) fv[b0 + q] = rv[q];
-      if (lane == 0 && rv[dp] == 0.0) {
-        atomicCAS(&s_bad, 0, ILUK_EZEROPIVOT);
-        atomicMin(&s_badrow, (long long)row);
+      if (lane == 0) {
+        const double d = rv[dp];
+        rdx[row] = div_prep(d).x;
+        if (d == 0.0) {
+          atomicCAS(&s_bad, 0, ILUK_EZEROPIVOT);
+          atomicMin(&s_badrow, (long long)row);
+        }
       }
       __syncwarp();
     }
@@ -303,13 +483,13 @@ __device__ bool cta_numeric(const BatchItemDev &it, double *fv, double *svals, i
 }
 
 template <int NT, bool SPIN>
-__device__ bool cta_apply(const BatchItemDev &it, const double *fv, const double *p, double *tmp,
-                          double *y, int64_t limit_ns) {
+__device__ bool cta_apply(const BatchItemDev &it, const double *fv, const unsigned long long *rdx,
+                          const double *p, double *tmp, double *y, int64_t limit_ns) {
   if (SPIN)
-    return cta_sweep_spin<NT, true>(it, fv, p, tmp, limit_ns) &&
-           cta_sweep_spin<NT, false>(it, fv, tmp, y, limit_ns);
-  cta_sweep<NT, true>(it, fv, p, tmp);
-  cta_sweep<NT, false>(it, fv, tmp, y);
+    return cta_sweep_spin<NT, true>(it, fv, rdx, p, tmp, limit_ns) &&
+           cta_sweep_spin<NT, false>(it, fv, rdx, tmp, y, limit_ns);
+  cta_sweep<NT, true>(it, fv, rdx, p, tmp);
+  cta_sweep<NT, false>(it, fv, rdx, tmp, y);
   return true;
 }
 
@@ -341,6 +521,8 @@ k_batch_solve(const BatchItemDev *items, int64_t nitems, BatchResultDev *results
   double *yv = gv + m + 1;                                       // m
   double *svals = yv + m;                                        // kBWarps * cap
   int32_t *scols = reinterpret_cast<int32_t *>(svals + (size_t)kBWarps * cap);
+  // the published reciprocals of the diagonal (div_prep), one per row
+  unsigned long long *rdx = reinterpret_cast<unsigned long long *>(work[blockIdx.x].u);
   __shared__ unsigned long long s_item;
   __shared__ int s_stop;
   const BatchWork wk = work[blockIdx.x];
@@ -361,7 +543,7 @@ k_batch_solve(const BatchItemDev *items, int64_t nitems, BatchResultDev *results
       res->cycles = 0;
       res->relres = 0.0;
     }
-    if (!cta_numeric<NT>(it, wk.fval, svals, scols, cap, res)) continue;
+    if (!cta_numeric<NT>(it, wk.fval, rdx, svals, scols, sh, cap, res)) continue;
 
     // GMRES(m): the same steps, in the same order, as gmres_solve.
     const double bnorm = cta_dot<NT>(n, const_cast<double *>(it.b), nullptr, 0.0, false, nullptr,
@@ -385,7 +567,7 @@ k_batch_solve(const BatchItemDev *items, int64_t nitems, BatchResultDev *results
       for (int j = 0; j < m; ++j) {
         double *vj = wk.V + (size_t)j * wk.ldv;
         double *zj = wk.z + (size_t)j * wk.ldv;
-        if (!cta_apply<NT, SPIN>(it, wk.fval, vj, wk.tmp, zj, limit_ns)) {
+        if (!cta_apply<NT, SPIN>(it, wk.fval, rdx, vj, wk.tmp, zj, limit_ns)) {
           if (threadIdx.x == 0) s_stop = 3;  // a bounded wait ran out
           __syncthreads();
           break;

@@ -5,6 +5,7 @@
 // Host arithmetic (Givens rotations, back substitution of the small
 // Hessenberg system) is compiled with FMA contraction off, one IEEE rounding
 // per operation, like the kernels.
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdio>
@@ -1286,6 +1287,7 @@ struct iluk_batch {
   bool spin = false;  // in-CTA sweeps polling values instead of level barriers
   double rtol = 1e-8;
   int64_t nwork = 0;  // work slots (CTAs of the widest grid)
+  std::vector<int64_t> order;  // ticket t runs item order[t]: largest items first
   void *items = nullptr, *results = nullptr, *work = nullptr;
   unsigned long long *ticket = nullptr;
   std::vector<double *> bufs;
@@ -1326,12 +1328,27 @@ int iluk_batch_create(const iluk_batch_item *items, int64_t nitems, int restart,
       delete B;
       return ILUK_EINVAL;
     }
+  }
+  // The CTAs take items in ticket order.  Handing out the largest first
+  // (longest-processing-time list scheduling) keeps a large item from
+  // starting last and running on alone; an item's cost is its FP64 work per
+  // iteration, the entries of F and A plus a few vectors.
+  B->order.resize(nitems);
+  std::vector<int64_t> cost(nitems);
+  for (int64_t i = 0; i < nitems; ++i) {
+    B->order[i] = i;
+    cost[i] = items[i].S->nnz + items[i].S->nnzA + 4 * items[i].S->n;
+  }
+  std::stable_sort(B->order.begin(), B->order.end(),
+                   [&](int64_t a, int64_t b) { return cost[a] > cost[b]; });
+  for (int64_t t = 0; t < nitems; ++t) {
+    const iluk_batch_item &it = items[B->order[t]];
     const int lst = ensure_levels(it.S, s);  // the in-CTA sweeps walk the level orders
     if (lst != ILUK_OK) {
       delete B;
       return lst;
     }
-    batch_pack_item(hitems.data() + i * batch_item_bytes(), it.S, it.a_rowptr, it.a_colind,
+    batch_pack_item(hitems.data() + t * batch_item_bytes(), it.S, it.a_rowptr, it.a_colind,
                     it.a_val, it.b, it.x);
     if (it.S->n > maxn) maxn = it.S->n;
     if (it.S->nnz > maxf) maxf = it.S->nnz;
@@ -1342,8 +1359,10 @@ int iluk_batch_create(const iluk_batch_item *items, int64_t nitems, int restart,
     delete B;
     return ILUK_ENOMEM;  // a row of F too long for the per-warp slices
   }
-  // Work slots: enough for the widest grid (up to four 256-thread CTAs per SM).
+  // Work slots: enough for the widest grid (up to four 256-thread CTAs per
+  // SM), and no more than there are items.
   B->nwork = 4 * (int64_t)num_sms();
+  if (B->nwork > nitems) B->nwork = nitems > 0 ? nitems : 1;
   const int64_t ldv = maxn;
   auto cleanup = [&]() { iluk_batch_destroy(B); };
   if (dalloc((unsigned char **)&B->items, hitems.size(), s) != cudaSuccess ||
@@ -1442,11 +1461,13 @@ int iluk_batch_results(iluk_batch *B, iluk_info *infos, void *stream) {
                      cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   int first = ILUK_OK;
+  std::vector<int64_t> slot(B->nitems);  // result slot of each item
+  for (int64_t t = 0; t < B->nitems; ++t) slot[B->order[t]] = t;
   for (int64_t i = 0; i < B->nitems; ++i) {
     int32_t st, it, cyc;
     int64_t row;
     double rel;
-    batch_unpack_result(h.data() + i * batch_result_bytes(), &st, &it, &cyc, &row, &rel);
+    batch_unpack_result(h.data() + slot[i] * batch_result_bytes(), &st, &it, &cyc, &row, &rel);
     if (infos) {
       std::memset(&infos[i], 0, sizeof(iluk_info));
       infos[i].status = st;
