@@ -492,7 +492,9 @@ int iluk_numeric_batched(const iluk_sym *S, int64_t nbatch, const double *A_vals
  *
  * iluk_batch_create: synchronous; copies the item descriptors (device
  * pointers, borrowed until iluk_batch_destroy) and allocates the workspace.
- * restart <= 64.
+ * restart <= 64.  The CTAs take the items largest first (by nnz_F + nnz_A +
+ * 4 n, ties in item order), so that no large item starts last; results are
+ * still reported per item in the caller's order.
  * iluk_batch_solve: asynchronous, no host round trip and no allocation, so it
  * can be recorded in a CUDA graph by stream capture; the first call outside a
  * capture times the CTA widths (256, 512 and 1024 threads per item) and keeps
