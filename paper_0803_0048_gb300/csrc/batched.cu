@@ -251,6 +251,41 @@ __device__ __forceinline__ bool spin_pending(double v) {
   return (unsigned long long)__double_as_longlong(v) == kSpinPending;
 }
 
+// A warp's chunk of the spinning sweep: position of its rows' chains and
+// right-hand sides, loaded while the chunk before waits for its inputs.
+struct SpinMeta {
+  int64_t first;     // position of the chain's first coefficient
+  int32_t row, len;  // row (-1: padding) and chain length
+  double s;          // right-hand side entry
+};
+
+template <bool FORWARD>
+__device__ __forceinline__ void spin_meta_load(const BatchItemDev &it, const int32_t *order,
+                                               int64_t slot, bool active, const double *in,
+                                               SpinMeta &m) {
+  m.row = active ? order[slot] : -1;
+  m.len = 0;
+  m.first = 0;
+  m.s = 0.0;
+  if (m.row >= 0) {
+    const int64_t d = it.fdiag[m.row];
+    if (FORWARD) {
+      m.first = it.frp[m.row];
+      m.len = (int)(d - m.first);
+    } else {
+      m.first = it.frp[m.row + 1] - 1;
+      m.len = (int)(m.first - d);
+    }
+    m.s = in[m.row];
+  }
+}
+
+// Per chunk: the first kSpinPf coefficients, their columns and (backward)
+// the divisor are loaded at once, and so are the next chunk's rows; then the
+// inputs are gathered together and only those still pending are polled
+// again.  Longer chains finish one coefficient at a time.
+constexpr int kSpinPf = 4;
+
 template <int NT, bool FORWARD>
 __device__ bool cta_sweep_spin(const BatchItemDev &it, const double *fv,
                                const unsigned long long *rdx, const double *in, double *out,
@@ -264,64 +299,102 @@ __device__ bool cta_sweep_spin(const BatchItemDev &it, const double *fv,
     out[i] = __longlong_as_double((long long)kSpinPending);
   __syncthreads();
   bool ok = true;
-  for (int64_t s0 = (int64_t)wid * 32; s0 < len && ok; s0 += NT) {
-    const int64_t row = order[s0 + lane];
-    int64_t first = 0, d = 0;
-    int mylen = 0;
-    double s = 0.0;
-    if (row >= 0) {
-      d = it.fdiag[row];
-      if (FORWARD) {
-        first = it.frp[row];
-        mylen = (int)(d - first);
-      } else {
-        first = it.frp[row + 1] - 1;
-        mylen = (int)(first - d);
+  SpinMeta cur;
+  spin_meta_load<FORWARD>(it, order, (int64_t)wid * 32 + lane, (int64_t)wid * 32 < len, in, cur);
+  for (int64_t s0 = (int64_t)wid * 32; s0 < len; s0 += NT) {
+    double cv[kSpinPf];
+    int32_t ci[kSpinPf];
+#pragma unroll
+    for (int q = 0; q < kSpinPf; ++q) {
+      cv[q] = 0.0;
+      ci[q] = 0;
+      if (q < cur.len) {
+        const int64_t pq = FORWARD ? cur.first + q : cur.first - q;
+        cv[q] = fv[pq];
+        ci[q] = it.fci[pq];
       }
-      s = in[row];
     }
-    const int maxlen = __reduce_max_sync(FULL_MASK, mylen);
-    const int off = maxlen - mylen;
-    for (int q = 0; q < maxlen; ++q) {
-      const int e = q - off;
-      const bool act = e >= 0;
+    unsigned long long rx = 0;
+    double diag = 0.0;
+    if (!FORWARD && cur.row >= 0) {
+      rx = rdx[cur.row];
+      diag = fv[cur.first - cur.len];
+    }
+    SpinMeta nxt;
+    spin_meta_load<FORWARD>(it, order, s0 + NT + lane, s0 + NT < len, in, nxt);
+    double xv[kSpinPf];
+    unsigned pend = 0;
+#pragma unroll
+    for (int q = 0; q < kSpinPf; ++q) {
+      xv[q] = 0.0;
+      if (q < cur.len) {
+        xv[q] = ld_cta_f64(&out[ci[q]]);
+        if (spin_pending(xv[q])) pend |= 1u << q;
+      }
+    }
+    if (__any_sync(FULL_MASK, pend != 0)) {
+      const uint64_t t0 = globaltimer_ns();
+      for (unsigned k = 0; __any_sync(FULL_MASK, pend != 0); ++k) {
+#pragma unroll
+        for (int q = 0; q < kSpinPf; ++q) {
+          if ((pend >> q) & 1u) {
+            xv[q] = ld_cta_f64(&out[ci[q]]);
+            if (!spin_pending(xv[q])) pend &= ~(1u << q);
+          }
+        }
+        const bool stop = (k & 31u) == 31u &&
+                          (*((volatile int *)&s_fail) ||
+                           (int64_t)(globaltimer_ns() - t0) > limit_ns);
+        if (__any_sync(FULL_MASK, stop)) {  // the whole warp gives up together
+          ok = false;
+          break;
+        }
+      }
+    }
+    if (!ok) break;
+    double sacc = cur.s;
+#pragma unroll
+    for (int q = 0; q < kSpinPf; ++q)
+      if (q < cur.len) sacc = __dsub_rn(sacc, __dmul_rn(cv[q], xv[q]));
+    const int maxlen = __reduce_max_sync(FULL_MASK, cur.len);
+    for (int q = kSpinPf; q < maxlen; ++q) {
+      const bool act = q < cur.len;
       int64_t pq = 0;
       double x = 0.0;
       if (act) {
-        pq = FORWARD ? first + e : first - e;
+        pq = FORWARD ? cur.first + q : cur.first - q;
         x = ld_cta_f64(&out[it.fci[pq]]);
       }
-      bool pend = act && spin_pending(x);
-      if (__any_sync(FULL_MASK, pend)) {
+      bool pq_pend = act && spin_pending(x);
+      if (__any_sync(FULL_MASK, pq_pend)) {
         const uint64_t t0 = globaltimer_ns();
-        for (unsigned k = 0; __any_sync(FULL_MASK, pend); ++k) {
-          if (pend) {
+        for (unsigned k = 0; __any_sync(FULL_MASK, pq_pend); ++k) {
+          if (pq_pend) {
             x = ld_cta_f64(&out[it.fci[pq]]);
-            pend = spin_pending(x);
+            pq_pend = spin_pending(x);
           }
           const bool stop = (k & 31u) == 31u &&
                             (*((volatile int *)&s_fail) ||
                              (int64_t)(globaltimer_ns() - t0) > limit_ns);
-          if (__any_sync(FULL_MASK, stop)) {  // the whole warp gives up together
+          if (__any_sync(FULL_MASK, stop)) {
             ok = false;
             break;
           }
         }
         if (!ok) break;
       }
-      if (act) s = __dsub_rn(s, __dmul_rn(fv[pq], x));
+      if (act) sacc = __dsub_rn(sacc, __dmul_rn(fv[pq], x));
     }
-    if (!ok) {
-      if (lane == 0) atomicExch(&s_fail, 1);
-      break;
-    }
-    if (row >= 0) {
-      double y = FORWARD ? s : div_fin(s, DivPrep{rdx[row], fv[d]});
+    if (!ok) break;
+    if (cur.row >= 0) {
+      double y = FORWARD ? sacc : div_fin(sacc, DivPrep{rx, diag});
       if ((unsigned long long)__double_as_longlong(y) == kSpinPending)
         y = __longlong_as_double(0x7FF8000000000000ll);  // never the marker
-      st_cta_f64(&out[row], y);
+      st_cta_f64(&out[cur.row], y);
     }
+    cur = nxt;
   }
+  if (!ok && lane == 0) atomicExch(&s_fail, 1);
   __syncthreads();
   return s_fail == 0;
 }
