@@ -8,7 +8,7 @@ fixed-tree inner products), item by item, so that the batched kernel is held
 to the paper's bit-compatibility promise (Sec. 1) directly and not only
 through the single-instance path.
 
-Two batch shapes:
+Three batch shapes:
 * a small batch (three value sets on one 9^3 pattern and uneven grids of side
   6, 11, 13 and 33, the last one 35,937 rows), under every in-CTA schedule
   (256/512/1024 threads per item, level-barrier or spinning sweeps) and under
@@ -16,7 +16,10 @@ Two batch shapes:
 * the full batched workload (512 value sets on one 32^3 7-point pattern plus
   64 uneven grids with sides in [16, 40]), one launch, of which a seeded
   sample of items, always including the largest grid (40^3 = 64,000 rows)
-  and the smallest, is compared with the oracle.
+  and the smallest, is compared with the oracle;
+* items of other patterns and levels of fill (k = 1..3) whose rows have more
+  pivots or pivot-row entries than the numeric phase's per-warp staging area
+  holds, beside rows that fit, under every schedule.
 """
 import numpy as np
 import pytest
@@ -156,3 +159,52 @@ def test_full_batched_workload_sampled_items_vs_oracle():
         i = vals.shape[0] + g
         check_item(grids[g].A, grids[g].b, items[i][3], res[i],
                    f"grid {g} (side {round(grids[g].A.n ** (1 / 3))})")
+
+
+def mixed_k_batch():
+    """Items whose rows have more pivots, or more pivot-row entries, than a
+    warp's staging area of the numeric phase holds at some or all CTA widths
+    (so those rows take the pivot-by-pivot path), beside rows that fit:
+    a random band matrix at k = 3 (up to 60 pivots, 2,884 pivot entries),
+    the 27-point Poisson matrix at k = 1 (31 pivots), a 7-point grid at k = 2
+    (11 pivots, 121 entries) and a random sparse matrix at k = 3 (rows of up
+    to 307 entries)."""
+    dev = torch.device("cuda")
+    cases = [(W.random_band(600, 9, 60, 21), 3), (W.poisson27(8), 1),
+             (W.conv_diff(10, 3, (20.0, 20.0, 20.0)), 2), (W.random_sparse(400, 0.02, 9), 3)]
+    items, host = [], []
+    for A, k in cases:
+        b = W.uniform(W.stream_key(77, f"mixed.rhs.{A.n}"), np.arange(A.n), -1.0, 1.0)
+        r = torch.from_numpy(A.rowptr).to(dev)
+        c = torch.from_numpy(A.colind).to(dev)
+        items.append((P.symbolic(r, c, k), torch.from_numpy(A.val).to(dev),
+                      torch.from_numpy(b).to(dev), torch.empty(A.n, dtype=torch.float64, device=dev)))
+        host.append((A, b, k))
+    return items, host
+
+
+@pytest.fixture(scope="module")
+def mixed():
+    items, host = mixed_k_batch()
+    ref = [oracle_solve(A, b, k=k) for A, b, k in host]
+    return items, host, ref
+
+
+@pytest.mark.parametrize("sched", [(256, False), (256, True), (512, False), (512, True),
+                                   (1024, False), (1024, True)],
+                         ids=["256-level", "256-spin", "512-level", "512-spin", "1024-level",
+                              "1024-spin"])
+def test_batched_long_rows_bit_exact_vs_oracle(mixed, sched):
+    items, host, ref = mixed
+    for _, _, _, x in items:
+        x.fill_(float("nan"))
+    B = P.BatchSolve(items, restart=RESTART, rtol=RTOL)
+    B.set_schedule(*sched)
+    B.solve()
+    res = B.results()
+    for i, ((_, _, _, x), (A, b, k), r, (st, xo, it, rel, cyc)) in enumerate(
+            zip(items, host, res, ref)):
+        assert st == 0 and r.status == 0, (i, r.status, st)
+        assert (r.iters, r.cycles) == (it, cyc), (i, r.iters, it)
+        assert bits([r.relres])[0] == bits([rel])[0], (i, r.relres, rel)
+        assert_bits_equal(x, xo, f"item {i} (n={A.n}, k={k}) x")
