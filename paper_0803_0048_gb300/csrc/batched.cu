@@ -433,12 +433,219 @@ struct WarpStage {
         off(pos + kPairs) {}
 };
 
+__device__ __forceinline__ void numeric_report(int *s_bad, long long *s_badrow, int code,
+                                               int64_t row) {
+  atomicCAS(s_bad, 0, code);
+  atomicMin(s_badrow, (long long)row);
+}
+
+// One row by the whole warp.
+template <int NT>
+__device__ __forceinline__ void numeric_row_warp(const BatchItemDev &it, double *fv,
+                                                 unsigned long long *rdx, double *rv, int32_t *rc,
+                                                 const WarpStage<NT> &st, int64_t row, int lane,
+                                                 int *s_bad, long long *s_badrow) {
+  constexpr int kStagePiv = WarpStage<NT>::kPiv, kStagePairs = WarpStage<NT>::kPairs;
+  const int64_t b0 = it.frp[row];
+  const int m = (int)(it.frp[row + 1] - b0);
+  const int dp = (int)(it.fdiag[row] - b0);
+  for (int q = lane; q < m; q += 32) {
+    rc[q] = it.fci[b0 + q];
+    rv[q] = 0.0;
+  }
+  __syncwarp();
+  bool bad = false;
+  for (int64_t p = it.farp[row] + lane; p < it.farp[row + 1]; p += 32) {
+    const double a = it.aval[p];
+    if (!isfinite(a)) bad = true;
+    rv[it.a2f[p]] = a;
+  }
+  if (__any_sync(FULL_MASK, bad) && lane == 0) numeric_report(s_bad, s_badrow, ILUK_ENONFINITE, row);
+  // stage the pivots: lane q takes pivot q
+  int len = 0;
+  if (dp <= kStagePiv && lane < dp) {
+    const int h = rc[lane];
+    const int64_t hd = it.fdiag[h];
+    len = (int)(it.frp[h + 1] - hd - 1);
+    st.hd[lane] = hd;
+    st.x[lane] = rdx[h];
+    st.piv[lane] = fv[hd];
+  }
+  int incl = len;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(FULL_MASK, incl, o);
+    if (lane >= o) incl += t;
+  }
+  const int total = __shfl_sync(FULL_MASK, incl, 31);
+  if (dp <= kStagePiv && total <= kStagePairs) {
+    if (lane < dp) st.off[lane] = incl - len;
+    if (lane == 0) st.off[dp] = total;
+    __syncwarp();
+    for (int t = lane; t < total; t += 32) {
+      int q = 0;  // the pivot of entry t: the last q with off[q] <= t
+      for (int lo = 0, hi = dp; lo < hi;) {
+        const int mid = (lo + hi) >> 1;
+        if (st.off[mid] <= t) { q = mid; lo = mid + 1; } else { hi = mid; }
+      }
+      const int64_t r = st.hd[q] + 1 + (t - st.off[q]);
+      const int32_t j = it.fci[r];
+      st.v[t] = fv[r];
+      const int pos = lower_bound_i(rc, q + 1, m, j);
+      st.pos[t] = (pos < m && rc[pos] == j) ? pos : -1;
+    }
+    __syncwarp();
+    for (int q = 0; q < dp; ++q) {
+      const double fih = div_fin(rv[q], DivPrep{st.x[q], st.piv[q]});
+      for (int t = st.off[q] + lane; t < st.off[q + 1]; t += 32) {
+        const int pos = st.pos[t];
+        if (pos >= 0) rv[pos] = sub_prod(rv[pos], fih, st.v[t]);
+      }
+      __syncwarp();  // every lane has read rv[q] and applied this pivot
+      if (lane == 0) rv[q] = fih;
+    }
+  } else {
+    for (int q = 0; q < dp; ++q) {
+      const int h = rc[q];
+      const int64_t hd = it.fdiag[h];
+      const double fih = div_fin(rv[q], DivPrep{rdx[h], fv[hd]});
+      __syncwarp();
+      if (lane == 0) rv[q] = fih;
+      __syncwarp();
+      for (int64_t r = hd + 1 + lane; r < it.frp[h + 1]; r += 32) {
+        const int32_t j = it.fci[r];
+        const int pos = lower_bound_i(rc, q + 1, m, j);
+        if (pos < m && rc[pos] == j) rv[pos] = sub_prod(rv[pos], fih, fv[r]);
+      }
+      __syncwarp();
+    }
+  }
+  __syncwarp();
+  for (int q = lane; q < m; q += 32) fv[b0 + q] = rv[q];
+  if (lane == 0) {
+    const double d = rv[dp];
+    rdx[row] = div_prep(d).x;
+    if (d == 0.0) numeric_report(s_bad, s_badrow, ILUK_EZEROPIVOT, row);
+  }
+  __syncwarp();
+}
+
+// Two rows of a level side by side, one per half-warp (lanes 0-15 take rowA,
+// 16-31 rowB; -1: none), each with half of the warp's row slice and staging
+// area: the two rows' load and division latencies overlap, and one FP64
+// instruction applies both rows' updates.  Each row keeps the whole-warp
+// path's order of operations.  Returns false, having changed nothing the
+// whole-warp path relies on, when a row has more than 16 entries or does not
+// fit half a staging area.
+template <int NT>
+__device__ __forceinline__ bool numeric_rows_half(const BatchItemDev &it, double *fv,
+                                                  unsigned long long *rdx, double *rv_w,
+                                                  int32_t *rc_w, const WarpStage<NT> &st,
+                                                  int64_t rowA, int64_t rowB, int lane,
+                                                  int *s_bad, long long *s_badrow) {
+  constexpr int kHalfPiv = WarpStage<NT>::kPiv / 2;     // staged pivots per half, plus one offset
+  constexpr int kHalfPairs = WarpStage<NT>::kPairs / 2;  // staged entries per half
+  const int half = lane >> 4, hl = lane & 15;
+  const int64_t row = half ? rowB : rowA;
+  int64_t b0 = 0;
+  int m = 0, dp = 0;
+  if (row >= 0) {
+    b0 = it.frp[row];
+    m = (int)(it.frp[row + 1] - b0);
+    dp = (int)(it.fdiag[row] - b0);
+  }
+  if (!__all_sync(FULL_MASK, m <= 16 && dp < kHalfPiv)) return false;
+  double *rv = rv_w + half * 16;
+  int32_t *rc = rc_w + half * 16;
+  double *sv = st.v + half * kHalfPairs;
+  int32_t *spos = st.pos + half * kHalfPairs;
+  unsigned long long *sx = st.x + half * kHalfPiv;
+  double *spiv = st.piv + half * kHalfPiv;
+  int64_t *shd = st.hd + half * kHalfPiv;
+  int32_t *soff = st.off + half * kHalfPiv;
+  if (hl < m) {
+    rc[hl] = it.fci[b0 + hl];
+    rv[hl] = 0.0;
+  }
+  __syncwarp();
+  bool bad = false;
+  if (row >= 0) {
+    for (int64_t p = it.farp[row] + hl; p < it.farp[row + 1]; p += 16) {
+      const double a = it.aval[p];
+      if (!isfinite(a)) bad = true;
+      rv[it.a2f[p]] = a;
+    }
+  }
+  const unsigned badm = __ballot_sync(FULL_MASK, bad);
+  if (hl == 0 && ((badm >> (16 * half)) & 0xffffu))
+    numeric_report(s_bad, s_badrow, ILUK_ENONFINITE, row);
+  int len = 0;
+  if (hl < dp) {
+    const int h = rc[hl];
+    const int64_t hd = it.fdiag[h];
+    len = (int)(it.frp[h + 1] - hd - 1);
+    shd[hl] = hd;
+    sx[hl] = rdx[h];
+    spiv[hl] = fv[hd];
+  }
+  int incl = len;
+#pragma unroll
+  for (int o = 1; o < 16; o <<= 1) {
+    const int t = __shfl_up_sync(FULL_MASK, incl, o, 16);
+    if (hl >= o) incl += t;
+  }
+  const int total = __shfl_sync(FULL_MASK, incl, 15, 16);
+  if (!__all_sync(FULL_MASK, total <= kHalfPairs)) {
+    __syncwarp();
+    return false;
+  }
+  if (hl < dp) soff[hl] = incl - len;
+  if (hl == 0) soff[dp] = total;
+  __syncwarp();
+  for (int t = hl; t < total; t += 16) {
+    int q = 0;  // the pivot of entry t: the last q with off[q] <= t
+    for (int lo = 0, hi = dp; lo < hi;) {
+      const int mid = (lo + hi) >> 1;
+      if (soff[mid] <= t) { q = mid; lo = mid + 1; } else { hi = mid; }
+    }
+    const int64_t r = shd[q] + 1 + (t - soff[q]);
+    const int32_t j = it.fci[r];
+    sv[t] = fv[r];
+    const int pos = lower_bound_i(rc, q + 1, m, j);
+    spos[t] = (pos < m && rc[pos] == j) ? pos : -1;
+  }
+  __syncwarp();
+  const int dmax = __reduce_max_sync(FULL_MASK, dp);
+  for (int q = 0; q < dmax; ++q) {
+    double fih = 0.0;
+    if (q < dp) {
+      fih = div_fin(rv[q], DivPrep{sx[q], spiv[q]});
+      for (int t = soff[q] + hl; t < soff[q + 1]; t += 16) {
+        const int pos = spos[t];
+        if (pos >= 0) rv[pos] = sub_prod(rv[pos], fih, sv[t]);
+      }
+    }
+    __syncwarp();  // every lane has read rv[q] and applied this pivot
+    if (q < dp && hl == 0) rv[q] = fih;
+  }
+  __syncwarp();
+  if (hl < m) fv[b0 + hl] = rv[hl];
+  if (hl == 0 && row >= 0) {
+    const double d = rv[dp];
+    rdx[row] = div_prep(d).x;
+    if (d == 0.0) numeric_report(s_bad, s_badrow, ILUK_EZEROPIVOT, row);
+  }
+  __syncwarp();
+  return true;
+}
+
 template <int NT>
 __device__ bool cta_numeric(const BatchItemDev &it, double *fv, unsigned long long *rdx,
                             double *svals, int32_t *scols, double *stage_base, int cap,
                             BatchResultDev *res) {
   constexpr int kBWarps = NT / 32;
-  constexpr int kStagePiv = WarpStage<NT>::kPiv, kStagePairs = WarpStage<NT>::kPairs;
+  // half-warp pairs where half a staging area holds a 7-point ILU(1) row
+  constexpr bool kPairs = WarpStage<NT>::kPairs / 2 >= 40;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   double *rv = svals + (size_t)wid * cap;
   int32_t *rc = scols + (size_t)wid * cap;
@@ -451,99 +658,22 @@ __device__ bool cta_numeric(const BatchItemDev &it, double *fv, unsigned long lo
   }
   __syncthreads();
   for (int l = 0; l < it.nlev_l; ++l) {
-    for (int64_t slot = it.lstart[l] + wid; slot < it.lstart[l + 1]; slot += kBWarps) {
-      const int64_t row = it.lord[slot];
-      if (row < 0) continue;
-      const int64_t b0 = it.frp[row];
-      const int m = (int)(it.frp[row + 1] - b0);
-      const int dp = (int)(it.fdiag[row] - b0);
-      for (int q = lane; q < m; q += 32) {
-        rc[q] = it.fci[b0 + q];
-        rv[q] = 0.0;
-      }
-      __syncwarp();
-      bool bad = false;
-      for (int64_t p = it.farp[row] + lane; p < it.farp[row + 1]; p += 32) {
-        const double a = it.aval[p];
-        if (!isfinite(a)) bad = true;
-        rv[it.a2f[p]] = a;
-      }
-      if (__any_sync(FULL_MASK, bad)) {
-        if (lane == 0) {
-          atomicCAS(&s_bad, 0, ILUK_ENONFINITE);
-          atomicMin(&s_badrow, (long long)row);
+    const int64_t lb = it.lstart[l], le = it.lstart[l + 1];
+    if (kPairs) {
+      for (int64_t sp = lb + 2 * wid; sp < le; sp += 2 * kBWarps) {
+        const int64_t rowA = it.lord[sp];
+        const int64_t rowB = sp + 1 < le ? it.lord[sp + 1] : -1;
+        if (!numeric_rows_half<NT>(it, fv, rdx, rv, rc, st, rowA, rowB, lane, &s_bad,
+                                   &s_badrow)) {
+          if (rowA >= 0) numeric_row_warp<NT>(it, fv, rdx, rv, rc, st, rowA, lane, &s_bad, &s_badrow);
+          if (rowB >= 0) numeric_row_warp<NT>(it, fv, rdx, rv, rc, st, rowB, lane, &s_bad, &s_badrow);
         }
       }
-      // stage the pivots: lane q takes pivot q
-      int len = 0;
-      if (dp <= kStagePiv && lane < dp) {
-        const int h = rc[lane];
-        const int64_t hd = it.fdiag[h];
-        len = (int)(it.frp[h + 1] - hd - 1);
-        st.hd[lane] = hd;
-        st.x[lane] = rdx[h];
-        st.piv[lane] = fv[hd];
+    } else {
+      for (int64_t slot = lb + wid; slot < le; slot += kBWarps) {
+        const int64_t row = it.lord[slot];
+        if (row >= 0) numeric_row_warp<NT>(it, fv, rdx, rv, rc, st, row, lane, &s_bad, &s_badrow);
       }
-      int incl = len;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int t = __shfl_up_sync(FULL_MASK, incl, o);
-        if (lane >= o) incl += t;
-      }
-      const int total = __shfl_sync(FULL_MASK, incl, 31);
-      if (dp <= kStagePiv && total <= kStagePairs) {
-        if (lane < dp) st.off[lane] = incl - len;
-        if (lane == 0) st.off[dp] = total;
-        __syncwarp();
-        for (int t = lane; t < total; t += 32) {
-          int q = 0;  // the pivot of entry t: the last q with off[q] <= t
-          for (int lo = 0, hi = dp; lo < hi;) {
-            const int mid = (lo + hi) >> 1;
-            if (st.off[mid] <= t) { q = mid; lo = mid + 1; } else { hi = mid; }
-          }
-          const int64_t r = st.hd[q] + 1 + (t - st.off[q]);
-          const int32_t j = it.fci[r];
-          st.v[t] = fv[r];
-          const int pos = lower_bound_i(rc, q + 1, m, j);
-          st.pos[t] = (pos < m && rc[pos] == j) ? pos : -1;
-        }
-        __syncwarp();
-        for (int q = 0; q < dp; ++q) {
-          const double fih = div_fin(rv[q], DivPrep{st.x[q], st.piv[q]});
-          for (int t = st.off[q] + lane; t < st.off[q + 1]; t += 32) {
-            const int pos = st.pos[t];
-            if (pos >= 0) rv[pos] = sub_prod(rv[pos], fih, st.v[t]);
-          }
-          __syncwarp();  // every lane has read rv[q] and applied this pivot
-          if (lane == 0) rv[q] = fih;
-        }
-      } else {
-        for (int q = 0; q < dp; ++q) {
-          const int h = rc[q];
-          const int64_t hd = it.fdiag[h];
-          const double fih = div_fin(rv[q], DivPrep{rdx[h], fv[hd]});
-          __syncwarp();
-          if (lane == 0) rv[q] = fih;
-          __syncwarp();
-          for (int64_t r = hd + 1 + lane; r < it.frp[h + 1]; r += 32) {
-            const int32_t j = it.fci[r];
-            const int pos = lower_bound_i(rc, q + 1, m, j);
-            if (pos < m && rc[pos] == j) rv[pos] = sub_prod(rv[pos], fih, fv[r]);
-          }
-          __syncwarp();
-        }
-      }
-      __syncwarp();
-      for (int q = lane; q < m; q += 32) fv[b0 + q] = rv[q];
-      if (lane == 0) {
-        const double d = rv[dp];
-        rdx[row] = div_prep(d).x;
-        if (d == 0.0) {
-          atomicCAS(&s_bad, 0, ILUK_EZEROPIVOT);
-          atomicMin(&s_badrow, (long long)row);
-        }
-      }
-      __syncwarp();
     }
     __syncthreads();
   }
