@@ -284,7 +284,7 @@ __device__ __forceinline__ void spin_meta_load(const BatchItemDev &it, const int
 // the divisor are loaded at once, and so are the next chunk's rows; then the
 // inputs are gathered together and only those still pending are polled
 // again.  Longer chains finish one coefficient at a time.
-constexpr int kSpinPf = 4;
+constexpr int kSpinPf = 6;
 
 template <int NT, bool FORWARD>
 __device__ bool cta_sweep_spin(const BatchItemDev &it, const double *fv,
