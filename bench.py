@@ -588,8 +588,9 @@ def adjoint(args):
     Two arms of the plain single-instance path on the same GPU, both timed:
     * plain gradient: the same gradient by plain calls without factor reuse --
       numeric ILU(2) of A, GMRES for x, then the explicit A^T (iluk_transpose),
-      its own numeric ILU(2) (its symbolic phase cached outside the timing,
-      the most favourable case for the plain path), GMRES for lambda, the
+      its own numeric ILU(2) (its symbolic phase, and with it the sweep
+      schedule tuned on the pattern, kept from an untimed first call: the
+      most favourable case for the plain path), GMRES for lambda, the
       -lambda_i x_j scatter and autograd through the assembly;
     * finite-difference loop: central differences need 2 n_theta plain
       solves (numeric + GMRES); a sample of them is timed and the loop's time
@@ -703,8 +704,8 @@ def adjoint(args):
            "adjoint_iters": solver.last_backward.iters if solver.last_backward else None,
            "plain_gradient": {"ms": round(ms_plain, 3), "measured": True,
                               "what": "numeric ILU(2) of A + GMRES, explicit A^T + its own "
-                                      "numeric ILU(2) (symbolic cached) + GMRES, scatter, "
-                                      "autograd through the assembly",
+                                      "numeric ILU(2) (symbolic phase and sweep schedule "
+                                      "kept) + GMRES, scatter, autograd through the assembly",
                               "iters_forward_adjoint": list(plain_info.get("iters", ())),
                               "rel_diff_dtheta": rel_theta, "rel_diff_lambda": rel_lam},
            "speedup_vs_plain_gradient": round(ms_plain / ms_fb, 3),

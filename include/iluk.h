@@ -113,7 +113,9 @@ enum { ILUK_PREC_NONE = 0, ILUK_PREC_ILU = 1, ILUK_PREC_IILU = 2 };
 /* Sweep schedules (all give bit-identical results): rows of a level in
  * lockstep warps over all SMs (FLAGS), on one SM (SINGLE_CTA) or on one
  * thread-block cluster (CLUSTER); one warp per row over all SMs (WARP_GRID)
- * or on one cluster (WARP_CLUSTER).  AUTO times them and keeps the fastest.
+ * or on one cluster (WARP_CLUSTER).  AUTO times them and keeps the fastest;
+ * the pick is remembered by the symbolic handle, and later factorizations of
+ * the same pattern use it without timing again.
  * A schedule byte holds the kind in bits 0-3 and, for the warp-per-row
  * kinds, the threads per CTA / 128 in bits 4-7 (0: 1024 threads; for
  * WARP_GRID a non-zero width also means one CTA per SM), which bounds how
@@ -263,11 +265,15 @@ int iluk_apply(iluk_fac *F, const double *p, double *y, int transpose, void *str
 int iluk_apply_sched(iluk_fac *F, const double *p, double *y, int transpose, int sched,
                      void *stream);
 /* Fix the sweep schedule of F: one schedule byte for both sweeps, or
- * forward | backward << 8.  ILUK_SCHED_AUTO (the default) lets the first
- * application outside a stream capture time every schedule (and, for the
- * warp-per-row kinds, several CTA widths) on each sweep and keep the fastest
- * (iluk_get_schedule then returns the packed pair).  An unknown kind or width
- * falls back to WARP_GRID or 1024 threads. */
+ * forward | backward << 8; it applies to the sweeps of F and of its
+ * transpose.  ILUK_SCHED_AUTO (the default) lets the first application
+ * outside a stream capture time every schedule (and, for the warp-per-row
+ * kinds, several CTA widths) on each sweep and keep the fastest
+ * (iluk_get_schedule then returns the packed pair); the transposed sweeps are
+ * timed on their first use and keep their own pair.  Both picks are
+ * remembered by the symbolic handle: later factorizations of the same
+ * pattern use them without timing again.  An unknown kind or width is
+ * refused (ILUK_EINVAL). */
 int iluk_set_schedule(iluk_fac *F, int sched);
 int iluk_get_schedule(const iluk_fac *F);
 

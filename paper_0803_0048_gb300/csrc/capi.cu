@@ -947,10 +947,20 @@ static const SweepAux *sweep_aux(iluk_fac *F, int sched, cudaStream_t s) {
 
 // Autotuner: time every sweep schedule (the warp-per-row ones at several CTA
 // widths) on this factorization, forward and backward sweeps separately, and
-// keep the fastest of each (packed as forward | backward << 8).  Skipped
-// while the stream is being captured.
-static int pick_schedule(iluk_fac *F, cudaStream_t s) {
-  if (F->sched != ILUK_SCHED_AUTO) return F->sched;
+// keep the fastest of each (packed as forward | backward << 8); the sweeps of
+// the transpose (U^T then L^T, a different DAG) get their own pick, made the
+// first time they run (the transpose must exist).  The sweeps' speed depends
+// on the pattern, not on the values, so each pick is kept with the symbolic
+// handle and a later factorization of the same pattern starts from it instead
+// of timing again.  Skipped while the stream is being captured.
+static int pick_schedule(iluk_fac *F, cudaStream_t s, bool transpose = false) {
+  int &cur = transpose ? F->tsched : F->sched;
+  int &hint = transpose ? F->S->tsched_hint : F->S->sched_hint;
+  if (cur != ILUK_SCHED_AUTO) return cur;
+  if (hint != ILUK_SCHED_AUTO) {
+    cur = hint;
+    return cur;
+  }
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   cudaStreamIsCapturing(s, &cs);
   if (cs != cudaStreamCaptureStatusNone) return ILUK_SCHED_WARP_GRID;
@@ -998,11 +1008,17 @@ static int pick_schedule(iluk_fac *F, cudaStream_t s) {
       LevelOrder none;
       cudaEventRecord(e0, s);
       const SweepAux *aux = sweep_aux(F, sched, s);
-      const cudaError_t ef = launch_apply(S->n, S->rowptr, S->colind, S->diag, F->val, F->rdiag,
-                                          sweep_fwd(S), none, p, t, y, 0, sched, F->err, aux, s);
+      const cudaError_t ef =
+          transpose ? launch_apply(S->n, F->trowptr, F->tcolind, F->tdiag, F->tval, F->rdiag,
+                                   F->tlord, none, p, t, y, 1, sched, F->err, aux, s)
+                    : launch_apply(S->n, S->rowptr, S->colind, S->diag, F->val, F->rdiag,
+                                   sweep_fwd(S), none, p, t, y, 0, sched, F->err, aux, s);
       cudaEventRecord(e1, s);
-      const cudaError_t eb = launch_apply(S->n, S->rowptr, S->colind, S->diag, F->val, F->rdiag,
-                                          none, sweep_bwd(S), p, t, y, 0, sched, F->err, aux, s);
+      const cudaError_t eb =
+          transpose ? launch_apply(S->n, F->trowptr, F->tcolind, F->tdiag, F->tval, F->rdiag,
+                                   none, F->tuord, p, t, y, 1, sched, F->err, aux, s)
+                    : launch_apply(S->n, S->rowptr, S->colind, S->diag, F->val, F->rdiag, none,
+                                   sweep_bwd(S), p, t, y, 0, sched, F->err, aux, s);
       cudaEventRecord(e2, s);
       cudaEventSynchronize(e2);
       float a = 0, b = 0;
@@ -1035,8 +1051,9 @@ static int pick_schedule(iluk_fac *F, cudaStream_t s) {
   dfree(p, s);
   dfree(y, s);
   dfree(t, s);
-  F->sched = pick_f | (pick_b << 8);
-  return F->sched;
+  cur = pick_f | (pick_b << 8);
+  hint = cur;
+  return cur;
 }
 
 // The lockstep kinds (flags, single CTA, cluster) walk the padded level
@@ -1059,14 +1076,16 @@ int iluk_apply_sched(iluk_fac *F, const double *p, double *y, int transpose, int
   if (!F || (!p && F->S->n) || (!y && F->S->n)) return ILUK_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   const iluk_sym *S = F->S;
-  if (sched == ILUK_SCHED_AUTO) sched = pick_schedule(F, s);
+  if (transpose) {
+    int st = ensure_transpose(F, s);
+    if (st != ILUK_OK) return st;
+  }
+  if (sched == ILUK_SCHED_AUTO) sched = pick_schedule(F, s, transpose != 0);
   if (!transpose) {
     const int st = orders_for(F, sched, s);
     if (st != ILUK_OK) return st;
   }
   if (transpose) {
-    int st = ensure_transpose(F, s);
-    if (st != ILUK_OK) return st;
     CK(launch_apply(S->n, F->trowptr, F->tcolind, F->tdiag, F->tval, F->rdiag, F->tlord,
                     F->tuord, p, F->tmp, y, 1, sched, F->err, sweep_aux(F, sched, s), s));
   } else {
@@ -1101,6 +1120,7 @@ extern "C" {
 int iluk_set_schedule(iluk_fac *F, int sched) {
   if (!F || !sched_valid(sched)) return ILUK_EINVAL;
   F->sched = sched;
+  F->tsched = sched;
   return ILUK_OK;
 }
 
@@ -1577,7 +1597,7 @@ static int gmres_impl(const iluk_pattern *A, const double *A_val, int prec_kind,
     int st = ensure_transpose(F, s);
     if (st != ILUK_OK) return fail(info, st);
   }
-  int sched = F ? pick_schedule(F, s) : 0;
+  int sched = F ? pick_schedule(F, s, transpose != 0) : 0;
   if (F && !transpose) {
     const int st = orders_for(F, sched, s);
     if (st != ILUK_OK) return fail(info, st);

@@ -45,6 +45,10 @@ struct iluk_sym {
   LevelOrder lord, uord;       // forward / backward sweep level orders
   bool levels_built = false;   // lord/uord are built by the first numeric phase
   LevelOrder xlord, xuord;     // index orders (iluk_factor), for the sweeps until lord/uord exist
+  // the sweep schedules the autotuner picked for a factorization of this
+  // pattern, for the sweeps of F and of its transpose (0: none yet); later
+  // factorizations of the pattern start from them
+  mutable int sched_hint = 0, tsched_hint = 0;
 };
 
 // The orders the sweeps of S walk: the level orders once built, else the
@@ -81,6 +85,7 @@ struct iluk_fac {
   double *tval = nullptr;
   LevelOrder tlord, tuord;        // level orders of the transposed sweeps
   int sched = 0;                  // schedule picked for the sweeps (ILUK_SCHED_*)
+  int tsched = 0;                 // and for the transposed sweeps
   iluk::SweepAux aux;             // helped sweeps' scratch, made on first use
 };
 

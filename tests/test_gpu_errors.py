@@ -14,7 +14,7 @@ import paper_0803_0048_gb300 as P
 from paper_0803_0048_gb300 import _lib as L
 from paper_0803_0048_gb300 import workloads as W
 
-from gpu_helpers import to_dev
+from gpu_helpers import assert_bits_equal, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -121,6 +121,56 @@ def test_gmres_reports_nonconvergence():
     b = torch.ones(A.n, dtype=torch.float64, device="cuda")
     x, info = P.gmres(rp, ci, av, b, None, restart=5, rtol=1e-12, maxit=12, check=False)
     assert info.status == L.ENOCONV and info.iters == 12
+
+
+def test_tuned_schedule_kept_by_the_pattern():
+    """The first GMRES on a factorization times the sweep schedules; a later
+    factorization of the same pattern (new values) starts from that pick and
+    times nothing, and its results are those of the oracle either way."""
+    A = W.random_band(3000, 9, 100, 17)
+    rp, ci, av = to_dev(A)
+    S = P.symbolic(rp, ci, 2)
+    b = torch.ones(A.n, dtype=torch.float64, device="cuda")
+    F1 = P.numeric(S, av)
+    c0 = P.launch_count()
+    x1, i1 = P.gmres(rp, ci, av, b, F1, restart=20, rtol=1e-10)
+    tuned_launches = P.launch_count() - c0
+    s1 = F1.schedule()
+    assert s1 != L.SCHED_AUTO
+    av2 = av * 1.5  # other values, same pattern
+    F2 = P.numeric(S, av2)
+    assert F2.schedule() == L.SCHED_AUTO  # nothing fixed on the new factors yet
+    c0 = P.launch_count()
+    x2, i2 = P.gmres(rp, ci, av2, b, F2, restart=20, rtol=1e-10)
+    launches = P.launch_count() - c0
+    assert F2.schedule() == s1
+    # the timing runs (13 kinds/widths, 3 runs of 2 sweeps each) are gone
+    assert tuned_launches - launches >= 40, (tuned_launches, launches)
+    A2 = W.CSR(A.n, A.rowptr, A.colind, A.val * 1.5)
+    ref = oracle.factor(A2, 2)
+    st, xo, it, rel, cyc = oracle.gmres(A2.n, A2.rowptr, A2.colind, A2.val, np.ones(A.n),
+                                        oracle.PREC_ILU, (ref["rowptr"], ref["colind"], ref["val"]),
+                                        20, 1e-10, dotmode=oracle.DOT_TREE)
+    assert i2.iters == it
+    assert_bits_equal(x2, xo, "second factorization's solve")
+    # the transposed sweeps (A^T lambda = g) are timed on their own, once
+    c0 = P.launch_count()
+    P.gmres(rp, ci, av2, b, F2, restart=20, rtol=1e-10, transpose=True)
+    tuned_t = P.launch_count() - c0
+    F3 = P.numeric(S, av)
+    P.gmres(rp, ci, av, b, F3, restart=20, rtol=1e-10)  # schedule from the pattern
+    c0 = P.launch_count()
+    lam, it3 = P.gmres(rp, ci, av, b, F3, restart=20, rtol=1e-10, transpose=True)
+    assert tuned_t - (P.launch_count() - c0) >= 40
+    r1 = oracle.factor(A, 2)
+    x1o = oracle.gmres(A.n, A.rowptr, A.colind, A.val, np.ones(A.n), oracle.PREC_ILU,
+                       (r1["rowptr"], r1["colind"], r1["val"]), 20, 1e-10,
+                       dotmode=oracle.DOT_TREE)[1]
+    st, lo, _, itt, _ = oracle.adjoint(A.n, A.rowptr, A.colind, A.val, r1["rowptr"],
+                                       r1["colind"], r1["val"], x1o, np.ones(A.n), 20, 1e-10,
+                                       dotmode=oracle.DOT_TREE)
+    assert st == oracle.OK and it3.iters == itt
+    assert_bits_equal(lam, lo, "transposed solve with the pattern's schedule")
 
 
 def test_schedule_values_checked():
