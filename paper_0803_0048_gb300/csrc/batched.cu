@@ -46,7 +46,9 @@ struct BatchResultDev {
 };
 
 struct BatchWork {
-  double *fval, *V, *w, *z, *u, *tmp;  // z: the m preconditioned basis vectors of a cycle
+  // z: the m preconditioned basis vectors of a cycle; u: the reciprocals of
+  // the diagonal the numeric phase publishes (div_prep, one 64-bit word a row)
+  double *fval, *V, *w, *z, *u, *tmp;
   int64_t ldv;  // stride between basis vectors
 };
 
