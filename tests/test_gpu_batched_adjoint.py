@@ -14,6 +14,7 @@ import torch
 
 import oracle
 import paper_0803_0048_gb300 as P
+from paper_0803_0048_gb300 import _lib as L
 from paper_0803_0048_gb300 import workloads as W
 
 from gpu_helpers import assert_bits_equal, bits
@@ -101,15 +102,29 @@ def test_batched_solve_graph_capture_and_replay():
         assert_bits_equal(x, xs, "replayed x")
 
 
-def test_batched_solve_reports_zero_pivot_per_item():
+@pytest.mark.parametrize("sched", [None, (256, False), (256, True), (512, False), (512, True),
+                                   (1024, False), (1024, True)],
+                         ids=["auto", "256-level", "256-spin", "512-level", "512-spin",
+                              "1024-level", "1024-spin"])
+def test_batched_solve_reports_factorization_errors_per_item(sched):
+    """A zero pivot and a non-finite value of A, each in its own item, are
+    reported for that item with the row (the smallest offending one), under
+    every schedule (rows factored by half-warp pairs and by whole warps); the
+    other items solve as usual."""
     items, host = build_batch()
-    S, vals, b, x = items[2]
-    vals.zero_()  # all-zero matrix: zero pivot at row 0
+    items[2][1].zero_()  # all-zero matrix: zero pivot at row 0
+    S, vals, b, x = items[6]  # the 11^3 grid
+    bad_row = 700
+    rp = host[6][0]
+    vals[int(rp[bad_row].item()) + 1] = float("nan")
     B = P.BatchSolve(items, restart=30, rtol=1e-8)
+    if sched is not None:
+        B.set_schedule(*sched)
     B.solve()
     res = B.results()
-    assert res[2].status == 4 and res[2].row == 0
-    assert all(r.status == 0 for i, r in enumerate(res) if i != 2)
+    assert res[2].status == L.EZEROPIVOT and res[2].row == 0
+    assert res[6].status == L.ENONFINITE and res[6].row == bad_row
+    assert all(r.status == 0 for i, r in enumerate(res) if i not in (2, 6))
 
 
 def adjoint_setup(N=12, k=2):
