@@ -73,6 +73,9 @@ def parse():
                          "suite: every phase of every single-system configuration")
     ap.add_argument("--nsets", type=int, default=512)
     ap.add_argument("--ngrids", type=int, default=64)
+    ap.add_argument("--batch-schedule", default="auto",
+                    help="batched: 'auto' (the autotuner) or WIDTH/spin or WIDTH/level, "
+                         "e.g. 512/spin, fixed before the first solve")
     return ap.parse_args()
 
 
@@ -504,6 +507,9 @@ def batched(args):
         torch.cuda.synchronize()
 
     B = P.BatchSolve(items, restart=30, rtol=1e-8)
+    if args.batch_schedule != "auto":
+        width, kind = args.batch_schedule.split("/")
+        B.set_schedule(int(width), kind == "spin")
     for _ in range(max(args.warmup, 1)):
         B.solve()
     barrier()
