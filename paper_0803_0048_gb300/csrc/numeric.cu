@@ -800,13 +800,15 @@ static cudaError_t launch_numeric_impl(const iluk_sym *S, int64_t nbatch, const 
   // the forward level order, once built, is a valid and better-spread order
   const int32_t *order = S->levels_built ? S->lord.corder : nullptr;
   ProfScope prof_scope(ILUK_PROF_NUMERIC, s);
+  const bool wide = order != nullptr && S->n >= kWideLevelRows * (int64_t)S->lord.nlev;
   // rows publish their entries as soon as final (see apply_pivots) where F's
-  // rows are long; on short rows (grids) that measured slower
-  const bool early = S->nnz >= kEarlyRowLen * S->n;
+  // rows are long or the DAG is narrow (the band matrices at k <= 1 gain
+  // 20-35 %); on wide level orders with short rows (3D grids) it measured
+  // 5-10 % slower
+  const bool early = S->nnz >= kEarlyRowLen * S->n || !wide;
   const auto kern = early ? k_numeric<true> : k_numeric<false>;
   int warps, map_cap;
   size_t smem;
-  const bool wide = order != nullptr && S->n >= kWideLevelRows * (int64_t)S->lord.nlev;
   const int cap = numeric_cap(S, early ? kStaticSmem : 0, wide, &warps, &map_cap, &smem);
   if (cap < 0) return cudaErrorMemoryAllocation;
   {
