@@ -33,6 +33,10 @@ constexpr size_t kStaticSmem = (kNumThreads / 32) * kTouchedWords * sizeof(unsig
 // entries early (random band, k = 2, 119 a row: 30.6 -> 25.8 ms; grids of 9 to
 // 61 a row lost 5-10 %).
 constexpr int64_t kEarlyRowLen = 80;
+// Entries of L per forward level below which the refactorization publishes
+// early whatever the row length (band matrices: 560-830 a level; 3D grids:
+// 4,000-19,000).
+constexpr int64_t kEarlyLevelEntries = 2000;
 // Sixteenths of the fused factorization's CTAs that run the symbolic walk:
 // few with the level-map walk, which keeps ahead of the numeric rows easily;
 // more with the sorted-list walk of wide matrices, which is slower per row.
@@ -802,10 +806,12 @@ static cudaError_t launch_numeric_impl(const iluk_sym *S, int64_t nbatch, const 
   ProfScope prof_scope(ILUK_PROF_NUMERIC, s);
   const bool wide = order != nullptr && S->n >= kWideLevelRows * (int64_t)S->lord.nlev;
   // rows publish their entries as soon as final (see apply_pivots) where F's
-  // rows are long or the DAG is narrow (the band matrices at k <= 1 gain
-  // 20-35 %); on wide level orders with short rows (3D grids) it measured
-  // 5-10 % slower
-  const bool early = S->nnz >= kEarlyRowLen * S->n || !wide;
+  // rows are long, or where a level holds few entries of L (fewer than
+  // kEarlyLevelEntries: the band matrices at k <= 1 gain 15-35 %), or before
+  // the level orders exist; on grids, whose levels hold thousands of short
+  // rows' entries (3D 7- and 27-point stencils), it measured 5-10 % slower
+  const bool early = S->nnz >= kEarlyRowLen * S->n || order == nullptr ||
+                     (S->nnz - S->n) / 2 < kEarlyLevelEntries * (int64_t)S->lord.nlev;
   const auto kern = early ? k_numeric<true> : k_numeric<false>;
   int warps, map_cap;
   size_t smem;
