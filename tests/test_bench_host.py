@@ -1,6 +1,7 @@
 """Host-side parts of the benchmark on CPU: the oracle baseline it prints
-(timed steps, parity fields, host description) and the CPU description read
-from /proc/cpuinfo on both kinds of host."""
+(timed steps, parity fields, host description), the CPU description read
+from /proc/cpuinfo on both kinds of host, and the DRAM traffic it takes from
+the committed ncu summary only while the sweep sources match its stamp."""
 import json
 import os
 import sys
@@ -88,3 +89,32 @@ def test_bench_line_contract_with_stand_ins():
                                 "parallelism"}
     assert d["operand_stream"]["kernel"] == "factor"
     assert d["operand_stream"]["bytes_per_launch"] > 10 * d["kernels"]["factor"]["alg_bytes_per_launch"]
+
+
+def test_measured_traffic_only_while_the_sweep_sources_match(tmp_path, monkeypatch):
+    """The roofline's DRAM traffic comes from the committed ncu summary only
+    while the sweep kernels' sources are the ones it was captured on."""
+    import shutil
+    csrc = tmp_path / "paper_0803_0048_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    for f in ("sweeps.cu", "common.cuh"):
+        shutil.copy(os.path.join(bench.ROOT, "paper_0803_0048_gb300", "csrc", f), csrc / f)
+    (tmp_path / "profiles").mkdir()
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    digest = bench.sources_digest()
+    assert len(digest) == 16 and int(digest, 16) >= 0
+    prof = tmp_path / "profiles" / "sweep_band160k_k2.md"
+    prof.write_text("# summary\n"
+                    f"traffic: kernel=sweep_bwd k=2 bytes=123456 sources={digest}\n"
+                    f"traffic: kernel=sweep k=2 bytes=777 sources={digest}\n"
+                    "traffic: kernel=sweep_bwd k=3 bytes=999 sources=0000000000000000\n")
+    assert bench.measured_traffic("sweep_bwd", 2) == 123456
+    assert bench.measured_traffic("sweep", 2) == 777
+    assert bench.measured_traffic("sweep_bwd", 3) is None  # captured on other sources
+    assert bench.measured_traffic("factor", 2) is None     # no line for that kernel
+    with open(csrc / "sweeps.cu", "a") as fh:
+        fh.write("\n// changed\n")
+    assert bench.sources_digest() != digest
+    assert bench.measured_traffic("sweep_bwd", 2) is None  # the kernel changed since
+    prof.unlink()
+    assert bench.measured_traffic("sweep_bwd", 2) is None  # no summary at all
