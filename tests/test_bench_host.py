@@ -1,6 +1,7 @@
 """Host-side parts of the benchmark on CPU: the oracle baseline it prints
 (timed steps, parity fields, host description), the CPU description read
-from /proc/cpuinfo on both kinds of host, and the DRAM traffic it takes from
+from /proc/cpuinfo on both kinds of host, the clock samples it summarises, and
+the DRAM traffic it takes from
 the committed ncu summary only while the sweep sources match its stamp."""
 import json
 import os
@@ -118,3 +119,24 @@ def test_measured_traffic_only_while_the_sweep_sources_match(tmp_path, monkeypat
     assert bench.measured_traffic("sweep_bwd", 2) is None  # the kernel changed since
     prof.unlink()
     assert bench.measured_traffic("sweep_bwd", 2) is None  # no summary at all
+
+
+def test_clock_sampler_summary_parses_nvidia_smi_rows():
+    """The clocks object of the bench line: median SM clock under load, the
+    maximum clock, and every throttle reason seen active; malformed rows (a
+    header, a short row, "[N/A]" values) are skipped."""
+    c = bench.ClockSampler(0)
+    assert c.summary() == {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+    c.lines = [
+        "clocks.current.sm [MHz], clocks.max.sm [MHz], power.draw [W], ...",
+        "2070, 2070, 650.1, Not Active, Not Active, Not Active, Not Active",
+        "2055, 2070, 1390.5, Not Active, Not Active, Not Active, Active",
+        "1995, 2070, 1400.0, Not Active, Not Active, Not Active, Active",
+        "[N/A], 2070, 10.0, Not Active, Not Active, Not Active, Not Active",
+        "2070, 2070",
+        "2070, 2070, 700.0, Active, Not Active, Not Active, Not Active",
+    ]
+    s = c.summary()
+    assert s["samples"] == 4
+    assert s["sm_mhz"] == 2062.5 and s["sm_max_mhz"] == 2070.0
+    assert s["reasons"] == ["hw_slowdown", "sw_power_cap"]
