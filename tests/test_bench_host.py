@@ -1,8 +1,8 @@
 """Host-side parts of the benchmark on CPU: the oracle baseline it prints
 (timed steps, parity fields, host description), the CPU description read
-from /proc/cpuinfo on both kinds of host, the clock samples it summarises, and
-the DRAM traffic it takes from
-the committed ncu summary only while the sweep sources match its stamp."""
+from /proc/cpuinfo on both kinds of host, the clock samples it summarises,
+and the DRAM traffic it takes from the committed ncu summary only while the
+sweep sources match its stamp."""
 import json
 import os
 import sys
