@@ -505,8 +505,11 @@ class BatchSolve:
 
     ``items`` is a list of (Symbolic, a_vals, b, x) with device tensors; the
     x tensors receive the solutions.  ``solve()`` only enqueues work (it can be
-    captured in a CUDA graph after a first call outside the capture);
-    ``results()`` synchronizes and returns one Info per item."""
+    captured in a CUDA graph after a first call outside the capture); the
+    first call outside a capture times the schedules and keeps the fastest
+    (see ``set_schedule``).  The kernel takes the items largest first;
+    ``results()`` synchronizes and returns one Info per item, in the order
+    of ``items``."""
 
     def __init__(self, items, restart=30, rtol=1e-8, maxit=10000):
         self.items = list(items)  # keep the tensors alive
