@@ -95,7 +95,10 @@ def validate(rowptr: torch.Tensor, colind: torch.Tensor) -> Tuple[int, int]:
 
 
 class Symbolic:
-    """Result of the symbolic phase (pattern of F = L~ + U~ and levels)."""
+    """Result of the symbolic phase (pattern of F = L~ + U~ and levels).  It
+    also keeps, for its pattern, the sweep schedules the autotuner picked on
+    the first solve (and on the first transposed solve), which later
+    factorizations of the pattern reuse."""
 
     def __init__(self, handle, A: CsrPattern, k: int):
         self.h = handle
